@@ -1,0 +1,343 @@
+"""FP64 CPU oracle for the complex-valued holographic Gaussian renderer.
+
+TEST INFRASTRUCTURE ONLY: only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  It shares no code
+with the CUDA path (``paper_2506_08350_b300``) and never imports it.
+
+What each function follows (arXiv 2506.08350):
+
+* ``project``            Sec. 3 (Eq. gaussian_density, gaussian_decompose,
+                         gaussian_projection, gaussian_projection_2d) and the
+                         plane argmax of Eq. hard_assignment;
+* ``composite``          the per-plane complex field of Sec. 4.1 and
+                         Algorithm 2 (per-pixel walk in depth order);
+* ``transfer_function``  Eq. band_limited_asm_transfer_function;
+* ``propagate_planes``   Eq. layer2plane_asm and Eq. sum_planes (the plane sum
+                         is taken literally, after each inverse transform);
+* ``inverse_propagate``  Eq. plane2layer_asm, intensity I_l = |U|^2;
+* ``focal_stack_loss``   Eq. recon_loss (mean over planes, channels, pixels);
+* ``render_backward``    Supp. D.4, re-derived in reverse mode (C code);
+* ``adam_step``          Adam (the optimiser the full training step uses);
+* ``mlp_*``              the learned-initialisation network (no counterpart in
+                         the paper): plain float64 matrix products.
+
+The FFT is numpy's (a library primitive); everything else is plain loops in
+``hcgs_oracle.c`` or direct numpy expressions of the equations.
+
+Pins (closed forms, invariants, brute force) live in ``tests/test_oracle_*.py``.
+The paper prints no numeric worked example, so agreement with numbers the paper
+prints is "parity unpinned"; every pin comes from mathematics instead.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hcgs_oracle.c")
+_SO = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+DEFAULT_OPTS = dict(alpha_min=1.0 / 255.0, alpha_max=0.99, T_eps=1e-4, dilation=0.3,
+                    near_z=0.2, clip=1.3, order=0, tau=1e-3)
+# "exact" preset: no thresholds, no dilation, no clamp; support = whole grid.
+EXACT_OPTS = dict(alpha_min=0.0, alpha_max=1.0, T_eps=0.0, dilation=0.0,
+                  near_z=0.2, clip=0.0, order=0, tau=1e-3)
+
+
+def build() -> str:
+    """Compile the C part of the oracle (gcc, -O2, OpenMP)."""
+    os.makedirs(os.path.dirname(_SO), exist_ok=True)
+    if (not os.path.exists(_SO)) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _L():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_SO)
+            d = ctypes.POINTER(ctypes.c_double)
+            i = ctypes.POINTER(ctypes.c_int)
+            I = ctypes.c_int
+            lib.oracle_project.argtypes = [I, I, I, I, I] + [d] * 7 + [d, d, d] + [d, d, d, d, d, i, d, d, i]
+            lib.oracle_project.restype = None
+            lib.oracle_composite.argtypes = [I] * 5 + [d, d, d, d, i, d, d, i, d, I, I, d, d, i]
+            lib.oracle_composite.restype = None
+            lib.oracle_composite_backward.argtypes = [I] * 5 + [d, d, d, d, i, d, d, i, d, I, I, d, d, d, d, d]
+            lib.oracle_composite_backward.restype = None
+            lib.oracle_project_backward.argtypes = [I] * 5 + [d] * 7 + [d, d, d] + [d, d, d, d] + [d] * 7
+            lib.oracle_project_backward.restype = None
+            lib.oracle_sort.argtypes = [I, d, i, I, i]
+            lib.oracle_sort.restype = I
+            _lib = lib
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _ip(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _opt_vec(opts):
+    o = dict(DEFAULT_OPTS)
+    o.update(opts or {})
+    return np.array([o["alpha_min"], o["alpha_max"], o["T_eps"], o["dilation"], o["near_z"],
+                     o["clip"], float(o["order"]), o["tau"]], dtype=np.float64)
+
+
+PARAM_NAMES = ("means", "log_scales", "quats", "opacity_logits", "amplitude", "phase", "plane_logits")
+
+
+def _params64(g):
+    return {k: _f64(g[k]) for k in PARAM_NAMES}
+
+
+# ----------------------------------------------------------------------------
+# projection and compositing (C, FP64)
+# ----------------------------------------------------------------------------
+def project(gauss: dict, viewmat, intr, H: int, W: int, opts=None) -> dict:
+    """Per-Gaussian screen-space quantities for one view (Sec. 3, Eq.
+    gaussian_projection / gaussian_projection_2d; Eq. hard_assignment)."""
+    p = _params64(gauss)
+    N = p["means"].shape[0]
+    L = p["plane_logits"].shape[1]
+    C = p["amplitude"].shape[1]
+    out = dict(mu=np.zeros((N, 2)), conic=np.zeros((N, 3)), cov=np.zeros((N, 3)), opac=np.zeros(N),
+               depth=np.zeros(N), plane=np.zeros(N, dtype=np.int32), w=np.zeros((N, C, 2)),
+               bbox=np.zeros((N, 4)), valid=np.zeros(N, dtype=np.int32))
+    vm, it, ov = _f64(viewmat).reshape(16), _f64(intr).reshape(4), _opt_vec(opts)
+    _L().oracle_project(N, L, C, H, W, *[_dp(p[k]) for k in PARAM_NAMES], _dp(vm), _dp(it), _dp(ov),
+                        _dp(out["mu"]), _dp(out["conic"]), _dp(out["cov"]), _dp(out["opac"]),
+                        _dp(out["depth"]), _ip(out["plane"]), _dp(out["w"]), _dp(out["bbox"]),
+                        _ip(out["valid"]))
+    out.update(N=N, L=L, C=C, H=H, W=W)
+    return out
+
+
+def visiting_order(proj: dict, order: int = 0) -> np.ndarray:
+    N = proj["N"]
+    out = np.zeros(N, dtype=np.int32)
+    m = _L().oracle_sort(N, _dp(proj["depth"]), _ip(proj["valid"]), int(order), _ip(out))
+    return out[:m]
+
+
+def composite(proj: dict, opts=None, rows=None):
+    """Complex per-plane fields U[L][C][H][W] (complex128), final
+    transmittance T[L][H][W] and contributor counts for one view."""
+    N, L, C, H, W = (proj[k] for k in ("N", "L", "C", "H", "W"))
+    r0, r1 = (0, H) if rows is None else rows
+    U = np.zeros((L, C, H, W, 2))
+    T = np.ones((L, H, W))
+    nc = np.zeros((L, H, W), dtype=np.int32)
+    ov = _opt_vec(opts)
+    _L().oracle_composite(N, L, C, H, W, _dp(proj["mu"]), _dp(proj["conic"]), _dp(proj["opac"]),
+                          _dp(proj["depth"]), _ip(proj["plane"]), _dp(proj["w"]), _dp(proj["bbox"]),
+                          _ip(proj["valid"]), _dp(ov), int(r0), int(r1), _dp(U), _dp(T), _ip(nc))
+    return U[..., 0] + 1j * U[..., 1], T, nc
+
+
+def composite_backward(proj: dict, gU, opts=None):
+    """Adjoint of ``composite``: per-Gaussian gradients w.r.t. mu, conic
+    (A, B, C), the activated opacity and w (= c e^{j phi}, as Re/Im)."""
+    N, L, C, H, W = (proj[k] for k in ("N", "L", "C", "H", "W"))
+    g = np.ascontiguousarray(np.stack([np.real(gU), np.imag(gU)], axis=-1), dtype=np.float64)
+    out = dict(mu=np.zeros((N, 2)), conic=np.zeros((N, 3)), opac=np.zeros(N), w=np.zeros((N, C, 2)))
+    ov = _opt_vec(opts)
+    _L().oracle_composite_backward(N, L, C, H, W, _dp(proj["mu"]), _dp(proj["conic"]), _dp(proj["opac"]),
+                                   _dp(proj["depth"]), _ip(proj["plane"]), _dp(proj["w"]), _dp(proj["bbox"]),
+                                   _ip(proj["valid"]), _dp(ov), 0, H, _dp(g),
+                                   _dp(out["mu"]), _dp(out["conic"]), _dp(out["opac"]), _dp(out["w"]))
+    return out
+
+
+def project_backward(gauss: dict, viewmat, intr, H, W, g2d: dict, opts=None, acc=None) -> dict:
+    """Adjoint of ``project`` (plus the straight-through plane-logit rule of
+    Eq. ste), accumulated into ``acc`` (float64 arrays keyed like the params)."""
+    p = _params64(gauss)
+    N = p["means"].shape[0]
+    L = p["plane_logits"].shape[1]
+    C = p["amplitude"].shape[1]
+    if acc is None:
+        acc = {k: np.zeros_like(p[k]) for k in PARAM_NAMES}
+    vm, it, ov = _f64(viewmat).reshape(16), _f64(intr).reshape(4), _opt_vec(opts)
+    _L().oracle_project_backward(N, L, C, H, W, *[_dp(p[k]) for k in PARAM_NAMES], _dp(vm), _dp(it), _dp(ov),
+                                 _dp(g2d["mu"]), _dp(g2d["conic"]), _dp(g2d["opac"]), _dp(g2d["w"]),
+                                 *[_dp(acc[k]) for k in PARAM_NAMES])
+    return acc
+
+
+# ----------------------------------------------------------------------------
+# band-limited angular spectrum method (numpy FFT, FP64)
+# ----------------------------------------------------------------------------
+def frequencies(n: int, pitch: float) -> np.ndarray:
+    """Spatial frequencies of DFT bins in FFT order: k/(n pitch) for
+    k = 0..ceil(n/2)-1, then -floor(n/2)..-1."""
+    k = np.arange(n)
+    k = np.where(k < (n + 1) // 2, k, k - n)
+    return k / (n * pitch)
+
+
+def transfer_function(H: int, W: int, pitch: float, wavelength: float, z: float) -> np.ndarray:
+    """H_z(f_x, f_y) of Eq. band_limited_asm_transfer_function on the H x W
+    grid in FFT order: exp(j 2 pi z sqrt(1/lambda^2 - f^2)) inside
+    f^2 <= 1/lambda^2, zero outside."""
+    fx = frequencies(W, pitch)[None, :]
+    fy = frequencies(H, pitch)[:, None]
+    arg = 1.0 / wavelength ** 2 - (fx ** 2 + fy ** 2)
+    inside = arg >= 0
+    phase = 2.0 * np.pi * z * np.sqrt(np.where(inside, arg, 0.0))
+    return np.where(inside, np.exp(1j * phase), 0.0)
+
+
+def propagate(u: np.ndarray, pitch: float, wavelength: float, z: float) -> np.ndarray:
+    """One field through Eq. layer2plane_asm: IDFT(H_z DFT(u))."""
+    Hz = transfer_function(u.shape[-2], u.shape[-1], pitch, wavelength, z)
+    return np.fft.ifft2(Hz * np.fft.fft2(u))
+
+
+def propagate_planes(U: np.ndarray, pitch: float, wavelengths, plane_z) -> np.ndarray:
+    """Eq. layer2plane_asm for every plane, then Eq. sum_planes.
+    U[L][C][H][W] -> P[C][H][W]."""
+    L, C = U.shape[0], U.shape[1]
+    P = np.zeros(U.shape[1:], dtype=np.complex128)
+    for c in range(C):
+        for l in range(L):
+            P[c] += propagate(U[l, c], pitch, wavelengths[c], plane_z[l])
+    return P
+
+
+def propagate_planes_adjoint(gP: np.ndarray, pitch: float, wavelengths, plane_z) -> np.ndarray:
+    """Adjoint of ``propagate_planes`` for g = dL/dRe + j dL/dIm:
+    gU_l = IDFT(conj(H_{Z_l}) DFT(gP)).  (With F the unnormalised DFT,
+    (F^-1 D F)^H = F^-1 conj(D) F.)"""
+    C, H, W = gP.shape
+    L = len(plane_z)
+    gU = np.zeros((L, C, H, W), dtype=np.complex128)
+    for c in range(C):
+        G = np.fft.fft2(gP[c])
+        for l in range(L):
+            Hz = transfer_function(H, W, pitch, wavelengths[c], plane_z[l])
+            gU[l, c] = np.fft.ifft2(np.conj(Hz) * G)
+    return gU
+
+
+def inverse_propagate(P: np.ndarray, pitch: float, wavelengths, plane_z) -> np.ndarray:
+    """Eq. plane2layer_asm: V_l = IDFT(H_{-Z_l} DFT(P)), P[C][H][W] -> V[L][C][H][W]."""
+    C, H, W = P.shape
+    L = len(plane_z)
+    V = np.zeros((L, C, H, W), dtype=np.complex128)
+    for c in range(C):
+        S = np.fft.fft2(P[c])
+        for l in range(L):
+            V[l, c] = np.fft.ifft2(transfer_function(H, W, pitch, wavelengths[c], -plane_z[l]) * S)
+    return V
+
+
+def focal_stack_loss(P: np.ndarray, I_gt: np.ndarray, pitch: float, wavelengths, plane_z):
+    """Eq. recon_loss with the mean taken over planes, channels and pixels:
+    returns (loss, dL/dP as g = dL/dRe + j dL/dIm, intensities I[L][C][H][W])."""
+    V = inverse_propagate(P, pitch, wavelengths, plane_z)
+    I = np.abs(V) ** 2
+    n = I.size
+    loss = float(np.mean((I - I_gt) ** 2))
+    gV = (4.0 / n) * (I - I_gt) * V
+    C, H, W = P.shape
+    gP = np.zeros((C, H, W), dtype=np.complex128)
+    for c in range(C):
+        for l in range(len(plane_z)):
+            # adjoint of V_l = IDFT(conj-side transfer H_{-Z} DFT(P))
+            Hm = transfer_function(H, W, pitch, wavelengths[c], -plane_z[l])
+            gP[c] += np.fft.ifft2(np.conj(Hm) * np.fft.fft2(gV[l, c]))
+    return loss, gP, I
+
+
+# ----------------------------------------------------------------------------
+# whole view(s)
+# ----------------------------------------------------------------------------
+def render(gauss: dict, viewmats, intrs, optics, opts=None):
+    """Hologram P[V][C][H][W] and plane fields U[V][L][C][H][W] for V views."""
+    viewmats = np.asarray(viewmats).reshape(-1, 4, 4)
+    intrs = np.asarray(intrs).reshape(-1, 4)
+    Ps, Us, Ts, Ns = [], [], [], []
+    for v in range(viewmats.shape[0]):
+        pr = project(gauss, viewmats[v], intrs[v], optics.H, optics.W, opts)
+        U, T, nc = composite(pr, opts)
+        Ps.append(propagate_planes(U, optics.pitch, optics.wavelengths, optics.plane_z))
+        Us.append(U); Ts.append(T); Ns.append(nc)
+    return np.stack(Ps), np.stack(Us), np.stack(Ts), np.stack(Ns)
+
+
+def render_backward(gauss: dict, viewmats, intrs, optics, gP, opts=None) -> dict:
+    """dL/dparams (float64) for the loss Re<gP, P> summed over views."""
+    viewmats = np.asarray(viewmats).reshape(-1, 4, 4)
+    intrs = np.asarray(intrs).reshape(-1, 4)
+    acc = None
+    for v in range(viewmats.shape[0]):
+        pr = project(gauss, viewmats[v], intrs[v], optics.H, optics.W, opts)
+        gU = propagate_planes_adjoint(np.asarray(gP[v]), optics.pitch, optics.wavelengths, optics.plane_z)
+        g2d = composite_backward(pr, gU, opts)
+        acc = project_backward(gauss, viewmats[v], intrs[v], optics.H, optics.W, g2d, opts, acc)
+    return acc
+
+
+def loss_re_inner(P: np.ndarray, gP: np.ndarray) -> float:
+    """Scalar Re<gP, P> = sum Re(conj(gP) P): its gradient w.r.t. P in the
+    convention g = dL/dRe + j dL/dIm is gP itself."""
+    return float(np.sum(np.real(np.conj(gP) * P)))
+
+
+# ----------------------------------------------------------------------------
+# optimiser and learned-initialisation network
+# ----------------------------------------------------------------------------
+def adam_step(p, g, m, v, step: int, lr: float, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba), bias-corrected; returns new (p, m, v)."""
+    p, g, m, v = (np.asarray(x, dtype=np.float64) for x in (p, g, m, v))
+    m = beta1 * m + (1 - beta1) * g
+    v = beta2 * v + (1 - beta2) * g * g
+    mh = m / (1 - beta1 ** step)
+    vh = v / (1 - beta2 ** step)
+    return p - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+def mlp_forward(x, Ws, bs):
+    """ReLU MLP: h_0 = x, h_{k+1} = relu(h_k W_k^T + b_k) except the last layer
+    (linear).  Returns the output and the list of pre-activations."""
+    h = np.asarray(x, dtype=np.float64)
+    pre = []
+    for k, (Wk, bk) in enumerate(zip(Ws, bs)):
+        z = h @ np.asarray(Wk, dtype=np.float64).T + np.asarray(bk, dtype=np.float64)
+        pre.append((h, z))
+        h = np.maximum(z, 0.0) if k < len(Ws) - 1 else z
+    return h, pre
+
+
+def mlp_backward(x, Ws, bs, gy):
+    """Reverse mode of ``mlp_forward``: (dL/dW_k, dL/db_k, dL/dx)."""
+    _, pre = mlp_forward(x, Ws, bs)
+    g = np.asarray(gy, dtype=np.float64)
+    gW, gb = [None] * len(Ws), [None] * len(Ws)
+    for k in range(len(Ws) - 1, -1, -1):
+        h, z = pre[k]
+        if k < len(Ws) - 1:
+            g = g * (z > 0)
+        gW[k] = g.T @ h
+        gb[k] = g.sum(axis=0)
+        g = g @ np.asarray(Ws[k], dtype=np.float64)
+    return gW, gb, g
