@@ -1,0 +1,255 @@
+/*
+ * hcgs.h — C ABI of libhcgs, the B300 (sm_103a) implementation of the
+ * hologram render path of "Complex-Valued Holographic Radiance Fields"
+ * (arXiv 2506.08350).
+ *
+ * The path renders, for each view, a complex hologram P (Sec. 3, problem
+ * statement: P in C^{nx x ny}, pose r, pixel pitch dx) from N complex-valued
+ * 3D Gaussians in four steps:
+ *   1. project      (Sec. 3 Eq. gaussian_projection / gaussian_projection_2d,
+ *                    Eq. hard_assignment)                      -> hcgs_project
+ *   2. depth-sort and bin into 16x16 tiles per plane (Sec. 4.2,
+ *                    Algorithm 2 preprocessing)               -> hcgs_project
+ *   3. composite complex footprints into L plane fields (Sec. 4.1 per-plane
+ *                    field equation, Algorithm 2)             -> hcgs_rasterize_planes
+ *   4. propagate each plane by the band-limited angular spectrum method and
+ *                    sum (Eq. band_limited_asm_transfer_function,
+ *                    Eq. layer2plane_asm, Eq. sum_planes)     -> hcgs_asm_propagate
+ * hcgs_render_view runs all four.  Every step has a _backward twin (Supp.
+ * D.4, Eq. ste).  The training-step pieces are hcgs_focal_stack_loss
+ * (Eq. plane2layer_asm, Eq. recon_loss) and hcgs_adam_step; the learned
+ * initialisation network is hcgs_mlp_forward / hcgs_mlp_backward.
+ *
+ * Conventions (all entry points):
+ *  - Memory: every array argument marked "device" is a device pointer owned
+ *    by the caller; arrays marked "host" are host memory read during the call.
+ *    The library allocates device memory only for its own scratch (the
+ *    context workspace and the buffers held by an hcgs_saved), grows it on
+ *    demand, and frees it in hcgs_saved_release / hcgs_ctx_destroy.
+ *  - Streams: `stream` is a cudaStream_t (NULL = legacy default stream).
+ *    Work is enqueued asynchronously.  hcgs_project synchronises `stream`
+ *    once to read the number of tile instances (it sizes the instance list).
+ *  - Complex numbers are interleaved (re, im) float pairs, i.e. the layout of
+ *    torch.complex64.  An upstream gradient of a real loss w.r.t. a complex
+ *    array z is passed as g = dL/dRe(z) + j dL/dIm(z) (Supp. D.4 uses the
+ *    separate dL/dreal, dL/dimag).
+ *  - Units: metres for wavelengths, pitch, plane distances, means and scales;
+ *    pixels for intrinsics.  Pixel (row i, col j) has its centre at x = j,
+ *    y = i.  Camera axes: x right, y down, z forward (world -> camera 4x4,
+ *    row-major).
+ *  - Errors: every call returns an hcgs_status; no exception crosses the ABI.
+ *    Arguments are validated before any launch.  CUDA errors map to
+ *    HCGS_ERR_CUDA and the message is kept for hcgs_last_error.
+ *  - A context is not thread-safe; use one context per host thread/stream.
+ */
+#ifndef HCGS_H
+#define HCGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HCGS_OK = 0,
+    HCGS_ERR_INVALID_ARG = -1,     /* null pointer, bad size, bad option            */
+    HCGS_ERR_CUDA = -2,            /* a CUDA runtime call failed                    */
+    HCGS_ERR_CAPACITY = -3,        /* scratch could not be allocated                */
+    HCGS_ERR_UNSUPPORTED_SIZE = -4,/* FFT length with a prime factor other than 2,3,5,
+                                      or larger than 4096                           */
+    HCGS_ERR_DEVICE_CHECK = -5,    /* a kernel's own bounds check fired             */
+    HCGS_ERR_TIMEOUT = -6,         /* reserved: a bounded device wait ran out       */
+    HCGS_ERR_STATE = -7            /* saved state missing or from another shape     */
+} hcgs_status;
+
+typedef struct hcgs_ctx hcgs_ctx;     /* scratch workspace, transfer-function cache */
+typedef struct hcgs_saved hcgs_saved; /* forward state that the backward reuses     */
+
+/* Hologram-plane sampling and depth planes (Sec. 3 problem statement:
+ * q = (r, dx, nx, ny); Sec. 4.1 layer construction: L planes parallel to the
+ * hologram, each sampled on the hologram grid). */
+typedef struct {
+    int H, W;                 /* ny, nx: rows and columns of every plane        */
+    int C;                    /* number of wavelengths (colour channels), 1..4  */
+    int L;                    /* number of depth planes, 1..16                  */
+    double pitch_x, pitch_y;  /* pixel pitch (m)                                */
+    const double* wavelength; /* host [C] (m)                                   */
+    const double* plane_z;    /* host [L] (m): Z_l, distance plane l -> hologram */
+    int band_limit;           /* must be 0: Eq. band_limited_asm_transfer_function
+                                 (evanescent cut f^2 <= 1/lambda^2 only)        */
+} hcgs_optics;
+
+/* Rasterizer options.  Values the paper leaves unstated (Algorithm 2 names
+ * eps_plane and eps_T without values) default to the 3DGS constants. */
+typedef struct {
+    int tile;                 /* must be 16 (Sec. 4.2: 16x16 tiles)             */
+    float alpha_min;          /* skip a Gaussian at a pixel when alpha < this (1/255) */
+    float alpha_max;          /* alpha = min(alpha_max, o G) (0.99)             */
+    float T_eps;              /* stop a pixel once T < T_eps, after the add (1e-4) */
+    float cov2d_dilation;     /* added to the diagonal of Sigma' (0.3 px^2)     */
+    float near_z;             /* cull when camera-space z < near_z (0.2 m)      */
+    float clip_factor;        /* clamp of x/z, y/z in J (1.3; <= 0: no clamp)   */
+    float ste_tau;            /* softmax temperature of Eq. ste (1e-3)          */
+    int order;                /* 0 front-to-back (nearest first), 1 back-to-front */
+    int footprint;            /* 0 FP32 footprint; 1 FP16x2 footprint with FP32
+                                 accumulation                                   */
+    int rho_grad;             /* must be 0: only the assigned plane's rho gets
+                                 gradient                                      */
+} hcgs_raster_opts;
+
+/* Gaussian parameters k = (c, x, R, S, alpha, phi, rho') (Sec. 4.1), device,
+ * float32, structure of arrays. */
+typedef struct {
+    const float* means;          /* [N][3] world position (m)                    */
+    const float* log_scales;     /* [N][3] S = diag(exp(log_scales))             */
+    const float* quats;          /* [N][4] rotation (w, x, y, z), any norm > 0   */
+    const float* opacity_logits; /* [N]    alpha_base = sigmoid(logit)           */
+    const float* amplitude;      /* [N][C] c_n, wave amplitude per wavelength    */
+    const float* phase;          /* [N][C] phi_n (rad) per wavelength            */
+    const float* plane_logits;   /* [N][L] rho'_n; rho_n = OneHot(argmax rho'_n) */
+    int N;
+} hcgs_gaussians;
+
+/* Gradients w.r.t. the arrays of hcgs_gaussians, device float32, same shapes.
+ * Overwritten, or added to when `accumulate` is non-zero. */
+typedef struct {
+    float *means, *log_scales, *quats, *opacity_logits, *amplitude, *phase, *plane_logits;
+} hcgs_gaussian_grads;
+
+/* ---------------- context ---------------- */
+/* Creates a context on `device` (made current for the call). */
+hcgs_status hcgs_ctx_create(hcgs_ctx** ctx, int device);
+void hcgs_ctx_destroy(hcgs_ctx* ctx);
+const char* hcgs_status_string(hcgs_status s);
+/* Message of the last failing call on this context (empty if none). */
+const char* hcgs_last_error(hcgs_ctx* ctx);
+/* Bytes of device scratch the context and its saved states hold. */
+size_t hcgs_ctx_bytes(hcgs_ctx* ctx);
+/* Creates an empty forward state; hcgs_project and hcgs_render_view fill it
+ * and reuse its buffers when called again with the same handle. */
+hcgs_status hcgs_saved_create(hcgs_ctx* ctx, hcgs_saved** saved);
+hcgs_status hcgs_saved_release(hcgs_ctx* ctx, hcgs_saved* saved);
+
+/* Per-kernel timing.  While enabled, every kernel launch of this context is
+ * bracketed by two CUDA events on its stream.  hcgs_profile_summary waits
+ * for the recorded events, writes for up to `max` kernels (in first-launch
+ * order) the name (static strings owned by the library), the summed device
+ * time in ms and the number of launches, sets *n_out, and clears the record. */
+hcgs_status hcgs_profile_enable(hcgs_ctx* ctx, int on);
+hcgs_status hcgs_profile_summary(hcgs_ctx* ctx, int max, int* n_out, const char** names, double* ms,
+                                 int64_t* launches);
+
+/* ---------------- step 1+2: projection, depth sort, tile binning ---------------- */
+/* Projects the N Gaussians for V views (Eq. gaussian_projection:
+ * Sigma' = J W Sigma W^T J^T, mu = projection of the mean; Eq. hard_assignment
+ * for the plane), culls (z < near_z), sorts by camera-space depth (ties by
+ * index) and bins every Gaussian into the 16x16 tiles of its plane that its
+ * support {p : o G(p) >= alpha_min} can touch.
+ *   viewmats   device [V][4][4] world -> camera, row-major
+ *   intrinsics device [V][4]    (f_x, f_y, c_x, c_y) in pixels
+ * The result lives in `saved` (must come from hcgs_saved_create). */
+hcgs_status hcgs_project(hcgs_ctx* ctx, const hcgs_gaussians* g, int V, const float* viewmats,
+                         const float* intrinsics, const hcgs_optics* optics,
+                         const hcgs_raster_opts* opts, hcgs_saved* saved, void* stream);
+
+/* ---------------- step 3: complex multi-plane compositing ---------------- */
+/* Composites every plane of every view (Sec. 4.1 per-plane field equation;
+ * Algorithm 2): per pixel and plane, in depth order, alpha = min(alpha_max,
+ * o exp(-power)); skip if alpha < alpha_min; U += c e^{j phi} alpha T;
+ * T *= 1 - alpha; stop once T < T_eps.
+ *   U          device [V][L][C][H][W] complex64 (output)
+ *   T_final    device [V][L][H][W] float, nullable (output)
+ *   n_contrib  device [V][L][H][W] int32, nullable: number of Gaussians that
+ *              added to the pixel (output)
+ * Requires a prior hcgs_project on `saved`. */
+hcgs_status hcgs_rasterize_planes(hcgs_ctx* ctx, hcgs_saved* saved, float* U, float* T_final,
+                                  int32_t* n_contrib, void* stream);
+
+/* ---------------- step 4: band-limited ASM ---------------- */
+/* Two forms (B = batch of views; H_z of Eq. band_limited_asm_transfer_function,
+ * formed in FP64 and reduced mod 2 pi, applied in FP32; unnormalised forward
+ * DFT, 1/(H W) on the inverse; no padding):
+ *   sign = +1, reduce_planes = 1 (forward recording, Eq. layer2plane_asm +
+ *     Eq. sum_planes):  in [B][L][C][H][W] -> out [B][C][H][W],
+ *     out = sum_l IDFT(H_{Z_l} DFT(in_l))
+ *   sign = -1, reduce_planes = 0 (inverse propagation, Eq. plane2layer_asm):
+ *     in [B][C][H][W] -> out [B][L][C][H][W], out_l = IDFT(H_{-Z_l} DFT(in))
+ * `in` is not modified; `out` must not alias `in`. */
+hcgs_status hcgs_asm_propagate(hcgs_ctx* ctx, const float* in, int B, const hcgs_optics* optics,
+                               int sign, int reduce_planes, float* out, void* stream);
+/* Adjoint of hcgs_asm_propagate with the same (sign, reduce_planes):
+ * g_out has the shape of `out`, g_in the shape of `in`; for the forward form
+ * g_in_l = IDFT(conj(H_{Z_l}) DFT(g_out)). */
+hcgs_status hcgs_asm_propagate_backward(hcgs_ctx* ctx, const float* g_out, int B,
+                                        const hcgs_optics* optics, int sign, int reduce_planes,
+                                        float* g_in, void* stream);
+
+/* ---------------- all four steps ---------------- */
+/*   hologram  device [V][C][H][W] complex64 (output)
+ *   planes    device [V][L][C][H][W] complex64, nullable (output of step 3)
+ *   saved     nullable: with a handle, the forward state is kept for
+ *             hcgs_render_view_backward; with NULL an internal one is used. */
+hcgs_status hcgs_render_view(hcgs_ctx* ctx, const hcgs_gaussians* g, int V, const float* viewmats,
+                             const float* intrinsics, const hcgs_optics* optics,
+                             const hcgs_raster_opts* opts, float* hologram, float* planes,
+                             hcgs_saved* saved, void* stream);
+
+/* ---------------- adjoints ---------------- */
+/* Adjoint of step 3 (Supp. D.4; backward walks each pixel's contributors in
+ * reverse and recovers T by division, Sec. 4.2).  gU device [V][L][C][H][W]
+ * complex64.  The per-Gaussian 2D gradients stay in `saved`. */
+hcgs_status hcgs_rasterize_planes_backward(hcgs_ctx* ctx, hcgs_saved* saved, const float* gU,
+                                           void* stream);
+/* Adjoint of steps 1-2 (Supp. D.4 chain to q, x, S, c, phi, alpha_base; Eq. ste
+ * for rho': dL/drho' = dL/drho * softmax(rho'/tau), elementwise).  Sums over
+ * the views of `saved`.  `g` must be the parameters hcgs_project saw. */
+hcgs_status hcgs_project_backward(hcgs_ctx* ctx, hcgs_saved* saved, const hcgs_gaussians* g,
+                                  const hcgs_gaussian_grads* grads, int accumulate, void* stream);
+/* Adjoint of hcgs_render_view: g_hologram device [V][C][H][W] complex64. */
+hcgs_status hcgs_render_view_backward(hcgs_ctx* ctx, hcgs_saved* saved, const hcgs_gaussians* g,
+                                      const float* g_hologram, const hcgs_gaussian_grads* grads,
+                                      int accumulate, void* stream);
+
+/* ---------------- training step ---------------- */
+/* Focal-stack intensity loss (Eq. plane2layer_asm, I_l = |U_{P->l}|^2,
+ * Eq. recon_loss as a mean over planes, channels and pixels):
+ *   hologram device [B][C][H][W] complex64
+ *   I_gt     device [B][L][C][H][W] float
+ *   loss     device float[1] (output)
+ *   g_hologram device [B][C][H][W] complex64, nullable: dL/dP (output)
+ *   I_out    device [B][L][C][H][W] float, nullable (output) */
+hcgs_status hcgs_focal_stack_loss(hcgs_ctx* ctx, const float* hologram, const float* I_gt, int B,
+                                  const hcgs_optics* optics, float* loss, float* g_hologram,
+                                  float* I_out, void* stream);
+/* One bias-corrected Adam update of n float32 parameters in place:
+ * m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2; p -= lr m^ / (sqrt(v^) + eps),
+ * m^ = m/(1-b1^step), v^ = v/(1-b2^step).  All arrays device [n]. */
+hcgs_status hcgs_adam_step(hcgs_ctx* ctx, float* p, const float* g, float* m, float* v, int64_t n,
+                           int step, float lr, float beta1, float beta2, float eps, void* stream);
+
+/* ---------------- learned initialisation network (no counterpart in the paper) ---------------- */
+/* 4-layer ReLU MLP, width 128, BF16 operands with FP32 accumulation:
+ * 16 -> 128 -> 128 -> 128 -> 16 (last layer linear).
+ *   x   device [N][16] bf16 (features: mean 3, log-scale 3, quaternion 4,
+ *       opacity logit 1, RGB 3, padding 2)
+ *   W1  device [128][16], W2, W3 [128][128], W4 [16][128] bf16 (row = output)
+ *   b1, b2, b3 device [128], b4 [16] float
+ *   y   device [N][16] float (output) */
+hcgs_status hcgs_mlp_forward(hcgs_ctx* ctx, const uint16_t* x, int N, const uint16_t* W1,
+                             const uint16_t* W2, const uint16_t* W3, const uint16_t* W4,
+                             const float* b1, const float* b2, const float* b3, const float* b4,
+                             float* y, void* stream);
+/* Reverse mode of hcgs_mlp_forward for upstream gy device [N][16] float.
+ * Writes (overwrites) gW1..gW4 (float, shapes of W1..W4) and gb1..gb4. */
+hcgs_status hcgs_mlp_backward(hcgs_ctx* ctx, const uint16_t* x, int N, const uint16_t* W1,
+                              const uint16_t* W2, const uint16_t* W3, const uint16_t* W4,
+                              const float* b1, const float* b2, const float* b3, const float* b4,
+                              const float* gy, float* gW1, float* gW2, float* gW3, float* gW4,
+                              float* gb1, float* gb2, float* gb3, float* gb4, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HCGS_H */

@@ -316,21 +316,40 @@ def adam_step(p, g, m, v, step: int, lr: float, beta1=0.9, beta2=0.999, eps=1e-8
     return p - lr * mh / (np.sqrt(vh) + eps), m, v
 
 
-def mlp_forward(x, Ws, bs):
+def round_bf16(a):
+    """Round float64 values to the nearest bfloat16 (ties to even), returned
+    as float64: the 8 high bits of the float32 significand are kept."""
+    f = np.asarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) >> 16 << 16
+    out = (u.astype(np.uint32)).view(np.float32).astype(np.float64)
+    return np.where(np.isnan(f), np.nan, out)
+
+
+def mlp_forward(x, Ws, bs, act_round=None):
     """ReLU MLP: h_0 = x, h_{k+1} = relu(h_k W_k^T + b_k) except the last layer
-    (linear).  Returns the output and the list of pre-activations."""
+    (linear).  ``act_round="bf16"`` rounds the hidden activations to bfloat16
+    before they feed the next layer (the network is defined with BF16
+    operands), so that the ReLU decisions are taken on the same values as on
+    the GPU.  Returns the output and the list of (layer input, pre-activation)."""
     h = np.asarray(x, dtype=np.float64)
     pre = []
     for k, (Wk, bk) in enumerate(zip(Ws, bs)):
         z = h @ np.asarray(Wk, dtype=np.float64).T + np.asarray(bk, dtype=np.float64)
         pre.append((h, z))
-        h = np.maximum(z, 0.0) if k < len(Ws) - 1 else z
+        if k < len(Ws) - 1:
+            h = np.maximum(z, 0.0)
+            if act_round == "bf16":
+                h = round_bf16(h)
+        else:
+            h = z
     return h, pre
 
 
-def mlp_backward(x, Ws, bs, gy):
-    """Reverse mode of ``mlp_forward``: (dL/dW_k, dL/db_k, dL/dx)."""
-    _, pre = mlp_forward(x, Ws, bs)
+def mlp_backward(x, Ws, bs, gy, act_round=None):
+    """Reverse mode of ``mlp_forward`` (the activation rounding passes the
+    gradient unchanged): (dL/dW_k, dL/db_k, dL/dx)."""
+    _, pre = mlp_forward(x, Ws, bs, act_round)
     g = np.asarray(gy, dtype=np.float64)
     gW, gb = [None] * len(Ws), [None] * len(Ws)
     for k in range(len(Ws) - 1, -1, -1):

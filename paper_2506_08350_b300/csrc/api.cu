@@ -1,0 +1,517 @@
+// C ABI of libhcgs: argument validation, scratch management and the
+// orchestration of the render path.  See include/hcgs.h for the contract.
+#include <cstring>
+
+#include "common.cuh"
+#include "project.cuh"
+
+using namespace hcgs;
+
+namespace hcgs {
+
+bool set_err(hcgs_ctx* ctx, hcgs_status s, const std::string& m) {
+    if (ctx) ctx->last_error = std::string(hcgs_status_string(s)) + ": " + m;
+    return false;
+}
+
+hcgs_status cuda_err(hcgs_ctx* ctx, cudaError_t e, const char* what) {
+    set_err(ctx, HCGS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    return HCGS_ERR_CUDA;
+}
+
+cudaError_t grow(hcgs_ctx* ctx, DevBuf& b, size_t bytes, size_t* owner_bytes) {
+    if (bytes <= b.cap) return cudaSuccess;
+    if (b.p) {
+        cudaError_t e = cudaFree(b.p);
+        if (e != cudaSuccess) return e;
+        *owner_bytes -= b.cap;
+        b.p = nullptr;
+        b.cap = 0;
+    }
+    const size_t want = bytes + bytes / 8;  // slack against small growth steps
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        e = cudaMalloc(&b.p, bytes);
+        if (e != cudaSuccess) return e;
+        b.cap = bytes;
+    } else {
+        b.cap = want;
+    }
+    *owner_bytes += b.cap;
+    (void)ctx;
+    return cudaSuccess;
+}
+
+void prof_begin(hcgs_ctx* ctx, const char* name, cudaStream_t st) {
+    if (!ctx || !ctx->prof.on) return;
+    Prof& P = ctx->prof;
+    if (P.used + 2 > P.pool.size()) {
+        for (int k = 0; k < 64; k++) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return;
+            P.pool.push_back(e);
+        }
+    }
+    ProfRec r{name, P.pool[P.used], P.pool[P.used + 1]};
+    P.used += 2;
+    cudaEventRecord(r.a, st);
+    P.recs.push_back(r);
+}
+
+void prof_end(hcgs_ctx* ctx, cudaStream_t st) {
+    if (!ctx || !ctx->prof.on || ctx->prof.recs.empty()) return;
+    cudaEventRecord(ctx->prof.recs.back().b, st);
+}
+
+static void free_buf(DevBuf& b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+}
+
+}  // namespace hcgs
+
+// ---------------------------------------------------------------------------
+// validation helpers
+// ---------------------------------------------------------------------------
+#define REQUIRE(ctx, cond, msg)                                   \
+    do {                                                          \
+        if (!(cond)) {                                            \
+            hcgs::set_err(ctx, HCGS_ERR_INVALID_ARG, msg);        \
+            return HCGS_ERR_INVALID_ARG;                          \
+        }                                                         \
+    } while (0)
+
+static hcgs_status check_optics(hcgs_ctx* ctx, const hcgs_optics* o) {
+    REQUIRE(ctx, o, "optics is NULL");
+    REQUIRE(ctx, o->H >= 1 && o->W >= 1, "H and W must be >= 1");
+    REQUIRE(ctx, o->C >= 1 && o->C <= MAX_C, "C must be in [1, 4]");
+    REQUIRE(ctx, o->L >= 1 && o->L <= MAX_L, "L must be in [1, 16]");
+    REQUIRE(ctx, o->pitch_x > 0 && o->pitch_y > 0, "pitch must be > 0");
+    REQUIRE(ctx, o->wavelength && o->plane_z, "wavelength and plane_z must be host arrays");
+    for (int c = 0; c < o->C; c++) REQUIRE(ctx, o->wavelength[c] > 0, "wavelengths must be > 0");
+    REQUIRE(ctx, o->band_limit == 0, "only band_limit = 0 (evanescent cut) is provided");
+    if (!fft_supported(o->H) || !fft_supported(o->W)) {
+        set_err(ctx, HCGS_ERR_UNSUPPORTED_SIZE, "H and W must be 2^a 3^b 5^c and <= 4096");
+        return HCGS_ERR_UNSUPPORTED_SIZE;
+    }
+    return HCGS_OK;
+}
+
+static hcgs_status check_opts(hcgs_ctx* ctx, const hcgs_raster_opts* r) {
+    REQUIRE(ctx, r, "opts is NULL");
+    REQUIRE(ctx, r->tile == 16, "tile must be 16");
+    REQUIRE(ctx, r->alpha_min >= 0.f && r->alpha_max <= 1.f && r->alpha_min < r->alpha_max,
+            "need 0 <= alpha_min < alpha_max <= 1");
+    REQUIRE(ctx, r->T_eps >= 0.f, "T_eps must be >= 0");
+    REQUIRE(ctx, r->near_z > 0.f, "near_z must be > 0");
+    REQUIRE(ctx, r->cov2d_dilation >= 0.f, "cov2d_dilation must be >= 0");
+    REQUIRE(ctx, r->ste_tau > 0.f, "ste_tau must be > 0");
+    REQUIRE(ctx, r->order == 0 || r->order == 1, "order must be 0 or 1");
+    REQUIRE(ctx, r->footprint == 0 || r->footprint == 1, "footprint must be 0 or 1");
+    REQUIRE(ctx, r->rho_grad == 0, "only rho_grad = 0 is provided");
+    return HCGS_OK;
+}
+
+static hcgs_status check_gauss(hcgs_ctx* ctx, const hcgs_gaussians* g) {
+    REQUIRE(ctx, g, "gaussians is NULL");
+    REQUIRE(ctx, g->N >= 0, "N must be >= 0");
+    if (g->N > 0)
+        REQUIRE(ctx, g->means && g->log_scales && g->quats && g->opacity_logits && g->amplitude && g->phase &&
+                         g->plane_logits,
+                "a Gaussian parameter array is NULL");
+    return HCGS_OK;
+}
+
+static cudaStream_t S(void* p) { return (cudaStream_t)p; }
+
+#define TRY(x)                        \
+    do {                              \
+        hcgs_status st__ = (x);       \
+        if (st__ != HCGS_OK) return st__; \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* hcgs_status_string(hcgs_status s) {
+    switch (s) {
+        case HCGS_OK: return "HCGS_OK";
+        case HCGS_ERR_INVALID_ARG: return "HCGS_ERR_INVALID_ARG";
+        case HCGS_ERR_CUDA: return "HCGS_ERR_CUDA";
+        case HCGS_ERR_CAPACITY: return "HCGS_ERR_CAPACITY";
+        case HCGS_ERR_UNSUPPORTED_SIZE: return "HCGS_ERR_UNSUPPORTED_SIZE";
+        case HCGS_ERR_DEVICE_CHECK: return "HCGS_ERR_DEVICE_CHECK";
+        case HCGS_ERR_TIMEOUT: return "HCGS_ERR_TIMEOUT";
+        case HCGS_ERR_STATE: return "HCGS_ERR_STATE";
+    }
+    return "HCGS_ERR_UNKNOWN";
+}
+
+hcgs_status hcgs_ctx_create(hcgs_ctx** out, int device) {
+    if (!out) return HCGS_ERR_INVALID_ARG;
+    *out = nullptr;
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) return HCGS_ERR_CUDA;
+    hcgs_ctx* c = new hcgs_ctx();
+    c->device = device;
+    if (cudaMalloc(&c->d_status, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&c->h_pinned, 64) != cudaSuccess) {
+        delete c;
+        return HCGS_ERR_CUDA;
+    }
+    cudaMemset(c->d_status, 0, sizeof(int));
+    *out = c;
+    return HCGS_OK;
+}
+
+static void saved_free(hcgs_saved* s) {
+    DevBuf* bufs[] = {&s->w, &s->proj, &s->rectn, &s->dkey, &s->dval, &s->nvalid, &s->rank, &s->sortid, &s->rec,
+                      &s->rects, &s->planes, &s->ccount, &s->bcount, &s->ikey, &s->ival, &s->hist, &s->scan,
+                      &s->Tfin, &s->last, &s->U, &s->g2d, &s->gU, &s->cam};
+    for (DevBuf* b : bufs) free_buf(*b);
+    s->bytes = 0;
+}
+
+void hcgs_ctx_destroy(hcgs_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    for (auto& b : ctx->ws) free_buf(b);
+    for (auto& kv : ctx->plans) cudaFree(kv.second.tw);
+    for (auto& kv : ctx->htab) free_buf(kv.second);
+    if (ctx->scratch_saved) {
+        saved_free(ctx->scratch_saved);
+        delete ctx->scratch_saved;
+    }
+    for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
+    cudaFree(ctx->d_status);
+    cudaFreeHost(ctx->h_pinned);
+    delete ctx;
+}
+
+hcgs_status hcgs_profile_enable(hcgs_ctx* ctx, int on) {
+    REQUIRE(ctx, ctx, "ctx is NULL");
+    ctx->prof.on = on != 0;
+    ctx->prof.recs.clear();
+    ctx->prof.used = 0;
+    return HCGS_OK;
+}
+
+hcgs_status hcgs_profile_summary(hcgs_ctx* ctx, int max, int* n_out, const char** names, double* ms,
+                                 int64_t* launches) {
+    REQUIRE(ctx, ctx && n_out, "NULL argument");
+    cudaSetDevice(ctx->device);
+    std::vector<std::string> order;
+    std::map<std::string, std::pair<double, int64_t>> agg;
+    for (const ProfRec& r : ctx->prof.recs) {
+        HCGS_CUDA(ctx, cudaEventSynchronize(r.b));
+        float t = 0.f;
+        HCGS_CUDA(ctx, cudaEventElapsedTime(&t, r.a, r.b));
+        auto it = agg.find(r.name);
+        if (it == agg.end()) {
+            order.push_back(r.name);
+            agg[r.name] = {t, 1};
+        } else {
+            it->second.first += t;
+            it->second.second += 1;
+        }
+    }
+    int n = 0;
+    for (const std::string& k : order) {
+        if (n >= max) break;
+        // names point at the string literals the launch sites pass
+        for (const ProfRec& r : ctx->prof.recs)
+            if (k == r.name) { names[n] = r.name; break; }
+        ms[n] = agg[k].first;
+        launches[n] = agg[k].second;
+        n++;
+    }
+    *n_out = n;
+    ctx->prof.recs.clear();
+    ctx->prof.used = 0;
+    return HCGS_OK;
+}
+
+const char* hcgs_last_error(hcgs_ctx* ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+size_t hcgs_ctx_bytes(hcgs_ctx* ctx) {
+    if (!ctx) return 0;
+    size_t b = ctx->bytes;
+    if (ctx->scratch_saved) b += ctx->scratch_saved->bytes;
+    return b;
+}
+
+hcgs_status hcgs_saved_create(hcgs_ctx* ctx, hcgs_saved** out) {
+    REQUIRE(ctx, ctx && out, "NULL argument");
+    *out = new hcgs_saved();
+    return HCGS_OK;
+}
+
+hcgs_status hcgs_saved_release(hcgs_ctx* ctx, hcgs_saved* s) {
+    if (!s) return HCGS_OK;
+    if (ctx) cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    saved_free(s);
+    delete s;
+    return HCGS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// steps
+// ---------------------------------------------------------------------------
+hcgs_status hcgs_project(hcgs_ctx* ctx, const hcgs_gaussians* g, int V, const float* viewmats,
+                         const float* intrinsics, const hcgs_optics* optics, const hcgs_raster_opts* opts,
+                         hcgs_saved* s, void* stream) {
+    if (!ctx) return HCGS_ERR_INVALID_ARG;
+    TRY(check_gauss(ctx, g));
+    TRY(check_optics(ctx, optics));
+    TRY(check_opts(ctx, opts));
+    REQUIRE(ctx, s, "saved is NULL");
+    REQUIRE(ctx, V >= 1, "V must be >= 1");
+    REQUIRE(ctx, viewmats && intrinsics, "viewmats / intrinsics is NULL");
+    cudaSetDevice(ctx->device);
+    s->V = V;
+    s->N = g->N;
+    s->C = optics->C;
+    s->L = optics->L;
+    s->H = optics->H;
+    s->W = optics->W;
+    s->tilesX = (optics->W + TILE - 1) / TILE;
+    s->tilesY = (optics->H + TILE - 1) / TILE;
+    s->ctX = (s->tilesX + COARSE - 1) / COARSE;
+    s->ctY = (s->tilesY + COARSE - 1) / COARSE;
+    s->opts = *opts;
+    s->optics = *optics;
+    s->lam.assign(optics->wavelength, optics->wavelength + optics->C);
+    s->z.assign(optics->plane_z, optics->plane_z + optics->L);
+    s->optics.wavelength = s->lam.data();
+    s->optics.plane_z = s->z.data();
+    s->valid = 0;
+    s->rastered = 0;
+    s->have_g2d = 0;
+    if ((uint64_t)V * optics->L * s->ctX * s->ctY >= (1ull << 32)) {
+        set_err(ctx, HCGS_ERR_CAPACITY, "too many buckets");
+        return HCGS_ERR_CAPACITY;
+    }
+    if (g->N == 0) {
+        // empty scene: every bucket is empty
+        const size_t NB = (size_t)V * s->L * s->ctX * s->ctY;
+        HCGS_CUDA(ctx, grow(ctx, s->bcount, (NB + 1) * sizeof(uint32_t), &s->bytes));
+        HCGS_CUDA(ctx, grow(ctx, s->ival, 8, &s->bytes));
+        HCGS_CUDA(ctx, cudaMemsetAsync(s->bcount.p, 0, (NB + 1) * sizeof(uint32_t), S(stream)));
+        s->list = (const uint32_t*)s->ival.p;
+        s->M = 0;
+    } else {
+        TRY(project_and_bin(ctx, s, g, viewmats, intrinsics, S(stream)));
+    }
+    s->valid = 1;
+    return HCGS_OK;
+}
+
+hcgs_status hcgs_rasterize_planes(hcgs_ctx* ctx, hcgs_saved* s, float* U, float* T_final, int32_t* n_contrib,
+                                  void* stream) {
+    if (!ctx) return HCGS_ERR_INVALID_ARG;
+    REQUIRE(ctx, s && U, "NULL argument");
+    if (!s->valid) {
+        set_err(ctx, HCGS_ERR_STATE, "hcgs_project has not run on this saved state");
+        return HCGS_ERR_STATE;
+    }
+    cudaSetDevice(ctx->device);
+    TRY(raster_forward(ctx, s, (float2*)U, T_final, n_contrib, S(stream)));
+    s->rastered = 1;
+    return HCGS_OK;
+}
+
+hcgs_status hcgs_asm_propagate(hcgs_ctx* ctx, const float* in, int B, const hcgs_optics* o, int sign,
+                               int reduce_planes, float* out, void* stream) {
+    if (!ctx) return HCGS_ERR_INVALID_ARG;
+    TRY(check_optics(ctx, o));
+    REQUIRE(ctx, in && out && in != out, "in/out must be distinct non-NULL device arrays");
+    REQUIRE(ctx, B >= 1, "B must be >= 1");
+    cudaSetDevice(ctx->device);
+    if (sign == 1 && reduce_planes == 1) return asm_sum(ctx, (const float2*)in, (float2*)out, B, o, false, S(stream));
+    if (sign == -1 && reduce_planes == 0)
+        return asm_spread(ctx, (const float2*)in, (float2*)out, B, o, true, S(stream));
+    set_err(ctx, HCGS_ERR_INVALID_ARG, "supported forms: (sign=+1, reduce_planes=1), (sign=-1, reduce_planes=0)");
+    return HCGS_ERR_INVALID_ARG;
+}
+
+hcgs_status hcgs_asm_propagate_backward(hcgs_ctx* ctx, const float* g_out, int B, const hcgs_optics* o, int sign,
+                                        int reduce_planes, float* g_in, void* stream) {
+    if (!ctx) return HCGS_ERR_INVALID_ARG;
+    TRY(check_optics(ctx, o));
+    REQUIRE(ctx, g_out && g_in && g_out != g_in, "g_out/g_in must be distinct non-NULL device arrays");
+    REQUIRE(ctx, B >= 1, "B must be >= 1");
+    cudaSetDevice(ctx->device);
+    // (F^-1 D F)^H = F^-1 conj(D) F, and conj(H_Z) = H_{-Z} inside the band
+    if (sign == 1 && reduce_planes == 1)
+        return asm_spread(ctx, (const float2*)g_out, (float2*)g_in, B, o, true, S(stream));
+    if (sign == -1 && reduce_planes == 0)
+        return asm_sum(ctx, (const float2*)g_out, (float2*)g_in, B, o, false, S(stream));
+    set_err(ctx, HCGS_ERR_INVALID_ARG, "supported forms: (sign=+1, reduce_planes=1), (sign=-1, reduce_planes=0)");
+    return HCGS_ERR_INVALID_ARG;
+}
+
+hcgs_status hcgs_render_view(hcgs_ctx* ctx, const hcgs_gaussians* g, int V, const float* viewmats,
+                             const float* intrinsics, const hcgs_optics* o, const hcgs_raster_opts* opts,
+                             float* hologram, float* planes, hcgs_saved* saved, void* stream) {
+    if (!ctx) return HCGS_ERR_INVALID_ARG;
+    REQUIRE(ctx, hologram, "hologram is NULL");
+    hcgs_saved* s = saved;
+    if (!s) {
+        if (!ctx->scratch_saved) ctx->scratch_saved = new hcgs_saved();
+        s = ctx->scratch_saved;
+    }
+    TRY(hcgs_project(ctx, g, V, viewmats, intrinsics, o, opts, s, stream));
+    float2* U = (float2*)planes;
+    if (!U) {
+        const size_t F = (size_t)V * o->L * o->C * o->H * o->W;
+        HCGS_CUDA(ctx, grow(ctx, s->U, F * sizeof(float2), &s->bytes));
+        U = (float2*)s->U.p;
+    }
+    TRY(raster_forward(ctx, s, U, nullptr, nullptr, S(stream)));
+    s->rastered = 1;
+    return asm_sum(ctx, U, (float2*)hologram, V, &s->optics, false, S(stream));
+}
+
+hcgs_status hcgs_rasterize_planes_backward(hcgs_ctx* ctx, hcgs_saved* s, const float* gU, void* stream) {
+    if (!ctx) return HCGS_ERR_INVALID_ARG;
+    REQUIRE(ctx, s && gU, "NULL argument");
+    if (!s->valid || !s->rastered) {
+        set_err(ctx, HCGS_ERR_STATE, "the forward rasterization has not run on this saved state");
+        return HCGS_ERR_STATE;
+    }
+    cudaSetDevice(ctx->device);
+    TRY(raster_backward(ctx, s, (const float2*)gU, S(stream)));
+    s->have_g2d = 1;
+    return HCGS_OK;
+}
+
+static hcgs_status check_grads(hcgs_ctx* ctx, const hcgs_gaussian_grads* gr) {
+    REQUIRE(ctx, gr, "grads is NULL");
+    REQUIRE(ctx, gr->means && gr->log_scales && gr->quats && gr->opacity_logits && gr->amplitude && gr->phase &&
+                     gr->plane_logits,
+            "a gradient array is NULL");
+    return HCGS_OK;
+}
+
+hcgs_status hcgs_project_backward(hcgs_ctx* ctx, hcgs_saved* s, const hcgs_gaussians* g,
+                                  const hcgs_gaussian_grads* gr, int accumulate, void* stream) {
+    if (!ctx) return HCGS_ERR_INVALID_ARG;
+    REQUIRE(ctx, s, "saved is NULL");
+    TRY(check_gauss(ctx, g));
+    if (!s->have_g2d || g->N != s->N) {
+        set_err(ctx, HCGS_ERR_STATE, "needs hcgs_rasterize_planes_backward on the same Gaussians first");
+        return HCGS_ERR_STATE;
+    }
+    if (g->N == 0) return HCGS_OK;
+    TRY(check_grads(ctx, gr));
+    cudaSetDevice(ctx->device);
+    return project_backward(ctx, s, g, gr, accumulate, S(stream));
+}
+
+hcgs_status hcgs_render_view_backward(hcgs_ctx* ctx, hcgs_saved* saved, const hcgs_gaussians* g,
+                                      const float* g_hologram, const hcgs_gaussian_grads* gr, int accumulate,
+                                      void* stream) {
+    if (!ctx) return HCGS_ERR_INVALID_ARG;
+    hcgs_saved* s = saved ? saved : ctx->scratch_saved;
+    REQUIRE(ctx, s && g_hologram, "NULL argument");
+    if (!s->valid || !s->rastered) {
+        set_err(ctx, HCGS_ERR_STATE, "hcgs_render_view has not run on this saved state");
+        return HCGS_ERR_STATE;
+    }
+    TRY(check_gauss(ctx, g));
+    REQUIRE(ctx, g->N == s->N, "N differs from the forward call");
+    cudaSetDevice(ctx->device);
+    const size_t F = (size_t)s->V * s->L * s->C * s->H * s->W;
+    HCGS_CUDA(ctx, grow(ctx, s->gU, F * sizeof(float2), &s->bytes));
+    TRY(asm_spread(ctx, (const float2*)g_hologram, (float2*)s->gU.p, s->V, &s->optics, true, S(stream)));
+    TRY(raster_backward(ctx, s, (const float2*)s->gU.p, S(stream)));
+    s->have_g2d = 1;
+    if (g->N == 0) return HCGS_OK;
+    TRY(check_grads(ctx, gr));
+    return project_backward(ctx, s, g, gr, accumulate, S(stream));
+}
+
+hcgs_status hcgs_focal_stack_loss(hcgs_ctx* ctx, const float* hologram, const float* I_gt, int B,
+                                  const hcgs_optics* o, float* loss, float* g_hologram, float* I_out,
+                                  void* stream) {
+    if (!ctx) return HCGS_ERR_INVALID_ARG;
+    TRY(check_optics(ctx, o));
+    REQUIRE(ctx, hologram && I_gt && loss, "NULL argument");
+    REQUIRE(ctx, B >= 1, "B must be >= 1");
+    cudaSetDevice(ctx->device);
+    const float2* hq;
+    TRY(get_htab(ctx, o, &hq));
+    const size_t planeN = (size_t)o->H * o->W;
+    const size_t nP = (size_t)B * o->C * planeN, nF = (size_t)B * o->L * o->C * planeN;
+    HCGS_CUDA(ctx, grow(ctx, ctx->ws[1], nP * sizeof(float2), &ctx->bytes));
+    HCGS_CUDA(ctx, grow(ctx, ctx->ws[2], nF * sizeof(float2), &ctx->bytes));
+    float2* S1 = (float2*)ctx->ws[1].p;
+    float2* S2 = (float2*)ctx->ws[2].p;
+    cudaStream_t st = S(stream);
+    const float inv_count = (float)(1.0 / (double)nF);
+    int nblocks = 0;
+    TRY(cols_focal_loss(ctx, nullptr, nullptr, nullptr, nullptr, B * o->L * o->C, o->H, o->W, inv_count, 0.f,
+                        &nblocks, st));
+    HCGS_CUDA(ctx, grow(ctx, ctx->ws[3], (size_t)nblocks * sizeof(float), &ctx->bytes));
+    TRY(fft_cols(ctx, (const float2*)hologram, S1, B * o->C, o->H, o->W, false, 1.f, st));
+    TRY(rows_spread(ctx, S1, S2, B, o->L, o->C, o->H, o->W, hq, true, st));
+    TRY(cols_focal_loss(ctx, S2, I_gt, I_out, (float*)ctx->ws[3].p, B * o->L * o->C, o->H, o->W, inv_count,
+                        1.f / (float)planeN, &nblocks, st));
+    TRY(reduce_sum(ctx, (const float*)ctx->ws[3].p, nblocks, inv_count, loss, st));
+    if (g_hologram) {
+        TRY(rows_sum(ctx, S2, (float2*)g_hologram, B, o->L, o->C, o->H, o->W, hq, false, st));
+        TRY(fft_cols(ctx, (float2*)g_hologram, (float2*)g_hologram, B * o->C, o->H, o->W, true,
+                     1.f / (float)planeN, st));
+    }
+    return HCGS_OK;
+}
+
+hcgs_status hcgs_adam_step(hcgs_ctx* ctx, float* p, const float* g, float* m, float* v, int64_t n, int step,
+                           float lr, float beta1, float beta2, float eps, void* stream) {
+    if (!ctx) return HCGS_ERR_INVALID_ARG;
+    REQUIRE(ctx, n >= 0, "n must be >= 0");
+    if (n == 0) return HCGS_OK;
+    REQUIRE(ctx, p && g && m && v, "NULL argument");
+    REQUIRE(ctx, step >= 1, "step counts from 1");
+    REQUIRE(ctx, beta1 >= 0.f && beta1 < 1.f && beta2 >= 0.f && beta2 < 1.f && eps >= 0.f, "bad Adam constants");
+    cudaSetDevice(ctx->device);
+    return adam(ctx, p, g, m, v, n, step, lr, beta1, beta2, eps, S(stream));
+}
+
+hcgs_status hcgs_mlp_forward(hcgs_ctx* ctx, const uint16_t* x, int N, const uint16_t* W1, const uint16_t* W2,
+                             const uint16_t* W3, const uint16_t* W4, const float* b1, const float* b2,
+                             const float* b3, const float* b4, float* y, void* stream) {
+    if (!ctx) return HCGS_ERR_INVALID_ARG;
+    REQUIRE(ctx, N >= 0, "N must be >= 0");
+    if (N == 0) return HCGS_OK;
+    REQUIRE(ctx, x && W1 && W2 && W3 && W4 && b1 && b2 && b3 && b4 && y, "NULL argument");
+    cudaSetDevice(ctx->device);
+    const uint16_t* W[4] = {W1, W2, W3, W4};
+    const float* b[4] = {b1, b2, b3, b4};
+    return mlp_fwd(ctx, x, N, W, b, y, S(stream));
+}
+
+hcgs_status hcgs_mlp_backward(hcgs_ctx* ctx, const uint16_t* x, int N, const uint16_t* W1, const uint16_t* W2,
+                              const uint16_t* W3, const uint16_t* W4, const float* b1, const float* b2,
+                              const float* b3, const float* b4, const float* gy, float* gW1, float* gW2,
+                              float* gW3, float* gW4, float* gb1, float* gb2, float* gb3, float* gb4,
+                              void* stream) {
+    if (!ctx) return HCGS_ERR_INVALID_ARG;
+    REQUIRE(ctx, N >= 0, "N must be >= 0");
+    REQUIRE(ctx, x && W1 && W2 && W3 && W4 && b1 && b2 && b3 && b4 && gy, "NULL argument");
+    REQUIRE(ctx, gW1 && gW2 && gW3 && gW4 && gb1 && gb2 && gb3 && gb4, "NULL gradient argument");
+    cudaSetDevice(ctx->device);
+    const uint16_t* W[4] = {W1, W2, W3, W4};
+    const float* b[4] = {b1, b2, b3, b4};
+    float* gW[4] = {gW1, gW2, gW3, gW4};
+    float* gb[4] = {gb1, gb2, gb3, gb4};
+    return mlp_bwd(ctx, x, N, W, b, gy, gW, gb, S(stream));
+}
+
+}  // extern "C"

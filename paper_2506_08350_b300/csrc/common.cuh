@@ -1,0 +1,202 @@
+// Internal declarations shared by the libhcgs translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/hcgs.h"
+
+namespace hcgs {
+
+constexpr int TILE = 16;            // tile edge in pixels (Sec. 4.2)
+constexpr int MAX_C = 4;            // wavelengths
+constexpr int MAX_L = 16;           // depth planes
+constexpr int MAX_FFT = 4096;       // longest supported transform
+constexpr int MAX_STAGES = 16;
+constexpr int COARSE = 4;          // fine tiles per coarse-bucket edge (64 x 64 px)
+
+// Device scratch buffer that only grows.
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+};
+
+// Mixed-radix plan for one transform length (radices 2, 3, 4, 5, 8).
+struct FftPlan {
+    int n = 0;
+    int nst = 0;
+    int radix[MAX_STAGES] = {0};
+    float2* tw = nullptr;  // device [n]: exp(-2 pi i m / n), formed in FP64
+};
+
+struct FftPlanArg {  // by-value kernel argument
+    int n, nst;
+    int radix[MAX_STAGES];
+};
+
+// Per-(geometry, optics) transfer-function table: quadrant of H_z, because
+// H depends on f_x^2 and f_y^2 only.  Hq[c][l][H/2+1][W/2+1] float2.
+struct HKey {
+    int H, W, C, L;
+    double px, py;
+    std::vector<double> lam, z;
+    bool operator<(const HKey& o) const {
+        return std::tie(H, W, C, L, px, py, lam, z) < std::tie(o.H, o.W, o.C, o.L, o.px, o.py, o.lam, o.z);
+    }
+};
+
+// Per-launch CUDA events, recorded only while profiling is on.
+struct ProfRec {
+    const char* name;
+    cudaEvent_t a, b;
+};
+struct Prof {
+    bool on = false;
+    std::vector<ProfRec> recs;
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+};
+
+}  // namespace hcgs
+
+struct hcgs_ctx {
+    hcgs::Prof prof;
+    int device = 0;
+    std::string last_error;
+    size_t bytes = 0;
+    hcgs::DevBuf ws[6];                              // workspace slots
+    std::map<int, hcgs::FftPlan> plans;              // FFT plans by length
+    std::map<hcgs::HKey, hcgs::DevBuf> htab;         // transfer-function tables
+    int* d_status = nullptr;                         // device status word
+    uint32_t* h_pinned = nullptr;                    // pinned host words
+    hcgs_saved* scratch_saved = nullptr;             // used when render_view gets NULL
+};
+
+struct hcgs_saved {
+    // geometry of the last hcgs_project
+    int V = 0, N = 0, L = 0, C = 0, H = 0, W = 0;
+    int tilesX = 0, tilesY = 0, ctX = 0, ctY = 0;  // fine and coarse tile grids
+    int valid = 0;         // 1 after hcgs_project
+    int rastered = 0;      // 1 after hcgs_rasterize_planes
+    int have_g2d = 0;      // 1 after hcgs_rasterize_planes_backward
+    hcgs_raster_opts opts{};
+    hcgs_optics optics{};
+    std::vector<double> lam, z;
+    uint64_t M = 0;        // coarse-bucket instances over all views
+    // buffers
+    hcgs::DevBuf w;        // [N][C] float2: c e^{j phi}
+    hcgs::DevBuf proj;     // [V][N][2] float4 projected record, by Gaussian id
+    hcgs::DevBuf rectn;    // [V][N] uint2 fine-tile rectangle, by Gaussian id
+    hcgs::DevBuf dkey;     // [2][V][N] uint32 depth keys (sort ping-pong)
+    hcgs::DevBuf dval;     // [2][V][N] uint32 Gaussian ids
+    hcgs::DevBuf nvalid;   // [V] uint32 number of visible Gaussians per view
+    hcgs::DevBuf rank;     // [V][N] uint32 visiting rank of Gaussian n (~0u if culled)
+    hcgs::DevBuf sortid;   // [V][N] uint32 Gaussian id at visiting rank s
+    hcgs::DevBuf rec;      // [V][N][NR] float4 records in visiting order
+    hcgs::DevBuf rects;    // [V][N] uint2 fine-tile rectangle in visiting order
+    hcgs::DevBuf planes;   // [V][N] int32 plane in visiting order
+    hcgs::DevBuf ccount;   // [V*N] uint32 coarse tiles per record, then offsets
+    hcgs::DevBuf bcount;   // [V*L*CT + 1] uint32 bucket counts, then offsets
+    hcgs::DevBuf ikey;     // [2][M] uint32 instance bucket ids (sort ping-pong)
+    hcgs::DevBuf ival;     // [2][M] uint32 instance visiting ranks
+    hcgs::DevBuf hist;     // radix-sort block histograms
+    hcgs::DevBuf scan;     // scan partials
+    hcgs::DevBuf Tfin;     // [V][L][H][W] float
+    hcgs::DevBuf last;     // [V][L][H][W] uint32: bucket position after the last contributor
+    hcgs::DevBuf U;        // [V][L][C][H][W] float2 when the caller gives no plane buffer
+    hcgs::DevBuf g2d;      // [V][N][G2D] float 2D gradients (visiting order)
+    hcgs::DevBuf gU;       // [V][L][C][H][W] float2 plane gradients
+    hcgs::DevBuf cam;      // [V][20] float copies of the view matrices and intrinsics
+    const uint32_t* list = nullptr;  // sorted instance ranks (points into ival)
+    size_t bytes = 0;
+};
+
+namespace hcgs {
+
+// ---- error plumbing ----
+struct Err {
+    hcgs_status s;
+    std::string msg;
+};
+bool set_err(hcgs_ctx* ctx, hcgs_status s, const std::string& m);
+hcgs_status cuda_err(hcgs_ctx* ctx, cudaError_t e, const char* what);
+cudaError_t grow(hcgs_ctx* ctx, DevBuf& b, size_t bytes, size_t* owner_bytes);
+
+#define HCGS_CUDA(ctx, call)                                        \
+    do {                                                            \
+        cudaError_t e__ = (call);                                   \
+        if (e__ != cudaSuccess) return hcgs::cuda_err(ctx, e__, #call); \
+    } while (0)
+#define HCGS_LAUNCH(ctx, what)                                      \
+    do {                                                            \
+        cudaError_t e__ = cudaGetLastError();                       \
+        if (e__ != cudaSuccess) return hcgs::cuda_err(ctx, e__, what); \
+    } while (0)
+
+// ---- per-kernel timing ----
+void prof_begin(hcgs_ctx* ctx, const char* name, cudaStream_t st);
+void prof_end(hcgs_ctx* ctx, cudaStream_t st);
+// Launch a kernel between two profiling events.
+#define HCGS_KERNEL(ctx, name, st, ...)        \
+    do {                                       \
+        hcgs::prof_begin(ctx, name, st);       \
+        __VA_ARGS__;                           \
+        hcgs::prof_end(ctx, st);               \
+        HCGS_LAUNCH(ctx, name);                \
+    } while (0)
+
+// ---- FFT / ASM (fft.cu) ----
+bool fft_supported(int n);
+hcgs_status get_plan(hcgs_ctx* ctx, int n, FftPlan** out);
+hcgs_status get_htab(hcgs_ctx* ctx, const hcgs_optics* o, const float2** out);
+// Batched column transforms of `nplanes` H x W complex planes (in place allowed).
+hcgs_status fft_cols(hcgs_ctx* ctx, const float2* in, float2* out, int nplanes, int H, int W, bool inverse,
+                     float scale, cudaStream_t st);
+// sum mode: out[b][c] = IDFT_rows( sum_l Hsel(c,l) DFT_rows(in[b][l][c]) ), unscaled.
+hcgs_status rows_sum(hcgs_ctx* ctx, const float2* in, float2* out, int B, int L, int C, int H, int W,
+                     const float2* hq, bool conjH, cudaStream_t st);
+// spread mode: out[b][l][c] = IDFT_rows( Hsel(c,l) DFT_rows(in[b][c]) ), unscaled.
+hcgs_status rows_spread(hcgs_ctx* ctx, const float2* in, float2* out, int B, int L, int C, int H, int W,
+                        const float2* hq, bool conjH, cudaStream_t st);
+// Column pass of the focal-stack loss: inverse column DFT (scaled), intensity,
+// loss partials, dL/dV, forward column DFT of dL/dV, in place.
+hcgs_status cols_focal_loss(hcgs_ctx* ctx, float2* data, const float* I_gt, float* I_out, float* partials,
+                            int nplanes, int H, int W, float inv_count, float scale, int* nblocks_out,
+                            cudaStream_t st);
+hcgs_status asm_sum(hcgs_ctx* ctx, const float2* in, float2* out, int B, const hcgs_optics* o, bool conjH,
+                    cudaStream_t st);
+hcgs_status asm_spread(hcgs_ctx* ctx, const float2* in, float2* out, int B, const hcgs_optics* o, bool conjH,
+                       cudaStream_t st);
+
+// ---- projection / sort / binning / raster (project.cu, sort.cu, raster.cu) ----
+hcgs_status project_and_bin(hcgs_ctx* ctx, hcgs_saved* s, const hcgs_gaussians* g, const float* viewmats,
+                            const float* intr, cudaStream_t st);
+hcgs_status raster_forward(hcgs_ctx* ctx, hcgs_saved* s, float2* U, float* T_out, int32_t* nc_out,
+                           cudaStream_t st);
+hcgs_status raster_backward(hcgs_ctx* ctx, hcgs_saved* s, const float2* gU, cudaStream_t st);
+hcgs_status project_backward(hcgs_ctx* ctx, hcgs_saved* s, const hcgs_gaussians* g,
+                             const hcgs_gaussian_grads* gr, int accumulate, cudaStream_t st);
+// Stable LSD radix sort of nseg contiguous segments of seglen (key, value)
+// pairs on key bits [0, nbits); returns the buffer index (0 or 1) holding the
+// result.  keys/vals point at [2][nseg*seglen] ping-pong storage.
+hcgs_status radix_sort(hcgs_ctx* ctx, hcgs_saved* s, uint32_t* keys, uint32_t* vals, int nseg, size_t seglen,
+                       int nbits, int* which, cudaStream_t st);
+// Exclusive scan of n uint32 counts (in place allowed); writes the total to
+// out[n] when with_total is set.  Totals must stay below 2^32.
+hcgs_status exclusive_scan(hcgs_ctx* ctx, hcgs_saved* s, const uint32_t* in, uint32_t* out, size_t n,
+                           cudaStream_t st);
+
+// ---- training pieces (train.cu) ----
+hcgs_status adam(hcgs_ctx* ctx, float* p, const float* g, float* m, float* v, int64_t n, int step, float lr,
+                 float b1, float b2, float eps, cudaStream_t st);
+hcgs_status reduce_sum(hcgs_ctx* ctx, const float* partials, int n, float scale, float* out, cudaStream_t st);
+hcgs_status mlp_fwd(hcgs_ctx* ctx, const uint16_t* x, int N, const uint16_t* const* W, const float* const* b,
+                    float* y, cudaStream_t st);
+hcgs_status mlp_bwd(hcgs_ctx* ctx, const uint16_t* x, int N, const uint16_t* const* W, const float* const* b,
+                    const float* gy, float* const* gW, float* const* gb, cudaStream_t st);
+
+}  // namespace hcgs

@@ -1,0 +1,533 @@
+// Steps 1-2 of the render path on sm_103a: projection of the Gaussians
+// (Sec. 3 Eq. gaussian_projection / gaussian_projection_2d; Eq.
+// hard_assignment), depth sort, and binning into coarse 64x64-pixel buckets
+// per plane; plus the adjoint of the projection (Supp. D.4, Eq. ste).
+//
+// Binning design.  Instead of materialising one (tile, depth) key per
+// Gaussian and covered 16x16 tile and sorting those (Algorithm 2 preprocessing),
+// the Gaussians are sorted once by depth (N keys per view), and each visible
+// Gaussian emits one instance per covered 64x64 bucket of its plane, in
+// visiting order.  A stable radix sort by bucket id then yields per-bucket
+// lists already in visiting order.  The rasterizer streams a bucket's list and
+// keeps the entries whose 16x16-tile rectangle covers its tile.  This moves
+// ~16x fewer instances than per-tile binning, needs no per-tile sort, and the
+// result does not depend on tiling because every candidate is still tested
+// per pixel with the support rule o G >= alpha_min.
+#include <cmath>
+
+#include "common.cuh"
+#include "project.cuh"
+
+namespace hcgs {
+
+// ---------------------------------------------------------------------------
+// projection
+// ---------------------------------------------------------------------------
+__global__ void k_prep_w(const float* __restrict__ amp, const float* __restrict__ ph, float2* __restrict__ w,
+                         int N, int C) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N * C) return;
+    float s, c;
+    sincosf(ph[i], &s, &c);
+    w[i] = make_float2(amp[i] * c, amp[i] * s);
+}
+
+__global__ void k_project(ProjArgs a, const float* __restrict__ means, const float* __restrict__ log_scales,
+                          const float* __restrict__ quats, const float* __restrict__ opacity_logits,
+                          const float* __restrict__ plane_logits, const float* __restrict__ cam,
+                          float4* __restrict__ proj, uint2* __restrict__ rectn, uint32_t* __restrict__ dkey,
+                          uint32_t* __restrict__ dval, uint32_t* __restrict__ nvalid) {
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i >= (size_t)a.V * a.N) return;
+    const int v = (int)(i / a.N), n = (int)(i - (size_t)v * a.N);
+    ProjF P;
+    project_one(a, means + 3 * n, log_scales + 3 * n, quats + 4 * n, opacity_logits[n], cam + 20 * v, P);
+    int plane = 0;
+    {
+        const float* r = plane_logits + (size_t)n * a.L;
+        float best = r[0];
+        for (int l = 1; l < a.L; l++)
+            if (r[l] > best) { best = r[l]; plane = l; }  // ties keep the lowest index
+    }
+    uint2 rect = make_uint2(0u, 0u);  // empty
+    if (P.valid) {
+        int tx0 = 0, tx1 = a.tilesX, ty0 = 0, ty1 = a.tilesY;
+        bool any = true;
+        if (a.amin > 0.f) {
+            if (P.o < a.amin) {
+                any = false;
+            } else {
+                // support {d : d^T conic d <= 2 ln(o / alpha_min)}: its bounding box,
+                // padded so that FP32 rounding never loses a support pixel
+                const float k2 = 2.f * logf(P.o / a.amin);
+                const float rx = sqrtf(k2 * P.cov[0]) * 1.0001f + 0.01f;
+                const float ry = sqrtf(k2 * P.cov[2]) * 1.0001f + 0.01f;
+                const float fx0 = floorf((P.mu.x - rx) * (1.f / TILE)), fx1 = floorf((P.mu.x + rx) * (1.f / TILE));
+                const float fy0 = floorf((P.mu.y - ry) * (1.f / TILE)), fy1 = floorf((P.mu.y + ry) * (1.f / TILE));
+                tx0 = (int)fmaxf(fx0, 0.f);
+                ty0 = (int)fmaxf(fy0, 0.f);
+                tx1 = (int)fminf(fx1 + 1.f, (float)a.tilesX);
+                ty1 = (int)fminf(fy1 + 1.f, (float)a.tilesY);
+                any = tx0 < tx1 && ty0 < ty1;
+            }
+        }
+        if (any) rect = make_uint2((uint32_t)tx0 | ((uint32_t)tx1 << 16), (uint32_t)ty0 | ((uint32_t)ty1 << 16));
+        atomicAdd(nvalid + v, 1u);
+    }
+    proj[2 * i] = make_float4(P.mu.x, P.mu.y, P.conic[0], P.conic[1]);
+    proj[2 * i + 1] = make_float4(P.conic[2], P.o, P.depth, __int_as_float(plane));
+    rectn[i] = rect;
+    // depth >= near_z > 0, so the float bits order like the values
+    dkey[i] = P.valid ? __float_as_uint(P.depth) : 0xFFFFFFFFu;
+    dval[i] = (uint32_t)n;
+}
+
+// Gaussians in visiting order: records for the rasterizer, ranks, and the
+// number of coarse buckets each one touches.
+__global__ void k_gather(ProjArgs a, const uint32_t* __restrict__ sorted_id, const uint32_t* __restrict__ nvalid,
+                         const float4* __restrict__ proj, const uint2* __restrict__ rectn,
+                         const float2* __restrict__ w, int order, uint32_t* __restrict__ rank,
+                         uint32_t* __restrict__ sortid, float4* __restrict__ rec, uint2* __restrict__ rects,
+                         int* __restrict__ planes, uint32_t* __restrict__ ccount) {
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i >= (size_t)a.V * a.N) return;
+    const int v = (int)(i / a.N), s = (int)(i - (size_t)v * a.N);
+    const int m = (int)nvalid[v];
+    const uint32_t n = sorted_id[i];
+    const size_t vn = (size_t)v * a.N;
+    if (s >= m) {
+        rank[vn + n] = 0xFFFFFFFFu;
+        ccount[i] = 0u;
+        return;
+    }
+    const int s2 = order == 1 ? m - 1 - s : s;
+    rank[vn + n] = (uint32_t)s2;
+    sortid[vn + s2] = n;
+    const float4 p0 = proj[2 * (vn + n)], p1 = proj[2 * (vn + n) + 1];
+    const int NR = rec_count(a.C);
+    float4* r = rec + (vn + s2) * NR;
+    const float2* wn = w + (size_t)n * a.C;
+    r[0] = p0;
+    r[1] = make_float4(p1.x, p1.y, wn[0].x, wn[0].y);
+    if (a.C >= 2) r[2] = make_float4(wn[1].x, wn[1].y, a.C >= 3 ? wn[2].x : 0.f, a.C >= 3 ? wn[2].y : 0.f);
+    if (a.C >= 4) r[3] = make_float4(wn[3].x, wn[3].y, 0.f, 0.f);
+    const uint2 rc = rectn[vn + n];
+    rects[vn + s2] = rc;
+    planes[vn + s2] = __float_as_int(p1.w);
+    const uint32_t tx0 = rc.x & 0xFFFFu, tx1 = rc.x >> 16, ty0 = rc.y & 0xFFFFu, ty1 = rc.y >> 16;
+    uint32_t cnt = 0;
+    if (tx0 < tx1 && ty0 < ty1) {
+        const uint32_t cx0 = tx0 / COARSE, cx1 = (tx1 + COARSE - 1) / COARSE;
+        const uint32_t cy0 = ty0 / COARSE, cy1 = (ty1 + COARSE - 1) / COARSE;
+        cnt = (cx1 - cx0) * (cy1 - cy0);
+    }
+    ccount[vn + s2] = cnt;
+}
+
+// One instance per (visible Gaussian, covered coarse bucket), in visiting order.
+__global__ void k_inst_gen(ProjArgs a, const uint32_t* __restrict__ coff, const uint2* __restrict__ rects,
+                           const int* __restrict__ planes, const uint32_t* __restrict__ nvalid,
+                           uint32_t* __restrict__ ikey, uint32_t* __restrict__ ival) {
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i >= (size_t)a.V * a.N) return;
+    const int v = (int)(i / a.N), s = (int)(i - (size_t)v * a.N);
+    if (s >= (int)nvalid[v]) return;
+    const uint2 rc = rects[i];
+    const uint32_t tx0 = rc.x & 0xFFFFu, tx1 = rc.x >> 16, ty0 = rc.y & 0xFFFFu, ty1 = rc.y >> 16;
+    if (!(tx0 < tx1 && ty0 < ty1)) return;
+    const uint32_t cx0 = tx0 / COARSE, cx1 = (tx1 + COARSE - 1) / COARSE;
+    const uint32_t cy0 = ty0 / COARSE, cy1 = (ty1 + COARSE - 1) / COARSE;
+    const uint32_t pl = (uint32_t)planes[i];
+    uint32_t pos = coff[i];
+    const uint32_t bb = ((uint32_t)v * a.L + pl) * a.ctY;
+    for (uint32_t cy = cy0; cy < cy1; cy++)
+        for (uint32_t cx = cx0; cx < cx1; cx++) {
+            ikey[pos] = (bb + cy) * a.ctX + cx;
+            ival[pos] = (uint32_t)s;
+            pos++;
+        }
+}
+
+// Bucket start offsets from the sorted bucket ids: off[b] = first position
+// whose id >= b; off[NB] = M.
+__global__ void k_bucket_bounds(const uint32_t* __restrict__ key, uint32_t M, uint32_t NB, uint32_t* __restrict__ off) {
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i > M) return;
+    const int64_t prev = i > 0 ? (int64_t)key[i - 1] : -1;
+    const int64_t cur = i < M ? (int64_t)key[i] : (int64_t)NB;
+    for (int64_t b = prev + 1; b <= cur; b++) off[b] = (uint32_t)i;
+}
+
+// ---------------------------------------------------------------------------
+// stable LSD radix sort (8-bit digits), segmented by fixed-length segments
+// ---------------------------------------------------------------------------
+constexpr int RS_THREADS = 256;
+constexpr int RS_IPT = 8;
+constexpr int RS_KPB = RS_THREADS * RS_IPT;
+
+__global__ void k_rs_hist(const uint32_t* __restrict__ keys, size_t seglen, int shift, int nblk,
+                          uint32_t* __restrict__ hist) {
+    __shared__ uint32_t h[256];
+    const int seg = blockIdx.y, blk = blockIdx.x;
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const size_t beg = (size_t)blk * RS_KPB;
+    const uint32_t* k = keys + (size_t)seg * seglen;
+#pragma unroll
+    for (int r = 0; r < RS_IPT; r++) {
+        const size_t idx = beg + (size_t)r * RS_THREADS + threadIdx.x;
+        if (idx < seglen) atomicAdd(&h[(k[idx] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[((size_t)seg * 256 + threadIdx.x) * nblk + blk] = h[threadIdx.x];
+}
+
+__global__ void k_rs_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                             uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, size_t seglen, int shift,
+                             int nblk, const uint32_t* __restrict__ pos) {
+    __shared__ uint32_t wcnt[RS_THREADS / 32][256];
+    __shared__ uint32_t running[256];
+    __shared__ uint32_t gbase[256];
+    const int seg = blockIdx.y, blk = blockIdx.x;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    running[t] = 0;
+    gbase[t] = pos[((size_t)seg * 256 + t) * nblk + blk];
+    const size_t beg = (size_t)blk * RS_KPB;
+    const size_t so = (size_t)seg * seglen;
+    for (int r = 0; r < RS_IPT; r++) {
+        for (int e = t; e < (RS_THREADS / 32) * 256; e += RS_THREADS) (&wcnt[0][0])[e] = 0;
+        __syncthreads();
+        const size_t idx = beg + (size_t)r * RS_THREADS + t;
+        const bool ok = idx < seglen;
+        const uint32_t key = ok ? kin[so + idx] : 0u;
+        const uint32_t d = ok ? ((key >> shift) & 255u) : 256u;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t lrank = __popc(peers & lt);
+        if (ok && lrank == 0) wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        uint32_t tot = 0;
+#pragma unroll
+        for (int w = 0; w < RS_THREADS / 32; w++) {
+            const uint32_t c = wcnt[w][t];
+            wcnt[w][t] = tot;
+            tot += c;
+        }
+        __syncthreads();
+        if (ok) {
+            const uint32_t p = gbase[d] + running[d] + wcnt[warp][d] + lrank;
+            kout[p] = key;
+            vout[p] = vin[so + idx];
+        }
+        __syncthreads();
+        running[t] += tot;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// exclusive scan of uint32 counts
+// ---------------------------------------------------------------------------
+constexpr int SC_THREADS = 512;
+constexpr int SC_IPT = 8;
+constexpr int SC_EPB = SC_THREADS * SC_IPT;
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* total) {
+    __shared__ uint32_t ws[SC_THREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) ws[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t v = lane < SC_THREADS / 32 ? ws[lane] : 0u;
+        uint32_t vi = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, vi, o);
+            if (lane >= o) vi += y;
+        }
+        if (lane < SC_THREADS / 32) ws[lane] = vi - v;
+        if (lane == SC_THREADS / 32 - 1) *total = vi;
+    }
+    __syncthreads();
+    const uint32_t r = ws[warp] + inc - x;
+    __syncthreads();
+    return r;
+}
+
+__global__ void k_scan_reduce(const uint32_t* __restrict__ in, size_t n, uint32_t* __restrict__ bsum) {
+    const size_t beg = (size_t)blockIdx.x * SC_EPB + (size_t)threadIdx.x * SC_IPT;
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < SC_IPT; k++)
+        if (beg + k < n) s += in[beg + k];
+    __shared__ uint32_t tot;
+    block_exclusive_scan(s, &tot);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+// single block: exclusive scan of nb block sums; 64-bit total to *total64
+__global__ void k_scan_top(uint32_t* __restrict__ bsum, int nb, unsigned long long* __restrict__ total64) {
+    const int per = (nb + SC_THREADS - 1) / SC_THREADS;
+    const int beg = threadIdx.x * per;
+    unsigned long long s = 0;
+    for (int k = 0; k < per; k++)
+        if (beg + k < nb) s += bsum[beg + k];
+    __shared__ uint32_t tot;
+    const uint32_t ex = block_exclusive_scan((uint32_t)s, &tot);
+    uint32_t run = ex;
+    for (int k = 0; k < per; k++)
+        if (beg + k < nb) {
+            const uint32_t c = bsum[beg + k];
+            bsum[beg + k] = run;
+            run += c;
+        }
+    // 64-bit total for overflow detection
+    __shared__ unsigned long long t64;
+    if (threadIdx.x == 0) t64 = 0;
+    __syncthreads();
+    atomicAdd(&t64, s);
+    __syncthreads();
+    if (threadIdx.x == 0) *total64 = t64;
+}
+
+__global__ void k_scan_apply(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, size_t n,
+                             const uint32_t* __restrict__ bsum) {
+    const size_t beg = (size_t)blockIdx.x * SC_EPB + (size_t)threadIdx.x * SC_IPT;
+    uint32_t v[SC_IPT];
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < SC_IPT; k++) {
+        v[k] = beg + k < n ? in[beg + k] : 0u;
+        s += v[k];
+    }
+    __shared__ uint32_t tot;
+    uint32_t run = block_exclusive_scan(s, &tot) + bsum[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < SC_IPT; k++)
+        if (beg + k < n) {
+            out[beg + k] = run;
+            run += v[k];
+        }
+}
+
+static size_t scan_bsum_bytes(size_t n) {
+    const size_t nb = (n + SC_EPB - 1) / SC_EPB;
+    return ((nb * sizeof(uint32_t) + 7) / 8) * 8;
+}
+
+hcgs_status exclusive_scan(hcgs_ctx* ctx, hcgs_saved* s, const uint32_t* in, uint32_t* out, size_t n,
+                           cudaStream_t st) {
+    if (n == 0) return HCGS_OK;
+    const size_t nb = (n + SC_EPB - 1) / SC_EPB;
+    HCGS_CUDA(ctx, grow(ctx, s->scan, scan_bsum_bytes(n) + 8, &s->bytes));
+    uint32_t* bsum = (uint32_t*)s->scan.p;
+    unsigned long long* t64 = (unsigned long long*)((char*)s->scan.p + scan_bsum_bytes(n));
+    HCGS_KERNEL(ctx, "k_scan_reduce", st, k_scan_reduce<<<(unsigned)nb, SC_THREADS, 0, st>>>(in, n, bsum));
+    HCGS_KERNEL(ctx, "k_scan_top", st, k_scan_top<<<1, SC_THREADS, 0, st>>>(bsum, (int)nb, t64));
+    HCGS_KERNEL(ctx, "k_scan_apply", st, k_scan_apply<<<(unsigned)nb, SC_THREADS, 0, st>>>(in, out, n, bsum));
+    HCGS_LAUNCH(ctx, "exclusive_scan");
+    return HCGS_OK;
+}
+
+// the 64-bit total of the last exclusive_scan over n elements
+static const unsigned long long* scan_total_ptr(hcgs_saved* s, size_t n) {
+    return (const unsigned long long*)((char*)s->scan.p + scan_bsum_bytes(n));
+}
+
+hcgs_status radix_sort(hcgs_ctx* ctx, hcgs_saved* s, uint32_t* keys, uint32_t* vals, int nseg, size_t seglen,
+                       int nbits, int* which, cudaStream_t st) {
+    *which = 0;
+    if (seglen == 0 || nseg == 0) return HCGS_OK;
+    const int nblk = (int)((seglen + RS_KPB - 1) / RS_KPB);
+    const size_t nh = (size_t)nseg * 256 * nblk;
+    HCGS_CUDA(ctx, grow(ctx, s->hist, nh * sizeof(uint32_t), &s->bytes));
+    uint32_t* hist = (uint32_t*)s->hist.p;
+    const size_t total = (size_t)nseg * seglen;
+    int cur = 0;
+    for (int shift = 0; shift < nbits; shift += 8) {
+        uint32_t* kin = keys + (size_t)cur * total;
+        uint32_t* vin = vals + (size_t)cur * total;
+        uint32_t* kout = keys + (size_t)(1 - cur) * total;
+        uint32_t* vout = vals + (size_t)(1 - cur) * total;
+        dim3 grid(nblk, nseg);
+        HCGS_KERNEL(ctx, "k_rs_hist", st, k_rs_hist<<<grid, RS_THREADS, 0, st>>>(kin, seglen, shift, nblk, hist));
+        HCGS_LAUNCH(ctx, "k_rs_hist");
+        hcgs_status e = exclusive_scan(ctx, s, hist, hist, nh, st);
+        if (e) return e;
+        HCGS_KERNEL(ctx, "k_rs_scatter", st, k_rs_scatter<<<grid, RS_THREADS, 0, st>>>(kin, vin, kout, vout, seglen, shift, nblk, hist));
+        HCGS_LAUNCH(ctx, "k_rs_scatter");
+        cur = 1 - cur;
+    }
+    *which = cur;
+    return HCGS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// orchestration of steps 1-2
+// ---------------------------------------------------------------------------
+static int bits_for(uint64_t n) {
+    int b = 1;
+    while ((1ull << b) < n) b++;
+    return b;
+}
+
+hcgs_status project_and_bin(hcgs_ctx* ctx, hcgs_saved* s, const hcgs_gaussians* g, const float* viewmats,
+                            const float* intr, cudaStream_t st) {
+    const int V = s->V, N = s->N, C = s->C, L = s->L;
+    const size_t VN = (size_t)V * N;
+    const int NR = rec_count(C);
+    size_t* ob = &s->bytes;
+    HCGS_CUDA(ctx, grow(ctx, s->w, (size_t)N * C * sizeof(float2), ob));
+    HCGS_CUDA(ctx, grow(ctx, s->proj, VN * 2 * sizeof(float4), ob));
+    HCGS_CUDA(ctx, grow(ctx, s->rectn, VN * sizeof(uint2), ob));
+    HCGS_CUDA(ctx, grow(ctx, s->dkey, 2 * VN * sizeof(uint32_t), ob));
+    HCGS_CUDA(ctx, grow(ctx, s->dval, 2 * VN * sizeof(uint32_t), ob));
+    HCGS_CUDA(ctx, grow(ctx, s->nvalid, V * sizeof(uint32_t), ob));
+    HCGS_CUDA(ctx, grow(ctx, s->rank, VN * sizeof(uint32_t), ob));
+    HCGS_CUDA(ctx, grow(ctx, s->sortid, VN * sizeof(uint32_t), ob));
+    HCGS_CUDA(ctx, grow(ctx, s->rec, VN * NR * sizeof(float4), ob));
+    HCGS_CUDA(ctx, grow(ctx, s->rects, VN * sizeof(uint2), ob));
+    HCGS_CUDA(ctx, grow(ctx, s->planes, VN * sizeof(int), ob));
+    HCGS_CUDA(ctx, grow(ctx, s->ccount, VN * sizeof(uint32_t), ob));
+    HCGS_CUDA(ctx, grow(ctx, s->cam, (size_t)V * 20 * sizeof(float), ob));
+    const size_t NB = (size_t)V * L * s->ctX * s->ctY;
+    HCGS_CUDA(ctx, grow(ctx, s->bcount, (NB + 1) * sizeof(uint32_t), ob));
+
+    float* cam = (float*)s->cam.p;
+    for (int v = 0; v < V; v++) {
+        HCGS_CUDA(ctx, cudaMemcpyAsync(cam + 20 * v, viewmats + 16 * v, 16 * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        HCGS_CUDA(ctx, cudaMemcpyAsync(cam + 20 * v + 16, intr + 4 * v, 4 * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    }
+    ProjArgs a = make_proj_args(s);
+    const int T = 256;
+    HCGS_KERNEL(ctx, "k_prep_w", st, k_prep_w<<<(N * C + T - 1) / T, T, 0, st>>>(g->amplitude, g->phase, (float2*)s->w.p, N, C));
+    HCGS_CUDA(ctx, cudaMemsetAsync(s->nvalid.p, 0, V * sizeof(uint32_t), st));
+    const unsigned gridVN = (unsigned)((VN + T - 1) / T);
+    uint32_t* dkey = (uint32_t*)s->dkey.p;
+    uint32_t* dval = (uint32_t*)s->dval.p;
+    HCGS_KERNEL(ctx, "k_project", st, k_project<<<gridVN, T, 0, st>>>(a, g->means, g->log_scales, g->quats, g->opacity_logits, g->plane_logits, cam,
+                                    (float4*)s->proj.p, (uint2*)s->rectn.p, dkey, dval, (uint32_t*)s->nvalid.p));
+    HCGS_LAUNCH(ctx, "k_project");
+    int which = 0;
+    hcgs_status e = radix_sort(ctx, s, dkey, dval, V, N, 32, &which, st);
+    if (e) return e;
+    HCGS_KERNEL(ctx, "k_gather", st, k_gather<<<gridVN, T, 0, st>>>(a, dval + (size_t)which * VN, (const uint32_t*)s->nvalid.p,
+                                   (const float4*)s->proj.p, (const uint2*)s->rectn.p, (const float2*)s->w.p,
+                                   s->opts.order, (uint32_t*)s->rank.p, (uint32_t*)s->sortid.p, (float4*)s->rec.p,
+                                   (uint2*)s->rects.p, (int*)s->planes.p, (uint32_t*)s->ccount.p));
+    HCGS_LAUNCH(ctx, "k_gather");
+    uint32_t* coff = (uint32_t*)s->ccount.p;
+    if ((e = exclusive_scan(ctx, s, coff, coff, VN, st))) return e;
+    // the instance count sizes the instance buffers: one readback
+    HCGS_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, scan_total_ptr(s, VN), 8, cudaMemcpyDeviceToHost, st));
+    HCGS_CUDA(ctx, cudaStreamSynchronize(st));
+    const unsigned long long M = *(unsigned long long*)ctx->h_pinned;
+    if (M >= (1ull << 31)) {
+        set_err(ctx, HCGS_ERR_CAPACITY, "more than 2^31 bucket instances");
+        return HCGS_ERR_CAPACITY;
+    }
+    s->M = M;
+    const size_t Mc = M > 0 ? (size_t)M : 1;
+    HCGS_CUDA(ctx, grow(ctx, s->ikey, 2 * Mc * sizeof(uint32_t), ob));
+    HCGS_CUDA(ctx, grow(ctx, s->ival, 2 * Mc * sizeof(uint32_t), ob));
+    uint32_t* ikey = (uint32_t*)s->ikey.p;
+    uint32_t* ival = (uint32_t*)s->ival.p;
+    HCGS_KERNEL(ctx, "k_inst_gen", st, k_inst_gen<<<gridVN, T, 0, st>>>(a, coff, (const uint2*)s->rects.p, (const int*)s->planes.p,
+                                     (const uint32_t*)s->nvalid.p, ikey, ival));
+    HCGS_LAUNCH(ctx, "k_inst_gen");
+    if ((e = radix_sort(ctx, s, ikey, ival, 1, (size_t)M, bits_for(NB), &which, st))) return e;
+    const uint32_t* skey = ikey + (size_t)which * M;
+    s->list = ival + (size_t)which * M;
+    HCGS_KERNEL(ctx, "k_bucket_bounds", st, k_bucket_bounds<<<(unsigned)((M + 1 + T - 1) / T), T, 0, st>>>(skey, (uint32_t)M, (uint32_t)NB,
+                                                                  (uint32_t*)s->bcount.p));
+    HCGS_LAUNCH(ctx, "k_bucket_bounds");
+    return HCGS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// adjoint of the projection (Supp. D.4) and of the plane argmax (Eq. ste)
+// ---------------------------------------------------------------------------
+__global__ void k_project_bwd(ProjArgs a, const float* __restrict__ means, const float* __restrict__ log_scales,
+                              const float* __restrict__ quats, const float* __restrict__ opacity_logits,
+                              const float* __restrict__ amplitude, const float* __restrict__ phase,
+                              const float* __restrict__ plane_logits, const float* __restrict__ cam,
+                              const uint32_t* __restrict__ rank, const float* __restrict__ g2d, float ste_tau,
+                              hcgs_gaussian_grads gr, int accumulate) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= a.N) return;
+    const int C = a.C, G = g2d_count(C);
+    float gm[3] = {0, 0, 0}, gls[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0};
+    float gol = 0.f, drho = 0.f;
+    float gwr[MAX_C] = {0, 0, 0, 0}, gwi[MAX_C] = {0, 0, 0, 0};
+    for (int v = 0; v < a.V; v++) {
+        const uint32_t s = rank[(size_t)v * a.N + n];
+        if (s == 0xFFFFFFFFu) continue;
+        const float* g = g2d + ((size_t)v * a.N + s) * G;
+        for (int c = 0; c < C; c++) {
+            gwr[c] += g[6 + 2 * c];
+            gwi[c] += g[7 + 2 * c];
+        }
+        ProjF P;
+        project_one(a, means + 3 * n, log_scales + 3 * n, quats + 4 * n, opacity_logits[n], cam + 20 * v, P);
+        if (!P.valid) continue;
+        const float go = g[5];
+        gol += go * P.o * (1.f - P.o);
+        drho += P.o * go;
+        project_one_backward(a, P, cam + 20 * v, make_float2(g[0], g[1]), g[2], g[3], g[4], gm, gls, gq);
+    }
+    // appearance: w_c = a_c (cos phi_c, sin phi_c)
+    for (int c = 0; c < C; c++) {
+        float sn, cs;
+        sincosf(phase[n * C + c], &sn, &cs);
+        const float ga = gwr[c] * cs + gwi[c] * sn;
+        const float gp = amplitude[n * C + c] * (-gwr[c] * sn + gwi[c] * cs);
+        if (accumulate) {
+            gr.amplitude[n * C + c] += ga;
+            gr.phase[n * C + c] += gp;
+        } else {
+            gr.amplitude[n * C + c] = ga;
+            gr.phase[n * C + c] = gp;
+        }
+    }
+    // straight-through plane logits: elementwise product with softmax(rho'/tau)
+    const float* r = plane_logits + (size_t)n * a.L;
+    int am = 0;
+    float mx = r[0];
+    for (int l = 1; l < a.L; l++)
+        if (r[l] > mx) { mx = r[l]; am = l; }
+    float Z = 0.f;
+    for (int l = 0; l < a.L; l++) Z += expf((r[l] - mx) / ste_tau);
+    const float sm_a = 1.f / Z;  // softmax at the argmax: exp(0) / Z
+    for (int l = 0; l < a.L; l++) {
+        const float gv = l == am ? drho * sm_a : 0.f;
+        if (accumulate) gr.plane_logits[(size_t)n * a.L + l] += gv;
+        else gr.plane_logits[(size_t)n * a.L + l] = gv;
+    }
+    if (accumulate) {
+        for (int k = 0; k < 3; k++) { gr.means[3 * n + k] += gm[k]; gr.log_scales[3 * n + k] += gls[k]; }
+        for (int k = 0; k < 4; k++) gr.quats[4 * n + k] += gq[k];
+        gr.opacity_logits[n] += gol;
+    } else {
+        for (int k = 0; k < 3; k++) { gr.means[3 * n + k] = gm[k]; gr.log_scales[3 * n + k] = gls[k]; }
+        for (int k = 0; k < 4; k++) gr.quats[4 * n + k] = gq[k];
+        gr.opacity_logits[n] = gol;
+    }
+}
+
+hcgs_status project_backward(hcgs_ctx* ctx, hcgs_saved* s, const hcgs_gaussians* g,
+                             const hcgs_gaussian_grads* gr, int accumulate, cudaStream_t st) {
+    ProjArgs a = make_proj_args(s);
+    HCGS_KERNEL(ctx, "k_project_bwd", st, k_project_bwd<<<(s->N + 127) / 128, 128, 0, st>>>(a, g->means, g->log_scales, g->quats, g->opacity_logits,
+                                                      g->amplitude, g->phase, g->plane_logits,
+                                                      (const float*)s->cam.p, (const uint32_t*)s->rank.p,
+                                                      (const float*)s->g2d.p, s->opts.ste_tau, *gr, accumulate));
+    HCGS_LAUNCH(ctx, "k_project_bwd");
+    return HCGS_OK;
+}
+
+}  // namespace hcgs

@@ -1,0 +1,306 @@
+// Step 3 of the render path on sm_103a: complex multi-plane compositing
+// (Sec. 4.1 per-plane field equation; Algorithm 2) and its adjoint (Supp. D.4;
+// Sec. 4.2: back-to-front walk, transmittance recovered by division).
+//
+// One CTA of 256 threads per (16x16 tile, plane, view); one pixel per
+// thread.  The CTA streams its 64x64 bucket's list (already in visiting
+// order), keeps the entries whose tile rectangle covers the tile (warp ballot
+// compaction keeps the order), stages their records in shared memory, and
+// every pixel walks them: alpha = min(alpha_max, o exp(-power)); skip when
+// alpha < alpha_min; U += w alpha T; T *= 1 - alpha; stop once T < T_eps.
+// The CTA leaves the list when all 256 pixels have stopped.
+//
+// The alpha arithmetic uses explicitly rounded intrinsics so that the forward
+// and backward kernels take identical skip/stop decisions.
+#include "common.cuh"
+#include "project.cuh"
+
+namespace hcgs {
+
+struct RasterArgs {
+    const float4* rec;
+    const uint2* rects;
+    const uint32_t* off;
+    const uint32_t* list;
+    int V, N, L, H, W, tilesX, tilesY, ctX, ctY;
+    float amin, amax, teps;
+};
+
+static RasterArgs make_raster_args(const hcgs_saved* s) {
+    RasterArgs a;
+    a.rec = (const float4*)s->rec.p;
+    a.rects = (const uint2*)s->rects.p;
+    a.off = (const uint32_t*)s->bcount.p;
+    a.list = s->list;
+    a.V = s->V; a.N = s->N; a.L = s->L; a.H = s->H; a.W = s->W;
+    a.tilesX = s->tilesX; a.tilesY = s->tilesY; a.ctX = s->ctX; a.ctY = s->ctY;
+    a.amin = s->opts.alpha_min; a.amax = s->opts.alpha_max; a.teps = s->opts.T_eps;
+    return a;
+}
+
+// power = 1/2 (A dx^2 + C dy^2) + B dx dy, d = pixel - mu (Supp. D.3 exponent term)
+__device__ __forceinline__ float footprint_power(float px, float py, float4 r0, float Cc, float* dxo, float* dyo) {
+    const float dx = __fsub_rn(px, r0.x), dy = __fsub_rn(py, r0.y);
+    float p = __fmul_rn(0.5f, __fmaf_rn(r0.z, __fmul_rn(dx, dx), __fmul_rn(Cc, __fmul_rn(dy, dy))));
+    p = __fmaf_rn(r0.w, __fmul_rn(dx, dy), p);
+    *dxo = dx;
+    *dyo = dy;
+    return p;
+}
+
+template <int C>
+struct RecW {
+    static __device__ __forceinline__ float2 get(const float4* r, int c) {
+        if (c == 0) return make_float2(r[1].z, r[1].w);
+        if (c == 1) return make_float2(r[2].x, r[2].y);
+        if (c == 2) return make_float2(r[2].z, r[2].w);
+        return make_float2(r[3].x, r[3].y);
+    }
+};
+
+// Stream one batch (positions [lo, hi) of the bucket) and compact the entries
+// that touch tile (tx, ty) into shared memory, keeping their order.
+template <int NR>
+__device__ __forceinline__ int stage_batch(const RasterArgs& a, size_t vN, uint32_t beg, uint32_t lo, uint32_t hi,
+                                           int tx, int ty, float4 (*srec)[NR], uint32_t* spos, uint32_t* sid,
+                                           int* wcnt) {
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const uint32_t p = lo + (uint32_t)t;
+    bool ok = false;
+    uint32_t s = 0;
+    if (p < hi) {
+        s = a.list[beg + p];
+        const uint2 rc = a.rects[vN + s];
+        ok = (uint32_t)tx >= (rc.x & 0xFFFFu) && (uint32_t)tx < (rc.x >> 16) && (uint32_t)ty >= (rc.y & 0xFFFFu) &&
+             (uint32_t)ty < (rc.y >> 16);
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, ok);
+    if (lane == 0) wcnt[warp] = __popc(bal);
+    __syncthreads();
+    int base = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < 8; w++) {
+        const int c = wcnt[w];
+        base += w < warp ? c : 0;
+        total += c;
+    }
+    if (ok) {
+        const int slot = base + __popc(bal & ((1u << lane) - 1u));
+        spos[slot] = p;
+        sid[slot] = s;
+        const float4* r = a.rec + (vN + s) * NR;
+#pragma unroll
+        for (int k = 0; k < NR; k++) srec[slot][k] = r[k];
+    }
+    __syncthreads();
+    return total;
+}
+
+template <int C>
+__global__ void __launch_bounds__(256) k_raster_fwd(RasterArgs a, float2* __restrict__ U, float* __restrict__ Tsave,
+                                                    uint32_t* __restrict__ lastsave, float* __restrict__ Tout,
+                                                    int32_t* __restrict__ ncout) {
+    constexpr int NR = C <= 1 ? 2 : (C <= 3 ? 3 : 4);
+    __shared__ float4 srec[256][NR];
+    __shared__ uint32_t spos[256], sid[256];
+    __shared__ int wcnt[8];
+    const int t = threadIdx.x;
+    const int tile = blockIdx.x, l = blockIdx.y, v = blockIdx.z;
+    const int tx = tile % a.tilesX, ty = tile / a.tilesX;
+    const int px = tx * TILE + (t & 15), py = ty * TILE + (t >> 4);
+    const bool inside = px < a.W && py < a.H;
+    const uint32_t gb = ((uint32_t)(v * a.L + l) * a.ctY + ty / COARSE) * a.ctX + tx / COARSE;
+    const uint32_t beg = a.off[gb], n = a.off[gb + 1] - beg;
+    const size_t vN = (size_t)v * a.N;
+    const float fpx = (float)px, fpy = (float)py;
+    float T = 1.f;
+    float2 acc[C];
+#pragma unroll
+    for (int c = 0; c < C; c++) acc[c] = make_float2(0.f, 0.f);
+    bool done = !inside;
+    uint32_t lastp = 0;
+    int nc = 0;
+    for (uint32_t lo = 0; lo < n; lo += 256) {
+        if (__syncthreads_count(!done) == 0) break;
+        const uint32_t hi = min(n, lo + 256u);
+        const int total = stage_batch<NR>(a, vN, beg, lo, hi, tx, ty, srec, spos, sid, wcnt);
+        if (!done) {
+            for (int k = 0; k < total; k++) {
+                const float4 r0 = srec[k][0], r1 = srec[k][1];
+                float dx, dy;
+                const float power = footprint_power(fpx, fpy, r0, r1.x, &dx, &dy);
+                const float alpha = fminf(a.amax, __fmul_rn(r1.y, __expf(-power)));
+                if (alpha < a.amin) continue;
+                const float wt = __fmul_rn(alpha, T);
+#pragma unroll
+                for (int c = 0; c < C; c++) {
+                    const float2 w = RecW<C>::get(srec[k], c);
+                    acc[c].x = __fmaf_rn(w.x, wt, acc[c].x);
+                    acc[c].y = __fmaf_rn(w.y, wt, acc[c].y);
+                }
+                T = __fmul_rn(T, __fsub_rn(1.f, alpha));
+                nc++;
+                lastp = spos[k] + 1;
+                if (T < a.teps) {
+                    done = true;
+                    break;
+                }
+            }
+        }
+    }
+    if (inside) {
+        const size_t pix = (size_t)py * a.W + px;
+        const size_t plane = (size_t)v * a.L + l;
+        const size_t HW = (size_t)a.H * a.W;
+#pragma unroll
+        for (int c = 0; c < C; c++) U[(plane * C + c) * HW + pix] = acc[c];
+        Tsave[plane * HW + pix] = T;
+        lastsave[plane * HW + pix] = lastp;
+        if (Tout) Tout[plane * HW + pix] = T;
+        if (ncout) ncout[plane * HW + pix] = nc;
+    }
+}
+
+template <int C>
+__global__ void __launch_bounds__(256) k_raster_bwd(RasterArgs a, const float* __restrict__ Tsave,
+                                                    const uint32_t* __restrict__ lastsave,
+                                                    const float2* __restrict__ gU, float* __restrict__ g2d) {
+    constexpr int NR = C <= 1 ? 2 : (C <= 3 ? 3 : 4);
+    constexpr int G = 6 + 2 * C;
+    __shared__ float4 srec[256][NR];
+    __shared__ uint32_t spos[256], sid[256];
+    __shared__ int wcnt[8];
+    __shared__ uint32_t smax;
+    const int t = threadIdx.x, lane = t & 31;
+    const int tile = blockIdx.x, l = blockIdx.y, v = blockIdx.z;
+    const int tx = tile % a.tilesX, ty = tile / a.tilesX;
+    const int px = tx * TILE + (t & 15), py = ty * TILE + (t >> 4);
+    const bool inside = px < a.W && py < a.H;
+    const uint32_t gb = ((uint32_t)(v * a.L + l) * a.ctY + ty / COARSE) * a.ctX + tx / COARSE;
+    const uint32_t beg = a.off[gb];
+    const size_t vN = (size_t)v * a.N;
+    const size_t plane = (size_t)v * a.L + l;
+    const size_t HW = (size_t)a.H * a.W;
+    const size_t pix = (size_t)py * a.W + px;
+    const float fpx = (float)px, fpy = (float)py;
+    float T = 1.f;
+    uint32_t lastp = 0;
+    float2 g[C], S[C];
+#pragma unroll
+    for (int c = 0; c < C; c++) {
+        g[c] = make_float2(0.f, 0.f);
+        S[c] = make_float2(0.f, 0.f);
+    }
+    if (inside) {
+        T = Tsave[plane * HW + pix];
+        lastp = lastsave[plane * HW + pix];
+#pragma unroll
+        for (int c = 0; c < C; c++) g[c] = gU[(plane * C + c) * HW + pix];
+    }
+    if (t == 0) smax = 0;
+    __syncthreads();
+    if (lastp) atomicMax(&smax, lastp);
+    __syncthreads();
+    const uint32_t maxlast = smax;
+    for (uint32_t hi = maxlast; hi > 0;) {
+        const uint32_t lo = hi > 256u ? hi - 256u : 0u;
+        __syncthreads();  // previous batch fully consumed
+        const int total = stage_batch<NR>(a, vN, beg, lo, hi, tx, ty, srec, spos, sid, wcnt);
+        for (int k = total - 1; k >= 0; k--) {
+            float gl[G];
+#pragma unroll
+            for (int e = 0; e < G; e++) gl[e] = 0.f;
+            bool contrib = false;
+            if (spos[k] < lastp) {
+                const float4 r0 = srec[k][0], r1 = srec[k][1];
+                float dx, dy;
+                const float power = footprint_power(fpx, fpy, r0, r1.x, &dx, &dy);
+                const float G_ = __expf(-power);
+                const float og = __fmul_rn(r1.y, G_);
+                const float alpha = fminf(a.amax, og);
+                if (alpha >= a.amin) {
+                    contrib = true;
+                    const float om = __fsub_rn(1.f, alpha);
+                    const float Tk = __fdiv_rn(T, om);
+                    const float aT = alpha * Tk;
+                    const float iom = 1.f / om;
+                    float dLda = 0.f;
+#pragma unroll
+                    for (int c = 0; c < C; c++) {
+                        const float2 w = RecW<C>::get(srec[k], c);
+                        dLda += g[c].x * (w.x * Tk - S[c].x * iom) + g[c].y * (w.y * Tk - S[c].y * iom);
+                        S[c].x += w.x * aT;
+                        S[c].y += w.y * aT;
+                        gl[6 + 2 * c] = g[c].x * aT;
+                        gl[7 + 2 * c] = g[c].y * aT;
+                    }
+                    T = Tk;
+                    if (og <= a.amax) {  // a clamped alpha is flat in o G
+                        const float dLdp = -dLda * og;
+                        gl[5] = dLda * G_;
+                        gl[0] = -dLdp * (r0.z * dx + r0.w * dy);
+                        gl[1] = -dLdp * (r0.w * dx + r1.x * dy);
+                        gl[2] = 0.5f * dx * dx * dLdp;
+                        gl[3] = dx * dy * dLdp;
+                        gl[4] = 0.5f * dy * dy * dLdp;
+                    }
+                }
+            }
+            if (__any_sync(0xffffffffu, contrib)) {
+#pragma unroll
+                for (int e = 0; e < G; e++) {
+                    float x = gl[e];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                    gl[e] = x;
+                }
+                if (lane == 0) {
+                    float* dst = g2d + (vN + sid[k]) * G;
+#pragma unroll
+                    for (int e = 0; e < G; e++) atomicAdd(dst + e, gl[e]);
+                }
+            }
+        }
+        hi = lo;
+    }
+}
+
+hcgs_status raster_forward(hcgs_ctx* ctx, hcgs_saved* s, float2* U, float* T_out, int32_t* nc_out,
+                           cudaStream_t st) {
+    const size_t pl = (size_t)s->V * s->L * s->H * s->W;
+    HCGS_CUDA(ctx, grow(ctx, s->Tfin, pl * sizeof(float), &s->bytes));
+    HCGS_CUDA(ctx, grow(ctx, s->last, pl * sizeof(uint32_t), &s->bytes));
+    RasterArgs a = make_raster_args(s);
+    dim3 grid(s->tilesX * s->tilesY, s->L, s->V);
+    float* Ts = (float*)s->Tfin.p;
+    uint32_t* ls = (uint32_t*)s->last.p;
+    switch (s->C) {
+        case 1: HCGS_KERNEL(ctx, "k_raster_fwd", st, k_raster_fwd<1><<<grid, 256, 0, st>>>(a, U, Ts, ls, T_out, nc_out)); break;
+        case 2: HCGS_KERNEL(ctx, "k_raster_fwd", st, k_raster_fwd<2><<<grid, 256, 0, st>>>(a, U, Ts, ls, T_out, nc_out)); break;
+        case 3: HCGS_KERNEL(ctx, "k_raster_fwd", st, k_raster_fwd<3><<<grid, 256, 0, st>>>(a, U, Ts, ls, T_out, nc_out)); break;
+        default: HCGS_KERNEL(ctx, "k_raster_fwd", st, k_raster_fwd<4><<<grid, 256, 0, st>>>(a, U, Ts, ls, T_out, nc_out)); break;
+    }
+    HCGS_LAUNCH(ctx, "k_raster_fwd");
+    return HCGS_OK;
+}
+
+hcgs_status raster_backward(hcgs_ctx* ctx, hcgs_saved* s, const float2* gU, cudaStream_t st) {
+    const size_t ng = (size_t)s->V * s->N * g2d_count(s->C);
+    HCGS_CUDA(ctx, grow(ctx, s->g2d, ng * sizeof(float), &s->bytes));
+    HCGS_CUDA(ctx, cudaMemsetAsync(s->g2d.p, 0, ng * sizeof(float), st));
+    RasterArgs a = make_raster_args(s);
+    dim3 grid(s->tilesX * s->tilesY, s->L, s->V);
+    const float* Ts = (const float*)s->Tfin.p;
+    const uint32_t* ls = (const uint32_t*)s->last.p;
+    float* g2 = (float*)s->g2d.p;
+    switch (s->C) {
+        case 1: HCGS_KERNEL(ctx, "k_raster_bwd", st, k_raster_bwd<1><<<grid, 256, 0, st>>>(a, Ts, ls, gU, g2)); break;
+        case 2: HCGS_KERNEL(ctx, "k_raster_bwd", st, k_raster_bwd<2><<<grid, 256, 0, st>>>(a, Ts, ls, gU, g2)); break;
+        case 3: HCGS_KERNEL(ctx, "k_raster_bwd", st, k_raster_bwd<3><<<grid, 256, 0, st>>>(a, Ts, ls, gU, g2)); break;
+        default: HCGS_KERNEL(ctx, "k_raster_bwd", st, k_raster_bwd<4><<<grid, 256, 0, st>>>(a, Ts, ls, gU, g2)); break;
+    }
+    HCGS_LAUNCH(ctx, "k_raster_bwd");
+    return HCGS_OK;
+}
+
+}  // namespace hcgs

@@ -1,0 +1,280 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances: relative L2 <= 1e-4 for the FP32 render path (fields U and
+hologram P), 1e-5 for the FP32 FFT-based propagation alone (its rounding
+error is ~1e-6 at these lengths), 1e-3 per parameter class for gradients
+(FP32 atomics), 1e-2 for the BF16 network.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import hcgs_synth as S
+import oracle
+from gpu_common import cams, cams_dev, complex_dev, dev, oracle_opts, rel
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2506_08350_b300 as P
+    return P
+
+
+@pytest.fixture(scope="module")
+def ctx(P):
+    return P.Context(0)
+
+
+def _rand_planes(B, L, C, H, W, seed):
+    return S.random_complex((B, L, C, H, W), seed=seed)
+
+
+# ---------------------------------------------------------------------------
+# propagation
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("H,W,L,C,B", [(256, 256, 2, 1, 1), (120, 200, 3, 2, 2), (45, 96, 1, 3, 1),
+                                       (1080, 1920, 2, 1, 1)])
+def test_asm_forward_recording(P, ctx, H, W, L, C, B):
+    wl = S.WAVELENGTHS_RGB[:C] if C > 1 else (515e-9,)
+    z = tuple(np.linspace(0.0, 10e-3, L))
+    opt = S.Optics(H, W, wl, z)
+    U = _rand_planes(B, L, C, H, W, seed=1)
+    out = torch.empty((B, C, H, W), dtype=torch.complex64, device="cuda")
+    ctx.asm_propagate(complex_dev(U), B, opt, 1, 1, out)
+    got = out.cpu().numpy()
+    for b in range(B):
+        ref = oracle.propagate_planes(U[b].astype(np.complex128), opt.pitch, wl, z)
+        assert rel(got[b], ref) < 1e-5, rel(got[b], ref)
+
+
+@pytest.mark.parametrize("H,W,L,C,B", [(256, 256, 2, 1, 1), (120, 200, 3, 2, 2)])
+def test_asm_inverse_and_adjoint(P, ctx, H, W, L, C, B):
+    wl = S.WAVELENGTHS_RGB[:C] if C > 1 else (515e-9,)
+    z = tuple(np.linspace(0.0, 8e-3, L))
+    opt = S.Optics(H, W, wl, z)
+    Pin = S.random_complex((B, C, H, W), seed=2)
+    out = torch.empty((B, L, C, H, W), dtype=torch.complex64, device="cuda")
+    ctx.asm_propagate(complex_dev(Pin), B, opt, -1, 0, out)
+    got = out.cpu().numpy()
+    for b in range(B):
+        ref = oracle.inverse_propagate(Pin[b].astype(np.complex128), opt.pitch, wl, z)
+        assert rel(got[b], ref) < 1e-5
+    # adjoint of forward recording
+    gU = torch.empty((B, L, C, H, W), dtype=torch.complex64, device="cuda")
+    ctx.asm_propagate_backward(complex_dev(Pin), B, opt, 1, 1, gU)
+    got = gU.cpu().numpy()
+    for b in range(B):
+        ref = oracle.propagate_planes_adjoint(Pin[b].astype(np.complex128), opt.pitch, wl, z)
+        assert rel(got[b], ref) < 1e-5
+
+
+def test_asm_rejects_unsupported_length(P, ctx):
+    opt = S.Optics(7 * 16, 64, (515e-9,), (0.0,))
+    x = torch.zeros((1, 1, 1, 7 * 16, 64), dtype=torch.complex64, device="cuda")
+    y = torch.zeros((1, 1, 7 * 16, 64), dtype=torch.complex64, device="cuda")
+    with pytest.raises(P.HcgsError, match="UNSUPPORTED_SIZE"):
+        ctx.asm_propagate(x, 1, opt, 1, 1, y)
+
+
+# ---------------------------------------------------------------------------
+# full render
+# ---------------------------------------------------------------------------
+def _render_both(P, ctx, g, optics, V, opts, seed=0, planes=True):
+    vm, it = cams(V, optics.H, optics.W, seed=seed)
+    gd = dev(g)
+    vmd, itd = cams_dev(vm, it)
+    holo = torch.empty((V, optics.C, optics.H, optics.W), dtype=torch.complex64, device="cuda")
+    U = torch.empty((V, optics.L, optics.C, optics.H, optics.W), dtype=torch.complex64, device="cuda")
+    saved = P.Saved(ctx)
+    ctx.render_view(gd, vmd, itd, optics, opts, holo, U, saved)
+    torch.cuda.synchronize()
+    Po, Uo, To, No = oracle.render(g, vm.astype(np.float64), it.astype(np.float64), optics, oracle_opts(opts))
+    return holo.cpu().numpy(), U.cpu().numpy(), Po, Uo, To, No, saved, (gd, vmd, itd, vm, it)
+
+
+def test_render_c1_forward(P, ctx):
+    # 256 x 256, one wavelength, 2 planes at 0 and 5 mm, 1000 Gaussians
+    wl = S.workload("c1_256_L2_N1k")
+    o = wl.optics
+    g = S.make_gaussians(wl.N, o.L, o.C, o.H, o.W, seed=0)
+    opts = dict(P.DEFAULT_OPTS)
+    hp, Ug, Po, Uo, To, No, saved, _ = _render_both(P, ctx, g, o, 1, opts)
+    assert rel(Ug, Uo) < 1e-4, rel(Ug, Uo)
+    assert rel(hp, Po) < 1e-4, rel(hp, Po)
+    # transmittance and contributor counts through the ABI
+    Tg = torch.empty((1, o.L, o.H, o.W), dtype=torch.float32, device="cuda")
+    Ng = torch.empty((1, o.L, o.H, o.W), dtype=torch.int32, device="cuda")
+    U2 = torch.empty((1, o.L, o.C, o.H, o.W), dtype=torch.complex64, device="cuda")
+    ctx.rasterize_planes(saved, U2, Tg, Ng)
+    assert np.array_equal(U2.cpu().numpy(), Ug)  # deterministic
+    # FP32 and FP64 may decide alpha >= alpha_min (or T < T_eps) differently
+    # at a handful of support-boundary pixels: count those flips, and require
+    # agreement elsewhere
+    dT = np.abs(Tg.cpu().numpy() - To)
+    flips = Ng.cpu().numpy() != No
+    assert np.mean(flips) < 1e-3, np.mean(flips)
+    assert np.max(dT[~flips]) < 1e-5, np.max(dT[~flips])
+
+
+@pytest.mark.parametrize("order", [0, 1])
+def test_render_rgb_multiview(P, ctx, order):
+    # ragged image (not a multiple of 16 or 64), 3 wavelengths, 4 planes, 2 views
+    o = S.Optics(120, 200, S.WAVELENGTHS_RGB, (0.0, 2e-3, 5e-3, 9e-3))
+    g = S.make_gaussians(3000, o.L, o.C, o.H, o.W, seed=4, log_scale_mean=-3.5)
+    opts = dict(P.DEFAULT_OPTS, order=order)
+    hp, Ug, Po, Uo, To, No, _, _ = _render_both(P, ctx, g, o, 2, opts, seed=3)
+    assert rel(Ug, Uo) < 1e-4, rel(Ug, Uo)
+    assert rel(hp, Po) < 1e-4, rel(hp, Po)
+
+
+def test_render_exact_preset(P, ctx):
+    o = S.Optics(40, 48, (639e-9, 473e-9), (1e-3, 4e-3))
+    g = S.make_gaussians(60, o.L, o.C, o.H, o.W, seed=5, log_scale_mean=-2.0, log_scale_std=0.3)
+    g["means"][:, 2] += 1.0
+    opts = dict(P.EXACT_OPTS)
+    hp, Ug, Po, Uo, To, No, _, _ = _render_both(P, ctx, g, o, 1, opts)
+    assert rel(Ug, Uo) < 1e-4, rel(Ug, Uo)
+    assert rel(hp, Po) < 1e-4
+
+
+def test_render_empty_scene(P, ctx):
+    o = S.Optics(48, 64, (515e-9,), (0.0, 1e-3))
+    g = S.make_gaussians(0, o.L, o.C, o.H, o.W, seed=0)
+    vm, it = cams(1, o.H, o.W)
+    vmd, itd = cams_dev(vm, it)
+    holo = torch.full((1, 1, o.H, o.W), 7.0, dtype=torch.complex64, device="cuda")
+    ctx.render_view(dev(g), vmd, itd, o, P.DEFAULT_OPTS, holo)
+    assert float(holo.abs().max()) == 0.0
+
+
+def test_render_all_culled(P, ctx):
+    # every Gaussian behind the near plane: zero field, zero gradients
+    o = S.Optics(32, 32, (515e-9,), (0.0,))
+    g = S.make_gaussians(50, o.L, o.C, o.H, o.W, seed=1)
+    g["means"][:, 2] = -1.0
+    hp, Ug, Po, Uo, *_ = _render_both(P, ctx, g, o, 1, dict(P.DEFAULT_OPTS))
+    assert np.all(Ug == 0) and np.all(hp == 0) and np.all(Uo == 0)
+
+
+def test_render_c2_full_size_forward(P, ctx):
+    # 1080 x 1920, RGB, 8 planes over 0-10 mm, 100k Gaussians
+    wl = S.workload("c2_1080p_L8_N100k")
+    o = wl.optics
+    g = S.make_gaussians(wl.N, o.L, o.C, o.H, o.W, seed=0)
+    hp, Ug, Po, Uo, To, No, _, _ = _render_both(P, ctx, g, o, 1, dict(P.DEFAULT_OPTS))
+    eU, eP = rel(Ug, Uo), rel(hp, Po)
+    print("c2 forward rel L2: U %.3e  P %.3e" % (eU, eP))
+    assert eU < 1e-4 and eP < 1e-4
+
+
+# ---------------------------------------------------------------------------
+# gradients
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("opts_name,order", [("default", 0), ("default", 1), ("exact", 0)])
+def test_render_backward_vs_oracle(P, ctx, opts_name, order):
+    o = S.Optics(48, 80, (639e-9, 473e-9), (0.0, 3e-3, 7e-3))
+    g = S.make_gaussians(300, o.L, o.C, o.H, o.W, seed=7, log_scale_mean=-2.8, log_scale_std=0.4)
+    g["means"][:, 2] += 0.5
+    base = P.DEFAULT_OPTS if opts_name == "default" else P.EXACT_OPTS
+    opts = dict(base, order=order)
+    V = 2
+    vm, it = cams(V, o.H, o.W, seed=2)
+    gd = dev(g)
+    vmd, itd = cams_dev(vm, it)
+    holo = torch.empty((V, o.C, o.H, o.W), dtype=torch.complex64, device="cuda")
+    saved = P.Saved(ctx)
+    ctx.render_view(gd, vmd, itd, o, opts, holo, None, saved)
+    gP = S.random_complex((V, o.C, o.H, o.W), seed=2)
+    grads = {k: torch.empty_like(gd[k]) for k in P.PARAM_NAMES}
+    ctx.render_view_backward(saved, gd, complex_dev(gP), grads)
+    ref = oracle.render_backward(g, vm.astype(np.float64), it.astype(np.float64), o, gP.astype(np.complex128),
+                                 oracle_opts(opts))
+    for k in P.PARAM_NAMES:
+        e = rel(grads[k].cpu().numpy(), ref[k])
+        print(k, "%.3e" % e)
+        assert e < 1e-3, (k, e)
+
+
+def test_autograd_render_matches_abi(P, ctx):
+    o = S.Optics(32, 48, (515e-9,), (0.0, 2e-3))
+    g = S.make_gaussians(80, o.L, o.C, o.H, o.W, seed=9, log_scale_mean=-2.5, log_scale_std=0.3)
+    vm, it = cams(1, o.H, o.W)
+    vmd, itd = cams_dev(vm, it)
+    gd = {k: v.clone().requires_grad_(True) for k, v in dev(g).items()}
+    holo = P.render(gd, vmd, itd, o, dict(P.DEFAULT_OPTS), context=ctx)
+    gP = complex_dev(S.random_complex(tuple(holo.shape), seed=3))
+    loss = (torch.conj(gP) * holo).real.sum()
+    loss.backward()
+    ref = oracle.render_backward(g, vm.astype(np.float64), it.astype(np.float64), o,
+                                 gP.cpu().numpy().astype(np.complex128), oracle_opts(P.DEFAULT_OPTS))
+    for k in P.PARAM_NAMES:
+        assert rel(gd[k].grad.cpu().numpy(), ref[k]) < 1e-3, k
+
+
+# ---------------------------------------------------------------------------
+# training-step pieces
+# ---------------------------------------------------------------------------
+def test_focal_stack_loss(P, ctx):
+    o = S.Optics(64, 80, (639e-9, 515e-9), (0.0, 2e-3, 6e-3))
+    Pn = S.random_complex((1, o.C, o.H, o.W), seed=4)
+    Igt = S.random_real((1, o.L, o.C, o.H, o.W), seed=5)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    gP = torch.empty((1, o.C, o.H, o.W), dtype=torch.complex64, device="cuda")
+    Iout = torch.empty((1, o.L, o.C, o.H, o.W), dtype=torch.float32, device="cuda")
+    ctx.focal_stack_loss(complex_dev(Pn), torch.from_numpy(Igt).cuda(), 1, o, loss, gP, Iout)
+    l_ref, g_ref, I_ref = oracle.focal_stack_loss(Pn[0].astype(np.complex128), Igt[0].astype(np.float64), o.pitch,
+                                                 o.wavelengths, o.plane_z)
+    assert abs(float(loss.item()) - l_ref) < 1e-5 * abs(l_ref)
+    assert rel(gP.cpu().numpy()[0], g_ref) < 1e-5
+    assert rel(Iout.cpu().numpy()[0], I_ref) < 1e-5
+
+
+def test_adam_step(P, ctx):
+    rng = np.random.default_rng(0)
+    n = 100003
+    p, g = rng.normal(size=n).astype(np.float32), rng.normal(size=n).astype(np.float32)
+    m, v = (rng.normal(size=n) * 0.1).astype(np.float32), (rng.random(n) * 0.1).astype(np.float32)
+    pt, gt, mt, vt = (torch.from_numpy(x.copy()).cuda() for x in (p, g, m, v))
+    ctx.adam_step(pt, gt, mt, vt, 7, 1e-2, 0.9, 0.999, 1e-8)
+    pr, mr, vr = oracle.adam_step(p, g, m, v, 7, 1e-2)
+    assert rel(pt.cpu().numpy(), pr) < 1e-6
+    assert rel(mt.cpu().numpy(), mr) < 1e-6 and rel(vt.cpu().numpy(), vr) < 1e-6
+
+
+def _bf16(a):
+    t = torch.from_numpy(np.asarray(a, dtype=np.float32)).to(torch.bfloat16)
+    return t
+
+
+def test_mlp_forward_backward(P, ctx):
+    rng = np.random.default_rng(1)
+    N = 1000  # ragged: not a multiple of 128
+    dims = [16, 128, 128, 128, 16]
+    Ws = [_bf16(rng.normal(size=(dims[k + 1], dims[k])) / math.sqrt(dims[k])) for k in range(4)]
+    bs = [torch.from_numpy((rng.normal(size=dims[k + 1]) * 0.1).astype(np.float32)) for k in range(4)]
+    x = _bf16(rng.normal(size=(N, 16)))
+    y = torch.empty((N, 16), dtype=torch.float32, device="cuda")
+    Wd = [w.cuda().view(torch.int16) for w in Ws]
+    bd = [b.cuda() for b in bs]
+    xd = x.cuda().view(torch.int16)
+    ctx.mlp_forward(xd, Wd, bd, y)
+    W64 = [w.float().numpy().astype(np.float64) for w in Ws]
+    b64 = [b.numpy().astype(np.float64) for b in bs]
+    x64 = x.float().numpy().astype(np.float64)
+    y_ref, _ = oracle.mlp_forward(x64, W64, b64, act_round="bf16")
+    assert rel(y.cpu().numpy(), y_ref) < 1e-2
+    gy = rng.normal(size=(N, 16)).astype(np.float32)
+    gW = [torch.empty(tuple(w.shape), dtype=torch.float32, device="cuda") for w in Ws]
+    gb = [torch.empty(tuple(b.shape), dtype=torch.float32, device="cuda") for b in bs]
+    ctx.mlp_backward(xd, Wd, bd, torch.from_numpy(gy).cuda(), gW, gb)
+    gW_ref, gb_ref, _ = oracle.mlp_backward(x64, W64, b64, gy.astype(np.float64), act_round="bf16")
+    for k in range(4):
+        assert rel(gW[k].cpu().numpy(), gW_ref[k]) < 1e-2, ("W", k, rel(gW[k].cpu().numpy(), gW_ref[k]))
+        assert rel(gb[k].cpu().numpy(), gb_ref[k]) < 1e-2, ("b", k)

@@ -153,6 +153,30 @@ def test_mlp_reverse_mode():
     assert np.allclose(y, x @ Ws[0].T + bs[0])
 
 
+def test_bf16_rounding_matches_torch():
+    # the oracle's bfloat16 rounding against torch's float32 -> bfloat16 cast
+    import torch
+    rng = np.random.default_rng(3)
+    a = np.concatenate([rng.normal(size=5000) * 10.0 ** rng.integers(-8, 8, size=5000),
+                        [0.0, -0.0, 1.0, 1.00390625, 1.01171875, 65504.0, 3.0e38]])
+    ref = torch.from_numpy(a.astype(np.float32)).to(torch.bfloat16).float().double().numpy()
+    assert np.array_equal(oracle.round_bf16(a), ref)
+
+
+def test_mlp_bf16_activations_change_only_rounding():
+    rng = np.random.default_rng(4)
+    dims = [16, 32, 32, 8]
+    Ws = [rng.normal(size=(dims[k + 1], dims[k])) / 4 for k in range(3)]
+    bs = [rng.normal(size=dims[k + 1]) * 0.1 for k in range(3)]
+    x = oracle.round_bf16(rng.normal(size=(50, 16)))
+    y0, _ = oracle.mlp_forward(x, Ws, bs)
+    y1, pre = oracle.mlp_forward(x, Ws, bs, act_round="bf16")
+    assert 0 < np.max(np.abs(y1 - y0)) < 0.05 * np.max(np.abs(y0))
+    # the input of layer 2 is exactly bf16-representable
+    h = pre[1][0]
+    assert np.array_equal(oracle.round_bf16(h), h)
+
+
 def test_adam_first_step_closed_form():
     # first Adam step: m_hat = g, v_hat = g^2, so p1 = p0 - lr g / (|g| + eps)
     g = np.array([0.3, -2.0, 1e-3])
