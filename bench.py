@@ -1,0 +1,400 @@
+#!/usr/bin/env python
+"""Benchmark of the hologram render path: fwd+bwd views/s.
+
+Workload (default): 1080 x 1920 RGB holograms (639/515/473 nm, 8 um pitch),
+12 depth planes over 0-12 mm, 1M synthetic complex Gaussians, 16 views per
+step.  One step = the whole render path forward (project, depth sort, bin,
+composite, band-limited ASM + plane sum) and its adjoint from a fixed upstream
+gradient dL/dP, through the C ABI, on inputs resident in HBM.  The per-step
+working set (~30 GB) is far larger than L2, so no flush is needed.
+
+Also reported: forward-only views/s, an end-to-end number through the same
+C-ABI calls with the inputs copied from pinned host memory and the parameter
+gradients copied back inside the timed region, per-kernel device time from
+CUDA events with each kernel's roofline, the SM clocks seen during the timed
+region, and the FP64 CPU oracle timed on a bounded sample of the same workload.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import hcgs_synth as S  # noqa: E402
+
+METRIC = "hologram views/s & fwd+bwd steps/s, 1080p RGB 1M Gaussians, vs plain FP32"
+WORKLOAD = "1080p_rgb_L12_N1M_V16"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+
+# FP32-pipe instructions per contributing (pixel, Gaussian) pair, counted from
+# the loop bodies (C = 3): forward 24, adjoint 58 (see the design notes).
+OPS_PER_PAIR = {"k_raster_fwd": 24, "k_raster_bwd": 58}
+KERNEL_SOURCE = {"k_fft_cols": "fft.cu", "k_rows_sum": "fft.cu", "k_rows_spread": "fft.cu",
+                 "k_raster_fwd": "raster.cu", "k_raster_bwd": "raster.cu", "k_project": "project.cu",
+                 "k_project_bwd": "project.cu", "k_rs_scatter": "project.cu", "k_rs_hist": "project.cu",
+                 "k_inst_gen": "project.cu", "k_gather": "project.cu"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernels-out", default=None, help="write the per-kernel table (JSON) here")
+    return ap.parse_args()
+
+
+def src_hash(fname):
+    with open(os.path.join(ROOT, "paper_2506_08350_b300", "csrc", fname), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 7:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx = float(p[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# the CPU oracle on a bounded sample (cpu_baseline leg and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample(wl, rows=16, seed=0):
+    """Times the FP64 oracle on one view of the workload: projection of all N
+    Gaussians, compositing and its adjoint on a band of `rows` image rows (all
+    planes), and one plane-channel of the propagation and of its adjoint;
+    scales each part to a full view.  Returns (views/s for fwd+bwd, s/view,
+    description)."""
+    import oracle
+    o = wl.optics
+    g = S.make_gaussians(wl.N, o.L, o.C, o.H, o.W, seed=seed)
+    vm, it = S.view_batch(1, o.H, o.W, seed=seed)
+    vm, it = vm.astype(np.float32).astype(np.float64), it.astype(np.float32).astype(np.float64)
+    r0 = o.H // 2 - rows // 2
+    t0 = time.perf_counter()
+    pr = oracle.project(g, vm[0], it[0], o.H, o.W)
+    t1 = time.perf_counter()
+    U, T, nc = oracle.composite(pr, rows=(r0, r0 + rows))
+    t2 = time.perf_counter()
+    u = np.asarray(U[0, 0])
+    oracle.propagate(u, o.pitch, o.wavelengths[0], o.plane_z[-1])
+    t3 = time.perf_counter()
+    gP = S.random_complex((1, o.H, o.W), seed=2).astype(np.complex128)
+    oracle.propagate_planes_adjoint(gP, o.pitch, o.wavelengths[:1], o.plane_z[-1:])
+    t4 = time.perf_counter()
+    gU = np.zeros((o.L, o.C, o.H, o.W), dtype=np.complex128)
+    gU[:, :, r0:r0 + rows] = S.random_complex((o.L, o.C, rows, o.W), seed=3)
+    g2 = oracle.composite_backward(pr, gU, rows=(r0, r0 + rows))
+    t5 = time.perf_counter()
+    oracle.project_backward(g, vm[0], it[0], o.H, o.W, g2)
+    t6 = time.perf_counter()
+    frac = rows / o.H
+    LC = o.L * o.C
+    per_view = ((t1 - t0) + (t2 - t1) / frac + (t3 - t2) * LC + (t4 - t3) * LC + (t5 - t4) / frac + (t6 - t5))
+    desc = ("one view of %s: projection and projection adjoint of all %d Gaussians, compositing and its "
+            "adjoint on %d of %d rows (all %d planes), one of %d plane-channel propagations and adjoints; "
+            "each part scaled to a full view" % (wl.name, wl.N, rows, o.H, o.L, LC))
+    return 1.0 / per_view, per_view, desc, time.perf_counter() - t0
+
+
+def omp_threads():
+    try:
+        return int(os.environ.get("OMP_NUM_THREADS", "")) or os.cpu_count()
+    except ValueError:
+        return os.cpu_count()
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 oracle (this method has no reference implementation)
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = S.workload(args.workload)
+    rows = 8
+    times = []
+    for k in range(args.warmup + args.steps):
+        _, per_view, desc, _ = oracle_sample(wl, rows=rows, seed=k)
+        if k >= args.warmup:
+            times.append(per_view)
+    per_view = statistics.median(times)
+    value = 1.0 / per_view
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "views/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_view * wl.V * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wl.name, "H": wl.optics.H, "W": wl.optics.W,
+                                            "C": wl.optics.C, "L": wl.optics.L, "N": wl.N, "V": wl.V},
+            "cpu_baseline": {"value": value, "unit": "views/s", "cores": omp_threads(), "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": "views/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def kernel_models(wl, pairs):
+    """(bound, algorithmic units per step) per kernel: bytes for HBM-bound
+    kernels, FP32-pipe instructions for the ALU-bound rasterizer."""
+    o = wl.optics
+    HW, V, L, C = o.H * o.W, wl.V, o.L, o.C
+    F = V * L * C * HW * 8
+    Pc = V * C * HW * 8
+    table = C * L * (o.H // 2 + 1) * (o.W // 2 + 1) * 8
+    return {
+        # fwd: DFT_cols over V*L*C planes, IDFT_cols over V*C; bwd: DFT_cols over V*C, IDFT_cols over V*L*C
+        "k_fft_cols": ("hbm", 2 * F + 2 * Pc + 2 * Pc + 2 * F),
+        "k_rows_sum": ("hbm", F + Pc + table),
+        "k_rows_spread": ("hbm", Pc + F + table),
+        "k_raster_fwd": ("alu", pairs * OPS_PER_PAIR["k_raster_fwd"]),
+        "k_raster_bwd": ("alu", pairs * OPS_PER_PAIR["k_raster_bwd"]),
+    }
+
+
+def run_ours(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    import paper_2506_08350_b300 as P
+
+    wl = S.workload(args.workload)
+    o = wl.optics
+    V = wl.V
+    # inputs (each rank renders its own batch of views: independent problems)
+    g_np = S.make_gaussians(wl.N, o.L, o.C, o.H, o.W, seed=rank)
+    vm_np, it_np = S.view_batch(V, o.H, o.W, seed=rank)
+    vm_np, it_np = vm_np.astype(np.float32), it_np.astype(np.float32)
+    gP_np = S.random_complex((V, o.C, o.H, o.W), seed=2 + rank)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    g = {k: torch.from_numpy(g_np[k]).to(dev) for k in P.PARAM_NAMES}
+    vm = torch.from_numpy(vm_np).to(dev)
+    it = torch.from_numpy(it_np).to(dev)
+    gP = torch.from_numpy(gP_np).to(dev)
+    holo = torch.empty((V, o.C, o.H, o.W), dtype=torch.complex64, device=dev)
+    grads = {k: torch.empty_like(g[k]) for k in P.PARAM_NAMES}
+    ctx = P.Context(dev.index)
+    saved = P.Saved(ctx)
+    opts = dict(P.DEFAULT_OPTS)
+    stream = torch.cuda.current_stream()
+
+    def fwd():
+        ctx.render_view(g, vm, it, o, opts, holo, None, saved)
+
+    def step():
+        fwd()
+        ctx.render_view_backward(saved, g, gP, grads)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(fn, K):
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1) / K
+        if dist is not None:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # --- headline: fwd+bwd, with per-kernel events and clocks ---
+    ctx.profile_enable(True)
+    with ClockSampler(dev.index) as clk:
+        ms_step = timed(step, args.steps)
+    prof = ctx.profile_summary()
+    ctx.profile_enable(False)
+    clocks = clk.summary()
+    # --- forward only ---
+    for _ in range(2):
+        fwd()
+    ms_fwd = timed(fwd, args.steps)
+    # --- contributing pairs (deterministic; same as in the timed steps) ---
+    U = torch.empty((V, o.L, o.C, o.H, o.W), dtype=torch.complex64, device=dev)
+    nc = torch.empty((V, o.L, o.H, o.W), dtype=torch.int32, device=dev)
+    fwd()
+    ctx.rasterize_planes(saved, U, None, nc)
+    pairs = int(nc.sum(dtype=torch.int64).item())
+    del U, nc
+    # --- end to end through the C ABI with host buffers ---
+    h_in = {k: torch.from_numpy(g_np[k]).pin_memory() for k in P.PARAM_NAMES}
+    h_vm, h_it = torch.from_numpy(vm_np).pin_memory(), torch.from_numpy(it_np).pin_memory()
+    h_gP = torch.from_numpy(gP_np).pin_memory()
+    h_out = {k: torch.empty(tuple(g[k].shape), dtype=torch.float32).pin_memory() for k in P.PARAM_NAMES}
+    h2d = sum(t.numel() * t.element_size() for t in list(h_in.values()) + [h_vm, h_it, h_gP])
+    d2h = sum(t.numel() * t.element_size() for t in h_out.values())
+
+    def e2e_step():
+        for k in P.PARAM_NAMES:
+            g[k].copy_(h_in[k], non_blocking=True)
+        vm.copy_(h_vm, non_blocking=True)
+        it.copy_(h_it, non_blocking=True)
+        gP.copy_(h_gP, non_blocking=True)
+        step()
+        for k in P.PARAM_NAMES:
+            h_out[k].copy_(grads[k], non_blocking=True)
+
+    e2e_step()
+    ms_e2e = timed(e2e_step, args.steps)
+
+    views = V * world
+    value = views / (ms_step / 1e3)
+    result = {"metric": METRIC, "value": value, "unit": "views/s", "n_gpus": world, "steps": args.steps,
+              "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+              "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+              "config": {"workload": wl.name, "H": o.H, "W": o.W, "C": o.C, "L": o.L, "N": wl.N,
+                         "views_per_step_per_gpu": V, "step": "render forward + adjoint from a fixed dL/dP",
+                         "l2": "inputs larger than L2 (~30 GB per step working set), no flush"},
+              "steps_per_s": 1e3 / ms_step, "fwd_views_per_s": views / (ms_fwd / 1e3),
+              "ms_per_fwd": ms_fwd, "clocks": clocks,
+              "e2e": {"value": views / (ms_e2e / 1e3), "unit": "views/s", "h2d_bytes_per_step": h2d,
+                      "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e},
+              "gpu_launches": int(sum(c for _, c in prof.values()))}
+    # --- roofline of the dominant kernel ---
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else None
+    hbm_peak = peaks["hbm_gbs"] if peaks else 6400.0
+    hbm_src = "measured" if peaks else "fallback"
+    f_mhz = clocks["sm_mhz"] or (peaks or {}).get("sm_max_mhz", 2032.0)
+    alu_peak_tops = 148 * 128 * f_mhz * 1e6 / 1e12
+    traffic = json.load(open(TRAFFIC_FILE)) if os.path.exists(TRAFFIC_FILE) else {}
+    models = kernel_models(wl, pairs)
+    table = {}
+    total_ms = sum(ms for ms, _ in prof.values())
+    for name, (ms_tot, cnt) in prof.items():
+        ent = {"ms_per_step": ms_tot / args.steps, "launches_per_step": cnt / args.steps,
+               "share": ms_tot / total_ms if total_ms else None}
+        if name in models:
+            bound, units = models[name]
+            sec = (ms_tot / args.steps) / 1e3
+            if bound == "hbm":
+                ach = units / sec / 1e9
+                ent.update(bound="hbm", achieved=ach, peak=hbm_peak, unit="GB/s", frac=ach / hbm_peak,
+                           algorithmic_bytes_per_step=units)
+            else:
+                ach = units / sec / 1e12
+                ent.update(bound="alu", achieved=ach, peak=alu_peak_tops, unit="Top/s", frac=ach / alu_peak_tops,
+                           pairs_per_step=pairs, ops_per_pair=OPS_PER_PAIR[name])
+            tr = traffic.get(name)
+            if tr and tr.get("source_sha") == src_hash(KERNEL_SOURCE[name]) and tr.get("workload") == wl.name:
+                ent["traffic_bytes_per_launch"] = tr["dram_bytes_per_launch"]
+        table[name] = ent
+    dom = max((k for k in table if "bound" in table[k]), key=lambda k: table[k]["ms_per_step"], default=None)
+    if dom:
+        d = table[dom]
+        lps = d["launches_per_step"] or 1
+        ach_launch = d["achieved"]
+        result["roofline"] = {"kernel": dom, "bound": d["bound"], "achieved": ach_launch, "peak": d["peak"],
+                              "unit": d["unit"], "frac": d["frac"],
+                              "traffic": d.get("traffic_bytes_per_launch"),
+                              "peak_source": (hbm_src if d["bound"] == "hbm" else
+                                              "148 SMs x 128 FP32 lanes x median SM clock %.0f MHz" % f_mhz),
+                              "launches_per_step": lps}
+    result["kernels"] = table
+    if args.kernels_out:
+        with open(args.kernels_out, "w") as fh:
+            json.dump({"workload": wl.name, "pairs": pairs, "kernels": table, "clocks": clocks}, fh, indent=1)
+    # --- CPU oracle baseline (rank 0, N = 1 only) ---
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, per_view, desc, wall = oracle_sample(wl, rows=48)
+        result["cpu_baseline"] = {"value": v, "unit": "views/s", "cores": omp_threads(), "kind": "oracle",
+                                  "sample": desc, "wall_s": wall}
+    saved.release()
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

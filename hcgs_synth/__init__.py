@@ -75,6 +75,9 @@ def workload(name: str) -> Workload:
     if name == "1080p_rgb_L12_N1M_V16":
         z = tuple(float(v) for v in np.linspace(0.0, 12e-3, 12))
         return Workload(name, Optics(1080, 1920, WAVELENGTHS_RGB, z), 1_000_000, 16)
+    if name == "1080p_rgb_L12_N1M_V1":  # one view of the same scene (profiling captures)
+        z = tuple(float(v) for v in np.linspace(0.0, 12e-3, 12))
+        return Workload(name, Optics(1080, 1920, WAVELENGTHS_RGB, z), 1_000_000, 1)
     raise KeyError(name)
 
 

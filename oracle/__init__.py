@@ -153,16 +153,18 @@ def composite(proj: dict, opts=None, rows=None):
     return U[..., 0] + 1j * U[..., 1], T, nc
 
 
-def composite_backward(proj: dict, gU, opts=None):
+def composite_backward(proj: dict, gU, opts=None, rows=None):
     """Adjoint of ``composite``: per-Gaussian gradients w.r.t. mu, conic
-    (A, B, C), the activated opacity and w (= c e^{j phi}, as Re/Im)."""
+    (A, B, C), the activated opacity and w (= c e^{j phi}, as Re/Im).
+    ``rows`` = (row0, row1) restricts the sum to a band of image rows."""
     N, L, C, H, W = (proj[k] for k in ("N", "L", "C", "H", "W"))
+    r0, r1 = (0, H) if rows is None else rows
     g = np.ascontiguousarray(np.stack([np.real(gU), np.imag(gU)], axis=-1), dtype=np.float64)
     out = dict(mu=np.zeros((N, 2)), conic=np.zeros((N, 3)), opac=np.zeros(N), w=np.zeros((N, C, 2)))
     ov = _opt_vec(opts)
     _L().oracle_composite_backward(N, L, C, H, W, _dp(proj["mu"]), _dp(proj["conic"]), _dp(proj["opac"]),
                                    _dp(proj["depth"]), _ip(proj["plane"]), _dp(proj["w"]), _dp(proj["bbox"]),
-                                   _ip(proj["valid"]), _dp(ov), 0, H, _dp(g),
+                                   _ip(proj["valid"]), _dp(ov), int(r0), int(r1), _dp(g),
                                    _dp(out["mu"]), _dp(out["conic"]), _dp(out["opac"]), _dp(out["w"]))
     return out
 

@@ -96,6 +96,22 @@ __device__ __forceinline__ int stage_batch(const RasterArgs& a, size_t vN, uint3
     return total;
 }
 
+// Warp reduce-scatter of 16 values: afterwards lanes 2i and 2i+1 both hold the
+// warp-wide sum of value i (16 shuffles instead of 80 for a full butterfly).
+__device__ __forceinline__ float warp_reduce_scatter16(float (&v)[16], int lane) {
+#pragma unroll
+    for (int half = 8, off = 16; half >= 1; half >>= 1, off >>= 1) {
+        const bool up = lane & off;
+#pragma unroll
+        for (int i = 0; i < half; i++) {
+            const float send = up ? v[i] : v[i + half];
+            const float keep = up ? v[i + half] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
 template <int C>
 __global__ void __launch_bounds__(256) k_raster_fwd(RasterArgs a, float2* __restrict__ U, float* __restrict__ Tsave,
                                                     uint32_t* __restrict__ lastsave, float* __restrict__ Tout,
@@ -207,9 +223,9 @@ __global__ void __launch_bounds__(256) k_raster_bwd(RasterArgs a, const float* _
         __syncthreads();  // previous batch fully consumed
         const int total = stage_batch<NR>(a, vN, beg, lo, hi, tx, ty, srec, spos, sid, wcnt);
         for (int k = total - 1; k >= 0; k--) {
-            float gl[G];
+            float gl[16];
 #pragma unroll
-            for (int e = 0; e < G; e++) gl[e] = 0.f;
+            for (int e = 0; e < 16; e++) gl[e] = 0.f;
             bool contrib = false;
             if (spos[k] < lastp) {
                 const float4 r0 = srec[k][0], r1 = srec[k][1];
@@ -247,18 +263,9 @@ __global__ void __launch_bounds__(256) k_raster_bwd(RasterArgs a, const float* _
                 }
             }
             if (__any_sync(0xffffffffu, contrib)) {
-#pragma unroll
-                for (int e = 0; e < G; e++) {
-                    float x = gl[e];
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-                    gl[e] = x;
-                }
-                if (lane == 0) {
-                    float* dst = g2d + (vN + sid[k]) * G;
-#pragma unroll
-                    for (int e = 0; e < G; e++) atomicAdd(dst + e, gl[e]);
-                }
+                const float sum = warp_reduce_scatter16(gl, lane);
+                const int idx = lane >> 1;
+                if (!(lane & 1) && idx < G) atomicAdd(g2d + (vN + sid[k]) * G + idx, sum);
             }
         }
         hi = lo;
