@@ -36,7 +36,7 @@ __global__ void k_project(ProjArgs a, const float* __restrict__ means, const flo
                           const float* __restrict__ quats, const float* __restrict__ opacity_logits,
                           const float* __restrict__ plane_logits, const float* __restrict__ cam,
                           float4* __restrict__ proj, uint2* __restrict__ rectn, uint32_t* __restrict__ dkey,
-                          uint32_t* __restrict__ dval, uint32_t* __restrict__ nvalid) {
+                          uint32_t* __restrict__ dval) {
     const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (i >= (size_t)a.V * a.N) return;
     const int v = (int)(i / a.N), n = (int)(i - (size_t)v * a.N);
@@ -72,7 +72,6 @@ __global__ void k_project(ProjArgs a, const float* __restrict__ means, const flo
             }
         }
         if (any) rect = make_uint2((uint32_t)tx0 | ((uint32_t)tx1 << 16), (uint32_t)ty0 | ((uint32_t)ty1 << 16));
-        atomicAdd(nvalid + v, 1u);
     }
     proj[2 * i] = make_float4(P.mu.x, P.mu.y, P.conic[0], P.conic[1]);
     proj[2 * i + 1] = make_float4(P.conic[2], P.o, P.depth, __int_as_float(plane));
@@ -80,6 +79,21 @@ __global__ void k_project(ProjArgs a, const float* __restrict__ means, const flo
     // depth >= near_z > 0, so the float bits order like the values
     dkey[i] = P.valid ? __float_as_uint(P.depth) : 0xFFFFFFFFu;
     dval[i] = (uint32_t)n;
+}
+
+// Number of visible Gaussians per view: culled ones carry the key ~0u and
+// sort last, so it is the position of the first ~0u key (binary search).
+__global__ void k_count_visible(const uint32_t* __restrict__ sorted_keys, int N, uint32_t* __restrict__ nvalid) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= gridDim.x * blockDim.x) return;
+    const uint32_t* k = sorted_keys + (size_t)v * N;
+    int lo = 0, hi = N;  // first index with key == ~0u lies in [lo, hi]
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (k[mid] == 0xFFFFFFFFu) hi = mid;
+        else lo = mid + 1;
+    }
+    nvalid[v] = (uint32_t)lo;
 }
 
 // Gaussians in visiting order: records for the rasterizer, ranks, and the
@@ -406,16 +420,16 @@ hcgs_status project_and_bin(hcgs_ctx* ctx, hcgs_saved* s, const hcgs_gaussians* 
     ProjArgs a = make_proj_args(s);
     const int T = 256;
     HCGS_KERNEL(ctx, "k_prep_w", st, k_prep_w<<<(N * C + T - 1) / T, T, 0, st>>>(g->amplitude, g->phase, (float2*)s->w.p, N, C));
-    HCGS_CUDA(ctx, cudaMemsetAsync(s->nvalid.p, 0, V * sizeof(uint32_t), st));
     const unsigned gridVN = (unsigned)((VN + T - 1) / T);
     uint32_t* dkey = (uint32_t*)s->dkey.p;
     uint32_t* dval = (uint32_t*)s->dval.p;
     HCGS_KERNEL(ctx, "k_project", st, k_project<<<gridVN, T, 0, st>>>(a, g->means, g->log_scales, g->quats, g->opacity_logits, g->plane_logits, cam,
-                                    (float4*)s->proj.p, (uint2*)s->rectn.p, dkey, dval, (uint32_t*)s->nvalid.p));
+                                    (float4*)s->proj.p, (uint2*)s->rectn.p, dkey, dval));
     HCGS_LAUNCH(ctx, "k_project");
     int which = 0;
     hcgs_status e = radix_sort(ctx, s, dkey, dval, V, N, 32, &which, st);
     if (e) return e;
+    HCGS_KERNEL(ctx, "k_count_visible", st, k_count_visible<<<V, 1, 0, st>>>(dkey + (size_t)which * VN, N, (uint32_t*)s->nvalid.p));
     HCGS_KERNEL(ctx, "k_gather", st, k_gather<<<gridVN, T, 0, st>>>(a, dval + (size_t)which * VN, (const uint32_t*)s->nvalid.p,
                                    (const float4*)s->proj.p, (const uint2*)s->rectn.p, (const float2*)s->w.p,
                                    s->opts.order, (uint32_t*)s->rank.p, (uint32_t*)s->sortid.p, (float4*)s->rec.p,

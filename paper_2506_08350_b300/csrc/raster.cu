@@ -96,6 +96,30 @@ __device__ __forceinline__ int stage_batch(const RasterArgs& a, size_t vN, uint3
     return total;
 }
 
+// Can Gaussian (mu, conic A B C, opacity o) reach alpha >= alpha_min at any
+// pixel centre of the strip x in [x0, x0 + 15], y in {y0, y0 + 1}?  For each
+// row the footprint quadratic q = A dx^2 + 2 B dx dy + C dy^2 is minimised
+// over the row segment (a convex 1D problem: the unconstrained minimiser
+// clamped to the segment) and compared with 2 ln(o / alpha_min), with a
+// relative and absolute margin far above FP32 rounding.  Never rejects a
+// pixel that the per-pixel test would accept, so skipping is exact.
+__device__ __forceinline__ bool strip_hits(float4 r0, float Cc, float o, float x0, float y0, float amin) {
+    if (amin <= 0.f) return true;
+    if (o < amin) return false;
+    const float k2 = 2.f * __logf(o / amin) * 1.001f + 1e-3f;
+    const float x1 = x0 + 15.f;
+    bool hit = false;
+#pragma unroll
+    for (int r = 0; r < 2; r++) {
+        const float dy = (y0 + (float)r) - r0.y;
+        const float xs = fminf(fmaxf(r0.x - r0.w * dy / r0.z, x0), x1);
+        const float dx = xs - r0.x;
+        const float q = r0.z * dx * dx + 2.f * r0.w * dx * dy + Cc * dy * dy;
+        hit |= q <= k2;
+    }
+    return hit;
+}
+
 // Warp reduce-scatter of 16 values: afterwards lanes 2i and 2i+1 both hold the
 // warp-wide sum of value i (16 shuffles instead of 80 for a full butterfly).
 __device__ __forceinline__ float warp_reduce_scatter16(float (&v)[16], int lane) {
@@ -120,11 +144,12 @@ __global__ void __launch_bounds__(256) k_raster_fwd(RasterArgs a, float2* __rest
     __shared__ float4 srec[256][NR];
     __shared__ uint32_t spos[256], sid[256];
     __shared__ int wcnt[8];
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, lane = t & 31;
     const int tile = blockIdx.x, l = blockIdx.y, v = blockIdx.z;
     const int tx = tile % a.tilesX, ty = tile / a.tilesX;
     const int px = tx * TILE + (t & 15), py = ty * TILE + (t >> 4);
     const bool inside = px < a.W && py < a.H;
+    const float sx0 = (float)(tx * TILE), sy0 = (float)(ty * TILE + 2 * (t >> 5));  // this warp's strip
     const uint32_t gb = ((uint32_t)(v * a.L + l) * a.ctY + ty / COARSE) * a.ctX + tx / COARSE;
     const uint32_t beg = a.off[gb], n = a.off[gb + 1] - beg;
     const size_t vN = (size_t)v * a.N;
@@ -140,8 +165,19 @@ __global__ void __launch_bounds__(256) k_raster_fwd(RasterArgs a, float2* __rest
         if (__syncthreads_count(!done) == 0) break;
         const uint32_t hi = min(n, lo + 256u);
         const int total = stage_batch<NR>(a, vN, beg, lo, hi, tx, ty, srec, spos, sid, wcnt);
-        if (!done) {
-            for (int k = 0; k < total; k++) {
+        for (int k0 = 0; k0 < total; k0 += 32) {
+            if (__all_sync(0xffffffffu, done)) break;
+            // the warp tests 32 staged entries at once against its 16 x 2 strip
+            bool hit = false;
+            if (k0 + lane < total) {
+                const float4 q0 = srec[k0 + lane][0], q1 = srec[k0 + lane][1];
+                hit = strip_hits(q0, q1.x, q1.y, sx0, sy0, a.amin);
+            }
+            unsigned m = __ballot_sync(0xffffffffu, hit);
+            while (m) {
+                const int k = k0 + __ffs(m) - 1;
+                m &= m - 1;
+                if (done) continue;
                 const float4 r0 = srec[k][0], r1 = srec[k][1];
                 float dx, dy;
                 const float power = footprint_power(fpx, fpy, r0, r1.x, &dx, &dy);
@@ -157,10 +193,7 @@ __global__ void __launch_bounds__(256) k_raster_fwd(RasterArgs a, float2* __rest
                 T = __fmul_rn(T, __fsub_rn(1.f, alpha));
                 nc++;
                 lastp = spos[k] + 1;
-                if (T < a.teps) {
-                    done = true;
-                    break;
-                }
+                if (T < a.teps) done = true;
             }
         }
     }
@@ -192,6 +225,7 @@ __global__ void __launch_bounds__(256) k_raster_bwd(RasterArgs a, const float* _
     const int tx = tile % a.tilesX, ty = tile / a.tilesX;
     const int px = tx * TILE + (t & 15), py = ty * TILE + (t >> 4);
     const bool inside = px < a.W && py < a.H;
+    const float sx0 = (float)(tx * TILE), sy0 = (float)(ty * TILE + 2 * (t >> 5));  // this warp's strip
     const uint32_t gb = ((uint32_t)(v * a.L + l) * a.ctY + ty / COARSE) * a.ctX + tx / COARSE;
     const uint32_t beg = a.off[gb];
     const size_t vN = (size_t)v * a.N;
@@ -222,50 +256,62 @@ __global__ void __launch_bounds__(256) k_raster_bwd(RasterArgs a, const float* _
         const uint32_t lo = hi > 256u ? hi - 256u : 0u;
         __syncthreads();  // previous batch fully consumed
         const int total = stage_batch<NR>(a, vN, beg, lo, hi, tx, ty, srec, spos, sid, wcnt);
-        for (int k = total - 1; k >= 0; k--) {
-            float gl[16];
+        for (int k1 = total; k1 > 0; k1 -= 32) {
+            const int k0 = k1 > 32 ? k1 - 32 : 0;
+            bool hit = false;
+            if (k0 + lane < k1) {
+                const float4 q0 = srec[k0 + lane][0], q1 = srec[k0 + lane][1];
+                hit = strip_hits(q0, q1.x, q1.y, sx0, sy0, a.amin);
+            }
+            unsigned m = __ballot_sync(0xffffffffu, hit);
+            while (m) {  // highest bit first: back-to-front over the visiting order
+                const int b = 31 - __clz(m);
+                m &= ~(1u << b);
+                const int k = k0 + b;
+                float gl[16];
 #pragma unroll
-            for (int e = 0; e < 16; e++) gl[e] = 0.f;
-            bool contrib = false;
-            if (spos[k] < lastp) {
-                const float4 r0 = srec[k][0], r1 = srec[k][1];
-                float dx, dy;
-                const float power = footprint_power(fpx, fpy, r0, r1.x, &dx, &dy);
-                const float G_ = __expf(-power);
-                const float og = __fmul_rn(r1.y, G_);
-                const float alpha = fminf(a.amax, og);
-                if (alpha >= a.amin) {
-                    contrib = true;
-                    const float om = __fsub_rn(1.f, alpha);
-                    const float Tk = __fdiv_rn(T, om);
-                    const float aT = alpha * Tk;
-                    const float iom = 1.f / om;
-                    float dLda = 0.f;
+                for (int e = 0; e < 16; e++) gl[e] = 0.f;
+                bool contrib = false;
+                if (spos[k] < lastp) {
+                    const float4 r0 = srec[k][0], r1 = srec[k][1];
+                    float dx, dy;
+                    const float power = footprint_power(fpx, fpy, r0, r1.x, &dx, &dy);
+                    const float G_ = __expf(-power);
+                    const float og = __fmul_rn(r1.y, G_);
+                    const float alpha = fminf(a.amax, og);
+                    if (alpha >= a.amin) {
+                        contrib = true;
+                        const float om = __fsub_rn(1.f, alpha);
+                        const float Tk = __fdiv_rn(T, om);
+                        const float aT = alpha * Tk;
+                        const float iom = 1.f / om;
+                        float dLda = 0.f;
 #pragma unroll
-                    for (int c = 0; c < C; c++) {
-                        const float2 w = RecW<C>::get(srec[k], c);
-                        dLda += g[c].x * (w.x * Tk - S[c].x * iom) + g[c].y * (w.y * Tk - S[c].y * iom);
-                        S[c].x += w.x * aT;
-                        S[c].y += w.y * aT;
-                        gl[6 + 2 * c] = g[c].x * aT;
-                        gl[7 + 2 * c] = g[c].y * aT;
-                    }
-                    T = Tk;
-                    if (og <= a.amax) {  // a clamped alpha is flat in o G
-                        const float dLdp = -dLda * og;
-                        gl[5] = dLda * G_;
-                        gl[0] = -dLdp * (r0.z * dx + r0.w * dy);
-                        gl[1] = -dLdp * (r0.w * dx + r1.x * dy);
-                        gl[2] = 0.5f * dx * dx * dLdp;
-                        gl[3] = dx * dy * dLdp;
-                        gl[4] = 0.5f * dy * dy * dLdp;
+                        for (int c = 0; c < C; c++) {
+                            const float2 w = RecW<C>::get(srec[k], c);
+                            dLda += g[c].x * (w.x * Tk - S[c].x * iom) + g[c].y * (w.y * Tk - S[c].y * iom);
+                            S[c].x += w.x * aT;
+                            S[c].y += w.y * aT;
+                            gl[6 + 2 * c] = g[c].x * aT;
+                            gl[7 + 2 * c] = g[c].y * aT;
+                        }
+                        T = Tk;
+                        if (og <= a.amax) {  // a clamped alpha is flat in o G
+                            const float dLdp = -dLda * og;
+                            gl[5] = dLda * G_;
+                            gl[0] = -dLdp * (r0.z * dx + r0.w * dy);
+                            gl[1] = -dLdp * (r0.w * dx + r1.x * dy);
+                            gl[2] = 0.5f * dx * dx * dLdp;
+                            gl[3] = dx * dy * dLdp;
+                            gl[4] = 0.5f * dy * dy * dLdp;
+                        }
                     }
                 }
-            }
-            if (__any_sync(0xffffffffu, contrib)) {
-                const float sum = warp_reduce_scatter16(gl, lane);
-                const int idx = lane >> 1;
-                if (!(lane & 1) && idx < G) atomicAdd(g2d + (vN + sid[k]) * G + idx, sum);
+                if (__any_sync(0xffffffffu, contrib)) {
+                    const float sum = warp_reduce_scatter16(gl, lane);
+                    const int idx = lane >> 1;
+                    if (!(lane & 1) && idx < G) atomicAdd(g2d + (vN + sid[k]) * G + idx, sum);
+                }
             }
         }
         hi = lo;
