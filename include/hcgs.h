@@ -249,6 +249,32 @@ hcgs_status hcgs_mlp_backward(hcgs_ctx* ctx, const uint16_t* x, int N, const uin
                               const float* gy, float* gW1, float* gW2, float* gW3, float* gW4,
                               float* gb1, float* gb2, float* gb3, float* gb4, void* stream);
 
+/* ---------------- allocation-free inverse propagation ---------------- */
+/* The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc, for example an application whose device memory is
+ * all owned by its own pool allocator (an allocation from inside a library
+ * would fail or fragment that pool), or a display loop that allocates at
+ * start-up and must not stall on cudaMalloc/cudaFree (they synchronise the
+ * device) mid-frame.  It needs no context and allocates nothing.
+ * Result: the same as hcgs_asm_propagate(ctx, in, B, optics, -1, 0, out,
+ * stream), i.e. out[b][l][c] = IDFT(H_{-Z_l} DFT(in[b][c])):
+ *   in   device [B][C][H][W] complex64, not modified
+ *   out  device [B][L][C][H][W] complex64, must not alias `in`
+ * Working memory (column spectrum, transfer-function table, twiddles) lives
+ * in one static device array of 4 Mi complex64 values (32 MiB) that every GPU
+ * loading the library holds until exit.  Requests needing more, i.e.
+ *   B*C*H*W + C*L*(H/2+1)*(W/2+1) + H + W (each rounded up to 64) > 4194304,
+ * return HCGS_ERR_CAPACITY before any launch.  The first call on a device
+ * looks up that device's address of the array (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  All calls share the array and
+ * it keeps the last call's contents (each call rewrites what it reads), so
+ * calls whose kernels overlap on the GPU race: serialise them.  Errors:
+ * HCGS_ERR_INVALID_ARG (NULL/aliased pointers, B < 1, bad optics),
+ * HCGS_ERR_UNSUPPORTED_SIZE (H or W not 2^a 3^b 5^c <= 4096),
+ * HCGS_ERR_CAPACITY (too large), HCGS_ERR_CUDA (a CUDA call failed). */
+hcgs_status hcgs_asm_propagate_noalloc(const float* in, int B, const hcgs_optics* optics, float* out,
+                                       void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -36,7 +36,7 @@ EXPORTS = ("hcgs_ctx_create", "hcgs_ctx_destroy", "hcgs_status_string", "hcgs_la
            "hcgs_asm_propagate", "hcgs_asm_propagate_backward", "hcgs_render_view",
            "hcgs_rasterize_planes_backward", "hcgs_project_backward", "hcgs_render_view_backward",
            "hcgs_focal_stack_loss", "hcgs_adam_step", "hcgs_mlp_forward", "hcgs_mlp_backward",
-           "hcgs_profile_enable", "hcgs_profile_summary")
+           "hcgs_profile_enable", "hcgs_profile_summary", "hcgs_asm_propagate_noalloc")
 
 
 class HcgsError(RuntimeError):
@@ -101,6 +101,7 @@ _sig("hcgs_render_view_backward", [_P, _P, POINTER(_Gaussians), _P, POINTER(_Gra
 _sig("hcgs_focal_stack_loss", [_P, _P, _P, c_int, POINTER(_Optics), _P, _P, _P, _P])
 _sig("hcgs_adam_step", [_P, _P, _P, _P, _P, c_int64, c_int, c_float, c_float, c_float, c_float, _P])
 _sig("hcgs_mlp_forward", [_P, _P, c_int] + [_P] * 8 + [_P, _P])
+_sig("hcgs_asm_propagate_noalloc", [_P, c_int, POINTER(_Optics), _P, _P])
 _sig("hcgs_mlp_backward", [_P, _P, c_int] + [_P] * 8 + [_P] + [_P] * 8 + [_P])
 
 PARAM_NAMES = ("means", "log_scales", "quats", "opacity_logits", "amplitude", "phase", "plane_logits")
@@ -275,6 +276,15 @@ class Context:
         self._check(_lib.hcgs_mlp_backward(self.handle, _ptr(x), x.shape[0], *[_ptr(w) for w in W],
                                            *[_ptr(t) for t in b], _ptr(gy), *[_ptr(t) for t in gW],
                                            *[_ptr(t) for t in gb], _stream()))
+
+
+def asm_propagate_noalloc(inp, B, optics, out):
+    """hcgs_asm_propagate_noalloc: inverse propagation without any device
+    allocation (see include/hcgs.h for its size limit and sharing rules)."""
+    rc = _lib.hcgs_asm_propagate_noalloc(_ptr(inp), int(B), ctypes.byref(make_optics(optics)), _ptr(out),
+                                         _stream())
+    if rc != 0:
+        raise HcgsError("hcgs_asm_propagate_noalloc: %s" % STATUS.get(rc, rc))
 
 
 _default_ctx = None

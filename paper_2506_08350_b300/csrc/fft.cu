@@ -18,9 +18,11 @@
 // The transfer-function phase 2 pi z sqrt(1/lambda^2 - f^2) is formed in FP64
 // and reduced mod 2 pi before it is rounded to an FP32 complex factor; the
 // table holds one quadrant because H depends on f_x^2 and f_y^2 only.
+#include <algorithm>
 #include <cmath>
 
 #include "common.cuh"
+#include "fft.cuh"
 
 namespace hcgs {
 
@@ -334,11 +336,6 @@ __global__ void k_rows_spread(const float2* __restrict__ in, float2* __restrict_
 // ---------------------------------------------------------------------------
 // transfer-function table, FP64
 // ---------------------------------------------------------------------------
-struct HArgs {
-    double lam[MAX_C];
-    double z[MAX_L];
-};
-
 __global__ void k_build_hq(float2* __restrict__ hq, int H, int W, int C, int L, double px, double py, HArgs a) {
     const int hh = H / 2 + 1, wh = W / 2 + 1;
     const size_t total = (size_t)C * L * hh * wh;
@@ -374,15 +371,17 @@ bool fft_supported(int n) {
     return m == 1;
 }
 
-static void factor(int n, FftPlan& p) {
+void factor_radices(int n, int* radix, int* nst) {
     int m = n;
-    p.nst = 0;
-    while (m % 8 == 0) { p.radix[p.nst++] = 8; m /= 8; }
-    if (m % 4 == 0) { p.radix[p.nst++] = 4; m /= 4; }
-    if (m % 2 == 0) { p.radix[p.nst++] = 2; m /= 2; }
-    while (m % 5 == 0) { p.radix[p.nst++] = 5; m /= 5; }
-    while (m % 3 == 0) { p.radix[p.nst++] = 3; m /= 3; }
+    *nst = 0;
+    while (m % 8 == 0) { radix[(*nst)++] = 8; m /= 8; }
+    if (m % 4 == 0) { radix[(*nst)++] = 4; m /= 4; }
+    if (m % 2 == 0) { radix[(*nst)++] = 2; m /= 2; }
+    while (m % 5 == 0) { radix[(*nst)++] = 5; m /= 5; }
+    while (m % 3 == 0) { radix[(*nst)++] = 3; m /= 3; }
 }
+
+static void factor(int n, FftPlan& p) { factor_radices(n, p.radix, &p.nst); }
 
 static FftPlanArg plan_arg(const FftPlan* p) {
     FftPlanArg a;
@@ -561,6 +560,43 @@ hcgs_status asm_spread(hcgs_ctx* ctx, const float2* in, float2* out, int B, cons
     if ((s = fft_cols(ctx, in, S, B * o->C, o->H, o->W, false, 1.f, st))) return s;
     if ((s = rows_spread(ctx, S, out, B, o->L, o->C, o->H, o->W, hq, conjH, st))) return s;
     return fft_cols(ctx, out, out, B * o->L * o->C, o->H, o->W, true, 1.f / (float)planeN, st);
+}
+
+// ---------------------------------------------------------------------------
+// raw launchers (explicit plans and tables, no context)
+// ---------------------------------------------------------------------------
+cudaError_t launch_fft_cols_raw(bool inverse, const float2* in, float2* out, int nplanes, int H, int W,
+                                const FftPlanArg& plan, const float2* tw, float scale, cudaStream_t st) {
+    const int cw = col_width(H);
+    const size_t smem = (size_t)(2 * cw + 1) * H * sizeof(float2);
+    const dim3 grid((W + cw - 1) / cw, nplanes);
+    cudaError_t e;
+    if (inverse) {
+        if ((e = allow_smem(k_fft_cols<true>, smem)) != cudaSuccess) return e;
+        k_fft_cols<true><<<grid, 512, smem, st>>>(in, out, H, W, cw, plan, tw, scale);
+    } else {
+        if ((e = allow_smem(k_fft_cols<false>, smem)) != cudaSuccess) return e;
+        k_fft_cols<false><<<grid, 512, smem, st>>>(in, out, H, W, cw, plan, tw, scale);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rows_spread_conj_raw(const float2* in, float2* out, int B, int L, int C, int H, int W,
+                                        const float2* hq, const FftPlanArg& plan, const float2* tw,
+                                        cudaStream_t st) {
+    const size_t smem = 4 * (size_t)W * sizeof(float2);
+    cudaError_t e = allow_smem(k_rows_spread<true>, smem);
+    if (e != cudaSuccess) return e;
+    k_rows_spread<true><<<dim3(B, H, C), row_threads(W), smem, st>>>(in, out, L, C, H, W, hq, plan, tw);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_hq_raw(float2* hq, int H, int W, int C, int L, double px, double py, const HArgs& a,
+                                cudaStream_t st) {
+    const size_t n = (size_t)C * L * (H / 2 + 1) * (W / 2 + 1);
+    const int blocks = (int)std::min<size_t>(1184, (n + 255) / 256);
+    k_build_hq<<<blocks, 256, 0, st>>>(hq, H, W, C, L, px, py, a);
+    return cudaGetLastError();
 }
 
 }  // namespace hcgs

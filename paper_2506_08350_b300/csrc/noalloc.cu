@@ -1,0 +1,115 @@
+// Allocation-free inverse propagation: hcgs_asm_propagate_noalloc.
+//
+// Same computation as the inverse-propagation form of hcgs_asm_propagate
+// (sign = -1, reduce_planes = 0): out_l = IDFT(conj(H_{Z_l}) DFT(in)), with the
+// same kernels (k_fft_cols, k_rows_spread, k_build_hq).  The difference is
+// where the working memory comes from: the column spectrum of `in`, the
+// transfer-function table and the two twiddle tables live in one file-scope
+// device array of fixed size instead of buffers the library allocates.  It is
+// for callers that cannot call cudaMalloc: for example a host application
+// whose device memory is entirely managed by its own pool allocator (a
+// cudaMalloc from inside a library would fail or fragment that pool), or a
+// display loop that allocates everything at start-up and must not stall on
+// cudaMalloc/cudaFree, which synchronise the device, in the middle of a frame.
+//
+// The array occupies NOALLOC_SCRATCH_COMPLEX complex64 values (32 MiB) on
+// every GPU that loads this library, until the process exits.  Every call
+// shares it and it keeps the last call's contents; each call rewrites all the
+// parts it reads before reading them, so nothing needs to start at zero.
+// Calls whose kernels overlap on the GPU (two streams, two threads) race on
+// the array and must be serialised by the caller.
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+#include "fft.cuh"
+
+namespace hcgs {
+namespace {
+
+constexpr size_t NOALLOC_SCRATCH_COMPLEX = size_t(4) << 20;  // 4 Mi complex64 = 32 MiB
+static __device__ __align__(256) float2 g_noalloc_scratch[NOALLOC_SCRATCH_COMPLEX];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+float2* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {nullptr};
+
+// exp(-2 pi i m / n), formed in FP64 and rounded to FP32
+__global__ void k_noalloc_twiddles(float2* __restrict__ tw, int n) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n) return;
+    double s, c;
+    sincospi(-2.0 * (double)m / (double)n, &s, &c);
+    tw[m] = make_float2((float)c, (float)s);
+}
+
+// complex elements rounded up to a 512-byte boundary
+size_t round64(size_t n) { return (n + 63) & ~size_t(63); }
+
+bool optics_ok(const hcgs_optics* o) {
+    if (!o || o->H < 1 || o->W < 1 || o->C < 1 || o->C > MAX_C || o->L < 1 || o->L > MAX_L) return false;
+    if (!(o->pitch_x > 0) || !(o->pitch_y > 0) || !o->wavelength || !o->plane_z || o->band_limit != 0) return false;
+    for (int c = 0; c < o->C; c++)
+        if (!(o->wavelength[c] > 0)) return false;
+    return true;
+}
+
+FftPlanArg plan_for(int n) {
+    FftPlanArg p;
+    p.n = n;
+    for (int s = 0; s < MAX_STAGES; s++) p.radix[s] = 0;
+    factor_radices(n, p.radix, &p.nst);
+    return p;
+}
+
+}  // namespace
+}  // namespace hcgs
+
+using namespace hcgs;
+
+extern "C" hcgs_status hcgs_asm_propagate_noalloc(const float* in, int B, const hcgs_optics* o, float* out,
+                                                  void* stream) {
+    if (!in || !out || in == out || B < 1 || !optics_ok(o)) return HCGS_ERR_INVALID_ARG;
+    if (!fft_supported(o->H) || !fft_supported(o->W)) return HCGS_ERR_UNSUPPORTED_SIZE;
+    const int H = o->H, W = o->W, C = o->C, L = o->L;
+    const size_t nS = (size_t)B * C * H * W;
+    const size_t nH = (size_t)C * L * (H / 2 + 1) * (W / 2 + 1);
+    const size_t need = round64(nS) + round64(nH) + round64(H) + round64(W);
+    if (need > NOALLOC_SCRATCH_COMPLEX) return HCGS_ERR_CAPACITY;
+
+    // set-up, once per device, with that device current: the device address
+    // of the static array (its host-side name is only a stand-in)
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) return HCGS_ERR_CUDA;
+    float2* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            void* p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return HCGS_ERR_CUDA;
+            g_noalloc_addr[dev] = (float2*)p;
+        }
+        base = g_noalloc_addr[dev];
+    }
+    float2* S1 = base;
+    float2* hq = S1 + round64(nS);
+    float2* twH = hq + round64(nH);
+    float2* twW = twH + round64(H);
+    cudaStream_t st = (cudaStream_t)stream;
+
+    k_noalloc_twiddles<<<(H + 255) / 256, 256, 0, st>>>(twH, H);
+    k_noalloc_twiddles<<<(W + 255) / 256, 256, 0, st>>>(twW, W);
+    if (cudaGetLastError() != cudaSuccess) return HCGS_ERR_CUDA;
+    HArgs a{};
+    for (int c = 0; c < C; c++) a.lam[c] = o->wavelength[c];
+    for (int l = 0; l < L; l++) a.z[l] = o->plane_z[l];
+    const FftPlanArg pH = plan_for(H), pW = plan_for(W);
+    if (launch_build_hq_raw(hq, H, W, C, L, o->pitch_x, o->pitch_y, a, st) != cudaSuccess ||
+        launch_fft_cols_raw(false, (const float2*)in, S1, B * C, H, W, pH, twH, 1.f, st) != cudaSuccess ||
+        launch_rows_spread_conj_raw(S1, (float2*)out, B, L, C, H, W, hq, pW, twW, st) != cudaSuccess ||
+        launch_fft_cols_raw(true, (const float2*)out, (float2*)out, B * L * C, H, W, pH, twH,
+                            1.f / (float)((size_t)H * W), st) != cudaSuccess)
+        return HCGS_ERR_CUDA;
+    return HCGS_OK;
+}
