@@ -182,6 +182,161 @@ __device__ float2* run_fft(float2* a, float2* b, const FftPlanArg& p, int ntrans
 __device__ __forceinline__ int mirror(int k, int n) { return k <= n / 2 ? k : n - k; }
 
 // ---------------------------------------------------------------------------
+// Compile-time plans for the lengths of the paper-shaped workloads (1080,
+// 1920, 256, 512): constant divisors, unrolled radix sequence, and a padded
+// shared-memory layout (one extra slot every 32 complex values) that spreads
+// the strided Stockham stores over the banks.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int pad32(int e) { return e + (e >> 5); }
+__host__ __device__ constexpr int padded_len(int e) { return e + e / 32 + 1; }
+
+template <int N, int NS, int R, bool INV, int NTRANS, int ES, int TS>
+__device__ __forceinline__ void stage_ct(const float2* __restrict__ src, float2* __restrict__ dst,
+                                         const float2* __restrict__ tw) {
+    constexpr int M = N / R, TOTAL = M * NTRANS, TWSTEP = N / (NS * R);
+    for (int w = threadIdx.x; w < TOTAL; w += blockDim.x) {
+        const int t = w % NTRANS, j = w / NTRANS, k = j % NS;
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; r++) v[r] = src[pad32(t * TS + (j + r * M) * ES)];
+        if (NS > 1) {
+#pragma unroll
+            for (int r = 1; r < R; r++) {
+                float2 w_ = tw[r * k * TWSTEP];
+                if (INV) w_.y = -w_.y;
+                v[r] = cmul(v[r], w_);
+            }
+        }
+        dft<R, INV>(v);
+        const int idxD = (j / NS) * NS * R + k;
+#pragma unroll
+        for (int r = 0; r < R; r++) dst[pad32(t * TS + (idxD + r * NS) * ES)] = v[r];
+    }
+}
+
+template <bool INV, int N, int NTRANS, int ES, int TS, int NS, int R, int... RS>
+struct CtStages {
+    static __device__ __forceinline__ float2* run(float2* a, float2* b, const float2* tw) {
+        stage_ct<N, NS, R, INV, NTRANS, ES, TS>(a, b, tw);
+        __syncthreads();
+        if constexpr (sizeof...(RS) == 0) {
+            return b;
+        } else {
+            return CtStages<INV, N, NTRANS, ES, TS, NS * R, RS...>::run(b, a, tw);
+        }
+    }
+};
+
+template <int N, int... RS>
+struct CtPlan {
+    static constexpr int n = N;
+    template <bool INV, int NTRANS, int ES, int TS>
+    static __device__ __forceinline__ float2* run(float2* a, float2* b, const float2* tw) {
+        return CtStages<INV, N, NTRANS, ES, TS, 1, RS...>::run(a, b, tw);
+    }
+};
+using Plan1080 = CtPlan<1080, 8, 5, 3, 3, 3>;
+using Plan1920 = CtPlan<1920, 8, 8, 2, 5, 3>;
+using Plan512 = CtPlan<512, 8, 8, 8>;
+using Plan256 = CtPlan<256, 8, 8, 4>;
+
+// columns: grid (ceil(W/CW), nplanes), CW adjacent columns per CTA
+template <bool INV, class PL, int CW>
+__global__ void __launch_bounds__(256) k_fft_cols_ct(const float2* __restrict__ in, float2* __restrict__ out, int W,
+                                                     const float2* __restrict__ tw_g, float scale) {
+    constexpr int N = PL::n, E = N * CW, EP = padded_len(E);
+    extern __shared__ float2 sm[];
+    float2* A = sm;
+    float2* Bb = sm + EP;
+    float2* tw = sm + 2 * EP;
+    const int col0 = blockIdx.x * CW;
+    const size_t base = (size_t)blockIdx.y * N * W;
+    for (int e = threadIdx.x; e < N; e += blockDim.x) tw[e] = tw_g[e];
+    for (int e = threadIdx.x; e < E; e += blockDim.x) {
+        const int i = e / CW, cc = e % CW, col = col0 + cc;
+        A[pad32(e)] = col < W ? in[base + (size_t)i * W + col] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const float2* res = PL::template run<INV, CW, CW, 1>(A, Bb, tw);
+    for (int e = threadIdx.x; e < E; e += blockDim.x) {
+        const int i = e / CW, cc = e % CW, col = col0 + cc;
+        if (col < W) out[base + (size_t)i * W + col] = cscale(res[pad32(e)], scale);
+    }
+}
+
+template <bool CONJ, class PL>
+__global__ void __launch_bounds__(512) k_rows_sum_ct(const float2* __restrict__ in, float2* __restrict__ out, int L,
+                                                     int C, int H, const float2* __restrict__ hq,
+                                                     const float2* __restrict__ tw_g) {
+    constexpr int W = PL::n, EP = padded_len(W);
+    extern __shared__ float2 sm[];
+    float2* A = sm;
+    float2* Bb = sm + EP;
+    float2* acc = sm + 2 * EP;
+    float2* tw = sm + 3 * EP;
+    const int b = blockIdx.x, i = blockIdx.y, c = blockIdx.z;
+    const int ky = mirror(i, H);
+    constexpr int hw2 = W / 2 + 1;
+    for (int j = threadIdx.x; j < W; j += blockDim.x) {
+        tw[j] = tw_g[j];
+        acc[pad32(j)] = make_float2(0.f, 0.f);
+    }
+    for (int l = 0; l < L; l++) {
+        const float2* src = in + ((((size_t)b * L + l) * C + c) * H + i) * W;
+        for (int j = threadIdx.x; j < W; j += blockDim.x) A[pad32(j)] = src[j];
+        __syncthreads();
+        const float2* res = PL::template run<false, 1, 1, 0>(A, Bb, tw);
+        const float2* hrow = hq + (((size_t)c * L + l) * (H / 2 + 1) + ky) * hw2;
+        for (int j = threadIdx.x; j < W; j += blockDim.x) {
+            float2 h = hrow[mirror(j, W)];
+            if (CONJ) h.y = -h.y;
+            acc[pad32(j)] = cadd(acc[pad32(j)], cmul(res[pad32(j)], h));
+        }
+        __syncthreads();
+    }
+    const float2* res = PL::template run<true, 1, 1, 0>(acc, A, tw);
+    float2* dst = out + (((size_t)b * C + c) * H + i) * W;
+    for (int j = threadIdx.x; j < W; j += blockDim.x) dst[j] = res[pad32(j)];
+}
+
+template <bool CONJ, class PL>
+__global__ void __launch_bounds__(512) k_rows_spread_ct(const float2* __restrict__ in, float2* __restrict__ out,
+                                                        int L, int C, int H, const float2* __restrict__ hq,
+                                                        const float2* __restrict__ tw_g) {
+    constexpr int W = PL::n, EP = padded_len(W);
+    extern __shared__ float2 sm[];
+    float2* A = sm;
+    float2* Bb = sm + EP;
+    float2* S = sm + 2 * EP;
+    float2* tw = sm + 3 * EP;
+    const int b = blockIdx.x, i = blockIdx.y, c = blockIdx.z;
+    const int ky = mirror(i, H);
+    constexpr int hw2 = W / 2 + 1;
+    const float2* src = in + (((size_t)b * C + c) * H + i) * W;
+    for (int j = threadIdx.x; j < W; j += blockDim.x) {
+        tw[j] = tw_g[j];
+        A[pad32(j)] = src[j];
+    }
+    __syncthreads();
+    const float2* spec = PL::template run<false, 1, 1, 0>(A, Bb, tw);
+    for (int j = threadIdx.x; j < W; j += blockDim.x) S[j] = spec[pad32(j)];
+    __syncthreads();
+    for (int l = 0; l < L; l++) {
+        const float2* hrow = hq + (((size_t)c * L + l) * (H / 2 + 1) + ky) * hw2;
+        for (int j = threadIdx.x; j < W; j += blockDim.x) {
+            float2 h = hrow[mirror(j, W)];
+            if (CONJ) h.y = -h.y;
+            A[pad32(j)] = cmul(S[j], h);
+        }
+        __syncthreads();
+        const float2* res = PL::template run<true, 1, 1, 0>(A, Bb, tw);
+        float2* dst = out + ((((size_t)b * L + l) * C + c) * H + i) * W;
+        for (int j = threadIdx.x; j < W; j += blockDim.x) dst[j] = res[pad32(j)];
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // column transforms: grid (ceil(W/CW), nplanes); each CTA transforms CW
 // adjacent columns of one plane, staged as smem[row][CW].
 // ---------------------------------------------------------------------------
@@ -453,12 +608,32 @@ static cudaError_t allow_smem(K kern, size_t bytes) {
     return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+template <class PL, int CW>
+static hcgs_status fft_cols_ct(hcgs_ctx* ctx, const float2* in, float2* out, int nplanes, int W, bool inverse,
+                               float scale, const float2* tw, cudaStream_t st) {
+    constexpr int N = PL::n;
+    const size_t smem = (2 * (size_t)padded_len(N * CW) + N) * sizeof(float2);
+    dim3 grid((W + CW - 1) / CW, nplanes);
+    if (inverse) {
+        HCGS_CUDA(ctx, allow_smem(k_fft_cols_ct<true, PL, CW>, smem));
+        HCGS_KERNEL(ctx, "k_fft_cols", st, k_fft_cols_ct<true, PL, CW><<<grid, 256, smem, st>>>(in, out, W, tw, scale));
+    } else {
+        HCGS_CUDA(ctx, allow_smem(k_fft_cols_ct<false, PL, CW>, smem));
+        HCGS_KERNEL(ctx, "k_fft_cols", st, k_fft_cols_ct<false, PL, CW><<<grid, 256, smem, st>>>(in, out, W, tw, scale));
+    }
+    return HCGS_OK;
+}
+
 hcgs_status fft_cols(hcgs_ctx* ctx, const float2* in, float2* out, int nplanes, int H, int W, bool inverse,
                      float scale, cudaStream_t st) {
     if (nplanes <= 0) return HCGS_OK;
     FftPlan* p;
     hcgs_status s = get_plan(ctx, H, &p);
     if (s) return s;
+    if (H == 1080) return fft_cols_ct<Plan1080, 4>(ctx, in, out, nplanes, W, inverse, scale, p->tw, st);
+    if (H == 1920) return fft_cols_ct<Plan1920, 4>(ctx, in, out, nplanes, W, inverse, scale, p->tw, st);
+    if (H == 512) return fft_cols_ct<Plan512, 8>(ctx, in, out, nplanes, W, inverse, scale, p->tw, st);
+    if (H == 256) return fft_cols_ct<Plan256, 8>(ctx, in, out, nplanes, W, inverse, scale, p->tw, st);
     const int cw = col_width(H);
     const size_t smem = (size_t)(2 * cw + 1) * H * sizeof(float2);
     dim3 grid((W + cw - 1) / cw, nplanes);
@@ -496,11 +671,49 @@ static int row_threads(int W) {
     return t < 32 ? 32 : (t > 512 ? 512 : t);
 }
 
+template <class PL>
+static hcgs_status rows_ct(hcgs_ctx* ctx, bool sum, const float2* in, float2* out, int B, int L, int C, int H,
+                           const float2* hq, bool conjH, const float2* tw, cudaStream_t st) {
+    constexpr int W = PL::n;
+    const size_t smem = (3 * (size_t)padded_len(W) + W) * sizeof(float2);
+    const int thr = row_threads(W);
+    dim3 grid(B, H, C);
+    if (sum) {
+        if (conjH) {
+            HCGS_CUDA(ctx, allow_smem(k_rows_sum_ct<true, PL>, smem));
+            HCGS_KERNEL(ctx, "k_rows_sum", st, k_rows_sum_ct<true, PL><<<grid, thr, smem, st>>>(in, out, L, C, H, hq, tw));
+        } else {
+            HCGS_CUDA(ctx, allow_smem(k_rows_sum_ct<false, PL>, smem));
+            HCGS_KERNEL(ctx, "k_rows_sum", st, k_rows_sum_ct<false, PL><<<grid, thr, smem, st>>>(in, out, L, C, H, hq, tw));
+        }
+    } else {
+        if (conjH) {
+            HCGS_CUDA(ctx, allow_smem(k_rows_spread_ct<true, PL>, smem));
+            HCGS_KERNEL(ctx, "k_rows_spread", st, k_rows_spread_ct<true, PL><<<grid, thr, smem, st>>>(in, out, L, C, H, hq, tw));
+        } else {
+            HCGS_CUDA(ctx, allow_smem(k_rows_spread_ct<false, PL>, smem));
+            HCGS_KERNEL(ctx, "k_rows_spread", st, k_rows_spread_ct<false, PL><<<grid, thr, smem, st>>>(in, out, L, C, H, hq, tw));
+        }
+    }
+    return HCGS_OK;
+}
+
+static bool rows_ct_dispatch(hcgs_ctx* ctx, bool sum, const float2* in, float2* out, int B, int L, int C, int H,
+                             int W, const float2* hq, bool conjH, const float2* tw, cudaStream_t st,
+                             hcgs_status* res) {
+    if (W == 1920) { *res = rows_ct<Plan1920>(ctx, sum, in, out, B, L, C, H, hq, conjH, tw, st); return true; }
+    if (W == 1080) { *res = rows_ct<Plan1080>(ctx, sum, in, out, B, L, C, H, hq, conjH, tw, st); return true; }
+    if (W == 512) { *res = rows_ct<Plan512>(ctx, sum, in, out, B, L, C, H, hq, conjH, tw, st); return true; }
+    if (W == 256) { *res = rows_ct<Plan256>(ctx, sum, in, out, B, L, C, H, hq, conjH, tw, st); return true; }
+    return false;
+}
+
 hcgs_status rows_sum(hcgs_ctx* ctx, const float2* in, float2* out, int B, int L, int C, int H, int W,
                      const float2* hq, bool conjH, cudaStream_t st) {
     FftPlan* p;
     hcgs_status s = get_plan(ctx, W, &p);
     if (s) return s;
+    if (rows_ct_dispatch(ctx, true, in, out, B, L, C, H, W, hq, conjH, p->tw, st, &s)) return s;
     const size_t smem = 4 * (size_t)W * sizeof(float2);
     dim3 grid(B, H, C);
     if (conjH) {
@@ -519,6 +732,7 @@ hcgs_status rows_spread(hcgs_ctx* ctx, const float2* in, float2* out, int B, int
     FftPlan* p;
     hcgs_status s = get_plan(ctx, W, &p);
     if (s) return s;
+    if (rows_ct_dispatch(ctx, false, in, out, B, L, C, H, W, hq, conjH, p->tw, st, &s)) return s;
     const size_t smem = 4 * (size_t)W * sizeof(float2);
     dim3 grid(B, H, C);
     if (conjH) {

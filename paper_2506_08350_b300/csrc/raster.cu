@@ -2,13 +2,18 @@
 // (Sec. 4.1 per-plane field equation; Algorithm 2) and its adjoint (Supp. D.4;
 // Sec. 4.2: back-to-front walk, transmittance recovered by division).
 //
-// One CTA of 256 threads per (16x16 tile, plane, view); one pixel per
-// thread.  The CTA streams its 64x64 bucket's list (already in visiting
-// order), keeps the entries whose tile rectangle covers the tile (warp ballot
-// compaction keeps the order), stages their records in shared memory, and
-// every pixel walks them: alpha = min(alpha_max, o exp(-power)); skip when
-// alpha < alpha_min; U += w alpha T; T *= 1 - alpha; stop once T < T_eps.
-// The CTA leaves the list when all 256 pixels have stopped.
+// One CTA of 128 threads per (16x16 tile, plane, view); two pixels per
+// thread (rows r and r + 2 of the warp's 16 x 4 strip).  The CTA streams its
+// 64x64 bucket's list (already in visiting order), keeps the entries whose
+// tile rectangle covers the tile (warp ballot compaction keeps the order) and
+// stages their records in shared memory.  Each warp tests 32 staged entries
+// at a time against its strip (exact superset test), and for every hit both
+// pixels of every lane take the step of Algorithm 2: alpha = min(alpha_max,
+// o exp(-power)); skip when alpha < alpha_min; U += w alpha T; T *= 1 - alpha;
+// stop once T < T_eps.  The record load, the loop control and (in the
+// adjoint) the per-entry warp reduction are shared by the two pixels; the
+// second pixel's exponent is the first one's plus 2 (B dx + C dy + C).
+// The CTA leaves the list when all its pixels have stopped.
 //
 // The alpha arithmetic uses explicitly rounded intrinsics so that the forward
 // and backward kernels take identical skip/stop decisions.
@@ -58,6 +63,9 @@ struct RecW {
     }
 };
 
+constexpr int RT = 128;            // threads per CTA
+constexpr int RWARPS = RT / 32;
+
 // Stream one batch (positions [lo, hi) of the bucket) and compact the entries
 // that touch tile (tx, ty) into shared memory, keeping their order.
 template <int NR>
@@ -79,7 +87,7 @@ __device__ __forceinline__ int stage_batch(const RasterArgs& a, size_t vN, uint3
     __syncthreads();
     int base = 0, total = 0;
 #pragma unroll
-    for (int w = 0; w < 8; w++) {
+    for (int w = 0; w < RWARPS; w++) {
         const int c = wcnt[w];
         base += w < warp ? c : 0;
         total += c;
@@ -97,7 +105,7 @@ __device__ __forceinline__ int stage_batch(const RasterArgs& a, size_t vN, uint3
 }
 
 // Can Gaussian (mu, conic A B C, opacity o) reach alpha >= alpha_min at any
-// pixel centre of the strip x in [x0, x0 + 15], y in {y0, y0 + 1}?  For each
+// pixel centre of the strip x in [x0, x0 + 15], y in [y0, y0 + 3]?  For each
 // row the footprint quadratic q = A dx^2 + 2 B dx dy + C dy^2 is minimised
 // over the row segment (a convex 1D problem: the unconstrained minimiser
 // clamped to the segment) and compared with 2 ln(o / alpha_min), with a
@@ -108,16 +116,27 @@ __device__ __forceinline__ bool strip_hits(float4 r0, float Cc, float o, float x
     if (o < amin) return false;
     const float k2 = 2.f * __logf(o / amin) * 1.001f + 1e-3f;
     const float x1 = x0 + 15.f;
+    const float slope = r0.w / r0.z;
     bool hit = false;
 #pragma unroll
-    for (int r = 0; r < 2; r++) {
+    for (int r = 0; r < 4; r++) {
         const float dy = (y0 + (float)r) - r0.y;
-        const float xs = fminf(fmaxf(r0.x - r0.w * dy / r0.z, x0), x1);
+        const float xs = fminf(fmaxf(r0.x - slope * dy, x0), x1);
         const float dx = xs - r0.x;
         const float q = r0.z * dx * dx + 2.f * r0.w * dx * dy + Cc * dy * dy;
         hit |= q <= k2;
     }
     return hit;
+}
+
+// Footprint exponents of the thread's two pixels (rows y and y + 2):
+// power_a = 1/2 (A dx^2 + C dy^2) + B dx dy (Supp. D.3), power_b = power_a +
+// 2 (B dx + C dy + C).  Shared by forward and adjoint, so both take the same
+// decisions.
+__device__ __forceinline__ void footprint_pair(float px, float py, float4 r0, float Cc, float* pa, float* pb,
+                                               float* dx, float* dy) {
+    *pa = footprint_power(px, py, r0, Cc, dx, dy);
+    *pb = __fmaf_rn(2.f, __fmaf_rn(r0.w, *dx, __fmaf_rn(Cc, *dy, Cc)), *pa);
 }
 
 // Warp reduce-scatter of 16 values: afterwards lanes 2i and 2i+1 both hold the
@@ -136,38 +155,58 @@ __device__ __forceinline__ float warp_reduce_scatter16(float (&v)[16], int lane)
     return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
+// Forward step of one pixel for one entry (Algorithm 2).
 template <int C>
-__global__ void __launch_bounds__(256) k_raster_fwd(RasterArgs a, float2* __restrict__ U, float* __restrict__ Tsave,
-                                                    uint32_t* __restrict__ lastsave, float* __restrict__ Tout,
-                                                    int32_t* __restrict__ ncout) {
+__device__ __forceinline__ void composite_step(float power, float o, const float4* rec, float amin, float amax,
+                                               float teps, uint32_t pos, float& T, float2 (&acc)[C], bool& done,
+                                               uint32_t& lastp, int& nc) {
+    const float alpha = fminf(amax, __fmul_rn(o, __expf(-power)));
+    if (alpha < amin) return;
+    const float wt = __fmul_rn(alpha, T);
+#pragma unroll
+    for (int c = 0; c < C; c++) {
+        const float2 w = RecW<C>::get(rec, c);
+        acc[c].x = __fmaf_rn(w.x, wt, acc[c].x);
+        acc[c].y = __fmaf_rn(w.y, wt, acc[c].y);
+    }
+    T = __fmul_rn(T, __fsub_rn(1.f, alpha));
+    nc++;
+    lastp = pos + 1;
+    if (T < teps) done = true;
+}
+
+template <int C>
+__global__ void __launch_bounds__(RT) k_raster_fwd(RasterArgs a, float2* __restrict__ U, float* __restrict__ Tsave,
+                                                   uint32_t* __restrict__ lastsave, float* __restrict__ Tout,
+                                                   int32_t* __restrict__ ncout) {
     constexpr int NR = C <= 1 ? 2 : (C <= 3 ? 3 : 4);
-    __shared__ float4 srec[256][NR];
-    __shared__ uint32_t spos[256], sid[256];
-    __shared__ int wcnt[8];
-    const int t = threadIdx.x, lane = t & 31;
+    __shared__ float4 srec[RT][NR];
+    __shared__ uint32_t spos[RT], sid[RT];
+    __shared__ int wcnt[RWARPS];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int tile = blockIdx.x, l = blockIdx.y, v = blockIdx.z;
     const int tx = tile % a.tilesX, ty = tile / a.tilesX;
-    const int px = tx * TILE + (t & 15), py = ty * TILE + (t >> 4);
-    const bool inside = px < a.W && py < a.H;
-    const float sx0 = (float)(tx * TILE), sy0 = (float)(ty * TILE + 2 * (t >> 5));  // this warp's strip
+    const int px = tx * TILE + (lane & 15);
+    const int py0 = ty * TILE + 4 * warp + (lane >> 4), py1 = py0 + 2;
+    const bool in0 = px < a.W && py0 < a.H, in1 = px < a.W && py1 < a.H;
+    const float sx0 = (float)(tx * TILE), sy0 = (float)(ty * TILE + 4 * warp);  // this warp's strip
     const uint32_t gb = ((uint32_t)(v * a.L + l) * a.ctY + ty / COARSE) * a.ctX + tx / COARSE;
     const uint32_t beg = a.off[gb], n = a.off[gb + 1] - beg;
     const size_t vN = (size_t)v * a.N;
-    const float fpx = (float)px, fpy = (float)py;
-    float T = 1.f;
-    float2 acc[C];
+    const float fpx = (float)px, fpy = (float)py0;
+    float T0 = 1.f, T1 = 1.f;
+    float2 acc0[C], acc1[C];
 #pragma unroll
-    for (int c = 0; c < C; c++) acc[c] = make_float2(0.f, 0.f);
-    bool done = !inside;
-    uint32_t lastp = 0;
-    int nc = 0;
-    for (uint32_t lo = 0; lo < n; lo += 256) {
-        if (__syncthreads_count(!done) == 0) break;
-        const uint32_t hi = min(n, lo + 256u);
+    for (int c = 0; c < C; c++) acc0[c] = acc1[c] = make_float2(0.f, 0.f);
+    bool d0 = !in0, d1 = !in1;
+    uint32_t last0 = 0, last1 = 0;
+    int nc0 = 0, nc1 = 0;
+    for (uint32_t lo = 0; lo < n; lo += RT) {
+        if (__syncthreads_count(!(d0 && d1)) == 0) break;
+        const uint32_t hi = min(n, lo + (uint32_t)RT);
         const int total = stage_batch<NR>(a, vN, beg, lo, hi, tx, ty, srec, spos, sid, wcnt);
         for (int k0 = 0; k0 < total; k0 += 32) {
-            if (__all_sync(0xffffffffu, done)) break;
-            // the warp tests 32 staged entries at once against its 16 x 2 strip
+            if (__all_sync(0xffffffffu, d0 && d1)) break;
             bool hit = false;
             if (k0 + lane < total) {
                 const float4 q0 = srec[k0 + lane][0], q1 = srec[k0 + lane][1];
@@ -177,83 +216,129 @@ __global__ void __launch_bounds__(256) k_raster_fwd(RasterArgs a, float2* __rest
             while (m) {
                 const int k = k0 + __ffs(m) - 1;
                 m &= m - 1;
-                if (done) continue;
+                if (d0 && d1) continue;
                 const float4 r0 = srec[k][0], r1 = srec[k][1];
-                float dx, dy;
-                const float power = footprint_power(fpx, fpy, r0, r1.x, &dx, &dy);
-                const float alpha = fminf(a.amax, __fmul_rn(r1.y, __expf(-power)));
-                if (alpha < a.amin) continue;
-                const float wt = __fmul_rn(alpha, T);
-#pragma unroll
-                for (int c = 0; c < C; c++) {
-                    const float2 w = RecW<C>::get(srec[k], c);
-                    acc[c].x = __fmaf_rn(w.x, wt, acc[c].x);
-                    acc[c].y = __fmaf_rn(w.y, wt, acc[c].y);
-                }
-                T = __fmul_rn(T, __fsub_rn(1.f, alpha));
-                nc++;
-                lastp = spos[k] + 1;
-                if (T < a.teps) done = true;
+                float pa, pb, dx, dy;
+                footprint_pair(fpx, fpy, r0, r1.x, &pa, &pb, &dx, &dy);
+                const uint32_t pos = spos[k];
+                if (!d0) composite_step<C>(pa, r1.y, srec[k], a.amin, a.amax, a.teps, pos, T0, acc0, d0, last0, nc0);
+                if (!d1) composite_step<C>(pb, r1.y, srec[k], a.amin, a.amax, a.teps, pos, T1, acc1, d1, last1, nc1);
             }
         }
     }
-    if (inside) {
-        const size_t pix = (size_t)py * a.W + px;
-        const size_t plane = (size_t)v * a.L + l;
-        const size_t HW = (size_t)a.H * a.W;
+    const size_t plane = (size_t)v * a.L + l;
+    const size_t HW = (size_t)a.H * a.W;
+    if (in0) {
+        const size_t pix = (size_t)py0 * a.W + px;
 #pragma unroll
-        for (int c = 0; c < C; c++) U[(plane * C + c) * HW + pix] = acc[c];
-        Tsave[plane * HW + pix] = T;
-        lastsave[plane * HW + pix] = lastp;
-        if (Tout) Tout[plane * HW + pix] = T;
-        if (ncout) ncout[plane * HW + pix] = nc;
+        for (int c = 0; c < C; c++) U[(plane * C + c) * HW + pix] = acc0[c];
+        Tsave[plane * HW + pix] = T0;
+        lastsave[plane * HW + pix] = last0;
+        if (Tout) Tout[plane * HW + pix] = T0;
+        if (ncout) ncout[plane * HW + pix] = nc0;
+    }
+    if (in1) {
+        const size_t pix = (size_t)py1 * a.W + px;
+#pragma unroll
+        for (int c = 0; c < C; c++) U[(plane * C + c) * HW + pix] = acc1[c];
+        Tsave[plane * HW + pix] = T1;
+        lastsave[plane * HW + pix] = last1;
+        if (Tout) Tout[plane * HW + pix] = T1;
+        if (ncout) ncout[plane * HW + pix] = nc1;
     }
 }
 
+// Adjoint step of one pixel for one entry, walking back-to-front: recovers
+// T_k = T_{k+1} / (1 - alpha_k) (Sec. 4.2) and adds this pixel's
+// dL/d(mu, conic, o, w) to gl (mu 0-1, conic 2-4, o 5, w 6..).
 template <int C>
-__global__ void __launch_bounds__(256) k_raster_bwd(RasterArgs a, const float* __restrict__ Tsave,
-                                                    const uint32_t* __restrict__ lastsave,
-                                                    const float2* __restrict__ gU, float* __restrict__ g2d) {
+__device__ __forceinline__ bool adjoint_step(float power, float dx, float dy, const float4* rec, float amin,
+                                             float amax, float& T, float2 (&S)[C], const float2 (&g)[C],
+                                             float (&gl)[16]) {
+    const float4 r0 = rec[0], r1 = rec[1];
+    const float G_ = __expf(-power);
+    const float og = __fmul_rn(r1.y, G_);
+    const float alpha = fminf(amax, og);
+    if (alpha < amin) return false;
+    const float om = __fsub_rn(1.f, alpha);
+    const float iom = __frcp_rn(om);
+    const float Tk = T * iom;
+    const float aT = alpha * Tk;
+    float dLda = 0.f;
+#pragma unroll
+    for (int c = 0; c < C; c++) {
+        const float2 w = RecW<C>::get(rec, c);
+        dLda += g[c].x * (w.x * Tk - S[c].x * iom) + g[c].y * (w.y * Tk - S[c].y * iom);
+        S[c].x += w.x * aT;
+        S[c].y += w.y * aT;
+        gl[6 + 2 * c] += g[c].x * aT;
+        gl[7 + 2 * c] += g[c].y * aT;
+    }
+    T = Tk;
+    if (og <= amax) {  // a clamped alpha is flat in o G
+        const float dLdp = -dLda * og;
+        gl[5] += dLda * G_;
+        gl[0] += -dLdp * (r0.z * dx + r0.w * dy);
+        gl[1] += -dLdp * (r0.w * dx + r1.x * dy);
+        gl[2] += 0.5f * dx * dx * dLdp;
+        gl[3] += dx * dy * dLdp;
+        gl[4] += 0.5f * dy * dy * dLdp;
+    }
+    return true;
+}
+
+template <int C>
+__global__ void __launch_bounds__(RT) k_raster_bwd(RasterArgs a, const float* __restrict__ Tsave,
+                                                   const uint32_t* __restrict__ lastsave,
+                                                   const float2* __restrict__ gU, float* __restrict__ g2d) {
     constexpr int NR = C <= 1 ? 2 : (C <= 3 ? 3 : 4);
     constexpr int G = 6 + 2 * C;
-    __shared__ float4 srec[256][NR];
-    __shared__ uint32_t spos[256], sid[256];
-    __shared__ int wcnt[8];
+    __shared__ float4 srec[RT][NR];
+    __shared__ uint32_t spos[RT], sid[RT];
+    __shared__ int wcnt[RWARPS];
     __shared__ uint32_t smax;
-    const int t = threadIdx.x, lane = t & 31;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int tile = blockIdx.x, l = blockIdx.y, v = blockIdx.z;
     const int tx = tile % a.tilesX, ty = tile / a.tilesX;
-    const int px = tx * TILE + (t & 15), py = ty * TILE + (t >> 4);
-    const bool inside = px < a.W && py < a.H;
-    const float sx0 = (float)(tx * TILE), sy0 = (float)(ty * TILE + 2 * (t >> 5));  // this warp's strip
+    const int px = tx * TILE + (lane & 15);
+    const int py0 = ty * TILE + 4 * warp + (lane >> 4), py1 = py0 + 2;
+    const bool in0 = px < a.W && py0 < a.H, in1 = px < a.W && py1 < a.H;
+    const float sx0 = (float)(tx * TILE), sy0 = (float)(ty * TILE + 4 * warp);
     const uint32_t gb = ((uint32_t)(v * a.L + l) * a.ctY + ty / COARSE) * a.ctX + tx / COARSE;
     const uint32_t beg = a.off[gb];
     const size_t vN = (size_t)v * a.N;
     const size_t plane = (size_t)v * a.L + l;
     const size_t HW = (size_t)a.H * a.W;
-    const size_t pix = (size_t)py * a.W + px;
-    const float fpx = (float)px, fpy = (float)py;
-    float T = 1.f;
-    uint32_t lastp = 0;
-    float2 g[C], S[C];
+    const float fpx = (float)px, fpy = (float)py0;
+    float T0 = 1.f, T1 = 1.f;
+    uint32_t last0 = 0, last1 = 0;
+    float2 g0[C], g1[C], S0[C], S1[C];
 #pragma unroll
     for (int c = 0; c < C; c++) {
-        g[c] = make_float2(0.f, 0.f);
-        S[c] = make_float2(0.f, 0.f);
+        g0[c] = g1[c] = S0[c] = S1[c] = make_float2(0.f, 0.f);
     }
-    if (inside) {
-        T = Tsave[plane * HW + pix];
-        lastp = lastsave[plane * HW + pix];
+    if (in0) {
+        const size_t pix = (size_t)py0 * a.W + px;
+        T0 = Tsave[plane * HW + pix];
+        last0 = lastsave[plane * HW + pix];
 #pragma unroll
-        for (int c = 0; c < C; c++) g[c] = gU[(plane * C + c) * HW + pix];
+        for (int c = 0; c < C; c++) g0[c] = gU[(plane * C + c) * HW + pix];
+    }
+    if (in1) {
+        const size_t pix = (size_t)py1 * a.W + px;
+        T1 = Tsave[plane * HW + pix];
+        last1 = lastsave[plane * HW + pix];
+#pragma unroll
+        for (int c = 0; c < C; c++) g1[c] = gU[(plane * C + c) * HW + pix];
     }
     if (t == 0) smax = 0;
     __syncthreads();
-    if (lastp) atomicMax(&smax, lastp);
+    const uint32_t lmax = max(last0, last1);
+    if (lmax) atomicMax(&smax, lmax);
     __syncthreads();
     const uint32_t maxlast = smax;
     for (uint32_t hi = maxlast; hi > 0;) {
-        const uint32_t lo = hi > 256u ? hi - 256u : 0u;
+        const uint32_t lo = hi > (uint32_t)RT ? hi - RT : 0u;
         __syncthreads();  // previous batch fully consumed
         const int total = stage_batch<NR>(a, vN, beg, lo, hi, tx, ty, srec, spos, sid, wcnt);
         for (int k1 = total; k1 > 0; k1 -= 32) {
@@ -268,43 +353,19 @@ __global__ void __launch_bounds__(256) k_raster_bwd(RasterArgs a, const float* _
                 const int b = 31 - __clz(m);
                 m &= ~(1u << b);
                 const int k = k0 + b;
+                const uint32_t pos = spos[k];
                 float gl[16];
 #pragma unroll
                 for (int e = 0; e < 16; e++) gl[e] = 0.f;
                 bool contrib = false;
-                if (spos[k] < lastp) {
+                if (pos < last0 || pos < last1) {
                     const float4 r0 = srec[k][0], r1 = srec[k][1];
-                    float dx, dy;
-                    const float power = footprint_power(fpx, fpy, r0, r1.x, &dx, &dy);
-                    const float G_ = __expf(-power);
-                    const float og = __fmul_rn(r1.y, G_);
-                    const float alpha = fminf(a.amax, og);
-                    if (alpha >= a.amin) {
-                        contrib = true;
-                        const float om = __fsub_rn(1.f, alpha);
-                        const float Tk = __fdiv_rn(T, om);
-                        const float aT = alpha * Tk;
-                        const float iom = 1.f / om;
-                        float dLda = 0.f;
-#pragma unroll
-                        for (int c = 0; c < C; c++) {
-                            const float2 w = RecW<C>::get(srec[k], c);
-                            dLda += g[c].x * (w.x * Tk - S[c].x * iom) + g[c].y * (w.y * Tk - S[c].y * iom);
-                            S[c].x += w.x * aT;
-                            S[c].y += w.y * aT;
-                            gl[6 + 2 * c] = g[c].x * aT;
-                            gl[7 + 2 * c] = g[c].y * aT;
-                        }
-                        T = Tk;
-                        if (og <= a.amax) {  // a clamped alpha is flat in o G
-                            const float dLdp = -dLda * og;
-                            gl[5] = dLda * G_;
-                            gl[0] = -dLdp * (r0.z * dx + r0.w * dy);
-                            gl[1] = -dLdp * (r0.w * dx + r1.x * dy);
-                            gl[2] = 0.5f * dx * dx * dLdp;
-                            gl[3] = dx * dy * dLdp;
-                            gl[4] = 0.5f * dy * dy * dLdp;
-                        }
+                    float pa, pb, dx, dy;
+                    footprint_pair(fpx, fpy, r0, r1.x, &pa, &pb, &dx, &dy);
+                    if (pos < last0) contrib |= adjoint_step<C>(pa, dx, dy, srec[k], a.amin, a.amax, T0, S0, g0, gl);
+                    if (pos < last1) {
+                        const float dy1 = __fsub_rn((float)py1, r0.y);
+                        contrib |= adjoint_step<C>(pb, dx, dy1, srec[k], a.amin, a.amax, T1, S1, g1, gl);
                     }
                 }
                 if (__any_sync(0xffffffffu, contrib)) {
@@ -328,10 +389,10 @@ hcgs_status raster_forward(hcgs_ctx* ctx, hcgs_saved* s, float2* U, float* T_out
     float* Ts = (float*)s->Tfin.p;
     uint32_t* ls = (uint32_t*)s->last.p;
     switch (s->C) {
-        case 1: HCGS_KERNEL(ctx, "k_raster_fwd", st, k_raster_fwd<1><<<grid, 256, 0, st>>>(a, U, Ts, ls, T_out, nc_out)); break;
-        case 2: HCGS_KERNEL(ctx, "k_raster_fwd", st, k_raster_fwd<2><<<grid, 256, 0, st>>>(a, U, Ts, ls, T_out, nc_out)); break;
-        case 3: HCGS_KERNEL(ctx, "k_raster_fwd", st, k_raster_fwd<3><<<grid, 256, 0, st>>>(a, U, Ts, ls, T_out, nc_out)); break;
-        default: HCGS_KERNEL(ctx, "k_raster_fwd", st, k_raster_fwd<4><<<grid, 256, 0, st>>>(a, U, Ts, ls, T_out, nc_out)); break;
+        case 1: HCGS_KERNEL(ctx, "k_raster_fwd", st, k_raster_fwd<1><<<grid, RT, 0, st>>>(a, U, Ts, ls, T_out, nc_out)); break;
+        case 2: HCGS_KERNEL(ctx, "k_raster_fwd", st, k_raster_fwd<2><<<grid, RT, 0, st>>>(a, U, Ts, ls, T_out, nc_out)); break;
+        case 3: HCGS_KERNEL(ctx, "k_raster_fwd", st, k_raster_fwd<3><<<grid, RT, 0, st>>>(a, U, Ts, ls, T_out, nc_out)); break;
+        default: HCGS_KERNEL(ctx, "k_raster_fwd", st, k_raster_fwd<4><<<grid, RT, 0, st>>>(a, U, Ts, ls, T_out, nc_out)); break;
     }
     HCGS_LAUNCH(ctx, "k_raster_fwd");
     return HCGS_OK;
@@ -347,10 +408,10 @@ hcgs_status raster_backward(hcgs_ctx* ctx, hcgs_saved* s, const float2* gU, cuda
     const uint32_t* ls = (const uint32_t*)s->last.p;
     float* g2 = (float*)s->g2d.p;
     switch (s->C) {
-        case 1: HCGS_KERNEL(ctx, "k_raster_bwd", st, k_raster_bwd<1><<<grid, 256, 0, st>>>(a, Ts, ls, gU, g2)); break;
-        case 2: HCGS_KERNEL(ctx, "k_raster_bwd", st, k_raster_bwd<2><<<grid, 256, 0, st>>>(a, Ts, ls, gU, g2)); break;
-        case 3: HCGS_KERNEL(ctx, "k_raster_bwd", st, k_raster_bwd<3><<<grid, 256, 0, st>>>(a, Ts, ls, gU, g2)); break;
-        default: HCGS_KERNEL(ctx, "k_raster_bwd", st, k_raster_bwd<4><<<grid, 256, 0, st>>>(a, Ts, ls, gU, g2)); break;
+        case 1: HCGS_KERNEL(ctx, "k_raster_bwd", st, k_raster_bwd<1><<<grid, RT, 0, st>>>(a, Ts, ls, gU, g2)); break;
+        case 2: HCGS_KERNEL(ctx, "k_raster_bwd", st, k_raster_bwd<2><<<grid, RT, 0, st>>>(a, Ts, ls, gU, g2)); break;
+        case 3: HCGS_KERNEL(ctx, "k_raster_bwd", st, k_raster_bwd<3><<<grid, RT, 0, st>>>(a, Ts, ls, gU, g2)); break;
+        default: HCGS_KERNEL(ctx, "k_raster_bwd", st, k_raster_bwd<4><<<grid, RT, 0, st>>>(a, Ts, ls, gU, g2)); break;
     }
     HCGS_LAUNCH(ctx, "k_raster_bwd");
     return HCGS_OK;
