@@ -129,14 +129,29 @@ __device__ __forceinline__ bool strip_hits(float4 r0, float Cc, float o, float x
     return hit;
 }
 
-// Footprint exponents of the thread's two pixels (rows y and y + 2):
-// power_a = 1/2 (A dx^2 + C dy^2) + B dx dy (Supp. D.3), power_b = power_a +
-// 2 (B dx + C dy + C).  Shared by forward and adjoint, so both take the same
-// decisions.
-__device__ __forceinline__ void footprint_pair(float px, float py, float4 r0, float Cc, float* pa, float* pb,
-                                               float* dx, float* dy) {
-    *pa = footprint_power(px, py, r0, Cc, dx, dy);
-    *pb = __fmaf_rn(2.f, __fmaf_rn(r0.w, *dx, __fmaf_rn(Cc, *dy, Cc)), *pa);
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
+// The thread's two pixels (same column, rows y0 and y0 + 2) against one
+// Gaussian record, as packed FP32x2 arithmetic: d = pixel - mu,
+// power = 1/2 (A dx^2 + C dy^2) + B dx dy (Supp. D.3), G = exp(-power),
+// o G and alpha = min(alpha_max, o G).  Shared by forward and adjoint, so
+// both take identical decisions.
+__device__ __forceinline__ void eval_pair(float px, float2 py2, float4 r0, float Cc, float o, float amax,
+                                          float& dx, float2& dy2, float2& G2, float2& og2, float2& a2) {
+    dx = __fsub_rn(px, r0.x);
+    dy2 = __fadd2_rn(py2, f2(-r0.y));
+    const float adx2 = __fmul_rn(r0.z, __fmul_rn(dx, dx));
+    float2 p = __fmul2_rn(f2(0.5f), __ffma2_rn(f2(Cc), __fmul2_rn(dy2, dy2), f2(adx2)));
+    p = __ffma2_rn(f2(__fmul_rn(r0.w, dx)), dy2, p);
+    const float2 e = __fmul2_rn(p, f2(-1.4426950408889634f));  // exp(-p) = 2^(-p log2 e)
+    G2 = make_float2(ex2_approx(e.x), ex2_approx(e.y));
+    og2 = __fmul2_rn(f2(o), G2);
+    a2 = make_float2(fminf(amax, og2.x), fminf(amax, og2.y));
 }
 
 // Warp reduce-scatter of 16 values: afterwards lanes 2i and 2i+1 both hold the
@@ -153,26 +168,6 @@ __device__ __forceinline__ float warp_reduce_scatter16(float (&v)[16], int lane)
         }
     }
     return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
-}
-
-// Forward step of one pixel for one entry (Algorithm 2).
-template <int C>
-__device__ __forceinline__ void composite_step(float power, float o, const float4* rec, float amin, float amax,
-                                               float teps, uint32_t pos, float& T, float2 (&acc)[C], bool& done,
-                                               uint32_t& lastp, int& nc) {
-    const float alpha = fminf(amax, __fmul_rn(o, __expf(-power)));
-    if (alpha < amin) return;
-    const float wt = __fmul_rn(alpha, T);
-#pragma unroll
-    for (int c = 0; c < C; c++) {
-        const float2 w = RecW<C>::get(rec, c);
-        acc[c].x = __fmaf_rn(w.x, wt, acc[c].x);
-        acc[c].y = __fmaf_rn(w.y, wt, acc[c].y);
-    }
-    T = __fmul_rn(T, __fsub_rn(1.f, alpha));
-    nc++;
-    lastp = pos + 1;
-    if (T < teps) done = true;
 }
 
 template <int C>
@@ -193,11 +188,12 @@ __global__ void __launch_bounds__(RT) k_raster_fwd(RasterArgs a, float2* __restr
     const uint32_t gb = ((uint32_t)(v * a.L + l) * a.ctY + ty / COARSE) * a.ctX + tx / COARSE;
     const uint32_t beg = a.off[gb], n = a.off[gb + 1] - beg;
     const size_t vN = (size_t)v * a.N;
-    const float fpx = (float)px, fpy = (float)py0;
-    float T0 = 1.f, T1 = 1.f;
-    float2 acc0[C], acc1[C];
+    const float fpx = (float)px;
+    const float2 py2 = make_float2((float)py0, (float)py1);
+    float2 T2 = f2(1.f);
+    float2 accX[C], accY[C];  // (pixel 0, pixel 1) pairs of Re and Im
 #pragma unroll
-    for (int c = 0; c < C; c++) acc0[c] = acc1[c] = make_float2(0.f, 0.f);
+    for (int c = 0; c < C; c++) accX[c] = accY[c] = f2(0.f);
     bool d0 = !in0, d1 = !in1;
     uint32_t last0 = 0, last1 = 0;
     int nc0 = 0, nc1 = 0;
@@ -218,11 +214,32 @@ __global__ void __launch_bounds__(RT) k_raster_fwd(RasterArgs a, float2* __restr
                 m &= m - 1;
                 if (d0 && d1) continue;
                 const float4 r0 = srec[k][0], r1 = srec[k][1];
-                float pa, pb, dx, dy;
-                footprint_pair(fpx, fpy, r0, r1.x, &pa, &pb, &dx, &dy);
+                float dx;
+                float2 dy2, G2, og2, a2;
+                eval_pair(fpx, py2, r0, r1.x, r1.y, a.amax, dx, dy2, G2, og2, a2);
+                const bool c0 = !d0 && a2.x >= a.amin, c1 = !d1 && a2.y >= a.amin;
+                if (!(c0 || c1)) continue;
+                // a pixel that does not take this step gets alpha 0: no add, T unchanged
+                const float2 al = make_float2(c0 ? a2.x : 0.f, c1 ? a2.y : 0.f);
+                const float2 wt = __fmul2_rn(al, T2);
+#pragma unroll
+                for (int c = 0; c < C; c++) {
+                    const float2 w = RecW<C>::get(srec[k], c);
+                    accX[c] = __ffma2_rn(f2(w.x), wt, accX[c]);
+                    accY[c] = __ffma2_rn(f2(w.y), wt, accY[c]);
+                }
+                T2 = __fmul2_rn(T2, __fadd2_rn(f2(1.f), make_float2(-al.x, -al.y)));
                 const uint32_t pos = spos[k];
-                if (!d0) composite_step<C>(pa, r1.y, srec[k], a.amin, a.amax, a.teps, pos, T0, acc0, d0, last0, nc0);
-                if (!d1) composite_step<C>(pb, r1.y, srec[k], a.amin, a.amax, a.teps, pos, T1, acc1, d1, last1, nc1);
+                if (c0) {
+                    nc0++;
+                    last0 = pos + 1;
+                    if (T2.x < a.teps) d0 = true;
+                }
+                if (c1) {
+                    nc1++;
+                    last1 = pos + 1;
+                    if (T2.y < a.teps) d1 = true;
+                }
             }
         }
     }
@@ -231,60 +248,21 @@ __global__ void __launch_bounds__(RT) k_raster_fwd(RasterArgs a, float2* __restr
     if (in0) {
         const size_t pix = (size_t)py0 * a.W + px;
 #pragma unroll
-        for (int c = 0; c < C; c++) U[(plane * C + c) * HW + pix] = acc0[c];
-        Tsave[plane * HW + pix] = T0;
+        for (int c = 0; c < C; c++) U[(plane * C + c) * HW + pix] = make_float2(accX[c].x, accY[c].x);
+        Tsave[plane * HW + pix] = T2.x;
         lastsave[plane * HW + pix] = last0;
-        if (Tout) Tout[plane * HW + pix] = T0;
+        if (Tout) Tout[plane * HW + pix] = T2.x;
         if (ncout) ncout[plane * HW + pix] = nc0;
     }
     if (in1) {
         const size_t pix = (size_t)py1 * a.W + px;
 #pragma unroll
-        for (int c = 0; c < C; c++) U[(plane * C + c) * HW + pix] = acc1[c];
-        Tsave[plane * HW + pix] = T1;
+        for (int c = 0; c < C; c++) U[(plane * C + c) * HW + pix] = make_float2(accX[c].y, accY[c].y);
+        Tsave[plane * HW + pix] = T2.y;
         lastsave[plane * HW + pix] = last1;
-        if (Tout) Tout[plane * HW + pix] = T1;
+        if (Tout) Tout[plane * HW + pix] = T2.y;
         if (ncout) ncout[plane * HW + pix] = nc1;
     }
-}
-
-// Adjoint step of one pixel for one entry, walking back-to-front: recovers
-// T_k = T_{k+1} / (1 - alpha_k) (Sec. 4.2) and adds this pixel's
-// dL/d(mu, conic, o, w) to gl (mu 0-1, conic 2-4, o 5, w 6..).
-template <int C>
-__device__ __forceinline__ bool adjoint_step(float power, float dx, float dy, const float4* rec, float amin,
-                                             float amax, float& T, float2 (&S)[C], const float2 (&g)[C],
-                                             float (&gl)[16]) {
-    const float4 r0 = rec[0], r1 = rec[1];
-    const float G_ = __expf(-power);
-    const float og = __fmul_rn(r1.y, G_);
-    const float alpha = fminf(amax, og);
-    if (alpha < amin) return false;
-    const float om = __fsub_rn(1.f, alpha);
-    const float iom = __frcp_rn(om);
-    const float Tk = T * iom;
-    const float aT = alpha * Tk;
-    float dLda = 0.f;
-#pragma unroll
-    for (int c = 0; c < C; c++) {
-        const float2 w = RecW<C>::get(rec, c);
-        dLda += g[c].x * (w.x * Tk - S[c].x * iom) + g[c].y * (w.y * Tk - S[c].y * iom);
-        S[c].x += w.x * aT;
-        S[c].y += w.y * aT;
-        gl[6 + 2 * c] += g[c].x * aT;
-        gl[7 + 2 * c] += g[c].y * aT;
-    }
-    T = Tk;
-    if (og <= amax) {  // a clamped alpha is flat in o G
-        const float dLdp = -dLda * og;
-        gl[5] += dLda * G_;
-        gl[0] += -dLdp * (r0.z * dx + r0.w * dy);
-        gl[1] += -dLdp * (r0.w * dx + r1.x * dy);
-        gl[2] += 0.5f * dx * dx * dLdp;
-        gl[3] += dx * dy * dLdp;
-        gl[4] += 0.5f * dy * dy * dLdp;
-    }
-    return true;
 }
 
 template <int C>
@@ -297,6 +275,10 @@ __global__ void __launch_bounds__(RT) k_raster_bwd(RasterArgs a, const float* __
     __shared__ uint32_t spos[RT], sid[RT];
     __shared__ int wcnt[RWARPS];
     __shared__ uint32_t smax;
+    // per staged entry: the CTA's sum of its warps' gradient contributions,
+    // flushed to global memory once per batch (one atomic per value)
+    __shared__ float gacc[RT][16];
+    __shared__ int gany[RT];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int tile = blockIdx.x, l = blockIdx.y, v = blockIdx.z;
     const int tx = tile % a.tilesX, ty = tile / a.tilesX;
@@ -309,29 +291,39 @@ __global__ void __launch_bounds__(RT) k_raster_bwd(RasterArgs a, const float* __
     const size_t vN = (size_t)v * a.N;
     const size_t plane = (size_t)v * a.L + l;
     const size_t HW = (size_t)a.H * a.W;
-    const float fpx = (float)px, fpy = (float)py0;
-    float T0 = 1.f, T1 = 1.f;
+    const float fpx = (float)px;
+    const float2 py2 = make_float2((float)py0, (float)py1);
+    float2 T2 = f2(1.f);
     uint32_t last0 = 0, last1 = 0;
-    float2 g0[C], g1[C], S0[C], S1[C];
+    float2 gX[C], gY[C], SX[C], SY[C];  // (pixel 0, pixel 1) pairs
 #pragma unroll
-    for (int c = 0; c < C; c++) {
-        g0[c] = g1[c] = S0[c] = S1[c] = make_float2(0.f, 0.f);
-    }
+    for (int c = 0; c < C; c++) gX[c] = gY[c] = SX[c] = SY[c] = f2(0.f);
     if (in0) {
         const size_t pix = (size_t)py0 * a.W + px;
-        T0 = Tsave[plane * HW + pix];
+        T2.x = Tsave[plane * HW + pix];
         last0 = lastsave[plane * HW + pix];
 #pragma unroll
-        for (int c = 0; c < C; c++) g0[c] = gU[(plane * C + c) * HW + pix];
+        for (int c = 0; c < C; c++) {
+            const float2 gg = gU[(plane * C + c) * HW + pix];
+            gX[c].x = gg.x;
+            gY[c].x = gg.y;
+        }
     }
     if (in1) {
         const size_t pix = (size_t)py1 * a.W + px;
-        T1 = Tsave[plane * HW + pix];
+        T2.y = Tsave[plane * HW + pix];
         last1 = lastsave[plane * HW + pix];
 #pragma unroll
-        for (int c = 0; c < C; c++) g1[c] = gU[(plane * C + c) * HW + pix];
+        for (int c = 0; c < C; c++) {
+            const float2 gg = gU[(plane * C + c) * HW + pix];
+            gX[c].y = gg.x;
+            gY[c].y = gg.y;
+        }
     }
     if (t == 0) smax = 0;
+#pragma unroll
+    for (int e = 0; e < 16; e++) gacc[t][e] = 0.f;
+    gany[t] = 0;
     __syncthreads();
     const uint32_t lmax = max(last0, last1);
     if (lmax) atomicMax(&smax, lmax);
@@ -360,20 +352,68 @@ __global__ void __launch_bounds__(RT) k_raster_bwd(RasterArgs a, const float* __
                 bool contrib = false;
                 if (pos < last0 || pos < last1) {
                     const float4 r0 = srec[k][0], r1 = srec[k][1];
-                    float pa, pb, dx, dy;
-                    footprint_pair(fpx, fpy, r0, r1.x, &pa, &pb, &dx, &dy);
-                    if (pos < last0) contrib |= adjoint_step<C>(pa, dx, dy, srec[k], a.amin, a.amax, T0, S0, g0, gl);
-                    if (pos < last1) {
-                        const float dy1 = __fsub_rn((float)py1, r0.y);
-                        contrib |= adjoint_step<C>(pb, dx, dy1, srec[k], a.amin, a.amax, T1, S1, g1, gl);
+                    float dx;
+                    float2 dy2, G2, og2, a2;
+                    eval_pair(fpx, py2, r0, r1.x, r1.y, a.amax, dx, dy2, G2, og2, a2);
+                    const bool c0 = pos < last0 && a2.x >= a.amin, c1 = pos < last1 && a2.y >= a.amin;
+                    if (c0 || c1) {
+                        contrib = true;
+                        // back-to-front step (Sec. 4.2): T_k = T_{k+1} / (1 - alpha_k);
+                        // dU/dalpha_k = w T_k - S_k / (1 - alpha_k), S_k = sum_{m>k} w alpha T
+                        const float2 al = make_float2(c0 ? a2.x : 0.f, c1 ? a2.y : 0.f);
+                        const float2 om = __fadd2_rn(f2(1.f), make_float2(-al.x, -al.y));
+                        const float2 iom = make_float2(__frcp_rn(om.x), __frcp_rn(om.y));
+                        const float2 Tk = __fmul2_rn(T2, iom);
+                        const float2 aT = __fmul2_rn(al, Tk);
+                        float2 dLda = f2(0.f);
+#pragma unroll
+                        for (int c = 0; c < C; c++) {
+                            const float2 w = RecW<C>::get(srec[k], c);
+                            const float2 ux = __ffma2_rn(make_float2(-SX[c].x, -SX[c].y), iom, __fmul2_rn(f2(w.x), Tk));
+                            const float2 uy = __ffma2_rn(make_float2(-SY[c].x, -SY[c].y), iom, __fmul2_rn(f2(w.y), Tk));
+                            dLda = __ffma2_rn(gX[c], ux, __ffma2_rn(gY[c], uy, dLda));
+                            SX[c] = __ffma2_rn(f2(w.x), aT, SX[c]);
+                            SY[c] = __ffma2_rn(f2(w.y), aT, SY[c]);
+                            const float2 gwx = __fmul2_rn(gX[c], aT), gwy = __fmul2_rn(gY[c], aT);
+                            gl[6 + 2 * c] = gwx.x + gwx.y;
+                            gl[7 + 2 * c] = gwy.x + gwy.y;
+                        }
+                        T2 = Tk;
+                        // a clamped alpha (o G > alpha_max) is flat in o G
+                        const float2 dLa = make_float2(c0 && og2.x <= a.amax ? dLda.x : 0.f,
+                                                       c1 && og2.y <= a.amax ? dLda.y : 0.f);
+                        const float2 dLdp = __fmul2_rn(make_float2(-dLa.x, -dLa.y), og2);  // dL/dpower
+                        const float2 go = __fmul2_rn(dLa, G2);
+                        gl[5] = go.x + go.y;
+                        const float adx = __fmul_rn(r0.z, dx), bdx = __fmul_rn(r0.w, dx);
+                        const float2 q0 = __ffma2_rn(f2(r0.w), dy2, f2(adx));   // A dx + B dy
+                        const float2 q1 = __ffma2_rn(f2(r1.x), dy2, f2(bdx));   // B dx + C dy
+                        const float2 m0 = __fmul2_rn(dLdp, q0), m1 = __fmul2_rn(dLdp, q1);
+                        gl[0] = -(m0.x + m0.y);
+                        gl[1] = -(m1.x + m1.y);
+                        const float sp = dLdp.x + dLdp.y;
+                        const float2 pdy = __fmul2_rn(dLdp, dy2);
+                        gl[2] = 0.5f * dx * dx * sp;
+                        gl[3] = dx * (pdy.x + pdy.y);
+                        gl[4] = 0.5f * (pdy.x * dy2.x + pdy.y * dy2.y);
                     }
                 }
                 if (__any_sync(0xffffffffu, contrib)) {
                     const float sum = warp_reduce_scatter16(gl, lane);
                     const int idx = lane >> 1;
-                    if (!(lane & 1) && idx < G) atomicAdd(g2d + (vN + sid[k]) * G + idx, sum);
+                    if (!(lane & 1) && idx < G) atomicAdd(&gacc[k][idx], sum);
+                    if (lane == 0) gany[k] = 1;
                 }
             }
+        }
+        __syncthreads();
+        if (t < total && gany[t]) {
+            float* dst = g2d + (vN + sid[t]) * G;
+#pragma unroll
+            for (int e = 0; e < G; e++) atomicAdd(dst + e, gacc[t][e]);
+#pragma unroll
+            for (int e = 0; e < 16; e++) gacc[t][e] = 0.f;
+            gany[t] = 0;
         }
         hi = lo;
     }
