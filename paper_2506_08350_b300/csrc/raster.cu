@@ -2,17 +2,18 @@
 // (Sec. 4.1 per-plane field equation; Algorithm 2) and its adjoint (Supp. D.4;
 // Sec. 4.2: back-to-front walk, transmittance recovered by division).
 //
-// One CTA of 128 threads per (16x16 tile, plane, view); two pixels per
-// thread (rows r and r + 2 of the warp's 16 x 4 strip).  The CTA streams its
-// 64x64 bucket's list (already in visiting order), keeps the entries whose
-// tile rectangle covers the tile (warp ballot compaction keeps the order) and
-// stages their records in shared memory.  Each warp tests 32 staged entries
-// at a time against its strip (exact superset test), and for every hit both
-// pixels of every lane take the step of Algorithm 2: alpha = min(alpha_max,
+// One CTA of 128 threads per (16 x 32 pixel region = two vertically adjacent
+// 16x16 tiles, plane, view); four pixels per thread (one column, rows r,
+// r + 2, r + 4, r + 6 of the warp's 16 x 8 strip), evaluated as two packed
+// FP32x2 pairs.  Both tiles lie in the same 64x64 bucket: the CTA streams
+// the bucket's list (already in visiting order) once, keeps the entries whose
+// tile rectangle covers either tile (warp ballot compaction keeps the order)
+// and stages their records in shared memory.  Each warp tests 32 staged
+// entries at a time against its strip (exact superset test), and for every
+// hit each of its pixels takes the step of Algorithm 2: alpha = min(alpha_max,
 // o exp(-power)); skip when alpha < alpha_min; U += w alpha T; T *= 1 - alpha;
 // stop once T < T_eps.  The record load, the loop control and (in the
-// adjoint) the per-entry warp reduction are shared by the two pixels; the
-// second pixel's exponent is the first one's plus 2 (B dx + C dy + C).
+// adjoint) the per-entry warp reduction are shared by the four pixels.
 // The CTA leaves the list when all its pixels have stopped.
 //
 // The alpha arithmetic uses explicitly rounded intrinsics so that the forward
@@ -79,8 +80,9 @@ __device__ __forceinline__ int stage_batch(const RasterArgs& a, size_t vN, uint3
     if (p < hi) {
         s = a.list[beg + p];
         const uint2 rc = a.rects[vN + s];
-        ok = (uint32_t)tx >= (rc.x & 0xFFFFu) && (uint32_t)tx < (rc.x >> 16) && (uint32_t)ty >= (rc.y & 0xFFFFu) &&
-             (uint32_t)ty < (rc.y >> 16);
+        // tile column tx, tile rows ty and ty + 1
+        ok = (uint32_t)tx >= (rc.x & 0xFFFFu) && (uint32_t)tx < (rc.x >> 16) && (rc.y & 0xFFFFu) < (uint32_t)ty + 2u &&
+             (rc.y >> 16) > (uint32_t)ty;
     }
     const unsigned bal = __ballot_sync(0xffffffffu, ok);
     if (lane == 0) wcnt[warp] = __popc(bal);
@@ -105,7 +107,7 @@ __device__ __forceinline__ int stage_batch(const RasterArgs& a, size_t vN, uint3
 }
 
 // Can Gaussian (mu, conic A B C, opacity o) reach alpha >= alpha_min at any
-// pixel centre of the strip x in [x0, x0 + 15], y in [y0, y0 + 3]?  For each
+// pixel centre of the strip x in [x0, x0 + 15], y in [y0, y0 + 7]?  For each
 // row the footprint quadratic q = A dx^2 + 2 B dx dy + C dy^2 is minimised
 // over the row segment (a convex 1D problem: the unconstrained minimiser
 // clamped to the segment) and compared with 2 ln(o / alpha_min), with a
@@ -119,7 +121,7 @@ __device__ __forceinline__ bool strip_hits(float4 r0, float Cc, float o, float x
     const float slope = r0.w / r0.z;
     bool hit = false;
 #pragma unroll
-    for (int r = 0; r < 4; r++) {
+    for (int r = 0; r < 8; r++) {
         const float dy = (y0 + (float)r) - r0.y;
         const float xs = fminf(fmaxf(r0.x - slope * dy, x0), x1);
         const float dx = xs - r0.x;
@@ -170,6 +172,30 @@ __device__ __forceinline__ float warp_reduce_scatter16(float (&v)[16], int lane)
     return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
+// Forward step of a pixel pair that takes it (c0/c1) for one record: a pixel
+// that does not take it gets alpha 0 (no add, T unchanged).
+template <int C>
+__device__ __forceinline__ void fwd_pair(const float4* rec, float2 a2, bool c0, bool c1, float2& T2,
+                                         float2 (&accX)[C], float2 (&accY)[C]) {
+    const float2 al = make_float2(c0 ? a2.x : 0.f, c1 ? a2.y : 0.f);
+    const float2 wt = __fmul2_rn(al, T2);
+#pragma unroll
+    for (int c = 0; c < C; c++) {
+        const float2 w = RecW<C>::get(rec, c);
+        accX[c] = __ffma2_rn(f2(w.x), wt, accX[c]);
+        accY[c] = __ffma2_rn(f2(w.y), wt, accY[c]);
+    }
+    T2 = __fmul2_rn(T2, __fadd2_rn(f2(1.f), make_float2(-al.x, -al.y)));
+}
+
+__device__ __forceinline__ void book(bool c, float T, float teps, uint32_t pos, int& nc, uint32_t& last, bool& d) {
+    if (c) {
+        nc++;
+        last = pos + 1;
+        if (T < teps) d = true;
+    }
+}
+
 template <int C>
 __global__ void __launch_bounds__(RT) k_raster_fwd(RasterArgs a, float2* __restrict__ U, float* __restrict__ Tsave,
                                                    uint32_t* __restrict__ lastsave, float* __restrict__ Tout,
@@ -179,30 +205,36 @@ __global__ void __launch_bounds__(RT) k_raster_fwd(RasterArgs a, float2* __restr
     __shared__ uint32_t spos[RT], sid[RT];
     __shared__ int wcnt[RWARPS];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int tile = blockIdx.x, l = blockIdx.y, v = blockIdx.z;
-    const int tx = tile % a.tilesX, ty = tile / a.tilesX;
+    const int ry = (a.tilesY + 1) / 2;
+    const int reg = blockIdx.x, l = blockIdx.y, v = blockIdx.z;
+    const int tx = reg % a.tilesX, ty = 2 * (reg / a.tilesX);  // tiles (tx, ty) and (tx, ty + 1)
+    (void)ry;
     const int px = tx * TILE + (lane & 15);
-    const int py0 = ty * TILE + 4 * warp + (lane >> 4), py1 = py0 + 2;
-    const bool in0 = px < a.W && py0 < a.H, in1 = px < a.W && py1 < a.H;
-    const float sx0 = (float)(tx * TILE), sy0 = (float)(ty * TILE + 4 * warp);  // this warp's strip
+    const int py = ty * TILE + 8 * warp + (lane >> 4);  // rows py, py + 2, py + 4, py + 6
+    bool in[4], d[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        in[q] = px < a.W && py + 2 * q < a.H;
+        d[q] = !in[q];
+    }
+    const float sx0 = (float)(tx * TILE), sy0 = (float)(ty * TILE + 8 * warp);  // this warp's strip
     const uint32_t gb = ((uint32_t)(v * a.L + l) * a.ctY + ty / COARSE) * a.ctX + tx / COARSE;
     const uint32_t beg = a.off[gb], n = a.off[gb + 1] - beg;
     const size_t vN = (size_t)v * a.N;
     const float fpx = (float)px;
-    const float2 py2 = make_float2((float)py0, (float)py1);
-    float2 T2 = f2(1.f);
-    float2 accX[C], accY[C];  // (pixel 0, pixel 1) pairs of Re and Im
+    const float2 pyA = make_float2((float)py, (float)(py + 2)), pyB = make_float2((float)(py + 4), (float)(py + 6));
+    float2 TA = f2(1.f), TB = f2(1.f);
+    float2 aAX[C], aAY[C], aBX[C], aBY[C];
 #pragma unroll
-    for (int c = 0; c < C; c++) accX[c] = accY[c] = f2(0.f);
-    bool d0 = !in0, d1 = !in1;
-    uint32_t last0 = 0, last1 = 0;
-    int nc0 = 0, nc1 = 0;
+    for (int c = 0; c < C; c++) aAX[c] = aAY[c] = aBX[c] = aBY[c] = f2(0.f);
+    uint32_t last[4] = {0, 0, 0, 0};
+    int nc[4] = {0, 0, 0, 0};
     for (uint32_t lo = 0; lo < n; lo += RT) {
-        if (__syncthreads_count(!(d0 && d1)) == 0) break;
+        if (__syncthreads_count(!(d[0] && d[1] && d[2] && d[3])) == 0) break;
         const uint32_t hi = min(n, lo + (uint32_t)RT);
         const int total = stage_batch<NR>(a, vN, beg, lo, hi, tx, ty, srec, spos, sid, wcnt);
         for (int k0 = 0; k0 < total; k0 += 32) {
-            if (__all_sync(0xffffffffu, d0 && d1)) break;
+            if (__all_sync(0xffffffffu, d[0] && d[1] && d[2] && d[3])) break;
             bool hit = false;
             if (k0 + lane < total) {
                 const float4 q0 = srec[k0 + lane][0], q1 = srec[k0 + lane][1];
@@ -212,57 +244,98 @@ __global__ void __launch_bounds__(RT) k_raster_fwd(RasterArgs a, float2* __restr
             while (m) {
                 const int k = k0 + __ffs(m) - 1;
                 m &= m - 1;
-                if (d0 && d1) continue;
+                if (d[0] && d[1] && d[2] && d[3]) continue;
                 const float4 r0 = srec[k][0], r1 = srec[k][1];
+                const uint32_t pos = spos[k];
                 float dx;
                 float2 dy2, G2, og2, a2;
-                eval_pair(fpx, py2, r0, r1.x, r1.y, a.amax, dx, dy2, G2, og2, a2);
-                const bool c0 = !d0 && a2.x >= a.amin, c1 = !d1 && a2.y >= a.amin;
-                if (!(c0 || c1)) continue;
-                // a pixel that does not take this step gets alpha 0: no add, T unchanged
-                const float2 al = make_float2(c0 ? a2.x : 0.f, c1 ? a2.y : 0.f);
-                const float2 wt = __fmul2_rn(al, T2);
-#pragma unroll
-                for (int c = 0; c < C; c++) {
-                    const float2 w = RecW<C>::get(srec[k], c);
-                    accX[c] = __ffma2_rn(f2(w.x), wt, accX[c]);
-                    accY[c] = __ffma2_rn(f2(w.y), wt, accY[c]);
+                if (!(d[0] && d[1])) {
+                    eval_pair(fpx, pyA, r0, r1.x, r1.y, a.amax, dx, dy2, G2, og2, a2);
+                    const bool c0 = !d[0] && a2.x >= a.amin, c1 = !d[1] && a2.y >= a.amin;
+                    if (c0 || c1) {
+                        fwd_pair<C>(srec[k], a2, c0, c1, TA, aAX, aAY);
+                        book(c0, TA.x, a.teps, pos, nc[0], last[0], d[0]);
+                        book(c1, TA.y, a.teps, pos, nc[1], last[1], d[1]);
+                    }
                 }
-                T2 = __fmul2_rn(T2, __fadd2_rn(f2(1.f), make_float2(-al.x, -al.y)));
-                const uint32_t pos = spos[k];
-                if (c0) {
-                    nc0++;
-                    last0 = pos + 1;
-                    if (T2.x < a.teps) d0 = true;
-                }
-                if (c1) {
-                    nc1++;
-                    last1 = pos + 1;
-                    if (T2.y < a.teps) d1 = true;
+                if (!(d[2] && d[3])) {
+                    eval_pair(fpx, pyB, r0, r1.x, r1.y, a.amax, dx, dy2, G2, og2, a2);
+                    const bool c2 = !d[2] && a2.x >= a.amin, c3 = !d[3] && a2.y >= a.amin;
+                    if (c2 || c3) {
+                        fwd_pair<C>(srec[k], a2, c2, c3, TB, aBX, aBY);
+                        book(c2, TB.x, a.teps, pos, nc[2], last[2], d[2]);
+                        book(c3, TB.y, a.teps, pos, nc[3], last[3], d[3]);
+                    }
                 }
             }
         }
     }
     const size_t plane = (size_t)v * a.L + l;
     const size_t HW = (size_t)a.H * a.W;
-    if (in0) {
-        const size_t pix = (size_t)py0 * a.W + px;
 #pragma unroll
-        for (int c = 0; c < C; c++) U[(plane * C + c) * HW + pix] = make_float2(accX[c].x, accY[c].x);
-        Tsave[plane * HW + pix] = T2.x;
-        lastsave[plane * HW + pix] = last0;
-        if (Tout) Tout[plane * HW + pix] = T2.x;
-        if (ncout) ncout[plane * HW + pix] = nc0;
-    }
-    if (in1) {
-        const size_t pix = (size_t)py1 * a.W + px;
+    for (int q = 0; q < 4; q++) {
+        if (!in[q]) continue;
+        const size_t pix = (size_t)(py + 2 * q) * a.W + px;
+        const float T = q == 0 ? TA.x : q == 1 ? TA.y : q == 2 ? TB.x : TB.y;
 #pragma unroll
-        for (int c = 0; c < C; c++) U[(plane * C + c) * HW + pix] = make_float2(accX[c].y, accY[c].y);
-        Tsave[plane * HW + pix] = T2.y;
-        lastsave[plane * HW + pix] = last1;
-        if (Tout) Tout[plane * HW + pix] = T2.y;
-        if (ncout) ncout[plane * HW + pix] = nc1;
+        for (int c = 0; c < C; c++) {
+            const float2 vv = q == 0 ? make_float2(aAX[c].x, aAY[c].x)
+                            : q == 1 ? make_float2(aAX[c].y, aAY[c].y)
+                            : q == 2 ? make_float2(aBX[c].x, aBY[c].x)
+                                     : make_float2(aBX[c].y, aBY[c].y);
+            U[(plane * C + c) * HW + pix] = vv;
+        }
+        Tsave[plane * HW + pix] = T;
+        lastsave[plane * HW + pix] = last[q];
+        if (Tout) Tout[plane * HW + pix] = T;
+        if (ncout) ncout[plane * HW + pix] = nc[q];
     }
+}
+
+// Adjoint step of a pixel pair (c0/c1: the pixels that took this step in the
+// forward) walking back-to-front (Sec. 4.2): T_k = T_{k+1} / (1 - alpha_k);
+// dU/dalpha_k = w T_k - S_k / (1 - alpha_k), S_k = sum_{m>k} w alpha T.
+// Adds the pair's dL/d(mu 0-1, conic 2-4, o 5, w 6..) to gl.
+template <int C>
+__device__ __forceinline__ void bwd_pair(const float4* rec, float dx, float2 dy2, float2 G2, float2 og2, float2 a2,
+                                         bool c0, bool c1, float amax, float2& T2, float2 (&SX)[C],
+                                         float2 (&SY)[C], const float2 (&gX)[C], const float2 (&gY)[C],
+                                         float (&gl)[16]) {
+    const float4 r0 = rec[0], r1 = rec[1];
+    const float2 al = make_float2(c0 ? a2.x : 0.f, c1 ? a2.y : 0.f);
+    const float2 om = __fadd2_rn(f2(1.f), make_float2(-al.x, -al.y));
+    const float2 iom = make_float2(__frcp_rn(om.x), __frcp_rn(om.y));
+    const float2 Tk = __fmul2_rn(T2, iom);
+    const float2 aT = __fmul2_rn(al, Tk);
+    float2 dLda = f2(0.f);
+#pragma unroll
+    for (int c = 0; c < C; c++) {
+        const float2 w = RecW<C>::get(rec, c);
+        const float2 ux = __ffma2_rn(make_float2(-SX[c].x, -SX[c].y), iom, __fmul2_rn(f2(w.x), Tk));
+        const float2 uy = __ffma2_rn(make_float2(-SY[c].x, -SY[c].y), iom, __fmul2_rn(f2(w.y), Tk));
+        dLda = __ffma2_rn(gX[c], ux, __ffma2_rn(gY[c], uy, dLda));
+        SX[c] = __ffma2_rn(f2(w.x), aT, SX[c]);
+        SY[c] = __ffma2_rn(f2(w.y), aT, SY[c]);
+        const float2 gwx = __fmul2_rn(gX[c], aT), gwy = __fmul2_rn(gY[c], aT);
+        gl[6 + 2 * c] += gwx.x + gwx.y;
+        gl[7 + 2 * c] += gwy.x + gwy.y;
+    }
+    T2 = Tk;
+    // a clamped alpha (o G > alpha_max) is flat in o G
+    const float2 dLa = make_float2(c0 && og2.x <= amax ? dLda.x : 0.f, c1 && og2.y <= amax ? dLda.y : 0.f);
+    const float2 dLdp = __fmul2_rn(make_float2(-dLa.x, -dLa.y), og2);  // dL/dpower
+    const float2 go = __fmul2_rn(dLa, G2);
+    gl[5] += go.x + go.y;
+    const float adx = __fmul_rn(r0.z, dx), bdx = __fmul_rn(r0.w, dx);
+    const float2 q0 = __ffma2_rn(f2(r0.w), dy2, f2(adx));  // A dx + B dy
+    const float2 q1 = __ffma2_rn(f2(r1.x), dy2, f2(bdx));  // B dx + C dy
+    const float2 m0 = __fmul2_rn(dLdp, q0), m1 = __fmul2_rn(dLdp, q1);
+    gl[0] -= m0.x + m0.y;
+    gl[1] -= m1.x + m1.y;
+    const float2 pdy = __fmul2_rn(dLdp, dy2);
+    gl[2] += 0.5f * dx * dx * (dLdp.x + dLdp.y);
+    gl[3] += dx * (pdy.x + pdy.y);
+    gl[4] += 0.5f * (pdy.x * dy2.x + pdy.y * dy2.y);
 }
 
 template <int C>
@@ -280,52 +353,49 @@ __global__ void __launch_bounds__(RT) k_raster_bwd(RasterArgs a, const float* __
     __shared__ float gacc[RT][16];
     __shared__ int gany[RT];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int tile = blockIdx.x, l = blockIdx.y, v = blockIdx.z;
-    const int tx = tile % a.tilesX, ty = tile / a.tilesX;
+    const int reg = blockIdx.x, l = blockIdx.y, v = blockIdx.z;
+    const int tx = reg % a.tilesX, ty = 2 * (reg / a.tilesX);
     const int px = tx * TILE + (lane & 15);
-    const int py0 = ty * TILE + 4 * warp + (lane >> 4), py1 = py0 + 2;
-    const bool in0 = px < a.W && py0 < a.H, in1 = px < a.W && py1 < a.H;
-    const float sx0 = (float)(tx * TILE), sy0 = (float)(ty * TILE + 4 * warp);
+    const int py = ty * TILE + 8 * warp + (lane >> 4);
+    const float sx0 = (float)(tx * TILE), sy0 = (float)(ty * TILE + 8 * warp);
     const uint32_t gb = ((uint32_t)(v * a.L + l) * a.ctY + ty / COARSE) * a.ctX + tx / COARSE;
     const uint32_t beg = a.off[gb];
     const size_t vN = (size_t)v * a.N;
     const size_t plane = (size_t)v * a.L + l;
     const size_t HW = (size_t)a.H * a.W;
     const float fpx = (float)px;
-    const float2 py2 = make_float2((float)py0, (float)py1);
-    float2 T2 = f2(1.f);
-    uint32_t last0 = 0, last1 = 0;
-    float2 gX[C], gY[C], SX[C], SY[C];  // (pixel 0, pixel 1) pairs
+    const float2 pyA = make_float2((float)py, (float)(py + 2)), pyB = make_float2((float)(py + 4), (float)(py + 6));
+    float Tq[4] = {1.f, 1.f, 1.f, 1.f};
+    uint32_t last[4] = {0, 0, 0, 0};
+    float2 gq[4][C];
 #pragma unroll
-    for (int c = 0; c < C; c++) gX[c] = gY[c] = SX[c] = SY[c] = f2(0.f);
-    if (in0) {
-        const size_t pix = (size_t)py0 * a.W + px;
-        T2.x = Tsave[plane * HW + pix];
-        last0 = lastsave[plane * HW + pix];
+    for (int q = 0; q < 4; q++) {
 #pragma unroll
-        for (int c = 0; c < C; c++) {
-            const float2 gg = gU[(plane * C + c) * HW + pix];
-            gX[c].x = gg.x;
-            gY[c].x = gg.y;
+        for (int c = 0; c < C; c++) gq[q][c] = make_float2(0.f, 0.f);
+        if (px < a.W && py + 2 * q < a.H) {
+            const size_t pix = (size_t)(py + 2 * q) * a.W + px;
+            Tq[q] = Tsave[plane * HW + pix];
+            last[q] = lastsave[plane * HW + pix];
+#pragma unroll
+            for (int c = 0; c < C; c++) gq[q][c] = gU[(plane * C + c) * HW + pix];
         }
     }
-    if (in1) {
-        const size_t pix = (size_t)py1 * a.W + px;
-        T2.y = Tsave[plane * HW + pix];
-        last1 = lastsave[plane * HW + pix];
+    float2 TA = make_float2(Tq[0], Tq[1]), TB = make_float2(Tq[2], Tq[3]);
+    float2 gAX[C], gAY[C], gBX[C], gBY[C], SAX[C], SAY[C], SBX[C], SBY[C];
 #pragma unroll
-        for (int c = 0; c < C; c++) {
-            const float2 gg = gU[(plane * C + c) * HW + pix];
-            gX[c].y = gg.x;
-            gY[c].y = gg.y;
-        }
+    for (int c = 0; c < C; c++) {
+        gAX[c] = make_float2(gq[0][c].x, gq[1][c].x);
+        gAY[c] = make_float2(gq[0][c].y, gq[1][c].y);
+        gBX[c] = make_float2(gq[2][c].x, gq[3][c].x);
+        gBY[c] = make_float2(gq[2][c].y, gq[3][c].y);
+        SAX[c] = SAY[c] = SBX[c] = SBY[c] = f2(0.f);
     }
     if (t == 0) smax = 0;
 #pragma unroll
     for (int e = 0; e < 16; e++) gacc[t][e] = 0.f;
     gany[t] = 0;
     __syncthreads();
-    const uint32_t lmax = max(last0, last1);
+    const uint32_t lmax = max(max(last[0], last[1]), max(last[2], last[3]));
     if (lmax) atomicMax(&smax, lmax);
     __syncthreads();
     const uint32_t maxlast = smax;
@@ -350,52 +420,23 @@ __global__ void __launch_bounds__(RT) k_raster_bwd(RasterArgs a, const float* __
 #pragma unroll
                 for (int e = 0; e < 16; e++) gl[e] = 0.f;
                 bool contrib = false;
-                if (pos < last0 || pos < last1) {
-                    const float4 r0 = srec[k][0], r1 = srec[k][1];
-                    float dx;
-                    float2 dy2, G2, og2, a2;
-                    eval_pair(fpx, py2, r0, r1.x, r1.y, a.amax, dx, dy2, G2, og2, a2);
-                    const bool c0 = pos < last0 && a2.x >= a.amin, c1 = pos < last1 && a2.y >= a.amin;
+                const float4 r0 = srec[k][0], r1 = srec[k][1];
+                float dx;
+                float2 dy2, G2, og2, a2;
+                if (pos < last[0] || pos < last[1]) {
+                    eval_pair(fpx, pyA, r0, r1.x, r1.y, a.amax, dx, dy2, G2, og2, a2);
+                    const bool c0 = pos < last[0] && a2.x >= a.amin, c1 = pos < last[1] && a2.y >= a.amin;
                     if (c0 || c1) {
                         contrib = true;
-                        // back-to-front step (Sec. 4.2): T_k = T_{k+1} / (1 - alpha_k);
-                        // dU/dalpha_k = w T_k - S_k / (1 - alpha_k), S_k = sum_{m>k} w alpha T
-                        const float2 al = make_float2(c0 ? a2.x : 0.f, c1 ? a2.y : 0.f);
-                        const float2 om = __fadd2_rn(f2(1.f), make_float2(-al.x, -al.y));
-                        const float2 iom = make_float2(__frcp_rn(om.x), __frcp_rn(om.y));
-                        const float2 Tk = __fmul2_rn(T2, iom);
-                        const float2 aT = __fmul2_rn(al, Tk);
-                        float2 dLda = f2(0.f);
-#pragma unroll
-                        for (int c = 0; c < C; c++) {
-                            const float2 w = RecW<C>::get(srec[k], c);
-                            const float2 ux = __ffma2_rn(make_float2(-SX[c].x, -SX[c].y), iom, __fmul2_rn(f2(w.x), Tk));
-                            const float2 uy = __ffma2_rn(make_float2(-SY[c].x, -SY[c].y), iom, __fmul2_rn(f2(w.y), Tk));
-                            dLda = __ffma2_rn(gX[c], ux, __ffma2_rn(gY[c], uy, dLda));
-                            SX[c] = __ffma2_rn(f2(w.x), aT, SX[c]);
-                            SY[c] = __ffma2_rn(f2(w.y), aT, SY[c]);
-                            const float2 gwx = __fmul2_rn(gX[c], aT), gwy = __fmul2_rn(gY[c], aT);
-                            gl[6 + 2 * c] = gwx.x + gwx.y;
-                            gl[7 + 2 * c] = gwy.x + gwy.y;
-                        }
-                        T2 = Tk;
-                        // a clamped alpha (o G > alpha_max) is flat in o G
-                        const float2 dLa = make_float2(c0 && og2.x <= a.amax ? dLda.x : 0.f,
-                                                       c1 && og2.y <= a.amax ? dLda.y : 0.f);
-                        const float2 dLdp = __fmul2_rn(make_float2(-dLa.x, -dLa.y), og2);  // dL/dpower
-                        const float2 go = __fmul2_rn(dLa, G2);
-                        gl[5] = go.x + go.y;
-                        const float adx = __fmul_rn(r0.z, dx), bdx = __fmul_rn(r0.w, dx);
-                        const float2 q0 = __ffma2_rn(f2(r0.w), dy2, f2(adx));   // A dx + B dy
-                        const float2 q1 = __ffma2_rn(f2(r1.x), dy2, f2(bdx));   // B dx + C dy
-                        const float2 m0 = __fmul2_rn(dLdp, q0), m1 = __fmul2_rn(dLdp, q1);
-                        gl[0] = -(m0.x + m0.y);
-                        gl[1] = -(m1.x + m1.y);
-                        const float sp = dLdp.x + dLdp.y;
-                        const float2 pdy = __fmul2_rn(dLdp, dy2);
-                        gl[2] = 0.5f * dx * dx * sp;
-                        gl[3] = dx * (pdy.x + pdy.y);
-                        gl[4] = 0.5f * (pdy.x * dy2.x + pdy.y * dy2.y);
+                        bwd_pair<C>(srec[k], dx, dy2, G2, og2, a2, c0, c1, a.amax, TA, SAX, SAY, gAX, gAY, gl);
+                    }
+                }
+                if (pos < last[2] || pos < last[3]) {
+                    eval_pair(fpx, pyB, r0, r1.x, r1.y, a.amax, dx, dy2, G2, og2, a2);
+                    const bool c2 = pos < last[2] && a2.x >= a.amin, c3 = pos < last[3] && a2.y >= a.amin;
+                    if (c2 || c3) {
+                        contrib = true;
+                        bwd_pair<C>(srec[k], dx, dy2, G2, og2, a2, c2, c3, a.amax, TB, SBX, SBY, gBX, gBY, gl);
                     }
                 }
                 if (__any_sync(0xffffffffu, contrib)) {
@@ -425,7 +466,7 @@ hcgs_status raster_forward(hcgs_ctx* ctx, hcgs_saved* s, float2* U, float* T_out
     HCGS_CUDA(ctx, grow(ctx, s->Tfin, pl * sizeof(float), &s->bytes));
     HCGS_CUDA(ctx, grow(ctx, s->last, pl * sizeof(uint32_t), &s->bytes));
     RasterArgs a = make_raster_args(s);
-    dim3 grid(s->tilesX * s->tilesY, s->L, s->V);
+    dim3 grid(s->tilesX * ((s->tilesY + 1) / 2), s->L, s->V);  // 16 x 32 pixel regions
     float* Ts = (float*)s->Tfin.p;
     uint32_t* ls = (uint32_t*)s->last.p;
     switch (s->C) {
@@ -443,7 +484,7 @@ hcgs_status raster_backward(hcgs_ctx* ctx, hcgs_saved* s, const float2* gU, cuda
     HCGS_CUDA(ctx, grow(ctx, s->g2d, ng * sizeof(float), &s->bytes));
     HCGS_CUDA(ctx, cudaMemsetAsync(s->g2d.p, 0, ng * sizeof(float), st));
     RasterArgs a = make_raster_args(s);
-    dim3 grid(s->tilesX * s->tilesY, s->L, s->V);
+    dim3 grid(s->tilesX * ((s->tilesY + 1) / 2), s->L, s->V);  // 16 x 32 pixel regions
     const float* Ts = (const float*)s->Tfin.p;
     const uint32_t* ls = (const uint32_t*)s->last.p;
     float* g2 = (float*)s->g2d.p;
