@@ -5,16 +5,15 @@
 // One CTA of 128 threads per (16 x 32 pixel region = two vertically adjacent
 // 16x16 tiles, plane, view); four pixels per thread (one column, rows r,
 // r + 2, r + 4, r + 6 of the warp's 16 x 8 strip), evaluated as two packed
-// FP32x2 pairs.  Both tiles lie in the same 64x64 bucket: the CTA streams
-// the bucket's list (already in visiting order) once, keeps the entries whose
-// tile rectangle covers either tile (warp ballot compaction keeps the order)
-// and stages their records in shared memory.  Each warp tests 32 staged
-// entries at a time against its strip (exact superset test), and for every
-// hit each of its pixels takes the step of Algorithm 2: alpha = min(alpha_max,
-// o exp(-power)); skip when alpha < alpha_min; U += w alpha T; T *= 1 - alpha;
-// stop once T < T_eps.  The record load, the loop control and (in the
-// adjoint) the per-entry warp reduction are shared by the four pixels.
-// The CTA leaves the list when all its pixels have stopped.
+// FP32x2 pairs.  Both tiles lie in the same 64x64 bucket.  The four warps
+// are independent (no block barrier): each streams the bucket's list (in
+// visiting order) 32 entries at a time, keeps the entries whose tile
+// rectangle covers its tile and whose footprint can reach its 16 x 8 strip
+// (exact superset test), compacts them in order into its own shared-memory
+// slots (warp ballot), and every pixel of the warp takes the step of
+// Algorithm 2 for each of them: alpha = min(alpha_max, o exp(-power)); skip
+// when alpha < alpha_min; U += w alpha T; T *= 1 - alpha; stop once T < T_eps.
+// A warp leaves the list as soon as its own pixels have all stopped.
 //
 // The alpha arithmetic uses explicitly rounded intrinsics so that the forward
 // and backward kernels take identical skip/stop decisions.
@@ -67,45 +66,6 @@ struct RecW {
 constexpr int RT = 128;            // threads per CTA
 constexpr int RWARPS = RT / 32;
 
-// Stream one batch (positions [lo, hi) of the bucket) and compact the entries
-// that touch tile (tx, ty) into shared memory, keeping their order.
-template <int NR>
-__device__ __forceinline__ int stage_batch(const RasterArgs& a, size_t vN, uint32_t beg, uint32_t lo, uint32_t hi,
-                                           int tx, int ty, float4 (*srec)[NR], uint32_t* spos, uint32_t* sid,
-                                           int* wcnt) {
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const uint32_t p = lo + (uint32_t)t;
-    bool ok = false;
-    uint32_t s = 0;
-    if (p < hi) {
-        s = a.list[beg + p];
-        const uint2 rc = a.rects[vN + s];
-        // tile column tx, tile rows ty and ty + 1
-        ok = (uint32_t)tx >= (rc.x & 0xFFFFu) && (uint32_t)tx < (rc.x >> 16) && (rc.y & 0xFFFFu) < (uint32_t)ty + 2u &&
-             (rc.y >> 16) > (uint32_t)ty;
-    }
-    const unsigned bal = __ballot_sync(0xffffffffu, ok);
-    if (lane == 0) wcnt[warp] = __popc(bal);
-    __syncthreads();
-    int base = 0, total = 0;
-#pragma unroll
-    for (int w = 0; w < RWARPS; w++) {
-        const int c = wcnt[w];
-        base += w < warp ? c : 0;
-        total += c;
-    }
-    if (ok) {
-        const int slot = base + __popc(bal & ((1u << lane) - 1u));
-        spos[slot] = p;
-        sid[slot] = s;
-        const float4* r = a.rec + (vN + s) * NR;
-#pragma unroll
-        for (int k = 0; k < NR; k++) srec[slot][k] = r[k];
-    }
-    __syncthreads();
-    return total;
-}
-
 // Can Gaussian (mu, conic A B C, opacity o) reach alpha >= alpha_min at any
 // pixel centre of the strip x in [x0, x0 + 15], y in [y0, y0 + 7]?  For each
 // row the footprint quadratic q = A dx^2 + 2 B dx dy + C dy^2 is minimised
@@ -129,6 +89,46 @@ __device__ __forceinline__ bool strip_hits(float4 r0, float Cc, float o, float x
         hit |= q <= k2;
     }
     return hit;
+}
+
+// Stream 32 list positions [p0, p0 + 32) of the bucket for one warp: keep the
+// entries whose rectangle covers tile (tx, ty) and whose footprint can reach
+// the warp's strip, and compact them, in list order, into the warp's slots.
+// Returns the number kept.
+template <int NR>
+__device__ __forceinline__ int stage_warp(const RasterArgs& a, size_t vN, uint32_t beg, uint32_t p0, uint32_t n,
+                                          int tx, int ty, float sx0, float sy0, float4 (*wrec)[NR],
+                                          uint32_t* wpos, uint32_t* wid) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t p = p0 + (uint32_t)lane;
+    bool ok = false;
+    uint32_t s = 0;
+    float4 q0, q1;
+    if (p < n) {
+        s = a.list[beg + p];
+        const uint2 rc = a.rects[vN + s];
+        ok = (uint32_t)tx >= (rc.x & 0xFFFFu) && (uint32_t)tx < (rc.x >> 16) && (uint32_t)ty >= (rc.y & 0xFFFFu) &&
+             (uint32_t)ty < (rc.y >> 16);
+        if (ok) {
+            const float4* r = a.rec + (vN + s) * NR;
+            q0 = r[0];
+            q1 = r[1];
+            ok = strip_hits(q0, q1.x, q1.y, sx0, sy0, a.amin);
+        }
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, ok);
+    if (ok) {
+        const int slot = __popc(m & ((1u << lane) - 1u));
+        const float4* r = a.rec + (vN + s) * NR;
+        wrec[slot][0] = q0;
+        wrec[slot][1] = q1;
+#pragma unroll
+        for (int k = 2; k < NR; k++) wrec[slot][k] = r[k];
+        wpos[slot] = p;
+        wid[slot] = s;
+    }
+    __syncwarp();
+    return __popc(m);
 }
 
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -197,27 +197,25 @@ __device__ __forceinline__ void book(bool c, float T, float teps, uint32_t pos, 
 }
 
 template <int C>
-__global__ void __launch_bounds__(RT) k_raster_fwd(RasterArgs a, float2* __restrict__ U, float* __restrict__ Tsave,
+__global__ void __launch_bounds__(RT, 6) k_raster_fwd(RasterArgs a, float2* __restrict__ U, float* __restrict__ Tsave,
                                                    uint32_t* __restrict__ lastsave, float* __restrict__ Tout,
                                                    int32_t* __restrict__ ncout) {
     constexpr int NR = C <= 1 ? 2 : (C <= 3 ? 3 : 4);
-    __shared__ float4 srec[RT][NR];
-    __shared__ uint32_t spos[RT], sid[RT];
-    __shared__ int wcnt[RWARPS];
+    __shared__ float4 srec[RWARPS][32][NR];
+    __shared__ uint32_t spos[RWARPS][32], sid[RWARPS][32];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int ry = (a.tilesY + 1) / 2;
     const int reg = blockIdx.x, l = blockIdx.y, v = blockIdx.z;
-    const int tx = reg % a.tilesX, ty = 2 * (reg / a.tilesX);  // tiles (tx, ty) and (tx, ty + 1)
-    (void)ry;
+    const int tx = reg % a.tilesX, ty = 2 * (reg / a.tilesX) + (warp >> 1);  // this warp's tile
     const int px = tx * TILE + (lane & 15);
-    const int py = ty * TILE + 8 * warp + (lane >> 4);  // rows py, py + 2, py + 4, py + 6
+    const int sy = ty * TILE + 8 * (warp & 1);       // this warp's 16 x 8 strip starts at row sy
+    const int py = sy + (lane >> 4);                 // rows py, py + 2, py + 4, py + 6
     bool in[4], d[4];
 #pragma unroll
     for (int q = 0; q < 4; q++) {
         in[q] = px < a.W && py + 2 * q < a.H;
         d[q] = !in[q];
     }
-    const float sx0 = (float)(tx * TILE), sy0 = (float)(ty * TILE + 8 * warp);  // this warp's strip
+    const float sx0 = (float)(tx * TILE), sy0 = (float)sy;
     const uint32_t gb = ((uint32_t)(v * a.L + l) * a.ctY + ty / COARSE) * a.ctX + tx / COARSE;
     const uint32_t beg = a.off[gb], n = a.off[gb + 1] - beg;
     const size_t vN = (size_t)v * a.N;
@@ -229,46 +227,31 @@ __global__ void __launch_bounds__(RT) k_raster_fwd(RasterArgs a, float2* __restr
     for (int c = 0; c < C; c++) aAX[c] = aAY[c] = aBX[c] = aBY[c] = f2(0.f);
     uint32_t last[4] = {0, 0, 0, 0};
     int nc[4] = {0, 0, 0, 0};
-    for (uint32_t lo = 0; lo < n; lo += RT) {
-        if (__syncthreads_count(!(d[0] && d[1] && d[2] && d[3])) == 0) break;
-        const uint32_t hi = min(n, lo + (uint32_t)RT);
-        const int total = stage_batch<NR>(a, vN, beg, lo, hi, tx, ty, srec, spos, sid, wcnt);
-        for (int k0 = 0; k0 < total; k0 += 32) {
-            if (__all_sync(0xffffffffu, d[0] && d[1] && d[2] && d[3])) break;
-            bool hit = false;
-            if (k0 + lane < total) {
-                const float4 q0 = srec[k0 + lane][0], q1 = srec[k0 + lane][1];
-                hit = strip_hits(q0, q1.x, q1.y, sx0, sy0, a.amin);
+    for (uint32_t p0 = 0; p0 < n; p0 += 32) {
+        if (__all_sync(0xffffffffu, d[0] && d[1] && d[2] && d[3])) break;
+        const int nh = stage_warp<NR>(a, vN, beg, p0, n, tx, ty, sx0, sy0, srec[warp], spos[warp], sid[warp]);
+        for (int k = 0; k < nh; k++) {
+            const float4* rec = srec[warp][k];
+            const float4 r0 = rec[0], r1 = rec[1];
+            const uint32_t pos = spos[warp][k];
+            float dxA, dxB;
+            float2 dyA, GA, ogA, aA, dyB, GB, ogB, aB;
+            eval_pair(fpx, pyA, r0, r1.x, r1.y, a.amax, dxA, dyA, GA, ogA, aA);
+            eval_pair(fpx, pyB, r0, r1.x, r1.y, a.amax, dxB, dyB, GB, ogB, aB);
+            const bool c0 = !d[0] && aA.x >= a.amin, c1 = !d[1] && aA.y >= a.amin;
+            const bool c2 = !d[2] && aB.x >= a.amin, c3 = !d[3] && aB.y >= a.amin;
+            if (c0 || c1) {
+                fwd_pair<C>(rec, aA, c0, c1, TA, aAX, aAY);
+                book(c0, TA.x, a.teps, pos, nc[0], last[0], d[0]);
+                book(c1, TA.y, a.teps, pos, nc[1], last[1], d[1]);
             }
-            unsigned m = __ballot_sync(0xffffffffu, hit);
-            while (m) {
-                const int k = k0 + __ffs(m) - 1;
-                m &= m - 1;
-                if (d[0] && d[1] && d[2] && d[3]) continue;
-                const float4 r0 = srec[k][0], r1 = srec[k][1];
-                const uint32_t pos = spos[k];
-                float dx;
-                float2 dy2, G2, og2, a2;
-                if (!(d[0] && d[1])) {
-                    eval_pair(fpx, pyA, r0, r1.x, r1.y, a.amax, dx, dy2, G2, og2, a2);
-                    const bool c0 = !d[0] && a2.x >= a.amin, c1 = !d[1] && a2.y >= a.amin;
-                    if (c0 || c1) {
-                        fwd_pair<C>(srec[k], a2, c0, c1, TA, aAX, aAY);
-                        book(c0, TA.x, a.teps, pos, nc[0], last[0], d[0]);
-                        book(c1, TA.y, a.teps, pos, nc[1], last[1], d[1]);
-                    }
-                }
-                if (!(d[2] && d[3])) {
-                    eval_pair(fpx, pyB, r0, r1.x, r1.y, a.amax, dx, dy2, G2, og2, a2);
-                    const bool c2 = !d[2] && a2.x >= a.amin, c3 = !d[3] && a2.y >= a.amin;
-                    if (c2 || c3) {
-                        fwd_pair<C>(srec[k], a2, c2, c3, TB, aBX, aBY);
-                        book(c2, TB.x, a.teps, pos, nc[2], last[2], d[2]);
-                        book(c3, TB.y, a.teps, pos, nc[3], last[3], d[3]);
-                    }
-                }
+            if (c2 || c3) {
+                fwd_pair<C>(rec, aB, c2, c3, TB, aBX, aBY);
+                book(c2, TB.x, a.teps, pos, nc[2], last[2], d[2]);
+                book(c3, TB.y, a.teps, pos, nc[3], last[3], d[3]);
             }
         }
+        __syncwarp();
     }
     const size_t plane = (size_t)v * a.L + l;
     const size_t HW = (size_t)a.H * a.W;
@@ -339,25 +322,20 @@ __device__ __forceinline__ void bwd_pair(const float4* rec, float dx, float2 dy2
 }
 
 template <int C>
-__global__ void __launch_bounds__(RT) k_raster_bwd(RasterArgs a, const float* __restrict__ Tsave,
+__global__ void __launch_bounds__(RT, 4) k_raster_bwd(RasterArgs a, const float* __restrict__ Tsave,
                                                    const uint32_t* __restrict__ lastsave,
                                                    const float2* __restrict__ gU, float* __restrict__ g2d) {
     constexpr int NR = C <= 1 ? 2 : (C <= 3 ? 3 : 4);
     constexpr int G = 6 + 2 * C;
-    __shared__ float4 srec[RT][NR];
-    __shared__ uint32_t spos[RT], sid[RT];
-    __shared__ int wcnt[RWARPS];
-    __shared__ uint32_t smax;
-    // per staged entry: the CTA's sum of its warps' gradient contributions,
-    // flushed to global memory once per batch (one atomic per value)
-    __shared__ float gacc[RT][16];
-    __shared__ int gany[RT];
+    __shared__ float4 srec[RWARPS][32][NR];
+    __shared__ uint32_t spos[RWARPS][32], sid[RWARPS][32];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int reg = blockIdx.x, l = blockIdx.y, v = blockIdx.z;
-    const int tx = reg % a.tilesX, ty = 2 * (reg / a.tilesX);
+    const int tx = reg % a.tilesX, ty = 2 * (reg / a.tilesX) + (warp >> 1);
     const int px = tx * TILE + (lane & 15);
-    const int py = ty * TILE + 8 * warp + (lane >> 4);
-    const float sx0 = (float)(tx * TILE), sy0 = (float)(ty * TILE + 8 * warp);
+    const int sy = ty * TILE + 8 * (warp & 1);
+    const int py = sy + (lane >> 4);
+    const float sx0 = (float)(tx * TILE), sy0 = (float)sy;
     const uint32_t gb = ((uint32_t)(v * a.L + l) * a.ctY + ty / COARSE) * a.ctX + tx / COARSE;
     const uint32_t beg = a.off[gb];
     const size_t vN = (size_t)v * a.N;
@@ -390,72 +368,34 @@ __global__ void __launch_bounds__(RT) k_raster_bwd(RasterArgs a, const float* __
         gBY[c] = make_float2(gq[2][c].y, gq[3][c].y);
         SAX[c] = SAY[c] = SBX[c] = SBY[c] = f2(0.f);
     }
-    if (t == 0) smax = 0;
+    uint32_t maxlast = max(max(last[0], last[1]), max(last[2], last[3]));
 #pragma unroll
-    for (int e = 0; e < 16; e++) gacc[t][e] = 0.f;
-    gany[t] = 0;
-    __syncthreads();
-    const uint32_t lmax = max(max(last[0], last[1]), max(last[2], last[3]));
-    if (lmax) atomicMax(&smax, lmax);
-    __syncthreads();
-    const uint32_t maxlast = smax;
+    for (int o = 16; o > 0; o >>= 1) maxlast = max(maxlast, __shfl_xor_sync(0xffffffffu, maxlast, o));
     for (uint32_t hi = maxlast; hi > 0;) {
-        const uint32_t lo = hi > (uint32_t)RT ? hi - RT : 0u;
-        __syncthreads();  // previous batch fully consumed
-        const int total = stage_batch<NR>(a, vN, beg, lo, hi, tx, ty, srec, spos, sid, wcnt);
-        for (int k1 = total; k1 > 0; k1 -= 32) {
-            const int k0 = k1 > 32 ? k1 - 32 : 0;
-            bool hit = false;
-            if (k0 + lane < k1) {
-                const float4 q0 = srec[k0 + lane][0], q1 = srec[k0 + lane][1];
-                hit = strip_hits(q0, q1.x, q1.y, sx0, sy0, a.amin);
-            }
-            unsigned m = __ballot_sync(0xffffffffu, hit);
-            while (m) {  // highest bit first: back-to-front over the visiting order
-                const int b = 31 - __clz(m);
-                m &= ~(1u << b);
-                const int k = k0 + b;
-                const uint32_t pos = spos[k];
-                float gl[16];
+        const uint32_t lo = hi > 32u ? hi - 32u : 0u;
+        const int nh = stage_warp<NR>(a, vN, beg, lo, hi, tx, ty, sx0, sy0, srec[warp], spos[warp], sid[warp]);
+        for (int k = nh - 1; k >= 0; k--) {  // back-to-front over the visiting order
+            const float4* rec = srec[warp][k];
+            const uint32_t pos = spos[warp][k];
+            float gl[16];
 #pragma unroll
-                for (int e = 0; e < 16; e++) gl[e] = 0.f;
-                bool contrib = false;
-                const float4 r0 = srec[k][0], r1 = srec[k][1];
-                float dx;
-                float2 dy2, G2, og2, a2;
-                if (pos < last[0] || pos < last[1]) {
-                    eval_pair(fpx, pyA, r0, r1.x, r1.y, a.amax, dx, dy2, G2, og2, a2);
-                    const bool c0 = pos < last[0] && a2.x >= a.amin, c1 = pos < last[1] && a2.y >= a.amin;
-                    if (c0 || c1) {
-                        contrib = true;
-                        bwd_pair<C>(srec[k], dx, dy2, G2, og2, a2, c0, c1, a.amax, TA, SAX, SAY, gAX, gAY, gl);
-                    }
-                }
-                if (pos < last[2] || pos < last[3]) {
-                    eval_pair(fpx, pyB, r0, r1.x, r1.y, a.amax, dx, dy2, G2, og2, a2);
-                    const bool c2 = pos < last[2] && a2.x >= a.amin, c3 = pos < last[3] && a2.y >= a.amin;
-                    if (c2 || c3) {
-                        contrib = true;
-                        bwd_pair<C>(srec[k], dx, dy2, G2, og2, a2, c2, c3, a.amax, TB, SBX, SBY, gBX, gBY, gl);
-                    }
-                }
-                if (__any_sync(0xffffffffu, contrib)) {
-                    const float sum = warp_reduce_scatter16(gl, lane);
-                    const int idx = lane >> 1;
-                    if (!(lane & 1) && idx < G) atomicAdd(&gacc[k][idx], sum);
-                    if (lane == 0) gany[k] = 1;
-                }
+            for (int e = 0; e < 16; e++) gl[e] = 0.f;
+            const float4 r0 = rec[0], r1 = rec[1];
+            float dxA, dxB;
+            float2 dyA, GA, ogA, aA, dyB, GB, ogB, aB;
+            eval_pair(fpx, pyA, r0, r1.x, r1.y, a.amax, dxA, dyA, GA, ogA, aA);
+            eval_pair(fpx, pyB, r0, r1.x, r1.y, a.amax, dxB, dyB, GB, ogB, aB);
+            const bool c0 = pos < last[0] && aA.x >= a.amin, c1 = pos < last[1] && aA.y >= a.amin;
+            const bool c2 = pos < last[2] && aB.x >= a.amin, c3 = pos < last[3] && aB.y >= a.amin;
+            if (c0 || c1) bwd_pair<C>(rec, dxA, dyA, GA, ogA, aA, c0, c1, a.amax, TA, SAX, SAY, gAX, gAY, gl);
+            if (c2 || c3) bwd_pair<C>(rec, dxB, dyB, GB, ogB, aB, c2, c3, a.amax, TB, SBX, SBY, gBX, gBY, gl);
+            if (__any_sync(0xffffffffu, c0 || c1 || c2 || c3)) {
+                const float sum = warp_reduce_scatter16(gl, lane);
+                const int idx = lane >> 1;
+                if (!(lane & 1) && idx < G) atomicAdd(g2d + (vN + sid[warp][k]) * G + idx, sum);
             }
         }
-        __syncthreads();
-        if (t < total && gany[t]) {
-            float* dst = g2d + (vN + sid[t]) * G;
-#pragma unroll
-            for (int e = 0; e < G; e++) atomicAdd(dst + e, gacc[t][e]);
-#pragma unroll
-            for (int e = 0; e < 16; e++) gacc[t][e] = 0.f;
-            gany[t] = 0;
-        }
+        __syncwarp();
         hi = lo;
     }
 }
