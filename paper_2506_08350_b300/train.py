@@ -1,0 +1,81 @@
+"""Optimisation step of the complex-valued holographic Gaussians on the GPU.
+
+One step (Algorithm 1 without densification; the optimiser is Adam as in the
+training configurations): render the hologram of one view (hcgs_render_view),
+inverse-propagate it to every depth plane and compare the intensities with the
+focal-stack targets (hcgs_focal_stack_loss: Eq. plane2layer_asm and
+Eq. recon_loss as a mean), run the adjoint (hcgs_render_view_backward) and
+update every parameter array with Adam (hcgs_adam_step).  All arithmetic runs
+in the library's kernels; this module only sequences the calls.
+
+Learning rates follow Sec. 5 (means and plane logits 0.01, scales 0.005,
+amplitude and phase 0.0025, opacity 0.025, rotation 0.001); a learning rate of
+0 freezes an array.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import PARAM_NAMES, Context, Saved
+
+PAPER_LR = dict(means=0.01, log_scales=0.005, quats=0.001, opacity_logits=0.025, amplitude=0.0025,
+                phase=0.0025, plane_logits=0.01)
+
+
+class HologramTrainer:
+    """Adam optimisation of the Gaussian parameters against focal stacks."""
+
+    def __init__(self, ctx: Context, params: dict, optics, opts=None, lrs=None, betas=(0.9, 0.999), eps=1e-8):
+        self.ctx = ctx
+        self.p = params
+        self.optics = optics
+        self.opts = opts
+        self.lrs = dict(PAPER_LR if lrs is None else lrs)
+        self.betas = betas
+        self.eps = eps
+        self.m = {k: torch.zeros_like(v) for k, v in params.items()}
+        self.v = {k: torch.zeros_like(v) for k, v in params.items()}
+        self.g = {k: torch.empty_like(v) for k, v in params.items()}
+        self.t = 0
+        self.saved = Saved(ctx)
+        dev = params["means"].device
+        o = optics
+        self.holo = torch.empty((1, len(o.wavelengths), o.H, o.W), dtype=torch.complex64, device=dev)
+        self.gholo = torch.empty_like(self.holo)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=dev)
+
+    def loss_only(self, viewmat, intr, I_gt):
+        """Focal-stack loss of the current parameters for one view (no update)."""
+        self.ctx.render_view(self.p, viewmat, intr, self.optics, self.opts, self.holo, None, self.saved)
+        self.ctx.focal_stack_loss(self.holo, I_gt, 1, self.optics, self.loss, None, None)
+        return self.loss
+
+    def step(self, viewmat, intr, I_gt):
+        """One optimisation step on one view; returns the loss before the update
+        (a device tensor)."""
+        self.ctx.render_view(self.p, viewmat, intr, self.optics, self.opts, self.holo, None, self.saved)
+        self.ctx.focal_stack_loss(self.holo, I_gt, 1, self.optics, self.loss, self.gholo, None)
+        self.ctx.render_view_backward(self.saved, self.p, self.gholo, self.g)
+        self.t += 1
+        for k in PARAM_NAMES:
+            lr = self.lrs.get(k, 0.0)
+            if lr > 0:
+                self.ctx.adam_step(self.p[k], self.g[k], self.m[k], self.v[k], self.t, lr, self.betas[0],
+                                   self.betas[1], self.eps)
+        return self.loss
+
+
+def focal_stack(ctx: Context, params: dict, viewmat, intr, optics, opts=None):
+    """Intensities I_l = |IDFT(H_{-Z_l} DFT(P))|^2 of the hologram of one view,
+    shape [1, L, C, H, W] (used to make targets from a teacher scene); computed
+    by the loss kernel against a zero target."""
+    o = optics
+    dev = params["means"].device
+    holo = torch.empty((1, len(o.wavelengths), o.H, o.W), dtype=torch.complex64, device=dev)
+    ctx.render_view(params, viewmat, intr, o, opts, holo)
+    shape = (1, len(o.plane_z), len(o.wavelengths), o.H, o.W)
+    I = torch.empty(shape, dtype=torch.float32, device=dev)
+    zero = torch.zeros(shape, dtype=torch.float32, device=dev)
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    ctx.focal_stack_loss(holo, zero, 1, o, loss, None, I)
+    return I

@@ -1,0 +1,76 @@
+"""GPU optimisation step (render -> focal-stack loss -> adjoint -> Adam)
+against the FP64 oracle, and a short optimisation that must reduce the loss."""
+import numpy as np
+import pytest
+
+import hcgs_synth as S
+import oracle
+from gpu_common import cams, cams_dev, dev, oracle_opts, rel
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2506_08350_b300 as P
+    return P
+
+
+def test_one_step_matches_oracle(P):
+    from paper_2506_08350_b300.train import HologramTrainer
+    ctx = P.Context(0)
+    o = S.Optics(64, 80, (639e-9, 473e-9), (0.0, 2e-3, 5e-3))
+    g = S.make_gaussians(300, o.L, o.C, o.H, o.W, seed=11, log_scale_mean=-2.8, log_scale_std=0.4)
+    vm, it = cams(1, o.H, o.W, seed=4)
+    Igt = S.random_real((1, o.L, o.C, o.H, o.W), seed=5, lo=0.0, hi=0.2)
+    gd = dev(g)
+    vmd, itd = cams_dev(vm, it)
+    tr = HologramTrainer(ctx, gd, o, dict(P.DEFAULT_OPTS))
+    loss = float(tr.step(vmd, itd, torch.from_numpy(Igt).cuda()).item())
+    torch.cuda.synchronize()
+    # oracle: same step in FP64
+    oo = oracle_opts(P.DEFAULT_OPTS)
+    Po, _, _, _ = oracle.render(g, vm.astype(np.float64), it.astype(np.float64), o, oo)
+    l_ref, gP_ref, _ = oracle.focal_stack_loss(Po[0], Igt[0].astype(np.float64), o.pitch, o.wavelengths, o.plane_z)
+    assert abs(loss - l_ref) < 1e-4 * l_ref, (loss, l_ref)
+    gref = oracle.render_backward(g, vm.astype(np.float64), it.astype(np.float64), o, gP_ref[None], oo)
+    for k in P.PARAM_NAMES:
+        e = rel(tr.g[k].cpu().numpy(), gref[k])
+        assert e < 2e-3, (k, e)
+    # Adam update of the first step from zero moments
+    from paper_2506_08350_b300.train import PAPER_LR
+    for k in P.PARAM_NAMES:
+        p_ref, _, _ = oracle.adam_step(g[k], tr.g[k].cpu().numpy(), np.zeros_like(g[k]), np.zeros_like(g[k]), 1,
+                                       PAPER_LR[k])
+        assert np.allclose(tr.p[k].cpu().numpy(), p_ref, rtol=1e-6, atol=1e-7), k
+
+
+def test_optimisation_reduces_focal_stack_loss(P):
+    # teacher scene -> focal-stack targets on a small ring of views; the
+    # student has the teacher's geometry with random phase and flat amplitude
+    from paper_2506_08350_b300.train import HologramTrainer, focal_stack
+    ctx = P.Context(0)
+    o = S.Optics(128, 128, S.WAVELENGTHS_RGB, (0.0, 3e-3, 6e-3, 9e-3))
+    teacher = S.make_gaussians(4000, o.L, o.C, o.H, o.W, seed=3, log_scale_mean=-3.5)
+    views, intr = S.view_batch(8, o.H, o.W, seed=7)
+    views = views.astype(np.float32)
+    itd = torch.from_numpy(intr[:1].astype(np.float32)).cuda()
+    td = dev(teacher)
+    targets = [focal_stack(ctx, td, torch.from_numpy(views[k:k + 1]).cuda(), itd, o) for k in range(8)]
+    student = {k: v.copy() for k, v in teacher.items()}
+    rng = np.random.default_rng(0)
+    student["phase"] = (rng.random(student["phase"].shape) * 2 * np.pi).astype(np.float32)
+    student["amplitude"][:] = 0.5
+    sd = dev(student)
+    lrs = dict(amplitude=0.01, phase=0.02)
+    tr = HologramTrainer(ctx, sd, o, dict(P.DEFAULT_OPTS), lrs=lrs)
+    vms = [torch.from_numpy(views[k:k + 1]).cuda() for k in range(8)]
+    first = np.mean([float(tr.loss_only(vms[k], itd, targets[k]).item()) for k in range(8)])
+    for s in range(240):
+        tr.step(vms[s % 8], itd, targets[s % 8])
+    last = np.mean([float(tr.loss_only(vms[k], itd, targets[k]).item()) for k in range(8)])
+    print("focal-stack loss: %.4e -> %.4e" % (first, last))
+    assert last < 0.5 * first, (first, last)
