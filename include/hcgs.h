@@ -249,6 +249,29 @@ hcgs_status hcgs_mlp_backward(hcgs_ctx* ctx, const uint16_t* x, int N, const uin
                               const float* gy, float* gW1, float* gW2, float* gW3, float* gW4,
                               float* gb1, float* gb2, float* gb3, float* gb4, void* stream);
 
+/* Training of the network (no counterpart in the paper): mean squared error
+ * of the first K (1..16) of the 16 output columns against target, both device
+ * [N][16] float; writes loss (device float[1]) and gy = dL/dy (device
+ * [N][16] float, zero in the unused columns). */
+hcgs_status hcgs_mlp_mse_loss(hcgs_ctx* ctx, const float* y, const float* target, int N, int K, float* loss,
+                              float* gy, void* stream);
+/* Rounds n device floats to bfloat16 (nearest, ties to even): the network's
+ * FP32 master weights -> the BF16 operands of hcgs_mlp_forward. */
+hcgs_status hcgs_cast_bf16(hcgs_ctx* ctx, const float* src, uint16_t* dst, int64_t n, void* stream);
+
+/* Marshalling of the network's data (no counterpart in the paper).
+ * hcgs_init_features: x device [N][16] bf16 = (mean 3, (log_scale + 4)/0.5 3,
+ *   unit quaternion 4, opacity logit 1, rgb 3, 0, 0) from g and rgb device [N][3].
+ * hcgs_init_targets: target device [N][16] float = (a_c cos phi_c, a_c sin phi_c)
+ *   for c < C, zero after, from amplitude/phase device [N][C].
+ * hcgs_init_apply: amplitude = |w_c|, phase = arg w_c from y device [N][16]. */
+hcgs_status hcgs_init_features(hcgs_ctx* ctx, const hcgs_gaussians* g, const float* rgb, uint16_t* x,
+                               void* stream);
+hcgs_status hcgs_init_targets(hcgs_ctx* ctx, const float* amplitude, const float* phase, int N, int C,
+                              float* target, void* stream);
+hcgs_status hcgs_init_apply(hcgs_ctx* ctx, const float* y, int N, int C, float* amplitude, float* phase,
+                            void* stream);
+
 /* ---------------- allocation-free inverse propagation ---------------- */
 /* The paper has no counterpart: this entry point exists for callers that
  * cannot call cudaMalloc, for example an application whose device memory is

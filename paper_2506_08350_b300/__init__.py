@@ -36,7 +36,8 @@ EXPORTS = ("hcgs_ctx_create", "hcgs_ctx_destroy", "hcgs_status_string", "hcgs_la
            "hcgs_asm_propagate", "hcgs_asm_propagate_backward", "hcgs_render_view",
            "hcgs_rasterize_planes_backward", "hcgs_project_backward", "hcgs_render_view_backward",
            "hcgs_focal_stack_loss", "hcgs_adam_step", "hcgs_mlp_forward", "hcgs_mlp_backward",
-           "hcgs_profile_enable", "hcgs_profile_summary", "hcgs_asm_propagate_noalloc")
+           "hcgs_profile_enable", "hcgs_profile_summary", "hcgs_asm_propagate_noalloc", "hcgs_mlp_mse_loss",
+           "hcgs_cast_bf16", "hcgs_init_features", "hcgs_init_targets", "hcgs_init_apply")
 
 
 class HcgsError(RuntimeError):
@@ -102,6 +103,11 @@ _sig("hcgs_focal_stack_loss", [_P, _P, _P, c_int, POINTER(_Optics), _P, _P, _P, 
 _sig("hcgs_adam_step", [_P, _P, _P, _P, _P, c_int64, c_int, c_float, c_float, c_float, c_float, _P])
 _sig("hcgs_mlp_forward", [_P, _P, c_int] + [_P] * 8 + [_P, _P])
 _sig("hcgs_asm_propagate_noalloc", [_P, c_int, POINTER(_Optics), _P, _P])
+_sig("hcgs_mlp_mse_loss", [_P, _P, _P, c_int, c_int, _P, _P, _P])
+_sig("hcgs_cast_bf16", [_P, _P, _P, c_int64, _P])
+_sig("hcgs_init_features", [_P, POINTER(_Gaussians), _P, _P, _P])
+_sig("hcgs_init_targets", [_P, _P, _P, c_int, c_int, _P, _P])
+_sig("hcgs_init_apply", [_P, _P, c_int, c_int, _P, _P, _P])
 _sig("hcgs_mlp_backward", [_P, _P, c_int] + [_P] * 8 + [_P] + [_P] * 8 + [_P])
 
 PARAM_NAMES = ("means", "log_scales", "quats", "opacity_logits", "amplitude", "phase", "plane_logits")
@@ -271,6 +277,25 @@ class Context:
     def mlp_forward(self, x, W, b, y):
         self._check(_lib.hcgs_mlp_forward(self.handle, _ptr(x), x.shape[0], *[_ptr(w) for w in W],
                                           *[_ptr(t) for t in b], _ptr(y), _stream()))
+
+    def mlp_mse_loss(self, y, target, K, loss, gy):
+        self._check(_lib.hcgs_mlp_mse_loss(self.handle, _ptr(y), _ptr(target), y.shape[0], int(K), _ptr(loss),
+                                           _ptr(gy), _stream()))
+
+    def cast_bf16(self, src, dst):
+        self._check(_lib.hcgs_cast_bf16(self.handle, _ptr(src), _ptr(dst), src.numel(), _stream()))
+
+    def init_features(self, g, rgb, x):
+        self._check(_lib.hcgs_init_features(self.handle, ctypes.byref(_gauss(g)), _ptr(rgb), _ptr(x), _stream()))
+
+    def init_targets(self, amplitude, phase, target):
+        N, C = amplitude.shape
+        self._check(_lib.hcgs_init_targets(self.handle, _ptr(amplitude), _ptr(phase), N, C, _ptr(target),
+                                           _stream()))
+
+    def init_apply(self, y, amplitude, phase):
+        N, C = amplitude.shape
+        self._check(_lib.hcgs_init_apply(self.handle, _ptr(y), N, C, _ptr(amplitude), _ptr(phase), _stream()))
 
     def mlp_backward(self, x, W, b, gy, gW, gb):
         self._check(_lib.hcgs_mlp_backward(self.handle, _ptr(x), x.shape[0], *[_ptr(w) for w in W],

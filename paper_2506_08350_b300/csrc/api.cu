@@ -514,4 +514,22 @@ hcgs_status hcgs_mlp_backward(hcgs_ctx* ctx, const uint16_t* x, int N, const uin
     return mlp_bwd(ctx, x, N, W, b, gy, gW, gb, S(stream));
 }
 
+hcgs_status hcgs_mlp_mse_loss(hcgs_ctx* ctx, const float* y, const float* target, int N, int K, float* loss,
+                              float* gy, void* stream) {
+    if (!ctx) return HCGS_ERR_INVALID_ARG;
+    REQUIRE(ctx, N >= 1 && K >= 1 && K <= 16, "need N >= 1 and 1 <= K <= 16");
+    REQUIRE(ctx, y && target && loss && gy, "NULL argument");
+    cudaSetDevice(ctx->device);
+    return mlp_mse(ctx, y, target, N, K, loss, gy, S(stream));
+}
+
+hcgs_status hcgs_cast_bf16(hcgs_ctx* ctx, const float* src, uint16_t* dst, int64_t n, void* stream) {
+    if (!ctx) return HCGS_ERR_INVALID_ARG;
+    REQUIRE(ctx, n >= 0, "n must be >= 0");
+    if (n == 0) return HCGS_OK;
+    REQUIRE(ctx, src && dst, "NULL argument");
+    cudaSetDevice(ctx->device);
+    return cast_bf16(ctx, src, dst, n, S(stream));
+}
+
 }  // extern "C"

@@ -198,5 +198,8 @@ hcgs_status mlp_fwd(hcgs_ctx* ctx, const uint16_t* x, int N, const uint16_t* con
                     float* y, cudaStream_t st);
 hcgs_status mlp_bwd(hcgs_ctx* ctx, const uint16_t* x, int N, const uint16_t* const* W, const float* const* b,
                     const float* gy, float* const* gW, float* const* gb, cudaStream_t st);
+hcgs_status mlp_mse(hcgs_ctx* ctx, const float* y, const float* tgt, int N, int K, float* loss, float* gy,
+                    cudaStream_t st);
+hcgs_status cast_bf16(hcgs_ctx* ctx, const float* src, uint16_t* dst, int64_t n, cudaStream_t st);
 
 }  // namespace hcgs

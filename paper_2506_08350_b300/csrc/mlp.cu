@@ -247,6 +247,56 @@ __global__ void __launch_bounds__(256) k_mlp_bwd(MlpW w, MlpG g, const uint16_t*
     weight_grad<MLP_HID, MLP_IN>(gz, LDH, sx, LDI, g.gW1, warp, gid, tig);
 }
 
+// Mean squared error of the first K of the 16 output columns against
+// target[N][16]; gy = dL/dy (zero in the unused columns).  Per-block partial
+// sums, reduced in a fixed order by k_reduce_sum.
+__global__ void k_mlp_mse(const float* __restrict__ y, const float* __restrict__ tgt, int N, int K, float scale,
+                          float* __restrict__ gy, float* __restrict__ partials) {
+    __shared__ float red[32];
+    float part = 0.f;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N * MLP_OUT; i += gridDim.x * blockDim.x) {
+        const int c = i % MLP_OUT;
+        float g = 0.f;
+        if (c < K) {
+            const float d = y[i] - tgt[i];
+            part += d * d;
+            g = 2.f * scale * d;
+        }
+        gy[i] = g;
+    }
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += red[w];
+        partials[blockIdx.x] = t;
+    }
+}
+
+// round-to-nearest-even float32 -> bfloat16
+__global__ void k_cast_bf16(const float* __restrict__ src, uint16_t* __restrict__ dst, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = f2bf(src[i]);
+}
+
+hcgs_status mlp_mse(hcgs_ctx* ctx, const float* y, const float* tgt, int N, int K, float* loss, float* gy,
+                    cudaStream_t st) {
+    const int blocks = 296;
+    HCGS_CUDA(ctx, grow(ctx, ctx->ws[5], blocks * sizeof(float), &ctx->bytes));
+    const float scale = 1.f / ((float)N * (float)K);
+    HCGS_KERNEL(ctx, "k_mlp_mse", st, k_mlp_mse<<<blocks, 256, 0, st>>>(y, tgt, N, K, scale, gy, (float*)ctx->ws[5].p));
+    return reduce_sum(ctx, (const float*)ctx->ws[5].p, blocks, scale, loss, st);
+}
+
+hcgs_status cast_bf16(hcgs_ctx* ctx, const float* src, uint16_t* dst, int64_t n, cudaStream_t st) {
+    if (n <= 0) return HCGS_OK;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 148 * 8) blocks = 148 * 8;
+    HCGS_KERNEL(ctx, "k_cast_bf16", st, k_cast_bf16<<<(unsigned)blocks, 256, 0, st>>>(src, dst, n));
+    return HCGS_OK;
+}
+
 static MlpW make_w(const uint16_t* const* W, const float* const* b) {
     MlpW w;
     w.W1 = W[0]; w.W2 = W[1]; w.W3 = W[2]; w.W4 = W[3];
