@@ -291,6 +291,27 @@ def run_ours(args):
     for _ in range(2):
         fwd()
     ms_fwd = timed(fwd, args.steps)
+    # --- reduced-precision footprint tier (FP16x2 exponent/exp, FP32 accumulation) on the same inputs ---
+    holo32 = holo.clone()
+    opts16 = dict(opts, footprint=1)
+    saved16 = P.Saved(ctx)
+    holo16 = torch.empty_like(holo)
+    grads16 = {k: torch.empty_like(g[k]) for k in P.PARAM_NAMES}
+
+    def step16():
+        ctx.render_view(g, vm, it, o, opts16, holo16, None, saved16)
+        ctx.render_view_backward(saved16, g, gP, grads16)
+
+    for _ in range(2):
+        step16()
+    ms_step16 = timed(step16, args.steps)
+    fwd()
+    torch.cuda.synchronize()
+    ctx.render_view(g, vm, it, o, opts16, holo16, None, saved16)
+    torch.cuda.synchronize()
+    tier_rel = float(torch.linalg.vector_norm(holo16 - holo) / torch.linalg.vector_norm(holo))
+    saved16.release()
+    del holo32, holo16, grads16
     # --- contributing pairs (deterministic; same as in the timed steps) ---
     U = torch.empty((V, o.L, o.C, o.H, o.W), dtype=torch.complex64, device=dev)
     nc = torch.empty((V, o.L, o.H, o.W), dtype=torch.int32, device=dev)
@@ -329,6 +350,9 @@ def run_ours(args):
                          "l2": "inputs larger than L2 (~30 GB per step working set), no flush"},
               "steps_per_s": 1e3 / ms_step, "fwd_views_per_s": views / (ms_fwd / 1e3),
               "ms_per_fwd": ms_fwd, "clocks": clocks,
+              "fp16_footprint_tier": {"value": views / (ms_step16 / 1e3), "unit": "views/s", "ms_per_step": ms_step16,
+                                      "speedup_vs_fp32": ms_step / ms_step16,
+                                      "hologram_rel_l2_vs_fp32_path": tier_rel},
               "e2e": {"value": views / (ms_e2e / 1e3), "unit": "views/s", "h2d_bytes_per_step": h2d,
                       "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e},
               "gpu_launches": int(sum(c for _, c in prof.values()))}

@@ -17,6 +17,8 @@
 //
 // The alpha arithmetic uses explicitly rounded intrinsics so that the forward
 // and backward kernels take identical skip/stop decisions.
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 #include "project.cuh"
 
@@ -156,6 +158,35 @@ __device__ __forceinline__ void eval_pair(float px, float2 py2, float4 r0, float
     a2 = make_float2(fminf(amax, og2.x), fminf(amax, og2.y));
 }
 
+// Reduced-precision footprint (the FP16x2 tier): the same quantities, with the
+// exponent and exp() evaluated in packed half precision.  To stay well
+// conditioned for footprints of any size the quadratic is formed in the
+// footprint's normalised frame, u = dx sqrt(A), v = dy sqrt(C),
+// q = u^2 + 2 rho u v + v^2 with rho = B / sqrt(A C) in (-1, 1), all O(1)
+// inside the support.  Accumulation stays FP32.
+__device__ __forceinline__ void eval_pair_h(float px, float2 py2, float4 r0, float Cc, float o, float amax,
+                                            float& dx, float2& dy2, float2& G2, float2& og2, float2& a2) {
+    dx = __fsub_rn(px, r0.x);
+    dy2 = __fadd2_rn(py2, f2(-r0.y));
+    const float sa = sqrtf(r0.z), sc = sqrtf(Cc);
+    const float rho2 = 2.f * r0.w / (sa * sc);
+    const __half2 u = __float2half2_rn(dx * sa);
+    const __half2 v = __floats2half2_rn(dy2.x * sc, dy2.y * sc);
+    __half2 q = __hfma2(v, v, __hmul2(u, u));
+    q = __hfma2(__float2half2_rn(rho2), __hmul2(u, v), q);
+    const __half2 e = __hmul2(q, __float2half2_rn(-0.72134752044448170f));  // -log2(e) / 2
+    G2 = __half22float2(h2exp2(e));
+    og2 = __fmul2_rn(f2(o), G2);
+    a2 = make_float2(fminf(amax, og2.x), fminf(amax, og2.y));
+}
+
+template <bool H16>
+__device__ __forceinline__ void eval_tier(float px, float2 py2, float4 r0, float Cc, float o, float amax, float& dx,
+                                          float2& dy2, float2& G2, float2& og2, float2& a2) {
+    if (H16) eval_pair_h(px, py2, r0, Cc, o, amax, dx, dy2, G2, og2, a2);
+    else eval_pair(px, py2, r0, Cc, o, amax, dx, dy2, G2, og2, a2);
+}
+
 // Warp reduce-scatter of 16 values: afterwards lanes 2i and 2i+1 both hold the
 // warp-wide sum of value i (16 shuffles instead of 80 for a full butterfly).
 __device__ __forceinline__ float warp_reduce_scatter16(float (&v)[16], int lane) {
@@ -196,7 +227,7 @@ __device__ __forceinline__ void book(bool c, float T, float teps, uint32_t pos, 
     }
 }
 
-template <int C>
+template <int C, bool H16>
 __global__ void __launch_bounds__(RT, 6) k_raster_fwd(RasterArgs a, float2* __restrict__ U, float* __restrict__ Tsave,
                                                    uint32_t* __restrict__ lastsave, float* __restrict__ Tout,
                                                    int32_t* __restrict__ ncout) {
@@ -236,8 +267,8 @@ __global__ void __launch_bounds__(RT, 6) k_raster_fwd(RasterArgs a, float2* __re
             const uint32_t pos = spos[warp][k];
             float dxA, dxB;
             float2 dyA, GA, ogA, aA, dyB, GB, ogB, aB;
-            eval_pair(fpx, pyA, r0, r1.x, r1.y, a.amax, dxA, dyA, GA, ogA, aA);
-            eval_pair(fpx, pyB, r0, r1.x, r1.y, a.amax, dxB, dyB, GB, ogB, aB);
+            eval_tier<H16>(fpx, pyA, r0, r1.x, r1.y, a.amax, dxA, dyA, GA, ogA, aA);
+            eval_tier<H16>(fpx, pyB, r0, r1.x, r1.y, a.amax, dxB, dyB, GB, ogB, aB);
             const bool c0 = !d[0] && aA.x >= a.amin, c1 = !d[1] && aA.y >= a.amin;
             const bool c2 = !d[2] && aB.x >= a.amin, c3 = !d[3] && aB.y >= a.amin;
             if (c0 || c1) {
@@ -321,7 +352,7 @@ __device__ __forceinline__ void bwd_pair(const float4* rec, float dx, float2 dy2
     gl[4] += 0.5f * (pdy.x * dy2.x + pdy.y * dy2.y);
 }
 
-template <int C>
+template <int C, bool H16>
 __global__ void __launch_bounds__(RT, 4) k_raster_bwd(RasterArgs a, const float* __restrict__ Tsave,
                                                    const uint32_t* __restrict__ lastsave,
                                                    const float2* __restrict__ gU, float* __restrict__ g2d) {
@@ -383,8 +414,8 @@ __global__ void __launch_bounds__(RT, 4) k_raster_bwd(RasterArgs a, const float*
             const float4 r0 = rec[0], r1 = rec[1];
             float dxA, dxB;
             float2 dyA, GA, ogA, aA, dyB, GB, ogB, aB;
-            eval_pair(fpx, pyA, r0, r1.x, r1.y, a.amax, dxA, dyA, GA, ogA, aA);
-            eval_pair(fpx, pyB, r0, r1.x, r1.y, a.amax, dxB, dyB, GB, ogB, aB);
+            eval_tier<H16>(fpx, pyA, r0, r1.x, r1.y, a.amax, dxA, dyA, GA, ogA, aA);
+            eval_tier<H16>(fpx, pyB, r0, r1.x, r1.y, a.amax, dxB, dyB, GB, ogB, aB);
             const bool c0 = pos < last[0] && aA.x >= a.amin, c1 = pos < last[1] && aA.y >= a.amin;
             const bool c2 = pos < last[2] && aB.x >= a.amin, c3 = pos < last[3] && aB.y >= a.amin;
             if (c0 || c1) bwd_pair<C>(rec, dxA, dyA, GA, ogA, aA, c0, c1, a.amax, TA, SAX, SAY, gAX, gAY, gl);
@@ -409,12 +440,17 @@ hcgs_status raster_forward(hcgs_ctx* ctx, hcgs_saved* s, float2* U, float* T_out
     dim3 grid(s->tilesX * ((s->tilesY + 1) / 2), s->L, s->V);  // 16 x 32 pixel regions
     float* Ts = (float*)s->Tfin.p;
     uint32_t* ls = (uint32_t*)s->last.p;
+    const bool h16 = s->opts.footprint == 1;
+#define HCGS_FWD(CC)                                                                                       \
+    if (h16) HCGS_KERNEL(ctx, "k_raster_fwd", st, k_raster_fwd<CC, true><<<grid, RT, 0, st>>>(a, U, Ts, ls, T_out, nc_out)); \
+    else HCGS_KERNEL(ctx, "k_raster_fwd", st, k_raster_fwd<CC, false><<<grid, RT, 0, st>>>(a, U, Ts, ls, T_out, nc_out))
     switch (s->C) {
-        case 1: HCGS_KERNEL(ctx, "k_raster_fwd", st, k_raster_fwd<1><<<grid, RT, 0, st>>>(a, U, Ts, ls, T_out, nc_out)); break;
-        case 2: HCGS_KERNEL(ctx, "k_raster_fwd", st, k_raster_fwd<2><<<grid, RT, 0, st>>>(a, U, Ts, ls, T_out, nc_out)); break;
-        case 3: HCGS_KERNEL(ctx, "k_raster_fwd", st, k_raster_fwd<3><<<grid, RT, 0, st>>>(a, U, Ts, ls, T_out, nc_out)); break;
-        default: HCGS_KERNEL(ctx, "k_raster_fwd", st, k_raster_fwd<4><<<grid, RT, 0, st>>>(a, U, Ts, ls, T_out, nc_out)); break;
+        case 1: HCGS_FWD(1); break;
+        case 2: HCGS_FWD(2); break;
+        case 3: HCGS_FWD(3); break;
+        default: HCGS_FWD(4); break;
     }
+#undef HCGS_FWD
     HCGS_LAUNCH(ctx, "k_raster_fwd");
     return HCGS_OK;
 }
@@ -428,12 +464,17 @@ hcgs_status raster_backward(hcgs_ctx* ctx, hcgs_saved* s, const float2* gU, cuda
     const float* Ts = (const float*)s->Tfin.p;
     const uint32_t* ls = (const uint32_t*)s->last.p;
     float* g2 = (float*)s->g2d.p;
+    const bool h16 = s->opts.footprint == 1;
+#define HCGS_BWD(CC)                                                                                        \
+    if (h16) HCGS_KERNEL(ctx, "k_raster_bwd", st, k_raster_bwd<CC, true><<<grid, RT, 0, st>>>(a, Ts, ls, gU, g2)); \
+    else HCGS_KERNEL(ctx, "k_raster_bwd", st, k_raster_bwd<CC, false><<<grid, RT, 0, st>>>(a, Ts, ls, gU, g2))
     switch (s->C) {
-        case 1: HCGS_KERNEL(ctx, "k_raster_bwd", st, k_raster_bwd<1><<<grid, RT, 0, st>>>(a, Ts, ls, gU, g2)); break;
-        case 2: HCGS_KERNEL(ctx, "k_raster_bwd", st, k_raster_bwd<2><<<grid, RT, 0, st>>>(a, Ts, ls, gU, g2)); break;
-        case 3: HCGS_KERNEL(ctx, "k_raster_bwd", st, k_raster_bwd<3><<<grid, RT, 0, st>>>(a, Ts, ls, gU, g2)); break;
-        default: HCGS_KERNEL(ctx, "k_raster_bwd", st, k_raster_bwd<4><<<grid, RT, 0, st>>>(a, Ts, ls, gU, g2)); break;
+        case 1: HCGS_BWD(1); break;
+        case 2: HCGS_BWD(2); break;
+        case 3: HCGS_BWD(3); break;
+        default: HCGS_BWD(4); break;
     }
+#undef HCGS_BWD
     HCGS_LAUNCH(ctx, "k_raster_bwd");
     return HCGS_OK;
 }
