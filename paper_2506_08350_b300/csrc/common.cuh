@@ -8,7 +8,7 @@
 #include <tuple>
 #include <vector>
 
-#include "../../include/hcgs.h"
+#include "hcgs.h"
 
 namespace hcgs {
 

@@ -306,19 +306,28 @@ __global__ void __launch_bounds__(RT, 6) k_raster_fwd(RasterArgs a, float2* __re
     }
 }
 
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Adjoint step of a pixel pair (c0/c1: the pixels that took this step in the
 // forward) walking back-to-front (Sec. 4.2): T_k = T_{k+1} / (1 - alpha_k);
 // dU/dalpha_k = w T_k - S_k / (1 - alpha_k), S_k = sum_{m>k} w alpha T.
-// Adds the pair's dL/d(mu 0-1, conic 2-4, o 5, w 6..) to gl.
+// Adds the pair's dL/d(mu 0-1, conic 2-4, o 5, w 6..) to the packed
+// accumulators gl (one lane per pixel; the halves are summed once per entry).
+// The reciprocal of 1 - alpha only scales gradients (no decision depends on
+// it), so the hardware approximation is used.
 template <int C>
 __device__ __forceinline__ void bwd_pair(const float4* rec, float dx, float2 dy2, float2 G2, float2 og2, float2 a2,
                                          bool c0, bool c1, float amax, float2& T2, float2 (&SX)[C],
                                          float2 (&SY)[C], const float2 (&gX)[C], const float2 (&gY)[C],
-                                         float (&gl)[16]) {
+                                         float2 (&gl)[14]) {
     const float4 r0 = rec[0], r1 = rec[1];
     const float2 al = make_float2(c0 ? a2.x : 0.f, c1 ? a2.y : 0.f);
     const float2 om = __fadd2_rn(f2(1.f), make_float2(-al.x, -al.y));
-    const float2 iom = make_float2(__frcp_rn(om.x), __frcp_rn(om.y));
+    const float2 iom = make_float2(rcp_approx(om.x), rcp_approx(om.y));
     const float2 Tk = __fmul2_rn(T2, iom);
     const float2 aT = __fmul2_rn(al, Tk);
     float2 dLda = f2(0.f);
@@ -330,26 +339,23 @@ __device__ __forceinline__ void bwd_pair(const float4* rec, float dx, float2 dy2
         dLda = __ffma2_rn(gX[c], ux, __ffma2_rn(gY[c], uy, dLda));
         SX[c] = __ffma2_rn(f2(w.x), aT, SX[c]);
         SY[c] = __ffma2_rn(f2(w.y), aT, SY[c]);
-        const float2 gwx = __fmul2_rn(gX[c], aT), gwy = __fmul2_rn(gY[c], aT);
-        gl[6 + 2 * c] += gwx.x + gwx.y;
-        gl[7 + 2 * c] += gwy.x + gwy.y;
+        gl[6 + 2 * c] = __ffma2_rn(gX[c], aT, gl[6 + 2 * c]);
+        gl[7 + 2 * c] = __ffma2_rn(gY[c], aT, gl[7 + 2 * c]);
     }
     T2 = Tk;
     // a clamped alpha (o G > alpha_max) is flat in o G
     const float2 dLa = make_float2(c0 && og2.x <= amax ? dLda.x : 0.f, c1 && og2.y <= amax ? dLda.y : 0.f);
-    const float2 dLdp = __fmul2_rn(make_float2(-dLa.x, -dLa.y), og2);  // dL/dpower
-    const float2 go = __fmul2_rn(dLa, G2);
-    gl[5] += go.x + go.y;
-    const float adx = __fmul_rn(r0.z, dx), bdx = __fmul_rn(r0.w, dx);
-    const float2 q0 = __ffma2_rn(f2(r0.w), dy2, f2(adx));  // A dx + B dy
-    const float2 q1 = __ffma2_rn(f2(r1.x), dy2, f2(bdx));  // B dx + C dy
-    const float2 m0 = __fmul2_rn(dLdp, q0), m1 = __fmul2_rn(dLdp, q1);
-    gl[0] -= m0.x + m0.y;
-    gl[1] -= m1.x + m1.y;
-    const float2 pdy = __fmul2_rn(dLdp, dy2);
-    gl[2] += 0.5f * dx * dx * (dLdp.x + dLdp.y);
-    gl[3] += dx * (pdy.x + pdy.y);
-    gl[4] += 0.5f * (pdy.x * dy2.x + pdy.y * dy2.y);
+    const float2 dLdpn = __fmul2_rn(dLa, og2);  // -dL/dpower
+    gl[5] = __ffma2_rn(dLa, G2, gl[5]);
+    // power = 1/2 (A dx^2 + 2 B dx dy + C dy^2), d = pixel - mu
+    const float2 q0 = __ffma2_rn(f2(r0.w), dy2, f2(__fmul_rn(r0.z, dx)));  // A dx + B dy
+    const float2 q1 = __ffma2_rn(f2(r1.x), dy2, f2(__fmul_rn(r0.w, dx)));  // B dx + C dy
+    gl[0] = __ffma2_rn(dLdpn, q0, gl[0]);
+    gl[1] = __ffma2_rn(dLdpn, q1, gl[1]);
+    const float2 pdy = __fmul2_rn(dLdpn, dy2);
+    gl[2] = __ffma2_rn(f2(-0.5f * dx * dx), dLdpn, gl[2]);
+    gl[3] = __ffma2_rn(f2(-dx), pdy, gl[3]);
+    gl[4] = __ffma2_rn(__fmul2_rn(f2(-0.5f), dy2), pdy, gl[4]);
 }
 
 template <int C, bool H16>
@@ -408,9 +414,9 @@ __global__ void __launch_bounds__(RT, 4) k_raster_bwd(RasterArgs a, const float*
         for (int k = nh - 1; k >= 0; k--) {  // back-to-front over the visiting order
             const float4* rec = srec[warp][k];
             const uint32_t pos = spos[warp][k];
-            float gl[16];
+            float2 gl2[14];
 #pragma unroll
-            for (int e = 0; e < 16; e++) gl[e] = 0.f;
+            for (int e = 0; e < 14; e++) gl2[e] = f2(0.f);
             const float4 r0 = rec[0], r1 = rec[1];
             float dxA, dxB;
             float2 dyA, GA, ogA, aA, dyB, GB, ogB, aB;
@@ -418,9 +424,12 @@ __global__ void __launch_bounds__(RT, 4) k_raster_bwd(RasterArgs a, const float*
             eval_tier<H16>(fpx, pyB, r0, r1.x, r1.y, a.amax, dxB, dyB, GB, ogB, aB);
             const bool c0 = pos < last[0] && aA.x >= a.amin, c1 = pos < last[1] && aA.y >= a.amin;
             const bool c2 = pos < last[2] && aB.x >= a.amin, c3 = pos < last[3] && aB.y >= a.amin;
-            if (c0 || c1) bwd_pair<C>(rec, dxA, dyA, GA, ogA, aA, c0, c1, a.amax, TA, SAX, SAY, gAX, gAY, gl);
-            if (c2 || c3) bwd_pair<C>(rec, dxB, dyB, GB, ogB, aB, c2, c3, a.amax, TB, SBX, SBY, gBX, gBY, gl);
+            if (c0 || c1) bwd_pair<C>(rec, dxA, dyA, GA, ogA, aA, c0, c1, a.amax, TA, SAX, SAY, gAX, gAY, gl2);
+            if (c2 || c3) bwd_pair<C>(rec, dxB, dyB, GB, ogB, aB, c2, c3, a.amax, TB, SBX, SBY, gBX, gBY, gl2);
             if (__any_sync(0xffffffffu, c0 || c1 || c2 || c3)) {
+                float gl[16];
+#pragma unroll
+                for (int e = 0; e < 16; e++) gl[e] = e < 6 + 2 * C ? gl2[e].x + gl2[e].y : 0.f;
                 const float sum = warp_reduce_scatter16(gl, lane);
                 const int idx = lane >> 1;
                 if (!(lane & 1) && idx < G) atomicAdd(g2d + (vN + sid[warp][k]) * G + idx, sum);
