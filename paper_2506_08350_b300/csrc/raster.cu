@@ -314,34 +314,34 @@ __device__ __forceinline__ float rcp_approx(float x) {
 
 // Adjoint step of a pixel pair (c0/c1: the pixels that took this step in the
 // forward) walking back-to-front (Sec. 4.2): T_k = T_{k+1} / (1 - alpha_k);
-// dU/dalpha_k = w T_k - S_k / (1 - alpha_k), S_k = sum_{m>k} w alpha T.
+// dL/dalpha_k = sum_c Re(conj(g_c) (w_kc T_k - S_kc / (1 - alpha_k))) with
+// S_k = sum_{m>k} w_m alpha_m T_m.  Since g is fixed per pixel, only the
+// scalar B = sum_c Re(conj(g_c) S_c) is carried: dL/dalpha_k = T_k A_k -
+// B / (1 - alpha_k) and B <- B + alpha_k T_k A_k, A_k = sum_c Re(conj(g_c) w_kc).
 // Adds the pair's dL/d(mu 0-1, conic 2-4, o 5, w 6..) to the packed
 // accumulators gl (one lane per pixel; the halves are summed once per entry).
 // The reciprocal of 1 - alpha only scales gradients (no decision depends on
 // it), so the hardware approximation is used.
 template <int C>
 __device__ __forceinline__ void bwd_pair(const float4* rec, float dx, float2 dy2, float2 G2, float2 og2, float2 a2,
-                                         bool c0, bool c1, float amax, float2& T2, float2 (&SX)[C],
-                                         float2 (&SY)[C], const float2 (&gX)[C], const float2 (&gY)[C],
-                                         float2 (&gl)[14]) {
+                                         bool c0, bool c1, float amax, float2& T2, float2& B2,
+                                         const float2 (&gX)[C], const float2 (&gY)[C], float2 (&gl)[14]) {
     const float4 r0 = rec[0], r1 = rec[1];
     const float2 al = make_float2(c0 ? a2.x : 0.f, c1 ? a2.y : 0.f);
     const float2 om = __fadd2_rn(f2(1.f), make_float2(-al.x, -al.y));
     const float2 iom = make_float2(rcp_approx(om.x), rcp_approx(om.y));
     const float2 Tk = __fmul2_rn(T2, iom);
     const float2 aT = __fmul2_rn(al, Tk);
-    float2 dLda = f2(0.f);
+    float2 Ak = f2(0.f);
 #pragma unroll
     for (int c = 0; c < C; c++) {
         const float2 w = RecW<C>::get(rec, c);
-        const float2 ux = __ffma2_rn(make_float2(-SX[c].x, -SX[c].y), iom, __fmul2_rn(f2(w.x), Tk));
-        const float2 uy = __ffma2_rn(make_float2(-SY[c].x, -SY[c].y), iom, __fmul2_rn(f2(w.y), Tk));
-        dLda = __ffma2_rn(gX[c], ux, __ffma2_rn(gY[c], uy, dLda));
-        SX[c] = __ffma2_rn(f2(w.x), aT, SX[c]);
-        SY[c] = __ffma2_rn(f2(w.y), aT, SY[c]);
+        Ak = __ffma2_rn(gX[c], f2(w.x), __ffma2_rn(gY[c], f2(w.y), Ak));
         gl[6 + 2 * c] = __ffma2_rn(gX[c], aT, gl[6 + 2 * c]);
         gl[7 + 2 * c] = __ffma2_rn(gY[c], aT, gl[7 + 2 * c]);
     }
+    const float2 dLda = __ffma2_rn(Tk, Ak, __fmul2_rn(make_float2(-iom.x, -iom.y), B2));
+    B2 = __ffma2_rn(aT, Ak, B2);
     T2 = Tk;
     // a clamped alpha (o G > alpha_max) is flat in o G
     const float2 dLa = make_float2(c0 && og2.x <= amax ? dLda.x : 0.f, c1 && og2.y <= amax ? dLda.y : 0.f);
@@ -396,15 +396,15 @@ __global__ void __launch_bounds__(RT, 4) k_raster_bwd(RasterArgs a, const float*
         }
     }
     float2 TA = make_float2(Tq[0], Tq[1]), TB = make_float2(Tq[2], Tq[3]);
-    float2 gAX[C], gAY[C], gBX[C], gBY[C], SAX[C], SAY[C], SBX[C], SBY[C];
+    float2 gAX[C], gAY[C], gBX[C], gBY[C];
 #pragma unroll
     for (int c = 0; c < C; c++) {
         gAX[c] = make_float2(gq[0][c].x, gq[1][c].x);
         gAY[c] = make_float2(gq[0][c].y, gq[1][c].y);
         gBX[c] = make_float2(gq[2][c].x, gq[3][c].x);
         gBY[c] = make_float2(gq[2][c].y, gq[3][c].y);
-        SAX[c] = SAY[c] = SBX[c] = SBY[c] = f2(0.f);
     }
+    float2 BA = f2(0.f), BB = f2(0.f);  // sum_c Re(conj(g_c) S_c) per pixel
     uint32_t maxlast = max(max(last[0], last[1]), max(last[2], last[3]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) maxlast = max(maxlast, __shfl_xor_sync(0xffffffffu, maxlast, o));
@@ -424,8 +424,8 @@ __global__ void __launch_bounds__(RT, 4) k_raster_bwd(RasterArgs a, const float*
             eval_tier<H16>(fpx, pyB, r0, r1.x, r1.y, a.amax, dxB, dyB, GB, ogB, aB);
             const bool c0 = pos < last[0] && aA.x >= a.amin, c1 = pos < last[1] && aA.y >= a.amin;
             const bool c2 = pos < last[2] && aB.x >= a.amin, c3 = pos < last[3] && aB.y >= a.amin;
-            if (c0 || c1) bwd_pair<C>(rec, dxA, dyA, GA, ogA, aA, c0, c1, a.amax, TA, SAX, SAY, gAX, gAY, gl2);
-            if (c2 || c3) bwd_pair<C>(rec, dxB, dyB, GB, ogB, aB, c2, c3, a.amax, TB, SBX, SBY, gBX, gBY, gl2);
+            if (c0 || c1) bwd_pair<C>(rec, dxA, dyA, GA, ogA, aA, c0, c1, a.amax, TA, BA, gAX, gAY, gl2);
+            if (c2 || c3) bwd_pair<C>(rec, dxB, dyB, GB, ogB, aB, c2, c3, a.amax, TB, BB, gBX, gBY, gl2);
             if (__any_sync(0xffffffffu, c0 || c1 || c2 || c3)) {
                 float gl[16];
 #pragma unroll
