@@ -20,6 +20,8 @@
 // table holds one quadrant because H depends on f_x^2 and f_y^2 only.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
+#include <utility>
 
 #include "common.cuh"
 #include "fft.cuh"
@@ -182,157 +184,471 @@ __device__ float2* run_fft(float2* a, float2* b, const FftPlanArg& p, int ntrans
 __device__ __forceinline__ int mirror(int k, int n) { return k <= n / 2 ? k : n - k; }
 
 // ---------------------------------------------------------------------------
-// Compile-time plans for the lengths of the paper-shaped workloads (1080,
-// 1920, 256, 512): constant divisors, unrolled radix sequence, and a padded
-// shared-memory layout (one extra slot every 32 complex values) that spreads
-// the strided Stockham stores over the banks.
+// Register-resident transforms for the lengths of the paper-shaped workloads
+// (1080, 1920, 512, 256).
+//
+// A length-N transform is two or three Stockham stages of composite radix
+// (9, 10, 12, 16, ... each an in-register DFT built from the small ones with
+// compile-time twiddle constants).  A thread keeps its work items of a stage
+// in registers: the first stage reads its inputs straight from global memory,
+// the last stage hands its outputs to the caller in registers, and only the
+// exchanges between stages go through shared memory (one in-place buffer, a
+// write and a read per element each).  The padding of that buffer is chosen
+// per exchange so that the strided stores and loads of the two stages it
+// joins fall on distinct banks.  Because the last stage of one transform and
+// the first stage of a transform with the reversed radix order own the same
+// elements, a forward row transform can feed an inverse one, or an inverse
+// column transform a forward one, without an exchange.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int pad32(int e) { return e + (e >> 5); }
-__host__ __device__ constexpr int padded_len(int e) { return e + e / 32 + 1; }
+namespace rfft {
 
-template <int N, int NS, int R, bool INV, int NTRANS, int ES, int TS>
-__device__ __forceinline__ void stage_ct(const float2* __restrict__ src, float2* __restrict__ dst,
-                                         const float2* __restrict__ tw) {
-    constexpr int M = N / R, TOTAL = M * NTRANS, TWSTEP = N / (NS * R);
-    for (int w = threadIdx.x; w < TOTAL; w += blockDim.x) {
-        const int t = w % NTRANS, j = w / NTRANS, k = j % NS;
-        float2 v[R];
-#pragma unroll
-        for (int r = 0; r < R; r++) v[r] = src[pad32(t * TS + (j + r * M) * ES)];
-        if (NS > 1) {
-#pragma unroll
-            for (int r = 1; r < R; r++) {
-                float2 w_ = tw[r * k * TWSTEP];
-                if (INV) w_.y = -w_.y;
-                v[r] = cmul(v[r], w_);
+// compile-time loop over 0..n-1
+template <class F, int... I>
+__device__ __forceinline__ void sfor_impl(F&& f, std::integer_sequence<int, I...>) {
+    (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, class F>
+__device__ __forceinline__ void sfor(F&& f) {
+    sfor_impl(f, std::make_integer_sequence<int, N>{});
+}
+#define HCGS_CI(x) decltype(x)::value
+
+// sin and cos on [0, pi/2] by their Taylor series, evaluated in double at
+// compile time (the remainder after 12 terms is below 1e-20)
+__host__ __device__ constexpr double ct_sin(double x) {
+    double t = x, s = x;
+    for (int n = 1; n <= 12; n++) {
+        t *= -x * x / ((2.0 * n) * (2.0 * n + 1.0));
+        s += t;
+    }
+    return s;
+}
+__host__ __device__ constexpr double ct_cos(double x) {
+    double t = 1.0, s = 1.0;
+    for (int n = 1; n <= 12; n++) {
+        t *= -x * x / ((2.0 * n - 1.0) * (2.0 * n));
+        s += t;
+    }
+    return s;
+}
+// cos and sin of 2 pi m / n: quadrant q and remainder phi in [0, pi/2)
+__host__ __device__ constexpr double ct_cos2pi(int m, int n) {
+    const int a = ((m % n) + n) % n, q = (4 * a) / n;
+    const double phi = 1.5707963267948966 * (double)(4 * a - q * n) / (double)n;
+    return q == 0 ? ct_cos(phi) : q == 1 ? -ct_sin(phi) : q == 2 ? -ct_cos(phi) : ct_sin(phi);
+}
+__host__ __device__ constexpr double ct_sin2pi(int m, int n) {
+    const int a = ((m % n) + n) % n, q = (4 * a) / n;
+    const double phi = 1.5707963267948966 * (double)(4 * a - q * n) / (double)n;
+    return q == 0 ? ct_sin(phi) : q == 1 ? ct_cos(phi) : q == 2 ? -ct_sin(phi) : -ct_cos(phi);
+}
+
+// a * exp(-+ 2 pi i m / r) (forward: -, inverse: +), exact for quarter turns
+template <int M, int R, bool INV>
+__device__ __forceinline__ float2 twc(float2 a) {
+    constexpr int m = M % R;
+    if constexpr (m == 0) {
+        return a;
+    } else if constexpr (2 * m == R) {
+        return make_float2(-a.x, -a.y);
+    } else if constexpr (4 * m == R) {
+        return mul_mi<INV>(a);
+    } else if constexpr (4 * m == 3 * R) {
+        return mul_mi<!INV>(a);
+    } else {
+        constexpr float c = (float)ct_cos2pi(m, R);
+        constexpr float s = INV ? (float)ct_sin2pi(m, R) : -(float)ct_sin2pi(m, R);
+        return make_float2(a.x * c - a.y * s, a.x * s + a.y * c);
+    }
+}
+
+template <int R, bool INV>
+struct Dft {
+    static __device__ __forceinline__ void run(float2* v) { dft<R, INV>(v); }
+};
+// R = R1 R2: input n = R2 n1 + n2, output k = k1 + R1 k2;
+// X[k1 + R1 k2] = sum_n2 W_R2^(n2 k2) W_R^(n2 k1) sum_n1 x[R2 n1 + n2] W_R1^(n1 k1)
+template <int R1, int R2, bool INV>
+struct DftSplit {
+    static __device__ __forceinline__ void run(float2* v) {
+        float2 y[R2][R1];
+        sfor<R2>([&](auto a) {
+            constexpr int n2 = HCGS_CI(a);
+            sfor<R1>([&](auto b) { y[n2][HCGS_CI(b)] = v[R2 * HCGS_CI(b) + n2]; });
+            Dft<R1, INV>::run(y[n2]);
+            sfor<R1>([&](auto b) {
+                constexpr int k1 = HCGS_CI(b);
+                y[n2][k1] = twc<n2 * k1, R1 * R2, INV>(y[n2][k1]);
+            });
+        });
+        sfor<R1>([&](auto b) {
+            constexpr int k1 = HCGS_CI(b);
+            float2 z[R2];
+            sfor<R2>([&](auto a) { z[HCGS_CI(a)] = y[HCGS_CI(a)][k1]; });
+            Dft<R2, INV>::run(z);
+            sfor<R2>([&](auto a) { v[k1 + R1 * HCGS_CI(a)] = z[HCGS_CI(a)]; });
+        });
+    }
+};
+template <bool INV> struct Dft<6, INV> : DftSplit<2, 3, INV> {};
+template <bool INV> struct Dft<9, INV> : DftSplit<3, 3, INV> {};
+template <bool INV> struct Dft<10, INV> : DftSplit<2, 5, INV> {};
+template <bool INV> struct Dft<12, INV> : DftSplit<4, 3, INV> {};
+template <bool INV> struct Dft<15, INV> : DftSplit<3, 5, INV> {};
+template <bool INV> struct Dft<16, INV> : DftSplit<4, 4, INV> {};
+
+// Twiddles and DFT of one work item j of a stage (Ns = product of the earlier
+// radices): v[r] *= w^r with w = W_{Ns R}^(j mod Ns) read from the length-N
+// table, powers by halving (at most ceil(log2 r) products deep).
+template <int N, int NS, int R, bool INV>
+__device__ __forceinline__ void stage_math(float2 (&v)[R], int j, const float2* __restrict__ tw) {
+    if constexpr (NS > 1) {
+        float2 w = __ldg(tw + (j % NS) * (N / (NS * R)));
+        if (INV) w.y = -w.y;
+        float2 p[R];
+        p[1] = w;
+        sfor<R>([&](auto a) {
+            constexpr int r = HCGS_CI(a);
+            if constexpr (r >= 2) p[r] = cmul(p[r / 2], p[r - r / 2]);
+            if constexpr (r >= 1) v[r] = cmul(v[r], p[r]);
+        });
+    }
+    Dft<R, INV>::run(v);
+}
+
+template <int... RS> struct Seq {};
+// shared-memory slot of element e: one gap of Q slots after every P elements
+template <int P, int Q>
+struct Pad {
+    static __device__ __forceinline__ int at(int e) { return Q == 0 ? e : e + Q * (e / P); }
+    static constexpr int extent(int n) { return n + Q * ((n - 1) / P) + 1; }
+};
+template <class... Ls> struct Lays {};
+
+// Work items of a stage: w = threadIdx.x + u T (u < U), transform t = w mod
+// NTRANS, item j = w / NTRANS; element e of the buffer = position * NTRANS + t.
+template <int M, int NTRANS, int T>
+struct Items {
+    static constexpr int TOTAL = M * NTRANS, U = (TOTAL + T - 1) / T;
+    static __device__ __forceinline__ bool valid(int u) { return TOTAL % T == 0 || threadIdx.x + u * T < TOTAL; }
+    static __device__ __forceinline__ int t(int u) { return (threadIdx.x + u * T) % NTRANS; }
+    static __device__ __forceinline__ int j(int u) { return (threadIdx.x + u * T) / NTRANS; }
+};
+
+template <int N, bool INV, int NTRANS, int T, int NS, class RSeq, class LSeq>
+struct Stages;
+
+template <int N, bool INV, int NTRANS, int T, int NS, int R>
+struct Stages<N, INV, NTRANS, T, NS, Seq<R>, Lays<>> {
+    static constexpr int M = N / R;
+    using It = Items<M, NTRANS, T>;
+    static constexpr int U = It::U, RAD = R;
+    static constexpr int smem(int) { return 0; }
+    // v: this stage's inputs (element j + r M of item j); out(v) receives
+    // the outputs (element j + r M of the transform again)
+    template <class Out>
+    static __device__ __forceinline__ void run(float2 (&v)[U][R], float2*, const float2* __restrict__ tw, Out&& out) {
+        sfor<U>([&](auto a) { stage_math<N, NS, R, INV>(v[HCGS_CI(a)], It::j(HCGS_CI(a)), tw); });
+        out(v);
+    }
+};
+
+template <int N, bool INV, int NTRANS, int T, int NS, int R, int R2, int... RS, class L, class... LS>
+struct Stages<N, INV, NTRANS, T, NS, Seq<R, R2, RS...>, Lays<L, LS...>> {
+    static constexpr int M = N / R;
+    using It = Items<M, NTRANS, T>;
+    static constexpr int U = It::U, RAD = R;
+    using Next = Stages<N, INV, NTRANS, T, NS * R, Seq<R2, RS...>, Lays<LS...>>;
+    // complex slots of shared memory the exchanges use
+    static constexpr int smem(int n) {
+        return L::extent(n) > Next::smem(n) ? L::extent(n) : Next::smem(n);
+    }
+    template <class Out>
+    static __device__ __forceinline__ void run(float2 (&v)[U][R], float2* sm, const float2* __restrict__ tw,
+                                               Out&& out) {
+        sfor<U>([&](auto a) { stage_math<N, NS, R, INV>(v[HCGS_CI(a)], It::j(HCGS_CI(a)), tw); });
+        __syncthreads();  // earlier readers of the buffer are done
+        sfor<U>([&](auto a) {
+            constexpr int u = HCGS_CI(a);
+            if (It::valid(u)) {
+                const int j = It::j(u), t = It::t(u);
+                const int base = (j / NS) * NS * R + j % NS;
+                sfor<R>([&](auto b) {
+                    constexpr int r = HCGS_CI(b);
+                    sm[L::at((base + r * NS) * NTRANS + t)] = v[u][r];
+                });
             }
-        }
-        dft<R, INV>(v);
-        const int idxD = (j / NS) * NS * R + k;
-#pragma unroll
-        for (int r = 0; r < R; r++) dst[pad32(t * TS + (idxD + r * NS) * ES)] = v[r];
-    }
-}
-
-template <bool INV, int N, int NTRANS, int ES, int TS, int NS, int R, int... RS>
-struct CtStages {
-    static __device__ __forceinline__ float2* run(float2* a, float2* b, const float2* tw) {
-        stage_ct<N, NS, R, INV, NTRANS, ES, TS>(a, b, tw);
+        });
         __syncthreads();
-        if constexpr (sizeof...(RS) == 0) {
-            return b;
-        } else {
-            return CtStages<INV, N, NTRANS, ES, TS, NS * R, RS...>::run(b, a, tw);
-        }
+        using Nt = typename Next::It;
+        float2 v2[Next::U][R2];
+        sfor<Next::U>([&](auto a) {
+            constexpr int u = HCGS_CI(a);
+            const bool ok = Nt::valid(u);
+            const int j = Nt::j(u), t = Nt::t(u);
+            sfor<R2>([&](auto b) {
+                constexpr int r = HCGS_CI(b);
+                v2[u][r] = ok ? sm[L::at((j + r * Next::M) * NTRANS + t)] : make_float2(0.f, 0.f);
+            });
+        });
+        Next::run(v2, sm, tw, out);
     }
 };
 
-template <int N, int... RS>
-struct CtPlan {
-    static constexpr int n = N;
-    template <bool INV, int NTRANS, int ES, int TS>
-    static __device__ __forceinline__ float2* run(float2* a, float2* b, const float2* tw) {
-        return CtStages<INV, N, NTRANS, ES, TS, 1, RS...>::run(a, b, tw);
+template <class V>
+struct Shape {
+    using A = std::remove_reference_t<V>;
+    static constexpr int U = std::extent<A, 0>::value, R = std::extent<A, 1>::value;
+};
+
+// Column plan: N-point transforms of CW adjacent columns per CTA of T threads;
+// radix order A with exchange layouts LA, and the reversed order B with LB.
+template <int N_, int CW_, int T_, int MINB_, class A_, class LA_, class B_, class LB_>
+struct ColPlan {
+    static constexpr int N = N_, CW = CW_, T = T_, MINB = MINB_;
+    using A = A_;
+    using LA = LA_;
+    using B = B_;
+    using LB = LB_;
+    template <bool INV> using SA = Stages<N, INV, CW, T, 1, A, LA>;
+    template <bool INV> using SB = Stages<N, INV, CW, T, 1, B, LB>;
+    static constexpr int smem_slots() {
+        return SA<false>::smem(N * CW) > SB<false>::smem(N * CW) ? SA<false>::smem(N * CW) : SB<false>::smem(N * CW);
     }
 };
-using Plan1080 = CtPlan<1080, 8, 5, 3, 3, 3>;
-using Plan1920 = CtPlan<1920, 8, 8, 2, 5, 3>;
-using Plan512 = CtPlan<512, 8, 8, 8>;
-using Plan256 = CtPlan<256, 8, 8, 4>;
+// Row plan: one row per CTA of T threads.
+template <int N_, int T_, int MINB_, class A_, class LA_, class B_, class LB_>
+struct RowPlan {
+    static constexpr int N = N_, T = T_, MINB = MINB_;
+    template <bool INV> using SA = Stages<N, INV, 1, T, 1, A_, LA_>;
+    template <bool INV> using SB = Stages<N, INV, 1, T, 1, B_, LB_>;
+    static constexpr int smem_slots() {
+        return SA<false>::smem(N) > SB<false>::smem(N) ? SA<false>::smem(N) : SB<false>::smem(N);
+    }
+};
 
-// columns: grid (ceil(W/CW), nplanes), CW adjacent columns per CTA
-template <bool INV, class PL, int CW>
-__global__ void __launch_bounds__(256) k_fft_cols_ct(const float2* __restrict__ in, float2* __restrict__ out, int W,
-                                                     const float2* __restrict__ tw_g, float scale) {
-    constexpr int N = PL::n, E = N * CW, EP = padded_len(E);
-    extern __shared__ float2 sm[];
-    float2* A = sm;
-    float2* Bb = sm + EP;
-    float2* tw = sm + 2 * EP;
-    const int col0 = blockIdx.x * CW;
-    const size_t base = (size_t)blockIdx.y * N * W;
-    for (int e = threadIdx.x; e < N; e += blockDim.x) tw[e] = tw_g[e];
-    for (int e = threadIdx.x; e < E; e += blockDim.x) {
-        const int i = e / CW, cc = e % CW, col = col0 + cc;
-        A[pad32(e)] = col < W ? in[base + (size_t)i * W + col] : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    const float2* res = PL::template run<INV, CW, CW, 1>(A, Bb, tw);
-    for (int e = threadIdx.x; e < E; e += blockDim.x) {
-        const int i = e / CW, cc = e % CW, col = col0 + cc;
-        if (col < W) out[base + (size_t)i * W + col] = cscale(res[pad32(e)], scale);
-    }
+using Cols1080 = ColPlan<1080, 8, 480, 2, Seq<12, 10, 9>, Lays<Pad<16, 4>, Pad<160, 1>>, Seq<9, 10, 12>,
+                         Lays<Pad<1, 0>, Pad<160, 10>>>;
+using Cols1920 = ColPlan<1920, 4, 384, 1, Seq<16, 12, 10>, Lays<Pad<16, 1>, Pad<160, 1>>, Seq<10, 12, 16>,
+                         Lays<Pad<80, 4>, Pad<160, 8>>>;
+using Cols512 = ColPlan<512, 16, 512, 2, Seq<8, 8, 8>, Lays<Pad<1, 0>, Pad<1, 0>>, Seq<8, 8, 8>,
+                        Lays<Pad<1, 0>, Pad<1, 0>>>;
+using Cols256 = ColPlan<256, 16, 256, 3, Seq<16, 16>, Lays<Pad<1, 0>>, Seq<16, 16>, Lays<Pad<1, 0>>>;
+
+using Rows1920 = RowPlan<1920, 192, 2, Seq<16, 12, 10>, Lays<Pad<16, 1>, Pad<160, 1>>, Seq<10, 12, 16>,
+                         Lays<Pad<80, 1>, Pad<120, 2>>>;
+using Rows1080 = RowPlan<1080, 128, 4, Seq<12, 10, 9>, Lays<Pad<48, 1>, Pad<120, 4>>, Seq<9, 10, 12>,
+                         Lays<Pad<1, 0>, Pad<1, 0>>>;
+using Rows512 = RowPlan<512, 64, 8, Seq<8, 8, 8>, Lays<Pad<16, 1>, Pad<16, 2>>, Seq<8, 8, 8>,
+                        Lays<Pad<16, 1>, Pad<16, 2>>>;
+using Rows256 = RowPlan<256, 64, 8, Seq<4, 8, 8>, Lays<Pad<16, 1>, Pad<16, 2>>, Seq<8, 8, 4>,
+                        Lays<Pad<16, 1>, Pad<16, 2>>>;
+
+// Loads the first-stage inputs of a column slab (element row j + r M of
+// column t) from global memory; columns at or beyond ncols read as zero.
+template <class S, int CW>
+__device__ __forceinline__ void load_cols(float2 (&v)[S::U][S::RAD], const float2* src, int W, int ncols) {
+    using It = typename S::It;
+    sfor<S::U>([&](auto a) {
+        constexpr int u = HCGS_CI(a);
+        const int t = It::t(u), j = It::j(u);
+        const bool ok = It::valid(u) && t < ncols;
+        sfor<S::RAD>([&](auto b) {
+            constexpr int r = HCGS_CI(b);
+            v[u][r] = ok ? src[(size_t)(j + r * S::M) * W + t] : make_float2(0.f, 0.f);
+        });
+    });
 }
 
-template <bool CONJ, class PL>
-__global__ void __launch_bounds__(512) k_rows_sum_ct(const float2* __restrict__ in, float2* __restrict__ out, int L,
-                                                     int C, int H, const float2* __restrict__ hq,
-                                                     const float2* __restrict__ tw_g) {
-    constexpr int W = PL::n, EP = padded_len(W);
+template <class S>
+__device__ __forceinline__ void load_row(float2 (&v)[S::U][S::RAD], const float2* __restrict__ src) {
+    using It = typename S::It;
+    sfor<S::U>([&](auto a) {
+        constexpr int u = HCGS_CI(a);
+        const int j = It::j(u);
+        const bool ok = It::valid(u);
+        sfor<S::RAD>([&](auto b) {
+            constexpr int r = HCGS_CI(b);
+            v[u][r] = ok ? __ldg(src + j + r * S::M) : make_float2(0.f, 0.f);
+        });
+    });
+}
+
+// outputs of a last stage with U items of radix R: element j + r (N / R)
+template <int N, int NTRANS, int T, class V, class F>
+__device__ __forceinline__ void for_outputs(V& vo, F&& f) {
+    using Sh = Shape<V>;
+    using It = Items<N / Sh::R, NTRANS, T>;
+    sfor<Sh::U>([&](auto a) {
+        constexpr int u = HCGS_CI(a);
+        if (It::valid(u)) {
+            const int j = It::j(u), t = It::t(u);
+            sfor<Sh::R>([&](auto b) {
+                constexpr int r = HCGS_CI(b);
+                f(vo[u][r], j + r * (N / Sh::R), t);
+            });
+        }
+    });
+}
+
+}  // namespace rfft
+
+// columns: grid (ceil(W / CW), nplanes); in == out allowed (each CTA reads its
+// whole slab before it writes)
+template <bool INV, class CP>
+__global__ void __launch_bounds__(CP::T, CP::MINB) k_fft_cols_reg(const float2* in, float2* out, int W,
+                                                                  const float2* __restrict__ tw, float scale) {
+    using namespace rfft;
+    using S = typename CP::template SA<INV>;
     extern __shared__ float2 sm[];
-    float2* A = sm;
-    float2* Bb = sm + EP;
-    float2* acc = sm + 2 * EP;
-    float2* tw = sm + 3 * EP;
+    const int col0 = blockIdx.x * CP::CW, ncols = W - col0;
+    const size_t base = (size_t)blockIdx.y * CP::N * W + col0;
+    float2 v[S::U][S::RAD];
+    load_cols<S, CP::CW>(v, in + base, W, ncols);
+    S::run(v, sm, tw, [&](auto& vo) {
+        for_outputs<CP::N, CP::CW, CP::T>(vo, [&](float2 x, int pos, int t) {
+            if (t < ncols) out[base + (size_t)pos * W + t] = cscale(x, scale);
+        });
+    });
+}
+
+// Column pass of the focal-stack loss, in place on data[nplanes][N][W]:
+//   V = scale * IDFT_cols(data);  I = |V|^2;  d = I - I_gt;
+//   partial loss += d^2;  gV = 4 inv_count d V;  data = DFT_cols(gV).
+template <class CP>
+__global__ void __launch_bounds__(CP::T, CP::MINB)
+    k_cols_focal_loss_reg(float2* data, const float* __restrict__ Igt, float* __restrict__ Iout,
+                          float* __restrict__ partials, int W, const float2* __restrict__ tw, float scale,
+                          float inv_count) {
+    using namespace rfft;
+    using SI = typename CP::template SA<true>;
+    using SF = typename CP::template SB<false>;
+    extern __shared__ float2 sm[];
+    __shared__ float red[32];
+    const int col0 = blockIdx.x * CP::CW, ncols = W - col0;
+    const size_t base = (size_t)blockIdx.y * CP::N * W + col0;
+    float2 v[SI::U][SI::RAD];
+    load_cols<SI, CP::CW>(v, data + base, W, ncols);
+    SI::run(v, sm, tw, [&](auto& vo) {
+        float part = 0.f;
+        for_outputs<CP::N, CP::CW, CP::T>(vo, [&](float2& x, int pos, int t) {
+            float2 g = make_float2(0.f, 0.f);
+            if (t < ncols) {
+                const float2 V = cscale(x, scale);
+                const float I = V.x * V.x + V.y * V.y;
+                const size_t o = base + (size_t)pos * W + t;
+                const float d = I - Igt[o];
+                part += d * d;
+                if (Iout) Iout[o] = I;
+                g = cscale(V, 4.f * inv_count * d);
+            }
+            x = g;
+        });
+        // items outside the transform hold zeros (never read back)
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float s = 0.f;
+            for (int w = 0; w < CP::T / 32; w++) s += red[w];
+            partials[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = s;
+        }
+        static_assert(Shape<decltype(vo)>::R == SF::RAD && Shape<decltype(vo)>::U == SF::U,
+                      "the forward pass must start with the inverse pass's last radix");
+        SF::run(vo, sm, tw, [&](auto& vf) {
+            for_outputs<CP::N, CP::CW, CP::T>(vf, [&](float2 x, int pos, int t) {
+                if (t < ncols) data[base + (size_t)pos * W + t] = x;
+            });
+        });
+    });
+}
+
+// rows: grid (B, H, C) so that consecutive CTAs (views) share the
+// transfer-function rows through L2.
+// out[b][c][i] = IDFT( sum_l Hsel_l * DFT(in[b][l][c][i]) )
+template <bool CONJ, class RP>
+__global__ void __launch_bounds__(RP::T, RP::MINB)
+    k_rows_sum_reg(const float2* __restrict__ in, float2* __restrict__ out, int L, int C, int H,
+                   const float2* __restrict__ hq, const float2* __restrict__ tw) {
+    using namespace rfft;
+    constexpr int W = RP::N, hw2 = W / 2 + 1;
+    using SF = typename RP::template SA<false>;
+    using SI = typename RP::template SB<true>;
+    extern __shared__ float2 sm[];
     const int b = blockIdx.x, i = blockIdx.y, c = blockIdx.z;
     const int ky = mirror(i, H);
-    constexpr int hw2 = W / 2 + 1;
-    for (int j = threadIdx.x; j < W; j += blockDim.x) {
-        tw[j] = tw_g[j];
-        acc[pad32(j)] = make_float2(0.f, 0.f);
-    }
+    float2 acc[SI::U][SI::RAD];
+    sfor<SI::U>([&](auto a) { sfor<SI::RAD>([&](auto r) { acc[HCGS_CI(a)][HCGS_CI(r)] = make_float2(0.f, 0.f); }); });
     for (int l = 0; l < L; l++) {
         const float2* src = in + ((((size_t)b * L + l) * C + c) * H + i) * W;
-        for (int j = threadIdx.x; j < W; j += blockDim.x) A[pad32(j)] = src[j];
-        __syncthreads();
-        const float2* res = PL::template run<false, 1, 1, 0>(A, Bb, tw);
         const float2* hrow = hq + (((size_t)c * L + l) * (H / 2 + 1) + ky) * hw2;
-        for (int j = threadIdx.x; j < W; j += blockDim.x) {
-            float2 h = hrow[mirror(j, W)];
-            if (CONJ) h.y = -h.y;
-            acc[pad32(j)] = cadd(acc[pad32(j)], cmul(res[pad32(j)], h));
-        }
-        __syncthreads();
+        float2 v[SF::U][SF::RAD];
+        load_row<SF>(v, src);
+        SF::run(v, sm, tw, [&](auto& vo) {
+            static_assert(Shape<decltype(vo)>::R == SI::RAD && Shape<decltype(vo)>::U == SI::U,
+                          "the inverse pass must start with the forward pass's last radix");
+            sfor<SI::U>([&](auto a) {
+                constexpr int u = HCGS_CI(a);
+                const int j = SI::It::j(u);
+                if (SI::It::valid(u)) {
+                    sfor<SI::RAD>([&](auto rr) {
+                        constexpr int r = HCGS_CI(rr);
+                        float2 h = __ldg(hrow + mirror(j + r * SI::M, W));
+                        if (CONJ) h.y = -h.y;
+                        acc[u][r] = cadd(acc[u][r], cmul(vo[u][r], h));
+                    });
+                }
+            });
+        });
     }
-    const float2* res = PL::template run<true, 1, 1, 0>(acc, A, tw);
     float2* dst = out + (((size_t)b * C + c) * H + i) * W;
-    for (int j = threadIdx.x; j < W; j += blockDim.x) dst[j] = res[pad32(j)];
+    SI::run(acc, sm, tw, [&](auto& vo) {
+        for_outputs<W, 1, RP::T>(vo, [&](float2 x, int pos, int) { dst[pos] = x; });
+    });
 }
 
-template <bool CONJ, class PL>
-__global__ void __launch_bounds__(512) k_rows_spread_ct(const float2* __restrict__ in, float2* __restrict__ out,
-                                                        int L, int C, int H, const float2* __restrict__ hq,
-                                                        const float2* __restrict__ tw_g) {
-    constexpr int W = PL::n, EP = padded_len(W);
+// out[b][l][c][i] = IDFT( Hsel_l * DFT(in[b][c][i]) )
+template <bool CONJ, class RP>
+__global__ void __launch_bounds__(RP::T, RP::MINB)
+    k_rows_spread_reg(const float2* __restrict__ in, float2* __restrict__ out, int L, int C, int H,
+                      const float2* __restrict__ hq, const float2* __restrict__ tw) {
+    using namespace rfft;
+    constexpr int W = RP::N, hw2 = W / 2 + 1;
+    using SF = typename RP::template SA<false>;
+    using SI = typename RP::template SB<true>;
     extern __shared__ float2 sm[];
-    float2* A = sm;
-    float2* Bb = sm + EP;
-    float2* S = sm + 2 * EP;
-    float2* tw = sm + 3 * EP;
     const int b = blockIdx.x, i = blockIdx.y, c = blockIdx.z;
     const int ky = mirror(i, H);
-    constexpr int hw2 = W / 2 + 1;
-    const float2* src = in + (((size_t)b * C + c) * H + i) * W;
-    for (int j = threadIdx.x; j < W; j += blockDim.x) {
-        tw[j] = tw_g[j];
-        A[pad32(j)] = src[j];
+    float2 spec[SI::U][SI::RAD];
+    {
+        float2 v[SF::U][SF::RAD];
+        load_row<SF>(v, in + (((size_t)b * C + c) * H + i) * W);
+        SF::run(v, sm, tw, [&](auto& vo) {
+            static_assert(Shape<decltype(vo)>::R == SI::RAD && Shape<decltype(vo)>::U == SI::U,
+                          "the inverse pass must start with the forward pass's last radix");
+            sfor<SI::U>([&](auto a) {
+                sfor<SI::RAD>([&](auto r) { spec[HCGS_CI(a)][HCGS_CI(r)] = vo[HCGS_CI(a)][HCGS_CI(r)]; });
+            });
+        });
     }
-    __syncthreads();
-    const float2* spec = PL::template run<false, 1, 1, 0>(A, Bb, tw);
-    for (int j = threadIdx.x; j < W; j += blockDim.x) S[j] = spec[pad32(j)];
-    __syncthreads();
     for (int l = 0; l < L; l++) {
         const float2* hrow = hq + (((size_t)c * L + l) * (H / 2 + 1) + ky) * hw2;
-        for (int j = threadIdx.x; j < W; j += blockDim.x) {
-            float2 h = hrow[mirror(j, W)];
-            if (CONJ) h.y = -h.y;
-            A[pad32(j)] = cmul(S[j], h);
-        }
-        __syncthreads();
-        const float2* res = PL::template run<true, 1, 1, 0>(A, Bb, tw);
+        float2 v[SI::U][SI::RAD];
+        sfor<SI::U>([&](auto a) {
+            constexpr int u = HCGS_CI(a);
+            const int j = SI::It::j(u);
+            const bool ok = SI::It::valid(u);
+            sfor<SI::RAD>([&](auto rr) {
+                constexpr int r = HCGS_CI(rr);
+                float2 h = ok ? __ldg(hrow + mirror(j + r * SI::M, W)) : make_float2(0.f, 0.f);
+                if (CONJ) h.y = -h.y;
+                v[u][r] = cmul(spec[u][r], h);
+            });
+        });
         float2* dst = out + ((((size_t)b * L + l) * C + c) * H + i) * W;
-        for (int j = threadIdx.x; j < W; j += blockDim.x) dst[j] = res[pad32(j)];
-        __syncthreads();
+        SI::run(v, sm, tw, [&](auto& vo) {
+            for_outputs<W, 1, RP::T>(vo, [&](float2 x, int pos, int) { dst[pos] = x; });
+        });
     }
 }
 
@@ -608,19 +924,19 @@ static cudaError_t allow_smem(K kern, size_t bytes) {
     return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <class PL, int CW>
-static hcgs_status fft_cols_ct(hcgs_ctx* ctx, const float2* in, float2* out, int nplanes, int W, bool inverse,
-                               float scale, const float2* tw, cudaStream_t st) {
-    constexpr int N = PL::n;
-    const size_t smem = (2 * (size_t)padded_len(N * CW) + N) * sizeof(float2);
-    dim3 grid((W + CW - 1) / CW, nplanes);
+template <class CP>
+static hcgs_status fft_cols_reg(hcgs_ctx* ctx, const float2* in, float2* out, int nplanes, int W, bool inverse,
+                                float scale, const float2* tw, cudaStream_t st) {
+    const size_t smem = (size_t)CP::smem_slots() * sizeof(float2);
+    const dim3 grid((W + CP::CW - 1) / CP::CW, nplanes);
     if (inverse) {
-        HCGS_CUDA(ctx, allow_smem(k_fft_cols_ct<true, PL, CW>, smem));
-        HCGS_KERNEL(ctx, "k_fft_cols", st, k_fft_cols_ct<true, PL, CW><<<grid, 256, smem, st>>>(in, out, W, tw, scale));
+        HCGS_CUDA(ctx, allow_smem(k_fft_cols_reg<true, CP>, smem));
+        HCGS_KERNEL(ctx, "k_fft_cols", st, k_fft_cols_reg<true, CP><<<grid, CP::T, smem, st>>>(in, out, W, tw, scale));
     } else {
-        HCGS_CUDA(ctx, allow_smem(k_fft_cols_ct<false, PL, CW>, smem));
-        HCGS_KERNEL(ctx, "k_fft_cols", st, k_fft_cols_ct<false, PL, CW><<<grid, 256, smem, st>>>(in, out, W, tw, scale));
+        HCGS_CUDA(ctx, allow_smem(k_fft_cols_reg<false, CP>, smem));
+        HCGS_KERNEL(ctx, "k_fft_cols", st, k_fft_cols_reg<false, CP><<<grid, CP::T, smem, st>>>(in, out, W, tw, scale));
     }
+    HCGS_LAUNCH(ctx, "k_fft_cols");
     return HCGS_OK;
 }
 
@@ -630,10 +946,10 @@ hcgs_status fft_cols(hcgs_ctx* ctx, const float2* in, float2* out, int nplanes, 
     FftPlan* p;
     hcgs_status s = get_plan(ctx, H, &p);
     if (s) return s;
-    if (H == 1080) return fft_cols_ct<Plan1080, 4>(ctx, in, out, nplanes, W, inverse, scale, p->tw, st);
-    if (H == 1920) return fft_cols_ct<Plan1920, 4>(ctx, in, out, nplanes, W, inverse, scale, p->tw, st);
-    if (H == 512) return fft_cols_ct<Plan512, 8>(ctx, in, out, nplanes, W, inverse, scale, p->tw, st);
-    if (H == 256) return fft_cols_ct<Plan256, 8>(ctx, in, out, nplanes, W, inverse, scale, p->tw, st);
+    if (H == 1080) return fft_cols_reg<rfft::Cols1080>(ctx, in, out, nplanes, W, inverse, scale, p->tw, st);
+    if (H == 1920) return fft_cols_reg<rfft::Cols1920>(ctx, in, out, nplanes, W, inverse, scale, p->tw, st);
+    if (H == 512) return fft_cols_reg<rfft::Cols512>(ctx, in, out, nplanes, W, inverse, scale, p->tw, st);
+    if (H == 256) return fft_cols_reg<rfft::Cols256>(ctx, in, out, nplanes, W, inverse, scale, p->tw, st);
     const int cw = col_width(H);
     const size_t smem = (size_t)(2 * cw + 1) * H * sizeof(float2);
     dim3 grid((W + cw - 1) / cw, nplanes);
@@ -648,12 +964,38 @@ hcgs_status fft_cols(hcgs_ctx* ctx, const float2* in, float2* out, int nplanes, 
     return HCGS_OK;
 }
 
+template <class CP>
+static hcgs_status cols_focal_loss_reg(hcgs_ctx* ctx, float2* data, const float* I_gt, float* I_out,
+                                       float* partials, int nplanes, int W, float inv_count, float scale,
+                                       int* nblocks_out, const float2* tw, cudaStream_t st) {
+    const size_t smem = (size_t)CP::smem_slots() * sizeof(float2);
+    const dim3 grid((W + CP::CW - 1) / CP::CW, nplanes);
+    *nblocks_out = grid.x * grid.y;
+    if (!partials) return HCGS_OK;  // size query
+    HCGS_CUDA(ctx, allow_smem(k_cols_focal_loss_reg<CP>, smem));
+    HCGS_KERNEL(ctx, "k_cols_focal_loss", st, k_cols_focal_loss_reg<CP><<<grid, CP::T, smem, st>>>(data, I_gt, I_out, partials, W, tw, scale, inv_count));
+    HCGS_LAUNCH(ctx, "k_cols_focal_loss");
+    return HCGS_OK;
+}
+
 hcgs_status cols_focal_loss(hcgs_ctx* ctx, float2* data, const float* I_gt, float* I_out, float* partials,
                             int nplanes, int H, int W, float inv_count, float scale, int* nblocks_out,
                             cudaStream_t st) {
     FftPlan* p;
     hcgs_status s = get_plan(ctx, H, &p);
     if (s) return s;
+    if (H == 1080)
+        return cols_focal_loss_reg<rfft::Cols1080>(ctx, data, I_gt, I_out, partials, nplanes, W, inv_count, scale,
+                                                   nblocks_out, p->tw, st);
+    if (H == 1920)
+        return cols_focal_loss_reg<rfft::Cols1920>(ctx, data, I_gt, I_out, partials, nplanes, W, inv_count, scale,
+                                                   nblocks_out, p->tw, st);
+    if (H == 512)
+        return cols_focal_loss_reg<rfft::Cols512>(ctx, data, I_gt, I_out, partials, nplanes, W, inv_count, scale,
+                                                  nblocks_out, p->tw, st);
+    if (H == 256)
+        return cols_focal_loss_reg<rfft::Cols256>(ctx, data, I_gt, I_out, partials, nplanes, W, inv_count, scale,
+                                                  nblocks_out, p->tw, st);
     const int cw = col_width(H);
     const size_t smem = (size_t)(2 * cw + 1) * H * sizeof(float2);
     dim3 grid((W + cw - 1) / cw, nplanes);
@@ -671,40 +1013,40 @@ static int row_threads(int W) {
     return t < 32 ? 32 : (t > 512 ? 512 : t);
 }
 
-template <class PL>
-static hcgs_status rows_ct(hcgs_ctx* ctx, bool sum, const float2* in, float2* out, int B, int L, int C, int H,
-                           const float2* hq, bool conjH, const float2* tw, cudaStream_t st) {
-    constexpr int W = PL::n;
-    const size_t smem = (3 * (size_t)padded_len(W) + W) * sizeof(float2);
-    const int thr = row_threads(W);
-    dim3 grid(B, H, C);
+template <class RP>
+static hcgs_status rows_reg(hcgs_ctx* ctx, bool sum, const float2* in, float2* out, int B, int L, int C, int H,
+                            const float2* hq, bool conjH, const float2* tw, cudaStream_t st) {
+    const size_t smem = (size_t)RP::smem_slots() * sizeof(float2);
+    const dim3 grid(B, H, C);
     if (sum) {
         if (conjH) {
-            HCGS_CUDA(ctx, allow_smem(k_rows_sum_ct<true, PL>, smem));
-            HCGS_KERNEL(ctx, "k_rows_sum", st, k_rows_sum_ct<true, PL><<<grid, thr, smem, st>>>(in, out, L, C, H, hq, tw));
+            HCGS_CUDA(ctx, allow_smem(k_rows_sum_reg<true, RP>, smem));
+            HCGS_KERNEL(ctx, "k_rows_sum", st, k_rows_sum_reg<true, RP><<<grid, RP::T, smem, st>>>(in, out, L, C, H, hq, tw));
         } else {
-            HCGS_CUDA(ctx, allow_smem(k_rows_sum_ct<false, PL>, smem));
-            HCGS_KERNEL(ctx, "k_rows_sum", st, k_rows_sum_ct<false, PL><<<grid, thr, smem, st>>>(in, out, L, C, H, hq, tw));
+            HCGS_CUDA(ctx, allow_smem(k_rows_sum_reg<false, RP>, smem));
+            HCGS_KERNEL(ctx, "k_rows_sum", st, k_rows_sum_reg<false, RP><<<grid, RP::T, smem, st>>>(in, out, L, C, H, hq, tw));
         }
+        HCGS_LAUNCH(ctx, "k_rows_sum");
     } else {
         if (conjH) {
-            HCGS_CUDA(ctx, allow_smem(k_rows_spread_ct<true, PL>, smem));
-            HCGS_KERNEL(ctx, "k_rows_spread", st, k_rows_spread_ct<true, PL><<<grid, thr, smem, st>>>(in, out, L, C, H, hq, tw));
+            HCGS_CUDA(ctx, allow_smem(k_rows_spread_reg<true, RP>, smem));
+            HCGS_KERNEL(ctx, "k_rows_spread", st, k_rows_spread_reg<true, RP><<<grid, RP::T, smem, st>>>(in, out, L, C, H, hq, tw));
         } else {
-            HCGS_CUDA(ctx, allow_smem(k_rows_spread_ct<false, PL>, smem));
-            HCGS_KERNEL(ctx, "k_rows_spread", st, k_rows_spread_ct<false, PL><<<grid, thr, smem, st>>>(in, out, L, C, H, hq, tw));
+            HCGS_CUDA(ctx, allow_smem(k_rows_spread_reg<false, RP>, smem));
+            HCGS_KERNEL(ctx, "k_rows_spread", st, k_rows_spread_reg<false, RP><<<grid, RP::T, smem, st>>>(in, out, L, C, H, hq, tw));
         }
+        HCGS_LAUNCH(ctx, "k_rows_spread");
     }
     return HCGS_OK;
 }
 
-static bool rows_ct_dispatch(hcgs_ctx* ctx, bool sum, const float2* in, float2* out, int B, int L, int C, int H,
-                             int W, const float2* hq, bool conjH, const float2* tw, cudaStream_t st,
-                             hcgs_status* res) {
-    if (W == 1920) { *res = rows_ct<Plan1920>(ctx, sum, in, out, B, L, C, H, hq, conjH, tw, st); return true; }
-    if (W == 1080) { *res = rows_ct<Plan1080>(ctx, sum, in, out, B, L, C, H, hq, conjH, tw, st); return true; }
-    if (W == 512) { *res = rows_ct<Plan512>(ctx, sum, in, out, B, L, C, H, hq, conjH, tw, st); return true; }
-    if (W == 256) { *res = rows_ct<Plan256>(ctx, sum, in, out, B, L, C, H, hq, conjH, tw, st); return true; }
+static bool rows_reg_dispatch(hcgs_ctx* ctx, bool sum, const float2* in, float2* out, int B, int L, int C, int H,
+                              int W, const float2* hq, bool conjH, const float2* tw, cudaStream_t st,
+                              hcgs_status* res) {
+    if (W == 1920) { *res = rows_reg<rfft::Rows1920>(ctx, sum, in, out, B, L, C, H, hq, conjH, tw, st); return true; }
+    if (W == 1080) { *res = rows_reg<rfft::Rows1080>(ctx, sum, in, out, B, L, C, H, hq, conjH, tw, st); return true; }
+    if (W == 512) { *res = rows_reg<rfft::Rows512>(ctx, sum, in, out, B, L, C, H, hq, conjH, tw, st); return true; }
+    if (W == 256) { *res = rows_reg<rfft::Rows256>(ctx, sum, in, out, B, L, C, H, hq, conjH, tw, st); return true; }
     return false;
 }
 
@@ -713,7 +1055,7 @@ hcgs_status rows_sum(hcgs_ctx* ctx, const float2* in, float2* out, int B, int L,
     FftPlan* p;
     hcgs_status s = get_plan(ctx, W, &p);
     if (s) return s;
-    if (rows_ct_dispatch(ctx, true, in, out, B, L, C, H, W, hq, conjH, p->tw, st, &s)) return s;
+    if (rows_reg_dispatch(ctx, true, in, out, B, L, C, H, W, hq, conjH, p->tw, st, &s)) return s;
     const size_t smem = 4 * (size_t)W * sizeof(float2);
     dim3 grid(B, H, C);
     if (conjH) {
@@ -732,7 +1074,7 @@ hcgs_status rows_spread(hcgs_ctx* ctx, const float2* in, float2* out, int B, int
     FftPlan* p;
     hcgs_status s = get_plan(ctx, W, &p);
     if (s) return s;
-    if (rows_ct_dispatch(ctx, false, in, out, B, L, C, H, W, hq, conjH, p->tw, st, &s)) return s;
+    if (rows_reg_dispatch(ctx, false, in, out, B, L, C, H, W, hq, conjH, p->tw, st, &s)) return s;
     const size_t smem = 4 * (size_t)W * sizeof(float2);
     dim3 grid(B, H, C);
     if (conjH) {

@@ -40,7 +40,7 @@ def _rand_planes(B, L, C, H, W, seed):
 # propagation
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("H,W,L,C,B", [(256, 256, 2, 1, 1), (120, 200, 3, 2, 2), (45, 96, 1, 3, 1),
-                                       (1080, 1920, 2, 1, 1)])
+                                       (1080, 1920, 2, 1, 1), (512, 512, 3, 1, 2), (1920, 1080, 2, 1, 1)])
 def test_asm_forward_recording(P, ctx, H, W, L, C, B):
     wl = S.WAVELENGTHS_RGB[:C] if C > 1 else (515e-9,)
     z = tuple(np.linspace(0.0, 10e-3, L))
@@ -54,7 +54,8 @@ def test_asm_forward_recording(P, ctx, H, W, L, C, B):
         assert rel(got[b], ref) < 1e-5, rel(got[b], ref)
 
 
-@pytest.mark.parametrize("H,W,L,C,B", [(256, 256, 2, 1, 1), (120, 200, 3, 2, 2)])
+@pytest.mark.parametrize("H,W,L,C,B", [(256, 256, 2, 1, 1), (120, 200, 3, 2, 2), (1080, 1920, 2, 1, 1),
+                                       (512, 512, 2, 1, 2), (1920, 1080, 2, 1, 1)])
 def test_asm_inverse_and_adjoint(P, ctx, H, W, L, C, B):
     wl = S.WAVELENGTHS_RGB[:C] if C > 1 else (515e-9,)
     z = tuple(np.linspace(0.0, 8e-3, L))
@@ -246,8 +247,9 @@ def test_autograd_render_matches_abi(P, ctx):
 # ---------------------------------------------------------------------------
 # training-step pieces
 # ---------------------------------------------------------------------------
-def test_focal_stack_loss(P, ctx):
-    o = S.Optics(64, 80, (639e-9, 515e-9), (0.0, 2e-3, 6e-3))
+@pytest.mark.parametrize("H,W,C", [(64, 80, 2), (256, 256, 2), (512, 512, 1), (1080, 1920, 1), (1920, 1080, 1)])
+def test_focal_stack_loss(P, ctx, H, W, C):
+    o = S.Optics(H, W, (639e-9, 515e-9)[:C], (0.0, 2e-3, 6e-3))
     Pn = S.random_complex((1, o.C, o.H, o.W), seed=4)
     Igt = S.random_real((1, o.L, o.C, o.H, o.W), seed=5)
     loss = torch.zeros(1, dtype=torch.float32, device="cuda")
