@@ -99,7 +99,7 @@ __device__ __forceinline__ bool strip_hits(float4 r0, float Cc, float o, float x
 // Returns the number kept.
 template <int NR>
 __device__ __forceinline__ int stage_warp(const RasterArgs& a, size_t vN, uint32_t beg, uint32_t p0, uint32_t n,
-                                          int tx, int ty, float sx0, float sy0, float4 (*wrec)[NR],
+                                          int tx, int ty, float sx0, float sy0, float4 (*wrec)[NR + 1],
                                           uint32_t* wpos, uint32_t* wid) {
     const int lane = threadIdx.x & 31;
     const uint32_t p = p0 + (uint32_t)lane;
@@ -126,6 +126,9 @@ __device__ __forceinline__ int stage_warp(const RasterArgs& a, size_t vN, uint32
         wrec[slot][1] = q1;
 #pragma unroll
         for (int k = 2; k < NR; k++) wrec[slot][k] = r[k];
+        // base-2 exponent of o G: o G = 2^(A' dx^2 + B' dx dy + C' dy^2 + log2 o)
+        constexpr float L2E = 1.4426950408889634f;
+        wrec[slot][NR] = make_float4(-0.5f * L2E * q0.z, -L2E * q0.w, -0.5f * L2E * q1.x, log2f(q1.y));
         wpos[slot] = p;
         wid[slot] = s;
     }
@@ -141,20 +144,19 @@ __device__ __forceinline__ float ex2_approx(float x) {
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 
 // The thread's two pixels (same column, rows y0 and y0 + 2) against one
-// Gaussian record, as packed FP32x2 arithmetic: d = pixel - mu,
-// power = 1/2 (A dx^2 + C dy^2) + B dx dy (Supp. D.3), G = exp(-power),
-// o G and alpha = min(alpha_max, o G).  Shared by forward and adjoint, so
-// both take identical decisions.
-__device__ __forceinline__ void eval_pair(float px, float2 py2, float4 r0, float Cc, float o, float amax,
-                                          float& dx, float2& dy2, float2& G2, float2& og2, float2& a2) {
-    dx = __fsub_rn(px, r0.x);
-    dy2 = __fadd2_rn(py2, f2(-r0.y));
-    const float adx2 = __fmul_rn(r0.z, __fmul_rn(dx, dx));
-    float2 p = __fmul2_rn(f2(0.5f), __ffma2_rn(f2(Cc), __fmul2_rn(dy2, dy2), f2(adx2)));
-    p = __ffma2_rn(f2(__fmul_rn(r0.w, dx)), dy2, p);
-    const float2 e = __fmul2_rn(p, f2(-1.4426950408889634f));  // exp(-p) = 2^(-p log2 e)
-    G2 = make_float2(ex2_approx(e.x), ex2_approx(e.y));
-    og2 = __fmul2_rn(f2(o), G2);
+// Gaussian record, as packed FP32x2 arithmetic.  With d = pixel - mu the
+// exponent term is power = 1/2 (A dx^2 + C dy^2) + B dx dy (Supp. D.3) and
+// o G = o exp(-power) = 2^(A' dx^2 + B' dx dy + C' dy^2 + log2 o), with the
+// coefficients A' B' C' log2 o prepared once per staged entry (k) and the
+// dx terms once per entry and thread (t0 = A' dx^2 + log2 o, bdx = B' dx);
+// alpha = min(alpha_max, o G).  Shared by forward and adjoint, so both take
+// identical decisions.
+__device__ __forceinline__ void eval_pair(float2 py2, float my, float4 k, float t0, float bdx, float amax,
+                                          float2& dy2, float2& og2, float2& a2) {
+    dy2 = __fadd2_rn(py2, f2(-my));
+    float2 e = __ffma2_rn(f2(bdx), dy2, f2(t0));
+    e = __ffma2_rn(__fmul2_rn(f2(k.z), dy2), dy2, e);
+    og2 = make_float2(ex2_approx(e.x), ex2_approx(e.y));
     a2 = make_float2(fminf(amax, og2.x), fminf(amax, og2.y));
 }
 
@@ -164,9 +166,8 @@ __device__ __forceinline__ void eval_pair(float px, float2 py2, float4 r0, float
 // footprint's normalised frame, u = dx sqrt(A), v = dy sqrt(C),
 // q = u^2 + 2 rho u v + v^2 with rho = B / sqrt(A C) in (-1, 1), all O(1)
 // inside the support.  Accumulation stays FP32.
-__device__ __forceinline__ void eval_pair_h(float px, float2 py2, float4 r0, float Cc, float o, float amax,
-                                            float& dx, float2& dy2, float2& G2, float2& og2, float2& a2) {
-    dx = __fsub_rn(px, r0.x);
+__device__ __forceinline__ void eval_pair_h(float dx, float2 py2, float4 r0, float Cc, float o, float amax,
+                                            float2& dy2, float2& og2, float2& a2) {
     dy2 = __fadd2_rn(py2, f2(-r0.y));
     const float sa = sqrtf(r0.z), sc = sqrtf(Cc);
     const float rho2 = 2.f * r0.w / (sa * sc);
@@ -175,16 +176,29 @@ __device__ __forceinline__ void eval_pair_h(float px, float2 py2, float4 r0, flo
     __half2 q = __hfma2(v, v, __hmul2(u, u));
     q = __hfma2(__float2half2_rn(rho2), __hmul2(u, v), q);
     const __half2 e = __hmul2(q, __float2half2_rn(-0.72134752044448170f));  // -log2(e) / 2
-    G2 = __half22float2(h2exp2(e));
+    const float2 G2 = __half22float2(h2exp2(e));
     og2 = __fmul2_rn(f2(o), G2);
     a2 = make_float2(fminf(amax, og2.x), fminf(amax, og2.y));
 }
 
+// Per-entry, per-thread part of the evaluation (the pixel column is fixed):
+// dx and, for the FP32 tier, t0 = A' dx^2 + log2 o and bdx = B' dx.
+struct EntryX {
+    float dx, t0, bdx;
+};
+__device__ __forceinline__ EntryX entry_x(float px, float4 r0, float4 k) {
+    EntryX x;
+    x.dx = __fsub_rn(px, r0.x);
+    x.t0 = __fmaf_rn(k.x, __fmul_rn(x.dx, x.dx), k.w);
+    x.bdx = __fmul_rn(k.y, x.dx);
+    return x;
+}
+
 template <bool H16>
-__device__ __forceinline__ void eval_tier(float px, float2 py2, float4 r0, float Cc, float o, float amax, float& dx,
-                                          float2& dy2, float2& G2, float2& og2, float2& a2) {
-    if (H16) eval_pair_h(px, py2, r0, Cc, o, amax, dx, dy2, G2, og2, a2);
-    else eval_pair(px, py2, r0, Cc, o, amax, dx, dy2, G2, og2, a2);
+__device__ __forceinline__ void eval_tier(const EntryX& x, float2 py2, float4 r0, float4 r1, float4 k, float amax,
+                                          float2& dy2, float2& og2, float2& a2) {
+    if (H16) eval_pair_h(x.dx, py2, r0, r1.x, r1.y, amax, dy2, og2, a2);
+    else eval_pair(py2, r0.y, k, x.t0, x.bdx, amax, dy2, og2, a2);
 }
 
 // Warp reduce-scatter of 16 values: afterwards lanes 2i and 2i+1 both hold the
@@ -205,6 +219,8 @@ __device__ __forceinline__ float warp_reduce_scatter16(float (&v)[16], int lane)
 
 // Forward step of a pixel pair that takes it (c0/c1) for one record: a pixel
 // that does not take it gets alpha 0 (no add, T unchanged).
+// Forward step of a pixel pair that takes it (c0/c1) for one record: a pixel
+// that does not take it gets alpha 0 (no add, T unchanged).
 template <int C>
 __device__ __forceinline__ void fwd_pair(const float4* rec, float2 a2, bool c0, bool c1, float2& T2,
                                          float2 (&accX)[C], float2 (&accY)[C]) {
@@ -216,23 +232,18 @@ __device__ __forceinline__ void fwd_pair(const float4* rec, float2 a2, bool c0, 
         accX[c] = __ffma2_rn(f2(w.x), wt, accX[c]);
         accY[c] = __ffma2_rn(f2(w.y), wt, accY[c]);
     }
-    T2 = __fmul2_rn(T2, __fadd2_rn(f2(1.f), make_float2(-al.x, -al.y)));
+    T2 = __fadd2_rn(T2, make_float2(-wt.x, -wt.y));  // T (1 - alpha)
 }
 
-__device__ __forceinline__ void book(bool c, float T, float teps, uint32_t pos, int& nc, uint32_t& last, bool& d) {
-    if (c) {
-        nc++;
-        last = pos + 1;
-        if (T < teps) d = true;
-    }
-}
-
-template <int C, bool H16>
+// A pixel is still compositing while T >= T_eps (T only changes when the
+// pixel takes a step, so this is the "stop once T < T_eps" rule); pixels
+// outside the image start with T = 0.
+template <int C, bool H16, bool NCOUNT>
 __global__ void __launch_bounds__(RT, 6) k_raster_fwd(RasterArgs a, float2* __restrict__ U, float* __restrict__ Tsave,
                                                    uint32_t* __restrict__ lastsave, float* __restrict__ Tout,
                                                    int32_t* __restrict__ ncout) {
     constexpr int NR = C <= 1 ? 2 : (C <= 3 ? 3 : 4);
-    __shared__ float4 srec[RWARPS][32][NR];
+    __shared__ float4 srec[RWARPS][32][NR + 1];
     __shared__ uint32_t spos[RWARPS][32], sid[RWARPS][32];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int reg = blockIdx.x, l = blockIdx.y, v = blockIdx.z;
@@ -240,46 +251,46 @@ __global__ void __launch_bounds__(RT, 6) k_raster_fwd(RasterArgs a, float2* __re
     const int px = tx * TILE + (lane & 15);
     const int sy = ty * TILE + 8 * (warp & 1);       // this warp's 16 x 8 strip starts at row sy
     const int py = sy + (lane >> 4);                 // rows py, py + 2, py + 4, py + 6
-    bool in[4], d[4];
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-        in[q] = px < a.W && py + 2 * q < a.H;
-        d[q] = !in[q];
-    }
+    const bool colin = px < a.W;
     const float sx0 = (float)(tx * TILE), sy0 = (float)sy;
     const uint32_t gb = ((uint32_t)(v * a.L + l) * a.ctY + ty / COARSE) * a.ctX + tx / COARSE;
     const uint32_t beg = a.off[gb], n = a.off[gb + 1] - beg;
     const size_t vN = (size_t)v * a.N;
     const float fpx = (float)px;
+    const float teps = a.teps;
     const float2 pyA = make_float2((float)py, (float)(py + 2)), pyB = make_float2((float)(py + 4), (float)(py + 6));
-    float2 TA = f2(1.f), TB = f2(1.f);
+    float2 TA = make_float2(colin && py < a.H ? 1.f : 0.f, colin && py + 2 < a.H ? 1.f : 0.f);
+    float2 TB = make_float2(colin && py + 4 < a.H ? 1.f : 0.f, colin && py + 6 < a.H ? 1.f : 0.f);
     float2 aAX[C], aAY[C], aBX[C], aBY[C];
 #pragma unroll
     for (int c = 0; c < C; c++) aAX[c] = aAY[c] = aBX[c] = aBY[c] = f2(0.f);
     uint32_t last[4] = {0, 0, 0, 0};
     int nc[4] = {0, 0, 0, 0};
     for (uint32_t p0 = 0; p0 < n; p0 += 32) {
-        if (__all_sync(0xffffffffu, d[0] && d[1] && d[2] && d[3])) break;
+        const bool live = TA.x >= teps || TA.y >= teps || TB.x >= teps || TB.y >= teps;
+        if (!__any_sync(0xffffffffu, live)) break;
         const int nh = stage_warp<NR>(a, vN, beg, p0, n, tx, ty, sx0, sy0, srec[warp], spos[warp], sid[warp]);
         for (int k = 0; k < nh; k++) {
             const float4* rec = srec[warp][k];
-            const float4 r0 = rec[0], r1 = rec[1];
-            const uint32_t pos = spos[warp][k];
-            float dxA, dxB;
-            float2 dyA, GA, ogA, aA, dyB, GB, ogB, aB;
-            eval_tier<H16>(fpx, pyA, r0, r1.x, r1.y, a.amax, dxA, dyA, GA, ogA, aA);
-            eval_tier<H16>(fpx, pyB, r0, r1.x, r1.y, a.amax, dxB, dyB, GB, ogB, aB);
-            const bool c0 = !d[0] && aA.x >= a.amin, c1 = !d[1] && aA.y >= a.amin;
-            const bool c2 = !d[2] && aB.x >= a.amin, c3 = !d[3] && aB.y >= a.amin;
+            const float4 r0 = rec[0], r1 = rec[1], kk = rec[NR];
+            const uint32_t pos1 = spos[warp][k] + 1u;
+            const EntryX x = entry_x(fpx, r0, kk);
+            float2 dyA, ogA, aA, dyB, ogB, aB;
+            eval_tier<H16>(x, pyA, r0, r1, kk, a.amax, dyA, ogA, aA);
+            eval_tier<H16>(x, pyB, r0, r1, kk, a.amax, dyB, ogB, aB);
+            const bool c0 = TA.x >= teps && aA.x >= a.amin, c1 = TA.y >= teps && aA.y >= a.amin;
+            const bool c2 = TB.x >= teps && aB.x >= a.amin, c3 = TB.y >= teps && aB.y >= a.amin;
             if (c0 || c1) {
                 fwd_pair<C>(rec, aA, c0, c1, TA, aAX, aAY);
-                book(c0, TA.x, a.teps, pos, nc[0], last[0], d[0]);
-                book(c1, TA.y, a.teps, pos, nc[1], last[1], d[1]);
+                last[0] = c0 ? pos1 : last[0];
+                last[1] = c1 ? pos1 : last[1];
+                if (NCOUNT) { nc[0] += c0; nc[1] += c1; }
             }
             if (c2 || c3) {
                 fwd_pair<C>(rec, aB, c2, c3, TB, aBX, aBY);
-                book(c2, TB.x, a.teps, pos, nc[2], last[2], d[2]);
-                book(c3, TB.y, a.teps, pos, nc[3], last[3], d[3]);
+                last[2] = c2 ? pos1 : last[2];
+                last[3] = c3 ? pos1 : last[3];
+                if (NCOUNT) { nc[2] += c2; nc[3] += c3; }
             }
         }
         __syncwarp();
@@ -288,7 +299,7 @@ __global__ void __launch_bounds__(RT, 6) k_raster_fwd(RasterArgs a, float2* __re
     const size_t HW = (size_t)a.H * a.W;
 #pragma unroll
     for (int q = 0; q < 4; q++) {
-        if (!in[q]) continue;
+        if (!(colin && py + 2 * q < a.H)) continue;
         const size_t pix = (size_t)(py + 2 * q) * a.W + px;
         const float T = q == 0 ? TA.x : q == 1 ? TA.y : q == 2 ? TB.x : TB.y;
 #pragma unroll
@@ -302,7 +313,7 @@ __global__ void __launch_bounds__(RT, 6) k_raster_fwd(RasterArgs a, float2* __re
         Tsave[plane * HW + pix] = T;
         lastsave[plane * HW + pix] = last[q];
         if (Tout) Tout[plane * HW + pix] = T;
-        if (ncout) ncout[plane * HW + pix] = nc[q];
+        if (NCOUNT) ncout[plane * HW + pix] = nc[q];
     }
 }
 
@@ -318,14 +329,14 @@ __device__ __forceinline__ float rcp_approx(float x) {
 // S_k = sum_{m>k} w_m alpha_m T_m.  Since g is fixed per pixel, only the
 // scalar B = sum_c Re(conj(g_c) S_c) is carried: dL/dalpha_k = T_k A_k -
 // B / (1 - alpha_k) and B <- B + alpha_k T_k A_k, A_k = sum_c Re(conj(g_c) w_kc).
-// Adds the pair's dL/d(mu 0-1, conic 2-4, o 5, w 6..) to the packed
-// accumulators gl (one lane per pixel; the halves are summed once per entry).
-// The reciprocal of 1 - alpha only scales gradients (no decision depends on
-// it), so the hardware approximation is used.
-template <int C>
-__device__ __forceinline__ void bwd_pair(const float4* rec, float dx, float2 dy2, float2 G2, float2 og2, float2 a2,
-                                         bool c0, bool c1, float amax, float2& T2, float2& B2,
-                                         const float2 (&gX)[C], const float2 (&gY)[C], float2 (&gl)[14]) {
+// Adds the pair's dL/d(mu 0-1, conic 2-4), o dL/do (5) and dL/dw (6..) to the
+// packed accumulators gl (one lane per pixel; the halves are summed once per
+// entry).  The reciprocal of 1 - alpha only scales gradients (no decision
+// depends on it), so the hardware approximation is used.
+template <int C, bool FIRST>
+__device__ __forceinline__ void bwd_pair(const float4* rec, float dx, float2 dy2, float2 og2, float2 a2, bool c0,
+                                         bool c1, float amax, float2& T2, float2& B2, const float2 (&gX)[C],
+                                         const float2 (&gY)[C], float2 (&gl)[14]) {
     const float4 r0 = rec[0], r1 = rec[1];
     const float2 al = make_float2(c0 ? a2.x : 0.f, c1 ? a2.y : 0.f);
     const float2 om = __fadd2_rn(f2(1.f), make_float2(-al.x, -al.y));
@@ -337,34 +348,44 @@ __device__ __forceinline__ void bwd_pair(const float4* rec, float dx, float2 dy2
     for (int c = 0; c < C; c++) {
         const float2 w = RecW<C>::get(rec, c);
         Ak = __ffma2_rn(gX[c], f2(w.x), __ffma2_rn(gY[c], f2(w.y), Ak));
-        gl[6 + 2 * c] = __ffma2_rn(gX[c], aT, gl[6 + 2 * c]);
-        gl[7 + 2 * c] = __ffma2_rn(gY[c], aT, gl[7 + 2 * c]);
+        gl[6 + 2 * c] = FIRST ? __fmul2_rn(gX[c], aT) : __ffma2_rn(gX[c], aT, gl[6 + 2 * c]);
+        gl[7 + 2 * c] = FIRST ? __fmul2_rn(gY[c], aT) : __ffma2_rn(gY[c], aT, gl[7 + 2 * c]);
     }
     const float2 dLda = __ffma2_rn(Tk, Ak, __fmul2_rn(make_float2(-iom.x, -iom.y), B2));
     B2 = __ffma2_rn(aT, Ak, B2);
     T2 = Tk;
     // a clamped alpha (o G > alpha_max) is flat in o G
     const float2 dLa = make_float2(c0 && og2.x <= amax ? dLda.x : 0.f, c1 && og2.y <= amax ? dLda.y : 0.f);
-    const float2 dLdpn = __fmul2_rn(dLa, og2);  // -dL/dpower
-    gl[5] = __ffma2_rn(dLa, G2, gl[5]);
+    const float2 dLdpn = __fmul2_rn(dLa, og2);  // -dL/dpower = o dL/do
     // power = 1/2 (A dx^2 + 2 B dx dy + C dy^2), d = pixel - mu
     const float2 q0 = __ffma2_rn(f2(r0.w), dy2, f2(__fmul_rn(r0.z, dx)));  // A dx + B dy
     const float2 q1 = __ffma2_rn(f2(r1.x), dy2, f2(__fmul_rn(r0.w, dx)));  // B dx + C dy
-    gl[0] = __ffma2_rn(dLdpn, q0, gl[0]);
-    gl[1] = __ffma2_rn(dLdpn, q1, gl[1]);
     const float2 pdy = __fmul2_rn(dLdpn, dy2);
-    gl[2] = __ffma2_rn(f2(-0.5f * dx * dx), dLdpn, gl[2]);
-    gl[3] = __ffma2_rn(f2(-dx), pdy, gl[3]);
-    gl[4] = __ffma2_rn(__fmul2_rn(f2(-0.5f), dy2), pdy, gl[4]);
+    const float2 hdy = __fmul2_rn(f2(-0.5f), dy2);
+    if (FIRST) {
+        gl[5] = dLdpn;
+        gl[0] = __fmul2_rn(dLdpn, q0);
+        gl[1] = __fmul2_rn(dLdpn, q1);
+        gl[2] = __fmul2_rn(f2(-0.5f * dx * dx), dLdpn);
+        gl[3] = __fmul2_rn(f2(-dx), pdy);
+        gl[4] = __fmul2_rn(hdy, pdy);
+    } else {
+        gl[5] = __fadd2_rn(dLdpn, gl[5]);
+        gl[0] = __ffma2_rn(dLdpn, q0, gl[0]);
+        gl[1] = __ffma2_rn(dLdpn, q1, gl[1]);
+        gl[2] = __ffma2_rn(f2(-0.5f * dx * dx), dLdpn, gl[2]);
+        gl[3] = __ffma2_rn(f2(-dx), pdy, gl[3]);
+        gl[4] = __ffma2_rn(hdy, pdy, gl[4]);
+    }
 }
 
 template <int C, bool H16>
-__global__ void __launch_bounds__(RT, 4) k_raster_bwd(RasterArgs a, const float* __restrict__ Tsave,
+__global__ void __launch_bounds__(RT, 5) k_raster_bwd(RasterArgs a, const float* __restrict__ Tsave,
                                                    const uint32_t* __restrict__ lastsave,
                                                    const float2* __restrict__ gU, float* __restrict__ g2d) {
     constexpr int NR = C <= 1 ? 2 : (C <= 3 ? 3 : 4);
     constexpr int G = 6 + 2 * C;
-    __shared__ float4 srec[RWARPS][32][NR];
+    __shared__ float4 srec[RWARPS][32][NR + 1];
     __shared__ uint32_t spos[RWARPS][32], sid[RWARPS][32];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int reg = blockIdx.x, l = blockIdx.y, v = blockIdx.z;
@@ -414,25 +435,32 @@ __global__ void __launch_bounds__(RT, 4) k_raster_bwd(RasterArgs a, const float*
         for (int k = nh - 1; k >= 0; k--) {  // back-to-front over the visiting order
             const float4* rec = srec[warp][k];
             const uint32_t pos = spos[warp][k];
-            float2 gl2[14];
-#pragma unroll
-            for (int e = 0; e < 14; e++) gl2[e] = f2(0.f);
-            const float4 r0 = rec[0], r1 = rec[1];
-            float dxA, dxB;
-            float2 dyA, GA, ogA, aA, dyB, GB, ogB, aB;
-            eval_tier<H16>(fpx, pyA, r0, r1.x, r1.y, a.amax, dxA, dyA, GA, ogA, aA);
-            eval_tier<H16>(fpx, pyB, r0, r1.x, r1.y, a.amax, dxB, dyB, GB, ogB, aB);
+            const float4 r0 = rec[0], r1 = rec[1], kk = rec[NR];
+            const EntryX x = entry_x(fpx, r0, kk);
+            float2 dyA, ogA, aA, dyB, ogB, aB;
+            eval_tier<H16>(x, pyA, r0, r1, kk, a.amax, dyA, ogA, aA);
+            eval_tier<H16>(x, pyB, r0, r1, kk, a.amax, dyB, ogB, aB);
             const bool c0 = pos < last[0] && aA.x >= a.amin, c1 = pos < last[1] && aA.y >= a.amin;
             const bool c2 = pos < last[2] && aB.x >= a.amin, c3 = pos < last[3] && aB.y >= a.amin;
-            if (c0 || c1) bwd_pair<C>(rec, dxA, dyA, GA, ogA, aA, c0, c1, a.amax, TA, BA, gAX, gAY, gl2);
-            if (c2 || c3) bwd_pair<C>(rec, dxB, dyB, GB, ogB, aB, c2, c3, a.amax, TB, BB, gBX, gBY, gl2);
-            if (__any_sync(0xffffffffu, c0 || c1 || c2 || c3)) {
+            const bool anyA = __any_sync(0xffffffffu, c0 || c1), anyB = __any_sync(0xffffffffu, c2 || c3);
+            if (anyA || anyB) {
+                // warp-uniform: pixels that did not take the step carry alpha 0
+                // through the pair (T and B unchanged, zero gradient)
+                float2 gl2[14];
+                if (anyA) {
+                    bwd_pair<C, true>(rec, x.dx, dyA, ogA, aA, c0, c1, a.amax, TA, BA, gAX, gAY, gl2);
+                    if (anyB) bwd_pair<C, false>(rec, x.dx, dyB, ogB, aB, c2, c3, a.amax, TB, BB, gBX, gBY, gl2);
+                } else {
+                    bwd_pair<C, true>(rec, x.dx, dyB, ogB, aB, c2, c3, a.amax, TB, BB, gBX, gBY, gl2);
+                }
                 float gl[16];
 #pragma unroll
                 for (int e = 0; e < 16; e++) gl[e] = e < 6 + 2 * C ? gl2[e].x + gl2[e].y : 0.f;
                 const float sum = warp_reduce_scatter16(gl, lane);
                 const int idx = lane >> 1;
-                if (!(lane & 1) && idx < G) atomicAdd(g2d + (vN + sid[warp][k]) * G + idx, sum);
+                // slot 5 holds o dL/do (1/o only scales a gradient: approximate)
+                const float val = idx == 5 ? sum * rcp_approx(r1.y) : sum;
+                if (!(lane & 1) && idx < G) atomicAdd(g2d + (vN + sid[warp][k]) * G + idx, val);
             }
         }
         __syncwarp();
@@ -451,8 +479,13 @@ hcgs_status raster_forward(hcgs_ctx* ctx, hcgs_saved* s, float2* U, float* T_out
     uint32_t* ls = (uint32_t*)s->last.p;
     const bool h16 = s->opts.footprint == 1;
 #define HCGS_FWD(CC)                                                                                       \
-    if (h16) HCGS_KERNEL(ctx, "k_raster_fwd", st, k_raster_fwd<CC, true><<<grid, RT, 0, st>>>(a, U, Ts, ls, T_out, nc_out)); \
-    else HCGS_KERNEL(ctx, "k_raster_fwd", st, k_raster_fwd<CC, false><<<grid, RT, 0, st>>>(a, U, Ts, ls, T_out, nc_out))
+    if (nc_out) {                                                                                          \
+        if (h16) HCGS_KERNEL(ctx, "k_raster_fwd", st, k_raster_fwd<CC, true, true><<<grid, RT, 0, st>>>(a, U, Ts, ls, T_out, nc_out)); \
+        else HCGS_KERNEL(ctx, "k_raster_fwd", st, k_raster_fwd<CC, false, true><<<grid, RT, 0, st>>>(a, U, Ts, ls, T_out, nc_out)); \
+    } else {                                                                                               \
+        if (h16) HCGS_KERNEL(ctx, "k_raster_fwd", st, k_raster_fwd<CC, true, false><<<grid, RT, 0, st>>>(a, U, Ts, ls, T_out, nc_out)); \
+        else HCGS_KERNEL(ctx, "k_raster_fwd", st, k_raster_fwd<CC, false, false><<<grid, RT, 0, st>>>(a, U, Ts, ls, T_out, nc_out)); \
+    }
     switch (s->C) {
         case 1: HCGS_FWD(1); break;
         case 2: HCGS_FWD(2); break;
