@@ -65,8 +65,7 @@ struct RecW {
     }
 };
 
-constexpr int RT = 128;            // threads per CTA
-constexpr int RWARPS = RT / 32;
+constexpr int RT = 32;  // one warp per CTA: one 16 x 8 strip
 
 // Can Gaussian (mu, conic A B C, opacity o) reach alpha >= alpha_min at any
 // pixel centre of the strip x in [x0, x0 + 15], y in [y0, y0 + 7]?  For each
@@ -239,17 +238,17 @@ __device__ __forceinline__ void fwd_pair(const float4* rec, float2 a2, bool c0, 
 // pixel takes a step, so this is the "stop once T < T_eps" rule); pixels
 // outside the image start with T = 0.
 template <int C, bool H16, bool NCOUNT>
-__global__ void __launch_bounds__(RT, 6) k_raster_fwd(RasterArgs a, float2* __restrict__ U, float* __restrict__ Tsave,
+__global__ void __launch_bounds__(RT, 24) k_raster_fwd(RasterArgs a, float2* __restrict__ U, float* __restrict__ Tsave,
                                                    uint32_t* __restrict__ lastsave, float* __restrict__ Tout,
                                                    int32_t* __restrict__ ncout) {
     constexpr int NR = C <= 1 ? 2 : (C <= 3 ? 3 : 4);
-    __shared__ float4 srec[RWARPS][32][NR + 1];
-    __shared__ uint32_t spos[RWARPS][32], sid[RWARPS][32];
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int reg = blockIdx.x, l = blockIdx.y, v = blockIdx.z;
-    const int tx = reg % a.tilesX, ty = 2 * (reg / a.tilesX) + (warp >> 1);  // this warp's tile
+    __shared__ float4 srec[32][NR + 1];
+    __shared__ uint32_t spos[32], sid[32];
+    const int lane = threadIdx.x;
+    const int strip = blockIdx.x, l = blockIdx.y, v = blockIdx.z;
+    const int tx = strip % a.tilesX, ty = (strip / a.tilesX) >> 1;  // this warp's tile
     const int px = tx * TILE + (lane & 15);
-    const int sy = ty * TILE + 8 * (warp & 1);       // this warp's 16 x 8 strip starts at row sy
+    const int sy = ty * TILE + 8 * ((strip / a.tilesX) & 1);  // this warp's 16 x 8 strip starts at row sy
     const int py = sy + (lane >> 4);                 // rows py, py + 2, py + 4, py + 6
     const bool colin = px < a.W;
     const float sx0 = (float)(tx * TILE), sy0 = (float)sy;
@@ -269,11 +268,11 @@ __global__ void __launch_bounds__(RT, 6) k_raster_fwd(RasterArgs a, float2* __re
     for (uint32_t p0 = 0; p0 < n; p0 += 32) {
         const bool live = TA.x >= teps || TA.y >= teps || TB.x >= teps || TB.y >= teps;
         if (!__any_sync(0xffffffffu, live)) break;
-        const int nh = stage_warp<NR>(a, vN, beg, p0, n, tx, ty, sx0, sy0, srec[warp], spos[warp], sid[warp]);
+        const int nh = stage_warp<NR>(a, vN, beg, p0, n, tx, ty, sx0, sy0, srec, spos, sid);
         for (int k = 0; k < nh; k++) {
-            const float4* rec = srec[warp][k];
+            const float4* rec = srec[k];
             const float4 r0 = rec[0], r1 = rec[1], kk = rec[NR];
-            const uint32_t pos1 = spos[warp][k] + 1u;
+            const uint32_t pos1 = spos[k] + 1u;
             const EntryX x = entry_x(fpx, r0, kk);
             float2 dyA, ogA, aA, dyB, ogB, aB;
             eval_tier<H16>(x, pyA, r0, r1, kk, a.amax, dyA, ogA, aA);
@@ -380,18 +379,20 @@ __device__ __forceinline__ void bwd_pair(const float4* rec, float dx, float2 dy2
 }
 
 template <int C, bool H16>
-__global__ void __launch_bounds__(RT, 5) k_raster_bwd(RasterArgs a, const float* __restrict__ Tsave,
+__global__ void __launch_bounds__(RT, 20) k_raster_bwd(RasterArgs a, const float* __restrict__ Tsave,
                                                    const uint32_t* __restrict__ lastsave,
                                                    const float2* __restrict__ gU, float* __restrict__ g2d) {
     constexpr int NR = C <= 1 ? 2 : (C <= 3 ? 3 : 4);
     constexpr int G = 6 + 2 * C;
-    __shared__ float4 srec[RWARPS][32][NR + 1];
-    __shared__ uint32_t spos[RWARPS][32], sid[RWARPS][32];
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int reg = blockIdx.x, l = blockIdx.y, v = blockIdx.z;
-    const int tx = reg % a.tilesX, ty = 2 * (reg / a.tilesX) + (warp >> 1);
+    constexpr int RS = 36;  // row stride of the reduction buffer (floats)
+    __shared__ float4 srec[32][NR + 1];
+    __shared__ uint32_t spos[32], sid[32];
+    __shared__ __align__(16) float sred[G][RS];
+    const int lane = threadIdx.x;
+    const int strip = blockIdx.x, l = blockIdx.y, v = blockIdx.z;
+    const int tx = strip % a.tilesX, ty = (strip / a.tilesX) >> 1;
     const int px = tx * TILE + (lane & 15);
-    const int sy = ty * TILE + 8 * (warp & 1);
+    const int sy = ty * TILE + 8 * ((strip / a.tilesX) & 1);
     const int py = sy + (lane >> 4);
     const float sx0 = (float)(tx * TILE), sy0 = (float)sy;
     const uint32_t gb = ((uint32_t)(v * a.L + l) * a.ctY + ty / COARSE) * a.ctX + tx / COARSE;
@@ -431,10 +432,10 @@ __global__ void __launch_bounds__(RT, 5) k_raster_bwd(RasterArgs a, const float*
     for (int o = 16; o > 0; o >>= 1) maxlast = max(maxlast, __shfl_xor_sync(0xffffffffu, maxlast, o));
     for (uint32_t hi = maxlast; hi > 0;) {
         const uint32_t lo = hi > 32u ? hi - 32u : 0u;
-        const int nh = stage_warp<NR>(a, vN, beg, lo, hi, tx, ty, sx0, sy0, srec[warp], spos[warp], sid[warp]);
+        const int nh = stage_warp<NR>(a, vN, beg, lo, hi, tx, ty, sx0, sy0, srec, spos, sid);
         for (int k = nh - 1; k >= 0; k--) {  // back-to-front over the visiting order
-            const float4* rec = srec[warp][k];
-            const uint32_t pos = spos[warp][k];
+            const float4* rec = srec[k];
+            const uint32_t pos = spos[k];
             const float4 r0 = rec[0], r1 = rec[1], kk = rec[NR];
             const EntryX x = entry_x(fpx, r0, kk);
             float2 dyA, ogA, aA, dyB, ogB, aB;
@@ -453,14 +454,30 @@ __global__ void __launch_bounds__(RT, 5) k_raster_bwd(RasterArgs a, const float*
                 } else {
                     bwd_pair<C, true>(rec, x.dx, dyB, ogB, aB, c2, c3, a.amax, TB, BB, gBX, gBY, gl2);
                 }
-                float gl[16];
+                // warp sum of the G values: each lane writes its column of the
+                // G x 32 buffer, lane (e, h) adds the 16 values of row e in
+                // half h, one shuffle joins the halves
+                float* red = &sred[0][0];
 #pragma unroll
-                for (int e = 0; e < 16; e++) gl[e] = e < 6 + 2 * C ? gl2[e].x + gl2[e].y : 0.f;
-                const float sum = warp_reduce_scatter16(gl, lane);
-                const int idx = lane >> 1;
+                for (int e = 0; e < G; e++) red[e * RS + lane] = gl2[e].x + gl2[e].y;
+                __syncwarp();
+                const int e = lane >> 1, h = lane & 1;
+                float sum = 0.f;
+                if (e < G) {
+                    const float4* row = reinterpret_cast<const float4*>(red + e * RS + 16 * h);
+                    const float4 u0 = row[0], u1 = row[1], u2 = row[2], u3 = row[3];
+                    const float2 s0 = __fadd2_rn(make_float2(u0.x, u0.y), make_float2(u0.z, u0.w));
+                    const float2 s1 = __fadd2_rn(make_float2(u1.x, u1.y), make_float2(u1.z, u1.w));
+                    const float2 s2 = __fadd2_rn(make_float2(u2.x, u2.y), make_float2(u2.z, u2.w));
+                    const float2 s3 = __fadd2_rn(make_float2(u3.x, u3.y), make_float2(u3.z, u3.w));
+                    const float2 s4 = __fadd2_rn(__fadd2_rn(s0, s1), __fadd2_rn(s2, s3));
+                    sum = s4.x + s4.y;
+                }
+                sum += __shfl_xor_sync(0xffffffffu, sum, 1);
                 // slot 5 holds o dL/do (1/o only scales a gradient: approximate)
-                const float val = idx == 5 ? sum * rcp_approx(r1.y) : sum;
-                if (!(lane & 1) && idx < G) atomicAdd(g2d + (vN + sid[warp][k]) * G + idx, val);
+                const float val = e == 5 ? sum * rcp_approx(r1.y) : sum;
+                if (!h && e < G) atomicAdd(g2d + (vN + sid[k]) * G + e, val);
+                __syncwarp();
             }
         }
         __syncwarp();
@@ -474,7 +491,7 @@ hcgs_status raster_forward(hcgs_ctx* ctx, hcgs_saved* s, float2* U, float* T_out
     HCGS_CUDA(ctx, grow(ctx, s->Tfin, pl * sizeof(float), &s->bytes));
     HCGS_CUDA(ctx, grow(ctx, s->last, pl * sizeof(uint32_t), &s->bytes));
     RasterArgs a = make_raster_args(s);
-    dim3 grid(s->tilesX * ((s->tilesY + 1) / 2), s->L, s->V);  // 16 x 32 pixel regions
+    dim3 grid(s->tilesX * s->tilesY * 2, s->L, s->V);  // 16 x 8 pixel strips
     float* Ts = (float*)s->Tfin.p;
     uint32_t* ls = (uint32_t*)s->last.p;
     const bool h16 = s->opts.footprint == 1;
@@ -502,7 +519,7 @@ hcgs_status raster_backward(hcgs_ctx* ctx, hcgs_saved* s, const float2* gU, cuda
     HCGS_CUDA(ctx, grow(ctx, s->g2d, ng * sizeof(float), &s->bytes));
     HCGS_CUDA(ctx, cudaMemsetAsync(s->g2d.p, 0, ng * sizeof(float), st));
     RasterArgs a = make_raster_args(s);
-    dim3 grid(s->tilesX * ((s->tilesY + 1) / 2), s->L, s->V);  // 16 x 32 pixel regions
+    dim3 grid(s->tilesX * s->tilesY * 2, s->L, s->V);  // 16 x 8 pixel strips
     const float* Ts = (const float*)s->Tfin.p;
     const uint32_t* ls = (const uint32_t*)s->last.p;
     float* g2 = (float*)s->g2d.p;
