@@ -106,7 +106,8 @@ struct hcgs_saved {
     hcgs::DevBuf hist;     // radix-sort block histograms
     hcgs::DevBuf scan;     // scan partials
     hcgs::DevBuf Tfin;     // [V][L][H][W] float
-    hcgs::DevBuf last;     // [V][L][H][W] uint32: bucket position after the last contributor
+    hcgs::DevBuf last;     // [V][L][H][W] uint32: staged index after the last contributor
+    hcgs::DevBuf slist;    // [32 M] uint32: per 16x8 strip, the Gaussians its forward pass kept, in order
     hcgs::DevBuf U;        // [V][L][C][H][W] float2 when the caller gives no plane buffer
     hcgs::DevBuf g2d;      // [V][N][G2D] float 2D gradients (visiting order)
     hcgs::DevBuf gU;       // [V][L][C][H][W] float2 plane gradients

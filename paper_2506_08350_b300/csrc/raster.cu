@@ -29,6 +29,7 @@ struct RasterArgs {
     const uint2* rects;
     const uint32_t* off;
     const uint32_t* list;
+    uint32_t* slist;
     int V, N, L, H, W, tilesX, tilesY, ctX, ctY;
     float amin, amax, teps;
 };
@@ -39,6 +40,7 @@ static RasterArgs make_raster_args(const hcgs_saved* s) {
     a.rects = (const uint2*)s->rects.p;
     a.off = (const uint32_t*)s->bcount.p;
     a.list = s->list;
+    a.slist = (uint32_t*)s->slist.p;
     a.V = s->V; a.N = s->N; a.L = s->L; a.H = s->H; a.W = s->W;
     a.tilesX = s->tilesX; a.tilesY = s->tilesY; a.ctX = s->ctX; a.ctY = s->ctY;
     a.amin = s->opts.alpha_min; a.amax = s->opts.alpha_max; a.teps = s->opts.T_eps;
@@ -66,6 +68,14 @@ struct RecW {
 };
 
 constexpr int RT = 32;  // one warp per CTA: one 16 x 8 strip
+
+// Start of a strip's kept-id list: bucket list offset beg, length n; the
+// bucket's 32 strips (4 x 4 tiles, two strips each) take consecutive slices
+// of n entries.  srow = strip row (tile row * 2 + half).
+__device__ __forceinline__ size_t strip_list_base(uint32_t beg, uint32_t n, int tx, int srow) {
+    const int local = ((srow >> 1) % COARSE * COARSE + tx % COARSE) * 2 + (srow & 1);
+    return (size_t)COARSE * COARSE * 2 * beg + (size_t)local * n;
+}
 
 // Can Gaussian (mu, conic A B C, opacity o) reach alpha >= alpha_min at any
 // pixel centre of the strip x in [x0, x0 + 15], y in [y0, y0 + 7]?  For each
@@ -99,7 +109,7 @@ __device__ __forceinline__ bool strip_hits(float4 r0, float Cc, float o, float x
 template <int NR>
 __device__ __forceinline__ int stage_warp(const RasterArgs& a, size_t vN, uint32_t beg, uint32_t p0, uint32_t n,
                                           int tx, int ty, float sx0, float sy0, float4 (*wrec)[NR + 1],
-                                          uint32_t* wpos, uint32_t* wid) {
+                                          uint32_t* wpos, uint32_t* wid, uint32_t* kept) {
     const int lane = threadIdx.x & 31;
     const uint32_t p = p0 + (uint32_t)lane;
     bool ok = false;
@@ -130,6 +140,7 @@ __device__ __forceinline__ int stage_warp(const RasterArgs& a, size_t vN, uint32
         wrec[slot][NR] = make_float4(-0.5f * L2E * q0.z, -L2E * q0.w, -0.5f * L2E * q1.x, log2f(q1.y));
         wpos[slot] = p;
         wid[slot] = s;
+        kept[slot] = s;
     }
     __syncwarp();
     return __popc(m);
@@ -257,6 +268,10 @@ __global__ void __launch_bounds__(RT, 24) k_raster_fwd(RasterArgs a, float2* __r
     const size_t vN = (size_t)v * a.N;
     const float fpx = (float)px;
     const float teps = a.teps;
+    // this strip's slice of the kept-id lists: the 32 strips of a bucket each
+    // have room for the bucket's whole list
+    uint32_t* kept = a.slist + strip_list_base(beg, n, tx, strip / a.tilesX);
+    uint32_t nkept = 0;
     const float2 pyA = make_float2((float)py, (float)(py + 2)), pyB = make_float2((float)(py + 4), (float)(py + 6));
     float2 TA = make_float2(colin && py < a.H ? 1.f : 0.f, colin && py + 2 < a.H ? 1.f : 0.f);
     float2 TB = make_float2(colin && py + 4 < a.H ? 1.f : 0.f, colin && py + 6 < a.H ? 1.f : 0.f);
@@ -268,11 +283,11 @@ __global__ void __launch_bounds__(RT, 24) k_raster_fwd(RasterArgs a, float2* __r
     for (uint32_t p0 = 0; p0 < n; p0 += 32) {
         const bool live = TA.x >= teps || TA.y >= teps || TB.x >= teps || TB.y >= teps;
         if (!__any_sync(0xffffffffu, live)) break;
-        const int nh = stage_warp<NR>(a, vN, beg, p0, n, tx, ty, sx0, sy0, srec, spos, sid);
+        const int nh = stage_warp<NR>(a, vN, beg, p0, n, tx, ty, sx0, sy0, srec, spos, sid, kept + nkept);
         for (int k = 0; k < nh; k++) {
             const float4* rec = srec[k];
             const float4 r0 = rec[0], r1 = rec[1], kk = rec[NR];
-            const uint32_t pos1 = spos[k] + 1u;
+            const uint32_t pos1 = nkept + (uint32_t)k + 1u;  // staged index + 1
             const EntryX x = entry_x(fpx, r0, kk);
             float2 dyA, ogA, aA, dyB, ogB, aB;
             eval_tier<H16>(x, pyA, r0, r1, kk, a.amax, dyA, ogA, aA);
@@ -292,6 +307,7 @@ __global__ void __launch_bounds__(RT, 24) k_raster_fwd(RasterArgs a, float2* __r
                 if (NCOUNT) { nc[2] += c2; nc[3] += c3; }
             }
         }
+        nkept += (uint32_t)nh;
         __syncwarp();
     }
     const size_t plane = (size_t)v * a.L + l;
@@ -378,15 +394,36 @@ __device__ __forceinline__ void bwd_pair(const float4* rec, float dx, float2 dy2
     }
 }
 
+// Loads kept entries [lo, lo + cnt) of a strip (Gaussian ids from the forward
+// pass) into the warp's slots: record and base-2 exponent coefficients.
+template <int NR>
+__device__ __forceinline__ void stage_kept(const RasterArgs& a, size_t vN, const uint32_t* kept, uint32_t lo, int cnt,
+                                           float4 (*wrec)[NR + 1], uint32_t* wid) {
+    const int lane = threadIdx.x & 31;
+    if (lane < cnt) {
+        const uint32_t s = kept[lo + lane];
+        const float4* r = a.rec + (vN + s) * NR;
+        const float4 q0 = r[0], q1 = r[1];
+        wrec[lane][0] = q0;
+        wrec[lane][1] = q1;
+#pragma unroll
+        for (int k = 2; k < NR; k++) wrec[lane][k] = r[k];
+        constexpr float L2E = 1.4426950408889634f;
+        wrec[lane][NR] = make_float4(-0.5f * L2E * q0.z, -L2E * q0.w, -0.5f * L2E * q1.x, log2f(q1.y));
+        wid[lane] = s;
+    }
+    __syncwarp();
+}
+
 template <int C, bool H16>
 __global__ void __launch_bounds__(RT, 20) k_raster_bwd(RasterArgs a, const float* __restrict__ Tsave,
-                                                   const uint32_t* __restrict__ lastsave,
-                                                   const float2* __restrict__ gU, float* __restrict__ g2d) {
+                                                    const uint32_t* __restrict__ lastsave,
+                                                    const float2* __restrict__ gU, float* __restrict__ g2d) {
     constexpr int NR = C <= 1 ? 2 : (C <= 3 ? 3 : 4);
     constexpr int G = 6 + 2 * C;
     constexpr int RS = 36;  // row stride of the reduction buffer (floats)
     __shared__ float4 srec[32][NR + 1];
-    __shared__ uint32_t spos[32], sid[32];
+    __shared__ uint32_t sid[32];
     __shared__ __align__(16) float sred[G][RS];
     const int lane = threadIdx.x;
     const int strip = blockIdx.x, l = blockIdx.y, v = blockIdx.z;
@@ -394,9 +431,9 @@ __global__ void __launch_bounds__(RT, 20) k_raster_bwd(RasterArgs a, const float
     const int px = tx * TILE + (lane & 15);
     const int sy = ty * TILE + 8 * ((strip / a.tilesX) & 1);
     const int py = sy + (lane >> 4);
-    const float sx0 = (float)(tx * TILE), sy0 = (float)sy;
     const uint32_t gb = ((uint32_t)(v * a.L + l) * a.ctY + ty / COARSE) * a.ctX + tx / COARSE;
-    const uint32_t beg = a.off[gb];
+    const uint32_t beg = a.off[gb], n = a.off[gb + 1] - beg;
+    const uint32_t* kept = a.slist + strip_list_base(beg, n, tx, strip / a.tilesX);
     const size_t vN = (size_t)v * a.N;
     const size_t plane = (size_t)v * a.L + l;
     const size_t HW = (size_t)a.H * a.W;
@@ -432,10 +469,11 @@ __global__ void __launch_bounds__(RT, 20) k_raster_bwd(RasterArgs a, const float
     for (int o = 16; o > 0; o >>= 1) maxlast = max(maxlast, __shfl_xor_sync(0xffffffffu, maxlast, o));
     for (uint32_t hi = maxlast; hi > 0;) {
         const uint32_t lo = hi > 32u ? hi - 32u : 0u;
-        const int nh = stage_warp<NR>(a, vN, beg, lo, hi, tx, ty, sx0, sy0, srec, spos, sid);
+        const int nh = (int)(hi - lo);
+        stage_kept<NR>(a, vN, kept, lo, nh, srec, sid);
         for (int k = nh - 1; k >= 0; k--) {  // back-to-front over the visiting order
             const float4* rec = srec[k];
-            const uint32_t pos = spos[k];
+            const uint32_t pos = lo + (uint32_t)k;
             const float4 r0 = rec[0], r1 = rec[1], kk = rec[NR];
             const EntryX x = entry_x(fpx, r0, kk);
             float2 dyA, ogA, aA, dyB, ogB, aB;
@@ -490,6 +528,7 @@ hcgs_status raster_forward(hcgs_ctx* ctx, hcgs_saved* s, float2* U, float* T_out
     const size_t pl = (size_t)s->V * s->L * s->H * s->W;
     HCGS_CUDA(ctx, grow(ctx, s->Tfin, pl * sizeof(float), &s->bytes));
     HCGS_CUDA(ctx, grow(ctx, s->last, pl * sizeof(uint32_t), &s->bytes));
+    HCGS_CUDA(ctx, grow(ctx, s->slist, (size_t)COARSE * COARSE * 2 * s->M * sizeof(uint32_t) + 16, &s->bytes));
     RasterArgs a = make_raster_args(s);
     dim3 grid(s->tilesX * s->tilesY * 2, s->L, s->V);  // 16 x 8 pixel strips
     float* Ts = (float*)s->Tfin.p;
