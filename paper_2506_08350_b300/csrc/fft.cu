@@ -31,9 +31,10 @@ namespace hcgs {
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// complex add, subtract and real scaling as packed FP32x2 operations
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return __fmul2_rn(a, make_float2(s, s)); }
 // multiply by -i (forward transform) or +i (inverse transform)
 template <bool INV>
 __device__ __forceinline__ float2 mul_mi(float2 a) {
@@ -57,7 +58,7 @@ __device__ __forceinline__ void dft3(float2* v) {
     const float s = 0.86602540378443865f;  // sin(2 pi / 3)
     float2 t = cadd(v[1], v[2]);
     float2 d = csub(v[1], v[2]);
-    float2 a = make_float2(v[0].x - 0.5f * t.x, v[0].y - 0.5f * t.y);
+    float2 a = __ffma2_rn(make_float2(-0.5f, -0.5f), t, v[0]);
     float2 b = cscale(mul_mi<INV>(d), s);
     v[0] = cadd(v[0], t);
     v[1] = cadd(a, b);
@@ -90,10 +91,12 @@ __device__ __forceinline__ void dft5(float2* v) {
     const float s2 = 0.58778525229247313f;   // sin(4 pi / 5)
     float2 t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
     float2 t3 = csub(v[1], v[4]), t4 = csub(v[2], v[3]);
-    float2 a1 = make_float2(v[0].x + c1 * t1.x + c2 * t2.x, v[0].y + c1 * t1.y + c2 * t2.y);
-    float2 a2 = make_float2(v[0].x + c2 * t1.x + c1 * t2.x, v[0].y + c2 * t1.y + c1 * t2.y);
-    float2 b1 = mul_mi<INV>(make_float2(s1 * t3.x + s2 * t4.x, s1 * t3.y + s2 * t4.y));
-    float2 b2 = mul_mi<INV>(make_float2(s2 * t3.x - s1 * t4.x, s2 * t3.y - s1 * t4.y));
+    const float2 C1 = make_float2(c1, c1), C2 = make_float2(c2, c2);
+    const float2 S1 = make_float2(s1, s1), S2 = make_float2(s2, s2);
+    float2 a1 = __ffma2_rn(C2, t2, __ffma2_rn(C1, t1, v[0]));
+    float2 a2 = __ffma2_rn(C1, t2, __ffma2_rn(C2, t1, v[0]));
+    float2 b1 = mul_mi<INV>(__ffma2_rn(S2, t4, __fmul2_rn(S1, t3)));
+    float2 b2 = mul_mi<INV>(__ffma2_rn(make_float2(-s1, -s1), t4, __fmul2_rn(S2, t3)));
     v[0] = cadd(v[0], cadd(t1, t2));
     v[1] = cadd(a1, b1);
     v[4] = csub(a1, b1);
@@ -299,18 +302,32 @@ template <bool INV> struct Dft<16, INV> : DftSplit<4, 4, INV> {};
 
 // Twiddles and DFT of one work item j of a stage (Ns = product of the earlier
 // radices): v[r] *= w^r with w = W_{Ns R}^(j mod Ns) read from the length-N
-// table, powers by halving (at most ceil(log2 r) products deep).
+// table.  The powers are a running product restarted from the table every
+// four steps (w^4 read alongside w), so at most three products deep.
 template <int N, int NS, int R, bool INV>
 __device__ __forceinline__ void stage_math(float2 (&v)[R], int j, const float2* __restrict__ tw) {
     if constexpr (NS > 1) {
-        float2 w = __ldg(tw + (j % NS) * (N / (NS * R)));
+        constexpr int STEP = N / (NS * R);
+        const int k = j % NS;
+        float2 w = __ldg(tw + k * STEP);
         if (INV) w.y = -w.y;
-        float2 p[R];
-        p[1] = w;
+        float2 w4 = make_float2(1.f, 0.f);
+        if constexpr (R > 4) {
+            w4 = __ldg(tw + 4 * k * STEP);
+            if (INV) w4.y = -w4.y;
+        }
+        float2 base = w4, p = w;  // p = w^r, base = w^(4 floor(r / 4))
         sfor<R>([&](auto a) {
             constexpr int r = HCGS_CI(a);
-            if constexpr (r >= 2) p[r] = cmul(p[r / 2], p[r - r / 2]);
-            if constexpr (r >= 1) v[r] = cmul(v[r], p[r]);
+            if constexpr (r >= 1) {
+                if constexpr (r % 4 == 0) {
+                    if constexpr (r > 4) base = cmul(base, w4);
+                    p = base;
+                } else if constexpr (r > 1) {
+                    p = cmul(p, w);
+                }
+                v[r] = cmul(v[r], p);
+            }
         });
     }
     Dft<R, INV>::run(v);
