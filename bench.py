@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--train-steps", type=int, default=1000,
+                    help="steps of the ring optimisation run per footprint tier (0: skip)")
     ap.add_argument("--kernels-out", default=None, help="write the per-kernel table (JSON) here")
     return ap.parse_args()
 
@@ -361,6 +363,17 @@ def run_ours(args):
     e2e_step()
     ms_e2e = timed(e2e_step, args.steps)
 
+    # --- full optimisation step on the ring configuration (512^2 RGB, 8
+    # planes, 500k Gaussians, 50 views): FP32 path vs FP16x2 footprint tier ---
+    training = None
+    if args.train_steps > 0:
+        from paper_2506_08350_b300.train import ring_run
+        wt = S.workload("c3_512_L8_N500k")
+        training = {"workload": wt.name, "unit": "steps/s",
+                    "step": "render + inverse propagation + focal-stack loss + adjoint + Adam, one ring view per step"}
+        for fp in (0, 1):
+            training["fp16x2" if fp else "fp32"] = ring_run(ctx, wt.optics, wt.N, args.train_steps, footprint=fp)
+
     views = V * world
     value = views / (ms_step / 1e3)
     result = {"metric": METRIC, "value": value, "unit": "views/s", "n_gpus": world, "steps": args.steps,
@@ -377,6 +390,8 @@ def run_ours(args):
               "e2e": {"value": views / (ms_e2e / 1e3), "unit": "views/s", "h2d_bytes_per_step": h2d,
                       "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e},
               "gpu_launches": int(sum(c for _, c in prof.values()))}
+    if training is not None:
+        result["training_c3"] = training
     # --- roofline of the dominant kernel ---
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else None
     hbm_peak = peaks["hbm_gbs"] if peaks else 6400.0

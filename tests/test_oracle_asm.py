@@ -222,3 +222,27 @@ def test_inverse_propagation_and_loss():
     # zero field: the loss is the mean of I_gt^2 and the gradient vanishes
     l0, g0, _ = oracle.focal_stack_loss(np.zeros_like(P), Igt, PITCH, (LAM,), zs)
     assert abs(l0 - np.mean(Igt ** 2)) < 1e-15 and np.all(g0 == 0)
+
+
+def test_fp32_phase_formation_misses_the_bound_at_10mm():
+    # Negative control for the precision split of the propagation: at z = 10 mm
+    # the phase 2 pi z sqrt(1/lambda^2 - f^2) is ~1.2e5 rad, where FP32 values
+    # are 2^-7 rad apart, so a table whose phase is formed in FP32 misses the
+    # 1e-4 parity bound; formed in FP64 (reduced mod 2 pi) and only then
+    # rounded to complex64, it stays far below it.
+    H = W = 128
+    z = 10e-3
+    rng = np.random.default_rng(7)
+    u = rng.normal(size=(H, W)) + 1j * rng.normal(size=(H, W))
+    ref = oracle.propagate(u, PITCH, LAM, z)
+    fx = oracle.frequencies(W, PITCH).astype(np.float32)[None, :]
+    fy = oracle.frequencies(H, PITCH).astype(np.float32)[:, None]
+    arg32 = np.float32(1.0) / np.float32(LAM) ** 2 - (fx * fx + fy * fy)
+    phase32 = np.float32(2.0 * np.pi) * np.float32(z) * np.sqrt(arg32)
+    assert phase32.dtype == np.float32 and float(phase32.max()) > 1e5
+    h32 = np.exp(1j * phase32.astype(np.float64))
+    bad = np.fft.ifft2(h32 * np.fft.fft2(u))
+    h64 = oracle.transfer_function(H, W, PITCH, LAM, z).astype(np.complex64).astype(np.complex128)
+    good = np.fft.ifft2(h64 * np.fft.fft2(u))
+    assert rel(bad, ref) > 1e-3
+    assert rel(good, ref) < 1e-6
