@@ -41,6 +41,7 @@ class Optics:
     wavelengths: tuple  # metres, one per colour channel
     plane_z: tuple  # metres, distance Z_l from plane l to the hologram plane
     pitch: float = 8e-6  # metres, square pixels
+    band_limit: int = 0  # 1: Matsushima-Shimobaba band limit on top of the evanescent cut
 
     @property
     def C(self) -> int:

@@ -77,8 +77,15 @@ typedef struct {
     double pitch_x, pitch_y;  /* pixel pitch (m)                                */
     const double* wavelength; /* host [C] (m)                                   */
     const double* plane_z;    /* host [L] (m): Z_l, distance plane l -> hologram */
-    int band_limit;           /* must be 0: Eq. band_limited_asm_transfer_function
-                                 (evanescent cut f^2 <= 1/lambda^2 only)        */
+    int band_limit;           /* 0: Eq. band_limited_asm_transfer_function as
+                                 printed (evanescent cut f^2 <= 1/lambda^2);
+                                 1: also the band limit of Matsushima and
+                                 Shimobaba, the reference the paper cites for
+                                 the method: with du = 1/(n pitch) on an n-sample
+                                 axis, H is kept only where |f| <= 1/(lambda
+                                 sqrt((2 du z)^2 + 1)) on both axes (inactive
+                                 at 8 um pitch for the paper-shaped grids);
+                                 other values: HCGS_ERR_INVALID_ARG            */
 } hcgs_optics;
 
 /* Rasterizer options.  Values the paper leaves unstated (Algorithm 2 names

@@ -196,36 +196,45 @@ def frequencies(n: int, pitch: float) -> np.ndarray:
     return k / (n * pitch)
 
 
-def transfer_function(H: int, W: int, pitch: float, wavelength: float, z: float) -> np.ndarray:
+def transfer_function(H: int, W: int, pitch: float, wavelength: float, z: float, band_limit: int = 0) -> np.ndarray:
     """H_z(f_x, f_y) of Eq. band_limited_asm_transfer_function on the H x W
     grid in FFT order: exp(j 2 pi z sqrt(1/lambda^2 - f^2)) inside
-    f^2 <= 1/lambda^2, zero outside."""
+    f^2 <= 1/lambda^2, zero outside.  With band_limit = 1 the band limit of
+    Matsushima and Shimobaba (the reference the paper gives for the
+    band-limited method) is applied as well: on a grid of n samples the
+    frequency spacing is du = 1/(n pitch), and H is kept only where
+    |f_x| <= 1/(lambda sqrt((2 du_x z)^2 + 1)) and likewise for f_y."""
     fx = frequencies(W, pitch)[None, :]
     fy = frequencies(H, pitch)[:, None]
     arg = 1.0 / wavelength ** 2 - (fx ** 2 + fy ** 2)
     inside = arg >= 0
+    if band_limit:
+        dux, duy = 1.0 / (W * pitch), 1.0 / (H * pitch)
+        lim_x = 1.0 / (wavelength * np.sqrt((2.0 * dux * z) ** 2 + 1.0))
+        lim_y = 1.0 / (wavelength * np.sqrt((2.0 * duy * z) ** 2 + 1.0))
+        inside = inside & (np.abs(fx) <= lim_x) & (np.abs(fy) <= lim_y)
     phase = 2.0 * np.pi * z * np.sqrt(np.where(inside, arg, 0.0))
     return np.where(inside, np.exp(1j * phase), 0.0)
 
 
-def propagate(u: np.ndarray, pitch: float, wavelength: float, z: float) -> np.ndarray:
+def propagate(u: np.ndarray, pitch: float, wavelength: float, z: float, band_limit: int = 0) -> np.ndarray:
     """One field through Eq. layer2plane_asm: IDFT(H_z DFT(u))."""
-    Hz = transfer_function(u.shape[-2], u.shape[-1], pitch, wavelength, z)
+    Hz = transfer_function(u.shape[-2], u.shape[-1], pitch, wavelength, z, band_limit)
     return np.fft.ifft2(Hz * np.fft.fft2(u))
 
 
-def propagate_planes(U: np.ndarray, pitch: float, wavelengths, plane_z) -> np.ndarray:
+def propagate_planes(U: np.ndarray, pitch: float, wavelengths, plane_z, band_limit: int = 0) -> np.ndarray:
     """Eq. layer2plane_asm for every plane, then Eq. sum_planes.
     U[L][C][H][W] -> P[C][H][W]."""
     L, C = U.shape[0], U.shape[1]
     P = np.zeros(U.shape[1:], dtype=np.complex128)
     for c in range(C):
         for l in range(L):
-            P[c] += propagate(U[l, c], pitch, wavelengths[c], plane_z[l])
+            P[c] += propagate(U[l, c], pitch, wavelengths[c], plane_z[l], band_limit)
     return P
 
 
-def propagate_planes_adjoint(gP: np.ndarray, pitch: float, wavelengths, plane_z) -> np.ndarray:
+def propagate_planes_adjoint(gP: np.ndarray, pitch: float, wavelengths, plane_z, band_limit: int = 0) -> np.ndarray:
     """Adjoint of ``propagate_planes`` for g = dL/dRe + j dL/dIm:
     gU_l = IDFT(conj(H_{Z_l}) DFT(gP)).  (With F the unnormalised DFT,
     (F^-1 D F)^H = F^-1 conj(D) F.)"""
@@ -235,12 +244,12 @@ def propagate_planes_adjoint(gP: np.ndarray, pitch: float, wavelengths, plane_z)
     for c in range(C):
         G = np.fft.fft2(gP[c])
         for l in range(L):
-            Hz = transfer_function(H, W, pitch, wavelengths[c], plane_z[l])
+            Hz = transfer_function(H, W, pitch, wavelengths[c], plane_z[l], band_limit)
             gU[l, c] = np.fft.ifft2(np.conj(Hz) * G)
     return gU
 
 
-def inverse_propagate(P: np.ndarray, pitch: float, wavelengths, plane_z) -> np.ndarray:
+def inverse_propagate(P: np.ndarray, pitch: float, wavelengths, plane_z, band_limit: int = 0) -> np.ndarray:
     """Eq. plane2layer_asm: V_l = IDFT(H_{-Z_l} DFT(P)), P[C][H][W] -> V[L][C][H][W]."""
     C, H, W = P.shape
     L = len(plane_z)
@@ -248,7 +257,7 @@ def inverse_propagate(P: np.ndarray, pitch: float, wavelengths, plane_z) -> np.n
     for c in range(C):
         S = np.fft.fft2(P[c])
         for l in range(L):
-            V[l, c] = np.fft.ifft2(transfer_function(H, W, pitch, wavelengths[c], -plane_z[l]) * S)
+            V[l, c] = np.fft.ifft2(transfer_function(H, W, pitch, wavelengths[c], -plane_z[l], band_limit) * S)
     return V
 
 

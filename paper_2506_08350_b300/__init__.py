@@ -134,11 +134,13 @@ def _stream():
 
 
 def make_optics(o):
-    """hcgs_optics from any object with H, W, wavelengths, plane_z, pitch."""
+    """hcgs_optics from any object with H, W, wavelengths, plane_z, pitch (and
+    optionally band_limit, default 0)."""
     lam = (c_double * len(o.wavelengths))(*[float(x) for x in o.wavelengths])
     z = (c_double * len(o.plane_z))(*[float(x) for x in o.plane_z])
     s = _Optics(int(o.H), int(o.W), len(o.wavelengths), len(o.plane_z), float(o.pitch), float(o.pitch),
-                ctypes.cast(lam, POINTER(c_double)), ctypes.cast(z, POINTER(c_double)), 0)
+                ctypes.cast(lam, POINTER(c_double)), ctypes.cast(z, POINTER(c_double)),
+                int(getattr(o, "band_limit", 0)))
     s._keep = (lam, z)
     return s
 

@@ -91,7 +91,7 @@ static hcgs_status check_optics(hcgs_ctx* ctx, const hcgs_optics* o) {
     REQUIRE(ctx, o->pitch_x > 0 && o->pitch_y > 0, "pitch must be > 0");
     REQUIRE(ctx, o->wavelength && o->plane_z, "wavelength and plane_z must be host arrays");
     for (int c = 0; c < o->C; c++) REQUIRE(ctx, o->wavelength[c] > 0, "wavelengths must be > 0");
-    REQUIRE(ctx, o->band_limit == 0, "only band_limit = 0 (evanescent cut) is provided");
+    REQUIRE(ctx, o->band_limit == 0 || o->band_limit == 1, "band_limit must be 0 or 1");
     if (!fft_supported(o->H) || !fft_supported(o->W)) {
         set_err(ctx, HCGS_ERR_UNSUPPORTED_SIZE, "H and W must be 2^a 3^b 5^c and <= 4096");
         return HCGS_ERR_UNSUPPORTED_SIZE;

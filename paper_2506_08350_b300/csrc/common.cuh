@@ -41,11 +41,12 @@ struct FftPlanArg {  // by-value kernel argument
 // Per-(geometry, optics) transfer-function table: quadrant of H_z, because
 // H depends on f_x^2 and f_y^2 only.  Hq[c][l][H/2+1][W/2+1] float2.
 struct HKey {
-    int H, W, C, L;
+    int H, W, C, L, band_limit;
     double px, py;
     std::vector<double> lam, z;
     bool operator<(const HKey& o) const {
-        return std::tie(H, W, C, L, px, py, lam, z) < std::tie(o.H, o.W, o.C, o.L, o.px, o.py, o.lam, o.z);
+        return std::tie(H, W, C, L, band_limit, px, py, lam, z) <
+               std::tie(o.H, o.W, o.C, o.L, o.band_limit, o.px, o.py, o.lam, o.z);
     }
 };
 

@@ -824,7 +824,12 @@ __global__ void k_rows_spread(const float2* __restrict__ in, float2* __restrict_
 // ---------------------------------------------------------------------------
 // transfer-function table, FP64
 // ---------------------------------------------------------------------------
-__global__ void k_build_hq(float2* __restrict__ hq, int H, int W, int C, int L, double px, double py, HArgs a) {
+// band_limit = 1 adds the limit of Matsushima and Shimobaba: on an n-sample
+// grid du = 1/(n pitch) and H is kept where |f_x| <= 1/(lambda sqrt((2 du_x
+// z)^2 + 1)) (likewise for f_y), the region where the sampled phase does not
+// alias.
+__global__ void k_build_hq(float2* __restrict__ hq, int H, int W, int C, int L, double px, double py, HArgs a,
+                           int band_limit) {
     const int hh = H / 2 + 1, wh = W / 2 + 1;
     const size_t total = (size_t)C * L * hh * wh;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
@@ -835,8 +840,14 @@ __global__ void k_build_hq(float2* __restrict__ hq, int H, int W, int C, int L, 
         const double fx = kx / (W * px), fy = ky / (H * py);
         const double lam = a.lam[c];
         const double arg = 1.0 / (lam * lam) - (fx * fx + fy * fy);
+        bool keep = arg >= 0.0;
+        if (band_limit) {
+            const double z = a.z[l];
+            const double bx = 2.0 * z / (W * px), by = 2.0 * z / (H * py);
+            keep = keep && fx <= 1.0 / (lam * sqrt(bx * bx + 1.0)) && fy <= 1.0 / (lam * sqrt(by * by + 1.0));
+        }
         float2 h = make_float2(0.f, 0.f);
-        if (arg >= 0.0) {
+        if (keep) {
             const double twopi = 6.283185307179586476925286766559;
             double ph = twopi * a.z[l] * sqrt(arg);
             ph = ph - twopi * rint(ph / twopi);  // reduce to [-pi, pi] in FP64
@@ -906,7 +917,7 @@ hcgs_status get_plan(hcgs_ctx* ctx, int n, FftPlan** out) {
 }
 
 hcgs_status get_htab(hcgs_ctx* ctx, const hcgs_optics* o, const float2** out) {
-    HKey k{o->H, o->W, o->C, o->L, o->pitch_x, o->pitch_y,
+    HKey k{o->H, o->W, o->C, o->L, o->band_limit, o->pitch_x, o->pitch_y,
            std::vector<double>(o->wavelength, o->wavelength + o->C), std::vector<double>(o->plane_z, o->plane_z + o->L)};
     auto it = ctx->htab.find(k);
     if (it != ctx->htab.end()) {
@@ -921,7 +932,7 @@ hcgs_status get_htab(hcgs_ctx* ctx, const hcgs_optics* o, const float2** out) {
     HArgs a{};
     for (int c = 0; c < o->C; c++) a.lam[c] = o->wavelength[c];
     for (int l = 0; l < o->L; l++) a.z[l] = o->plane_z[l];
-    HCGS_KERNEL(ctx, "k_build_hq", 0, k_build_hq<<<1184, 256>>>((float2*)b.p, o->H, o->W, o->C, o->L, o->pitch_x, o->pitch_y, a));
+    HCGS_KERNEL(ctx, "k_build_hq", 0, k_build_hq<<<1184, 256>>>((float2*)b.p, o->H, o->W, o->C, o->L, o->pitch_x, o->pitch_y, a, o->band_limit));
     HCGS_LAUNCH(ctx, "k_build_hq");
     HCGS_CUDA(ctx, cudaDeviceSynchronize());
     ctx->htab.emplace(k, b);
@@ -1165,10 +1176,10 @@ cudaError_t launch_rows_spread_conj_raw(const float2* in, float2* out, int B, in
 }
 
 cudaError_t launch_build_hq_raw(float2* hq, int H, int W, int C, int L, double px, double py, const HArgs& a,
-                                cudaStream_t st) {
+                                int band_limit, cudaStream_t st) {
     const size_t n = (size_t)C * L * (H / 2 + 1) * (W / 2 + 1);
     const int blocks = (int)std::min<size_t>(1184, (n + 255) / 256);
-    k_build_hq<<<blocks, 256, 0, st>>>(hq, H, W, C, L, px, py, a);
+    k_build_hq<<<blocks, 256, 0, st>>>(hq, H, W, C, L, px, py, a, band_limit);
     return cudaGetLastError();
 }
 

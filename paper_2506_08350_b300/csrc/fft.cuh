@@ -19,6 +19,6 @@ cudaError_t launch_rows_spread_conj_raw(const float2* in, float2* out, int B, in
                                         const float2* hq, const FftPlanArg& plan, const float2* tw,
                                         cudaStream_t st);
 cudaError_t launch_build_hq_raw(float2* hq, int H, int W, int C, int L, double px, double py, const HArgs& a,
-                                cudaStream_t st);
+                                int band_limit, cudaStream_t st);
 
 }  // namespace hcgs

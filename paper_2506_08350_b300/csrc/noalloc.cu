@@ -49,7 +49,8 @@ size_t round64(size_t n) { return (n + 63) & ~size_t(63); }
 
 bool optics_ok(const hcgs_optics* o) {
     if (!o || o->H < 1 || o->W < 1 || o->C < 1 || o->C > MAX_C || o->L < 1 || o->L > MAX_L) return false;
-    if (!(o->pitch_x > 0) || !(o->pitch_y > 0) || !o->wavelength || !o->plane_z || o->band_limit != 0) return false;
+    if (!(o->pitch_x > 0) || !(o->pitch_y > 0) || !o->wavelength || !o->plane_z) return false;
+    if (o->band_limit != 0 && o->band_limit != 1) return false;
     for (int c = 0; c < o->C; c++)
         if (!(o->wavelength[c] > 0)) return false;
     return true;
@@ -105,7 +106,7 @@ extern "C" hcgs_status hcgs_asm_propagate_noalloc(const float* in, int B, const 
     for (int c = 0; c < C; c++) a.lam[c] = o->wavelength[c];
     for (int l = 0; l < L; l++) a.z[l] = o->plane_z[l];
     const FftPlanArg pH = plan_for(H), pW = plan_for(W);
-    if (launch_build_hq_raw(hq, H, W, C, L, o->pitch_x, o->pitch_y, a, st) != cudaSuccess ||
+    if (launch_build_hq_raw(hq, H, W, C, L, o->pitch_x, o->pitch_y, a, o->band_limit, st) != cudaSuccess ||
         launch_fft_cols_raw(false, (const float2*)in, S1, B * C, H, W, pH, twH, 1.f, st) != cudaSuccess ||
         launch_rows_spread_conj_raw(S1, (float2*)out, B, L, C, H, W, hq, pW, twW, st) != cudaSuccess ||
         launch_fft_cols_raw(true, (const float2*)out, (float2*)out, B * L * C, H, W, pH, twH,

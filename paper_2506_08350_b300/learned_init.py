@@ -70,12 +70,19 @@ class InitNet:
         self._sync()
         return self.loss
 
-    def fit(self, x, target, K: int, steps: int, lr: float = 1e-3):
-        y = torch.empty((x.shape[0], 16), dtype=torch.float32, device=x.device)
+    def fit(self, x, target, K: int, steps: int, lr: float = 1e-3, batch: int | None = None, seed: int = 0):
+        """Adam steps on (x, target); with ``batch`` each step takes a random
+        window of that many consecutive rows (the rows of a scene are already
+        in random order, so a window is a random sample of it)."""
+        N = x.shape[0]
+        B = N if batch is None or batch >= N else int(batch)
+        y = torch.empty((B, 16), dtype=torch.float32, device=x.device)
         gy = torch.empty_like(y)
+        rng = np.random.default_rng(seed)
         hist = []
         for s in range(steps):
-            l = self.train_step(x, target, K, lr, y, gy)
+            off = 0 if B == N else int(rng.integers(0, N - B + 1))
+            l = self.train_step(x[off:off + B], target[off:off + B], K, lr, y, gy)
             if s % max(1, steps // 20) == 0 or s == steps - 1:
                 hist.append((s, float(l.item())))
         return hist
@@ -157,7 +164,7 @@ def steps_to(curve, psnr):
 
 def run_experiment(ctx: Context, optics, n_train=16, n_test=4, N=3000, n_views=4, opt_steps=150,
                    mlp_steps=1500, lr_app=(0.01, 0.02), seed=0, opts=None, train_init="zero", mlp_lr=1e-3,
-                   log=print):
+                   mlp_batch=None, log=print):
     """Trains the network on n_train scenes optimised by the plain method
     (started from zero phase, or from random phase with train_init="random")
     and compares, on n_test held-out scenes, the plain initialisation, zero
@@ -189,7 +196,7 @@ def run_experiment(ctx: Context, optics, n_train=16, n_test=4, N=3000, n_views=4
     T = torch.cat(ts).contiguous()
     net = InitNet(ctx, seed=seed)
     t1 = time.time()
-    hist = net.fit(X, T, K=2 * o.C, steps=mlp_steps, lr=mlp_lr)
+    hist = net.fit(X, T, K=2 * o.C, steps=mlp_steps, lr=mlp_lr, batch=mlp_batch, seed=seed)
     torch.cuda.synchronize()
     t_fit = time.time() - t1
     log("network fit on %d Gaussians: loss %.4e -> %.4e (%.1f s)" % (X.shape[0], hist[0][1], hist[-1][1], t_fit))
@@ -228,6 +235,47 @@ def run_experiment(ctx: Context, optics, n_train=16, n_test=4, N=3000, n_views=4
         }
     summary["target_psnr"] = target_psnr
     summary["train_scenes_final_psnr"] = float(np.mean(train_final))
-    summary["network_fit"] = {"first": hist[0][1], "last": hist[-1][1], "seconds": t_fit}
+    summary["network_fit"] = {"first": hist[0][1], "last": hist[-1][1], "seconds": t_fit, "rows": int(X.shape[0]),
+                              "steps": mlp_steps, "batch": mlp_batch}
     summary["data_seconds"] = t_data
     return summary
+
+
+def main(argv=None):
+    """Runs the experiment and prints its summary as one JSON line, e.g.
+    ``python -m paper_2506_08350_b300.learned_init`` for 200 training scenes of
+    100k Gaussians (256 x 256 RGB, 4 planes over 0-6 mm, 4 views per scene,
+    100 optimiser steps) and 8 held-out scenes."""
+    import argparse
+    import json
+
+    import hcgs_synth as S
+    ap = argparse.ArgumentParser(description=main.__doc__)
+    ap.add_argument("--train-scenes", type=int, default=200)
+    ap.add_argument("--test-scenes", type=int, default=8)
+    ap.add_argument("--gaussians", type=int, default=100_000)
+    ap.add_argument("--size", type=int, default=256)
+    ap.add_argument("--planes", type=int, default=4)
+    ap.add_argument("--views", type=int, default=4)
+    ap.add_argument("--opt-steps", type=int, default=100)
+    ap.add_argument("--mlp-steps", type=int, default=1500)
+    ap.add_argument("--mlp-batch", type=int, default=65536)
+    ap.add_argument("--train-init", default="zero", choices=["zero", "random"])
+    a = ap.parse_args(argv)
+    z = tuple(float(v) for v in np.linspace(0.0, 6e-3, a.planes))
+    o = S.Optics(a.size, a.size, S.WAVELENGTHS_RGB, z)
+    ctx = Context(0)
+    t = time.time()
+    r = run_experiment(ctx, o, n_train=a.train_scenes, n_test=a.test_scenes, N=a.gaussians, n_views=a.views,
+                       opt_steps=a.opt_steps, mlp_steps=a.mlp_steps, train_init=a.train_init,
+                       mlp_batch=a.mlp_batch, log=lambda *x: None)
+    r["wall_seconds"] = time.time() - t
+    r["config"] = vars(a)
+    for k in ("plain", "zero_phase", "network"):
+        r[k].pop("psnr_curve", None)
+    print(json.dumps(r))
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -246,3 +246,39 @@ def test_fp32_phase_formation_misses_the_bound_at_10mm():
     good = np.fft.ifft2(h64 * np.fft.fft2(u))
     assert rel(bad, ref) > 1e-3
     assert rel(good, ref) < 1e-6
+
+
+def test_band_limit_is_the_unaliased_phase_region():
+    # band_limit = 1: the kept frequencies are those where the sampled phase
+    # of the transfer function does not alias, i.e. where the phase changes
+    # by at most pi between neighbouring frequency samples.  The phase
+    # increments are computed here numerically from 2 pi z sqrt(1/lambda^2 -
+    # f^2) on the sample grid, independently of the limit's closed form; the
+    # two may disagree only at the first sample past the boundary.
+    n, z = 96, 30e-3
+    f = oracle.frequencies(n, PITCH)
+    du = 1.0 / (n * PITCH)
+    phase = lambda x: 2.0 * np.pi * z * np.sqrt(np.maximum(1.0 / LAM ** 2 - x ** 2, 0.0))
+    step = np.abs(phase(f + 0.5 * du) - phase(f - 0.5 * du))
+    unaliased = step <= np.pi
+    Hb = oracle.transfer_function(1, n, PITCH, LAM, z, band_limit=1)[0]
+    kept = np.abs(Hb) > 0
+    assert 0 < kept.sum() < n  # the limit is active at this distance and grid
+    edge = np.abs(f[kept]).max()
+    near_edge = np.abs(np.abs(f) - edge) <= 1.0001 * du
+    assert np.all((kept == unaliased) | near_edge)
+    assert np.array_equal(kept, np.abs(f) <= edge)  # one contiguous band
+    # the kept set is symmetric and inside it the plain transfer function is unchanged
+    H0 = oracle.transfer_function(1, n, PITCH, LAM, z, band_limit=0)[0]
+    assert np.array_equal(Hb[kept], H0[kept])
+    assert np.array_equal(kept, kept[(-np.arange(n)) % n])
+
+
+def test_band_limit_inactive_on_the_paper_shaped_grids():
+    # At 8 um pitch the limit lies above the grid's highest frequency for the
+    # workloads' sizes and distances, so band_limit = 1 changes nothing there.
+    for (H, W, z) in ((1080, 1920, 12e-3), (512, 512, 10e-3), (256, 256, 5e-3)):
+        for lam in (639e-9, 515e-9, 473e-9):
+            a = oracle.transfer_function(H, W, PITCH, lam, z, band_limit=0)
+            b = oracle.transfer_function(H, W, PITCH, lam, z, band_limit=1)
+            assert np.array_equal(a, b)
