@@ -489,9 +489,11 @@ __global__ void k_project_bwd(ProjArgs a, const float* __restrict__ means, const
         ProjF P;
         project_one(a, means + 3 * n, log_scales + 3 * n, quats + 4 * n, opacity_logits[n], cam + 20 * v, P);
         if (!P.valid) continue;
-        const float go = g[5];
-        gol += go * P.o * (1.f - P.o);
-        drho += P.o * go;
+        // slot 5 holds o dL/do: dL/dlogit = o (1 - o) dL/do, and dL/drho =
+        // o G dL/dalpha summed = o dL/do for the assigned plane
+        const float ogo = g[5];
+        gol += ogo * (1.f - P.o);
+        drho += ogo;
         project_one_backward(a, P, cam + 20 * v, make_float2(g[0], g[1]), g[2], g[3], g[4], gm, gls, gq);
     }
     // appearance: w_c = a_c (cos phi_c, sin phi_c)

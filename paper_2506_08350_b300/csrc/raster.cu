@@ -249,7 +249,7 @@ __device__ __forceinline__ void fwd_pair(const float4* rec, float2 a2, bool c0, 
 // pixel takes a step, so this is the "stop once T < T_eps" rule); pixels
 // outside the image start with T = 0.
 template <int C, bool H16, bool NCOUNT>
-__global__ void __launch_bounds__(RT, 24) k_raster_fwd(RasterArgs a, float2* __restrict__ U, float* __restrict__ Tsave,
+__global__ void __launch_bounds__(RT, 32) k_raster_fwd(RasterArgs a, float2* __restrict__ U, float* __restrict__ Tsave,
                                                    uint32_t* __restrict__ lastsave, float* __restrict__ Tout,
                                                    int32_t* __restrict__ ncout) {
     constexpr int NR = C <= 1 ? 2 : (C <= 3 ? 3 : 4);
@@ -512,9 +512,8 @@ __global__ void __launch_bounds__(RT, 20) k_raster_bwd(RasterArgs a, const float
                     sum = s4.x + s4.y;
                 }
                 sum += __shfl_xor_sync(0xffffffffu, sum, 1);
-                // slot 5 holds o dL/do (1/o only scales a gradient: approximate)
-                const float val = e == 5 ? sum * rcp_approx(r1.y) : sum;
-                if (!h && e < G) atomicAdd(g2d + (vN + sid[k]) * G + e, val);
+                // slot 5 holds o dL/do (the projection adjoint needs no more)
+                if (!h && e < G) atomicAdd(g2d + (vN + sid[k]) * G + e, sum);
                 __syncwarp();
             }
         }
