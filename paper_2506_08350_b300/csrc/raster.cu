@@ -294,18 +294,14 @@ __global__ void __launch_bounds__(RT, 32) k_raster_fwd(RasterArgs a, float2* __r
             eval_tier<H16>(x, pyB, r0, r1, kk, a.amax, dyB, ogB, aB);
             const bool c0 = TA.x >= teps && aA.x >= a.amin, c1 = TA.y >= teps && aA.y >= a.amin;
             const bool c2 = TB.x >= teps && aB.x >= a.amin, c3 = TB.y >= teps && aB.y >= a.amin;
-            if (c0 || c1) {
-                fwd_pair<C>(rec, aA, c0, c1, TA, aAX, aAY);
-                last[0] = c0 ? pos1 : last[0];
-                last[1] = c1 ? pos1 : last[1];
-                if (NCOUNT) { nc[0] += c0; nc[1] += c1; }
-            }
-            if (c2 || c3) {
-                fwd_pair<C>(rec, aB, c2, c3, TB, aBX, aBY);
-                last[2] = c2 ? pos1 : last[2];
-                last[3] = c3 ? pos1 : last[3];
-                if (NCOUNT) { nc[2] += c2; nc[3] += c3; }
-            }
+            fwd_pair<C>(rec, aA, c0, c1, TA, aAX, aAY);
+            last[0] = c0 ? pos1 : last[0];
+            last[1] = c1 ? pos1 : last[1];
+            if (NCOUNT) { nc[0] += c0; nc[1] += c1; }
+            fwd_pair<C>(rec, aB, c2, c3, TB, aBX, aBY);
+            last[2] = c2 ? pos1 : last[2];
+            last[3] = c3 ? pos1 : last[3];
+            if (NCOUNT) { nc[2] += c2; nc[3] += c3; }
         }
         nkept += (uint32_t)nh;
         __syncwarp();
@@ -481,17 +477,12 @@ __global__ void __launch_bounds__(RT, 20) k_raster_bwd(RasterArgs a, const float
             eval_tier<H16>(x, pyB, r0, r1, kk, a.amax, dyB, ogB, aB);
             const bool c0 = pos < last[0] && aA.x >= a.amin, c1 = pos < last[1] && aA.y >= a.amin;
             const bool c2 = pos < last[2] && aB.x >= a.amin, c3 = pos < last[3] && aB.y >= a.amin;
-            const bool anyA = __any_sync(0xffffffffu, c0 || c1), anyB = __any_sync(0xffffffffu, c2 || c3);
-            if (anyA || anyB) {
-                // warp-uniform: pixels that did not take the step carry alpha 0
+            {
+                // branch-free: pixels that did not take the step carry alpha 0
                 // through the pair (T and B unchanged, zero gradient)
                 float2 gl2[14];
-                if (anyA) {
-                    bwd_pair<C, true>(rec, x.dx, dyA, ogA, aA, c0, c1, a.amax, TA, BA, gAX, gAY, gl2);
-                    if (anyB) bwd_pair<C, false>(rec, x.dx, dyB, ogB, aB, c2, c3, a.amax, TB, BB, gBX, gBY, gl2);
-                } else {
-                    bwd_pair<C, true>(rec, x.dx, dyB, ogB, aB, c2, c3, a.amax, TB, BB, gBX, gBY, gl2);
-                }
+                bwd_pair<C, true>(rec, x.dx, dyA, ogA, aA, c0, c1, a.amax, TA, BA, gAX, gAY, gl2);
+                bwd_pair<C, false>(rec, x.dx, dyB, ogB, aB, c2, c3, a.amax, TB, BB, gBX, gBY, gl2);
                 // warp sum of the G values: each lane writes its column of the
                 // G x 32 buffer, lane (e, h) adds the 16 values of row e in
                 // half h, one shuffle joins the halves
