@@ -412,7 +412,7 @@ __device__ __forceinline__ void stage_kept(const RasterArgs& a, size_t vN, const
 }
 
 template <int C, bool H16>
-__global__ void __launch_bounds__(RT, 20) k_raster_bwd(RasterArgs a, const float* __restrict__ Tsave,
+__global__ void __launch_bounds__(RT, 24) k_raster_bwd(RasterArgs a, const float* __restrict__ Tsave,
                                                     const uint32_t* __restrict__ lastsave,
                                                     const float2* __restrict__ gU, float* __restrict__ g2d) {
     constexpr int NR = C <= 1 ? 2 : (C <= 3 ? 3 : 4);
