@@ -340,15 +340,17 @@ __device__ __forceinline__ float rcp_approx(float x) {
 // S_k = sum_{m>k} w_m alpha_m T_m.  Since g is fixed per pixel, only the
 // scalar B = sum_c Re(conj(g_c) S_c) is carried: dL/dalpha_k = T_k A_k -
 // B / (1 - alpha_k) and B <- B + alpha_k T_k A_k, A_k = sum_c Re(conj(g_c) w_kc).
-// Adds the pair's dL/d(mu 0-1, conic 2-4), o dL/do (5) and dL/dw (6..) to the
-// packed accumulators gl (one lane per pixel; the halves are summed once per
-// entry).  The reciprocal of 1 - alpha only scales gradients (no decision
-// depends on it), so the hardware approximation is used.
+// Adds to the packed accumulators (one lane per pixel): dL/dw_c (gw) and the
+// moments of p = -dL/dpower over the pixels, S0 = sum p, Sy = sum p dy,
+// Syy = sum p dy^2; all pixels of a thread share dx, so the thread's
+// gradients of mu and the conic follow from the moments once per entry.
+// The reciprocal of 1 - alpha only scales gradients (no decision depends on
+// it), so the hardware approximation is used.
 template <int C, bool FIRST>
-__device__ __forceinline__ void bwd_pair(const float4* rec, float dx, float2 dy2, float2 og2, float2 a2, bool c0,
-                                         bool c1, float amax, float2& T2, float2& B2, const float2 (&gX)[C],
-                                         const float2 (&gY)[C], float2 (&gl)[14]) {
-    const float4 r0 = rec[0], r1 = rec[1];
+__device__ __forceinline__ void bwd_pair(const float4* rec, float2 dy2, float2 og2, float2 a2, bool c0, bool c1,
+                                         float amax, float2& T2, float2& B2, const float2 (&gX)[C],
+                                         const float2 (&gY)[C], float2 (&gw)[2 * C], float2& S0, float2& Sy,
+                                         float2& Syy) {
     const float2 al = make_float2(c0 ? a2.x : 0.f, c1 ? a2.y : 0.f);
     const float2 om = __fadd2_rn(f2(1.f), make_float2(-al.x, -al.y));
     const float2 iom = make_float2(rcp_approx(om.x), rcp_approx(om.y));
@@ -359,35 +361,45 @@ __device__ __forceinline__ void bwd_pair(const float4* rec, float dx, float2 dy2
     for (int c = 0; c < C; c++) {
         const float2 w = RecW<C>::get(rec, c);
         Ak = __ffma2_rn(gX[c], f2(w.x), __ffma2_rn(gY[c], f2(w.y), Ak));
-        gl[6 + 2 * c] = FIRST ? __fmul2_rn(gX[c], aT) : __ffma2_rn(gX[c], aT, gl[6 + 2 * c]);
-        gl[7 + 2 * c] = FIRST ? __fmul2_rn(gY[c], aT) : __ffma2_rn(gY[c], aT, gl[7 + 2 * c]);
+        gw[2 * c] = FIRST ? __fmul2_rn(gX[c], aT) : __ffma2_rn(gX[c], aT, gw[2 * c]);
+        gw[2 * c + 1] = FIRST ? __fmul2_rn(gY[c], aT) : __ffma2_rn(gY[c], aT, gw[2 * c + 1]);
     }
     const float2 dLda = __ffma2_rn(Tk, Ak, __fmul2_rn(make_float2(-iom.x, -iom.y), B2));
     B2 = __ffma2_rn(aT, Ak, B2);
     T2 = Tk;
     // a clamped alpha (o G > alpha_max) is flat in o G
     const float2 dLa = make_float2(c0 && og2.x <= amax ? dLda.x : 0.f, c1 && og2.y <= amax ? dLda.y : 0.f);
-    const float2 dLdpn = __fmul2_rn(dLa, og2);  // -dL/dpower = o dL/do
-    // power = 1/2 (A dx^2 + 2 B dx dy + C dy^2), d = pixel - mu
-    const float2 q0 = __ffma2_rn(f2(r0.w), dy2, f2(__fmul_rn(r0.z, dx)));  // A dx + B dy
-    const float2 q1 = __ffma2_rn(f2(r1.x), dy2, f2(__fmul_rn(r0.w, dx)));  // B dx + C dy
-    const float2 pdy = __fmul2_rn(dLdpn, dy2);
-    const float2 hdy = __fmul2_rn(f2(-0.5f), dy2);
+    const float2 p = __fmul2_rn(dLa, og2);  // -dL/dpower = o dL/do
+    const float2 pdy = __fmul2_rn(p, dy2);
     if (FIRST) {
-        gl[5] = dLdpn;
-        gl[0] = __fmul2_rn(dLdpn, q0);
-        gl[1] = __fmul2_rn(dLdpn, q1);
-        gl[2] = __fmul2_rn(f2(-0.5f * dx * dx), dLdpn);
-        gl[3] = __fmul2_rn(f2(-dx), pdy);
-        gl[4] = __fmul2_rn(hdy, pdy);
+        S0 = p;
+        Sy = pdy;
+        Syy = __fmul2_rn(pdy, dy2);
     } else {
-        gl[5] = __fadd2_rn(dLdpn, gl[5]);
-        gl[0] = __ffma2_rn(dLdpn, q0, gl[0]);
-        gl[1] = __ffma2_rn(dLdpn, q1, gl[1]);
-        gl[2] = __ffma2_rn(f2(-0.5f * dx * dx), dLdpn, gl[2]);
-        gl[3] = __ffma2_rn(f2(-dx), pdy, gl[3]);
-        gl[4] = __ffma2_rn(hdy, pdy, gl[4]);
+        S0 = __fadd2_rn(S0, p);
+        Sy = __fadd2_rn(Sy, pdy);
+        Syy = __ffma2_rn(pdy, dy2, Syy);
     }
+}
+
+// The entry's 6 + 2C gradient values of one thread from its accumulators:
+// with power = 1/2 (A dx^2 + 2 B dx dy + C dy^2), d = pixel - mu, and the
+// thread's moments s0, sy, syy of p = -dL/dpower (dx is the same for its
+// pixels):  dL/dmu = (A dx s0 + B sy, B dx s0 + C sy), dL/dA = -dx^2 s0 / 2,
+// dL/dB = -dx sy, dL/dC = -syy / 2, o dL/do = s0; then dL/dw_c.
+template <int C>
+__device__ __forceinline__ void entry_grads(float4 r0, float4 r1, float dx, float2 S0, float2 Sy, float2 Syy,
+                                            const float2 (&gw)[2 * C], float (&out)[6 + 2 * C]) {
+    const float s0 = S0.x + S0.y, sy = Sy.x + Sy.y, syy = Syy.x + Syy.y;
+    const float dxs0 = dx * s0;
+    out[0] = fmaf(r0.z, dxs0, r0.w * sy);
+    out[1] = fmaf(r0.w, dxs0, r1.x * sy);
+    out[2] = -0.5f * dx * dxs0;
+    out[3] = -dx * sy;
+    out[4] = -0.5f * syy;
+    out[5] = s0;
+#pragma unroll
+    for (int e = 0; e < 2 * C; e++) out[6 + e] = gw[e].x + gw[e].y;
 }
 
 // Loads kept entries [lo, lo + cnt) of a strip (Gaussian ids from the forward
@@ -480,15 +492,17 @@ __global__ void __launch_bounds__(RT, 24) k_raster_bwd(RasterArgs a, const float
             {
                 // branch-free: pixels that did not take the step carry alpha 0
                 // through the pair (T and B unchanged, zero gradient)
-                float2 gl2[14];
-                bwd_pair<C, true>(rec, x.dx, dyA, ogA, aA, c0, c1, a.amax, TA, BA, gAX, gAY, gl2);
-                bwd_pair<C, false>(rec, x.dx, dyB, ogB, aB, c2, c3, a.amax, TB, BB, gBX, gBY, gl2);
+                float2 gw[2 * C], S0, Sy, Syy;
+                bwd_pair<C, true>(rec, dyA, ogA, aA, c0, c1, a.amax, TA, BA, gAX, gAY, gw, S0, Sy, Syy);
+                bwd_pair<C, false>(rec, dyB, ogB, aB, c2, c3, a.amax, TB, BB, gBX, gBY, gw, S0, Sy, Syy);
+                float gv[G];
+                entry_grads<C>(r0, r1, x.dx, S0, Sy, Syy, gw, gv);
                 // warp sum of the G values: each lane writes its column of the
                 // G x 32 buffer, lane (e, h) adds the 16 values of row e in
                 // half h, one shuffle joins the halves
                 float* red = &sred[0][0];
 #pragma unroll
-                for (int e = 0; e < G; e++) red[e * RS + lane] = gl2[e].x + gl2[e].y;
+                for (int e = 0; e < G; e++) red[e * RS + lane] = gv[e];
                 __syncwarp();
                 const int e = lane >> 1, h = lane & 1;
                 float sum = 0.f;
