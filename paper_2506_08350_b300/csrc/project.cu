@@ -196,26 +196,58 @@ __global__ void k_rs_hist(const uint32_t* __restrict__ keys, size_t seglen, int 
     hist[((size_t)seg * 256 + threadIdx.x) * nblk + blk] = h[threadIdx.x];
 }
 
-__global__ void k_rs_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
-                             uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, size_t seglen, int shift,
-                             int nblk, const uint32_t* __restrict__ pos) {
+// One pass of the stable scatter.  The block's RS_KPB elements are ranked
+// within their digit (in input order: warp match, per-warp counts, running
+// totals over the rounds), staged in shared memory grouped by digit, and then
+// written out so that consecutive threads write consecutive addresses of a
+// digit's output run (instead of 4-byte writes scattered over 256 runs).
+__global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t* __restrict__ kin,
+                                                           const uint32_t* __restrict__ vin,
+                                                           uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                           size_t seglen, int shift, int nblk,
+                                                           const uint32_t* __restrict__ pos) {
     __shared__ uint32_t wcnt[RS_THREADS / 32][256];
-    __shared__ uint32_t running[256];
-    __shared__ uint32_t gbase[256];
+    __shared__ uint32_t running[256], gbase[256], loff[256], wsum[RS_THREADS / 32];
+    __shared__ uint32_t sk[RS_KPB], sv[RS_KPB];
     const int seg = blockIdx.y, blk = blockIdx.x;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const unsigned lt = (1u << lane) - 1u;
-    running[t] = 0;
-    gbase[t] = pos[((size_t)seg * 256 + t) * nblk + blk];
     const size_t beg = (size_t)blk * RS_KPB;
     const size_t so = (size_t)seg * seglen;
+    const int nb = (int)min((size_t)RS_KPB, seglen - beg);  // elements of this block
+    running[t] = 0;
+    loff[t] = 0;
+    gbase[t] = pos[((size_t)seg * 256 + t) * nblk + blk];
+    __syncthreads();
+    uint32_t key[RS_IPT], val[RS_IPT];
+#pragma unroll
+    for (int r = 0; r < RS_IPT; r++) {
+        const int i = r * RS_THREADS + t;
+        key[r] = i < nb ? kin[so + beg + i] : 0u;
+        val[r] = i < nb ? vin[so + beg + i] : 0u;
+        if (i < nb) atomicAdd(&loff[(key[r] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    // exclusive scan of the block's digit counts (thread t: digit t)
+    {
+        const uint32_t c = loff[t];
+        uint32_t inc = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) wsum[warp] = inc;
+        __syncthreads();
+        uint32_t wb = 0;
+        for (int w = 0; w < warp; w++) wb += wsum[w];
+        loff[t] = wb + inc - c;
+    }
     for (int r = 0; r < RS_IPT; r++) {
         for (int e = t; e < (RS_THREADS / 32) * 256; e += RS_THREADS) (&wcnt[0][0])[e] = 0;
         __syncthreads();
-        const size_t idx = beg + (size_t)r * RS_THREADS + t;
-        const bool ok = idx < seglen;
-        const uint32_t key = ok ? kin[so + idx] : 0u;
-        const uint32_t d = ok ? ((key >> shift) & 255u) : 256u;
+        const bool ok = r * RS_THREADS + t < nb;
+        const uint32_t d = ok ? ((key[r] >> shift) & 255u) : 256u;
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         const uint32_t lrank = __popc(peers & lt);
         if (ok && lrank == 0) wcnt[warp][d] = __popc(peers);
@@ -229,12 +261,20 @@ __global__ void k_rs_scatter(const uint32_t* __restrict__ kin, const uint32_t* _
         }
         __syncthreads();
         if (ok) {
-            const uint32_t p = gbase[d] + running[d] + wcnt[warp][d] + lrank;
-            kout[p] = key;
-            vout[p] = vin[so + idx];
+            const uint32_t lp = loff[d] + running[d] + wcnt[warp][d] + lrank;
+            sk[lp] = key[r];
+            sv[lp] = val[r];
         }
         __syncthreads();
         running[t] += tot;
+    }
+    __syncthreads();
+    for (int i = t; i < nb; i += RS_THREADS) {
+        const uint32_t k = sk[i];
+        const uint32_t d = (k >> shift) & 255u;
+        const uint32_t p = gbase[d] + (uint32_t)i - loff[d];
+        kout[p] = k;
+        vout[p] = sv[i];
     }
 }
 
