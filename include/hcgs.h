@@ -60,7 +60,9 @@ typedef enum {
     HCGS_ERR_UNSUPPORTED_SIZE = -4,/* FFT length with a prime factor other than 2,3,5,
                                       or larger than 4096                           */
     HCGS_ERR_DEVICE_CHECK = -5,    /* a kernel's own bounds check fired             */
-    HCGS_ERR_TIMEOUT = -6,         /* reserved: a bounded device wait ran out       */
+    HCGS_ERR_TIMEOUT = -6,         /* a bounded device wait ran out in an earlier
+                                      launch of the context (reported at the
+                                      next hcgs_project / hcgs_render_view)    */
     HCGS_ERR_STATE = -7            /* saved state missing or from another shape     */
 } hcgs_status;
 
@@ -293,7 +295,8 @@ hcgs_status hcgs_init_apply(hcgs_ctx* ctx, const float* y, int N, int C, float* 
  * Working memory (column spectrum, transfer-function table, twiddles) lives
  * in one static device array of 4 Mi complex64 values (32 MiB) that every GPU
  * loading the library holds until exit.  Requests needing more, i.e.
- *   B*C*H*W + C*L*(H/2+1)*(W/2+1) + H + W (each rounded up to 64) > 4194304,
+ *   B*C*H*W + C*L*(H/2+1)*S + H + W (each rounded up to 64) > 4194304, with
+ *   S = W/2 + 1 rounded up to even (the table's row stride),
  * return HCGS_ERR_CAPACITY before any launch.  The first call on a device
  * looks up that device's address of the array (cudaGetSymbolAddress); make
  * that first call before any stream capture.  All calls share the array and

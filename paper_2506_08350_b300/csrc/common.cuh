@@ -39,7 +39,7 @@ struct FftPlanArg {  // by-value kernel argument
 };
 
 // Per-(geometry, optics) transfer-function table: quadrant of H_z, because
-// H depends on f_x^2 and f_y^2 only.  Hq[c][l][H/2+1][W/2+1] float2.
+// H depends on f_x^2 and f_y^2 only.  Hq[c][l][H/2+1][hq_stride(W)] float2.
 struct HKey {
     int H, W, C, L, band_limit;
     double px, py;
@@ -118,6 +118,54 @@ struct hcgs_saved {
 };
 
 namespace hcgs {
+
+// Row stride (complex elements) of the transfer-function quadrant table:
+// W/2 + 1 rounded up to even, so that every row starts on a 16-byte boundary
+// and spans a multiple of 16 bytes (whole rows are moved by bulk copies).
+__host__ __device__ constexpr int hq_stride(int W) { return (W / 2 + 2) & ~1; }
+
+// ---- bulk asynchronous copies into shared memory, completed on mbarriers ----
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// the calling thread arrives and announces `bytes` of copies for this phase
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+// dst (shared) and src (global) 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+// orders earlier generic-proxy accesses of shared memory before later bulk copies
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// Waits for phase `parity` of the barrier for at most ~1 s of SM clock;
+// false if it did not complete by then.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+    const uint32_t a = smem_addr(bar);
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > (1ll << 31)) return false;
+    }
+}
+// status word bits set by kernels (read back by the host at its next sync)
+constexpr int STATUS_WAIT_TIMEOUT = 1;
 
 // ---- error plumbing ----
 struct Err {

@@ -580,28 +580,85 @@ __global__ void __launch_bounds__(CP::T, CP::MINB)
     });
 }
 
-// rows: grid (B, H, C) so that consecutive CTAs (views) share the
-// transfer-function rows through L2.
+// Row passes: grid (B, H, C) so that consecutive CTAs (views) share the
+// transfer-function rows through L2.  The rows a CTA needs next (the next
+// plane's input row and transfer-function row) are brought into a second
+// shared-memory buffer by bulk copies while the current plane is transformed
+// (two buffers, one mbarrier each).  Shared memory: the exchange buffer, then
+// the row buffers, then the barriers.
+template <class RP, bool WITH_INPUT>
+struct RowSmem {
+    static constexpr int W = RP::N, HS = hq_stride(RP::N);
+    static constexpr int XS = (RP::smem_slots() + 1) & ~1;     // exchange (float2, even)
+    static constexpr int IN = WITH_INPUT ? 2 * W : 0;          // input rows
+    static constexpr size_t bytes = (size_t)(XS + IN + 2 * HS) * sizeof(float2) + 2 * sizeof(uint64_t);
+};
+
+// If a bulk copy for plane l does not arrive within the bounded wait, the CTA
+// waits once more (bounded) for it and for the next plane's copy if that was
+// issued, records the timeout in the status word and leaves without writing.
+__device__ __forceinline__ void rows_timeout(uint64_t* bar, int l, int L, int* status) {
+    if (threadIdx.x == 0) {
+        mbar_wait(&bar[l & 1], (l >> 1) & 1);
+        if (l + 1 < L) mbar_wait(&bar[(l + 1) & 1], ((l + 1) >> 1) & 1);
+        atomicOr(status, STATUS_WAIT_TIMEOUT);
+    }
+}
+
 // out[b][c][i] = IDFT( sum_l Hsel_l * DFT(in[b][l][c][i]) )
 template <bool CONJ, class RP>
 __global__ void __launch_bounds__(RP::T, RP::MINB)
     k_rows_sum_reg(const float2* __restrict__ in, float2* __restrict__ out, int L, int C, int H,
-                   const float2* __restrict__ hq, const float2* __restrict__ tw) {
+                   const float2* __restrict__ hq, const float2* __restrict__ tw, int* __restrict__ status) {
     using namespace rfft;
-    constexpr int W = RP::N, hw2 = W / 2 + 1;
+    using SM = RowSmem<RP, true>;
+    constexpr int W = RP::N, HS = SM::HS;
     using SF = typename RP::template SA<false>;
     using SI = typename RP::template SB<true>;
-    extern __shared__ float2 sm[];
+    extern __shared__ __align__(16) float2 sm[];
+    float2* xb = sm;
+    float2* rowb = sm + SM::XS;
+    float2* hb = rowb + SM::IN;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(hb + 2 * HS);
     const int b = blockIdx.x, i = blockIdx.y, c = blockIdx.z;
     const int ky = mirror(i, H);
+    const float2* src0 = in + (((size_t)b * L * C + c) * H + i) * W;  // plane 0; planes are C*H*W apart
+    const float2* h0 = hq + ((size_t)c * L * (H / 2 + 1) + ky) * HS;  // plane 0; planes are (H/2+1)*HS apart
+    const size_t sstep = (size_t)C * H * W, hstep = (size_t)(H / 2 + 1) * HS;
+    auto issue = [&](int l, int buf) {
+        mbar_expect_tx(&bar[buf], (unsigned)((W + HS) * sizeof(float2)));
+        bulk_load(rowb + buf * W, src0 + (size_t)l * sstep, W * sizeof(float2), &bar[buf]);
+        bulk_load(hb + buf * HS, h0 + (size_t)l * hstep, HS * sizeof(float2), &bar[buf]);
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_init_fence();
+        issue(0, 0);
+        if (L > 1) issue(1, 1);
+    }
+    __syncthreads();
     float2 acc[SI::U][SI::RAD];
     sfor<SI::U>([&](auto a) { sfor<SI::RAD>([&](auto r) { acc[HCGS_CI(a)][HCGS_CI(r)] = make_float2(0.f, 0.f); }); });
     for (int l = 0; l < L; l++) {
-        const float2* src = in + ((((size_t)b * L + l) * C + c) * H + i) * W;
-        const float2* hrow = hq + (((size_t)c * L + l) * (H / 2 + 1) + ky) * hw2;
+        const int buf = l & 1;
+        const bool ok = __syncthreads_and(mbar_wait(&bar[buf], (l >> 1) & 1));
+        if (!ok) {
+            rows_timeout(bar, l, L, status);
+            return;
+        }
+        const float2* srow = rowb + buf * W;
+        const float2* hrow = hb + buf * HS;
         float2 v[SF::U][SF::RAD];
-        load_row<SF>(v, src);
-        SF::run(v, sm, tw, [&](auto& vo) {
+        sfor<SF::U>([&](auto a) {
+            constexpr int u = HCGS_CI(a);
+            const int j = SF::It::j(u);
+            const bool okj = SF::It::valid(u);
+            sfor<SF::RAD>([&](auto r) {
+                v[u][HCGS_CI(r)] = okj ? srow[j + HCGS_CI(r) * SF::M] : make_float2(0.f, 0.f);
+            });
+        });
+        SF::run(v, xb, tw, [&](auto& vo) {
             static_assert(Shape<decltype(vo)>::R == SI::RAD && Shape<decltype(vo)>::U == SI::U,
                           "the inverse pass must start with the forward pass's last radix");
             sfor<SI::U>([&](auto a) {
@@ -610,16 +667,21 @@ __global__ void __launch_bounds__(RP::T, RP::MINB)
                 if (SI::It::valid(u)) {
                     sfor<SI::RAD>([&](auto rr) {
                         constexpr int r = HCGS_CI(rr);
-                        float2 h = __ldg(hrow + mirror(j + r * SI::M, W));
+                        float2 h = hrow[mirror(j + r * SI::M, W)];
                         if (CONJ) h.y = -h.y;
                         acc[u][r] = cadd(acc[u][r], cmul(vo[u][r], h));
                     });
                 }
             });
         });
+        __syncthreads();  // the buffer's rows are consumed
+        if (threadIdx.x == 0 && l + 2 < L) {
+            fence_proxy_async_smem();
+            issue(l + 2, buf);
+        }
     }
     float2* dst = out + (((size_t)b * C + c) * H + i) * W;
-    SI::run(acc, sm, tw, [&](auto& vo) {
+    SI::run(acc, xb, tw, [&](auto& vo) {
         for_outputs<W, 1, RP::T>(vo, [&](float2 x, int pos, int) { dst[pos] = x; });
     });
 }
@@ -628,19 +690,37 @@ __global__ void __launch_bounds__(RP::T, RP::MINB)
 template <bool CONJ, class RP>
 __global__ void __launch_bounds__(RP::T, RP::MINB)
     k_rows_spread_reg(const float2* __restrict__ in, float2* __restrict__ out, int L, int C, int H,
-                      const float2* __restrict__ hq, const float2* __restrict__ tw) {
+                      const float2* __restrict__ hq, const float2* __restrict__ tw, int* __restrict__ status) {
     using namespace rfft;
-    constexpr int W = RP::N, hw2 = W / 2 + 1;
+    using SM = RowSmem<RP, false>;
+    constexpr int W = RP::N, HS = SM::HS;
     using SF = typename RP::template SA<false>;
     using SI = typename RP::template SB<true>;
-    extern __shared__ float2 sm[];
+    extern __shared__ __align__(16) float2 sm[];
+    float2* xb = sm;
+    float2* hb = sm + SM::XS;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(hb + 2 * HS);
     const int b = blockIdx.x, i = blockIdx.y, c = blockIdx.z;
     const int ky = mirror(i, H);
+    const float2* h0 = hq + ((size_t)c * L * (H / 2 + 1) + ky) * HS;
+    const size_t hstep = (size_t)(H / 2 + 1) * HS;
+    auto issue = [&](int l, int buf) {
+        mbar_expect_tx(&bar[buf], (unsigned)(HS * sizeof(float2)));
+        bulk_load(hb + buf * HS, h0 + (size_t)l * hstep, HS * sizeof(float2), &bar[buf]);
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_init_fence();
+        issue(0, 0);
+        if (L > 1) issue(1, 1);
+    }
+    __syncthreads();
     float2 spec[SI::U][SI::RAD];
     {
         float2 v[SF::U][SF::RAD];
         load_row<SF>(v, in + (((size_t)b * C + c) * H + i) * W);
-        SF::run(v, sm, tw, [&](auto& vo) {
+        SF::run(v, xb, tw, [&](auto& vo) {
             static_assert(Shape<decltype(vo)>::R == SI::RAD && Shape<decltype(vo)>::U == SI::U,
                           "the inverse pass must start with the forward pass's last radix");
             sfor<SI::U>([&](auto a) {
@@ -649,21 +729,32 @@ __global__ void __launch_bounds__(RP::T, RP::MINB)
         });
     }
     for (int l = 0; l < L; l++) {
-        const float2* hrow = hq + (((size_t)c * L + l) * (H / 2 + 1) + ky) * hw2;
+        const int buf = l & 1;
+        const bool ok = __syncthreads_and(mbar_wait(&bar[buf], (l >> 1) & 1));
+        if (!ok) {
+            rows_timeout(bar, l, L, status);
+            return;
+        }
+        const float2* hrow = hb + buf * HS;
         float2 v[SI::U][SI::RAD];
         sfor<SI::U>([&](auto a) {
             constexpr int u = HCGS_CI(a);
             const int j = SI::It::j(u);
-            const bool ok = SI::It::valid(u);
+            const bool okj = SI::It::valid(u);
             sfor<SI::RAD>([&](auto rr) {
                 constexpr int r = HCGS_CI(rr);
-                float2 h = ok ? __ldg(hrow + mirror(j + r * SI::M, W)) : make_float2(0.f, 0.f);
+                float2 h = okj ? hrow[mirror(j + r * SI::M, W)] : make_float2(0.f, 0.f);
                 if (CONJ) h.y = -h.y;
                 v[u][r] = cmul(spec[u][r], h);
             });
         });
+        __syncthreads();  // the transfer-function row is consumed
+        if (threadIdx.x == 0 && l + 2 < L) {
+            fence_proxy_async_smem();
+            issue(l + 2, buf);
+        }
         float2* dst = out + ((((size_t)b * L + l) * C + c) * H + i) * W;
-        SI::run(v, sm, tw, [&](auto& vo) {
+        SI::run(v, xb, tw, [&](auto& vo) {
             for_outputs<W, 1, RP::T>(vo, [&](float2 x, int pos, int) { dst[pos] = x; });
         });
     }
@@ -762,7 +853,7 @@ __global__ void k_rows_sum(const float2* __restrict__ in, float2* __restrict__ o
     float2* tw = sm + 3 * W;
     const int b = blockIdx.x, i = blockIdx.y, c = blockIdx.z;
     const int ky = mirror(i, H);
-    const int hw2 = W / 2 + 1;
+    const int hw2 = hq_stride(W);
     for (int j = threadIdx.x; j < W; j += blockDim.x) {
         tw[j] = tw_g[j];
         acc[j] = make_float2(0.f, 0.f);
@@ -796,7 +887,7 @@ __global__ void k_rows_spread(const float2* __restrict__ in, float2* __restrict_
     float2* tw = sm + 3 * W;
     const int b = blockIdx.x, i = blockIdx.y, c = blockIdx.z;
     const int ky = mirror(i, H);
-    const int hw2 = W / 2 + 1;
+    const int hw2 = hq_stride(W);
     const float2* src = in + (((size_t)b * C + c) * H + i) * W;
     for (int j = threadIdx.x; j < W; j += blockDim.x) {
         tw[j] = tw_g[j];
@@ -830,13 +921,13 @@ __global__ void k_rows_spread(const float2* __restrict__ in, float2* __restrict_
 // alias.
 __global__ void k_build_hq(float2* __restrict__ hq, int H, int W, int C, int L, double px, double py, HArgs a,
                            int band_limit) {
-    const int hh = H / 2 + 1, wh = W / 2 + 1;
-    const size_t total = (size_t)C * L * hh * wh;
+    const int hh = H / 2 + 1, ws = hq_stride(W);
+    const size_t total = (size_t)C * L * hh * ws;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-        const int kx = (int)(e % wh);
-        const int ky = (int)((e / wh) % hh);
-        const int l = (int)((e / ((size_t)wh * hh)) % L);
-        const int c = (int)(e / ((size_t)wh * hh * L));
+        const int kx = (int)(e % ws);  // kx = W/2 + 1 is row padding (W odd: a mirrored value, never read)
+        const int ky = (int)((e / ws) % hh);
+        const int l = (int)((e / ((size_t)ws * hh)) % L);
+        const int c = (int)(e / ((size_t)ws * hh * L));
         const double fx = kx / (W * px), fy = ky / (H * py);
         const double lam = a.lam[c];
         const double arg = 1.0 / (lam * lam) - (fx * fx + fy * fy);
@@ -925,7 +1016,7 @@ hcgs_status get_htab(hcgs_ctx* ctx, const hcgs_optics* o, const float2** out) {
         return HCGS_OK;
     }
     DevBuf b;
-    const size_t n = (size_t)o->C * o->L * (o->H / 2 + 1) * (o->W / 2 + 1);
+    const size_t n = (size_t)o->C * o->L * (o->H / 2 + 1) * hq_stride(o->W);
     HCGS_CUDA(ctx, cudaMalloc(&b.p, n * sizeof(float2)));
     b.cap = n * sizeof(float2);
     ctx->bytes += b.cap;
@@ -1044,24 +1135,26 @@ static int row_threads(int W) {
 template <class RP>
 static hcgs_status rows_reg(hcgs_ctx* ctx, bool sum, const float2* in, float2* out, int B, int L, int C, int H,
                             const float2* hq, bool conjH, const float2* tw, cudaStream_t st) {
-    const size_t smem = (size_t)RP::smem_slots() * sizeof(float2);
     const dim3 grid(B, H, C);
+    int* status = ctx->d_status;
     if (sum) {
+        const size_t smem = RowSmem<RP, true>::bytes;
         if (conjH) {
             HCGS_CUDA(ctx, allow_smem(k_rows_sum_reg<true, RP>, smem));
-            HCGS_KERNEL(ctx, "k_rows_sum", st, k_rows_sum_reg<true, RP><<<grid, RP::T, smem, st>>>(in, out, L, C, H, hq, tw));
+            HCGS_KERNEL(ctx, "k_rows_sum", st, k_rows_sum_reg<true, RP><<<grid, RP::T, smem, st>>>(in, out, L, C, H, hq, tw, status));
         } else {
             HCGS_CUDA(ctx, allow_smem(k_rows_sum_reg<false, RP>, smem));
-            HCGS_KERNEL(ctx, "k_rows_sum", st, k_rows_sum_reg<false, RP><<<grid, RP::T, smem, st>>>(in, out, L, C, H, hq, tw));
+            HCGS_KERNEL(ctx, "k_rows_sum", st, k_rows_sum_reg<false, RP><<<grid, RP::T, smem, st>>>(in, out, L, C, H, hq, tw, status));
         }
         HCGS_LAUNCH(ctx, "k_rows_sum");
     } else {
+        const size_t smem = RowSmem<RP, false>::bytes;
         if (conjH) {
             HCGS_CUDA(ctx, allow_smem(k_rows_spread_reg<true, RP>, smem));
-            HCGS_KERNEL(ctx, "k_rows_spread", st, k_rows_spread_reg<true, RP><<<grid, RP::T, smem, st>>>(in, out, L, C, H, hq, tw));
+            HCGS_KERNEL(ctx, "k_rows_spread", st, k_rows_spread_reg<true, RP><<<grid, RP::T, smem, st>>>(in, out, L, C, H, hq, tw, status));
         } else {
             HCGS_CUDA(ctx, allow_smem(k_rows_spread_reg<false, RP>, smem));
-            HCGS_KERNEL(ctx, "k_rows_spread", st, k_rows_spread_reg<false, RP><<<grid, RP::T, smem, st>>>(in, out, L, C, H, hq, tw));
+            HCGS_KERNEL(ctx, "k_rows_spread", st, k_rows_spread_reg<false, RP><<<grid, RP::T, smem, st>>>(in, out, L, C, H, hq, tw, status));
         }
         HCGS_LAUNCH(ctx, "k_rows_spread");
     }
@@ -1177,7 +1270,7 @@ cudaError_t launch_rows_spread_conj_raw(const float2* in, float2* out, int B, in
 
 cudaError_t launch_build_hq_raw(float2* hq, int H, int W, int C, int L, double px, double py, const HArgs& a,
                                 int band_limit, cudaStream_t st) {
-    const size_t n = (size_t)C * L * (H / 2 + 1) * (W / 2 + 1);
+    const size_t n = (size_t)C * L * (H / 2 + 1) * hq_stride(W);
     const int blocks = (int)std::min<size_t>(1184, (n + 255) / 256);
     k_build_hq<<<blocks, 256, 0, st>>>(hq, H, W, C, L, px, py, a, band_limit);
     return cudaGetLastError();

@@ -75,7 +75,7 @@ extern "C" hcgs_status hcgs_asm_propagate_noalloc(const float* in, int B, const 
     if (!fft_supported(o->H) || !fft_supported(o->W)) return HCGS_ERR_UNSUPPORTED_SIZE;
     const int H = o->H, W = o->W, C = o->C, L = o->L;
     const size_t nS = (size_t)B * C * H * W;
-    const size_t nH = (size_t)C * L * (H / 2 + 1) * (W / 2 + 1);
+    const size_t nH = (size_t)C * L * (H / 2 + 1) * hq_stride(W);
     const size_t need = round64(nS) + round64(nH) + round64(H) + round64(W);
     if (need > NOALLOC_SCRATCH_COMPLEX) return HCGS_ERR_CAPACITY;
 

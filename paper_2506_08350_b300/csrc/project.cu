@@ -479,7 +479,15 @@ hcgs_status project_and_bin(hcgs_ctx* ctx, hcgs_saved* s, const hcgs_gaussians* 
     if ((e = exclusive_scan(ctx, s, coff, coff, VN, st))) return e;
     // the instance count sizes the instance buffers: one readback
     HCGS_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, scan_total_ptr(s, VN), 8, cudaMemcpyDeviceToHost, st));
+    // the device status word rides along: a bounded wait that ran out in an
+    // earlier launch of this context is reported here
+    HCGS_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned + 2, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
     HCGS_CUDA(ctx, cudaStreamSynchronize(st));
+    if (ctx->h_pinned[2] != 0) {
+        HCGS_CUDA(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st));
+        set_err(ctx, HCGS_ERR_TIMEOUT, "a bounded device wait ran out in an earlier launch");
+        return HCGS_ERR_TIMEOUT;
+    }
     const unsigned long long M = *(unsigned long long*)ctx->h_pinned;
     if (M >= (1ull << 31)) {
         set_err(ctx, HCGS_ERR_CAPACITY, "more than 2^31 bucket instances");
