@@ -146,6 +146,15 @@ hcgs_status hcgs_saved_release(hcgs_ctx* ctx, hcgs_saved* saved);
  * for the recorded events, writes for up to `max` kernels (in first-launch
  * order) the name (static strings owned by the library), the summed device
  * time in ms and the number of launches, sets *n_out, and clears the record. */
+/* Self-test of the bounded waits: launches, on `stream`, one kernel that
+ * waits on a shared-memory barrier nothing completes.  Its wait gives up
+ * after about one second of SM clock and sets the context's status word, as
+ * the row passes do when a bulk copy never arrives; the next hcgs_project or
+ * hcgs_render_view on the context then returns HCGS_ERR_TIMEOUT (and clears
+ * the word), and the calls after it work again.  Returns HCGS_OK once the
+ * kernel is launched; HCGS_ERR_INVALID_ARG for a null context. */
+hcgs_status hcgs_selftest_wait_timeout(hcgs_ctx* ctx, void* stream);
+
 hcgs_status hcgs_profile_enable(hcgs_ctx* ctx, int on);
 hcgs_status hcgs_profile_summary(hcgs_ctx* ctx, int max, int* n_out, const char** names, double* ms,
                                  int64_t* launches);

@@ -37,7 +37,8 @@ EXPORTS = ("hcgs_ctx_create", "hcgs_ctx_destroy", "hcgs_status_string", "hcgs_la
            "hcgs_rasterize_planes_backward", "hcgs_project_backward", "hcgs_render_view_backward",
            "hcgs_focal_stack_loss", "hcgs_adam_step", "hcgs_mlp_forward", "hcgs_mlp_backward",
            "hcgs_profile_enable", "hcgs_profile_summary", "hcgs_asm_propagate_noalloc", "hcgs_mlp_mse_loss",
-           "hcgs_cast_bf16", "hcgs_init_features", "hcgs_init_targets", "hcgs_init_apply")
+           "hcgs_cast_bf16", "hcgs_init_features", "hcgs_init_targets", "hcgs_init_apply",
+           "hcgs_selftest_wait_timeout")
 
 
 class HcgsError(RuntimeError):
@@ -87,6 +88,7 @@ _lib.hcgs_ctx_destroy.restype = None
 _sig("hcgs_ctx_create", [POINTER(c_void_p), c_int])
 _sig("hcgs_saved_create", [_P, POINTER(c_void_p)])
 _sig("hcgs_profile_enable", [_P, c_int])
+_sig("hcgs_selftest_wait_timeout", [_P, _P])
 _sig("hcgs_profile_summary", [_P, c_int, POINTER(c_int), POINTER(ctypes.c_char_p), POINTER(c_double),
                               POINTER(c_int64)])
 _sig("hcgs_saved_release", [_P, _P])
@@ -215,6 +217,11 @@ class Context:
 
     def bytes(self) -> int:
         return int(_lib.hcgs_ctx_bytes(self.handle))
+
+    def selftest_wait_timeout(self):
+        """Launches a kernel whose bounded wait runs out (about one second); the
+        next project / render_view call then raises HcgsError(HCGS_ERR_TIMEOUT)."""
+        self._check(_lib.hcgs_selftest_wait_timeout(self.handle, _stream()))
 
     def profile_enable(self, on=True):
         self._check(_lib.hcgs_profile_enable(self.handle, int(bool(on))))

@@ -605,6 +605,19 @@ __device__ __forceinline__ void rows_timeout(uint64_t* bar, int l, int L, int* s
     }
 }
 
+// A barrier that nothing completes (two arrivals expected, none made): the
+// bounded wait runs out and the status word records it.
+__global__ void k_wait_selftest(int* __restrict__ status) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 2);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    const bool ok = __syncthreads_and(mbar_wait(&bar, 0));
+    if (!ok && threadIdx.x == 0) atomicOr(status, STATUS_WAIT_TIMEOUT);
+}
+
 // out[b][c][i] = IDFT( sum_l Hsel_l * DFT(in[b][l][c][i]) )
 template <bool CONJ, class RP>
 __global__ void __launch_bounds__(RP::T, RP::MINB)
@@ -1277,3 +1290,10 @@ cudaError_t launch_build_hq_raw(float2* hq, int H, int W, int C, int L, double p
 }
 
 }  // namespace hcgs
+
+extern "C" hcgs_status hcgs_selftest_wait_timeout(hcgs_ctx* ctx, void* stream) {
+    if (!ctx) return HCGS_ERR_INVALID_ARG;
+    hcgs::k_wait_selftest<<<1, 32, 0, (cudaStream_t)stream>>>(ctx->d_status);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? HCGS_OK : hcgs::cuda_err(ctx, e, "k_wait_selftest");
+}

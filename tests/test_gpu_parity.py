@@ -334,3 +334,23 @@ def test_asm_band_limit_active(P, ctx, H, W):
     P.asm_propagate_noalloc(complex_dev(Pin), 1, opt, out2)
     ref = oracle.inverse_propagate(Pin[0].astype(np.complex128), opt.pitch, wl, z, band_limit=1)
     assert rel(out2.cpu().numpy()[0], ref) < 1e-5
+
+
+def test_bounded_wait_timeout_is_reported_and_context_recovers(P, ctx):
+    # A kernel whose barrier nothing completes gives up after about a second
+    # and marks the context's status word; the next render reports
+    # HCGS_ERR_TIMEOUT, and the one after it works again.  No fault, no hang.
+    o = S.Optics(32, 48, (515e-9,), (0.0, 2e-3))
+    g = S.make_gaussians(200, o.L, o.C, o.H, o.W, seed=3)
+    vm, it = cams(1, o.H, o.W, seed=0)
+    gd = dev(g)
+    vmd, itd = cams_dev(vm, it)
+    holo = torch.empty((1, o.C, o.H, o.W), dtype=torch.complex64, device="cuda")
+    ctx.render_view(gd, vmd, itd, o, P.DEFAULT_OPTS, holo)
+    ref = holo.clone()
+    ctx.selftest_wait_timeout()
+    with pytest.raises(P.HcgsError, match="TIMEOUT"):
+        ctx.render_view(gd, vmd, itd, o, P.DEFAULT_OPTS, holo)
+    ctx.render_view(gd, vmd, itd, o, P.DEFAULT_OPTS, holo)
+    torch.cuda.synchronize()
+    assert torch.equal(holo, ref)
