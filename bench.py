@@ -67,6 +67,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="skip the c1 / c2 / c4 rate measurements")
     ap.add_argument("--train-steps", type=int, default=1000,
                     help="steps of the ring optimisation run per footprint tier (0: skip)")
     ap.add_argument("--kernels-out", default=None, help="write the per-kernel table (JSON) here")
@@ -227,6 +228,57 @@ def kernel_models(wl, pairs):
     }
 
 
+def measure_config(ctx, P, S, name, tiers, dev, steps=5, warmup=2):
+    """Forward views/s and forward + adjoint steps/s of a named workload
+    (synthetic scene seed 0, views near camera 0, fixed random dL/dP), per
+    footprint tier (0 FP32, 1 FP16x2), CUDA events on the current stream."""
+    import torch
+    wl = S.workload(name)
+    o = wl.optics
+    V = wl.V
+    g_np = S.make_gaussians(wl.N, o.L, o.C, o.H, o.W, seed=0)
+    vm_np, it_np = S.view_batch(V, o.H, o.W, seed=0)
+    g = {k: torch.from_numpy(g_np[k]).to(dev) for k in P.PARAM_NAMES}
+    vm = torch.from_numpy(vm_np.astype(np.float32)).to(dev)
+    it = torch.from_numpy(it_np.astype(np.float32)).to(dev)
+    gP = torch.from_numpy(S.random_complex((V, o.C, o.H, o.W), seed=2)).to(dev)
+    holo = torch.empty((V, o.C, o.H, o.W), dtype=torch.complex64, device=dev)
+    grads = {k: torch.empty_like(g[k]) for k in P.PARAM_NAMES}
+    st = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(steps):
+            fn()
+        e1.record(st)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    out = {"H": o.H, "W": o.W, "C": o.C, "L": o.L, "N": wl.N, "views_per_step": V, "steps": steps}
+    for fp in tiers:
+        opts = dict(P.DEFAULT_OPTS, footprint=fp)
+        saved = P.Saved(ctx)
+
+        def fwd():
+            ctx.render_view(g, vm, it, o, opts, holo, None, saved)
+
+        def step():
+            fwd()
+            ctx.render_view_backward(saved, g, gP, grads)
+
+        ms_f = timed(fwd)
+        ms_s = timed(step)
+        out["fp16x2" if fp else "fp32"] = {"fwd_views_per_s": V * 1e3 / ms_f, "fwd_bwd_steps_per_s": 1e3 / ms_s,
+                                           "fwd_bwd_views_per_s": V * 1e3 / ms_s, "ms_fwd": ms_f, "ms_fwd_bwd": ms_s}
+        saved.release()
+    del g, grads, holo, gP
+    return out
+
+
 def run_ours(args):
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -363,6 +415,14 @@ def run_ours(args):
     e2e_step()
     ms_e2e = timed(e2e_step, args.steps)
 
+    # --- the other configurations: forward and forward + adjoint rates ---
+    configs = None
+    if not args.no_configs and rank == 0:
+        configs = {}
+        for name, tiers in (("c1_256_L2_N1k", (0,)), ("c2_1080p_L8_N100k", (0, 1)),
+                            ("c4_1080p_L12_N2M_V16", (0, 1))):
+            configs[name] = measure_config(ctx, P, S, name, tiers, dev)
+
     # --- full optimisation step on the ring configuration (512^2 RGB, 8
     # planes, 500k Gaussians, 50 views): FP32 path vs FP16x2 footprint tier ---
     training = None
@@ -392,6 +452,8 @@ def run_ours(args):
               "gpu_launches": int(sum(c for _, c in prof.values()))}
     if training is not None:
         result["training_c3"] = training
+    if configs is not None:
+        result["configs"] = configs
     # --- roofline of the dominant kernel ---
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else None
     hbm_peak = peaks["hbm_gbs"] if peaks else 6400.0

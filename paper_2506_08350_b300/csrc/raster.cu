@@ -153,22 +153,12 @@ __device__ __forceinline__ float ex2_approx(float x) {
 }
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 
-// The thread's two pixels (same column, rows y0 and y0 + 2) against one
-// Gaussian record, as packed FP32x2 arithmetic.  With d = pixel - mu the
+// The thread's pixels against one Gaussian record.  With d = pixel - mu the
 // exponent term is power = 1/2 (A dx^2 + C dy^2) + B dx dy (Supp. D.3) and
 // o G = o exp(-power) = 2^(A' dx^2 + B' dx dy + C' dy^2 + log2 o), with the
 // coefficients A' B' C' log2 o prepared once per staged entry (k) and the
 // dx terms once per entry and thread (t0 = A' dx^2 + log2 o, bdx = B' dx);
-// alpha = min(alpha_max, o G).  Shared by forward and adjoint, so both take
-// identical decisions.
-__device__ __forceinline__ void eval_pair(float2 py2, float my, float4 k, float t0, float bdx, float amax,
-                                          float2& dy2, float2& og2, float2& a2) {
-    dy2 = __fadd2_rn(py2, f2(-my));
-    float2 e = __ffma2_rn(f2(bdx), dy2, f2(t0));
-    e = __ffma2_rn(__fmul2_rn(f2(k.z), dy2), dy2, e);
-    og2 = make_float2(ex2_approx(e.x), ex2_approx(e.y));
-    a2 = make_float2(fminf(amax, og2.x), fminf(amax, og2.y));
-}
+// alpha = min(alpha_max, o G).
 
 // Reduced-precision footprint (the FP16x2 tier): the same quantities, with the
 // exponent and exp() evaluated in packed half precision.  To stay well
@@ -204,11 +194,30 @@ __device__ __forceinline__ EntryX entry_x(float px, float4 r0, float4 k) {
     return x;
 }
 
+// Both pixel pairs of a thread (rows r, r+2 and r+4, r+6 of its column).  In
+// the FP32 tier the exponent is quadratic in dy, so the second pair follows
+// from the first by a linear correction: e(dy + 4) - e(dy) = 4 B' dx +
+// 16 C' + 8 C' dy (two packed operations instead of four).  Forward and
+// adjoint both evaluate through here, so they take identical decisions.
 template <bool H16>
-__device__ __forceinline__ void eval_tier(const EntryX& x, float2 py2, float4 r0, float4 r1, float4 k, float amax,
-                                          float2& dy2, float2& og2, float2& a2) {
-    if (H16) eval_pair_h(x.dx, py2, r0, r1.x, r1.y, amax, dy2, og2, a2);
-    else eval_pair(py2, r0.y, k, x.t0, x.bdx, amax, dy2, og2, a2);
+__device__ __forceinline__ void eval_entry(const EntryX& x, float2 pyA, float2 pyB, float4 r0, float4 r1, float4 k,
+                                           float amax, float2& dyA, float2& ogA, float2& aA, float2& dyB,
+                                           float2& ogB, float2& aB) {
+    if (H16) {
+        eval_pair_h(x.dx, pyA, r0, r1.x, r1.y, amax, dyA, ogA, aA);
+        eval_pair_h(x.dx, pyB, r0, r1.x, r1.y, amax, dyB, ogB, aB);
+    } else {
+        dyA = __fadd2_rn(pyA, f2(-r0.y));
+        float2 e = __ffma2_rn(f2(x.bdx), dyA, f2(x.t0));
+        e = __ffma2_rn(__fmul2_rn(f2(k.z), dyA), dyA, e);
+        const float kc = __fmaf_rn(16.f, k.z, __fmul_rn(4.f, x.bdx));
+        const float2 eB = __fadd2_rn(e, __ffma2_rn(f2(8.f * k.z), dyA, f2(kc)));
+        dyB = __fadd2_rn(dyA, f2(4.f));
+        ogA = make_float2(ex2_approx(e.x), ex2_approx(e.y));
+        ogB = make_float2(ex2_approx(eB.x), ex2_approx(eB.y));
+        aA = make_float2(fminf(amax, ogA.x), fminf(amax, ogA.y));
+        aB = make_float2(fminf(amax, ogB.x), fminf(amax, ogB.y));
+    }
 }
 
 // Warp reduce-scatter of 16 values: afterwards lanes 2i and 2i+1 both hold the
@@ -290,8 +299,7 @@ __global__ void __launch_bounds__(RT, 32) k_raster_fwd(RasterArgs a, float2* __r
             const uint32_t pos1 = nkept + (uint32_t)k + 1u;  // staged index + 1
             const EntryX x = entry_x(fpx, r0, kk);
             float2 dyA, ogA, aA, dyB, ogB, aB;
-            eval_tier<H16>(x, pyA, r0, r1, kk, a.amax, dyA, ogA, aA);
-            eval_tier<H16>(x, pyB, r0, r1, kk, a.amax, dyB, ogB, aB);
+            eval_entry<H16>(x, pyA, pyB, r0, r1, kk, a.amax, dyA, ogA, aA, dyB, ogB, aB);
             const bool c0 = TA.x >= teps && aA.x >= a.amin, c1 = TA.y >= teps && aA.y >= a.amin;
             const bool c2 = TB.x >= teps && aB.x >= a.amin, c3 = TB.y >= teps && aB.y >= a.amin;
             fwd_pair<C>(rec, aA, c0, c1, TA, aAX, aAY);
@@ -485,8 +493,7 @@ __global__ void __launch_bounds__(RT, 24) k_raster_bwd(RasterArgs a, const float
             const float4 r0 = rec[0], r1 = rec[1], kk = rec[NR];
             const EntryX x = entry_x(fpx, r0, kk);
             float2 dyA, ogA, aA, dyB, ogB, aB;
-            eval_tier<H16>(x, pyA, r0, r1, kk, a.amax, dyA, ogA, aA);
-            eval_tier<H16>(x, pyB, r0, r1, kk, a.amax, dyB, ogB, aB);
+            eval_entry<H16>(x, pyA, pyB, r0, r1, kk, a.amax, dyA, ogA, aA, dyB, ogB, aB);
             const bool c0 = pos < last[0] && aA.x >= a.amin, c1 = pos < last[1] && aA.y >= a.amin;
             const bool c2 = pos < last[2] && aB.x >= a.amin, c3 = pos < last[3] && aB.y >= a.amin;
             {
