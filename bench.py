@@ -297,10 +297,12 @@ def run_ours(args):
     o = wl.optics
     V = wl.V
     # inputs (each rank renders its own batch of views: independent problems)
-    g_np = S.make_gaussians(wl.N, o.L, o.C, o.H, o.W, seed=rank)
-    vm_np, it_np = S.view_batch(V, o.H, o.W, seed=rank)
+    from paper_2506_08350_b300.parallel import max_over_ranks, rank_seeds
+    seeds = rank_seeds(rank)
+    g_np = S.make_gaussians(wl.N, o.L, o.C, o.H, o.W, seed=seeds["scene"])
+    vm_np, it_np = S.view_batch(V, o.H, o.W, seed=seeds["views"])
     vm_np, it_np = vm_np.astype(np.float32), it_np.astype(np.float32)
-    gP_np = S.random_complex((V, o.C, o.H, o.W), seed=2 + rank)
+    gP_np = S.random_complex((V, o.C, o.H, o.W), seed=seeds["grad"])
     dev = torch.device("cuda", torch.cuda.current_device())
     g = {k: torch.from_numpy(g_np[k]).to(dev) for k in P.PARAM_NAMES}
     vm = torch.from_numpy(vm_np).to(dev)
@@ -334,12 +336,7 @@ def run_ours(args):
         e1.record(stream)
         e1.synchronize()
         barrier()
-        ms = e0.elapsed_time(e1) / K
-        if dist is not None:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return max_over_ranks(e0.elapsed_time(e1) / K, dev)
 
     for _ in range(args.warmup):
         step()

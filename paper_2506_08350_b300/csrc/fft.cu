@@ -444,15 +444,15 @@ struct RowPlan {
     }
 };
 
-using Cols1080 = ColPlan<1080, 8, 480, 2, Seq<12, 10, 9>, Lays<Pad<16, 4>, Pad<160, 1>>, Seq<9, 10, 12>,
-                         Lays<Pad<1, 0>, Pad<160, 10>>>;
+using Cols1080 = ColPlan<1080, 8, 480, 2, Seq<12, 10, 9>, Lays<Pad<16, 4>, Pad<128, 1>>, Seq<9, 10, 12>,
+                         Lays<Pad<1, 0>, Pad<512, 8>>>;
 using Cols1920 = ColPlan<1920, 4, 384, 1, Seq<16, 12, 10>, Lays<Pad<16, 1>, Pad<160, 1>>, Seq<10, 12, 16>,
                          Lays<Pad<80, 4>, Pad<160, 8>>>;
 using Cols512 = ColPlan<512, 16, 512, 2, Seq<8, 8, 8>, Lays<Pad<1, 0>, Pad<1, 0>>, Seq<8, 8, 8>,
                         Lays<Pad<1, 0>, Pad<1, 0>>>;
 using Cols256 = ColPlan<256, 16, 256, 3, Seq<16, 16>, Lays<Pad<1, 0>>, Seq<16, 16>, Lays<Pad<1, 0>>>;
 
-using Rows1920 = RowPlan<1920, 192, 2, Seq<16, 12, 10>, Lays<Pad<16, 1>, Pad<160, 1>>, Seq<10, 12, 16>,
+using Rows1920 = RowPlan<1920, 192, 2, Seq<16, 12, 10>, Lays<Pad<16, 1>, Pad<128, 1>>, Seq<10, 12, 16>,
                          Lays<Pad<80, 1>, Pad<120, 2>>>;
 using Rows1080 = RowPlan<1080, 128, 4, Seq<12, 10, 9>, Lays<Pad<48, 1>, Pad<120, 4>>, Seq<9, 10, 12>,
                          Lays<Pad<1, 0>, Pad<1, 0>>>;

@@ -25,7 +25,8 @@ PAPER_LR = dict(means=0.01, log_scales=0.005, quats=0.001, opacity_logits=0.025,
 class HologramTrainer:
     """Adam optimisation of the Gaussian parameters against focal stacks."""
 
-    def __init__(self, ctx: Context, params: dict, optics, opts=None, lrs=None, betas=(0.9, 0.999), eps=1e-8):
+    def __init__(self, ctx: Context, params: dict, optics, opts=None, lrs=None, betas=(0.9, 0.999), eps=1e-8,
+                 data_parallel: bool = False):
         self.ctx = ctx
         self.p = params
         self.optics = optics
@@ -37,6 +38,7 @@ class HologramTrainer:
         self.v = {k: torch.zeros_like(v) for k, v in params.items()}
         self.g = {k: torch.empty_like(v) for k, v in params.items()}
         self.t = 0
+        self.data_parallel = data_parallel  # sum gradients over the ranks of the process group
         self.saved = Saved(ctx)
         dev = params["means"].device
         o = optics
@@ -56,6 +58,9 @@ class HologramTrainer:
         self.ctx.render_view(self.p, viewmat, intr, self.optics, self.opts, self.holo, None, self.saved)
         self.ctx.focal_stack_loss(self.holo, I_gt, 1, self.optics, self.loss, self.gholo, None)
         self.ctx.render_view_backward(self.saved, self.p, self.gholo, self.g)
+        if self.data_parallel:
+            from .parallel import allreduce_gradients
+            allreduce_gradients(self.g)
         self.t += 1
         for k in PARAM_NAMES:
             lr = self.lrs.get(k, 0.0)
