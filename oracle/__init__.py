@@ -17,7 +17,10 @@ What each function follows (arXiv 2506.08350):
 * ``inverse_propagate``  Eq. plane2layer_asm, intensity I_l = |U|^2;
 * ``focal_stack_loss``   Eq. recon_loss (mean over planes, channels, pixels);
 * ``render_backward``    Supp. D.4, re-derived in reverse mode (C code);
-* ``adam_step``          Adam (the optimiser the full training step uses);
+* ``adam_step``          Adam (the optimiser of the plain training step);
+* ``paper_loss``         the paper's training loss L_recon + L_SSIM (masked
+                         reconstruction loss and structural similarity);
+* ``adan_step``, ``cosine_lr``  the paper's optimiser and learning-rate schedule;
 * ``mlp_*``              the learned-initialisation network (no counterpart in
                          the paper): plain float64 matrix products.
 
@@ -277,6 +280,144 @@ def focal_stack_loss(P: np.ndarray, I_gt: np.ndarray, pitch: float, wavelengths,
             Hm = transfer_function(H, W, pitch, wavelengths[c], -plane_z[l])
             gP[c] += np.fft.ifft2(np.conj(Hm) * np.fft.fft2(gV[l, c]))
     return loss, gP, I
+
+
+# ----------------------------------------------------------------------------
+# the paper's training objective (Sec. 3 loss paragraph): L = L_recon + L_SSIM
+# ----------------------------------------------------------------------------
+SSIM_SIZE = 11          # Gaussian window, standard deviation 1.5 (structural similarity of Wang et al.)
+SSIM_SIGMA = 1.5
+SSIM_C1 = 0.01 ** 2     # stabilising constants for a data range of 1
+SSIM_C2 = 0.03 ** 2
+SSIM_LAMBDA = 0.005     # lambda_1 of L_SSIM
+
+
+def ssim_window(size: int = SSIM_SIZE, sigma: float = SSIM_SIGMA) -> np.ndarray:
+    """The 1D factor of the separable, normalised Gaussian window."""
+    x = np.arange(size, dtype=np.float64) - size // 2
+    g = np.exp(-(x * x) / (2.0 * sigma * sigma))
+    return g / g.sum()
+
+
+def _blur(a: np.ndarray) -> np.ndarray:
+    """Local mean under the window at every pixel of the last two axes, the
+    image continued by zeros (a 'same'-size correlation; the window is
+    symmetric, so this operator is its own adjoint)."""
+    from scipy.ndimage import correlate1d
+    g = ssim_window()
+    a = correlate1d(np.asarray(a, dtype=np.float64), g, axis=-1, mode="constant", cval=0.0)
+    return correlate1d(a, g, axis=-2, mode="constant", cval=0.0)
+
+
+def ssim_map(x: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """Per-pixel SSIM of images x, y (last two axes):
+    ((2 mx my + C1)(2 sxy + C2)) / ((mx^2 + my^2 + C1)(sxx + syy + C2)) with
+    local means m, variances s and covariance under the window."""
+    mx, my = _blur(x), _blur(y)
+    sxx = _blur(x * x) - mx * mx
+    syy = _blur(y * y) - my * my
+    sxy = _blur(x * y) - mx * my
+    return ((2 * mx * my + SSIM_C1) * (2 * sxy + SSIM_C2)) / ((mx * mx + my * my + SSIM_C1) * (sxx + syy + SSIM_C2))
+
+
+def ssim(x: np.ndarray, y: np.ndarray) -> float:
+    """Mean SSIM over the pixels of one image pair."""
+    return float(np.mean(ssim_map(x, y)))
+
+
+def ssim_grad(x: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """d mean(SSIM(x, y)) / dx.  With a = 2 mx my + C1, b = 2 sxy + C2,
+    c = mx^2 + my^2 + C1, d = sxx + syy + C2 and S = ab/(cd) at every pixel:
+    dS/dmx = 2 my (b - a)/(cd) - 2 mx S/c + 2 mx S/d (through mx, sxx and sxy),
+    dS/d<x^2> = -S/d, dS/d<xy> = 2a/(cd); the gradient is the adjoint of the
+    local means applied to these, G(dS/dmx) + 2x G(dS/d<x^2>) + y G(dS/d<xy>),
+    divided by the pixel count."""
+    mx, my = _blur(x), _blur(y)
+    sxx = _blur(x * x) - mx * mx
+    syy = _blur(y * y) - my * my
+    sxy = _blur(x * y) - mx * my
+    a = 2 * mx * my + SSIM_C1
+    b = 2 * sxy + SSIM_C2
+    c = mx * mx + my * my + SSIM_C1
+    d = sxx + syy + SSIM_C2
+    S = a * b / (c * d)
+    d_m = 2 * my * (b - a) / (c * d) - 2 * mx * S / c + 2 * mx * S / d
+    d_xx = -S / d
+    d_xy = 2 * a / (c * d)
+    n = x.shape[-1] * x.shape[-2]
+    return (_blur(d_m) + 2 * x * _blur(d_xx) + y * _blur(d_xy)) / n
+
+
+def paper_loss_intensities(I: np.ndarray, I_gt: np.ndarray, M: np.ndarray, lam: float = SSIM_LAMBDA):
+    """L = L_recon + L_SSIM on focal-stack intensities I, I_gt [L][C][H][W]
+    with binary plane masks M [L][H][W]:
+      L_recon = mean over (l, c, pixels) of d^2 + (M d)^2 + (I_gt d)^2 =
+                mean of d^2 (1 + M + I_gt^2), d = I - I_gt;
+      L_SSIM  = lambda_1 mean over (l, c) of (1 - SSIM(I_lc, I_gt,lc)).
+    Returns (loss, dL/dI)."""
+    I = np.asarray(I, dtype=np.float64)
+    I_gt = np.asarray(I_gt, dtype=np.float64)
+    L, C = I.shape[0], I.shape[1]
+    w = 1.0 + np.asarray(M, dtype=np.float64)[:, None] + I_gt * I_gt
+    dlt = I - I_gt
+    n = I.size
+    loss = float(np.sum(dlt * dlt * w) / n)
+    g = 2.0 * dlt * w / n
+    s_sum = 0.0
+    for l in range(L):
+        for c in range(C):
+            s_sum += ssim(I[l, c], I_gt[l, c])
+            g[l, c] -= lam / (L * C) * ssim_grad(I[l, c], I_gt[l, c])
+    loss += lam * (1.0 - s_sum / (L * C))
+    return loss, g
+
+
+def paper_loss(P: np.ndarray, I_gt: np.ndarray, M: np.ndarray, pitch: float, wavelengths, plane_z,
+               lam: float = SSIM_LAMBDA, band_limit: int = 0):
+    """The paper's training loss for one view's hologram P [C][H][W]: the
+    focal stack I_l = |V_l|^2 of Eq. plane2layer_asm against I_gt, with
+    L_recon + L_SSIM.  Returns (loss, dL/dP as g = dL/dRe + j dL/dIm, I)."""
+    V = inverse_propagate(P, pitch, wavelengths, plane_z, band_limit)
+    I = np.abs(V) ** 2
+    loss, gI = paper_loss_intensities(I, I_gt, M, lam)
+    gV = 2.0 * gI * V
+    C, H, W = P.shape
+    gP = np.zeros((C, H, W), dtype=np.complex128)
+    for c in range(C):
+        for l in range(len(plane_z)):
+            Hm = transfer_function(H, W, pitch, wavelengths[c], -plane_z[l], band_limit)
+            gP[c] += np.fft.ifft2(np.conj(Hm) * np.fft.fft2(gV[l, c]))
+    return loss, gP, I
+
+
+def adan_step(p, g, g_prev, m, v, n, step: int, lr: float, beta1=0.9, beta2=0.92, beta3=0.99, eps=1e-8,
+              weight_decay=0.0):
+    """One step of Adan (Xie et al., Algorithm 1), written with decay factors
+    (beta = 1 - the algorithm's small momentum coefficients): at the first step
+    m = g, v = 0, n = g^2; at the second v = g - g_prev; afterwards
+    m <- b1 m + (1 - b1) g, v <- b2 v + (1 - b2)(g - g_prev),
+    n <- b3 n + (1 - b3)(g + b2 (g - g_prev))^2 (m and n also at the second
+    step); then p <- (p - lr (m + b2 v) / (sqrt(n) + eps)) / (1 + weight_decay lr).
+    Returns new (p, m, v, n)."""
+    p, g, m, v, n = (np.asarray(x, dtype=np.float64) for x in (p, g, m, v, n))
+    if step == 1:
+        m, v, n = g.copy(), np.zeros_like(g), g * g
+    else:
+        dg = g - np.asarray(g_prev, dtype=np.float64)
+        m = beta1 * m + (1 - beta1) * g
+        v = dg if step == 2 else beta2 * v + (1 - beta2) * dg
+        u = g + beta2 * dg
+        n = beta3 * n + (1 - beta3) * u * u
+    p = (p - lr * (m + beta2 * v) / (np.sqrt(n) + eps)) / (1.0 + weight_decay * lr)
+    return p, m, v, n
+
+
+def cosine_lr(step: int, total: int, lr0: float, lr_min: float) -> float:
+    """Cosine annealing from lr0 at step 0 to lr_min at step ``total``:
+    lr_min + (lr0 - lr_min)(1 + cos(pi step / total)) / 2."""
+    import math
+    t = min(max(step, 0), total)
+    return lr_min + (lr0 - lr_min) * (1.0 + math.cos(math.pi * t / total)) / 2.0
 
 
 # ----------------------------------------------------------------------------
