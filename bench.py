@@ -279,6 +279,52 @@ def measure_config(ctx, P, S, name, tiers, dev, steps=5, warmup=2):
     return out
 
 
+def measure_losses(ctx, P, S, o, dev, peak_gbs, steps=10, warmup=3):
+    """Time of the two objectives on one view of the given optics, each with
+    its gradient dL/dP: the plain focal-stack loss and the paper's L_recon +
+    L_SSIM; and the SSIM + weighted-error passes alone on given intensities
+    (hcgs_paper_loss_intensities), with their algorithmic bytes: pass 1 reads
+    I, I_gt, M and writes three partial-derivative maps (20 + 4/C bytes per
+    value), pass 2 reads the maps, I, I_gt, M and writes dL/dI (24 + 4/C)."""
+    import torch
+    st = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(steps):
+            fn()
+        e1.record(st)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    holo = torch.from_numpy(S.random_complex((1, o.C, o.H, o.W), seed=4)).to(dev)
+    shape = (1, o.L, o.C, o.H, o.W)
+    Igt = torch.from_numpy(S.random_real(shape, seed=5)).to(dev)
+    M = torch.from_numpy(S.plane_masks(1, o.L, o.H, o.W, seed=6)).to(dev)
+    I = torch.from_numpy(S.random_real(shape, seed=7, hi=2.0)).to(dev)
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    gP = torch.empty_like(holo)
+    gI = torch.empty_like(I)
+    ms_mse = timed(lambda: ctx.focal_stack_loss(holo, Igt, 1, o, loss, gP, None))
+    ms_paper = timed(lambda: ctx.paper_loss(holo, Igt, M, 1, o, loss, gP, None))
+    ms_int = timed(lambda: ctx.paper_loss_intensities(I, Igt, M, loss, gI))
+    n = I.numel()
+    bytes_int = n * (44.0 + 8.0 / o.C)
+    out = {"H": o.H, "W": o.W, "C": o.C, "L": o.L, "views": 1,
+           "ms_focal_stack_loss_with_grad": ms_mse, "ms_paper_loss_with_grad": ms_paper,
+           "ms_ssim_recon_passes": ms_int,
+           "ssim_recon_passes_roofline": {"bound": "hbm", "achieved": bytes_int / (ms_int * 1e-3) / 1e9,
+                                          "peak": peak_gbs, "unit": "GB/s",
+                                          "frac": bytes_int / (ms_int * 1e-3) / 1e9 / peak_gbs,
+                                          "bytes_per_value": 44.0 + 8.0 / o.C}}
+    del holo, Igt, M, I, gP, gI
+    return out
+
+
 def run_ours(args):
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -430,6 +476,16 @@ def run_ours(args):
                     "step": "render + inverse propagation + focal-stack loss + adjoint + Adam, one ring view per step"}
         for fp in (0, 1):
             training["fp16x2" if fp else "fp32"] = ring_run(ctx, wt.optics, wt.N, args.train_steps, footprint=fp)
+        # the paper's recipe: L_recon + L_SSIM with teacher plane masks, Adan,
+        # cosine annealing of the means' and plane logits' learning rates
+        training["fp32_paper_objective_adan"] = ring_run(ctx, wt.optics, wt.N, args.train_steps, footprint=0,
+                                                         objective="paper", optimizer="adan", anneal=True)
+
+    # --- the two objectives on one view of this workload's optics ---
+    objective = None
+    if not args.no_configs and rank == 0:
+        pk = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else None
+        objective = measure_losses(ctx, P, S, o, dev, pk["hbm_gbs"] if pk else 6400.0)
 
     views = V * world
     value = views / (ms_step / 1e3)
@@ -451,6 +507,8 @@ def run_ours(args):
         result["training_c3"] = training
     if configs is not None:
         result["configs"] = configs
+    if objective is not None:
+        result["objective"] = objective
     # --- roofline of the dominant kernel ---
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else None
     hbm_peak = peaks["hbm_gbs"] if peaks else 6400.0

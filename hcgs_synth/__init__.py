@@ -179,6 +179,27 @@ def random_real(shape, seed: int, lo: float = 0.0, hi: float = 1.0) -> np.ndarra
     return (lo + (hi - lo) * rng.random(shape)).astype(np.float32)
 
 
+def plane_masks(B: int, L: int, H: int, W: int, seed: int) -> np.ndarray:
+    """Binary plane masks [B][L][H][W] float32: a smooth random depth map per
+    view (a few low-frequency cosines) cut into L equal depth bins, so every
+    pixel lies on exactly one plane, in connected regions as a scene's depth
+    map would give."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    yy, xx = np.meshgrid(np.arange(H) / max(H, 1), np.arange(W) / max(W, 1), indexing="ij")
+    out = np.zeros((B, L, H, W), dtype=np.float32)
+    for b in range(B):
+        d = np.zeros((H, W))
+        for _ in range(4):
+            fx, fy = rng.uniform(0.5, 3.0, size=2)
+            ph = rng.uniform(0, 2 * math.pi)
+            d += np.cos(2 * math.pi * (fx * xx + fy * yy) + ph)
+        lo, hi = d.min(), d.max()
+        lab = np.minimum((L * (d - lo) / max(hi - lo, 1e-12)).astype(int), L - 1)
+        for l in range(L):
+            out[b, l] = lab == l
+    return out
+
+
 def sample_params(gauss: dict, k: int, seed: int = 1):
     """k random (array name, flat index) pairs over the continuous parameters
     (plane logits excluded: their forward is piecewise constant)."""

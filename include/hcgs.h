@@ -241,6 +241,49 @@ hcgs_status hcgs_render_view_backward(hcgs_ctx* ctx, hcgs_saved* saved, const hc
 hcgs_status hcgs_focal_stack_loss(hcgs_ctx* ctx, const float* hologram, const float* I_gt, int B,
                                   const hcgs_optics* optics, float* loss, float* g_hologram,
                                   float* I_out, void* stream);
+/* The paper's training objective on one batch of views (Sec. 3, loss):
+ * the focal stack I_l = |V_l|^2, V_l = ASM(P, -z_l) (Eq. plane2layer_asm),
+ * against the targets, with L = L_recon + L_SSIM averaged over views:
+ *   L_recon = mean over (b, l, c, pixel) of d^2 (1 + M + I_gt^2), d = I - I_gt
+ *             (the sum |I - I_gt|^2 + |I M - I_gt M|^2 + |I I_gt - I_gt I_gt|^2
+ *             for a binary M);
+ *   L_SSIM  = lambda_ssim mean over (b, l, c) of (1 - SSIM(I, I_gt)), SSIM
+ *             with an 11 x 11 Gaussian window (sigma 1.5, zeros outside the
+ *             image), C1 = 0.01^2, C2 = 0.03^2, averaged over the pixels.
+ *   hologram device [B][C][H][W] complex64
+ *   I_gt     device [B][L][C][H][W] float
+ *   masks    device [B][L][H][W] float (0 or 1: pixels whose depth falls on
+ *            plane l), nullable = all zero
+ *   lambda_ssim >= 0 (the paper's lambda_1 = 0.005)
+ *   loss     device [1] float (output)
+ *   g_hologram device [B][C][H][W] complex64, nullable: dL/dP (output)
+ *   I_out    device [B][L][C][H][W] float, nullable (output)
+ * Scratch: 2 B C H W + 2 B L C H W complex and 4 B L C H W floats (3 when
+ * I_out is given), held by the context. */
+hcgs_status hcgs_paper_loss(hcgs_ctx* ctx, const float* hologram, const float* I_gt, const float* masks, int B,
+                            const hcgs_optics* optics, float lambda_ssim, float* loss, float* g_hologram,
+                            float* I_out, void* stream);
+/* The same objective on given intensities I device [B][L][C][H][W] float (any
+ * H, W >= 1; B L C H W < 2^29): loss device [1] and g_I = dL/dI device
+ * [B][L][C][H][W] float (outputs); I_gt and masks as in hcgs_paper_loss. */
+hcgs_status hcgs_paper_loss_intensities(hcgs_ctx* ctx, const float* I, const float* I_gt, const float* masks,
+                                        int B, int L, int C, int H, int W, float lambda_ssim, float* loss,
+                                        float* g_I, void* stream);
+/* One Adan update (Xie et al., Algorithm 1; the optimiser of Sec. 5) of count
+ * float32 parameters in place, with decay factors b1 (first moment), b2
+ * (gradient difference) and b3 (second moment).  Sec. 5 gives two values,
+ * 0.9 and 0.99, read as b1 and b3; it is silent on b2, for which Adan's own
+ * default 0.92 is the usual choice:
+ *   step 1: m = g, v = 0, n = g^2;  step 2: v = g - g_prev;
+ *   then m = b1 m + (1-b1) g, v = b2 v + (1-b2)(g - g_prev),
+ *        n = b3 n + (1-b3)(g + b2 (g - g_prev))^2  (m, n also at step 2);
+ *   p = (p - lr (m + b2 v) / (sqrt(n) + eps)) / (1 + weight_decay lr);
+ *   g_prev = g.
+ * All arrays device [count] float; g_prev, m, v, n are the caller's state
+ * (any contents at step 1). */
+hcgs_status hcgs_adan_step(hcgs_ctx* ctx, float* p, const float* g, float* g_prev, float* m, float* v,
+                           float* n, int64_t count, int step, float lr, float beta1, float beta2, float beta3,
+                           float eps, float weight_decay, void* stream);
 /* One bias-corrected Adam update of n float32 parameters in place:
  * m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2; p -= lr m^ / (sqrt(v^) + eps),
  * m^ = m/(1-b1^step), v^ = v/(1-b2^step).  All arrays device [n]. */

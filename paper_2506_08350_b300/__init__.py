@@ -38,7 +38,7 @@ EXPORTS = ("hcgs_ctx_create", "hcgs_ctx_destroy", "hcgs_status_string", "hcgs_la
            "hcgs_focal_stack_loss", "hcgs_adam_step", "hcgs_mlp_forward", "hcgs_mlp_backward",
            "hcgs_profile_enable", "hcgs_profile_summary", "hcgs_asm_propagate_noalloc", "hcgs_mlp_mse_loss",
            "hcgs_cast_bf16", "hcgs_init_features", "hcgs_init_targets", "hcgs_init_apply",
-           "hcgs_selftest_wait_timeout")
+           "hcgs_selftest_wait_timeout", "hcgs_paper_loss", "hcgs_paper_loss_intensities", "hcgs_adan_step")
 
 
 class HcgsError(RuntimeError):
@@ -103,6 +103,10 @@ _sig("hcgs_project_backward", [_P, _P, POINTER(_Gaussians), POINTER(_Grads), c_i
 _sig("hcgs_render_view_backward", [_P, _P, POINTER(_Gaussians), _P, POINTER(_Grads), c_int, _P])
 _sig("hcgs_focal_stack_loss", [_P, _P, _P, c_int, POINTER(_Optics), _P, _P, _P, _P])
 _sig("hcgs_adam_step", [_P, _P, _P, _P, _P, c_int64, c_int, c_float, c_float, c_float, c_float, _P])
+_sig("hcgs_paper_loss", [_P, _P, _P, _P, c_int, POINTER(_Optics), c_float, _P, _P, _P, _P])
+_sig("hcgs_paper_loss_intensities", [_P, _P, _P, _P, c_int, c_int, c_int, c_int, c_int, c_float, _P, _P, _P])
+_sig("hcgs_adan_step", [_P, _P, _P, _P, _P, _P, _P, c_int64, c_int, c_float, c_float, c_float, c_float, c_float,
+                        c_float, _P])
 _sig("hcgs_mlp_forward", [_P, _P, c_int] + [_P] * 8 + [_P, _P])
 _sig("hcgs_asm_propagate_noalloc", [_P, c_int, POINTER(_Optics), _P, _P])
 _sig("hcgs_mlp_mse_loss", [_P, _P, _P, c_int, c_int, _P, _P, _P])
@@ -111,6 +115,8 @@ _sig("hcgs_init_features", [_P, POINTER(_Gaussians), _P, _P, _P])
 _sig("hcgs_init_targets", [_P, _P, _P, c_int, c_int, _P, _P])
 _sig("hcgs_init_apply", [_P, _P, c_int, c_int, _P, _P, _P])
 _sig("hcgs_mlp_backward", [_P, _P, c_int] + [_P] * 8 + [_P] + [_P] * 8 + [_P])
+
+SSIM_LAMBDA = 0.005  # lambda_1 of the SSIM term (Sec. 3, loss)
 
 PARAM_NAMES = ("means", "log_scales", "quats", "opacity_logits", "amplitude", "phase", "plane_logits")
 
@@ -278,6 +284,23 @@ class Context:
         self._check(_lib.hcgs_focal_stack_loss(self.handle, _ptr(hologram), _ptr(I_gt), int(B),
                                                ctypes.byref(make_optics(optics)), _ptr(loss), _ptr(g_hologram),
                                                _ptr(I_out), _stream()))
+
+    def paper_loss(self, hologram, I_gt, masks, B, optics, loss, g_hologram=None, I_out=None,
+                   lambda_ssim=SSIM_LAMBDA):
+        self._check(_lib.hcgs_paper_loss(self.handle, _ptr(hologram), _ptr(I_gt), _ptr(masks), int(B),
+                                         ctypes.byref(make_optics(optics)), float(lambda_ssim), _ptr(loss),
+                                         _ptr(g_hologram), _ptr(I_out), _stream()))
+
+    def paper_loss_intensities(self, I, I_gt, masks, loss, g_I, lambda_ssim=SSIM_LAMBDA):
+        B, L, C, H, W = I.shape
+        self._check(_lib.hcgs_paper_loss_intensities(self.handle, _ptr(I), _ptr(I_gt), _ptr(masks), B, L, C, H, W,
+                                                     float(lambda_ssim), _ptr(loss), _ptr(g_I), _stream()))
+
+    def adan_step(self, p, g, g_prev, m, v, n, step, lr, beta1=0.9, beta2=0.92, beta3=0.99, eps=1e-8,
+                  weight_decay=0.0):
+        self._check(_lib.hcgs_adan_step(self.handle, _ptr(p), _ptr(g), _ptr(g_prev), _ptr(m), _ptr(v), _ptr(n),
+                                        p.numel(), int(step), float(lr), float(beta1), float(beta2), float(beta3),
+                                        float(eps), float(weight_decay), _stream()))
 
     def adam_step(self, p, g, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
         self._check(_lib.hcgs_adam_step(self.handle, _ptr(p), _ptr(g), _ptr(m), _ptr(v), p.numel(), int(step),

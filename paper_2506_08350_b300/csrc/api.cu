@@ -1,5 +1,6 @@
 // C ABI of libhcgs: argument validation, scratch management and the
 // orchestration of the render path.  See include/hcgs.h for the contract.
+#include <cmath>
 #include <cstring>
 
 #include "common.cuh"
@@ -470,6 +471,94 @@ hcgs_status hcgs_focal_stack_loss(hcgs_ctx* ctx, const float* hologram, const fl
                      1.f / (float)planeN, st));
     }
     return HCGS_OK;
+}
+
+// Workspace of the SSIM passes: dmap (3 n floats), then the intensities (n)
+// when the caller gives no I_out; ws[3] takes the block partials.
+static hcgs_status paper_loss_ws(hcgs_ctx* ctx, size_t n, bool need_I, int nblocks, float** dmap, float** I) {
+    HCGS_CUDA(ctx, grow(ctx, ctx->ws[4], (need_I ? 4 : 3) * n * sizeof(float), &ctx->bytes));
+    HCGS_CUDA(ctx, grow(ctx, ctx->ws[3], (size_t)nblocks * sizeof(float), &ctx->bytes));
+    *dmap = (float*)ctx->ws[4].p;
+    *I = need_I ? *dmap + 3 * n : nullptr;
+    return HCGS_OK;
+}
+
+hcgs_status hcgs_paper_loss(hcgs_ctx* ctx, const float* hologram, const float* I_gt, const float* masks, int B,
+                            const hcgs_optics* o, float lambda_ssim, float* loss, float* g_hologram, float* I_out,
+                            void* stream) {
+    if (!ctx) return HCGS_ERR_INVALID_ARG;
+    TRY(check_optics(ctx, o));
+    REQUIRE(ctx, hologram && I_gt && loss, "NULL argument");
+    REQUIRE(ctx, B >= 1, "B must be >= 1");
+    REQUIRE(ctx, lambda_ssim >= 0.f && std::isfinite(lambda_ssim), "lambda_ssim must be finite and >= 0");
+    cudaSetDevice(ctx->device);
+    const float2* hq;
+    TRY(get_htab(ctx, o, &hq));
+    const size_t planeN = (size_t)o->H * o->W;
+    const size_t nP = (size_t)B * o->C * planeN, nF = (size_t)B * o->L * o->C * planeN;
+    HCGS_CUDA(ctx, grow(ctx, ctx->ws[1], nP * sizeof(float2), &ctx->bytes));
+    HCGS_CUDA(ctx, grow(ctx, ctx->ws[2], nF * sizeof(float2), &ctx->bytes));
+    float2* S1 = (float2*)ctx->ws[1].p;
+    float2* V = (float2*)ctx->ws[2].p;
+    cudaStream_t st = S(stream);
+    int nblocks = 0;
+    TRY(ssim_recon_loss(ctx, nullptr, nullptr, nullptr, nullptr, B, o->L, o->C, o->H, o->W, 0.f, nullptr, nullptr,
+                        &nblocks, nullptr, st));
+    float *dmap, *Iws;
+    TRY(paper_loss_ws(ctx, nF, I_out == nullptr, nblocks, &dmap, &Iws));
+    float* I = I_out ? I_out : Iws;
+    // V_l = ASM(P, -z_l) for every plane: column DFT, row DFT x conj(H), inverse rows, inverse columns
+    TRY(fft_cols(ctx, (const float2*)hologram, S1, B * o->C, o->H, o->W, false, 1.f, st));
+    TRY(rows_spread(ctx, S1, V, B, o->L, o->C, o->H, o->W, hq, true, st));
+    TRY(fft_cols(ctx, V, V, B * o->L * o->C, o->H, o->W, true, 1.f / (float)planeN, st));
+    // I = |V|^2, loss partials, and dL/dV = 2 (dL/dI) V in place over V
+    TRY(ssim_recon_loss(ctx, V, I, I_gt, masks, B, o->L, o->C, o->H, o->W, lambda_ssim, dmap,
+                        (float*)ctx->ws[3].p, &nblocks, nullptr, st));
+    TRY(reduce_sum(ctx, (const float*)ctx->ws[3].p, nblocks, (float)(1.0 / (double)nF), loss, st));
+    if (g_hologram) {
+        // dL/dP = sum over planes of the adjoint propagation of dL/dV
+        TRY(fft_cols(ctx, V, V, B * o->L * o->C, o->H, o->W, false, 1.f, st));
+        TRY(rows_sum(ctx, V, (float2*)g_hologram, B, o->L, o->C, o->H, o->W, hq, false, st));
+        TRY(fft_cols(ctx, (float2*)g_hologram, (float2*)g_hologram, B * o->C, o->H, o->W, true,
+                     1.f / (float)planeN, st));
+    }
+    return HCGS_OK;
+}
+
+hcgs_status hcgs_paper_loss_intensities(hcgs_ctx* ctx, const float* I, const float* I_gt, const float* masks, int B,
+                                        int L, int C, int H, int W, float lambda_ssim, float* loss, float* g_I,
+                                        void* stream) {
+    if (!ctx) return HCGS_ERR_INVALID_ARG;
+    REQUIRE(ctx, I && I_gt && loss && g_I, "NULL argument");
+    REQUIRE(ctx, B >= 1 && L >= 1 && C >= 1 && H >= 1 && W >= 1, "sizes must be >= 1");
+    REQUIRE(ctx, (double)B * L * C * H * W < 2147483648.0 / 4, "too many values");
+    REQUIRE(ctx, lambda_ssim >= 0.f && std::isfinite(lambda_ssim), "lambda_ssim must be finite and >= 0");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = S(stream);
+    const size_t n = (size_t)B * L * C * H * W;
+    int nblocks = 0;
+    TRY(ssim_recon_loss(ctx, nullptr, nullptr, nullptr, nullptr, B, L, C, H, W, 0.f, nullptr, nullptr, &nblocks,
+                        nullptr, st));
+    float *dmap, *unused;
+    TRY(paper_loss_ws(ctx, n, false, nblocks, &dmap, &unused));
+    TRY(ssim_recon_loss(ctx, nullptr, (float*)I, I_gt, masks, B, L, C, H, W, lambda_ssim, dmap,
+                        (float*)ctx->ws[3].p, &nblocks, g_I, st));
+    return reduce_sum(ctx, (const float*)ctx->ws[3].p, nblocks, (float)(1.0 / (double)n), loss, st);
+}
+
+hcgs_status hcgs_adan_step(hcgs_ctx* ctx, float* p, const float* g, float* g_prev, float* m, float* v, float* n,
+                           int64_t count, int step, float lr, float beta1, float beta2, float beta3, float eps,
+                           float weight_decay, void* stream) {
+    if (!ctx) return HCGS_ERR_INVALID_ARG;
+    REQUIRE(ctx, count >= 0, "count must be >= 0");
+    if (count == 0) return HCGS_OK;
+    REQUIRE(ctx, p && g && g_prev && m && v && n, "NULL argument");
+    REQUIRE(ctx, step >= 1, "step counts from 1");
+    REQUIRE(ctx, beta1 >= 0.f && beta1 < 1.f && beta2 >= 0.f && beta2 < 1.f && beta3 >= 0.f && beta3 < 1.f &&
+                     eps >= 0.f && weight_decay >= 0.f,
+            "bad Adan constants");
+    cudaSetDevice(ctx->device);
+    return adan(ctx, p, g, g_prev, m, v, n, count, step, lr, beta1, beta2, beta3, eps, weight_decay, S(stream));
 }
 
 hcgs_status hcgs_adam_step(hcgs_ctx* ctx, float* p, const float* g, float* m, float* v, int64_t n, int step,

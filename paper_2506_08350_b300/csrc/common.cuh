@@ -252,4 +252,11 @@ hcgs_status mlp_mse(hcgs_ctx* ctx, const float* y, const float* tgt, int N, int 
                     cudaStream_t st);
 hcgs_status cast_bf16(hcgs_ctx* ctx, const float* src, uint16_t* dst, int64_t n, cudaStream_t st);
 
+// ---- the paper's objective and optimiser (objective.cu) ----
+hcgs_status ssim_recon_loss(hcgs_ctx* ctx, float2* V, float* I, const float* Igt, const float* M, int B, int L,
+                            int C, int H, int W, float lam, float* dmap, float* partials, int* nblocks_out,
+                            float* gI, cudaStream_t st);
+hcgs_status adan(hcgs_ctx* ctx, float* p, const float* g, float* gp, float* m, float* v, float* n, int64_t count,
+                 int step, float lr, float b1, float b2, float b3, float eps, float wd, cudaStream_t st);
+
 }  // namespace hcgs

@@ -1,12 +1,16 @@
 """Optimisation step of the complex-valued holographic Gaussians on the GPU.
 
-One step (Algorithm 1 without densification; the optimiser is Adam as in the
-training configurations): render the hologram of one view (hcgs_render_view),
-inverse-propagate it to every depth plane and compare the intensities with the
-focal-stack targets (hcgs_focal_stack_loss: Eq. plane2layer_asm and
-Eq. recon_loss as a mean), run the adjoint (hcgs_render_view_backward) and
-update every parameter array with Adam (hcgs_adam_step).  All arithmetic runs
-in the library's kernels; this module only sequences the calls.
+One step (Algorithm 1 without densification): render the hologram of one view
+(hcgs_render_view), inverse-propagate it to every depth plane and compare the
+intensities with the focal-stack targets, run the adjoint
+(hcgs_render_view_backward) and update every parameter array.  Two objectives:
+"mse", the plain focal-stack loss (hcgs_focal_stack_loss: Eq. plane2layer_asm
+and Eq. recon_loss as a mean), and "paper", L_recon + L_SSIM with the plane
+masks (hcgs_paper_loss, Sec. 3); two optimisers: Adam (hcgs_adam_step) and
+Adan (hcgs_adan_step, the optimiser of Sec. 5), optionally with cosine
+annealing of the means' and plane logits' learning rates (minimum 1e-5).
+All arithmetic runs in the library's kernels; this module only sequences the
+calls.
 
 Learning rates follow Sec. 5 (means and plane logits 0.01, scales 0.005,
 amplitude and phase 0.0025, opacity 0.025, rotation 0.001); a learning rate of
@@ -16,27 +20,55 @@ from __future__ import annotations
 
 import torch
 
-from . import PARAM_NAMES, Context, Saved
+from . import PARAM_NAMES, SSIM_LAMBDA, Context, Saved
 
 PAPER_LR = dict(means=0.01, log_scales=0.005, quats=0.001, opacity_logits=0.025, amplitude=0.0025,
                 phase=0.0025, plane_logits=0.01)
+ANNEALED = ("means", "plane_logits")  # arrays whose learning rate follows the cosine schedule
+LR_MIN = 1e-5
+ADAN_BETAS = (0.9, 0.92, 0.99)  # decay factors of the first moment, the gradient difference, the second moment
+
+
+def cosine_lr(step: int, total: int, lr0: float, lr_min: float = LR_MIN) -> float:
+    """Cosine annealing from lr0 at step 0 to lr_min at step ``total`` (held after)."""
+    import math
+    t = min(max(step, 0), total)
+    return lr_min + (lr0 - lr_min) * (1.0 + math.cos(math.pi * t / total)) / 2.0
 
 
 class HologramTrainer:
-    """Adam optimisation of the Gaussian parameters against focal stacks."""
+    """Optimisation of the Gaussian parameters against focal stacks.
 
-    def __init__(self, ctx: Context, params: dict, optics, opts=None, lrs=None, betas=(0.9, 0.999), eps=1e-8,
-                 data_parallel: bool = False):
+    objective: "mse" (plain focal-stack loss) or "paper" (L_recon + L_SSIM;
+    step() then takes the view's plane masks); optimizer: "adam" or "adan";
+    total_steps: if given, the learning rates of the means and plane logits
+    follow cosine annealing over that many steps."""
+
+    def __init__(self, ctx: Context, params: dict, optics, opts=None, lrs=None, betas=None, eps=1e-8,
+                 data_parallel: bool = False, objective: str = "mse", optimizer: str = "adam",
+                 total_steps: int | None = None, lambda_ssim: float = SSIM_LAMBDA, weight_decay: float = 0.0):
+        if objective not in ("mse", "paper"):
+            raise ValueError("objective must be 'mse' or 'paper'")
+        if optimizer not in ("adam", "adan"):
+            raise ValueError("optimizer must be 'adam' or 'adan'")
         self.ctx = ctx
         self.p = params
         self.optics = optics
         self.opts = opts
         self.lrs = dict(PAPER_LR if lrs is None else lrs)
-        self.betas = betas
+        self.objective = objective
+        self.optimizer = optimizer
+        self.betas = betas if betas is not None else ((0.9, 0.999) if optimizer == "adam" else ADAN_BETAS)
         self.eps = eps
+        self.weight_decay = weight_decay
+        self.total_steps = total_steps
+        self.lambda_ssim = lambda_ssim
         self.m = {k: torch.zeros_like(v) for k, v in params.items()}
         self.v = {k: torch.zeros_like(v) for k, v in params.items()}
         self.g = {k: torch.empty_like(v) for k, v in params.items()}
+        if optimizer == "adan":
+            self.n = {k: torch.zeros_like(v) for k, v in params.items()}
+            self.g_prev = {k: torch.zeros_like(v) for k, v in params.items()}
         self.t = 0
         self.data_parallel = data_parallel  # sum gradients over the ranks of the process group
         self.saved = Saved(ctx)
@@ -47,24 +79,41 @@ class HologramTrainer:
         self.loss = torch.zeros(1, dtype=torch.float32, device=dev)
 
     def loss_only(self, viewmat, intr, I_gt):
-        """Focal-stack loss of the current parameters for one view (no update)."""
+        """Plain focal-stack loss of the current parameters for one view (no update)."""
         self.ctx.render_view(self.p, viewmat, intr, self.optics, self.opts, self.holo, None, self.saved)
         self.ctx.focal_stack_loss(self.holo, I_gt, 1, self.optics, self.loss, None, None)
         return self.loss
 
-    def step(self, viewmat, intr, I_gt):
+    def lr(self, k: str) -> float:
+        lr0 = self.lrs.get(k, 0.0)
+        if self.total_steps and k in ANNEALED and lr0 > 0:
+            return cosine_lr(self.t - 1, self.total_steps, lr0)
+        return lr0
+
+    def step(self, viewmat, intr, I_gt, mask=None):
         """One optimisation step on one view; returns the loss before the update
-        (a device tensor)."""
+        (a device tensor).  mask: the view's plane masks [1, L, H, W] (objective
+        "paper"; None = all zero)."""
         self.ctx.render_view(self.p, viewmat, intr, self.optics, self.opts, self.holo, None, self.saved)
-        self.ctx.focal_stack_loss(self.holo, I_gt, 1, self.optics, self.loss, self.gholo, None)
+        if self.objective == "paper":
+            self.ctx.paper_loss(self.holo, I_gt, mask, 1, self.optics, self.loss, self.gholo, None,
+                                lambda_ssim=self.lambda_ssim)
+        else:
+            self.ctx.focal_stack_loss(self.holo, I_gt, 1, self.optics, self.loss, self.gholo, None)
         self.ctx.render_view_backward(self.saved, self.p, self.gholo, self.g)
         if self.data_parallel:
             from .parallel import allreduce_gradients
             allreduce_gradients(self.g)
         self.t += 1
         for k in PARAM_NAMES:
-            lr = self.lrs.get(k, 0.0)
-            if lr > 0:
+            lr = self.lr(k)
+            if lr <= 0:
+                continue
+            if self.optimizer == "adan":
+                b1, b2, b3 = self.betas
+                self.ctx.adan_step(self.p[k], self.g[k], self.g_prev[k], self.m[k], self.v[k], self.n[k], self.t,
+                                   lr, b1, b2, b3, self.eps, self.weight_decay)
+            else:
                 self.ctx.adam_step(self.p[k], self.g[k], self.m[k], self.v[k], self.t, lr, self.betas[0],
                                    self.betas[1], self.eps)
         return self.loss
@@ -86,15 +135,44 @@ def focal_stack(ctx: Context, params: dict, viewmat, intr, optics, opts=None):
     return I
 
 
+def plane_masks(ctx: Context, params: dict, viewmat, intr, optics, opts=None):
+    """Binary plane masks [1, L, H, W] of one view of a scene, the synthetic
+    counterpart of masks cut from a target's quantised depth: a pixel belongs
+    to the plane whose Gaussians cover it most (1 - T_l largest), if that
+    coverage exceeds one half; otherwise to no plane.  The per-plane
+    transmittances come from the library's rasterizer; the arg-max is data
+    preparation on the host."""
+    import numpy as np
+
+    o = optics
+    dev = params["means"].device
+    saved = Saved(ctx)
+    ctx.project(params, viewmat, intr, o, opts, saved)
+    U = torch.empty((1, len(o.plane_z), len(o.wavelengths), o.H, o.W), dtype=torch.complex64, device=dev)
+    T = torch.empty((1, len(o.plane_z), o.H, o.W), dtype=torch.float32, device=dev)
+    ctx.rasterize_planes(saved, U, T)
+    cov = 1.0 - T.cpu().numpy()[0]
+    saved.release()
+    best = np.argmax(cov, axis=0)
+    keep = np.take_along_axis(cov, best[None], axis=0)[0] > 0.5
+    M = np.zeros((1,) + cov.shape, dtype=np.float32)
+    for l in range(cov.shape[0]):
+        M[0, l] = (best == l) & keep
+    return torch.from_numpy(M).to(dev)
+
+
 def ring_run(ctx: Context, optics, N: int, steps: int, n_views: int = 50, footprint: int = 0, teacher_seed: int = 3,
-             student_seed: int = 0, lrs=None, device: str = "cuda"):
+             student_seed: int = 0, lrs=None, device: str = "cuda", objective: str = "mse",
+             optimizer: str = "adam", anneal: bool = False):
     """A full optimisation run on synthetic data: the focal stacks of a teacher
     scene seen from ``n_views`` cameras on a ring are the targets; the student
     has the teacher's geometry and a fresh draw of amplitude and phase
     (amplitude U[0, 1], phase U[0, 2 pi), the plain initialisation) and is
-    optimised one view per step (render, inverse propagation + focal-stack
-    loss, adjoint, Adam on every parameter array).  ``footprint`` selects the
-    FP32 (0) or FP16x2 (1) footprint tier.
+    optimised one view per step (render, inverse propagation + loss, adjoint,
+    optimiser step on every parameter array).  ``footprint`` selects the FP32
+    (0) or FP16x2 (1) footprint tier; ``objective``, ``optimizer`` and
+    ``anneal`` (cosine schedule over ``steps``) as in HologramTrainer; with the
+    "paper" objective the plane masks come from the teacher (plane_masks).
 
     Returns steps/s over the timed steps (CUDA events) and the PSNR over all
     views before and after, PSNR = 10 log10(peak^2 / MSE) with the view's
@@ -113,6 +191,7 @@ def ring_run(ctx: Context, optics, N: int, steps: int, n_views: int = 50, footpr
     teacher = S.make_gaussians(N, o.L, o.C, o.H, o.W, seed=teacher_seed)
     tdev = {k: torch.from_numpy(teacher[k]).to(device) for k in PARAM_NAMES}
     targets = [focal_stack(ctx, tdev, vm, it, o) for vm in vms]
+    masks = [plane_masks(ctx, tdev, vm, it, o, DEFAULT_OPTS) for vm in vms] if objective == "paper" else None
     peaks = [float(t.max().item()) for t in targets]
     del tdev
     student = dict(teacher)
@@ -121,7 +200,8 @@ def ring_run(ctx: Context, optics, N: int, steps: int, n_views: int = 50, footpr
     student["phase"] = (rng.random(teacher["phase"].shape) * 2.0 * np.pi).astype(np.float32)
     p = {k: torch.from_numpy(np.ascontiguousarray(student[k])).to(device) for k in PARAM_NAMES}
     opts = dict(DEFAULT_OPTS, footprint=int(footprint))
-    tr = HologramTrainer(ctx, p, o, opts, lrs=lrs)
+    tr = HologramTrainer(ctx, p, o, opts, lrs=lrs, objective=objective, optimizer=optimizer,
+                         total_steps=steps if anneal else None)
 
     def psnr():
         vals = []
@@ -135,11 +215,13 @@ def ring_run(ctx: Context, optics, N: int, steps: int, n_views: int = 50, footpr
     torch.cuda.synchronize()
     e0.record()
     for s in range(steps):
-        tr.step(vms[s % n_views], it, targets[s % n_views])
+        k = s % n_views
+        tr.step(vms[k], it, targets[k], masks[k] if masks else None)
     e1.record()
     e1.synchronize()
     ms = e0.elapsed_time(e1) / max(steps, 1)
     p1 = psnr()
     tr.saved.release()
     return {"steps_per_s": 1e3 / ms, "ms_per_step": ms, "psnr_start": p0, "psnr_end": p1, "steps": steps,
-            "views": n_views, "footprint": "fp16x2" if footprint else "fp32"}
+            "views": n_views, "footprint": "fp16x2" if footprint else "fp32", "objective": objective,
+            "optimizer": optimizer, "anneal": bool(anneal)}

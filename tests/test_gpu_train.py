@@ -90,3 +90,25 @@ def test_ring_run_fp16_tier_tracks_fp32(P):
     assert r16["psnr_end"] > r16["psnr_start"] + 2.0, r16
     assert abs(r16["psnr_end"] - r32["psnr_end"]) < 0.5, (r32, r16)
     ctx.close()
+
+
+def test_ring_run_paper_objective_with_adan(P):
+    # The paper's recipe on the reduced ring configuration: L_recon + L_SSIM
+    # with teacher plane masks, Adan, cosine annealing of the means' and plane
+    # logits' learning rates; the focal-stack PSNR must rise as with Adam.
+    from paper_2506_08350_b300.train import plane_masks, ring_run
+    ctx = P.Context(0)
+    o = S.workload("c3_512_L8_N500k").optics
+    r = ring_run(ctx, o, 100_000, steps=300, n_views=10, objective="paper", optimizer="adan", anneal=True)
+    print("ring run, paper objective + Adan:", r)
+    assert r["psnr_end"] > r["psnr_start"] + 2.0, r
+    # the masks are one-hot where the teacher covers a pixel
+    g = S.make_gaussians(20_000, o.L, o.C, o.H, o.W, seed=3)
+    gd = {k: torch.from_numpy(g[k]).cuda() for k in P.PARAM_NAMES}
+    vm = torch.from_numpy(S.ring_cameras(1).astype(np.float32)).cuda()
+    it = torch.from_numpy(S.intrinsics(o.H, o.W).astype(np.float32)[None]).cuda()
+    M = plane_masks(ctx, gd, vm, it, o, P.DEFAULT_OPTS).cpu().numpy()
+    assert M.shape == (1, o.L, o.H, o.W)
+    assert set(np.unique(M)) <= {0.0, 1.0} and M.sum(1).max() <= 1.0
+    assert M.sum() > 0.01 * o.H * o.W
+    ctx.close()
