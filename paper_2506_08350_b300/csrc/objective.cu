@@ -9,196 +9,387 @@
 // SSIM is the structural similarity of Wang et al.: local means, variances
 // and covariance under an 11 x 11 Gaussian window (standard deviation 1.5,
 // the image continued by zeros), constants C1 = 0.01^2, C2 = 0.03^2.  With
-// n the number of intensity values, L = lambda_1 + (1/n) sum (d^2 w -
-// lambda_1 S) and dL/dI = (2 d w - lambda_1 (G(dS/dmx) + 2 I G(dS/d<x^2>) +
-// I_gt G(dS/d<xy>))) / n, G the (self-adjoint) window average.
+// n the number of intensity values, L = (1/n) sum (d^2 w + lambda_1 (1 - S))
+// and dL/dI = (2 d w - lambda_1 (G(dS/dmx) + 2 I G(dS/dm2) + I_gt G(dS/dmxy)))
+// / n, G the (self-adjoint) window average, m2 = G(x^2 + y^2) and mxy =
+// G(x y): the variances enter SSIM only through their sum, so pass 1 needs
+// four window averages (x, y, x^2 + y^2, x y) and pass 2 three.
+//
+// Both passes take a 32 x 32 output tile per 128-thread block.  The window is
+// separable: a horizontal pass over the 42 halo rows (each thread slides over
+// four neighbouring columns, so an input is read 3.5 times, not 11) writes the
+// row sums to shared memory, and a vertical pass in registers (each thread
+// owns a column and eight output rows and scatters every row sum into the
+// outputs it touches) finishes the window.  Quantities travel in pairs through
+// packed FP32x2 FMAs.  A shared input row holds 48 columns starting 16-byte
+// aligned three columns left of the halo, so the halo arrives by 16-byte
+// asynchronous copies when rows are 16-byte aligned in memory (W a multiple
+// of 4) and the horizontal pass reads it with 16-byte loads (eight lanes of a
+// row cover all banks).
 #include <cmath>
 
 #include "common.cuh"
 
 namespace hcgs {
 
-constexpr int SS_R = 5;                 // window radius
-constexpr int SS_T = 32;                // output tile (SS_T x SS_T pixels)
-constexpr int SS_E = SS_T + 2 * SS_R;   // tile with halo
-constexpr int SS_TY = 8;                // threads: SS_T x SS_TY, four rows each
+constexpr int SS_R = 5;                  // window radius
+constexpr int SS_TAPS = 2 * SS_R + 1;    // 11
+constexpr int SS_TW = 32, SS_TH = 32;    // output tile
+constexpr int SS_EW = SS_TW + 2 * SS_R;  // halo tile width (42)
+constexpr int SS_EH = SS_TH + 2 * SS_R;  // halo tile height (42)
+constexpr int SS_XW = 48;                // shared row of an input plane: columns x0 - 3 .. x0 + 44
+constexpr int SS_XO = 3;                 // shared column of the halo's first column x0 = tile x - 5
+constexpr int SS_K = 4;                  // columns per thread in the horizontal pass
+constexpr int SS_ROWS = 8;               // output rows per thread in the vertical pass
+constexpr int SS_NT = SS_TH / SS_ROWS * 32;  // 128 threads
 constexpr float SS_C1 = 0.01f * 0.01f, SS_C2 = 0.03f * 0.03f;
+static_assert(SS_XW % 4 == 0 && SS_XO + SS_EW <= SS_XW && (SS_XO + SS_R) % 4 == 0, "row layout");
 
-// the normalised 1D factor of the window, formed on the host in double
-__constant__ float c_ssim_g[2 * SS_R + 1];
+// the normalised 1D factor of the window, formed on the host in double, and
+// the same taps paired for the packed FP32x2 FMAs
+__constant__ float c_ssim_g[SS_TAPS];
+__constant__ float2 c_ssim_g2[SS_TAPS];
 
 static cudaError_t ssim_window_upload() {
-    static bool done = false;  // one upload per process (the table never changes)
-    if (done) return cudaSuccess;
-    double g[2 * SS_R + 1], s = 0.0;
-    for (int k = 0; k <= 2 * SS_R; k++) {
+    static bool done[256] = {};  // per device (the table never changes)
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 256 && done[dev]) return cudaSuccess;
+    double g[SS_TAPS], s = 0.0;
+    for (int k = 0; k < SS_TAPS; k++) {
         const double x = k - SS_R;
         g[k] = std::exp(-x * x / (2.0 * 1.5 * 1.5));
         s += g[k];
     }
-    float gf[2 * SS_R + 1];
-    for (int k = 0; k <= 2 * SS_R; k++) gf[k] = (float)(g[k] / s);
-    const cudaError_t e = cudaMemcpyToSymbol(c_ssim_g, gf, sizeof(gf));
-    if (e == cudaSuccess) done = true;
+    float gf[SS_TAPS];
+    for (int k = 0; k < SS_TAPS; k++) gf[k] = (float)(g[k] / s);
+    float2 gf2[SS_TAPS];
+    for (int k = 0; k < SS_TAPS; k++) gf2[k] = make_float2(gf[k], gf[k]);
+    e = cudaMemcpyToSymbol(c_ssim_g, gf, sizeof(gf));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_ssim_g2, gf2, sizeof(gf2));
+    if (e == cudaSuccess && dev >= 0 && dev < 256) done[dev] = true;
     return e;
 }
 
-// Window averages of NQ quantities at the tile's pixels: q holds the NQ
-// inputs on the halo tile [NQ][SS_E][SS_E] (zeros outside the image); the
-// horizontal pass goes to h [NQ][SS_E][SS_T], the vertical one to the caller.
-template <int NQ>
-__device__ __forceinline__ void window_rows(const float (*q)[SS_E][SS_E], float (*h)[SS_E][SS_T]) {
-    for (int e = threadIdx.y * SS_T + threadIdx.x; e < SS_E * SS_T; e += SS_T * SS_TY) {
-        const int r = e / SS_T, cc = e % SS_T;
+__device__ __forceinline__ float2 gtap(int t) { return c_ssim_g2[t]; }
+
+// Horizontal window sums of NP quantity pairs and NS single quantities
+// derived from NIN input planes: inp[NIN][SS_EH][SS_XW] -> h2[NP][SS_EH][SS_TW]
+// (float2) and h1[NS][SS_EH][SS_TW].  quant(in, pairs, singles) forms the
+// quantities of one input column.
+template <int NIN, int NP, int NS, class Quant>
+__device__ __forceinline__ void ssim_rows(const float (*inp)[SS_EH][SS_XW], float2 (*h2)[SS_EH][SS_TW],
+                                          float (*h1)[SS_EH][SS_TW], Quant quant) {
+    constexpr int NS1 = NS > 0 ? NS : 1;
+    constexpr int NV = (SS_XO + SS_K + 2 * SS_R + 3) / 4;  // 16-byte loads per row segment (5)
+    for (int it = threadIdx.x; it < SS_EH * (SS_TW / SS_K); it += SS_NT) {
+        const int r = it / (SS_TW / SS_K), c0 = (it % (SS_TW / SS_K)) * SS_K;
+        float2 a2[NP][SS_K];
+        float a1[NS1][SS_K];
 #pragma unroll
-        for (int k = 0; k < NQ; k++) {
-            float s = 0.f;
+        for (int k = 0; k < SS_K; k++) {
 #pragma unroll
-            for (int t = 0; t <= 2 * SS_R; t++) s = fmaf(c_ssim_g[t], q[k][r][cc + t], s);
-            h[k][r][cc] = s;
+            for (int q = 0; q < NP; q++) a2[q][k] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int q = 0; q < NS1; q++) a1[q][k] = 0.f;
         }
+        // the row segment of the outputs c0 .. c0 + 3: halo columns c0 .. c0 + 13
+        float seg[NIN][4 * NV];
+#pragma unroll
+        for (int a = 0; a < NIN; a++) {
+            const float4* src = reinterpret_cast<const float4*>(&inp[a][r][c0]);
+#pragma unroll
+            for (int u = 0; u < NV; u++) {
+                const float4 v = src[u];
+                seg[a][4 * u] = v.x;
+                seg[a][4 * u + 1] = v.y;
+                seg[a][4 * u + 2] = v.z;
+                seg[a][4 * u + 3] = v.w;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < SS_K + 2 * SS_R; i++) {
+            float in[NIN];
+            float2 v2[NP];
+            float v1[NS1];
+#pragma unroll
+            for (int a = 0; a < NIN; a++) in[a] = seg[a][SS_XO + i];
+            quant(in, v2, v1);
+#pragma unroll
+            for (int k = 0; k < SS_K; k++) {
+                const int t = i - k;
+                if (t >= 0 && t < SS_TAPS) {
+#pragma unroll
+                    for (int q = 0; q < NP; q++) a2[q][k] = __ffma2_rn(gtap(t), v2[q], a2[q][k]);
+#pragma unroll
+                    for (int q = 0; q < NS; q++) a1[q][k] = fmaf(c_ssim_g[t], v1[q], a1[q][k]);
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NP; q++) {
+            float4* d = reinterpret_cast<float4*>(&h2[q][r][c0]);
+            d[0] = make_float4(a2[q][0].x, a2[q][0].y, a2[q][1].x, a2[q][1].y);
+            d[1] = make_float4(a2[q][2].x, a2[q][2].y, a2[q][3].x, a2[q][3].y);
+        }
+#pragma unroll
+        for (int q = 0; q < NS; q++)
+            *reinterpret_cast<float4*>(&h1[q][r][c0]) = make_float4(a1[q][0], a1[q][1], a1[q][2], a1[q][3]);
     }
 }
 
-template <int NQ>
-__device__ __forceinline__ void window_col(const float (*h)[SS_E][SS_T], int r, int cc, float (&out)[NQ]) {
+// Vertical window sums for the thread's column and SS_ROWS output rows.
+template <int NP, int NS>
+__device__ __forceinline__ void ssim_cols(const float2 (*h2)[SS_EH][SS_TW], const float (*h1)[SS_EH][SS_TW],
+                                          int col, int row0, float2 (&o2)[NP][SS_ROWS],
+                                          float (&o1)[NS > 0 ? NS : 1][SS_ROWS]) {
 #pragma unroll
-    for (int k = 0; k < NQ; k++) {
-        float s = 0.f;
+    for (int k = 0; k < SS_ROWS; k++) {
 #pragma unroll
-        for (int t = 0; t <= 2 * SS_R; t++) s = fmaf(c_ssim_g[t], h[k][r + t][cc], s);
-        out[k] = s;
+        for (int q = 0; q < NP; q++) o2[q][k] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < NS; q++) o1[q][k] = 0.f;
+    }
+#pragma unroll
+    for (int i = 0; i < SS_ROWS + 2 * SS_R; i++) {
+        float2 v2[NP];
+        float v1[NS > 0 ? NS : 1];
+#pragma unroll
+        for (int q = 0; q < NP; q++) v2[q] = h2[q][row0 + i][col];
+#pragma unroll
+        for (int q = 0; q < NS; q++) v1[q] = h1[q][row0 + i][col];
+#pragma unroll
+        for (int k = 0; k < SS_ROWS; k++) {
+            const int t = i - k;
+            if (t >= 0 && t < SS_TAPS) {
+#pragma unroll
+                for (int q = 0; q < NP; q++) o2[q][k] = __ffma2_rn(gtap(t), v2[q], o2[q][k]);
+#pragma unroll
+                for (int q = 0; q < NS; q++) o1[q][k] = fmaf(c_ssim_g[t], v1[q], o1[q][k]);
+            }
+        }
     }
 }
 
 __device__ __forceinline__ float block_sum(float v, float* red) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int w = (threadIdx.y * SS_T + threadIdx.x) >> 5;
-    if ((threadIdx.x & 31) == 0) red[w] = v;
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
     float s = 0.f;
-    if (threadIdx.x == 0 && threadIdx.y == 0)
-        for (int i = 0; i < SS_T * SS_TY / 32; i++) s += red[i];  // fixed order: deterministic
+    if (threadIdx.x == 0)
+        for (int i = 0; i < SS_NT / 32; i++) s += red[i];  // fixed order: deterministic
     return s;
 }
 
-// Pass 1 over each (view, plane, channel) image: the SSIM map's partial
-// derivatives dS/dmx, dS/d<x^2>, dS/d<xy> (written to dmap[3][n]) and the
-// block's part of sum (d^2 w + lambda (1 - S)).  The intensities come either
-// from I or, when V is given, as |V|^2 of the propagated field (then also
-// written to I for pass 2).  grid (tiles x, tiles y, B L C).
-template <bool FROM_FIELD>
-__global__ void __launch_bounds__(SS_T * SS_TY)
+// Asynchronous 4- / 8-byte copies global -> shared; a copy with valid = false
+// reads nothing and writes zeros (the window's zero continuation).
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, bool valid) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_addr(dst)), "l"(src),
+                 "r"(valid ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, bool valid) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_addr(dst)), "l"(src),
+                 "r"(valid ? 8 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst)), "l"(src),
+                 "r"(valid ? 16 : 0)
+                 : "memory");
+}
+
+// Copies of the halo rows y0 .. y0 + SS_EH - 1 of one image into shared rows
+// of SS_XW columns starting at column xs of the image (elements of ES bytes).
+// VEC: 16-byte chunks (xs and the image's row pitch 16-byte aligned: a chunk
+// lies wholly inside or wholly outside the row); otherwise one element per
+// copy, the halo columns only.  put(dst_row, dst_col, off, ok, bytes) issues
+// one copy of `bytes` at element offset `off` of the image (0 where ok is false).
+template <bool VEC, int ES, class Put>
+__device__ __forceinline__ void halo_copy(int xs, int y0, int H, int W, Put put) {
+    if constexpr (VEC) {
+        constexpr int PER = 16 / ES, NCH = SS_XW / PER, TOT = SS_EH * NCH;
+#pragma unroll
+        for (int k = 0; k < (TOT + SS_NT - 1) / SS_NT; k++) {
+            const int e = threadIdx.x + k * SS_NT;
+            const int r = e / NCH, ch = e % NCH, gy = y0 + r, gx = xs + ch * PER;
+            const bool ok = gy >= 0 && gy < H && gx >= 0 && gx < W;
+            if (e < TOT) put(r, ch * PER, ok ? (unsigned)gy * (unsigned)W + gx : 0u, ok, 16);
+        }
+    } else {
+        const int lane = threadIdx.x & 31;
+        const int gx0 = xs + SS_XO + lane, gx1 = gx0 + 32;
+        const bool c0ok = gx0 >= 0 && gx0 < W, c1ok = lane < SS_EW - 32 && gx1 >= 0 && gx1 < W;
+        for (int r = threadIdx.x >> 5; r < SS_EH; r += SS_NT / 32) {
+            const int gy = y0 + r;
+            const bool rok = gy >= 0 && gy < H;
+            const unsigned row = rok ? (unsigned)gy * (unsigned)W : 0u;
+            put(r, SS_XO + lane, rok && c0ok ? row + gx0 : 0u, rok && c0ok, ES);
+            if (lane < SS_EW - 32) put(r, SS_XO + 32 + lane, rok && c1ok ? row + gx1 : 0u, rok && c1ok, ES);
+        }
+    }
+}
+
+__device__ __forceinline__ void cp_async_n(void* dst, const void* src, bool ok, int bytes) {
+    if (bytes == 16)
+        cp_async16(dst, src, ok);
+    else if (bytes == 8)
+        cp_async8(dst, src, ok);
+    else
+        cp_async4(dst, src, ok);
+}
+
+// Pass 1 over each (view, plane, channel) image: the partial derivatives of
+// the SSIM map dS/dmx, dS/dm2, dS/dmxy (to dmap[3][n]) and the block's part of
+// sum (d^2 w + lambda (1 - S)).  The intensities come either from I or, when
+// V is given, as |V|^2 of the propagated field (then also written to I for
+// pass 2).  grid (tiles x, tiles y, B L C), SS_NT threads.
+template <bool FROM_FIELD, bool VEC>
+__global__ void __launch_bounds__(SS_NT)
     k_ssim_partials(const float2* __restrict__ V, float* __restrict__ I, const float* __restrict__ Igt,
                     const float* __restrict__ M, int C, int H, int W, float lam, float* __restrict__ dmap,
                     float* __restrict__ partials) {
-    __shared__ float q[2][SS_E][SS_E];
-    __shared__ float h[5][SS_E][SS_T];
-    __shared__ float red[SS_T * SS_TY / 32];
+    __shared__ __align__(16) float inp[2][SS_EH][SS_XW];
+    __shared__ __align__(16) float2 h[2][SS_EH][SS_TW];
+    __shared__ float red[SS_NT / 32];
     const int img = blockIdx.z;
     const size_t HW = (size_t)H * W, n = (size_t)gridDim.z * HW;
-    const float* y = Igt + (size_t)img * HW;
+    const int xs = blockIdx.x * SS_TW - SS_R - SS_XO, y0 = blockIdx.y * SS_TH - SS_R;
+    const float* ysrc = Igt + (size_t)img * HW;
+    const float* xsrc = I + (size_t)img * HW;
+    const float2* vsrc = FROM_FIELD ? V + (size_t)img * HW : nullptr;
+    // the field's halo is staged in the row-sum buffer (idle until the row pass)
+    float2 (*stage)[SS_XW] = reinterpret_cast<float2 (*)[SS_XW]>(&h[0][0][0]);
+    static_assert(sizeof(float2) * SS_EH * SS_XW <= sizeof(h), "staging fits");
+    halo_copy<VEC, 4>(xs, y0, H, W, [&](int r, int c, unsigned off, bool ok, int bytes) {
+        cp_async_n(&inp[1][r][c], ysrc + off, ok, bytes);
+        if constexpr (!FROM_FIELD) cp_async_n(&inp[0][r][c], xsrc + off, ok, bytes);
+    });
+    if constexpr (FROM_FIELD)
+        halo_copy<VEC, 8>(xs, y0, H, W, [&](int r, int c, unsigned off, bool ok, int bytes) {
+            cp_async_n(&stage[r][c], vsrc + off, ok, bytes);
+        });
+    // the mask values of the thread's outputs, needed in the epilogue
+    const int col = threadIdx.x & 31, row0 = (threadIdx.x >> 5) * SS_ROWS;
     const float* m = M ? M + (size_t)(img / C) * HW : nullptr;  // masks per (view, plane)
-    const int x0 = blockIdx.x * SS_T - SS_R, y0 = blockIdx.y * SS_T - SS_R;
-    for (int e = threadIdx.y * SS_T + threadIdx.x; e < SS_E * SS_E; e += SS_T * SS_TY) {
-        const int r = e / SS_E, cc = e % SS_E, gy = y0 + r, gx = x0 + cc;
-        const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
-        const size_t p = (size_t)img * HW + (size_t)gy * W + gx;
-        float xv = 0.f;
-        if (in) {
-            if constexpr (FROM_FIELD) {
-                const float2 v = V[p];
-                xv = fmaf(v.x, v.x, v.y * v.y);
-            } else {
-                xv = I[p];
+    const int gx = blockIdx.x * SS_TW + col;
+    float mv[SS_ROWS];
+#pragma unroll
+    for (int k = 0; k < SS_ROWS; k++) {
+        const int gy = blockIdx.y * SS_TH + row0 + k;
+        mv[k] = (m && gx < W && gy < H) ? m[(size_t)gy * W + gx] : 0.f;
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    if constexpr (FROM_FIELD) {
+        const int lane = threadIdx.x & 31;
+        for (int r = threadIdx.x >> 5; r < SS_EH; r += SS_NT / 32) {
+            const float2 v = stage[r][SS_XO + lane];
+            inp[0][r][SS_XO + lane] = fmaf(v.x, v.x, v.y * v.y);
+            if (lane < SS_EW - 32) {
+                const float2 u = stage[r][SS_XO + 32 + lane];
+                inp[0][r][SS_XO + 32 + lane] = fmaf(u.x, u.x, u.y * u.y);
             }
         }
-        q[0][r][cc] = xv;
-        q[1][r][cc] = in ? y[(size_t)gy * W + gx] : 0.f;
+        __syncthreads();
     }
+    // row sums of the pairs (x, y) and (x^2 + y^2, x y)
+    ssim_rows<2, 2, 0>(inp, h, nullptr, [](const float (&a)[2], float2 (&v2)[2], float (&)[1]) {
+        v2[0] = make_float2(a[0], a[1]);
+        v2[1] = make_float2(fmaf(a[0], a[0], a[1] * a[1]), a[0] * a[1]);
+    });
     __syncthreads();
-    // horizontal window sums of x, y, x^2, y^2, x y
-    for (int e = threadIdx.y * SS_T + threadIdx.x; e < SS_E * SS_T; e += SS_T * SS_TY) {
-        const int r = e / SS_T, cc = e % SS_T;
-        float s[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int t = 0; t <= 2 * SS_R; t++) {
-            const float a = q[0][r][cc + t], b = q[1][r][cc + t], g = c_ssim_g[t];
-            s[0] = fmaf(g, a, s[0]);
-            s[1] = fmaf(g, b, s[1]);
-            s[2] = fmaf(g, a * a, s[2]);
-            s[3] = fmaf(g, b * b, s[3]);
-            s[4] = fmaf(g, a * b, s[4]);
-        }
-#pragma unroll
-        for (int k = 0; k < 5; k++) h[k][r][cc] = s[k];
-    }
-    __syncthreads();
+    float2 mu[2][SS_ROWS];
+    float unused[1][SS_ROWS];
+    ssim_cols<2, 0>(h, nullptr, col, row0, mu, unused);
     float acc = 0.f;
-    const int cc = threadIdx.x, gx = blockIdx.x * SS_T + cc;
 #pragma unroll
-    for (int k = 0; k < SS_T / SS_TY; k++) {
-        const int r = threadIdx.y + k * SS_TY, gy = blockIdx.y * SS_T + r;
+    for (int k = 0; k < SS_ROWS; k++) {
+        const int gy = blockIdx.y * SS_TH + row0 + k;
         if (gx >= W || gy >= H) continue;
-        float mu[5];
-        window_col<5>(h, r, cc, mu);
-        const float mx = mu[0], my = mu[1];
-        const float sxx = mu[2] - mx * mx, syy = mu[3] - my * my, sxy = mu[4] - mx * my;
-        const float a = 2.f * mx * my + SS_C1, b = 2.f * sxy + SS_C2;
-        const float c = mx * mx + my * my + SS_C1, d = sxx + syy + SS_C2;
-        const float icd = 1.f / (c * d);
+        const float mx = mu[0][k].x, my = mu[0][k].y, m2 = mu[1][k].x, mxy = mu[1][k].y;
+        const float c = fmaf(mx, mx, fmaf(my, my, SS_C1));
+        const float a = fmaf(2.f * mx, my, SS_C1);
+        const float b = 2.f * (mxy - mx * my) + SS_C2;
+        const float d = m2 - mx * mx - my * my + SS_C2;
+        const float icd = __frcp_rn(c * d);
         const float S = a * b * icd;
+        const float Sc = S * d * icd, Sd = S * c * icd;  // S / c, S / d
         const size_t p = (size_t)img * HW + (size_t)gy * W + gx;
-        dmap[p] = 2.f * my * (b - a) * icd - 2.f * mx * S / c + 2.f * mx * S / d;
-        dmap[n + p] = -S / d;
+        dmap[p] = 2.f * my * (b - a) * icd + 2.f * mx * (Sd - Sc);
+        dmap[n + p] = -Sd;
         dmap[2 * n + p] = 2.f * a * icd;
-        const float xv = q[0][r + SS_R][cc + SS_R], yv = q[1][r + SS_R][cc + SS_R];
+        const float xv = inp[0][row0 + k + SS_R][SS_XO + SS_R + col];
+        const float yv = inp[1][row0 + k + SS_R][SS_XO + SS_R + col];
         if constexpr (FROM_FIELD) I[p] = xv;
         const float dl = xv - yv;
-        const float w = 1.f + (m ? m[(size_t)gy * W + gx] : 0.f) + yv * yv;
+        const float w = 1.f + mv[k] + yv * yv;
         acc += dl * dl * w + lam * (1.f - S);
     }
     const float s = block_sum(acc, red);
-    if (threadIdx.x == 0 && threadIdx.y == 0)
-        partials[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = s;
+    if (threadIdx.x == 0) partials[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = s;
 }
 
 // Pass 2: g = dL/dI = (2 d w - lambda (G dmap0 + 2 I G dmap1 + I_gt G dmap2)) / n,
 // written to gI, or (TO_FIELD) turned into dL/dV = 2 g V in place over V.
-template <bool TO_FIELD>
-__global__ void __launch_bounds__(SS_T * SS_TY)
+template <bool TO_FIELD, bool VEC>
+__global__ void __launch_bounds__(SS_NT)
     k_ssim_grad(const float* __restrict__ I, const float* __restrict__ Igt, const float* __restrict__ M, int C,
                 int H, int W, float lam, float inv_n, const float* __restrict__ dmap, float* __restrict__ gI,
                 float2* __restrict__ V) {
-    __shared__ float q[3][SS_E][SS_E];
-    __shared__ float h[3][SS_E][SS_T];
+    __shared__ __align__(16) float inp[3][SS_EH][SS_XW];
+    __shared__ __align__(16) float2 h2[1][SS_EH][SS_TW];
+    __shared__ __align__(16) float h1[1][SS_EH][SS_TW];
     const int img = blockIdx.z;
     const size_t HW = (size_t)H * W, n = (size_t)gridDim.z * HW;
-    const int x0 = blockIdx.x * SS_T - SS_R, y0 = blockIdx.y * SS_T - SS_R;
-    for (int e = threadIdx.y * SS_T + threadIdx.x; e < SS_E * SS_E; e += SS_T * SS_TY) {
-        const int r = e / SS_E, cc = e % SS_E, gy = y0 + r, gx = x0 + cc;
-        const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
-        const size_t p = (size_t)img * HW + (size_t)gy * W + gx;
-#pragma unroll
-        for (int k = 0; k < 3; k++) q[k][r][cc] = in ? dmap[k * n + p] : 0.f;
-    }
-    __syncthreads();
-    window_rows<3>(q, h);
-    __syncthreads();
-    const int cc = threadIdx.x, gx = blockIdx.x * SS_T + cc;
+    const int xs = blockIdx.x * SS_TW - SS_R - SS_XO, y0 = blockIdx.y * SS_TH - SS_R;
+    const float* d0 = dmap + (size_t)img * HW;
+    const float* d1 = d0 + n;
+    const float* d2 = d1 + n;
+    halo_copy<VEC, 4>(xs, y0, H, W, [&](int r, int c, unsigned off, bool ok, int bytes) {
+        cp_async_n(&inp[0][r][c], d0 + off, ok, bytes);
+        cp_async_n(&inp[1][r][c], d1 + off, ok, bytes);
+        cp_async_n(&inp[2][r][c], d2 + off, ok, bytes);
+    });
+    // the thread's own I, I_gt, M for the epilogue, loaded meanwhile
+    const int col = threadIdx.x & 31, row0 = (threadIdx.x >> 5) * SS_ROWS;
     const float* m = M ? M + (size_t)(img / C) * HW : nullptr;
+    const int gx = blockIdx.x * SS_TW + col;
+    float xo[SS_ROWS], yo[SS_ROWS], mv[SS_ROWS];
+    float2 vo[TO_FIELD ? SS_ROWS : 1];
 #pragma unroll
-    for (int k = 0; k < SS_T / SS_TY; k++) {
-        const int r = threadIdx.y + k * SS_TY, gy = blockIdx.y * SS_T + r;
-        if (gx >= W || gy >= H) continue;
-        float gd[3];
-        window_col<3>(h, r, cc, gd);
+    for (int k = 0; k < SS_ROWS; k++) {
+        const int gy = blockIdx.y * SS_TH + row0 + k;
+        const bool in = gx < W && gy < H;
         const size_t p = (size_t)img * HW + (size_t)gy * W + gx;
-        const float xv = I[p], yv = Igt[p];
-        const float w = 1.f + (m ? m[(size_t)gy * W + gx] : 0.f) + yv * yv;
-        const float g = inv_n * (2.f * (xv - yv) * w - lam * (gd[0] + 2.f * xv * gd[1] + yv * gd[2]));
+        xo[k] = in ? I[p] : 0.f;
+        yo[k] = in ? Igt[p] : 0.f;
+        mv[k] = (m && in) ? m[(size_t)gy * W + gx] : 0.f;
+        if constexpr (TO_FIELD) vo[k] = in ? V[p] : make_float2(0.f, 0.f);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    ssim_rows<3, 1, 1>(inp, h2, h1, [](const float (&a)[3], float2 (&v2)[1], float (&v1)[1]) {
+        v2[0] = make_float2(a[0], a[1]);
+        v1[0] = a[2];
+    });
+    __syncthreads();
+    float2 g01[1][SS_ROWS];
+    float g2[1][SS_ROWS];
+    ssim_cols<1, 1>(h2, h1, col, row0, g01, g2);
+#pragma unroll
+    for (int k = 0; k < SS_ROWS; k++) {
+        const int gy = blockIdx.y * SS_TH + row0 + k;
+        if (gx >= W || gy >= H) continue;
+        const size_t p = (size_t)img * HW + (size_t)gy * W + gx;
+        const float xv = xo[k], yv = yo[k];
+        const float w = 1.f + mv[k] + yv * yv;
+        const float g = inv_n * (2.f * (xv - yv) * w - lam * (g01[0][k].x + 2.f * xv * g01[0][k].y + yv * g2[0][k]));
         if constexpr (TO_FIELD) {
-            const float2 v = V[p];
+            const float2 v = vo[TO_FIELD ? k : 0];
             V[p] = make_float2(2.f * g * v.x, 2.f * g * v.y);
         } else {
             gI[p] = g;
@@ -213,23 +404,32 @@ __global__ void __launch_bounds__(SS_T * SS_TY)
 hcgs_status ssim_recon_loss(hcgs_ctx* ctx, float2* V, float* I, const float* Igt, const float* M, int B, int L,
                             int C, int H, int W, float lam, float* dmap, float* partials, int* nblocks_out,
                             float* gI, cudaStream_t st) {
-    const dim3 grid((W + SS_T - 1) / SS_T, (H + SS_T - 1) / SS_T, B * L * C);
+    const dim3 grid((W + SS_TW - 1) / SS_TW, (H + SS_TH - 1) / SS_TH, B * L * C);
     *nblocks_out = (int)(grid.x * grid.y * grid.z);
     if (!partials) return HCGS_OK;  // size query
     HCGS_CUDA(ctx, ssim_window_upload());
-    const dim3 blk(SS_T, SS_TY);
+    const int blk = SS_NT;
     const float inv_n = (float)(1.0 / ((double)B * L * C * H * W));
-    if (V) {
-        HCGS_KERNEL(ctx, "k_ssim_partials", st,
-                    k_ssim_partials<true><<<grid, blk, 0, st>>>(V, I, Igt, M, C, H, W, lam, dmap, partials));
-        HCGS_KERNEL(ctx, "k_ssim_grad", st,
-                    k_ssim_grad<true><<<grid, blk, 0, st>>>(I, Igt, M, C, H, W, lam, inv_n, dmap, nullptr, V));
-    } else {
-        HCGS_KERNEL(ctx, "k_ssim_partials", st,
-                    k_ssim_partials<false><<<grid, blk, 0, st>>>(nullptr, I, Igt, M, C, H, W, lam, dmap, partials));
-        HCGS_KERNEL(ctx, "k_ssim_grad", st,
-                    k_ssim_grad<false><<<grid, blk, 0, st>>>(I, Igt, M, C, H, W, lam, inv_n, dmap, gI, nullptr));
-    }
+    // 16-byte copies need 16-byte aligned rows: W a multiple of 4 and aligned bases
+    auto al = [](const void* q) { return q == nullptr || ((uintptr_t)q & 15) == 0; };
+    const bool vec = W % 4 == 0 && al(V) && al(I) && al(Igt) && al(dmap);
+#define HCGS_SSIM_LAUNCH(F, VEC)                                                                              \
+    do {                                                                                                      \
+        HCGS_KERNEL(ctx, "k_ssim_partials", st,                                                               \
+                    (k_ssim_partials<F, VEC><<<grid, blk, 0, st>>>(V, I, Igt, M, C, H, W, lam, dmap, partials))); \
+        HCGS_KERNEL(ctx, "k_ssim_grad", st,                                                                   \
+                    (k_ssim_grad<F, VEC><<<grid, blk, 0, st>>>(I, Igt, M, C, H, W, lam, inv_n, dmap,            \
+                                                               F ? nullptr : gI, F ? V : nullptr)));          \
+    } while (0)
+    if (V && vec)
+        HCGS_SSIM_LAUNCH(true, true);
+    else if (V)
+        HCGS_SSIM_LAUNCH(true, false);
+    else if (vec)
+        HCGS_SSIM_LAUNCH(false, true);
+    else
+        HCGS_SSIM_LAUNCH(false, false);
+#undef HCGS_SSIM_LAUNCH
     return HCGS_OK;
 }
 
