@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--train-steps", type=int, default=1000,
                     help="steps of the ring optimisation run per footprint tier (0: skip)")
     ap.add_argument("--kernels-out", default=None, help="write the per-kernel table (JSON) here")
+    ap.add_argument("--objective-only", action="store_true",
+                    help="time only the two objectives on one view of the workload's optics and print them")
     return ap.parse_args()
 
 
@@ -565,9 +567,24 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_objective_only(args):
+    import torch
+    torch.cuda.set_device(0)
+    import paper_2506_08350_b300 as P
+    ctx = P.Context(0)
+    o = S.workload(args.workload).optics
+    pk = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else None
+    out = measure_losses(ctx, P, S, o, torch.device("cuda", 0), pk["hbm_gbs"] if pk else 6400.0,
+                         steps=args.steps, warmup=args.warmup)
+    ctx.close()
+    print(json.dumps({"workload": args.workload, "objective": out}), flush=True)
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.objective_only:
+        run_objective_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
