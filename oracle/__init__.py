@@ -21,6 +21,11 @@ What each function follows (arXiv 2506.08350):
 * ``paper_loss``         the paper's training loss L_recon + L_SSIM (masked
                          reconstruction loss and structural similarity);
 * ``adan_step``, ``cosine_lr``  the paper's optimiser and learning-rate schedule;
+* ``philox4x32_10``, ``philox_normals``  the counter-based generator that
+                         draws the densification noise (Salmon et al. 2011)
+                         and standard normals from it by Box-Muller;
+* ``densify_accumulate``, ``densify``  Algorithm 1's pruning and phase-aware
+                         clone / split (the 3DGS densification rules);
 * ``mlp_*``              the learned-initialisation network (no counterpart in
                          the paper): plain float64 matrix products.
 
@@ -418,6 +423,166 @@ def cosine_lr(step: int, total: int, lr0: float, lr_min: float) -> float:
     import math
     t = min(max(step, 0), total)
     return lr_min + (lr0 - lr_min) * (1.0 + math.cos(math.pi * t / total)) / 2.0
+
+
+# ----------------------------------------------------------------------------
+# densification (Algorithm 1) and its counter-based noise
+# ----------------------------------------------------------------------------
+PHILOX_M = (0xD2511F53, 0xCD9E8D57)   # round multipliers of Philox4x32
+PHILOX_W = (0x9E3779B9, 0xBB67AE85)   # Weyl key increments
+
+
+def philox4x32_10(ctr, key):
+    """Philox4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, SC'11): ctr
+    [..., 4] and key [..., 2] uint32 -> [..., 4] uint32.  Each round multiplies
+    words 0 and 2 by the two constants (64-bit products split into high and low
+    halves), permutes and mixes in the key; the key is bumped by the Weyl
+    increments between rounds."""
+    c = np.array(ctr, dtype=np.uint64) & 0xFFFFFFFF
+    k = np.array(key, dtype=np.uint64) & 0xFFFFFFFF
+    c0, c1, c2, c3 = (c[..., i].copy() for i in range(4))
+    k0, k1 = k[..., 0].copy(), k[..., 1].copy()
+    mask = np.uint64(0xFFFFFFFF)
+    for r in range(10):
+        if r > 0:
+            k0 = (k0 + np.uint64(PHILOX_W[0])) & mask
+            k1 = (k1 + np.uint64(PHILOX_W[1])) & mask
+        p0 = c0 * np.uint64(PHILOX_M[0])
+        p1 = c2 * np.uint64(PHILOX_M[1])
+        hi0, lo0 = p0 >> np.uint64(32), p0 & mask
+        hi1, lo1 = p1 >> np.uint64(32), p1 & mask
+        c0, c1, c2, c3 = hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0
+    return np.stack([c0, c1, c2, c3], axis=-1).astype(np.uint32)
+
+
+def philox_words(seed: int, n_words: int, stream: int = 0) -> np.ndarray:
+    """n_words uint32 of the stream (seed, stream): block b is
+    Philox(counter = (b, stream, 0, 0), key = (seed low, seed high))."""
+    nb = (n_words + 3) // 4
+    ctr = np.zeros((nb, 4), dtype=np.uint64)
+    ctr[:, 0] = np.arange(nb, dtype=np.uint64)
+    ctr[:, 1] = stream & 0xFFFFFFFF
+    key = np.array([seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF], dtype=np.uint64)
+    return philox4x32_10(ctr, np.broadcast_to(key, (nb, 2))).reshape(-1)[:n_words]
+
+
+def philox_normals(seed: int, n: int, stream: int = 0) -> np.ndarray:
+    """n standard normals (float64) from the words of ``philox_words``: each
+    word pair (a, b) gives u = (a + 1/2) 2^-32, v = (b + 1/2) 2^-32 and, by
+    Box-Muller, sqrt(-2 ln u) (cos 2 pi v, sin 2 pi v)."""
+    m = (n + 1) // 2
+    w = philox_words(seed, 2 * m, stream).astype(np.float64).reshape(m, 2)
+    u = (w[:, 0] + 0.5) * 2.0 ** -32
+    v = (w[:, 1] + 0.5) * 2.0 ** -32
+    r = np.sqrt(-2.0 * np.log(u))
+    z = np.stack([r * np.cos(2 * np.pi * v), r * np.sin(2 * np.pi * v)], axis=1).reshape(-1)
+    return z[:n]
+
+
+DENSIFY_OPTS = dict(grad_threshold=2e-4, split_scale=0.02, prune_opacity=5e-3, prune_scale=0.0,
+                    split_shrink=1.6, phase_noise=0.1)
+KEEP, PRUNE, CLONE, SPLIT = 0, 1, 2, 3
+
+
+def densify_accumulate(accum, denom, valid, gmu, H: int, W: int):
+    """Add one view's screen-space mean gradients to the densification
+    statistics: for every visible Gaussian, accum += |(dL/dmu_x W/2,
+    dL/dmu_y H/2)| (the gradient w.r.t. the mean in normalised device
+    coordinates) and denom += 1.  In FP32, as the statistic is stored."""
+    accum = np.asarray(accum, dtype=np.float32).copy()
+    denom = np.asarray(denom, dtype=np.float32).copy()
+    vis = np.asarray(valid) != 0
+    g = np.asarray(gmu, dtype=np.float64)
+    nrm = np.sqrt((g[:, 0] * (W / 2.0)) ** 2 + (g[:, 1] * (H / 2.0)) ** 2)
+    accum[vis] += nrm[vis].astype(np.float32)
+    denom[vis] += np.float32(1.0)
+    return accum, denom
+
+
+def densify_actions(gauss: dict, accum, denom, opts=None) -> np.ndarray:
+    """Per-Gaussian decision of Algorithm 1's densification step, taken in
+    FP32 (the precision the statistics are stored in): prune if the opacity
+    sigmoid(logit) < prune_opacity or the largest scale exceeds prune_scale
+    (when > 0); otherwise, if the mean screen-space gradient accum / denom
+    reaches grad_threshold, split when the largest scale exceeds split_scale
+    and clone otherwise; else keep."""
+    o = {**DENSIFY_OPTS, **(opts or {})}
+    f = np.float32
+    logit = np.asarray(gauss["opacity_logits"], dtype=f)
+    opac = f(1.0) / (f(1.0) + np.exp(-logit))
+    smax = np.exp(np.max(np.asarray(gauss["log_scales"], dtype=f), axis=1))
+    accum, denom = np.asarray(accum, dtype=f), np.asarray(denom, dtype=f)
+    avg = np.where(denom > 0, accum / np.where(denom > 0, denom, f(1.0)), f(0.0))
+    prune = opac < f(o["prune_opacity"])
+    if o["prune_scale"] > 0:
+        prune |= smax > f(o["prune_scale"])
+    dens = avg >= f(o["grad_threshold"])
+    act = np.full(len(logit), KEEP, dtype=np.int32)
+    act[dens & (smax <= f(o["split_scale"]))] = CLONE
+    act[dens & (smax > f(o["split_scale"]))] = SPLIT
+    act[prune] = PRUNE
+    return act
+
+
+def _rotation(q):
+    q = np.asarray(q, dtype=np.float64)
+    w, x, y, z = q / np.linalg.norm(q)
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+def densify(gauss: dict, accum, denom, noise, opts=None, extra=()):
+    """Algorithm 1's pruning and densification with phase-aware copies.
+    Outputs follow the input order: a kept Gaussian once; a clone as the
+    original followed by a copy whose phases are perturbed by
+    phase_noise * noise[n, 0, 3:]; a split as two children k = 0, 1 with means
+    mu + R diag(s) noise[n, k, :3] (a draw from the Gaussian itself), log-scales
+    lowered by log(split_shrink), phases perturbed by phase_noise *
+    noise[n, k, 3:] and everything else copied; a pruned Gaussian not at all.
+    ``noise`` is [N][2][3 + C] standard normals.  ``extra`` arrays (per-Gaussian
+    optimiser state) follow kept Gaussians and clone originals, and start at
+    zero for copies and children.  Returns (new params, new extras, actions)."""
+    o = {**DENSIFY_OPTS, **(opts or {})}
+    act = densify_actions(gauss, accum, denom, o)
+    p = {k: np.asarray(v, dtype=np.float64) for k, v in gauss.items()}
+    C = p["amplitude"].shape[1]
+    z = np.asarray(noise, dtype=np.float64).reshape(len(act), 2, 3 + C)
+    out = {k: [] for k in p}
+    ex_out = [[] for _ in extra]
+    shrink = np.log(o["split_shrink"])
+    for n, a in enumerate(act):
+        if a == PRUNE:
+            continue
+        if a in (KEEP, CLONE):
+            for k in p:
+                out[k].append(p[k][n])
+            for i, e in enumerate(extra):
+                ex_out[i].append(np.asarray(e[n], dtype=np.float64))
+        if a == CLONE:
+            for k in p:
+                out[k].append(p[k][n] + (o["phase_noise"] * z[n, 0, 3:] if k == "phase" else 0.0))
+            for i, e in enumerate(extra):
+                ex_out[i].append(np.zeros_like(np.asarray(e[n], dtype=np.float64)))
+        if a == SPLIT:
+            R = _rotation(p["quats"][n])
+            s = np.exp(p["log_scales"][n])
+            for child in range(2):
+                for k in p:
+                    if k == "means":
+                        out[k].append(p[k][n] + R @ (s * z[n, child, :3]))
+                    elif k == "log_scales":
+                        out[k].append(p[k][n] - shrink)
+                    elif k == "phase":
+                        out[k].append(p[k][n] + o["phase_noise"] * z[n, child, 3:])
+                    else:
+                        out[k].append(p[k][n])
+                for i, e in enumerate(extra):
+                    ex_out[i].append(np.zeros_like(np.asarray(e[n], dtype=np.float64)))
+    shapes = {k: p[k].shape[1:] for k in p}
+    newp = {k: (np.array(v) if v else np.zeros((0,) + shapes[k])) for k, v in out.items()}
+    newe = [np.array(v) if v else np.zeros((0,) + np.asarray(e).shape[1:]) for v, e in zip(ex_out, extra)]
+    return newp, newe, act
 
 
 # ----------------------------------------------------------------------------
