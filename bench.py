@@ -482,6 +482,10 @@ def run_ours(args):
         # cosine annealing of the means' and plane logits' learning rates
         training["fp32_paper_objective_adan"] = ring_run(ctx, wt.optics, wt.N, args.train_steps, footprint=0,
                                                          objective="paper", optimizer="adan", anneal=True)
+        # and with Algorithm 1's densification every 300 steps (3DGS thresholds)
+        training["fp32_paper_objective_adan_densify"] = ring_run(ctx, wt.optics, wt.N, args.train_steps, footprint=0,
+                                                                 objective="paper", optimizer="adan", anneal=True,
+                                                                 densify=dict(P.DEFAULT_DENSIFY))
 
     # --- the two objectives on one view of this workload's optics ---
     objective = None

@@ -360,6 +360,63 @@ hcgs_status hcgs_init_apply(hcgs_ctx* ctx, const float* y, int N, int C, float* 
 hcgs_status hcgs_asm_propagate_noalloc(const float* in, int B, const hcgs_optics* optics, float* out,
                                        void* stream);
 
+/* ---------------- densification (Algorithm 1, Supp. C) ---------------- */
+/* The 3DGS densification rules that Sec. 5 adopts (period: 300 steps),
+ * with phase-aware copies (Supp. C: copies and children get a small random
+ * phase perturbation). */
+typedef struct {
+    float grad_threshold; /* densify when the mean NDC gradient norm of the 2D mean >= this (2e-4) */
+    float split_scale;    /* split when the largest scale exp(log_scale) > this (m), else clone  */
+    float prune_opacity;  /* prune when sigmoid(opacity_logit) < this (0.005)                 */
+    float prune_scale;    /* prune when the largest scale > this (m); <= 0: no size pruning   */
+    float split_shrink;   /* children's scales are the parent's / split_shrink (1.6)          */
+    float phase_noise;    /* standard deviation of the phase perturbation (rad)               */
+} hcgs_densify_opts;
+#define HCGS_DENSIFY_MAX_EXTRA 32
+
+/* Adds the last backward pass's screen-space statistics: for every view of
+ * `saved` in which Gaussian n is visible, accum[n] += |(dL/dmu_x W/2,
+ * dL/dmu_y H/2)| (the gradient w.r.t. the 2D mean in normalised device
+ * coordinates) and denom[n] += 1.  accum, denom device [N] float (in/out).
+ * Needs hcgs_rasterize_planes_backward (or hcgs_render_view_backward) on
+ * `saved` first (HCGS_ERR_STATE otherwise). */
+hcgs_status hcgs_densify_accumulate(hcgs_ctx* ctx, hcgs_saved* saved, float* accum, float* denom, void* stream);
+/* Decides every Gaussian's fate and sizes the output: action device [N]
+ * int32 (out: 0 keep, 1 prune, 2 clone, 3 split), offsets device [N + 1]
+ * uint32 (out: exclusive prefix sum of 1 / 0 / 2 / 2 outputs per Gaussian;
+ * offsets[N] = the new count), *n_out (host, out) the new count.  Decisions
+ * in FP32: prune if sigmoid(logit) < prune_opacity or (prune_scale > 0 and
+ * the largest scale > prune_scale); otherwise densify if denom > 0 and
+ * accum / denom >= grad_threshold, splitting when the largest scale >
+ * split_scale.  Synchronises `stream` once to read the count. */
+hcgs_status hcgs_densify_plan(hcgs_ctx* ctx, const hcgs_gaussians* g, const float* accum, const float* denom,
+                              const hcgs_densify_opts* opts, int32_t* action, uint32_t* offsets,
+                              int64_t* n_out, void* stream);
+/* Writes the new Gaussians: output offsets[n] onward receives, for a kept
+ * Gaussian, its copy; for a clone, the original then a copy with phases
+ * phi + phase_noise noise[n][0][3 + c]; for a split, two children k = 0, 1
+ * with means mu + R diag(exp(log_scales)) noise[n][k][0:3] (R of the
+ * normalised quaternion), log-scales - log(split_shrink), phases phi +
+ * phase_noise noise[n][k][3 + c], the rest copied; pruned Gaussians write
+ * nothing.  noise device [N][2][3 + C] float standard normals (e.g.
+ * hcgs_philox).  g_out: the output arrays (device, n_out rows; the struct of
+ * writable arrays), must not alias g_in.  extra_in / extra_out: host arrays
+ * of n_extra (<= HCGS_DENSIFY_MAX_EXTRA) device pointers to per-Gaussian
+ * float arrays of extra_width[e] columns (optimiser state): copied for kept
+ * Gaussians and clone originals, zero for copies and children. */
+hcgs_status hcgs_densify_apply(hcgs_ctx* ctx, const hcgs_gaussians* g_in, int C, int L, const int32_t* action,
+                               const uint32_t* offsets, const float* noise, const hcgs_densify_opts* opts,
+                               const hcgs_gaussian_grads* g_out, int n_extra, const float* const* extra_in,
+                               float* const* extra_out, const int* extra_width, void* stream);
+/* Counter-based random numbers (Philox4x32-10 of Salmon et al., SC'11): word
+ * block b of stream (seed, stream_id) is Philox(counter (b, stream_id, 0, 0),
+ * key (seed low 32 bits, seed high 32 bits)), four uint32 words per block.
+ * kind 0: out device [n] uint32, the words in order; kind 1: out device [n]
+ * float standard normals, each word pair (a, b) giving, with u = (a + 1/2)
+ * 2^-32, v = (b + 1/2) 2^-32, sqrt(-2 ln u) (cos 2 pi v, sin 2 pi v). */
+hcgs_status hcgs_philox(hcgs_ctx* ctx, uint64_t seed, uint32_t stream_id, int64_t n, int kind, void* out,
+                        void* stream);
+
 #ifdef __cplusplus
 }
 #endif

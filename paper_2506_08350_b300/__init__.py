@@ -38,7 +38,8 @@ EXPORTS = ("hcgs_ctx_create", "hcgs_ctx_destroy", "hcgs_status_string", "hcgs_la
            "hcgs_focal_stack_loss", "hcgs_adam_step", "hcgs_mlp_forward", "hcgs_mlp_backward",
            "hcgs_profile_enable", "hcgs_profile_summary", "hcgs_asm_propagate_noalloc", "hcgs_mlp_mse_loss",
            "hcgs_cast_bf16", "hcgs_init_features", "hcgs_init_targets", "hcgs_init_apply",
-           "hcgs_selftest_wait_timeout", "hcgs_paper_loss", "hcgs_paper_loss_intensities", "hcgs_adan_step")
+           "hcgs_selftest_wait_timeout", "hcgs_paper_loss", "hcgs_paper_loss_intensities", "hcgs_adan_step",
+           "hcgs_densify_accumulate", "hcgs_densify_plan", "hcgs_densify_apply", "hcgs_philox")
 
 
 class HcgsError(RuntimeError):
@@ -61,6 +62,11 @@ class _Gaussians(ctypes.Structure):
     _fields_ = [("means", c_void_p), ("log_scales", c_void_p), ("quats", c_void_p),
                 ("opacity_logits", c_void_p), ("amplitude", c_void_p), ("phase", c_void_p),
                 ("plane_logits", c_void_p), ("N", c_int)]
+
+
+class _DensifyOpts(ctypes.Structure):
+    _fields_ = [("grad_threshold", c_float), ("split_scale", c_float), ("prune_opacity", c_float),
+                ("prune_scale", c_float), ("split_shrink", c_float), ("phase_noise", c_float)]
 
 
 class _Grads(ctypes.Structure):
@@ -103,6 +109,11 @@ _sig("hcgs_project_backward", [_P, _P, POINTER(_Gaussians), POINTER(_Grads), c_i
 _sig("hcgs_render_view_backward", [_P, _P, POINTER(_Gaussians), _P, POINTER(_Grads), c_int, _P])
 _sig("hcgs_focal_stack_loss", [_P, _P, _P, c_int, POINTER(_Optics), _P, _P, _P, _P])
 _sig("hcgs_adam_step", [_P, _P, _P, _P, _P, c_int64, c_int, c_float, c_float, c_float, c_float, _P])
+_sig("hcgs_densify_accumulate", [_P, _P, _P, _P, _P])
+_sig("hcgs_densify_plan", [_P, POINTER(_Gaussians), _P, _P, POINTER(_DensifyOpts), _P, _P, POINTER(c_int64), _P])
+_sig("hcgs_densify_apply", [_P, POINTER(_Gaussians), c_int, c_int, _P, _P, _P, POINTER(_DensifyOpts),
+                            POINTER(_Grads), c_int, _P, _P, _P, _P])
+_sig("hcgs_philox", [_P, ctypes.c_uint64, ctypes.c_uint32, c_int64, c_int, _P, _P])
 _sig("hcgs_paper_loss", [_P, _P, _P, _P, c_int, POINTER(_Optics), c_float, _P, _P, _P, _P])
 _sig("hcgs_paper_loss_intensities", [_P, _P, _P, _P, c_int, c_int, c_int, c_int, c_int, c_float, _P, _P, _P])
 _sig("hcgs_adan_step", [_P, _P, _P, _P, _P, _P, _P, c_int64, c_int, c_float, c_float, c_float, c_float, c_float,
@@ -117,6 +128,11 @@ _sig("hcgs_init_apply", [_P, _P, c_int, c_int, _P, _P, _P])
 _sig("hcgs_mlp_backward", [_P, _P, c_int] + [_P] * 8 + [_P] + [_P] * 8 + [_P])
 
 SSIM_LAMBDA = 0.005  # lambda_1 of the SSIM term (Sec. 3, loss)
+# densification (Algorithm 1; the 3DGS rules Sec. 5 adopts); split_scale is
+# scene-dependent (3DGS: 1 % of the scene extent; 0.02 m for the 1-3 m scenes here)
+DEFAULT_DENSIFY = dict(grad_threshold=2e-4, split_scale=0.02, prune_opacity=5e-3, prune_scale=0.0,
+                       split_shrink=1.6, phase_noise=0.1)
+DENSIFY_PERIOD = 300
 
 PARAM_NAMES = ("means", "log_scales", "quats", "opacity_logits", "amplitude", "phase", "plane_logits")
 
@@ -305,6 +321,42 @@ class Context:
     def adam_step(self, p, g, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
         self._check(_lib.hcgs_adam_step(self.handle, _ptr(p), _ptr(g), _ptr(m), _ptr(v), p.numel(), int(step),
                                         float(lr), float(beta1), float(beta2), float(eps), _stream()))
+
+    def philox(self, seed, n, out, kind=1, stream_id=0):
+        """n counter-based random numbers into `out` (kind 0: uint32 words as
+        int32/uint32 storage, 1: float32 standard normals)."""
+        self._check(_lib.hcgs_philox(self.handle, int(seed) & (2 ** 64 - 1), int(stream_id) & 0xFFFFFFFF, int(n),
+                                     int(kind), _ptr(out), _stream()))
+
+    def densify_accumulate(self, saved, accum, denom):
+        self._check(_lib.hcgs_densify_accumulate(self.handle, saved.handle, _ptr(accum), _ptr(denom), _stream()))
+
+    def densify_plan(self, g, accum, denom, opts=None):
+        """Returns (action int32 [N], offsets int32 storage of uint32 [N + 1], new count)."""
+        import torch
+        o = _DensifyOpts(**{**DEFAULT_DENSIFY, **(opts or {})})
+        N = g["means"].shape[0]
+        dev = g["means"].device
+        action = torch.empty(N, dtype=torch.int32, device=dev)
+        offsets = torch.empty(N + 1, dtype=torch.int32, device=dev)
+        n_out = c_int64(0)
+        self._check(_lib.hcgs_densify_plan(self.handle, ctypes.byref(_gauss(g)), _ptr(accum), _ptr(denom),
+                                           ctypes.byref(o), _ptr(action), _ptr(offsets), ctypes.byref(n_out),
+                                           _stream()))
+        return action, offsets, int(n_out.value)
+
+    def densify_apply(self, g, C, L, action, offsets, noise, g_out, opts=None, extras=()):
+        """Write the densified Gaussians into g_out (dict of arrays with the new
+        count of rows); extras: (in, out) pairs of per-Gaussian float arrays."""
+        o = _DensifyOpts(**{**DEFAULT_DENSIFY, **(opts or {})})
+        k = len(extras)
+        ins = (c_void_p * max(k, 1))(*[_ptr(a) for a, _ in extras])
+        outs = (c_void_p * max(k, 1))(*[_ptr(b) for _, b in extras])
+        widths = (c_int * max(k, 1))(*[int(a[0].numel()) if a.shape[0] > 0 and a.dim() > 1 else 1
+                                       for a, _ in extras])
+        self._check(_lib.hcgs_densify_apply(self.handle, ctypes.byref(_gauss(g)), int(C), int(L), _ptr(action),
+                                            _ptr(offsets), _ptr(noise), ctypes.byref(o), ctypes.byref(_grads(g_out)),
+                                            k, ins, outs, widths, _stream()))
 
     def mlp_forward(self, x, W, b, y):
         self._check(_lib.hcgs_mlp_forward(self.handle, _ptr(x), x.shape[0], *[_ptr(w) for w in W],

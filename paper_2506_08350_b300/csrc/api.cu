@@ -561,6 +561,87 @@ hcgs_status hcgs_adan_step(hcgs_ctx* ctx, float* p, const float* g, float* g_pre
     return adan(ctx, p, g, g_prev, m, v, n, count, step, lr, beta1, beta2, beta3, eps, weight_decay, S(stream));
 }
 
+static hcgs_status check_densify_opts(hcgs_ctx* ctx, const hcgs_densify_opts* o) {
+    REQUIRE(ctx, o, "densify opts is NULL");
+    REQUIRE(ctx, std::isfinite(o->grad_threshold) && std::isfinite(o->split_scale) &&
+                     std::isfinite(o->prune_opacity) && std::isfinite(o->prune_scale) &&
+                     std::isfinite(o->phase_noise) && o->split_shrink > 1.f && std::isfinite(o->split_shrink),
+            "densify opts must be finite, split_shrink > 1");
+    return HCGS_OK;
+}
+
+hcgs_status hcgs_densify_accumulate(hcgs_ctx* ctx, hcgs_saved* s, float* accum, float* denom, void* stream) {
+    if (!ctx) return HCGS_ERR_INVALID_ARG;
+    REQUIRE(ctx, s && accum && denom, "NULL argument");
+    if (!s->have_g2d) {
+        set_err(ctx, HCGS_ERR_STATE, "needs the backward pass of the compositor on this saved state first");
+        return HCGS_ERR_STATE;
+    }
+    cudaSetDevice(ctx->device);
+    return densify_accumulate(ctx, s, accum, denom, S(stream));
+}
+
+hcgs_status hcgs_densify_plan(hcgs_ctx* ctx, const hcgs_gaussians* g, const float* accum, const float* denom,
+                              const hcgs_densify_opts* opts, int32_t* action, uint32_t* offsets, int64_t* n_out,
+                              void* stream) {
+    if (!ctx) return HCGS_ERR_INVALID_ARG;
+    TRY(check_gauss(ctx, g));
+    TRY(check_densify_opts(ctx, opts));
+    REQUIRE(ctx, offsets && n_out, "NULL argument");
+    REQUIRE(ctx, g->N < (1 << 30), "N must be < 2^30 (the output count is uint32)");
+    if (g->N > 0) REQUIRE(ctx, accum && denom && action, "NULL argument");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = S(stream);
+    if (g->N > 0) {
+        HCGS_CUDA(ctx, grow(ctx, ctx->ws[5], (size_t)g->N * sizeof(uint32_t), &ctx->bytes));
+        uint32_t* count = (uint32_t*)ctx->ws[5].p;
+        TRY(densify_decide(ctx, g, accum, denom, *opts, action, count, st));
+        if (!ctx->scratch_saved) ctx->scratch_saved = new hcgs_saved();
+        TRY(exclusive_scan(ctx, ctx->scratch_saved, count, offsets, (size_t)g->N, st));
+        TRY(densify_offsets_tail(ctx, count, offsets, g->N, st));
+    } else {
+        HCGS_CUDA(ctx, cudaMemsetAsync(offsets, 0, sizeof(uint32_t), st));
+    }
+    HCGS_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, offsets + g->N, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    HCGS_CUDA(ctx, cudaStreamSynchronize(st));
+    *n_out = (int64_t)ctx->h_pinned[0];
+    return HCGS_OK;
+}
+
+hcgs_status hcgs_densify_apply(hcgs_ctx* ctx, const hcgs_gaussians* g_in, int C, int L, const int32_t* action,
+                               const uint32_t* offsets, const float* noise, const hcgs_densify_opts* opts,
+                               const hcgs_gaussian_grads* g_out, int n_extra, const float* const* extra_in,
+                               float* const* extra_out, const int* extra_width, void* stream) {
+    if (!ctx) return HCGS_ERR_INVALID_ARG;
+    TRY(check_gauss(ctx, g_in));
+    TRY(check_densify_opts(ctx, opts));
+    REQUIRE(ctx, C >= 1 && C <= MAX_C && L >= 1 && L <= MAX_L, "bad C or L");
+    REQUIRE(ctx, n_extra >= 0 && n_extra <= HCGS_DENSIFY_MAX_EXTRA, "n_extra out of range");
+    if (g_in->N == 0) return HCGS_OK;
+    REQUIRE(ctx, action && offsets && noise && g_out, "NULL argument");
+    TRY(check_grads(ctx, g_out));
+    REQUIRE(ctx, g_out->means != g_in->means && g_out->phase != g_in->phase, "g_out must not alias g_in");
+    if (n_extra > 0) REQUIRE(ctx, extra_in && extra_out && extra_width, "NULL extra array list");
+    for (int e = 0; e < n_extra; e++) {
+        REQUIRE(ctx, extra_in[e] && extra_out[e] && extra_in[e] != extra_out[e], "bad extra array");
+        REQUIRE(ctx, extra_width[e] >= 1 && extra_width[e] <= 64, "extra width must be 1..64");
+    }
+    cudaSetDevice(ctx->device);
+    return densify_apply(ctx, g_in, C, L, action, offsets, noise, *opts, *g_out, n_extra, extra_in, extra_out,
+                         extra_width, S(stream));
+}
+
+hcgs_status hcgs_philox(hcgs_ctx* ctx, uint64_t seed, uint32_t stream_id, int64_t n, int kind, void* out,
+                        void* stream) {
+    if (!ctx) return HCGS_ERR_INVALID_ARG;
+    REQUIRE(ctx, n >= 0 && n < ((int64_t)1 << 34), "n out of range");
+    REQUIRE(ctx, kind == 0 || kind == 1, "kind must be 0 (words) or 1 (normals)");
+    if (n == 0) return HCGS_OK;
+    REQUIRE(ctx, out, "NULL argument");
+    cudaSetDevice(ctx->device);
+    return philox(ctx, seed, stream_id, n, kind, out, S(stream));
+}
+
 hcgs_status hcgs_adam_step(hcgs_ctx* ctx, float* p, const float* g, float* m, float* v, int64_t n, int step,
                            float lr, float beta1, float beta2, float eps, void* stream) {
     if (!ctx) return HCGS_ERR_INVALID_ARG;

@@ -252,6 +252,18 @@ hcgs_status mlp_mse(hcgs_ctx* ctx, const float* y, const float* tgt, int N, int 
                     cudaStream_t st);
 hcgs_status cast_bf16(hcgs_ctx* ctx, const float* src, uint16_t* dst, int64_t n, cudaStream_t st);
 
+// ---- densification (densify.cu) ----
+hcgs_status philox(hcgs_ctx* ctx, uint64_t seed, uint32_t stream_id, int64_t n, int normal, void* out,
+                   cudaStream_t st);
+hcgs_status densify_accumulate(hcgs_ctx* ctx, hcgs_saved* s, float* accum, float* denom, cudaStream_t st);
+hcgs_status densify_decide(hcgs_ctx* ctx, const hcgs_gaussians* g, const float* accum, const float* denom,
+                           const hcgs_densify_opts& o, int32_t* action, uint32_t* count, cudaStream_t st);
+hcgs_status densify_offsets_tail(hcgs_ctx* ctx, const uint32_t* count, uint32_t* offsets, int N, cudaStream_t st);
+hcgs_status densify_apply(hcgs_ctx* ctx, const hcgs_gaussians* gi, int C, int L, const int32_t* action,
+                          const uint32_t* offset, const float* noise, const hcgs_densify_opts& o,
+                          const hcgs_gaussian_grads& go, int n_extra, const float* const* extra_in,
+                          float* const* extra_out, const int* extra_width, cudaStream_t st);
+
 // ---- the paper's objective and optimiser (objective.cu) ----
 hcgs_status ssim_recon_loss(hcgs_ctx* ctx, float2* V, float* I, const float* Igt, const float* M, int B, int L,
                             int C, int H, int W, float lam, float* dmap, float* partials, int* nblocks_out,

@@ -20,7 +20,7 @@ from __future__ import annotations
 
 import torch
 
-from . import PARAM_NAMES, SSIM_LAMBDA, Context, Saved
+from . import DEFAULT_DENSIFY, DENSIFY_PERIOD, PARAM_NAMES, SSIM_LAMBDA, Context, Saved
 
 PAPER_LR = dict(means=0.01, log_scales=0.005, quats=0.001, opacity_logits=0.025, amplitude=0.0025,
                 phase=0.0025, plane_logits=0.01)
@@ -46,7 +46,9 @@ class HologramTrainer:
 
     def __init__(self, ctx: Context, params: dict, optics, opts=None, lrs=None, betas=None, eps=1e-8,
                  data_parallel: bool = False, objective: str = "mse", optimizer: str = "adam",
-                 total_steps: int | None = None, lambda_ssim: float = SSIM_LAMBDA, weight_decay: float = 0.0):
+                 total_steps: int | None = None, lambda_ssim: float = SSIM_LAMBDA, weight_decay: float = 0.0,
+                 densify: dict | None = None, densify_every: int = DENSIFY_PERIOD, densify_until: int | None = None,
+                 seed: int = 0):
         if objective not in ("mse", "paper"):
             raise ValueError("objective must be 'mse' or 'paper'")
         if optimizer not in ("adam", "adan"):
@@ -70,6 +72,17 @@ class HologramTrainer:
             self.n = {k: torch.zeros_like(v) for k, v in params.items()}
             self.g_prev = {k: torch.zeros_like(v) for k, v in params.items()}
         self.t = 0
+        # densification (Algorithm 1): statistics gathered every step, applied
+        # every `densify_every` steps up to `densify_until` (None: always)
+        self.densify_opts = None if densify is None else {**DEFAULT_DENSIFY, **densify}
+        self.densify_every = densify_every
+        self.densify_until = densify_until
+        self.seed = seed
+        self.densify_log = []
+        dev0 = params["means"].device
+        N0 = params["means"].shape[0]
+        self.accum = torch.zeros(N0, dtype=torch.float32, device=dev0)
+        self.denom = torch.zeros(N0, dtype=torch.float32, device=dev0)
         self.data_parallel = data_parallel  # sum gradients over the ranks of the process group
         self.saved = Saved(ctx)
         dev = params["means"].device
@@ -101,6 +114,8 @@ class HologramTrainer:
         else:
             self.ctx.focal_stack_loss(self.holo, I_gt, 1, self.optics, self.loss, self.gholo, None)
         self.ctx.render_view_backward(self.saved, self.p, self.gholo, self.g)
+        if self.densify_opts is not None:
+            self.ctx.densify_accumulate(self.saved, self.accum, self.denom)
         if self.data_parallel:
             from .parallel import allreduce_gradients
             allreduce_gradients(self.g)
@@ -116,7 +131,44 @@ class HologramTrainer:
             else:
                 self.ctx.adam_step(self.p[k], self.g[k], self.m[k], self.v[k], self.t, lr, self.betas[0],
                                    self.betas[1], self.eps)
+        if (self.densify_opts is not None and self.t % self.densify_every == 0
+                and (self.densify_until is None or self.t <= self.densify_until)):
+            self.densify()
         return self.loss
+
+    def densify(self):
+        """Prune, clone and split (Algorithm 1) with the gathered statistics;
+        the optimiser state follows kept Gaussians and starts at zero for new
+        ones; the statistics restart.  Returns (old N, new N, action counts)."""
+        ctx = self.ctx
+        N = self.p["means"].shape[0]
+        C, L = self.p["amplitude"].shape[1], self.p["plane_logits"].shape[1]
+        # quantiles of the mean statistic over the Gaussians seen (host copy, for the log)
+        import numpy as np
+        a_h, d_h = self.accum.cpu().numpy(), self.denom.cpu().numpy()
+        seen = d_h > 0
+        q = np.quantile(a_h[seen] / d_h[seen], [0.5, 0.9, 0.99]).tolist() if seen.any() else [0.0, 0.0, 0.0]
+        act, off, n_new = ctx.densify_plan(self.p, self.accum, self.denom, self.densify_opts)
+        dev = self.p["means"].device
+        noise = torch.empty((N, 2, 3 + C), dtype=torch.float32, device=dev)
+        ctx.philox(self.seed, noise.numel(), noise, kind=1, stream_id=self.t)
+        newp = {k: torch.empty((n_new,) + tuple(v.shape[1:]), dtype=v.dtype, device=dev) for k, v in self.p.items()}
+        states = [self.m, self.v] + ([self.n, self.g_prev] if self.optimizer == "adan" else [])
+        news = [{k: torch.empty_like(newp[k]) for k in PARAM_NAMES} for _ in states]
+        extras = [(st[k], ns[k]) for st, ns in zip(states, news) for k in PARAM_NAMES]
+        ctx.densify_apply(self.p, C, L, act, off, noise, newp, self.densify_opts, extras)
+        counts = np.bincount(act.cpu().numpy(), minlength=4).tolist() if N else [0, 0, 0, 0]
+        self.p.update(newp)
+        self.m, self.v = news[0], news[1]
+        if self.optimizer == "adan":
+            self.n, self.g_prev = news[2], news[3]
+        self.g = {k: torch.empty_like(v) for k, v in self.p.items()}
+        self.accum = torch.zeros(n_new, dtype=torch.float32, device=dev)
+        self.denom = torch.zeros(n_new, dtype=torch.float32, device=dev)
+        self.densify_log.append(dict(step=self.t, n_before=N, n_after=n_new, keep=counts[0], prune=counts[1],
+                                     clone=counts[2], split=counts[3], seen=int(seen.sum()),
+                                     stat_median=q[0], stat_p90=q[1], stat_p99=q[2]))
+        return self.densify_log[-1]
 
 
 def focal_stack(ctx: Context, params: dict, viewmat, intr, optics, opts=None):
@@ -163,7 +215,7 @@ def plane_masks(ctx: Context, params: dict, viewmat, intr, optics, opts=None):
 
 def ring_run(ctx: Context, optics, N: int, steps: int, n_views: int = 50, footprint: int = 0, teacher_seed: int = 3,
              student_seed: int = 0, lrs=None, device: str = "cuda", objective: str = "mse",
-             optimizer: str = "adam", anneal: bool = False):
+             optimizer: str = "adam", anneal: bool = False, densify: dict | None = None):
     """A full optimisation run on synthetic data: the focal stacks of a teacher
     scene seen from ``n_views`` cameras on a ring are the targets; the student
     has the teacher's geometry and a fresh draw of amplitude and phase
@@ -201,7 +253,7 @@ def ring_run(ctx: Context, optics, N: int, steps: int, n_views: int = 50, footpr
     p = {k: torch.from_numpy(np.ascontiguousarray(student[k])).to(device) for k in PARAM_NAMES}
     opts = dict(DEFAULT_OPTS, footprint=int(footprint))
     tr = HologramTrainer(ctx, p, o, opts, lrs=lrs, objective=objective, optimizer=optimizer,
-                         total_steps=steps if anneal else None)
+                         total_steps=steps if anneal else None, densify=densify)
 
     def psnr():
         vals = []
@@ -222,6 +274,10 @@ def ring_run(ctx: Context, optics, N: int, steps: int, n_views: int = 50, footpr
     ms = e0.elapsed_time(e1) / max(steps, 1)
     p1 = psnr()
     tr.saved.release()
-    return {"steps_per_s": 1e3 / ms, "ms_per_step": ms, "psnr_start": p0, "psnr_end": p1, "steps": steps,
-            "views": n_views, "footprint": "fp16x2" if footprint else "fp32", "objective": objective,
-            "optimizer": optimizer, "anneal": bool(anneal)}
+    out = {"steps_per_s": 1e3 / ms, "ms_per_step": ms, "psnr_start": p0, "psnr_end": p1, "steps": steps,
+           "views": n_views, "footprint": "fp16x2" if footprint else "fp32", "objective": objective,
+           "optimizer": optimizer, "anneal": bool(anneal)}
+    if densify is not None:
+        out["densify"] = tr.densify_log
+        out["N_end"] = int(tr.p["means"].shape[0])
+    return out
