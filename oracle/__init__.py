@@ -225,66 +225,100 @@ def transfer_function(H: int, W: int, pitch: float, wavelength: float, z: float,
     return np.where(inside, np.exp(1j * phase), 0.0)
 
 
-def propagate(u: np.ndarray, pitch: float, wavelength: float, z: float, band_limit: int = 0) -> np.ndarray:
-    """One field through Eq. layer2plane_asm: IDFT(H_z DFT(u))."""
+def zero_pad(u: np.ndarray) -> np.ndarray:
+    """Embed the last two axes (H, W) in a 2H x 2W grid of zeros, the field
+    at rows H//2 .. H//2 + H - 1 and columns W//2 .. W//2 + W - 1."""
+    H, W = u.shape[-2], u.shape[-1]
+    out = np.zeros(u.shape[:-2] + (2 * H, 2 * W), dtype=np.complex128)
+    out[..., H // 2:H // 2 + H, W // 2:W // 2 + W] = u
+    return out
+
+
+def crop(u: np.ndarray, H: int, W: int) -> np.ndarray:
+    """The H x W window of a 2H x 2W grid that ``zero_pad`` filled."""
+    return u[..., H // 2:H // 2 + H, W // 2:W // 2 + W]
+
+
+def propagate(u: np.ndarray, pitch: float, wavelength: float, z: float, band_limit: int = 0,
+              padding: int = 0) -> np.ndarray:
+    """One field through Eq. layer2plane_asm: IDFT(H_z DFT(u)).  padding = 1:
+    on the 2x zero-padded grid (a linear instead of a circular convolution;
+    H_z and its band limit then use that grid's frequencies), cropped back."""
+    if padding:
+        H, W = u.shape[-2], u.shape[-1]
+        return crop(propagate(zero_pad(u), pitch, wavelength, z, band_limit), H, W)
     Hz = transfer_function(u.shape[-2], u.shape[-1], pitch, wavelength, z, band_limit)
     return np.fft.ifft2(Hz * np.fft.fft2(u))
 
 
-def propagate_planes(U: np.ndarray, pitch: float, wavelengths, plane_z, band_limit: int = 0) -> np.ndarray:
+def propagate_planes(U: np.ndarray, pitch: float, wavelengths, plane_z, band_limit: int = 0,
+                     padding: int = 0) -> np.ndarray:
     """Eq. layer2plane_asm for every plane, then Eq. sum_planes.
     U[L][C][H][W] -> P[C][H][W]."""
     L, C = U.shape[0], U.shape[1]
     P = np.zeros(U.shape[1:], dtype=np.complex128)
     for c in range(C):
         for l in range(L):
-            P[c] += propagate(U[l, c], pitch, wavelengths[c], plane_z[l], band_limit)
+            P[c] += propagate(U[l, c], pitch, wavelengths[c], plane_z[l], band_limit, padding)
     return P
 
 
-def propagate_planes_adjoint(gP: np.ndarray, pitch: float, wavelengths, plane_z, band_limit: int = 0) -> np.ndarray:
+def propagate_planes_adjoint(gP: np.ndarray, pitch: float, wavelengths, plane_z, band_limit: int = 0,
+                             padding: int = 0) -> np.ndarray:
     """Adjoint of ``propagate_planes`` for g = dL/dRe + j dL/dIm:
     gU_l = IDFT(conj(H_{Z_l}) DFT(gP)).  (With F the unnormalised DFT,
-    (F^-1 D F)^H = F^-1 conj(D) F.)"""
+    (F^-1 D F)^H = F^-1 conj(D) F; with padding the adjoint of the zero
+    embedding is the crop and vice versa.)"""
     C, H, W = gP.shape
     L = len(plane_z)
     gU = np.zeros((L, C, H, W), dtype=np.complex128)
     for c in range(C):
-        G = np.fft.fft2(gP[c])
+        g = zero_pad(gP[c]) if padding else gP[c]
+        G = np.fft.fft2(g)
         for l in range(L):
-            Hz = transfer_function(H, W, pitch, wavelengths[c], plane_z[l], band_limit)
-            gU[l, c] = np.fft.ifft2(np.conj(Hz) * G)
+            Hz = transfer_function(g.shape[0], g.shape[1], pitch, wavelengths[c], plane_z[l], band_limit)
+            r = np.fft.ifft2(np.conj(Hz) * G)
+            gU[l, c] = crop(r, H, W) if padding else r
     return gU
 
 
-def inverse_propagate(P: np.ndarray, pitch: float, wavelengths, plane_z, band_limit: int = 0) -> np.ndarray:
+def inverse_propagate(P: np.ndarray, pitch: float, wavelengths, plane_z, band_limit: int = 0,
+                      padding: int = 0) -> np.ndarray:
     """Eq. plane2layer_asm: V_l = IDFT(H_{-Z_l} DFT(P)), P[C][H][W] -> V[L][C][H][W]."""
     C, H, W = P.shape
     L = len(plane_z)
     V = np.zeros((L, C, H, W), dtype=np.complex128)
     for c in range(C):
-        S = np.fft.fft2(P[c])
         for l in range(L):
-            V[l, c] = np.fft.ifft2(transfer_function(H, W, pitch, wavelengths[c], -plane_z[l], band_limit) * S)
+            V[l, c] = propagate(P[c], pitch, wavelengths[c], -plane_z[l], band_limit, padding)
     return V
 
 
-def focal_stack_loss(P: np.ndarray, I_gt: np.ndarray, pitch: float, wavelengths, plane_z):
+def inverse_propagate_adjoint(gV: np.ndarray, pitch: float, wavelengths, plane_z, band_limit: int = 0,
+                              padding: int = 0) -> np.ndarray:
+    """Adjoint of ``inverse_propagate``: gP = sum_l IDFT(conj(H_{-Z_l}) DFT(gV_l))
+    (through the zero embedding and crop when padding = 1)."""
+    L, C, H, W = gV.shape
+    gP = np.zeros((C, H, W), dtype=np.complex128)
+    for c in range(C):
+        for l in range(L):
+            g = zero_pad(gV[l, c]) if padding else gV[l, c]
+            Hm = transfer_function(g.shape[0], g.shape[1], pitch, wavelengths[c], -plane_z[l], band_limit)
+            r = np.fft.ifft2(np.conj(Hm) * np.fft.fft2(g))
+            gP[c] += crop(r, H, W) if padding else r
+    return gP
+
+
+def focal_stack_loss(P: np.ndarray, I_gt: np.ndarray, pitch: float, wavelengths, plane_z, band_limit: int = 0,
+                     padding: int = 0):
     """Eq. recon_loss with the mean taken over planes, channels and pixels:
     returns (loss, dL/dP as g = dL/dRe + j dL/dIm, intensities I[L][C][H][W])."""
-    V = inverse_propagate(P, pitch, wavelengths, plane_z)
+    V = inverse_propagate(P, pitch, wavelengths, plane_z, band_limit, padding)
     I = np.abs(V) ** 2
     n = I.size
     loss = float(np.mean((I - I_gt) ** 2))
     gV = (4.0 / n) * (I - I_gt) * V
-    C, H, W = P.shape
-    gP = np.zeros((C, H, W), dtype=np.complex128)
-    for c in range(C):
-        for l in range(len(plane_z)):
-            # adjoint of V_l = IDFT(conj-side transfer H_{-Z} DFT(P))
-            Hm = transfer_function(H, W, pitch, wavelengths[c], -plane_z[l])
-            gP[c] += np.fft.ifft2(np.conj(Hm) * np.fft.fft2(gV[l, c]))
-    return loss, gP, I
+    return loss, inverse_propagate_adjoint(gV, pitch, wavelengths, plane_z, band_limit, padding), I
 
 
 # ----------------------------------------------------------------------------
@@ -378,21 +412,15 @@ def paper_loss_intensities(I: np.ndarray, I_gt: np.ndarray, M: np.ndarray, lam: 
 
 
 def paper_loss(P: np.ndarray, I_gt: np.ndarray, M: np.ndarray, pitch: float, wavelengths, plane_z,
-               lam: float = SSIM_LAMBDA, band_limit: int = 0):
+               lam: float = SSIM_LAMBDA, band_limit: int = 0, padding: int = 0):
     """The paper's training loss for one view's hologram P [C][H][W]: the
     focal stack I_l = |V_l|^2 of Eq. plane2layer_asm against I_gt, with
     L_recon + L_SSIM.  Returns (loss, dL/dP as g = dL/dRe + j dL/dIm, I)."""
-    V = inverse_propagate(P, pitch, wavelengths, plane_z, band_limit)
+    V = inverse_propagate(P, pitch, wavelengths, plane_z, band_limit, padding)
     I = np.abs(V) ** 2
     loss, gI = paper_loss_intensities(I, I_gt, M, lam)
     gV = 2.0 * gI * V
-    C, H, W = P.shape
-    gP = np.zeros((C, H, W), dtype=np.complex128)
-    for c in range(C):
-        for l in range(len(plane_z)):
-            Hm = transfer_function(H, W, pitch, wavelengths[c], -plane_z[l], band_limit)
-            gP[c] += np.fft.ifft2(np.conj(Hm) * np.fft.fft2(gV[l, c]))
-    return loss, gP, I
+    return loss, inverse_propagate_adjoint(gV, pitch, wavelengths, plane_z, band_limit, padding), I
 
 
 def adan_step(p, g, g_prev, m, v, n, step: int, lr: float, beta1=0.9, beta2=0.92, beta3=0.99, eps=1e-8,

@@ -139,11 +139,9 @@ def _rs_brute(u0, pitch, lam, z, out_idx):
 
 
 def _asm_padded(u0, pitch, lam, z):
-    n = u0.shape[0]
-    pad = np.zeros((2 * n, 2 * n), dtype=np.complex128)
-    pad[n // 2:n // 2 + n, n // 2:n // 2 + n] = u0
-    out = oracle.propagate(pad, pitch, lam, z)
-    return out[n // 2:n // 2 + n, n // 2:n // 2 + n]
+    # the oracle's zero-padded mode: the field centred in a 2n x 2n grid of
+    # zeros, propagated, and the centre cropped back
+    return oracle.propagate(u0, pitch, lam, z, padding=1)
 
 
 def test_rayleigh_sommerfeld_brute_force():
@@ -282,3 +280,53 @@ def test_band_limit_inactive_on_the_paper_shaped_grids():
             a = oracle.transfer_function(H, W, PITCH, lam, z, band_limit=0)
             b = oracle.transfer_function(H, W, PITCH, lam, z, band_limit=1)
             assert np.array_equal(a, b)
+
+
+def test_zero_padding_is_the_embedding_done_by_hand():
+    # padding = 1 equals propagating an explicit zero embedding on the 2x
+    # grid and cropping the window the field occupied (odd sizes included)
+    rng = np.random.default_rng(12)
+    for H, W in ((16, 24), (15, 9)):
+        u = rng.normal(size=(H, W)) + 1j * rng.normal(size=(H, W))
+        big = np.zeros((2 * H, 2 * W), dtype=np.complex128)
+        big[H // 2:H // 2 + H, W // 2:W // 2 + W] = u
+        ref = oracle.propagate(big, PITCH, LAM, 3e-3)[H // 2:H // 2 + H, W // 2:W // 2 + W]
+        assert np.max(np.abs(oracle.propagate(u, PITCH, LAM, 3e-3, padding=1) - ref)) < 1e-12
+
+
+def test_zero_padding_removes_the_wrap_around_of_an_edge_source():
+    # a smooth source near the left edge (fully inside the grid: a truncated
+    # source would radiate outside the band): the padded ASM matches the
+    # brute-force (non-periodic) Rayleigh-Sommerfeld sum on both edges, while
+    # the circular ASM puts light on the far (right) edge that the
+    # non-periodic diffraction integral does not have
+    n, pitch, z = 48, 16e-6, 60e-3
+    s = 2 * 16e-6
+    i = np.arange(n)
+    I, J = np.meshgrid(i, i, indexing="ij")
+    u0 = np.exp(-(((I - n / 2) * pitch) ** 2 + ((J - 12) * pitch) ** 2) / (2 * s ** 2)).astype(np.complex128)
+    idx = [(n // 2, j) for j in (0, 2, 5, 10, n - 6, n - 3, n - 1)]
+    bf = _rs_brute(u0, pitch, LAM, z, idx)
+    pad = oracle.propagate(u0, pitch, LAM, z, padding=1)
+    circ = oracle.propagate(u0, pitch, LAM, z)
+    ep = rel(np.array([pad[p] for p in idx]), bf)
+    ec = rel(np.array([circ[p] for p in idx]), bf)
+    assert ep < 1e-6 and ec > 0.1, (ep, ec)
+
+
+@pytest.mark.parametrize("band_limit", [0, 1])
+def test_adjoint_dot_product_zero_padded(band_limit):
+    rng = np.random.default_rng(13)
+    L, C, H, W = 2, 2, 12, 20
+    wl, zs = (639e-9, 473e-9), (1e-3, 6e-3)
+    u = rng.normal(size=(L, C, H, W)) + 1j * rng.normal(size=(L, C, H, W))
+    g = rng.normal(size=(C, H, W)) + 1j * rng.normal(size=(C, H, W))
+    Au = oracle.propagate_planes(u, PITCH, wl, zs, band_limit, padding=1)
+    Ag = oracle.propagate_planes_adjoint(g, PITCH, wl, zs, band_limit, padding=1)
+    assert abs(np.sum(np.real(np.conj(g) * Au)) - np.sum(np.real(np.conj(Ag) * u))) < 1e-10 * np.sum(np.abs(g * Au))
+    # and the inverse propagation against its adjoint
+    P = rng.normal(size=(C, H, W)) + 1j * rng.normal(size=(C, H, W))
+    gV = rng.normal(size=(L, C, H, W)) + 1j * rng.normal(size=(L, C, H, W))
+    V = oracle.inverse_propagate(P, PITCH, wl, zs, band_limit, padding=1)
+    gP = oracle.inverse_propagate_adjoint(gV, PITCH, wl, zs, band_limit, padding=1)
+    assert abs(np.sum(np.real(np.conj(gV) * V)) - np.sum(np.real(np.conj(gP) * P))) < 1e-10 * np.sum(np.abs(gV * V))
