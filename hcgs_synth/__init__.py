@@ -42,6 +42,7 @@ class Optics:
     plane_z: tuple  # metres, distance Z_l from plane l to the hologram plane
     pitch: float = 8e-6  # metres, square pixels
     band_limit: int = 0  # 1: Matsushima-Shimobaba band limit on top of the evanescent cut
+    padding: int = 0  # 1: propagate on the 2x zero-padded grid (linear convolution)
 
     @property
     def C(self) -> int:

@@ -88,6 +88,15 @@ typedef struct {
                                  sqrt((2 du z)^2 + 1)) on both axes (inactive
                                  at 8 um pitch for the paper-shaped grids);
                                  other values: HCGS_ERR_INVALID_ARG            */
+    int padding;              /* 0: circular convolution on the H x W grid (the
+                                 DFTs of the equations taken on the grid as is);
+                                 1: linear convolution: every propagation runs on
+                                 a 2H x 2W grid with the field at rows H/2 ..
+                                 H/2 + H - 1, columns W/2 .. W/2 + W - 1 and zeros
+                                 elsewhere, H_z (and the band limit) on that
+                                 grid's frequencies, the same window cropped
+                                 back; 2H and 2W must be supported FFT lengths.
+                                 Not available in hcgs_asm_propagate_noalloc. */
 } hcgs_optics;
 
 /* Rasterizer options.  Values the paper leaves unstated (Algorithm 2 names

@@ -617,14 +617,16 @@ def densify(gauss: dict, accum, denom, noise, opts=None, extra=()):
 # whole view(s)
 # ----------------------------------------------------------------------------
 def render(gauss: dict, viewmats, intrs, optics, opts=None):
-    """Hologram P[V][C][H][W] and plane fields U[V][L][C][H][W] for V views."""
+    """Hologram P[V][C][H][W] and plane fields U[V][L][C][H][W] for V views
+    (the optics' band_limit and padding, when present, select the ASM variant)."""
     viewmats = np.asarray(viewmats).reshape(-1, 4, 4)
     intrs = np.asarray(intrs).reshape(-1, 4)
     Ps, Us, Ts, Ns = [], [], [], []
     for v in range(viewmats.shape[0]):
         pr = project(gauss, viewmats[v], intrs[v], optics.H, optics.W, opts)
         U, T, nc = composite(pr, opts)
-        Ps.append(propagate_planes(U, optics.pitch, optics.wavelengths, optics.plane_z))
+        Ps.append(propagate_planes(U, optics.pitch, optics.wavelengths, optics.plane_z,
+                                   getattr(optics, "band_limit", 0), getattr(optics, "padding", 0)))
         Us.append(U); Ts.append(T); Ns.append(nc)
     return np.stack(Ps), np.stack(Us), np.stack(Ts), np.stack(Ns)
 
@@ -636,7 +638,8 @@ def render_backward(gauss: dict, viewmats, intrs, optics, gP, opts=None) -> dict
     acc = None
     for v in range(viewmats.shape[0]):
         pr = project(gauss, viewmats[v], intrs[v], optics.H, optics.W, opts)
-        gU = propagate_planes_adjoint(np.asarray(gP[v]), optics.pitch, optics.wavelengths, optics.plane_z)
+        gU = propagate_planes_adjoint(np.asarray(gP[v]), optics.pitch, optics.wavelengths, optics.plane_z,
+                                      getattr(optics, "band_limit", 0), getattr(optics, "padding", 0))
         g2d = composite_backward(pr, gU, opts)
         acc = project_backward(gauss, viewmats[v], intrs[v], optics.H, optics.W, g2d, opts, acc)
     return acc

@@ -49,7 +49,7 @@ class HcgsError(RuntimeError):
 class _Optics(ctypes.Structure):
     _fields_ = [("H", c_int), ("W", c_int), ("C", c_int), ("L", c_int), ("pitch_x", c_double),
                 ("pitch_y", c_double), ("wavelength", POINTER(c_double)), ("plane_z", POINTER(c_double)),
-                ("band_limit", c_int)]
+                ("band_limit", c_int), ("padding", c_int)]
 
 
 class _RasterOpts(ctypes.Structure):
@@ -159,12 +159,12 @@ def _stream():
 
 def make_optics(o):
     """hcgs_optics from any object with H, W, wavelengths, plane_z, pitch (and
-    optionally band_limit, default 0)."""
+    optionally band_limit and padding, default 0)."""
     lam = (c_double * len(o.wavelengths))(*[float(x) for x in o.wavelengths])
     z = (c_double * len(o.plane_z))(*[float(x) for x in o.plane_z])
     s = _Optics(int(o.H), int(o.W), len(o.wavelengths), len(o.plane_z), float(o.pitch), float(o.pitch),
                 ctypes.cast(lam, POINTER(c_double)), ctypes.cast(z, POINTER(c_double)),
-                int(getattr(o, "band_limit", 0)))
+                int(getattr(o, "band_limit", 0)), int(getattr(o, "padding", 0)))
     s._keep = (lam, z)
     return s
 

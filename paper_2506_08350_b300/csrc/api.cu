@@ -93,8 +93,13 @@ static hcgs_status check_optics(hcgs_ctx* ctx, const hcgs_optics* o) {
     REQUIRE(ctx, o->wavelength && o->plane_z, "wavelength and plane_z must be host arrays");
     for (int c = 0; c < o->C; c++) REQUIRE(ctx, o->wavelength[c] > 0, "wavelengths must be > 0");
     REQUIRE(ctx, o->band_limit == 0 || o->band_limit == 1, "band_limit must be 0 or 1");
+    REQUIRE(ctx, o->padding == 0 || o->padding == 1, "padding must be 0 or 1");
     if (!fft_supported(o->H) || !fft_supported(o->W)) {
         set_err(ctx, HCGS_ERR_UNSUPPORTED_SIZE, "H and W must be 2^a 3^b 5^c and <= 4096");
+        return HCGS_ERR_UNSUPPORTED_SIZE;
+    }
+    if (o->padding && (!fft_supported(2 * o->H) || !fft_supported(2 * o->W))) {
+        set_err(ctx, HCGS_ERR_UNSUPPORTED_SIZE, "with padding, 2H and 2W must be 2^a 3^b 5^c and <= 4096");
         return HCGS_ERR_UNSUPPORTED_SIZE;
     }
     return HCGS_OK;
@@ -446,6 +451,20 @@ hcgs_status hcgs_focal_stack_loss(hcgs_ctx* ctx, const float* hologram, const fl
     REQUIRE(ctx, hologram && I_gt && loss, "NULL argument");
     REQUIRE(ctx, B >= 1, "B must be >= 1");
     cudaSetDevice(ctx->device);
+    if (o->padding) {
+        // zero-padded propagation: V by the general route, then the loss on V
+        const size_t nF = (size_t)B * o->L * o->C * o->H * o->W;
+        cudaStream_t st = S(stream);
+        HCGS_CUDA(ctx, grow(ctx, ctx->ws[2], nF * sizeof(float2), &ctx->bytes));
+        const int nb = focal_field_blocks((int64_t)nF);
+        HCGS_CUDA(ctx, grow(ctx, ctx->ws[3], (size_t)nb * sizeof(float), &ctx->bytes));
+        float2* V = (float2*)ctx->ws[2].p;
+        TRY(asm_spread(ctx, (const float2*)hologram, V, B, o, true, st));
+        TRY(focal_field(ctx, V, I_gt, I_out, (int64_t)nF, (float*)ctx->ws[3].p, st));
+        TRY(reduce_sum(ctx, (const float*)ctx->ws[3].p, nb, (float)(1.0 / (double)nF), loss, st));
+        if (g_hologram) TRY(asm_sum(ctx, V, (float2*)g_hologram, B, o, false, st));
+        return HCGS_OK;
+    }
     const float2* hq;
     TRY(get_htab(ctx, o, &hq));
     const size_t planeN = (size_t)o->H * o->W;
@@ -492,8 +511,8 @@ hcgs_status hcgs_paper_loss(hcgs_ctx* ctx, const float* hologram, const float* I
     REQUIRE(ctx, B >= 1, "B must be >= 1");
     REQUIRE(ctx, lambda_ssim >= 0.f && std::isfinite(lambda_ssim), "lambda_ssim must be finite and >= 0");
     cudaSetDevice(ctx->device);
-    const float2* hq;
-    TRY(get_htab(ctx, o, &hq));
+    const float2* hq = nullptr;
+    if (!o->padding) TRY(get_htab(ctx, o, &hq));
     const size_t planeN = (size_t)o->H * o->W;
     const size_t nP = (size_t)B * o->C * planeN, nF = (size_t)B * o->L * o->C * planeN;
     HCGS_CUDA(ctx, grow(ctx, ctx->ws[1], nP * sizeof(float2), &ctx->bytes));
@@ -507,15 +526,21 @@ hcgs_status hcgs_paper_loss(hcgs_ctx* ctx, const float* hologram, const float* I
     float *dmap, *Iws;
     TRY(paper_loss_ws(ctx, nF, I_out == nullptr, nblocks, &dmap, &Iws));
     float* I = I_out ? I_out : Iws;
-    // V_l = ASM(P, -z_l) for every plane: column DFT, row DFT x conj(H), inverse rows, inverse columns
-    TRY(fft_cols(ctx, (const float2*)hologram, S1, B * o->C, o->H, o->W, false, 1.f, st));
-    TRY(rows_spread(ctx, S1, V, B, o->L, o->C, o->H, o->W, hq, true, st));
-    TRY(fft_cols(ctx, V, V, B * o->L * o->C, o->H, o->W, true, 1.f / (float)planeN, st));
+    if (o->padding) {
+        TRY(asm_spread(ctx, (const float2*)hologram, V, B, o, true, st));
+    } else {
+        // V_l = ASM(P, -z_l) for every plane: column DFT, row DFT x conj(H), inverse rows, inverse columns
+        TRY(fft_cols(ctx, (const float2*)hologram, S1, B * o->C, o->H, o->W, false, 1.f, st));
+        TRY(rows_spread(ctx, S1, V, B, o->L, o->C, o->H, o->W, hq, true, st));
+        TRY(fft_cols(ctx, V, V, B * o->L * o->C, o->H, o->W, true, 1.f / (float)planeN, st));
+    }
     // I = |V|^2, loss partials, and dL/dV = 2 (dL/dI) V in place over V
     TRY(ssim_recon_loss(ctx, V, I, I_gt, masks, B, o->L, o->C, o->H, o->W, lambda_ssim, dmap,
                         (float*)ctx->ws[3].p, &nblocks, nullptr, st));
     TRY(reduce_sum(ctx, (const float*)ctx->ws[3].p, nblocks, (float)(1.0 / (double)nF), loss, st));
-    if (g_hologram) {
+    if (g_hologram && o->padding) {
+        TRY(asm_sum(ctx, V, (float2*)g_hologram, B, o, false, st));
+    } else if (g_hologram) {
         // dL/dP = sum over planes of the adjoint propagation of dL/dV
         TRY(fft_cols(ctx, V, V, B * o->L * o->C, o->H, o->W, false, 1.f, st));
         TRY(rows_sum(ctx, V, (float2*)g_hologram, B, o->L, o->C, o->H, o->W, hq, false, st));

@@ -69,7 +69,7 @@ struct hcgs_ctx {
     int device = 0;
     std::string last_error;
     size_t bytes = 0;
-    hcgs::DevBuf ws[6];                              // workspace slots
+    hcgs::DevBuf ws[8];                              // workspace slots (6, 7: zero-padded grids)
     std::map<int, hcgs::FftPlan> plans;              // FFT plans by length
     std::map<hcgs::HKey, hcgs::DevBuf> htab;         // transfer-function tables
     int* d_status = nullptr;                         // device status word
@@ -268,6 +268,9 @@ hcgs_status densify_apply(hcgs_ctx* ctx, const hcgs_gaussians* gi, int C, int L,
 hcgs_status ssim_recon_loss(hcgs_ctx* ctx, float2* V, float* I, const float* Igt, const float* M, int B, int L,
                             int C, int H, int W, float lam, float* dmap, float* partials, int* nblocks_out,
                             float* gI, cudaStream_t st);
+int focal_field_blocks(int64_t n);
+hcgs_status focal_field(hcgs_ctx* ctx, float2* V, const float* Igt, float* Iout, int64_t n, float* partials,
+                        cudaStream_t st);
 hcgs_status adan(hcgs_ctx* ctx, float* p, const float* g, float* gp, float* m, float* v, float* n, int64_t count,
                  int step, float lr, float b1, float b2, float b3, float eps, float wd, cudaStream_t st);
 

@@ -1223,8 +1223,66 @@ hcgs_status rows_spread(hcgs_ctx* ctx, const float2* in, float2* out, int B, int
 }
 
 // out[b][c] = sum_l IDFT(Hsel DFT(in[b][l][c])), Hsel = H_{Z_l} or its conjugate.
+// Zero embedding of P planes of H x W into 2H x 2W (field at rows H/2 ..,
+// columns W/2 ..), and the crop of that window back.
+__global__ void k_zero_pad(const float2* __restrict__ in, float2* __restrict__ out, int64_t P, int H, int W) {
+    const int W2 = 2 * W, H2 = 2 * H, oy = H / 2, ox = W / 2;
+    const int64_t total = P * H2 * W2;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % W2), y = (int)((i / W2) % H2);
+        const int64_t p = i / ((int64_t)W2 * H2);
+        const int yy = y - oy, xx = x - ox;
+        out[i] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? in[(p * H + yy) * W + xx] : make_float2(0.f, 0.f);
+    }
+}
+
+__global__ void k_crop(const float2* __restrict__ in, float2* __restrict__ out, int64_t P, int H, int W) {
+    const int oy = H / 2, ox = W / 2;
+    const int64_t total = P * H * W;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % W), y = (int)((i / W) % H);
+        const int64_t p = i / ((int64_t)W * H);
+        out[i] = in[(p * 2 * H + y + oy) * 2 * W + x + ox];
+    }
+}
+
+static hcgs_status pad_planes(hcgs_ctx* ctx, const float2* in, float2* out, int64_t P, int H, int W, cudaStream_t st) {
+    const int64_t total = P * 4 * H * W;
+    const int blocks = (int)std::min<int64_t>(148 * 16, (total + 255) / 256);
+    HCGS_KERNEL(ctx, "k_zero_pad", st, k_zero_pad<<<blocks, 256, 0, st>>>(in, out, P, H, W));
+    return HCGS_OK;
+}
+
+static hcgs_status crop_planes(hcgs_ctx* ctx, const float2* in, float2* out, int64_t P, int H, int W, cudaStream_t st) {
+    const int64_t total = P * H * W;
+    const int blocks = (int)std::min<int64_t>(148 * 16, (total + 255) / 256);
+    HCGS_KERNEL(ctx, "k_crop", st, k_crop<<<blocks, 256, 0, st>>>(in, out, P, H, W));
+    return HCGS_OK;
+}
+
+static hcgs_optics padded_optics(const hcgs_optics* o) {
+    hcgs_optics q = *o;
+    q.H = 2 * o->H;
+    q.W = 2 * o->W;
+    q.padding = 0;
+    return q;
+}
+
 hcgs_status asm_sum(hcgs_ctx* ctx, const float2* in, float2* out, int B, const hcgs_optics* o, bool conjH,
                     cudaStream_t st) {
+    if (o->padding) {
+        // linear convolution: embed, propagate and sum on the 2H x 2W grid, crop
+        const hcgs_optics q = padded_optics(o);
+        const size_t n4 = (size_t)4 * o->H * o->W;
+        HCGS_CUDA(ctx, grow(ctx, ctx->ws[6], (size_t)B * o->L * o->C * n4 * sizeof(float2), &ctx->bytes));
+        HCGS_CUDA(ctx, grow(ctx, ctx->ws[7], (size_t)B * o->C * n4 * sizeof(float2), &ctx->bytes));
+        float2* pin = (float2*)ctx->ws[6].p;
+        float2* pout = (float2*)ctx->ws[7].p;
+        hcgs_status s;
+        if ((s = pad_planes(ctx, in, pin, (int64_t)B * o->L * o->C, o->H, o->W, st))) return s;
+        if ((s = asm_sum(ctx, pin, pout, B, &q, conjH, st))) return s;
+        return crop_planes(ctx, pout, out, (int64_t)B * o->C, o->H, o->W, st);
+    }
     const float2* hq;
     hcgs_status s = get_htab(ctx, o, &hq);
     if (s) return s;
@@ -1240,6 +1298,18 @@ hcgs_status asm_sum(hcgs_ctx* ctx, const float2* in, float2* out, int B, const h
 // out[b][l][c] = IDFT(Hsel DFT(in[b][c])).
 hcgs_status asm_spread(hcgs_ctx* ctx, const float2* in, float2* out, int B, const hcgs_optics* o, bool conjH,
                        cudaStream_t st) {
+    if (o->padding) {
+        const hcgs_optics q = padded_optics(o);
+        const size_t n4 = (size_t)4 * o->H * o->W;
+        HCGS_CUDA(ctx, grow(ctx, ctx->ws[6], (size_t)B * o->C * n4 * sizeof(float2), &ctx->bytes));
+        HCGS_CUDA(ctx, grow(ctx, ctx->ws[7], (size_t)B * o->L * o->C * n4 * sizeof(float2), &ctx->bytes));
+        float2* pin = (float2*)ctx->ws[6].p;
+        float2* pout = (float2*)ctx->ws[7].p;
+        hcgs_status s;
+        if ((s = pad_planes(ctx, in, pin, (int64_t)B * o->C, o->H, o->W, st))) return s;
+        if ((s = asm_spread(ctx, pin, pout, B, &q, conjH, st))) return s;
+        return crop_planes(ctx, pout, out, (int64_t)B * o->L * o->C, o->H, o->W, st);
+    }
     const float2* hq;
     hcgs_status s = get_htab(ctx, o, &hq);
     if (s) return s;

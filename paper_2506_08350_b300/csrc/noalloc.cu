@@ -51,6 +51,7 @@ bool optics_ok(const hcgs_optics* o) {
     if (!o || o->H < 1 || o->W < 1 || o->C < 1 || o->C > MAX_C || o->L < 1 || o->L > MAX_L) return false;
     if (!(o->pitch_x > 0) || !(o->pitch_y > 0) || !o->wavelength || !o->plane_z) return false;
     if (o->band_limit != 0 && o->band_limit != 1) return false;
+    if (o->padding != 0) return false;  // the zero-padded grids need the context's workspace
     for (int c = 0; c < o->C; c++)
         if (!(o->wavelength[c] > 0)) return false;
     return true;

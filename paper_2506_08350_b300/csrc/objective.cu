@@ -433,6 +433,41 @@ hcgs_status ssim_recon_loss(hcgs_ctx* ctx, float2* V, float* I, const float* Igt
     return HCGS_OK;
 }
 
+// The plain focal-stack loss on a propagated field (the zero-padded route,
+// where the inverse propagation is not fused with the loss): I = |V|^2,
+// block partials of sum (I - I_gt)^2, and dL/dV = (4/n)(I - I_gt) V in place.
+__global__ void k_focal_field(float2* __restrict__ V, const float* __restrict__ Igt, float* __restrict__ Iout,
+                              int64_t n, float g4n, float* __restrict__ partials) {
+    __shared__ float red[8];
+    float acc = 0.f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 v = V[i];
+        const float I = fmaf(v.x, v.x, v.y * v.y);
+        const float d = I - Igt[i];
+        if (Iout) Iout[i] = I;
+        acc = fmaf(d, d, acc);
+        V[i] = make_float2(g4n * d * v.x, g4n * d * v.y);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += red[w];
+        partials[blockIdx.x] = t;
+    }
+}
+
+int focal_field_blocks(int64_t n) { return (int)std::min<int64_t>(148 * 8, (n + 255) / 256); }
+
+hcgs_status focal_field(hcgs_ctx* ctx, float2* V, const float* Igt, float* Iout, int64_t n, float* partials,
+                        cudaStream_t st) {
+    const float g4n = (float)(4.0 / (double)n);
+    HCGS_KERNEL(ctx, "k_focal_field", st,
+                k_focal_field<<<focal_field_blocks(n), 256, 0, st>>>(V, Igt, Iout, n, g4n, partials));
+    return HCGS_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Adan (Xie et al., Algorithm 1), decay-factor form: first step m = g, v = 0,
 // n = g^2; second step v = g - g_prev; then the moving averages
