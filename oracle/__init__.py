@@ -21,6 +21,8 @@ What each function follows (arXiv 2506.08350):
 * ``paper_loss``         the paper's training loss L_recon + L_SSIM (masked
                          reconstruction loss and structural similarity);
 * ``adan_step``, ``cosine_lr``  the paper's optimiser and learning-rate schedule;
+* ``phase_only_loss``    the phase-only hologram conversion objective (Sec. 6,
+                         phase-only hologram conversion paragraph);
 * ``philox4x32_10``, ``philox_normals``  the counter-based generator that
                          draws the densification noise (Salmon et al. 2011)
                          and standard normals from it by Box-Muller;
@@ -421,6 +423,38 @@ def paper_loss(P: np.ndarray, I_gt: np.ndarray, M: np.ndarray, pitch: float, wav
     loss, gI = paper_loss_intensities(I, I_gt, M, lam)
     gV = 2.0 * gI * V
     return loss, inverse_propagate_adjoint(gV, pitch, wavelengths, plane_z, band_limit, padding), I
+
+
+def phase_only_loss(U: np.ndarray, phase: np.ndarray, pitch: float, wavelengths, plane_z,
+                    lam: float = SSIM_LAMBDA, band_limit: int = 0, padding: int = 0):
+    """Objective of the phase-only conversion for one hologram: the target
+    fields U[L][C][H][W] (the complex hologram propagated to the planes) against
+    U_phi,l = IDFT(H_{-Z_l} DFT(e^{j phase})), phase[C][H][W]:
+      L = mean over (l, c, part, pixel) of d^2 + lambda mean over (l, c, part)
+          of (1 - SSIM), part = real and imaginary components, d = part(U_phi) - part(U).
+    Returns (loss, dL/dphase)."""
+    Pphi = np.exp(1j * np.asarray(phase, dtype=np.float64))
+    Uphi = inverse_propagate(Pphi, pitch, wavelengths, plane_z, band_limit, padding)
+    U = np.asarray(U, dtype=np.complex128)
+    # the two parts as 2 L C real images, part-major
+    X = np.stack([Uphi.real, Uphi.imag])
+    Y = np.stack([U.real, U.imag])
+    n = X.size
+    d = X - Y
+    loss = float(np.sum(d * d) / n)
+    g = 2.0 * d / n
+    K, L, C = X.shape[0], X.shape[1], X.shape[2]
+    s_sum = 0.0
+    for k in range(K):
+        for l in range(L):
+            for c in range(C):
+                s_sum += ssim(X[k, l, c], Y[k, l, c])
+                g[k, l, c] -= lam / (K * L * C) * ssim_grad(X[k, l, c], Y[k, l, c])
+    loss += lam * (1.0 - s_sum / (K * L * C))
+    gU = g[0] + 1j * g[1]
+    gP = inverse_propagate_adjoint(gU, pitch, wavelengths, plane_z, band_limit, padding)
+    # P = e^{j phase}: dL/dphase = gRe (-sin) + gIm cos = Im(conj(P) g)
+    return loss, np.imag(np.conj(Pphi) * gP)
 
 
 def adan_step(p, g, g_prev, m, v, n, step: int, lr: float, beta1=0.9, beta2=0.92, beta3=0.99, eps=1e-8,

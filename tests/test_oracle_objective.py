@@ -142,3 +142,38 @@ def test_cosine_schedule_endpoints():
     assert abs(oracle.cosine_lr(100, 100, 0.01, 1e-5) - 1e-5) < 1e-18
     assert abs(oracle.cosine_lr(50, 100, 0.01, 1e-5) - (0.01 + 1e-5) / 2) < 1e-15
     assert oracle.cosine_lr(250, 100, 0.01, 1e-5) == oracle.cosine_lr(100, 100, 0.01, 1e-5)
+
+
+def test_phase_only_loss_vanishes_at_a_phase_only_target():
+    # a unit-amplitude target: the optimum is its own phase, loss and
+    # gradient vanish there; elsewhere the gradient matches finite differences
+    C, H, W = 1, 14, 18
+    z = (1e-3, 4e-3)
+    rng = _rng(10)
+    phi0 = rng.uniform(0, 2 * np.pi, size=(C, H, W))
+    U = oracle.inverse_propagate(np.exp(1j * phi0), PITCH, (515e-9,), z)
+    loss, g = oracle.phase_only_loss(U, phi0, PITCH, (515e-9,), z, lam=0.3)
+    assert abs(loss) < 1e-12 and np.max(np.abs(g)) < 1e-12
+    phi = phi0 + rng.normal(0.0, 0.5, size=phi0.shape)
+    loss, g = oracle.phase_only_loss(U, phi, PITCH, (515e-9,), z, lam=0.3)
+    h = 1e-6
+    for (c, i, j) in [(0, 0, 0), (0, 7, 9), (0, 13, 17), (0, 3, 12)]:
+        pp, pm = phi.copy(), phi.copy()
+        pp[c, i, j] += h
+        pm[c, i, j] -= h
+        fd = (oracle.phase_only_loss(U, pp, PITCH, (515e-9,), z, lam=0.3)[0] -
+              oracle.phase_only_loss(U, pm, PITCH, (515e-9,), z, lam=0.3)[0]) / (2 * h)
+        assert abs(fd - g[c, i, j]) < 1e-6 * max(1.0, abs(fd)), (fd, g[c, i, j])
+
+
+def test_phase_only_loss_without_ssim_is_the_field_mse():
+    C, H, W = 2, 10, 12
+    z = (0.0, 2e-3)
+    rng = _rng(11)
+    P = rng.normal(size=(C, H, W)) + 1j * rng.normal(size=(C, H, W))
+    U = oracle.inverse_propagate(P, PITCH, (639e-9, 515e-9), z)
+    phi = rng.uniform(0, 2 * np.pi, size=(C, H, W))
+    Uphi = oracle.inverse_propagate(np.exp(1j * phi), PITCH, (639e-9, 515e-9), z)
+    loss, _ = oracle.phase_only_loss(U, phi, PITCH, (639e-9, 515e-9), z, lam=0.0)
+    # mean over the real and imaginary parts = half the mean squared complex distance
+    assert abs(loss - 0.5 * np.mean(np.abs(Uphi - U) ** 2)) < 1e-12 * loss
