@@ -369,6 +369,32 @@ hcgs_status hcgs_init_apply(hcgs_ctx* ctx, const float* y, int N, int C, float* 
 hcgs_status hcgs_asm_propagate_noalloc(const float* in, int B, const hcgs_optics* optics, float* out,
                                        void* stream);
 
+/* ---------------- phase-only hologram conversion (Sec. 6) ---------------- */
+/* Objective of the conversion of a complex hologram P = A e^{j phi} into a
+ * phase-only one e^{j phi_opt}: both are propagated to the planes,
+ * U_l = IDFT(H_{-Z_l} DFT(P)) (the target, given) and U_phi,l the same of
+ * e^{j phase}, and
+ *   L = mean over (b, l, c, part, pixel) of (part(U_phi) - part(U))^2
+ *       + lambda_ssim mean over (b, l, c, part) of (1 - SSIM(part(U_phi), part(U))),
+ * part = the real and the imaginary component (the SSIM of hcgs_paper_loss).
+ *   U_target device [B][L][C][H][W] complex64 (e.g. hcgs_asm_propagate with
+ *            sign -1, reduce_planes 0, of the complex hologram)
+ *   phase    device [B][C][H][W] float (rad)
+ *   loss     device [1] float (output)
+ *   g_phase  device [B][C][H][W] float, nullable: dL/dphase (output) */
+hcgs_status hcgs_phase_only_loss(hcgs_ctx* ctx, const float* U_target, const float* phase, int B,
+                                 const hcgs_optics* optics, float lambda_ssim, float* loss, float* g_phase,
+                                 void* stream);
+/* phase[i] = arg(hologram[i]) in (-pi, pi]: hologram device [n] complex64,
+ * phase device [n] float (the starting point of the conversion). */
+hcgs_status hcgs_hologram_phase(hcgs_ctx* ctx, const float* hologram, int64_t n, float* phase, void* stream);
+/* out[i] = s x[i] for n floats (device; out may equal x), e.g. to normalise
+ * a complex hologram's RMS amplitude to 1 before the conversion. */
+hcgs_status hcgs_scale(hcgs_ctx* ctx, const float* x, int64_t n, float s, float* out, void* stream);
+/* hologram[i] = e^{j phase[i]}: phase device [n] float, hologram device [n]
+ * complex64 (the phase-only hologram an SLM displays). */
+hcgs_status hcgs_phase_hologram(hcgs_ctx* ctx, const float* phase, int64_t n, float* hologram, void* stream);
+
 /* ---------------- densification (Algorithm 1, Supp. C) ---------------- */
 /* The 3DGS densification rules that Sec. 5 adopts (period: 300 steps),
  * with phase-aware copies (Supp. C: copies and children get a small random
@@ -422,7 +448,8 @@ hcgs_status hcgs_densify_apply(hcgs_ctx* ctx, const hcgs_gaussians* g_in, int C,
  * key (seed low 32 bits, seed high 32 bits)), four uint32 words per block.
  * kind 0: out device [n] uint32, the words in order; kind 1: out device [n]
  * float standard normals, each word pair (a, b) giving, with u = (a + 1/2)
- * 2^-32, v = (b + 1/2) 2^-32, sqrt(-2 ln u) (cos 2 pi v, sin 2 pi v). */
+ * 2^-32, v = (b + 1/2) 2^-32, sqrt(-2 ln u) (cos 2 pi v, sin 2 pi v);
+ * kind 2: out device [n] float uniforms (w + 1/2) 2^-32 in (0, 1). */
 hcgs_status hcgs_philox(hcgs_ctx* ctx, uint64_t seed, uint32_t stream_id, int64_t n, int kind, void* out,
                         void* stream);
 

@@ -541,6 +541,11 @@ def philox_normals(seed: int, n: int, stream: int = 0) -> np.ndarray:
     return z[:n]
 
 
+def philox_uniforms(seed: int, n: int, stream: int = 0) -> np.ndarray:
+    """n uniforms (w + 1/2) 2^-32 in (0, 1) from the words of ``philox_words``."""
+    return (philox_words(seed, n, stream).astype(np.float64) + 0.5) * 2.0 ** -32
+
+
 DENSIFY_OPTS = dict(grad_threshold=2e-4, split_scale=0.02, prune_opacity=5e-3, prune_scale=0.0,
                     split_shrink=1.6, phase_noise=0.1)
 KEEP, PRUNE, CLONE, SPLIT = 0, 1, 2, 3

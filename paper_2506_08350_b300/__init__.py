@@ -39,7 +39,8 @@ EXPORTS = ("hcgs_ctx_create", "hcgs_ctx_destroy", "hcgs_status_string", "hcgs_la
            "hcgs_profile_enable", "hcgs_profile_summary", "hcgs_asm_propagate_noalloc", "hcgs_mlp_mse_loss",
            "hcgs_cast_bf16", "hcgs_init_features", "hcgs_init_targets", "hcgs_init_apply",
            "hcgs_selftest_wait_timeout", "hcgs_paper_loss", "hcgs_paper_loss_intensities", "hcgs_adan_step",
-           "hcgs_densify_accumulate", "hcgs_densify_plan", "hcgs_densify_apply", "hcgs_philox")
+           "hcgs_densify_accumulate", "hcgs_densify_plan", "hcgs_densify_apply", "hcgs_philox",
+           "hcgs_phase_only_loss", "hcgs_hologram_phase", "hcgs_phase_hologram", "hcgs_scale")
 
 
 class HcgsError(RuntimeError):
@@ -114,6 +115,10 @@ _sig("hcgs_densify_plan", [_P, POINTER(_Gaussians), _P, _P, POINTER(_DensifyOpts
 _sig("hcgs_densify_apply", [_P, POINTER(_Gaussians), c_int, c_int, _P, _P, _P, POINTER(_DensifyOpts),
                             POINTER(_Grads), c_int, _P, _P, _P, _P])
 _sig("hcgs_philox", [_P, ctypes.c_uint64, ctypes.c_uint32, c_int64, c_int, _P, _P])
+_sig("hcgs_phase_only_loss", [_P, _P, _P, c_int, POINTER(_Optics), c_float, _P, _P, _P])
+_sig("hcgs_hologram_phase", [_P, _P, c_int64, _P, _P])
+_sig("hcgs_phase_hologram", [_P, _P, c_int64, _P, _P])
+_sig("hcgs_scale", [_P, _P, c_int64, c_float, _P, _P])
 _sig("hcgs_paper_loss", [_P, _P, _P, _P, c_int, POINTER(_Optics), c_float, _P, _P, _P, _P])
 _sig("hcgs_paper_loss_intensities", [_P, _P, _P, _P, c_int, c_int, c_int, c_int, c_int, c_float, _P, _P, _P])
 _sig("hcgs_adan_step", [_P, _P, _P, _P, _P, _P, _P, c_int64, c_int, c_float, c_float, c_float, c_float, c_float,
@@ -322,9 +327,25 @@ class Context:
         self._check(_lib.hcgs_adam_step(self.handle, _ptr(p), _ptr(g), _ptr(m), _ptr(v), p.numel(), int(step),
                                         float(lr), float(beta1), float(beta2), float(eps), _stream()))
 
+    def phase_only_loss(self, U_target, phase, B, optics, loss, g_phase=None, lambda_ssim=SSIM_LAMBDA):
+        self._check(_lib.hcgs_phase_only_loss(self.handle, _ptr(U_target), _ptr(phase), int(B),
+                                              ctypes.byref(make_optics(optics)), float(lambda_ssim), _ptr(loss),
+                                              _ptr(g_phase), _stream()))
+
+    def scale(self, x, s, out):
+        """out = s x elementwise (float32 storage; complex arrays as their floats)."""
+        n = x.numel() * (2 if x.is_complex() else 1)
+        self._check(_lib.hcgs_scale(self.handle, _ptr(x), n, float(s), _ptr(out), _stream()))
+
+    def phase_hologram(self, phase, hologram):
+        self._check(_lib.hcgs_phase_hologram(self.handle, _ptr(phase), phase.numel(), _ptr(hologram), _stream()))
+
+    def hologram_phase(self, hologram, phase):
+        self._check(_lib.hcgs_hologram_phase(self.handle, _ptr(hologram), hologram.numel(), _ptr(phase), _stream()))
+
     def philox(self, seed, n, out, kind=1, stream_id=0):
         """n counter-based random numbers into `out` (kind 0: uint32 words as
-        int32/uint32 storage, 1: float32 standard normals)."""
+        int32/uint32 storage, 1: float32 standard normals, 2: float32 uniforms in (0, 1))."""
         self._check(_lib.hcgs_philox(self.handle, int(seed) & (2 ** 64 - 1), int(stream_id) & 0xFFFFFFFF, int(n),
                                      int(kind), _ptr(out), _stream()))
 

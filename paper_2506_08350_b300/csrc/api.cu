@@ -660,11 +660,78 @@ hcgs_status hcgs_philox(hcgs_ctx* ctx, uint64_t seed, uint32_t stream_id, int64_
                         void* stream) {
     if (!ctx) return HCGS_ERR_INVALID_ARG;
     REQUIRE(ctx, n >= 0 && n < ((int64_t)1 << 34), "n out of range");
-    REQUIRE(ctx, kind == 0 || kind == 1, "kind must be 0 (words) or 1 (normals)");
+    REQUIRE(ctx, kind >= 0 && kind <= 2, "kind must be 0 (words), 1 (normals) or 2 (uniforms)");
     if (n == 0) return HCGS_OK;
     REQUIRE(ctx, out, "NULL argument");
     cudaSetDevice(ctx->device);
     return philox(ctx, seed, stream_id, n, kind, out, S(stream));
+}
+
+hcgs_status hcgs_phase_only_loss(hcgs_ctx* ctx, const float* U_target, const float* phase, int B,
+                                 const hcgs_optics* o, float lambda_ssim, float* loss, float* g_phase, void* stream) {
+    if (!ctx) return HCGS_ERR_INVALID_ARG;
+    TRY(check_optics(ctx, o));
+    REQUIRE(ctx, U_target && phase && loss, "NULL argument");
+    REQUIRE(ctx, B >= 1, "B must be >= 1");
+    REQUIRE(ctx, lambda_ssim >= 0.f && std::isfinite(lambda_ssim), "lambda_ssim must be finite and >= 0");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = S(stream);
+    const int64_t nP = (int64_t)B * o->C * o->H * o->W, nF = nP * o->L;
+    // e^{j phi} and its fields on the planes
+    HCGS_CUDA(ctx, grow(ctx, ctx->ws[8], (size_t)nP * sizeof(float2), &ctx->bytes));
+    HCGS_CUDA(ctx, grow(ctx, ctx->ws[2], (size_t)nF * sizeof(float2), &ctx->bytes));
+    HCGS_CUDA(ctx, grow(ctx, ctx->ws[9], (size_t)6 * nF * sizeof(float), &ctx->bytes));
+    float2* Pphi = (float2*)ctx->ws[8].p;
+    float2* Uphi = (float2*)ctx->ws[2].p;
+    float* X = (float*)ctx->ws[9].p;  // parts of U_phi [2][nF]
+    float* Y = X + 2 * nF;             // parts of the target
+    float* gX = Y + 2 * nF;
+    TRY(phasor(ctx, phase, Pphi, nP, st));
+    TRY(asm_spread(ctx, Pphi, Uphi, B, o, true, st));
+    TRY(split_parts(ctx, Uphi, X, nF, st));
+    TRY(split_parts(ctx, (const float2*)U_target, Y, nF, st));
+    // the parts are 2 B L C real images: squared error (weight 1) + SSIM
+    int nblocks = 0;
+    TRY(ssim_recon_loss(ctx, nullptr, nullptr, nullptr, nullptr, 2 * B, o->L, o->C, o->H, o->W, 0.f, nullptr,
+                        nullptr, &nblocks, nullptr, st, 1));
+    float *dmap, *unused;
+    TRY(paper_loss_ws(ctx, (size_t)(2 * nF), false, nblocks, &dmap, &unused));
+    TRY(ssim_recon_loss(ctx, nullptr, X, Y, nullptr, 2 * B, o->L, o->C, o->H, o->W, lambda_ssim, dmap,
+                        (float*)ctx->ws[3].p, &nblocks, gX, st, 1));
+    TRY(reduce_sum(ctx, (const float*)ctx->ws[3].p, nblocks, (float)(1.0 / (double)(2 * nF)), loss, st));
+    if (g_phase) {
+        TRY(merge_parts(ctx, gX, Uphi, nF, st));
+        TRY(asm_sum(ctx, Uphi, Pphi, B, o, false, st));
+        TRY(phase_grad(ctx, phase, Pphi, g_phase, nP, st));
+    }
+    return HCGS_OK;
+}
+
+hcgs_status hcgs_scale(hcgs_ctx* ctx, const float* x, int64_t n, float s, float* out, void* stream) {
+    if (!ctx) return HCGS_ERR_INVALID_ARG;
+    REQUIRE(ctx, n >= 0, "n must be >= 0");
+    if (n == 0) return HCGS_OK;
+    REQUIRE(ctx, x && out, "NULL argument");
+    cudaSetDevice(ctx->device);
+    return scale(ctx, x, s, out, n, S(stream));
+}
+
+hcgs_status hcgs_phase_hologram(hcgs_ctx* ctx, const float* phase, int64_t n, float* hologram, void* stream) {
+    if (!ctx) return HCGS_ERR_INVALID_ARG;
+    REQUIRE(ctx, n >= 0, "n must be >= 0");
+    if (n == 0) return HCGS_OK;
+    REQUIRE(ctx, hologram && phase, "NULL argument");
+    cudaSetDevice(ctx->device);
+    return phasor(ctx, phase, (float2*)hologram, n, S(stream));
+}
+
+hcgs_status hcgs_hologram_phase(hcgs_ctx* ctx, const float* hologram, int64_t n, float* phase, void* stream) {
+    if (!ctx) return HCGS_ERR_INVALID_ARG;
+    REQUIRE(ctx, n >= 0, "n must be >= 0");
+    if (n == 0) return HCGS_OK;
+    REQUIRE(ctx, hologram && phase, "NULL argument");
+    cudaSetDevice(ctx->device);
+    return phase_of(ctx, (const float2*)hologram, phase, n, S(stream));
 }
 
 hcgs_status hcgs_adam_step(hcgs_ctx* ctx, float* p, const float* g, float* m, float* v, int64_t n, int step,

@@ -69,7 +69,7 @@ struct hcgs_ctx {
     int device = 0;
     std::string last_error;
     size_t bytes = 0;
-    hcgs::DevBuf ws[8];                              // workspace slots (6, 7: zero-padded grids)
+    hcgs::DevBuf ws[10];                             // workspace slots (6, 7: zero-padded grids; 8, 9: phase-only conversion)
     std::map<int, hcgs::FftPlan> plans;              // FFT plans by length
     std::map<hcgs::HKey, hcgs::DevBuf> htab;         // transfer-function tables
     int* d_status = nullptr;                         // device status word
@@ -267,7 +267,13 @@ hcgs_status densify_apply(hcgs_ctx* ctx, const hcgs_gaussians* gi, int C, int L,
 // ---- the paper's objective and optimiser (objective.cu) ----
 hcgs_status ssim_recon_loss(hcgs_ctx* ctx, float2* V, float* I, const float* Igt, const float* M, int B, int L,
                             int C, int H, int W, float lam, float* dmap, float* partials, int* nblocks_out,
-                            float* gI, cudaStream_t st);
+                            float* gI, cudaStream_t st, int plain = 0);
+hcgs_status phasor(hcgs_ctx* ctx, const float* phi, float2* P, int64_t n, cudaStream_t st);
+hcgs_status split_parts(hcgs_ctx* ctx, const float2* U, float* out, int64_t n, cudaStream_t st);
+hcgs_status merge_parts(hcgs_ctx* ctx, const float* g, float2* out, int64_t n, cudaStream_t st);
+hcgs_status phase_grad(hcgs_ctx* ctx, const float* phi, const float2* gP, float* gphi, int64_t n, cudaStream_t st);
+hcgs_status phase_of(hcgs_ctx* ctx, const float2* P, float* phi, int64_t n, cudaStream_t st);
+hcgs_status scale(hcgs_ctx* ctx, const float* x, float s, float* out, int64_t n, cudaStream_t st);
 int focal_field_blocks(int64_t n);
 hcgs_status focal_field(hcgs_ctx* ctx, float2* V, const float* Igt, float* Iout, int64_t n, float* partials,
                         cudaStream_t st);

@@ -47,11 +47,17 @@ __global__ void k_philox(uint64_t seed, uint32_t stream, int64_t n, int normal, 
     for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
         const uint4 w = philox4x32_10(make_uint4((uint32_t)b, stream, 0u, 0u), key);
         const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
-        if (!normal) {
+        if (normal == 0) {
             uint32_t* o = (uint32_t*)out;
 #pragma unroll
             for (int i = 0; i < 4; i++)
                 if (4 * b + i < n) o[4 * b + i] = ws[i];
+        } else if (normal == 2) {
+            // uniforms (w + 1/2) 2^-32 in (0, 1), rounded to float
+            float* o = (float*)out;
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+                if (4 * b + i < n) o[4 * b + i] = (float)(((double)ws[i] + 0.5) * 0x1p-32);
         } else {
             // Box-Muller on the word pairs (in double: the draws are few)
             float* o = (float*)out;

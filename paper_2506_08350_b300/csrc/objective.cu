@@ -250,7 +250,7 @@ __device__ __forceinline__ void cp_async_n(void* dst, const void* src, bool ok, 
 template <bool FROM_FIELD, bool VEC>
 __global__ void __launch_bounds__(SS_NT)
     k_ssim_partials(const float2* __restrict__ V, float* __restrict__ I, const float* __restrict__ Igt,
-                    const float* __restrict__ M, int C, int H, int W, float lam, float* __restrict__ dmap,
+                    const float* __restrict__ M, int C, int H, int W, float lam, int plain, float* __restrict__ dmap,
                     float* __restrict__ partials) {
     __shared__ __align__(16) float inp[2][SS_EH][SS_XW];
     __shared__ __align__(16) float2 h[2][SS_EH][SS_TW];
@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(SS_NT)
         const float yv = inp[1][row0 + k + SS_R][SS_XO + SS_R + col];
         if constexpr (FROM_FIELD) I[p] = xv;
         const float dl = xv - yv;
-        const float w = 1.f + mv[k] + yv * yv;
+        const float w = plain ? 1.f : 1.f + mv[k] + yv * yv;
         acc += dl * dl * w + lam * (1.f - S);
     }
     const float s = block_sum(acc, red);
@@ -338,8 +338,8 @@ __global__ void __launch_bounds__(SS_NT)
 template <bool TO_FIELD, bool VEC>
 __global__ void __launch_bounds__(SS_NT)
     k_ssim_grad(const float* __restrict__ I, const float* __restrict__ Igt, const float* __restrict__ M, int C,
-                int H, int W, float lam, float inv_n, const float* __restrict__ dmap, float* __restrict__ gI,
-                float2* __restrict__ V) {
+                int H, int W, float lam, int plain, float inv_n, const float* __restrict__ dmap,
+                float* __restrict__ gI, float2* __restrict__ V) {
     __shared__ __align__(16) float inp[3][SS_EH][SS_XW];
     __shared__ __align__(16) float2 h2[1][SS_EH][SS_TW];
     __shared__ __align__(16) float h1[1][SS_EH][SS_TW];
@@ -386,7 +386,7 @@ __global__ void __launch_bounds__(SS_NT)
         if (gx >= W || gy >= H) continue;
         const size_t p = (size_t)img * HW + (size_t)gy * W + gx;
         const float xv = xo[k], yv = yo[k];
-        const float w = 1.f + mv[k] + yv * yv;
+        const float w = plain ? 1.f : 1.f + mv[k] + yv * yv;
         const float g = inv_n * (2.f * (xv - yv) * w - lam * (g01[0][k].x + 2.f * xv * g01[0][k].y + yv * g2[0][k]));
         if constexpr (TO_FIELD) {
             const float2 v = vo[TO_FIELD ? k : 0];
@@ -399,11 +399,12 @@ __global__ void __launch_bounds__(SS_NT)
 
 // Loss partials and gradient of L_recon + L_SSIM for B L C images of H x W.
 // V != nullptr: intensities |V|^2 (written to I), gradient dL/dV over V;
-// otherwise intensities read from I and dL/dI written to gI.  dmap holds
+// otherwise intensities read from I and dL/dI written to gI.  plain = 1: the
+// squared error carries weight 1 (no mask or target weighting).  dmap holds
 // 3 B L C H W floats; partials one float per block (query with partials = NULL).
 hcgs_status ssim_recon_loss(hcgs_ctx* ctx, float2* V, float* I, const float* Igt, const float* M, int B, int L,
                             int C, int H, int W, float lam, float* dmap, float* partials, int* nblocks_out,
-                            float* gI, cudaStream_t st) {
+                            float* gI, cudaStream_t st, int plain) {
     const dim3 grid((W + SS_TW - 1) / SS_TW, (H + SS_TH - 1) / SS_TH, B * L * C);
     *nblocks_out = (int)(grid.x * grid.y * grid.z);
     if (!partials) return HCGS_OK;  // size query
@@ -416,9 +417,9 @@ hcgs_status ssim_recon_loss(hcgs_ctx* ctx, float2* V, float* I, const float* Igt
 #define HCGS_SSIM_LAUNCH(F, VEC)                                                                              \
     do {                                                                                                      \
         HCGS_KERNEL(ctx, "k_ssim_partials", st,                                                               \
-                    (k_ssim_partials<F, VEC><<<grid, blk, 0, st>>>(V, I, Igt, M, C, H, W, lam, dmap, partials))); \
+                    (k_ssim_partials<F, VEC><<<grid, blk, 0, st>>>(V, I, Igt, M, C, H, W, lam, plain, dmap, partials))); \
         HCGS_KERNEL(ctx, "k_ssim_grad", st,                                                                   \
-                    (k_ssim_grad<F, VEC><<<grid, blk, 0, st>>>(I, Igt, M, C, H, W, lam, inv_n, dmap,            \
+                    (k_ssim_grad<F, VEC><<<grid, blk, 0, st>>>(I, Igt, M, C, H, W, lam, plain, inv_n, dmap,     \
                                                                F ? nullptr : gI, F ? V : nullptr)));          \
     } while (0)
     if (V && vec)
@@ -465,6 +466,79 @@ hcgs_status focal_field(hcgs_ctx* ctx, float2* V, const float* Igt, float* Iout,
     const float g4n = (float)(4.0 / (double)n);
     HCGS_KERNEL(ctx, "k_focal_field", st,
                 k_focal_field<<<focal_field_blocks(n), 256, 0, st>>>(V, Igt, Iout, n, g4n, partials));
+    return HCGS_OK;
+}
+
+// Phase-only conversion pieces: e^{j phi}; the real and imaginary parts of a
+// field as two planes (part-major) and back; dL/dphi = Im(conj(e^{j phi}) g)
+// for g = dL/dRe + j dL/dIm of e^{j phi}; the phase of a complex hologram.
+__global__ void k_phasor(const float* __restrict__ phi, float2* __restrict__ P, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float s, c;
+        sincosf(phi[i], &s, &c);
+        P[i] = make_float2(c, s);
+    }
+}
+
+__global__ void k_split_parts(const float2* __restrict__ U, float* __restrict__ out, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 u = U[i];
+        out[i] = u.x;
+        out[n + i] = u.y;
+    }
+}
+
+__global__ void k_merge_parts(const float* __restrict__ g, float2* __restrict__ out, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = make_float2(g[i], g[n + i]);
+}
+
+__global__ void k_phase_grad(const float* __restrict__ phi, const float2* __restrict__ gP, float* __restrict__ gphi,
+                             int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float s, c;
+        sincosf(phi[i], &s, &c);
+        const float2 g = gP[i];
+        gphi[i] = c * g.y - s * g.x;
+    }
+}
+
+__global__ void k_scale(const float* __restrict__ x, float s, float* __restrict__ out, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = s * x[i];
+}
+
+__global__ void k_phase_of(const float2* __restrict__ P, float* __restrict__ phi, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 p = P[i];
+        phi[i] = atan2f(p.y, p.x);
+    }
+}
+
+static int ew_blocks(int64_t n) { return (int)std::min<int64_t>(148 * 16, (n + 255) / 256); }
+
+hcgs_status phasor(hcgs_ctx* ctx, const float* phi, float2* P, int64_t n, cudaStream_t st) {
+    HCGS_KERNEL(ctx, "k_phasor", st, k_phasor<<<ew_blocks(n), 256, 0, st>>>(phi, P, n));
+    return HCGS_OK;
+}
+hcgs_status split_parts(hcgs_ctx* ctx, const float2* U, float* out, int64_t n, cudaStream_t st) {
+    HCGS_KERNEL(ctx, "k_split_parts", st, k_split_parts<<<ew_blocks(n), 256, 0, st>>>(U, out, n));
+    return HCGS_OK;
+}
+hcgs_status merge_parts(hcgs_ctx* ctx, const float* g, float2* out, int64_t n, cudaStream_t st) {
+    HCGS_KERNEL(ctx, "k_merge_parts", st, k_merge_parts<<<ew_blocks(n), 256, 0, st>>>(g, out, n));
+    return HCGS_OK;
+}
+hcgs_status phase_grad(hcgs_ctx* ctx, const float* phi, const float2* gP, float* gphi, int64_t n, cudaStream_t st) {
+    HCGS_KERNEL(ctx, "k_phase_grad", st, k_phase_grad<<<ew_blocks(n), 256, 0, st>>>(phi, gP, gphi, n));
+    return HCGS_OK;
+}
+hcgs_status scale(hcgs_ctx* ctx, const float* x, float s, float* out, int64_t n, cudaStream_t st) {
+    HCGS_KERNEL(ctx, "k_scale", st, k_scale<<<ew_blocks(n), 256, 0, st>>>(x, s, out, n));
+    return HCGS_OK;
+}
+hcgs_status phase_of(hcgs_ctx* ctx, const float2* P, float* phi, int64_t n, cudaStream_t st) {
+    HCGS_KERNEL(ctx, "k_phase_of", st, k_phase_of<<<ew_blocks(n), 256, 0, st>>>(P, phi, n));
     return HCGS_OK;
 }
 

@@ -41,6 +41,8 @@ def test_philox_words_and_normals(P, ctx, seed, stream, n):
     ctx.philox(seed, n, z, kind=1, stream_id=stream)
     ref = oracle.philox_normals(seed, n, stream)
     assert np.max(np.abs(z.cpu().numpy() - ref) / np.maximum(1.0, np.abs(ref))) < 1e-6
+    ctx.philox(seed, n, z, kind=2, stream_id=stream)
+    assert np.max(np.abs(z.cpu().numpy() - oracle.philox_uniforms(seed, n, stream))) < 1e-7
 
 def _scene(n, C=3, L=4, seed=0):
     rng = np.random.default_rng(seed)
