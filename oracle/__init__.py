@@ -89,6 +89,10 @@ def _L():
             lib.oracle_project_backward.restype = None
             lib.oracle_sort.argtypes = [I, d, i, I, i]
             lib.oracle_sort.restype = I
+            lib.oracle_composite_soft.argtypes = [I] * 5 + [d, d, d, d, d, d, d, i, d, d, d]
+            lib.oracle_composite_soft.restype = None
+            lib.oracle_composite_rho_dense.argtypes = [I] * 5 + [d, d, d, d, i, d, d, i, d, d, d]
+            lib.oracle_composite_rho_dense.restype = None
             _lib = lib
     return _lib
 
@@ -177,6 +181,41 @@ def composite_backward(proj: dict, gU, opts=None, rows=None):
                                    _ip(proj["valid"]), _dp(ov), int(r0), int(r1), _dp(g),
                                    _dp(out["mu"]), _dp(out["conic"]), _dp(out["opac"]), _dp(out["w"]))
     return out
+
+
+def composite_soft(proj: dict, rho, opts=None):
+    """Compositing with continuous plane weights rho[N][L] (alpha_eff = alpha
+    rho_l, every Gaussian visited on every plane): the smooth extension of
+    ``composite`` that defines the dense plane-weight gradient; equal to
+    ``composite`` at the one-hot rho of the argmax planes."""
+    N, L, C, H, W = (proj[k] for k in ("N", "L", "C", "H", "W"))
+    U = np.zeros((L, C, H, W, 2))
+    T = np.ones((L, H, W))
+    r = np.ascontiguousarray(rho, dtype=np.float64).reshape(N, L)
+    _L().oracle_composite_soft(N, L, C, H, W, _dp(proj["mu"]), _dp(proj["conic"]), _dp(proj["opac"]),
+                               _dp(proj["depth"]), _dp(r), _dp(proj["w"]), _dp(proj["bbox"]), _ip(proj["valid"]),
+                               _dp(_opt_vec(opts)), _dp(U), _dp(T))
+    return U[..., 0] + 1j * U[..., 1], T
+
+
+def composite_rho_dense(proj: dict, gU, opts=None) -> np.ndarray:
+    """dL/drho_{n,l} [N][L] of ``composite_soft`` at the one-hot rho, for the
+    planes each Gaussian is not assigned to (zero at the assigned plane, whose
+    value is o dL/do of ``composite_backward``)."""
+    N, L, C, H, W = (proj[k] for k in ("N", "L", "C", "H", "W"))
+    g = np.ascontiguousarray(np.stack([np.real(gU), np.imag(gU)], axis=-1), dtype=np.float64)
+    out = np.zeros((N, L))
+    _L().oracle_composite_rho_dense(N, L, C, H, W, _dp(proj["mu"]), _dp(proj["conic"]), _dp(proj["opac"]),
+                                    _dp(proj["depth"]), _ip(proj["plane"]), _dp(proj["w"]), _dp(proj["bbox"]),
+                                    _ip(proj["valid"]), _dp(_opt_vec(opts)), _dp(g), _dp(out))
+    return out
+
+
+def ste_softmax(plane_logits, tau: float) -> np.ndarray:
+    """softmax(rho'/tau) per Gaussian, max-subtracted (Eq. ste's backward weights)."""
+    r = np.asarray(plane_logits, dtype=np.float64)
+    e = np.exp((r - r.max(axis=1, keepdims=True)) / tau)
+    return e / e.sum(axis=1, keepdims=True)
 
 
 def project_backward(gauss: dict, viewmat, intr, H, W, g2d: dict, opts=None, acc=None) -> dict:
@@ -670,17 +709,27 @@ def render(gauss: dict, viewmats, intrs, optics, opts=None):
     return np.stack(Ps), np.stack(Us), np.stack(Ts), np.stack(Ns)
 
 
-def render_backward(gauss: dict, viewmats, intrs, optics, gP, opts=None) -> dict:
-    """dL/dparams (float64) for the loss Re<gP, P> summed over views."""
+def render_backward(gauss: dict, viewmats, intrs, optics, gP, opts=None, rho_grad: int = 0) -> dict:
+    """dL/dparams (float64) for the loss Re<gP, P> summed over views.
+    rho_grad = 1: the plane logits also receive the dense plane-weight
+    gradient of the planes a Gaussian is not assigned to, through the same
+    straight-through rule (elementwise product with softmax(rho'/tau))."""
     viewmats = np.asarray(viewmats).reshape(-1, 4, 4)
     intrs = np.asarray(intrs).reshape(-1, 4)
     acc = None
+    dense = None
     for v in range(viewmats.shape[0]):
         pr = project(gauss, viewmats[v], intrs[v], optics.H, optics.W, opts)
         gU = propagate_planes_adjoint(np.asarray(gP[v]), optics.pitch, optics.wavelengths, optics.plane_z,
                                       getattr(optics, "band_limit", 0), getattr(optics, "padding", 0))
         g2d = composite_backward(pr, gU, opts)
         acc = project_backward(gauss, viewmats[v], intrs[v], optics.H, optics.W, g2d, opts, acc)
+        if rho_grad:
+            d = composite_rho_dense(pr, gU, opts)
+            dense = d if dense is None else dense + d
+    if rho_grad and dense is not None:
+        tau = (opts or DEFAULT_OPTS).get("tau", DEFAULT_OPTS["tau"])
+        acc["plane_logits"] = acc["plane_logits"] + dense * ste_softmax(gauss["plane_logits"], tau)
     return acc
 
 

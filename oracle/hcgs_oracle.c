@@ -427,6 +427,146 @@ void oracle_composite_backward(int N, int L, int C, int H, int W,
 }
 
 /*
+ * Compositing with continuous plane weights rho[N][L] (the smooth extension of
+ * the per-plane field used to define a dense plane-weight gradient): per
+ * pixel and plane l, every visible Gaussian in visiting order, whatever its
+ * assigned plane, with alpha = min(alpha_max, o G) >= alpha_min adds
+ * w alpha rho_l T and T <- T (1 - alpha rho_l); the walk stops once
+ * T < T_eps (after the add).  With one-hot rho this is oracle_composite.
+ */
+void oracle_composite_soft(int N, int L, int C, int H, int W,
+                           const double* mu, const double* conic, const double* opac,
+                           const double* depth, const double* rho, const double* w,
+                           const double* bbox, const int* valid, const double* opt,
+                           double* U, double* T_final) {
+    int* ord = (int*)malloc(sizeof(int) * (N > 0 ? N : 1));
+    int* zero = (int*)calloc(N > 0 ? N : 1, sizeof(int));
+    int m = oracle_sort(N, depth, valid, (int)opt[O_ORDER], ord);
+    grid_t g;
+    grid_build(&g, 1, H, W, 0, H, m, ord, zero, bbox);
+    const double amin = opt[O_AMIN], amax = opt[O_AMAX], teps = opt[O_TEPS];
+#pragma omp parallel for collapse(2) schedule(dynamic, 4)
+    for (int l = 0; l < L; l++)
+        for (int i = 0; i < H; i++) {
+            double acc[2 * 16];
+            for (int j = 0; j < W; j++) {
+                size_t cell = (size_t)(i / CELL) * g.gx + j / CELL;
+                double T = 1.0;
+                for (int c = 0; c < 2 * C; c++) acc[c] = 0;
+                for (int64_t e = g.off[cell]; e < g.off[cell + 1]; e++) {
+                    int n = g.idx[e];
+                    double G, dx, dy; int cl;
+                    double a = eval_alpha(mu + 2 * n, conic + 3 * n, opac[n], (double)j, (double)i, amax, &G, &dx, &dy, &cl);
+                    if (a < amin) continue;
+                    double ae = a * rho[(size_t)n * L + l];
+                    if (ae == 0.0) continue;
+                    for (int c = 0; c < C; c++) {
+                        acc[2 * c] += w[2 * (C * n + c)] * ae * T;
+                        acc[2 * c + 1] += w[2 * (C * n + c) + 1] * ae * T;
+                    }
+                    T *= (1.0 - ae);
+                    if (T < teps) break;
+                }
+                for (int c = 0; c < C; c++) {
+                    size_t o = ((((size_t)l * C + c) * H + i) * W + j) * 2;
+                    U[o] = acc[2 * c]; U[o + 1] = acc[2 * c + 1];
+                }
+                T_final[((size_t)l * H + i) * W + j] = T;
+            }
+        }
+    grid_free(&g);
+    free(zero);
+    free(ord);
+}
+
+/*
+ * Dense plane-weight gradient of the hard-assignment compositing for one view:
+ * drho[N][L] (+=) is dL/drho_{n,l} of oracle_composite_soft at the one-hot rho
+ * of the argmax planes, for the planes l a Gaussian is NOT assigned to (the
+ * assigned plane's value comes from oracle_composite_backward as o dL/do).
+ * At rho_{n,l} = 0 Gaussian n adds nothing and attenuates nothing on plane l,
+ * so for every pixel the plane-l walk reaches it at (alpha = min(alpha_max,
+ * o G) >= alpha_min, the walk not yet stopped):
+ *   dU_l/drho_{n,l} = o G (w_n T_l - S_l),
+ * with T_l the plane's transmittance at n's place in the visiting order and
+ * S_l the sum of the plane's contributions behind it (d alpha_eff / d rho =
+ * o G: the alpha_max clamp is inactive at rho = 0).
+ */
+void oracle_composite_rho_dense(int N, int L, int C, int H, int W,
+                                const double* mu, const double* conic, const double* opac,
+                                const double* depth, const int* plane, const double* w,
+                                const double* bbox, const int* valid, const double* opt,
+                                const double* gU, double* drho) {
+    int* ord = (int*)malloc(sizeof(int) * (N > 0 ? N : 1));
+    int* zero = (int*)calloc(N > 0 ? N : 1, sizeof(int));
+    int m = oracle_sort(N, depth, valid, (int)opt[O_ORDER], ord);
+    grid_t g;
+    grid_build(&g, 1, H, W, 0, H, m, ord, zero, bbox);
+    const double amin = opt[O_AMIN], amax = opt[O_AMAX], teps = opt[O_TEPS];
+#pragma omp parallel
+    {
+        int cap = 1024;
+        int* vn = (int*)malloc(sizeof(int) * cap);       /* virtual entries: Gaussian,  */
+        double* vg = (double*)malloc(sizeof(double) * cap); /* o G, T at its place,      */
+        double* vT = (double*)malloc(sizeof(double) * cap);
+        double* vP = (double*)malloc(sizeof(double) * 2 * 16 * cap); /* prefix of the plane's field */
+#pragma omp for collapse(2) schedule(dynamic, 4)
+        for (int l = 0; l < L; l++)
+            for (int i = 0; i < H; i++)
+                for (int j = 0; j < W; j++) {
+                    size_t cell = (size_t)(i / CELL) * g.gx + j / CELL;
+                    double T = 1.0, pre[2 * 16];
+                    for (int c = 0; c < 2 * C; c++) pre[c] = 0;
+                    int K = 0;
+                    for (int64_t e = g.off[cell]; e < g.off[cell + 1]; e++) {
+                        int n = g.idx[e];
+                        double G, dx, dy; int cl;
+                        double a = eval_alpha(mu + 2 * n, conic + 3 * n, opac[n], (double)j, (double)i, amax, &G, &dx, &dy, &cl);
+                        if (a < amin) continue;
+                        if (plane[n] == l) {
+                            for (int c = 0; c < C; c++) {
+                                pre[2 * c] += w[2 * (C * n + c)] * a * T;
+                                pre[2 * c + 1] += w[2 * (C * n + c) + 1] * a * T;
+                            }
+                            T *= (1.0 - a);
+                            if (T < teps) break;
+                        } else {
+                            if (K == cap) {
+                                cap *= 2;
+                                vn = (int*)realloc(vn, sizeof(int) * cap);
+                                vg = (double*)realloc(vg, sizeof(double) * cap);
+                                vT = (double*)realloc(vT, sizeof(double) * cap);
+                                vP = (double*)realloc(vP, sizeof(double) * 2 * 16 * cap);
+                            }
+                            vn[K] = n; vg[K] = opac[n] * G; vT[K] = T;
+                            for (int c = 0; c < 2 * C; c++) vP[(size_t)K * 32 + c] = pre[c];
+                            K++;
+                        }
+                    }
+                    /* the plane's whole field; S = field - prefix at each virtual entry */
+                    for (int k = 0; k < K; k++) {
+                        int n = vn[k];
+                        double d = 0;
+                        for (int c = 0; c < C; c++) {
+                            size_t o = ((((size_t)l * C + c) * H + i) * W + j) * 2;
+                            double Sr = pre[2 * c] - vP[(size_t)k * 32 + 2 * c];
+                            double Si = pre[2 * c + 1] - vP[(size_t)k * 32 + 2 * c + 1];
+                            double dUr = w[2 * (C * n + c)] * vT[k] - Sr;
+                            double dUi = w[2 * (C * n + c) + 1] * vT[k] - Si;
+                            d += gU[o] * dUr + gU[o + 1] * dUi;
+                        }
+#pragma omp atomic
+                        drho[(size_t)n * L + l] += vg[k] * d;
+                    }
+                }
+        free(vn); free(vg); free(vT); free(vP);
+    }
+    grid_free(&g);
+    free(zero);
+    free(ord);
+}
+
+/*
  * Adjoint of oracle_project for one view, accumulating (+=) into the
  * parameter gradients.  Inputs are the per-Gaussian 2D gradients of
  * oracle_composite_backward.  The plane-logit gradient follows the
