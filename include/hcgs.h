@@ -113,8 +113,15 @@ typedef struct {
     int order;                /* 0 front-to-back (nearest first), 1 back-to-front */
     int footprint;            /* 0 FP32 footprint; 1 FP16x2 footprint with FP32
                                  accumulation                                   */
-    int rho_grad;             /* must be 0: only the assigned plane's rho gets
-                                 gradient                                      */
+    int rho_grad;             /* 0: only the assigned plane's rho gets gradient
+                                 (the forward skips the other planes);
+                                 1: dense plane-weight gradient: every plane's
+                                 logit also receives dL/drho_l of compositing
+                                 with continuous weights (alpha_eff = alpha
+                                 rho_l) at the one-hot argmax weights, through
+                                 the same straight-through rule; costs an
+                                 all-plane binning and an extra pass that walks
+                                 every plane against every Gaussian of a tile  */
 } hcgs_raster_opts;
 
 /* Gaussian parameters k = (c, x, R, S, alpha, phi, rho') (Sec. 4.1), device,

@@ -116,7 +116,7 @@ static hcgs_status check_opts(hcgs_ctx* ctx, const hcgs_raster_opts* r) {
     REQUIRE(ctx, r->ste_tau > 0.f, "ste_tau must be > 0");
     REQUIRE(ctx, r->order == 0 || r->order == 1, "order must be 0 or 1");
     REQUIRE(ctx, r->footprint == 0 || r->footprint == 1, "footprint must be 0 or 1");
-    REQUIRE(ctx, r->rho_grad == 0, "only rho_grad = 0 is provided");
+    REQUIRE(ctx, r->rho_grad == 0 || r->rho_grad == 1, "rho_grad must be 0 or 1");
     return HCGS_OK;
 }
 
@@ -177,7 +177,8 @@ hcgs_status hcgs_ctx_create(hcgs_ctx** out, int device) {
 static void saved_free(hcgs_saved* s) {
     DevBuf* bufs[] = {&s->w, &s->proj, &s->rectn, &s->dkey, &s->dval, &s->nvalid, &s->rank, &s->sortid, &s->rec,
                       &s->rects, &s->planes, &s->ccount, &s->bcount, &s->ikey, &s->ival, &s->hist, &s->scan,
-                      &s->Tfin, &s->last, &s->slist, &s->U, &s->g2d, &s->gU, &s->cam};
+                      &s->Tfin, &s->last, &s->slist, &s->U, &s->g2d, &s->gU, &s->cam, &s->akey, &s->aval,
+                      &s->abcount, &s->drho};
     for (DevBuf* b : bufs) free_buf(*b);
     s->bytes = 0;
 }

@@ -113,6 +113,11 @@ struct hcgs_saved {
     hcgs::DevBuf g2d;      // [V][N][G2D] float 2D gradients (visiting order): mu 2, conic 3, o dL/do, w 2C
     hcgs::DevBuf gU;       // [V][L][C][H][W] float2 plane gradients
     hcgs::DevBuf cam;      // [V][20] float copies of the view matrices and intrinsics
+    // dense plane-weight gradient (opts.rho_grad = 1 only)
+    hcgs::DevBuf akey, aval;  // [2][M] all-plane instance bucket ids / ranks (sort ping-pong)
+    hcgs::DevBuf abcount;     // [V*CT + 1] all-plane bucket offsets
+    hcgs::DevBuf drho;        // [N][L] float dL/drho of the unassigned planes, summed over views
+    const uint32_t* alist = nullptr;  // sorted all-plane instance ranks (points into aval)
     const uint32_t* list = nullptr;  // sorted instance ranks (points into ival)
     size_t bytes = 0;
 };

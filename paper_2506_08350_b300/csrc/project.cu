@@ -162,6 +162,30 @@ __global__ void k_inst_gen(ProjArgs a, const uint32_t* __restrict__ coff, const 
         }
 }
 
+// The same instances with the plane left out of the bucket id (per view and
+// coarse tile, every plane's Gaussians), for the dense plane-weight gradient.
+__global__ void k_inst_gen_all(ProjArgs a, const uint32_t* __restrict__ coff, const uint2* __restrict__ rects,
+                               const uint32_t* __restrict__ nvalid, uint32_t* __restrict__ ikey,
+                               uint32_t* __restrict__ ival) {
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i >= (size_t)a.V * a.N) return;
+    const int v = (int)(i / a.N), s = (int)(i - (size_t)v * a.N);
+    if (s >= (int)nvalid[v]) return;
+    const uint2 rc = rects[i];
+    const uint32_t tx0 = rc.x & 0xFFFFu, tx1 = rc.x >> 16, ty0 = rc.y & 0xFFFFu, ty1 = rc.y >> 16;
+    if (!(tx0 < tx1 && ty0 < ty1)) return;
+    const uint32_t cx0 = tx0 / COARSE, cx1 = (tx1 + COARSE - 1) / COARSE;
+    const uint32_t cy0 = ty0 / COARSE, cy1 = (ty1 + COARSE - 1) / COARSE;
+    uint32_t pos = coff[i];
+    const uint32_t bb = (uint32_t)v * a.ctY;
+    for (uint32_t cy = cy0; cy < cy1; cy++)
+        for (uint32_t cx = cx0; cx < cx1; cx++) {
+            ikey[pos] = (bb + cy) * a.ctX + cx;
+            ival[pos] = (uint32_t)s;
+            pos++;
+        }
+}
+
 // Bucket start offsets from the sorted bucket ids: off[b] = first position
 // whose id >= b; off[NB] = M.
 __global__ void k_bucket_bounds(const uint32_t* __restrict__ key, uint32_t M, uint32_t NB, uint32_t* __restrict__ off) {
@@ -508,6 +532,22 @@ hcgs_status project_and_bin(hcgs_ctx* ctx, hcgs_saved* s, const hcgs_gaussians* 
     HCGS_KERNEL(ctx, "k_bucket_bounds", st, k_bucket_bounds<<<(unsigned)((M + 1 + T - 1) / T), T, 0, st>>>(skey, (uint32_t)M, (uint32_t)NB,
                                                                   (uint32_t*)s->bcount.p));
     HCGS_LAUNCH(ctx, "k_bucket_bounds");
+    if (s->opts.rho_grad) {
+        // all-plane lists: the same instances bucketed by (view, coarse tile)
+        const size_t NBA = (size_t)V * s->ctX * s->ctY;
+        HCGS_CUDA(ctx, grow(ctx, s->akey, 2 * Mc * sizeof(uint32_t), ob));
+        HCGS_CUDA(ctx, grow(ctx, s->aval, 2 * Mc * sizeof(uint32_t), ob));
+        HCGS_CUDA(ctx, grow(ctx, s->abcount, (NBA + 1) * sizeof(uint32_t), ob));
+        uint32_t* akey = (uint32_t*)s->akey.p;
+        uint32_t* aval = (uint32_t*)s->aval.p;
+        HCGS_KERNEL(ctx, "k_inst_gen_all", st, k_inst_gen_all<<<gridVN, T, 0, st>>>(a, coff, (const uint2*)s->rects.p,
+                                                                             (const uint32_t*)s->nvalid.p, akey, aval));
+        if ((e = radix_sort(ctx, s, akey, aval, 1, (size_t)M, bits_for(NBA), &which, st))) return e;
+        s->alist = aval + (size_t)which * M;
+        HCGS_KERNEL(ctx, "k_bucket_bounds", st,
+                    k_bucket_bounds<<<(unsigned)((M + 1 + T - 1) / T), T, 0, st>>>(akey + (size_t)which * M, (uint32_t)M,
+                                                                                (uint32_t)NBA, (uint32_t*)s->abcount.p));
+    }
     return HCGS_OK;
 }
 
@@ -519,7 +559,7 @@ __global__ void k_project_bwd(ProjArgs a, const float* __restrict__ means, const
                               const float* __restrict__ amplitude, const float* __restrict__ phase,
                               const float* __restrict__ plane_logits, const float* __restrict__ cam,
                               const uint32_t* __restrict__ rank, const float* __restrict__ g2d, float ste_tau,
-                              hcgs_gaussian_grads gr, int accumulate) {
+                              const float* __restrict__ drho_dense, hcgs_gaussian_grads gr, int accumulate) {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= a.N) return;
     const int C = a.C, G = g2d_count(C);
@@ -568,7 +608,10 @@ __global__ void k_project_bwd(ProjArgs a, const float* __restrict__ means, const
     for (int l = 0; l < a.L; l++) Z += expf((r[l] - mx) / ste_tau);
     const float sm_a = 1.f / Z;  // softmax at the argmax: exp(0) / Z
     for (int l = 0; l < a.L; l++) {
-        const float gv = l == am ? drho * sm_a : 0.f;
+        // dense mode: the unassigned planes' weights, times their softmax values
+        const float gv = l == am ? drho * sm_a
+                                 : (drho_dense ? drho_dense[(size_t)n * a.L + l] * (expf((r[l] - mx) / ste_tau) / Z)
+                                               : 0.f);
         if (accumulate) gr.plane_logits[(size_t)n * a.L + l] += gv;
         else gr.plane_logits[(size_t)n * a.L + l] = gv;
     }
@@ -589,7 +632,9 @@ hcgs_status project_backward(hcgs_ctx* ctx, hcgs_saved* s, const hcgs_gaussians*
     HCGS_KERNEL(ctx, "k_project_bwd", st, k_project_bwd<<<(s->N + 127) / 128, 128, 0, st>>>(a, g->means, g->log_scales, g->quats, g->opacity_logits,
                                                       g->amplitude, g->phase, g->plane_logits,
                                                       (const float*)s->cam.p, (const uint32_t*)s->rank.p,
-                                                      (const float*)s->g2d.p, s->opts.ste_tau, *gr, accumulate));
+                                                      (const float*)s->g2d.p, s->opts.ste_tau,
+                                                      s->opts.rho_grad ? (const float*)s->drho.p : nullptr, *gr,
+                                                      accumulate));
     HCGS_LAUNCH(ctx, "k_project_bwd");
     return HCGS_OK;
 }

@@ -534,6 +534,134 @@ __global__ void __launch_bounds__(RT, 24) k_raster_bwd(RasterArgs a, const float
     }
 }
 
+// ---------------------------------------------------------------------------
+// Dense plane-weight gradient (rho_grad = 1).  For plane l and a Gaussian n
+// assigned elsewhere, compositing with continuous weights (alpha_eff = alpha
+// rho_l) has, at rho_{n,l} = 0, dU_l/drho_{n,l} = o G (w_n T_l - S_l) at every
+// pixel whose plane-l walk reaches n (alpha = min(alpha_max, o G) >= alpha_min,
+// not yet stopped), T_l the plane's transmittance at n's place in the
+// visiting order and S_l = U_l - (the plane's field in front of n).  One warp
+// per (16 x 8 strip, plane l, view): pass A forms U_l at the warp's pixels
+// from the plane's own list (the forward's decisions); pass B walks the tile's
+// all-plane list in visiting order, advancing T and the prefix on plane-l
+// entries and reducing the others' terms over the strip into drho[n][l].
+// ---------------------------------------------------------------------------
+template <int C, bool H16>
+__global__ void __launch_bounds__(RT) k_raster_rho_dense(RasterArgs a, const uint32_t* __restrict__ aoff,
+                                                         const uint32_t* __restrict__ alist,
+                                                         const int* __restrict__ planes,
+                                                         const uint32_t* __restrict__ sortid,
+                                                         const float2* __restrict__ gU, float* __restrict__ drho) {
+    constexpr int NR = C <= 1 ? 2 : (C <= 3 ? 3 : 4);
+    __shared__ float4 srec[32][NR + 1];
+    __shared__ uint32_t spos[32], sid[32], skept[32];
+    const int lane = threadIdx.x;
+    const int strip = blockIdx.x, l = blockIdx.y, v = blockIdx.z;
+    const int tx = strip % a.tilesX, ty = (strip / a.tilesX) >> 1;
+    const int px = tx * TILE + (lane & 15);
+    const int sy = ty * TILE + 8 * ((strip / a.tilesX) & 1);
+    const int py = sy + (lane >> 4);
+    const bool colin = px < a.W;
+    const float sx0 = (float)(tx * TILE), sy0 = (float)sy;
+    const size_t vN = (size_t)v * a.N;
+    const float fpx = (float)px;
+    const float teps = a.teps;
+    const float2 pyA = make_float2((float)py, (float)(py + 2)), pyB = make_float2((float)(py + 4), (float)(py + 6));
+    const float2 T0A = make_float2(colin && py < a.H ? 1.f : 0.f, colin && py + 2 < a.H ? 1.f : 0.f);
+    const float2 T0B = make_float2(colin && py + 4 < a.H ? 1.f : 0.f, colin && py + 6 < a.H ? 1.f : 0.f);
+    // pass A: U_l at the warp's pixels
+    float2 uAX[C], uAY[C], uBX[C], uBY[C];
+#pragma unroll
+    for (int c = 0; c < C; c++) uAX[c] = uAY[c] = uBX[c] = uBY[c] = f2(0.f);
+    {
+        const uint32_t gb = ((uint32_t)(v * a.L + l) * a.ctY + ty / COARSE) * a.ctX + tx / COARSE;
+        const uint32_t beg = a.off[gb], n = a.off[gb + 1] - beg;
+        float2 TA = T0A, TB = T0B;
+        for (uint32_t p0 = 0; p0 < n; p0 += 32) {
+            const bool live = TA.x >= teps || TA.y >= teps || TB.x >= teps || TB.y >= teps;
+            if (!__any_sync(0xffffffffu, live)) break;
+            const int nh = stage_warp<NR>(a, vN, beg, p0, n, tx, ty, sx0, sy0, srec, spos, sid, skept);
+            for (int k = 0; k < nh; k++) {
+                const float4* rec = srec[k];
+                const float4 r0 = rec[0], r1 = rec[1], kk = rec[NR];
+                const EntryX x = entry_x(fpx, r0, kk);
+                float2 dyA, ogA, aA, dyB, ogB, aB;
+                eval_entry<H16>(x, pyA, pyB, r0, r1, kk, a.amax, dyA, ogA, aA, dyB, ogB, aB);
+                const bool c0 = TA.x >= teps && aA.x >= a.amin, c1 = TA.y >= teps && aA.y >= a.amin;
+                const bool c2 = TB.x >= teps && aB.x >= a.amin, c3 = TB.y >= teps && aB.y >= a.amin;
+                fwd_pair<C>(rec, aA, c0, c1, TA, uAX, uAY);
+                fwd_pair<C>(rec, aB, c2, c3, TB, uBX, uBY);
+            }
+            __syncwarp();
+        }
+    }
+    // upstream gradient at the warp's pixels
+    const size_t HW = (size_t)a.H * a.W;
+    const size_t pbase = ((size_t)v * a.L + l) * C;
+    float2 gq[4][C];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const bool in = colin && py + 2 * q < a.H;
+        const size_t pix = (size_t)(py + 2 * q) * a.W + px;
+#pragma unroll
+        for (int c = 0; c < C; c++) gq[q][c] = in ? gU[(pbase + c) * HW + pix] : make_float2(0.f, 0.f);
+    }
+    // pass B: every plane's Gaussians of the tile, in visiting order
+    const uint32_t gba = ((uint32_t)v * a.ctY + ty / COARSE) * a.ctX + tx / COARSE;
+    const uint32_t beg = aoff[gba], n = aoff[gba + 1] - beg;
+    RasterArgs aa = a;
+    aa.list = alist;
+    float2 TA = T0A, TB = T0B;
+    float2 pAX[C], pAY[C], pBX[C], pBY[C];  // prefix of the plane's field
+#pragma unroll
+    for (int c = 0; c < C; c++) pAX[c] = pAY[c] = pBX[c] = pBY[c] = f2(0.f);
+    for (uint32_t p0 = 0; p0 < n; p0 += 32) {
+        const bool live = TA.x >= teps || TA.y >= teps || TB.x >= teps || TB.y >= teps;
+        if (!__any_sync(0xffffffffu, live)) break;
+        const int nh = stage_warp<NR>(aa, vN, beg, p0, n, tx, ty, sx0, sy0, srec, spos, sid, skept);
+        for (int k = 0; k < nh; k++) {
+            const float4* rec = srec[k];
+            const float4 r0 = rec[0], r1 = rec[1], kk = rec[NR];
+            const uint32_t srank = sid[k];
+            const bool own = planes[vN + srank] == l;  // warp-uniform
+            const EntryX x = entry_x(fpx, r0, kk);
+            float2 dyA, ogA, aA, dyB, ogB, aB;
+            eval_entry<H16>(x, pyA, pyB, r0, r1, kk, a.amax, dyA, ogA, aA, dyB, ogB, aB);
+            const bool c0 = TA.x >= teps && aA.x >= a.amin, c1 = TA.y >= teps && aA.y >= a.amin;
+            const bool c2 = TB.x >= teps && aB.x >= a.amin, c3 = TB.y >= teps && aB.y >= a.amin;
+            if (own) {
+                fwd_pair<C>(rec, aA, c0, c1, TA, pAX, pAY);
+                fwd_pair<C>(rec, aB, c2, c3, TB, pBX, pBY);
+            } else {
+                // o G sum_c Re(conj(g_c) (w_c T - (U_c - prefix_c))) over the reached pixels
+                float acc = 0.f;
+                const float Tq[4] = {TA.x, TA.y, TB.x, TB.y};
+                const float og[4] = {ogA.x, ogA.y, ogB.x, ogB.y};
+                const bool cq[4] = {c0, c1, c2, c3};
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    float d = 0.f;
+#pragma unroll
+                    for (int c = 0; c < C; c++) {
+                        const float2 w = RecW<C>::get(rec, c);
+                        const float ux = q == 0 ? uAX[c].x : q == 1 ? uAX[c].y : q == 2 ? uBX[c].x : uBX[c].y;
+                        const float uy = q == 0 ? uAY[c].x : q == 1 ? uAY[c].y : q == 2 ? uBY[c].x : uBY[c].y;
+                        const float qx = q == 0 ? pAX[c].x : q == 1 ? pAX[c].y : q == 2 ? pBX[c].x : pBX[c].y;
+                        const float qy = q == 0 ? pAY[c].x : q == 1 ? pAY[c].y : q == 2 ? pBY[c].x : pBY[c].y;
+                        d = fmaf(gq[q][c].x, fmaf(w.x, Tq[q], -(ux - qx)), d);
+                        d = fmaf(gq[q][c].y, fmaf(w.y, Tq[q], -(uy - qy)), d);
+                    }
+                    acc = fmaf(cq[q] ? og[q] : 0.f, d, acc);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                if (lane == 0 && acc != 0.f) atomicAdd(&drho[(size_t)sortid[vN + srank] * a.L + l], acc);
+            }
+        }
+        __syncwarp();
+    }
+}
+
 hcgs_status raster_forward(hcgs_ctx* ctx, hcgs_saved* s, float2* U, float* T_out, int32_t* nc_out,
                            cudaStream_t st) {
     const size_t pl = (size_t)s->V * s->L * s->H * s->W;
@@ -585,6 +713,28 @@ hcgs_status raster_backward(hcgs_ctx* ctx, hcgs_saved* s, const float2* gU, cuda
     }
 #undef HCGS_BWD
     HCGS_LAUNCH(ctx, "k_raster_bwd");
+    if (s->opts.rho_grad) {
+        const size_t nd = (size_t)s->N * s->L;
+        HCGS_CUDA(ctx, grow(ctx, s->drho, (nd > 0 ? nd : 1) * sizeof(float), &s->bytes));
+        HCGS_CUDA(ctx, cudaMemsetAsync(s->drho.p, 0, (nd > 0 ? nd : 1) * sizeof(float), st));
+        const uint32_t* aoff = (const uint32_t*)s->abcount.p;
+        const int* pl = (const int*)s->planes.p;
+        const uint32_t* sid = (const uint32_t*)s->sortid.p;
+        float* dr = (float*)s->drho.p;
+#define HCGS_DENSE(CC)                                                                                           \
+    if (h16) HCGS_KERNEL(ctx, "k_raster_rho_dense", st,                                                        \
+                         (k_raster_rho_dense<CC, true><<<grid, RT, 0, st>>>(a, aoff, s->alist, pl, sid, gU, dr))); \
+    else HCGS_KERNEL(ctx, "k_raster_rho_dense", st,                                                            \
+                     (k_raster_rho_dense<CC, false><<<grid, RT, 0, st>>>(a, aoff, s->alist, pl, sid, gU, dr)))
+        switch (s->C) {
+            case 1: HCGS_DENSE(1); break;
+            case 2: HCGS_DENSE(2); break;
+            case 3: HCGS_DENSE(3); break;
+            default: HCGS_DENSE(4); break;
+        }
+#undef HCGS_DENSE
+        HCGS_LAUNCH(ctx, "k_raster_rho_dense");
+    }
     return HCGS_OK;
 }
 
