@@ -619,8 +619,10 @@ __global__ void k_wait_selftest(int* __restrict__ status) {
 }
 
 // out[b][c][i] = IDFT( sum_l Hsel_l * DFT(in[b][l][c][i]) )
+// (1920-point rows: three CTAs per SM fit the register file without spills
+// here, unlike the spread pass, and hide more of the row loads)
 template <bool CONJ, class RP>
-__global__ void __launch_bounds__(RP::T, RP::MINB)
+__global__ void __launch_bounds__(RP::T, RP::N == 1920 ? 3 : RP::MINB)
     k_rows_sum_reg(const float2* __restrict__ in, float2* __restrict__ out, int L, int C, int H,
                    const float2* __restrict__ hq, const float2* __restrict__ tw, int* __restrict__ status) {
     using namespace rfft;
