@@ -496,6 +496,8 @@ __global__ void __launch_bounds__(RT, 24) k_raster_bwd(RasterArgs a, const float
             eval_entry<H16>(x, pyA, pyB, r0, r1, kk, a.amax, dyA, ogA, aA, dyB, ogB, aB);
             const bool c0 = pos < last[0] && aA.x >= a.amin, c1 = pos < last[1] && aA.y >= a.amin;
             const bool c2 = pos < last[2] && aB.x >= a.amin, c3 = pos < last[3] && aB.y >= a.amin;
+            // no pixel of the strip took this step: zero gradient, T and B unchanged
+            if (!__any_sync(0xffffffffu, c0 || c1 || c2 || c3)) continue;
             {
                 // branch-free: pixels that did not take the step carry alpha 0
                 // through the pair (T and B unchanged, zero gradient)
