@@ -102,11 +102,24 @@ __device__ __forceinline__ bool strip_hits(float4 r0, float Cc, float o, float x
     return hit;
 }
 
+// Per-entry coefficients staged with the record.  FP32 tier: the base-2
+// exponent of o G = 2^(A' dx^2 + B' dx dy + C' dy^2 + log2 o).  FP16x2 tier:
+// the normalised-frame factors sqrt(A), sqrt(C) and rho2 = 2 B / sqrt(A C).
+template <bool H16>
+__device__ __forceinline__ float4 entry_coeffs(float4 q0, float4 q1) {
+    if (H16) {
+        const float sa = sqrtf(q0.z), sc = sqrtf(q1.x);
+        return make_float4(sa, sc, 2.f * q0.w / (sa * sc), 0.f);
+    }
+    constexpr float L2E = 1.4426950408889634f;
+    return make_float4(-0.5f * L2E * q0.z, -L2E * q0.w, -0.5f * L2E * q1.x, log2f(q1.y));
+}
+
 // Stream 32 list positions [p0, p0 + 32) of the bucket for one warp: keep the
 // entries whose rectangle covers tile (tx, ty) and whose footprint can reach
 // the warp's strip, and compact them, in list order, into the warp's slots.
 // Returns the number kept.
-template <int NR>
+template <int NR, bool H16>
 __device__ __forceinline__ int stage_warp(const RasterArgs& a, size_t vN, uint32_t beg, uint32_t p0, uint32_t n,
                                           int tx, int ty, float sx0, float sy0, float4 (*wrec)[NR + 1],
                                           uint32_t* wpos, uint32_t* wid, uint32_t* kept) {
@@ -135,9 +148,7 @@ __device__ __forceinline__ int stage_warp(const RasterArgs& a, size_t vN, uint32
         wrec[slot][1] = q1;
 #pragma unroll
         for (int k = 2; k < NR; k++) wrec[slot][k] = r[k];
-        // base-2 exponent of o G: o G = 2^(A' dx^2 + B' dx dy + C' dy^2 + log2 o)
-        constexpr float L2E = 1.4426950408889634f;
-        wrec[slot][NR] = make_float4(-0.5f * L2E * q0.z, -L2E * q0.w, -0.5f * L2E * q1.x, log2f(q1.y));
+        wrec[slot][NR] = entry_coeffs<H16>(q0, q1);
         wpos[slot] = p;
         wid[slot] = s;
         kept[slot] = s;
@@ -166,11 +177,10 @@ __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 // footprint's normalised frame, u = dx sqrt(A), v = dy sqrt(C),
 // q = u^2 + 2 rho u v + v^2 with rho = B / sqrt(A C) in (-1, 1), all O(1)
 // inside the support.  Accumulation stays FP32.
-__device__ __forceinline__ void eval_pair_h(float dx, float2 py2, float4 r0, float Cc, float o, float amax,
+__device__ __forceinline__ void eval_pair_h(float dx, float2 py2, float4 r0, float4 k, float o, float amax,
                                             float2& dy2, float2& og2, float2& a2) {
     dy2 = __fadd2_rn(py2, f2(-r0.y));
-    const float sa = sqrtf(r0.z), sc = sqrtf(Cc);
-    const float rho2 = 2.f * r0.w / (sa * sc);
+    const float sa = k.x, sc = k.y, rho2 = k.z;  // staged per entry
     const __half2 u = __float2half2_rn(dx * sa);
     const __half2 v = __floats2half2_rn(dy2.x * sc, dy2.y * sc);
     __half2 q = __hfma2(v, v, __hmul2(u, u));
@@ -204,8 +214,8 @@ __device__ __forceinline__ void eval_entry(const EntryX& x, float2 pyA, float2 p
                                            float amax, float2& dyA, float2& ogA, float2& aA, float2& dyB,
                                            float2& ogB, float2& aB) {
     if (H16) {
-        eval_pair_h(x.dx, pyA, r0, r1.x, r1.y, amax, dyA, ogA, aA);
-        eval_pair_h(x.dx, pyB, r0, r1.x, r1.y, amax, dyB, ogB, aB);
+        eval_pair_h(x.dx, pyA, r0, k, r1.y, amax, dyA, ogA, aA);
+        eval_pair_h(x.dx, pyB, r0, k, r1.y, amax, dyB, ogB, aB);
     } else {
         dyA = __fadd2_rn(pyA, f2(-r0.y));
         float2 e = __ffma2_rn(f2(x.bdx), dyA, f2(x.t0));
@@ -292,7 +302,7 @@ __global__ void __launch_bounds__(RT, 32) k_raster_fwd(RasterArgs a, float2* __r
     for (uint32_t p0 = 0; p0 < n; p0 += 32) {
         const bool live = TA.x >= teps || TA.y >= teps || TB.x >= teps || TB.y >= teps;
         if (!__any_sync(0xffffffffu, live)) break;
-        const int nh = stage_warp<NR>(a, vN, beg, p0, n, tx, ty, sx0, sy0, srec, spos, sid, kept + nkept);
+        const int nh = stage_warp<NR, H16>(a, vN, beg, p0, n, tx, ty, sx0, sy0, srec, spos, sid, kept + nkept);
         for (int k = 0; k < nh; k++) {
             const float4* rec = srec[k];
             const float4 r0 = rec[0], r1 = rec[1], kk = rec[NR];
@@ -412,7 +422,7 @@ __device__ __forceinline__ void entry_grads(float4 r0, float4 r1, float dx, floa
 
 // Loads kept entries [lo, lo + cnt) of a strip (Gaussian ids from the forward
 // pass) into the warp's slots: record and base-2 exponent coefficients.
-template <int NR>
+template <int NR, bool H16>
 __device__ __forceinline__ void stage_kept(const RasterArgs& a, size_t vN, const uint32_t* kept, uint32_t lo, int cnt,
                                            float4 (*wrec)[NR + 1], uint32_t* wid) {
     const int lane = threadIdx.x & 31;
@@ -424,8 +434,7 @@ __device__ __forceinline__ void stage_kept(const RasterArgs& a, size_t vN, const
         wrec[lane][1] = q1;
 #pragma unroll
         for (int k = 2; k < NR; k++) wrec[lane][k] = r[k];
-        constexpr float L2E = 1.4426950408889634f;
-        wrec[lane][NR] = make_float4(-0.5f * L2E * q0.z, -L2E * q0.w, -0.5f * L2E * q1.x, log2f(q1.y));
+        wrec[lane][NR] = entry_coeffs<H16>(q0, q1);
         wid[lane] = s;
     }
     __syncwarp();
@@ -486,7 +495,7 @@ __global__ void __launch_bounds__(RT, 24) k_raster_bwd(RasterArgs a, const float
     for (uint32_t hi = maxlast; hi > 0;) {
         const uint32_t lo = hi > 32u ? hi - 32u : 0u;
         const int nh = (int)(hi - lo);
-        stage_kept<NR>(a, vN, kept, lo, nh, srec, sid);
+        stage_kept<NR, H16>(a, vN, kept, lo, nh, srec, sid);
         for (int k = nh - 1; k >= 0; k--) {  // back-to-front over the visiting order
             const float4* rec = srec[k];
             const uint32_t pos = lo + (uint32_t)k;
@@ -582,7 +591,7 @@ __global__ void __launch_bounds__(RT) k_raster_rho_dense(RasterArgs a, const uin
         for (uint32_t p0 = 0; p0 < n; p0 += 32) {
             const bool live = TA.x >= teps || TA.y >= teps || TB.x >= teps || TB.y >= teps;
             if (!__any_sync(0xffffffffu, live)) break;
-            const int nh = stage_warp<NR>(a, vN, beg, p0, n, tx, ty, sx0, sy0, srec, spos, sid, skept);
+            const int nh = stage_warp<NR, H16>(a, vN, beg, p0, n, tx, ty, sx0, sy0, srec, spos, sid, skept);
             for (int k = 0; k < nh; k++) {
                 const float4* rec = srec[k];
                 const float4 r0 = rec[0], r1 = rec[1], kk = rec[NR];
@@ -620,7 +629,7 @@ __global__ void __launch_bounds__(RT) k_raster_rho_dense(RasterArgs a, const uin
     for (uint32_t p0 = 0; p0 < n; p0 += 32) {
         const bool live = TA.x >= teps || TA.y >= teps || TB.x >= teps || TB.y >= teps;
         if (!__any_sync(0xffffffffu, live)) break;
-        const int nh = stage_warp<NR>(aa, vN, beg, p0, n, tx, ty, sx0, sy0, srec, spos, sid, skept);
+        const int nh = stage_warp<NR, H16>(aa, vN, beg, p0, n, tx, ty, sx0, sy0, srec, spos, sid, skept);
         for (int k = 0; k < nh; k++) {
             const float4* rec = srec[k];
             const float4 r0 = rec[0], r1 = rec[1], kk = rec[NR];
