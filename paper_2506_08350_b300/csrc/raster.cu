@@ -176,16 +176,13 @@ __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 // conditioned for footprints of any size the quadratic is formed in the
 // footprint's normalised frame, u = dx sqrt(A), v = dy sqrt(C),
 // q = u^2 + 2 rho u v + v^2 with rho = B / sqrt(A C) in (-1, 1), all O(1)
-// inside the support.  Accumulation stays FP32.
-__device__ __forceinline__ void eval_pair_h(float dx, float2 py2, float4 r0, float4 k, float o, float amax,
-                                            float2& dy2, float2& og2, float2& a2) {
+// inside the support; the exponent -q log2(e) / 2 is a quadratic in v whose
+// coefficients are formed once per thread and entry.  Accumulation stays FP32.
+__device__ __forceinline__ void eval_pair_h(float2 py2, float4 r0, float sc, __half2 nc, __half2 a1, __half2 a0,
+                                            float o, float amax, float2& dy2, float2& og2, float2& a2) {
     dy2 = __fadd2_rn(py2, f2(-r0.y));
-    const float sa = k.x, sc = k.y, rho2 = k.z;  // staged per entry
-    const __half2 u = __float2half2_rn(dx * sa);
-    const __half2 v = __floats2half2_rn(dy2.x * sc, dy2.y * sc);
-    __half2 q = __hfma2(v, v, __hmul2(u, u));
-    q = __hfma2(__float2half2_rn(rho2), __hmul2(u, v), q);
-    const __half2 e = __hmul2(q, __float2half2_rn(-0.72134752044448170f));  // -log2(e) / 2
+    const __half2 v = __float22half2_rn(__fmul2_rn(dy2, f2(sc)));
+    const __half2 e = __hfma2(__hfma2(nc, v, a1), v, a0);
     const float2 G2 = __half22float2(h2exp2(e));
     og2 = __fmul2_rn(f2(o), G2);
     a2 = make_float2(fminf(amax, og2.x), fminf(amax, og2.y));
@@ -214,8 +211,14 @@ __device__ __forceinline__ void eval_entry(const EntryX& x, float2 pyA, float2 p
                                            float amax, float2& dyA, float2& ogA, float2& aA, float2& dyB,
                                            float2& ogB, float2& aB) {
     if (H16) {
-        eval_pair_h(x.dx, pyA, r0, k, r1.y, amax, dyA, ogA, aA);
-        eval_pair_h(x.dx, pyB, r0, k, r1.y, amax, dyB, ogB, aB);
+        // e = -(log2 e / 2)(u^2 + rho2 u v + v^2) = (nc v + a1) v + a0 in half
+        // precision, with u = dx sqrt(A) fixed per thread and entry
+        const float u = x.dx * k.x;
+        constexpr float c = 0.72134752044448170f;  // log2(e) / 2
+        const __half2 nc = __float2half2_rn(-c), a1 = __float2half2_rn(-c * k.z * u),
+                      a0 = __float2half2_rn(-c * u * u);
+        eval_pair_h(pyA, r0, k.y, nc, a1, a0, r1.y, amax, dyA, ogA, aA);
+        eval_pair_h(pyB, r0, k.y, nc, a1, a0, r1.y, amax, dyB, ogB, aB);
     } else {
         dyA = __fadd2_rn(pyA, f2(-r0.y));
         float2 e = __ffma2_rn(f2(x.bdx), dyA, f2(x.t0));
