@@ -17,8 +17,14 @@
  *                    Eq. layer2plane_asm, Eq. sum_planes)     -> hcgs_asm_propagate
  * hcgs_render_view runs all four.  Every step has a _backward twin (Supp.
  * D.4, Eq. ste).  The training-step pieces are hcgs_focal_stack_loss
- * (Eq. plane2layer_asm, Eq. recon_loss) and hcgs_adam_step; the learned
- * initialisation network is hcgs_mlp_forward / hcgs_mlp_backward.
+ * (Eq. plane2layer_asm, Eq. recon_loss) and hcgs_adam_step, and the paper's
+ * own recipe: hcgs_paper_loss (L_recon + L_SSIM, Sec. 3) and hcgs_adan_step
+ * (Sec. 5); Algorithm 1's densification is hcgs_densify_accumulate / _plan /
+ * _apply with hcgs_philox for its noise; the phase-only conversion of Sec. 6
+ * is hcgs_phase_only_loss; the learned initialisation network is
+ * hcgs_mlp_forward / hcgs_mlp_backward.  Options select the zero-padded
+ * propagation (hcgs_optics.padding), the FP16x2 footprint tier and the dense
+ * plane-weight gradient (hcgs_raster_opts.footprint, .rho_grad).
  *
  * Conventions (all entry points):
  *  - Memory: every array argument marked "device" is a device pointer owned
