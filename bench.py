@@ -234,7 +234,7 @@ def measure_config(ctx, P, S, name, tiers, dev, steps=5, warmup=2):
     """Forward views/s and forward + adjoint steps/s of a named workload
     (synthetic scene seed 0, views near camera 0, fixed random dL/dP), per
     footprint tier (0 FP32, 1 FP16x2; 2 FP32 with the dense plane-weight
-    gradient), CUDA events on the current stream."""
+    gradient; 3 BF16x2), CUDA events on the current stream."""
     import torch
     wl = S.workload(name)
     o = wl.optics
@@ -263,8 +263,8 @@ def measure_config(ctx, P, S, name, tiers, dev, steps=5, warmup=2):
 
     out = {"H": o.H, "W": o.W, "C": o.C, "L": o.L, "N": wl.N, "views_per_step": V, "steps": steps}
     for fp in tiers:
-        # tier 2: FP32 footprint with the dense plane-weight gradient (rho_grad = 1)
-        opts = dict(P.DEFAULT_OPTS, footprint=1 if fp == 1 else 0, rho_grad=1 if fp == 2 else 0)
+        # tier 2: FP32 footprint with the dense plane-weight gradient (rho_grad = 1); 3: BF16x2
+        opts = dict(P.DEFAULT_OPTS, footprint={1: 1, 3: 2}.get(fp, 0), rho_grad=1 if fp == 2 else 0)
         saved = P.Saved(ctx)
 
         def fwd():
@@ -276,7 +276,7 @@ def measure_config(ctx, P, S, name, tiers, dev, steps=5, warmup=2):
 
         ms_f = timed(fwd)
         ms_s = timed(step)
-        out[("fp32", "fp16x2", "fp32_dense_rho")[fp]] = {"fwd_views_per_s": V * 1e3 / ms_f, "fwd_bwd_steps_per_s": 1e3 / ms_s,
+        out[("fp32", "fp16x2", "fp32_dense_rho", "bf16x2")[fp]] = {"fwd_views_per_s": V * 1e3 / ms_f, "fwd_bwd_steps_per_s": 1e3 / ms_s,
                                            "fwd_bwd_views_per_s": V * 1e3 / ms_s, "ms_fwd": ms_f, "ms_fwd_bwd": ms_s}
         saved.release()
     del g, grads, holo, gP
@@ -466,7 +466,7 @@ def run_ours(args):
     configs = None
     if not args.no_configs and rank == 0:
         configs = {}
-        for name, tiers in (("c1_256_L2_N1k", (0,)), ("c2_1080p_L8_N100k", (0, 1, 2)),
+        for name, tiers in (("c1_256_L2_N1k", (0,)), ("c2_1080p_L8_N100k", (0, 1, 2, 3)),
                             ("c4_1080p_L12_N2M_V16", (0, 1))):
             configs[name] = measure_config(ctx, P, S, name, tiers, dev)
 

@@ -23,7 +23,7 @@
  * _apply with hcgs_philox for its noise; the phase-only conversion of Sec. 6
  * is hcgs_phase_only_loss; the learned initialisation network is
  * hcgs_mlp_forward / hcgs_mlp_backward.  Options select the zero-padded
- * propagation (hcgs_optics.padding), the FP16x2 footprint tier and the dense
+ * propagation (hcgs_optics.padding), the FP16x2 / BF16x2 footprint tiers and the dense
  * plane-weight gradient (hcgs_raster_opts.footprint, .rho_grad).
  *
  * Conventions (all entry points):
@@ -117,8 +117,10 @@ typedef struct {
     float clip_factor;        /* clamp of x/z, y/z in J (1.3; <= 0: no clamp)   */
     float ste_tau;            /* softmax temperature of Eq. ste (1e-3)          */
     int order;                /* 0 front-to-back (nearest first), 1 back-to-front */
-    int footprint;            /* 0 FP32 footprint; 1 FP16x2 footprint with FP32
-                                 accumulation                                   */
+    int footprint;            /* 0 FP32 footprint; 1 FP16x2 and 2 BF16x2 footprint
+                                 (exponent and exp() in packed half / bfloat16
+                                 precision in the footprint's normalised frame)
+                                 with FP32 accumulation                         */
     int rho_grad;             /* 0: only the assigned plane's rho gets gradient
                                  (the forward skips the other planes);
                                  1: dense plane-weight gradient: every plane's

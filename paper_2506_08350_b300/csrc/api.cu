@@ -115,7 +115,7 @@ static hcgs_status check_opts(hcgs_ctx* ctx, const hcgs_raster_opts* r) {
     REQUIRE(ctx, r->cov2d_dilation >= 0.f, "cov2d_dilation must be >= 0");
     REQUIRE(ctx, r->ste_tau > 0.f, "ste_tau must be > 0");
     REQUIRE(ctx, r->order == 0 || r->order == 1, "order must be 0 or 1");
-    REQUIRE(ctx, r->footprint == 0 || r->footprint == 1, "footprint must be 0 or 1");
+    REQUIRE(ctx, r->footprint >= 0 && r->footprint <= 2, "footprint must be 0, 1 or 2");
     REQUIRE(ctx, r->rho_grad == 0 || r->rho_grad == 1, "rho_grad must be 0 or 1");
     return HCGS_OK;
 }

@@ -17,6 +17,7 @@
 //
 // The alpha arithmetic uses explicitly rounded intrinsics so that the forward
 // and backward kernels take identical skip/stop decisions.
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include "common.cuh"
@@ -105,9 +106,9 @@ __device__ __forceinline__ bool strip_hits(float4 r0, float Cc, float o, float x
 // Per-entry coefficients staged with the record.  FP32 tier: the base-2
 // exponent of o G = 2^(A' dx^2 + B' dx dy + C' dy^2 + log2 o).  FP16x2 tier:
 // the normalised-frame factors sqrt(A), sqrt(C) and rho2 = 2 B / sqrt(A C).
-template <bool H16>
+template <int FT>
 __device__ __forceinline__ float4 entry_coeffs(float4 q0, float4 q1) {
-    if (H16) {
+    if (FT) {
         const float sa = sqrtf(q0.z), sc = sqrtf(q1.x);
         return make_float4(sa, sc, 2.f * q0.w / (sa * sc), 0.f);
     }
@@ -119,7 +120,7 @@ __device__ __forceinline__ float4 entry_coeffs(float4 q0, float4 q1) {
 // entries whose rectangle covers tile (tx, ty) and whose footprint can reach
 // the warp's strip, and compact them, in list order, into the warp's slots.
 // Returns the number kept.
-template <int NR, bool H16>
+template <int NR, int FT>
 __device__ __forceinline__ int stage_warp(const RasterArgs& a, size_t vN, uint32_t beg, uint32_t p0, uint32_t n,
                                           int tx, int ty, float sx0, float sy0, float4 (*wrec)[NR + 1],
                                           uint32_t* wpos, uint32_t* wid, uint32_t* kept) {
@@ -148,7 +149,7 @@ __device__ __forceinline__ int stage_warp(const RasterArgs& a, size_t vN, uint32
         wrec[slot][1] = q1;
 #pragma unroll
         for (int k = 2; k < NR; k++) wrec[slot][k] = r[k];
-        wrec[slot][NR] = entry_coeffs<H16>(q0, q1);
+        wrec[slot][NR] = entry_coeffs<FT>(q0, q1);
         wpos[slot] = p;
         wid[slot] = s;
         kept[slot] = s;
@@ -178,12 +179,31 @@ __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 // q = u^2 + 2 rho u v + v^2 with rho = B / sqrt(A C) in (-1, 1), all O(1)
 // inside the support; the exponent -q log2(e) / 2 is a quadratic in v whose
 // coefficients are formed once per thread and entry.  Accumulation stays FP32.
-__device__ __forceinline__ void eval_pair_h(float2 py2, float4 r0, float sc, __half2 nc, __half2 a1, __half2 a0,
-                                            float o, float amax, float2& dy2, float2& og2, float2& a2) {
+template <int FT>
+struct Half2Of;
+template <>
+struct Half2Of<1> {
+    using T = __half2;
+    static __device__ __forceinline__ T from(float x) { return __float2half2_rn(x); }
+    static __device__ __forceinline__ T from2(float2 x) { return __float22half2_rn(x); }
+    static __device__ __forceinline__ float2 to2(T x) { return __half22float2(x); }
+};
+template <>
+struct Half2Of<2> {
+    using T = __nv_bfloat162;
+    static __device__ __forceinline__ T from(float x) { return __float2bfloat162_rn(x); }
+    static __device__ __forceinline__ T from2(float2 x) { return __float22bfloat162_rn(x); }
+    static __device__ __forceinline__ float2 to2(T x) { return __bfloat1622float2(x); }
+};
+
+template <int FT>
+__device__ __forceinline__ void eval_pair_h(float2 py2, float4 r0, float sc, typename Half2Of<FT>::T nc,
+                                            typename Half2Of<FT>::T a1, typename Half2Of<FT>::T a0, float o,
+                                            float amax, float2& dy2, float2& og2, float2& a2) {
     dy2 = __fadd2_rn(py2, f2(-r0.y));
-    const __half2 v = __float22half2_rn(__fmul2_rn(dy2, f2(sc)));
-    const __half2 e = __hfma2(__hfma2(nc, v, a1), v, a0);
-    const float2 G2 = __half22float2(h2exp2(e));
+    const auto v = Half2Of<FT>::from2(__fmul2_rn(dy2, f2(sc)));
+    const auto e = __hfma2(__hfma2(nc, v, a1), v, a0);
+    const float2 G2 = Half2Of<FT>::to2(h2exp2(e));
     og2 = __fmul2_rn(f2(o), G2);
     a2 = make_float2(fminf(amax, og2.x), fminf(amax, og2.y));
 }
@@ -206,19 +226,20 @@ __device__ __forceinline__ EntryX entry_x(float px, float4 r0, float4 k) {
 // from the first by a linear correction: e(dy + 4) - e(dy) = 4 B' dx +
 // 16 C' + 8 C' dy (two packed operations instead of four).  Forward and
 // adjoint both evaluate through here, so they take identical decisions.
-template <bool H16>
+template <int FT>
 __device__ __forceinline__ void eval_entry(const EntryX& x, float2 pyA, float2 pyB, float4 r0, float4 r1, float4 k,
                                            float amax, float2& dyA, float2& ogA, float2& aA, float2& dyB,
                                            float2& ogB, float2& aB) {
-    if (H16) {
+    if constexpr (FT != 0) {
         // e = -(log2 e / 2)(u^2 + rho2 u v + v^2) = (nc v + a1) v + a0 in half
-        // precision, with u = dx sqrt(A) fixed per thread and entry
+        // (FT 1) or bfloat16 (FT 2) precision, with u = dx sqrt(A) fixed per
+        // thread and entry
+        using H2 = typename Half2Of<FT>::T;
         const float u = x.dx * k.x;
         constexpr float c = 0.72134752044448170f;  // log2(e) / 2
-        const __half2 nc = __float2half2_rn(-c), a1 = __float2half2_rn(-c * k.z * u),
-                      a0 = __float2half2_rn(-c * u * u);
-        eval_pair_h(pyA, r0, k.y, nc, a1, a0, r1.y, amax, dyA, ogA, aA);
-        eval_pair_h(pyB, r0, k.y, nc, a1, a0, r1.y, amax, dyB, ogB, aB);
+        const H2 nc = Half2Of<FT>::from(-c), a1 = Half2Of<FT>::from(-c * k.z * u), a0 = Half2Of<FT>::from(-c * u * u);
+        eval_pair_h<FT>(pyA, r0, k.y, nc, a1, a0, r1.y, amax, dyA, ogA, aA);
+        eval_pair_h<FT>(pyB, r0, k.y, nc, a1, a0, r1.y, amax, dyB, ogB, aB);
     } else {
         dyA = __fadd2_rn(pyA, f2(-r0.y));
         float2 e = __ffma2_rn(f2(x.bdx), dyA, f2(x.t0));
@@ -270,7 +291,7 @@ __device__ __forceinline__ void fwd_pair(const float4* rec, float2 a2, bool c0, 
 // A pixel is still compositing while T >= T_eps (T only changes when the
 // pixel takes a step, so this is the "stop once T < T_eps" rule); pixels
 // outside the image start with T = 0.
-template <int C, bool H16, bool NCOUNT>
+template <int C, int FT, bool NCOUNT>
 __global__ void __launch_bounds__(RT, 32) k_raster_fwd(RasterArgs a, float2* __restrict__ U, float* __restrict__ Tsave,
                                                    uint32_t* __restrict__ lastsave, float* __restrict__ Tout,
                                                    int32_t* __restrict__ ncout) {
@@ -305,14 +326,14 @@ __global__ void __launch_bounds__(RT, 32) k_raster_fwd(RasterArgs a, float2* __r
     for (uint32_t p0 = 0; p0 < n; p0 += 32) {
         const bool live = TA.x >= teps || TA.y >= teps || TB.x >= teps || TB.y >= teps;
         if (!__any_sync(0xffffffffu, live)) break;
-        const int nh = stage_warp<NR, H16>(a, vN, beg, p0, n, tx, ty, sx0, sy0, srec, spos, sid, kept + nkept);
+        const int nh = stage_warp<NR, FT>(a, vN, beg, p0, n, tx, ty, sx0, sy0, srec, spos, sid, kept + nkept);
         for (int k = 0; k < nh; k++) {
             const float4* rec = srec[k];
             const float4 r0 = rec[0], r1 = rec[1], kk = rec[NR];
             const uint32_t pos1 = nkept + (uint32_t)k + 1u;  // staged index + 1
             const EntryX x = entry_x(fpx, r0, kk);
             float2 dyA, ogA, aA, dyB, ogB, aB;
-            eval_entry<H16>(x, pyA, pyB, r0, r1, kk, a.amax, dyA, ogA, aA, dyB, ogB, aB);
+            eval_entry<FT>(x, pyA, pyB, r0, r1, kk, a.amax, dyA, ogA, aA, dyB, ogB, aB);
             const bool c0 = TA.x >= teps && aA.x >= a.amin, c1 = TA.y >= teps && aA.y >= a.amin;
             const bool c2 = TB.x >= teps && aB.x >= a.amin, c3 = TB.y >= teps && aB.y >= a.amin;
             fwd_pair<C>(rec, aA, c0, c1, TA, aAX, aAY);
@@ -425,7 +446,7 @@ __device__ __forceinline__ void entry_grads(float4 r0, float4 r1, float dx, floa
 
 // Loads kept entries [lo, lo + cnt) of a strip (Gaussian ids from the forward
 // pass) into the warp's slots: record and base-2 exponent coefficients.
-template <int NR, bool H16>
+template <int NR, int FT>
 __device__ __forceinline__ void stage_kept(const RasterArgs& a, size_t vN, const uint32_t* kept, uint32_t lo, int cnt,
                                            float4 (*wrec)[NR + 1], uint32_t* wid) {
     const int lane = threadIdx.x & 31;
@@ -437,13 +458,13 @@ __device__ __forceinline__ void stage_kept(const RasterArgs& a, size_t vN, const
         wrec[lane][1] = q1;
 #pragma unroll
         for (int k = 2; k < NR; k++) wrec[lane][k] = r[k];
-        wrec[lane][NR] = entry_coeffs<H16>(q0, q1);
+        wrec[lane][NR] = entry_coeffs<FT>(q0, q1);
         wid[lane] = s;
     }
     __syncwarp();
 }
 
-template <int C, bool H16>
+template <int C, int FT>
 __global__ void __launch_bounds__(RT, 24) k_raster_bwd(RasterArgs a, const float* __restrict__ Tsave,
                                                     const uint32_t* __restrict__ lastsave,
                                                     const float2* __restrict__ gU, float* __restrict__ g2d) {
@@ -498,14 +519,14 @@ __global__ void __launch_bounds__(RT, 24) k_raster_bwd(RasterArgs a, const float
     for (uint32_t hi = maxlast; hi > 0;) {
         const uint32_t lo = hi > 32u ? hi - 32u : 0u;
         const int nh = (int)(hi - lo);
-        stage_kept<NR, H16>(a, vN, kept, lo, nh, srec, sid);
+        stage_kept<NR, FT>(a, vN, kept, lo, nh, srec, sid);
         for (int k = nh - 1; k >= 0; k--) {  // back-to-front over the visiting order
             const float4* rec = srec[k];
             const uint32_t pos = lo + (uint32_t)k;
             const float4 r0 = rec[0], r1 = rec[1], kk = rec[NR];
             const EntryX x = entry_x(fpx, r0, kk);
             float2 dyA, ogA, aA, dyB, ogB, aB;
-            eval_entry<H16>(x, pyA, pyB, r0, r1, kk, a.amax, dyA, ogA, aA, dyB, ogB, aB);
+            eval_entry<FT>(x, pyA, pyB, r0, r1, kk, a.amax, dyA, ogA, aA, dyB, ogB, aB);
             const bool c0 = pos < last[0] && aA.x >= a.amin, c1 = pos < last[1] && aA.y >= a.amin;
             const bool c2 = pos < last[2] && aB.x >= a.amin, c3 = pos < last[3] && aB.y >= a.amin;
             // no pixel of the strip took this step: zero gradient, T and B unchanged
@@ -560,7 +581,7 @@ __global__ void __launch_bounds__(RT, 24) k_raster_bwd(RasterArgs a, const float
 // all-plane list in visiting order, advancing T and the prefix on plane-l
 // entries and reducing the others' terms over the strip into drho[n][l].
 // ---------------------------------------------------------------------------
-template <int C, bool H16>
+template <int C, int FT>
 __global__ void __launch_bounds__(RT) k_raster_rho_dense(RasterArgs a, const uint32_t* __restrict__ aoff,
                                                          const uint32_t* __restrict__ alist,
                                                          const int* __restrict__ planes,
@@ -594,13 +615,13 @@ __global__ void __launch_bounds__(RT) k_raster_rho_dense(RasterArgs a, const uin
         for (uint32_t p0 = 0; p0 < n; p0 += 32) {
             const bool live = TA.x >= teps || TA.y >= teps || TB.x >= teps || TB.y >= teps;
             if (!__any_sync(0xffffffffu, live)) break;
-            const int nh = stage_warp<NR, H16>(a, vN, beg, p0, n, tx, ty, sx0, sy0, srec, spos, sid, skept);
+            const int nh = stage_warp<NR, FT>(a, vN, beg, p0, n, tx, ty, sx0, sy0, srec, spos, sid, skept);
             for (int k = 0; k < nh; k++) {
                 const float4* rec = srec[k];
                 const float4 r0 = rec[0], r1 = rec[1], kk = rec[NR];
                 const EntryX x = entry_x(fpx, r0, kk);
                 float2 dyA, ogA, aA, dyB, ogB, aB;
-                eval_entry<H16>(x, pyA, pyB, r0, r1, kk, a.amax, dyA, ogA, aA, dyB, ogB, aB);
+                eval_entry<FT>(x, pyA, pyB, r0, r1, kk, a.amax, dyA, ogA, aA, dyB, ogB, aB);
                 const bool c0 = TA.x >= teps && aA.x >= a.amin, c1 = TA.y >= teps && aA.y >= a.amin;
                 const bool c2 = TB.x >= teps && aB.x >= a.amin, c3 = TB.y >= teps && aB.y >= a.amin;
                 fwd_pair<C>(rec, aA, c0, c1, TA, uAX, uAY);
@@ -632,7 +653,7 @@ __global__ void __launch_bounds__(RT) k_raster_rho_dense(RasterArgs a, const uin
     for (uint32_t p0 = 0; p0 < n; p0 += 32) {
         const bool live = TA.x >= teps || TA.y >= teps || TB.x >= teps || TB.y >= teps;
         if (!__any_sync(0xffffffffu, live)) break;
-        const int nh = stage_warp<NR, H16>(aa, vN, beg, p0, n, tx, ty, sx0, sy0, srec, spos, sid, skept);
+        const int nh = stage_warp<NR, FT>(aa, vN, beg, p0, n, tx, ty, sx0, sy0, srec, spos, sid, skept);
         for (int k = 0; k < nh; k++) {
             const float4* rec = srec[k];
             const float4 r0 = rec[0], r1 = rec[1], kk = rec[NR];
@@ -640,7 +661,7 @@ __global__ void __launch_bounds__(RT) k_raster_rho_dense(RasterArgs a, const uin
             const bool own = planes[vN + srank] == l;  // warp-uniform
             const EntryX x = entry_x(fpx, r0, kk);
             float2 dyA, ogA, aA, dyB, ogB, aB;
-            eval_entry<H16>(x, pyA, pyB, r0, r1, kk, a.amax, dyA, ogA, aA, dyB, ogB, aB);
+            eval_entry<FT>(x, pyA, pyB, r0, r1, kk, a.amax, dyA, ogA, aA, dyB, ogB, aB);
             const bool c0 = TA.x >= teps && aA.x >= a.amin, c1 = TA.y >= teps && aA.y >= a.amin;
             const bool c2 = TB.x >= teps && aB.x >= a.amin, c3 = TB.y >= teps && aB.y >= a.amin;
             if (own) {
@@ -686,14 +707,19 @@ hcgs_status raster_forward(hcgs_ctx* ctx, hcgs_saved* s, float2* U, float* T_out
     dim3 grid(s->tilesX * s->tilesY * 2, s->L, s->V);  // 16 x 8 pixel strips
     float* Ts = (float*)s->Tfin.p;
     uint32_t* ls = (uint32_t*)s->last.p;
-    const bool h16 = s->opts.footprint == 1;
-#define HCGS_FWD(CC)                                                                                       \
-    if (nc_out) {                                                                                          \
-        if (h16) HCGS_KERNEL(ctx, "k_raster_fwd", st, k_raster_fwd<CC, true, true><<<grid, RT, 0, st>>>(a, U, Ts, ls, T_out, nc_out)); \
-        else HCGS_KERNEL(ctx, "k_raster_fwd", st, k_raster_fwd<CC, false, true><<<grid, RT, 0, st>>>(a, U, Ts, ls, T_out, nc_out)); \
-    } else {                                                                                               \
-        if (h16) HCGS_KERNEL(ctx, "k_raster_fwd", st, k_raster_fwd<CC, true, false><<<grid, RT, 0, st>>>(a, U, Ts, ls, T_out, nc_out)); \
-        else HCGS_KERNEL(ctx, "k_raster_fwd", st, k_raster_fwd<CC, false, false><<<grid, RT, 0, st>>>(a, U, Ts, ls, T_out, nc_out)); \
+    const int ft = s->opts.footprint;
+#define HCGS_FWD_T(CC, FTV)                                                                                                 \
+    if (nc_out)                                                                                                             \
+        HCGS_KERNEL(ctx, "k_raster_fwd", st, (k_raster_fwd<CC, FTV, true><<<grid, RT, 0, st>>>(a, U, Ts, ls, T_out, nc_out)));  \
+    else                                                                                                                    \
+        HCGS_KERNEL(ctx, "k_raster_fwd", st, (k_raster_fwd<CC, FTV, false><<<grid, RT, 0, st>>>(a, U, Ts, ls, T_out, nc_out)))
+#define HCGS_FWD(CC)                          \
+    if (ft == 1) {                            \
+        HCGS_FWD_T(CC, 1);                    \
+    } else if (ft == 2) {                     \
+        HCGS_FWD_T(CC, 2);                    \
+    } else {                                  \
+        HCGS_FWD_T(CC, 0);                    \
     }
     switch (s->C) {
         case 1: HCGS_FWD(1); break;
@@ -702,6 +728,7 @@ hcgs_status raster_forward(hcgs_ctx* ctx, hcgs_saved* s, float2* U, float* T_out
         default: HCGS_FWD(4); break;
     }
 #undef HCGS_FWD
+#undef HCGS_FWD_T
     HCGS_LAUNCH(ctx, "k_raster_fwd");
     return HCGS_OK;
 }
@@ -715,10 +742,14 @@ hcgs_status raster_backward(hcgs_ctx* ctx, hcgs_saved* s, const float2* gU, cuda
     const float* Ts = (const float*)s->Tfin.p;
     const uint32_t* ls = (const uint32_t*)s->last.p;
     float* g2 = (float*)s->g2d.p;
-    const bool h16 = s->opts.footprint == 1;
-#define HCGS_BWD(CC)                                                                                        \
-    if (h16) HCGS_KERNEL(ctx, "k_raster_bwd", st, k_raster_bwd<CC, true><<<grid, RT, 0, st>>>(a, Ts, ls, gU, g2)); \
-    else HCGS_KERNEL(ctx, "k_raster_bwd", st, k_raster_bwd<CC, false><<<grid, RT, 0, st>>>(a, Ts, ls, gU, g2))
+    const int ft = s->opts.footprint;
+#define HCGS_BWD(CC)                                                                                              \
+    if (ft == 1)                                                                                                  \
+        HCGS_KERNEL(ctx, "k_raster_bwd", st, (k_raster_bwd<CC, 1><<<grid, RT, 0, st>>>(a, Ts, ls, gU, g2)));      \
+    else if (ft == 2)                                                                                             \
+        HCGS_KERNEL(ctx, "k_raster_bwd", st, (k_raster_bwd<CC, 2><<<grid, RT, 0, st>>>(a, Ts, ls, gU, g2)));      \
+    else                                                                                                          \
+        HCGS_KERNEL(ctx, "k_raster_bwd", st, (k_raster_bwd<CC, 0><<<grid, RT, 0, st>>>(a, Ts, ls, gU, g2)))
     switch (s->C) {
         case 1: HCGS_BWD(1); break;
         case 2: HCGS_BWD(2); break;
@@ -735,11 +766,16 @@ hcgs_status raster_backward(hcgs_ctx* ctx, hcgs_saved* s, const float2* gU, cuda
         const int* pl = (const int*)s->planes.p;
         const uint32_t* sid = (const uint32_t*)s->sortid.p;
         float* dr = (float*)s->drho.p;
-#define HCGS_DENSE(CC)                                                                                           \
-    if (h16) HCGS_KERNEL(ctx, "k_raster_rho_dense", st,                                                        \
-                         (k_raster_rho_dense<CC, true><<<grid, RT, 0, st>>>(a, aoff, s->alist, pl, sid, gU, dr))); \
-    else HCGS_KERNEL(ctx, "k_raster_rho_dense", st,                                                            \
-                     (k_raster_rho_dense<CC, false><<<grid, RT, 0, st>>>(a, aoff, s->alist, pl, sid, gU, dr)))
+#define HCGS_DENSE(CC)                                                                                            \
+    if (ft == 1)                                                                                                  \
+        HCGS_KERNEL(ctx, "k_raster_rho_dense", st,                                                                \
+                    (k_raster_rho_dense<CC, 1><<<grid, RT, 0, st>>>(a, aoff, s->alist, pl, sid, gU, dr)));        \
+    else if (ft == 2)                                                                                             \
+        HCGS_KERNEL(ctx, "k_raster_rho_dense", st,                                                                \
+                    (k_raster_rho_dense<CC, 2><<<grid, RT, 0, st>>>(a, aoff, s->alist, pl, sid, gU, dr)));        \
+    else                                                                                                          \
+        HCGS_KERNEL(ctx, "k_raster_rho_dense", st,                                                                \
+                    (k_raster_rho_dense<CC, 0><<<grid, RT, 0, st>>>(a, aoff, s->alist, pl, sid, gU, dr)))
         switch (s->C) {
             case 1: HCGS_DENSE(1); break;
             case 2: HCGS_DENSE(2); break;

@@ -135,26 +135,27 @@ def test_render_rgb_multiview(P, ctx, order):
     assert rel(hp, Po) < 1e-4, rel(hp, Po)
 
 
-@pytest.mark.parametrize("order", [0, 1])
-def test_render_fp16_footprint_tier(P, ctx, order):
-    # reduced-precision tier: footprint exponent and exp in FP16x2, FP32
-    # accumulation; relative L2 against the FP64 oracle <= 1e-2
+@pytest.mark.parametrize("order,footprint", [(0, 1), (1, 1), (0, 2), (1, 2)])
+def test_render_fp16_footprint_tier(P, ctx, order, footprint):
+    # reduced-precision tiers: footprint exponent and exp in FP16x2 (1) or
+    # BF16x2 (2), FP32 accumulation; relative L2 against the FP64 oracle <= 1e-2
     o = S.Optics(120, 200, S.WAVELENGTHS_RGB, (0.0, 2e-3, 5e-3, 9e-3))
     g = S.make_gaussians(3000, o.L, o.C, o.H, o.W, seed=4, log_scale_mean=-3.5)
-    opts = dict(P.DEFAULT_OPTS, order=order, footprint=1)
+    opts = dict(P.DEFAULT_OPTS, order=order, footprint=footprint)
     hp, Ug, Po, Uo, To, No, _, _ = _render_both(P, ctx, g, o, 2, opts, seed=3)
     eU, eP = rel(Ug, Uo), rel(hp, Po)
-    print("FP16 tier rel L2: U %.3e  P %.3e" % (eU, eP))
+    print("footprint tier %d rel L2: U %.3e  P %.3e" % (footprint, eU, eP))
     assert eU < 1e-2 and eP < 1e-2
 
 
-def test_render_fp16_tier_c2_full_size(P, ctx):
+@pytest.mark.parametrize("footprint", [1, 2])
+def test_render_fp16_tier_c2_full_size(P, ctx, footprint):
     wl = S.workload("c2_1080p_L8_N100k")
     o = wl.optics
     g = S.make_gaussians(wl.N, o.L, o.C, o.H, o.W, seed=0)
-    hp, Ug, Po, Uo, To, No, _, _ = _render_both(P, ctx, g, o, 1, dict(P.DEFAULT_OPTS, footprint=1))
+    hp, Ug, Po, Uo, To, No, _, _ = _render_both(P, ctx, g, o, 1, dict(P.DEFAULT_OPTS, footprint=footprint))
     eU, eP = rel(Ug, Uo), rel(hp, Po)
-    print("c2 FP16 tier rel L2: U %.3e  P %.3e" % (eU, eP))
+    print("c2 footprint tier %d rel L2: U %.3e  P %.3e" % (footprint, eU, eP))
     assert eU < 1e-2 and eP < 1e-2
 
 
@@ -201,15 +202,15 @@ def test_render_c2_full_size_forward(P, ctx):
 # ---------------------------------------------------------------------------
 # gradients
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("opts_name,order", [("default", 0), ("default", 1), ("exact", 0), ("fp16", 0)])
+@pytest.mark.parametrize("opts_name,order", [("default", 0), ("default", 1), ("exact", 0), ("fp16", 0), ("bf16", 0)])
 def test_render_backward_vs_oracle(P, ctx, opts_name, order):
     o = S.Optics(48, 80, (639e-9, 473e-9), (0.0, 3e-3, 7e-3))
     g = S.make_gaussians(300, o.L, o.C, o.H, o.W, seed=7, log_scale_mean=-2.8, log_scale_std=0.4)
     g["means"][:, 2] += 0.5
     base = {"default": P.DEFAULT_OPTS, "exact": P.EXACT_OPTS,
-            "fp16": dict(P.DEFAULT_OPTS, footprint=1)}[opts_name]
+            "fp16": dict(P.DEFAULT_OPTS, footprint=1), "bf16": dict(P.DEFAULT_OPTS, footprint=2)}[opts_name]
     opts = dict(base, order=order)
-    tol = 2e-2 if opts_name == "fp16" else 1e-3
+    tol = 2e-2 if opts_name in ("fp16", "bf16") else 1e-3
     V = 2
     vm, it = cams(V, o.H, o.W, seed=2)
     gd = dev(g)
