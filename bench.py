@@ -438,29 +438,62 @@ def run_ours(args):
     h2d = sum(t.numel() * t.element_size() for t in list(h_in.values()) + [h_vm, h_it, h_gP])
     d2h = sum(t.numel() * t.element_size() for t in h_out.values())
 
-    # The upstream gradient dL/dP (the bulk of the input bytes) travels on a
-    # second stream while the forward pass runs; the adjoint waits for it.
-    # The copy of step k+1 starts only after step k's adjoint has read gP.
-    copy_stream = torch.cuda.Stream(device=dev)
-    gP_ready = torch.cuda.Event()
+    # Double-buffered: step k computes on input/output set k % 2.  At its start
+    # a copy stream brings step k + 1's inputs into the other set (free once
+    # step k - 1 is done), and after it the same stream returns step k's
+    # gradients, so the transfers overlap the neighbouring steps' compute.
+    # Every timed step makes one full host->device copy of a step's inputs
+    # and one device->host copy of its result.
+    cs = torch.cuda.Stream(device=dev)
+    sets = [dict(g=g, vm=vm, it=it, gP=gP, grads=grads),
+            dict(g={k: torch.empty_like(g[k]) for k in P.PARAM_NAMES}, vm=torch.empty_like(vm),
+                 it=torch.empty_like(it), gP=torch.empty_like(gP),
+                 grads={k: torch.empty_like(g[k]) for k in P.PARAM_NAMES})]
+    in_ready = [torch.cuda.Event(), torch.cuda.Event()]
+    done = [torch.cuda.Event(), torch.cuda.Event()]
+
+    def load(b):
+        with torch.cuda.stream(cs):
+            cs.wait_event(done[b])
+            sb = sets[b]
+            for k in P.PARAM_NAMES:
+                sb["g"][k].copy_(h_in[k], non_blocking=True)
+            sb["vm"].copy_(h_vm, non_blocking=True)
+            sb["it"].copy_(h_it, non_blocking=True)
+            sb["gP"].copy_(h_gP, non_blocking=True)
+            in_ready[b].record(cs)
+
+    counter = [0]
 
     def e2e_step():
-        for k in P.PARAM_NAMES:
-            g[k].copy_(h_in[k], non_blocking=True)
-        vm.copy_(h_vm, non_blocking=True)
-        it.copy_(h_it, non_blocking=True)
-        copy_stream.wait_stream(stream)
-        with torch.cuda.stream(copy_stream):
-            gP.copy_(h_gP, non_blocking=True)
-            gP_ready.record(copy_stream)
-        fwd()
-        stream.wait_event(gP_ready)
-        ctx.render_view_backward(saved, g, gP, grads)
-        for k in P.PARAM_NAMES:
-            h_out[k].copy_(grads[k], non_blocking=True)
+        b = counter[0] % 2
+        counter[0] += 1
+        load(1 - b)  # the inputs of the next step
+        sb = sets[b]
+        stream.wait_event(in_ready[b])
+        ctx.render_view(sb["g"], sb["vm"], sb["it"], o, opts, holo, None, saved)
+        ctx.render_view_backward(saved, sb["g"], sb["gP"], sb["grads"])
+        done[b].record(stream)
+        with torch.cuda.stream(cs):
+            cs.wait_event(done[b])
+            for k in P.PARAM_NAMES:
+                h_out[k].copy_(sb["grads"][k], non_blocking=True)
 
-    e2e_step()
-    ms_e2e = timed(e2e_step, args.steps)
+    load(0)
+    for _ in range(2):
+        e2e_step()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    stream.wait_stream(cs)  # the last step's gradients are on the host
+    e1.record(stream)
+    e1.synchronize()
+    barrier()
+    ms_e2e = max_over_ranks(e0.elapsed_time(e1) / args.steps, dev)
+    torch.cuda.synchronize()
+    del sets[1]
 
     # --- the other configurations: forward and forward + adjoint rates ---
     configs = None
