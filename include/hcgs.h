@@ -18,7 +18,7 @@
  * hcgs_render_view runs all four.  Every step has a _backward twin (Supp.
  * D.4, Eq. ste).  The training-step pieces are hcgs_focal_stack_loss
  * (Eq. plane2layer_asm, Eq. recon_loss) and hcgs_adam_step, and the paper's
- * own recipe: hcgs_paper_loss (L_recon + L_SSIM, Sec. 3) and hcgs_adan_step
+ * own recipe: hcgs_paper_loss (L_recon + L_SSIM, Sec. 4.1) and hcgs_adan_step
  * (Sec. 5); Algorithm 1's densification is hcgs_densify_accumulate / _plan /
  * _apply with hcgs_philox for its noise; the phase-only conversion of Sec. 6
  * is hcgs_phase_only_loss; the learned initialisation network is
@@ -265,7 +265,7 @@ hcgs_status hcgs_render_view_backward(hcgs_ctx* ctx, hcgs_saved* saved, const hc
 hcgs_status hcgs_focal_stack_loss(hcgs_ctx* ctx, const float* hologram, const float* I_gt, int B,
                                   const hcgs_optics* optics, float* loss, float* g_hologram,
                                   float* I_out, void* stream);
-/* The paper's training objective on one batch of views (Sec. 3, loss):
+/* The paper's training objective on one batch of views (Sec. 4.1, loss):
  * the focal stack I_l = |V_l|^2, V_l = ASM(P, -z_l) (Eq. plane2layer_asm),
  * against the targets, with L = L_recon + L_SSIM averaged over views:
  *   L_recon = mean over (b, l, c, pixel) of d^2 (1 + M + I_gt^2), d = I - I_gt
@@ -410,9 +410,9 @@ hcgs_status hcgs_scale(hcgs_ctx* ctx, const float* x, int64_t n, float s, float*
  * complex64 (the phase-only hologram an SLM displays). */
 hcgs_status hcgs_phase_hologram(hcgs_ctx* ctx, const float* phase, int64_t n, float* hologram, void* stream);
 
-/* ---------------- densification (Algorithm 1, Supp. C) ---------------- */
+/* ---------------- densification (Algorithm 1, Supp. D.2) ---------------- */
 /* The 3DGS densification rules that Sec. 5 adopts (period: 300 steps),
- * with phase-aware copies (Supp. C: copies and children get a small random
+ * with phase-aware copies (Supp. D.2: copies and children get a small random
  * phase perturbation). */
 typedef struct {
     float grad_threshold; /* densify when the mean NDC gradient norm of the 2D mean >= this (2e-4) */

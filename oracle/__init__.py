@@ -363,7 +363,7 @@ def focal_stack_loss(P: np.ndarray, I_gt: np.ndarray, pitch: float, wavelengths,
 
 
 # ----------------------------------------------------------------------------
-# the paper's training objective (Sec. 3 loss paragraph): L = L_recon + L_SSIM
+# the paper's training objective (Sec. 4.1 loss paragraph): L = L_recon + L_SSIM
 # ----------------------------------------------------------------------------
 SSIM_SIZE = 11          # Gaussian window, standard deviation 1.5 (structural similarity of Wang et al.)
 SSIM_SIGMA = 1.5

@@ -132,7 +132,7 @@ _sig("hcgs_init_targets", [_P, _P, _P, c_int, c_int, _P, _P])
 _sig("hcgs_init_apply", [_P, _P, c_int, c_int, _P, _P, _P])
 _sig("hcgs_mlp_backward", [_P, _P, c_int] + [_P] * 8 + [_P] + [_P] * 8 + [_P])
 
-SSIM_LAMBDA = 0.005  # lambda_1 of the SSIM term (Sec. 3, loss)
+SSIM_LAMBDA = 0.005  # lambda_1 of the SSIM term (Sec. 4.1, loss paragraph)
 # densification (Algorithm 1; the 3DGS rules Sec. 5 adopts); split_scale is
 # scene-dependent (3DGS: 1 % of the scene extent; 0.02 m for the 1-3 m scenes here)
 DEFAULT_DENSIFY = dict(grad_threshold=2e-4, split_scale=0.02, prune_opacity=5e-3, prune_scale=0.0,

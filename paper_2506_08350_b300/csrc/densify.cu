@@ -1,4 +1,4 @@
-// Densification of Algorithm 1 (Supp. C): statistics of the screen-space mean
+// Densification of Algorithm 1 (Supp. D.2): statistics of the screen-space mean
 // gradient, the per-Gaussian decision (prune / keep / clone / split), and the
 // compaction that writes the new parameter arrays with phase-aware copies;
 // plus the counter-based generator (Philox4x32-10, Salmon et al. 2011) that

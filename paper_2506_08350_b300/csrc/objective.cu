@@ -1,5 +1,5 @@
 // The paper's training objective on sm_103a: L = L_recon + L_SSIM on the
-// focal stack (the loss paragraph of Sec. 3), and the Adan optimiser step
+// focal stack (the loss paragraph of Sec. 4.1), and the Adan optimiser step
 // (Sec. 5, implementation).
 //
 //   L_recon = mean over (view, plane, channel, pixel) of d^2 (1 + M + I_gt^2),

@@ -6,7 +6,7 @@ intensities with the focal-stack targets, run the adjoint
 (hcgs_render_view_backward) and update every parameter array.  Two objectives:
 "mse", the plain focal-stack loss (hcgs_focal_stack_loss: Eq. plane2layer_asm
 and Eq. recon_loss as a mean), and "paper", L_recon + L_SSIM with the plane
-masks (hcgs_paper_loss, Sec. 3); two optimisers: Adam (hcgs_adam_step) and
+masks (hcgs_paper_loss, Sec. 4.1); two optimisers: Adam (hcgs_adam_step) and
 Adan (hcgs_adan_step, the optimiser of Sec. 5), optionally with cosine
 annealing of the means' and plane logits' learning rates (minimum 1e-5).
 All arithmetic runs in the library's kernels; this module only sequences the

@@ -1,6 +1,6 @@
 """Pins for the oracle's version of the paper's training objective.
 
-L = L_recon + L_SSIM (the loss paragraph of Sec. 3), the Adan optimiser and
+L = L_recon + L_SSIM (the loss paragraph of Sec. 4.1), the Adan optimiser and
 the cosine learning-rate schedule (Sec. 5, implementation).  Each check rests
 on something other than the oracle's own formula: a brute-force window sum,
 finite differences, reduction to the plain focal-stack loss, and properties
