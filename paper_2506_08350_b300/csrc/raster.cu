@@ -547,17 +547,15 @@ __global__ void __launch_bounds__(RT, 24) k_raster_bwd(RasterArgs a, const float
                 for (int e = 0; e < G; e++) red[e * RS + lane] = gv[e];
                 __syncwarp();
                 const int e = lane >> 1, h = lane & 1;
-                float sum = 0.f;
-                if (e < G) {
-                    const float4* row = reinterpret_cast<const float4*>(red + e * RS + 16 * h);
-                    const float4 u0 = row[0], u1 = row[1], u2 = row[2], u3 = row[3];
-                    const float2 s0 = __fadd2_rn(make_float2(u0.x, u0.y), make_float2(u0.z, u0.w));
-                    const float2 s1 = __fadd2_rn(make_float2(u1.x, u1.y), make_float2(u1.z, u1.w));
-                    const float2 s2 = __fadd2_rn(make_float2(u2.x, u2.y), make_float2(u2.z, u2.w));
-                    const float2 s3 = __fadd2_rn(make_float2(u3.x, u3.y), make_float2(u3.z, u3.w));
-                    const float2 s4 = __fadd2_rn(__fadd2_rn(s0, s1), __fadd2_rn(s2, s3));
-                    sum = s4.x + s4.y;
-                }
+                // lanes past the last row read it again (branch-free) and discard
+                const float4* row = reinterpret_cast<const float4*>(red + (e < G ? e : G - 1) * RS + 16 * h);
+                const float4 u0 = row[0], u1 = row[1], u2 = row[2], u3 = row[3];
+                const float2 s0 = __fadd2_rn(make_float2(u0.x, u0.y), make_float2(u0.z, u0.w));
+                const float2 s1 = __fadd2_rn(make_float2(u1.x, u1.y), make_float2(u1.z, u1.w));
+                const float2 s2 = __fadd2_rn(make_float2(u2.x, u2.y), make_float2(u2.z, u2.w));
+                const float2 s3 = __fadd2_rn(make_float2(u3.x, u3.y), make_float2(u3.z, u3.w));
+                const float2 s4 = __fadd2_rn(__fadd2_rn(s0, s1), __fadd2_rn(s2, s3));
+                float sum = s4.x + s4.y;
                 sum += __shfl_xor_sync(0xffffffffu, sum, 1);
                 // slot 5 holds o dL/do (the projection adjoint needs no more)
                 if (!h && e < G) atomicAdd(g2d + (vN + sid[k]) * G + e, sum);
