@@ -26,6 +26,9 @@
 // asynchronous copies when rows are 16-byte aligned in memory (W a multiple
 // of 4) and the horizontal pass reads it with 16-byte loads (eight lanes of a
 // row cover all banks).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <cmath>
 
 #include "common.cuh"
@@ -242,6 +245,42 @@ __device__ __forceinline__ void cp_async_n(void* dst, const void* src, bool ok, 
         cp_async4(dst, src, ok);
 }
 
+// ---- tensor-memory-access (TMA) halo tiles (16-byte aligned rows) ----
+// A box of SS_XW x SS_EH elements at (x, y) of image z lands in a dense
+// shared tile [SS_EH][SS_XW] (the layout of the copies above); elements
+// outside the image arrive as zeros (the window's zero continuation).
+struct SsimMaps {
+    CUtensorMap a, b;  // pass 1: intensities (or field) and targets; pass 2: the three maps (a)
+};
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* m, int x, int y, int z, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(m)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* m, int x, int y, int z, int w,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(m)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Waits (bounded) for the tile copies (the barrier initialised and the copies
+// issued before a block barrier); on a timeout waits once more for the copies
+// in flight, records it in the status word and tells the CTA to leave.
+__device__ __forceinline__ bool tma_tiles_ready(uint64_t* bar, int* status) {
+    const bool ok = __syncthreads_and(mbar_wait(bar, 0));
+    if (!ok && threadIdx.x == 0) {
+        mbar_wait(bar, 0);
+        atomicOr(status, STATUS_WAIT_TIMEOUT);
+    }
+    return ok;
+}
+
 // Pass 1 over each (view, plane, channel) image: the partial derivatives of
 // the SSIM map dS/dmx, dS/dm2, dS/dmxy (to dmap[3][n]) and the block's part of
 // sum (d^2 w + lambda (1 - S)).  The intensities come either from I or, when
@@ -251,10 +290,11 @@ template <bool FROM_FIELD, bool VEC>
 __global__ void __launch_bounds__(SS_NT)
     k_ssim_partials(const float2* __restrict__ V, float* __restrict__ I, const float* __restrict__ Igt,
                     const float* __restrict__ M, int C, int H, int W, float lam, int plain, float* __restrict__ dmap,
-                    float* __restrict__ partials) {
-    __shared__ __align__(16) float inp[2][SS_EH][SS_XW];
-    __shared__ __align__(16) float2 h[2][SS_EH][SS_TW];
+                    float* __restrict__ partials, const __grid_constant__ SsimMaps maps, int* status) {
+    __shared__ __align__(128) float inp[2][SS_EH][SS_XW];
+    __shared__ __align__(128) float2 h[2][SS_EH][SS_TW];
     __shared__ float red[SS_NT / 32];
+    __shared__ __align__(8) uint64_t bar;
     const int img = blockIdx.z;
     const size_t HW = (size_t)H * W, n = (size_t)gridDim.z * HW;
     const int xs = blockIdx.x * SS_TW - SS_R - SS_XO, y0 = blockIdx.y * SS_TH - SS_R;
@@ -264,14 +304,27 @@ __global__ void __launch_bounds__(SS_NT)
     // the field's halo is staged in the row-sum buffer (idle until the row pass)
     float2 (*stage)[SS_XW] = reinterpret_cast<float2 (*)[SS_XW]>(&h[0][0][0]);
     static_assert(sizeof(float2) * SS_EH * SS_XW <= sizeof(h), "staging fits");
-    halo_copy<VEC, 4>(xs, y0, H, W, [&](int r, int c, unsigned off, bool ok, int bytes) {
-        cp_async_n(&inp[1][r][c], ysrc + off, ok, bytes);
-        if constexpr (!FROM_FIELD) cp_async_n(&inp[0][r][c], xsrc + off, ok, bytes);
-    });
-    if constexpr (FROM_FIELD)
-        halo_copy<VEC, 8>(xs, y0, H, W, [&](int r, int c, unsigned off, bool ok, int bytes) {
-            cp_async_n(&stage[r][c], vsrc + off, ok, bytes);
+    if constexpr (VEC) {
+        // two tensor copies by one thread, completed on the barrier
+        if (threadIdx.x == 0) {
+            mbar_init(&bar, 1);
+            mbar_init_fence();
+            constexpr unsigned bytes = SS_EH * SS_XW * (sizeof(float) + (FROM_FIELD ? sizeof(float2) : sizeof(float)));
+            mbar_expect_tx(&bar, bytes);
+            tma_load_3d(&inp[1][0][0], &maps.b, xs, y0, img, &bar);
+            tma_load_3d(FROM_FIELD ? (void*)&stage[0][0] : (void*)&inp[0][0][0], &maps.a, xs, y0, img, &bar);
+        }
+        __syncthreads();  // the barrier is initialised before anyone waits on it
+    } else {
+        halo_copy<VEC, 4>(xs, y0, H, W, [&](int r, int c, unsigned off, bool ok, int bytes) {
+            cp_async_n(&inp[1][r][c], ysrc + off, ok, bytes);
+            if constexpr (!FROM_FIELD) cp_async_n(&inp[0][r][c], xsrc + off, ok, bytes);
         });
+        if constexpr (FROM_FIELD)
+            halo_copy<VEC, 8>(xs, y0, H, W, [&](int r, int c, unsigned off, bool ok, int bytes) {
+                cp_async_n(&stage[r][c], vsrc + off, ok, bytes);
+            });
+    }
     // the mask values of the thread's outputs, needed in the epilogue
     const int col = threadIdx.x & 31, row0 = (threadIdx.x >> 5) * SS_ROWS;
     const float* m = M ? M + (size_t)(img / C) * HW : nullptr;  // masks per (view, plane)
@@ -282,8 +335,12 @@ __global__ void __launch_bounds__(SS_NT)
         const int gy = blockIdx.y * SS_TH + row0 + k;
         mv[k] = (m && gx < W && gy < H) ? m[(size_t)gy * W + gx] : 0.f;
     }
-    cp_async_wait_all();
-    __syncthreads();
+    if constexpr (VEC) {
+        if (!tma_tiles_ready(&bar, status)) return;
+    } else {
+        cp_async_wait_all();
+        __syncthreads();
+    }
     if constexpr (FROM_FIELD) {
         const int lane = threadIdx.x & 31;
         for (int r = threadIdx.x >> 5; r < SS_EH; r += SS_NT / 32) {
@@ -339,21 +396,33 @@ template <bool TO_FIELD, bool VEC>
 __global__ void __launch_bounds__(SS_NT)
     k_ssim_grad(const float* __restrict__ I, const float* __restrict__ Igt, const float* __restrict__ M, int C,
                 int H, int W, float lam, int plain, float inv_n, const float* __restrict__ dmap,
-                float* __restrict__ gI, float2* __restrict__ V) {
-    __shared__ __align__(16) float inp[3][SS_EH][SS_XW];
+                float* __restrict__ gI, float2* __restrict__ V, const __grid_constant__ SsimMaps maps, int* status) {
+    __shared__ __align__(128) float inp[3][SS_EH][SS_XW];
     __shared__ __align__(16) float2 h2[1][SS_EH][SS_TW];
     __shared__ __align__(16) float h1[1][SS_EH][SS_TW];
+    __shared__ __align__(8) uint64_t bar;
     const int img = blockIdx.z;
     const size_t HW = (size_t)H * W, n = (size_t)gridDim.z * HW;
     const int xs = blockIdx.x * SS_TW - SS_R - SS_XO, y0 = blockIdx.y * SS_TH - SS_R;
     const float* d0 = dmap + (size_t)img * HW;
     const float* d1 = d0 + n;
     const float* d2 = d1 + n;
-    halo_copy<VEC, 4>(xs, y0, H, W, [&](int r, int c, unsigned off, bool ok, int bytes) {
-        cp_async_n(&inp[0][r][c], d0 + off, ok, bytes);
-        cp_async_n(&inp[1][r][c], d1 + off, ok, bytes);
-        cp_async_n(&inp[2][r][c], d2 + off, ok, bytes);
-    });
+    if constexpr (VEC) {
+        if (threadIdx.x == 0) {
+            mbar_init(&bar, 1);
+            mbar_init_fence();
+            mbar_expect_tx(&bar, 3 * SS_EH * SS_XW * sizeof(float));
+#pragma unroll
+            for (int q = 0; q < 3; q++) tma_load_4d(&inp[q][0][0], &maps.a, xs, y0, img, q, &bar);
+        }
+        __syncthreads();  // the barrier is initialised before anyone waits on it
+    } else {
+        halo_copy<VEC, 4>(xs, y0, H, W, [&](int r, int c, unsigned off, bool ok, int bytes) {
+            cp_async_n(&inp[0][r][c], d0 + off, ok, bytes);
+            cp_async_n(&inp[1][r][c], d1 + off, ok, bytes);
+            cp_async_n(&inp[2][r][c], d2 + off, ok, bytes);
+        });
+    }
     // the thread's own I, I_gt, M for the epilogue, loaded meanwhile
     const int col = threadIdx.x & 31, row0 = (threadIdx.x >> 5) * SS_ROWS;
     const float* m = M ? M + (size_t)(img / C) * HW : nullptr;
@@ -370,8 +439,12 @@ __global__ void __launch_bounds__(SS_NT)
         mv[k] = (m && in) ? m[(size_t)gy * W + gx] : 0.f;
         if constexpr (TO_FIELD) vo[k] = in ? V[p] : make_float2(0.f, 0.f);
     }
-    cp_async_wait_all();
-    __syncthreads();
+    if constexpr (VEC) {
+        if (!tma_tiles_ready(&bar, status)) return;
+    } else {
+        cp_async_wait_all();
+        __syncthreads();
+    }
     ssim_rows<3, 1, 1>(inp, h2, h1, [](const float (&a)[3], float2 (&v2)[1], float (&v1)[1]) {
         v2[0] = make_float2(a[0], a[1]);
         v1[0] = a[2];
@@ -397,6 +470,34 @@ __global__ void __launch_bounds__(SS_NT)
     }
 }
 
+// Tensor map of `planes` stacked images of H x W elements (es = 4 or 8 bytes)
+// at `base`: dims (W, H, nimg[, planes]), box SS_XW x SS_EH, zeros outside.
+// Rows must be 16-byte aligned (W es a multiple of 16).  The driver's encoder
+// is looked up once through the runtime.
+static bool encode_halo_map(CUtensorMap* m, const void* base, int es, int W, int H, uint64_t nimg, int planes) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        looked = true;
+        cudaDriverEntryPointQueryResult q;
+        void* fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+    if (!encode) return false;
+    const int rank = planes > 1 ? 4 : 3;
+    const cuuint64_t dims[4] = {(cuuint64_t)W, (cuuint64_t)H, nimg, (cuuint64_t)planes};
+    const cuuint64_t strides[3] = {(cuuint64_t)W * es, (cuuint64_t)H * W * es, nimg * H * W * es};
+    const cuuint32_t box[4] = {SS_XW, SS_EH, 1, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    return encode(m, es == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank,
+                  const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // Loss partials and gradient of L_recon + L_SSIM for B L C images of H x W.
 // V != nullptr: intensities |V|^2 (written to I), gradient dL/dV over V;
 // otherwise intensities read from I and dL/dI written to gI.  plain = 1: the
@@ -411,16 +512,25 @@ hcgs_status ssim_recon_loss(hcgs_ctx* ctx, float2* V, float* I, const float* Igt
     HCGS_CUDA(ctx, ssim_window_upload());
     const int blk = SS_NT;
     const float inv_n = (float)(1.0 / ((double)B * L * C * H * W));
-    // 16-byte copies need 16-byte aligned rows: W a multiple of 4 and aligned bases
+    // tensor copies need 16-byte aligned rows: W a multiple of 4 and aligned bases
     auto al = [](const void* q) { return q == nullptr || ((uintptr_t)q & 15) == 0; };
-    const bool vec = W % 4 == 0 && al(V) && al(I) && al(Igt) && al(dmap);
+    bool vec = W % 4 == 0 && al(V) && al(I) && al(Igt) && al(dmap);
+    SsimMaps m1{}, m2{};
+    if (vec) {
+        const uint64_t nimg = (uint64_t)B * L * C;
+        const bool ok = encode_halo_map(&m1.a, V ? (const void*)V : (const void*)I, V ? 8 : 4, W, H, nimg, 1) &&
+                        encode_halo_map(&m1.b, Igt, 4, W, H, nimg, 1) && encode_halo_map(&m2.a, dmap, 4, W, H, nimg, 3);
+        if (!ok) vec = false;  // driver without the entry point: element copies
+    }
 #define HCGS_SSIM_LAUNCH(F, VEC)                                                                              \
     do {                                                                                                      \
         HCGS_KERNEL(ctx, "k_ssim_partials", st,                                                               \
-                    (k_ssim_partials<F, VEC><<<grid, blk, 0, st>>>(V, I, Igt, M, C, H, W, lam, plain, dmap, partials))); \
+                    (k_ssim_partials<F, VEC><<<grid, blk, 0, st>>>(V, I, Igt, M, C, H, W, lam, plain, dmap, partials, \
+                                                                   m1, ctx->d_status)));                      \
         HCGS_KERNEL(ctx, "k_ssim_grad", st,                                                                   \
                     (k_ssim_grad<F, VEC><<<grid, blk, 0, st>>>(I, Igt, M, C, H, W, lam, plain, inv_n, dmap,     \
-                                                               F ? nullptr : gI, F ? V : nullptr)));          \
+                                                               F ? nullptr : gI, F ? V : nullptr, m2,         \
+                                                               ctx->d_status)));                              \
     } while (0)
     if (V && vec)
         HCGS_SSIM_LAUNCH(true, true);
