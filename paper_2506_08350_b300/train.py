@@ -136,6 +136,52 @@ class HologramTrainer:
             self.densify()
         return self.loss
 
+    # ---- checkpoint / resume ----
+    STATE_KEYS = ("m", "v", "n", "g_prev")
+
+    def state_dict(self) -> dict:
+        """Everything a resumed run needs, on the host: parameters, optimiser
+        state, step count, densification statistics and log, and the settings
+        that shape the next steps (learning rates, schedule, recipe, seed)."""
+        def host(d):
+            return {k: t.detach().cpu().clone() for k, t in d.items()}
+        st = {"params": host(self.p), "t": self.t, "accum": self.accum.cpu().clone(),
+              "denom": self.denom.cpu().clone(), "densify_log": list(self.densify_log),
+              "lrs": dict(self.lrs), "betas": tuple(self.betas), "eps": self.eps,
+              "weight_decay": self.weight_decay, "objective": self.objective, "optimizer": self.optimizer,
+              "total_steps": self.total_steps, "lambda_ssim": self.lambda_ssim, "seed": self.seed,
+              "densify_opts": self.densify_opts, "densify_every": self.densify_every,
+              "densify_until": self.densify_until}
+        for k in self.STATE_KEYS:
+            if hasattr(self, k):
+                st[k] = host(getattr(self, k))
+        return st
+
+    def load_state_dict(self, st: dict):
+        """Restore a state_dict (parameters and optimiser state are copied to
+        this trainer's device; array sizes may differ after densification)."""
+        dev = self.p["means"].device
+        for k, t in st["params"].items():
+            self.p[k] = t.to(dev).contiguous()
+        for k in self.STATE_KEYS:
+            if k in st:
+                setattr(self, k, {a: t.to(dev).contiguous() for a, t in st[k].items()})
+        self.g = {k: torch.empty_like(v) for k, v in self.p.items()}
+        self.accum = st["accum"].to(dev)
+        self.denom = st["denom"].to(dev)
+        self.t = int(st["t"])
+        self.densify_log = list(st["densify_log"])
+        for k in ("lrs", "eps", "weight_decay", "objective", "optimizer", "total_steps", "lambda_ssim", "seed",
+                  "densify_opts", "densify_every", "densify_until"):
+            setattr(self, k, st[k])
+        self.betas = tuple(st["betas"])
+
+    def save(self, path: str):
+        torch.save(self.state_dict(), path)
+
+    def load(self, path: str):
+        self.load_state_dict(torch.load(path, map_location="cpu", weights_only=False))
+
     def densify(self):
         """Prune, clone and split (Algorithm 1) with the gathered statistics;
         the optimiser state follows kept Gaussians and starts at zero for new

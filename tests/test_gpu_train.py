@@ -112,3 +112,46 @@ def test_ring_run_paper_objective_with_adan(P):
     assert set(np.unique(M)) <= {0.0, 1.0} and M.sum(1).max() <= 1.0
     assert M.sum() > 0.01 * o.H * o.W
     ctx.close()
+
+
+def test_checkpoint_resume(P, tmp_path):
+    # save after 12 steps (densification at step 10 on), then: continue 6
+    # steps in the same trainer, and restore the checkpoint into a new trainer
+    # and run the same 6 steps.  The restore itself is exact; the two
+    # continuations agree to the run-to-run spread of the atomic sums.
+    from paper_2506_08350_b300.train import HologramTrainer, focal_stack, plane_masks
+    ctx = P.Context(0)
+    o = S.Optics(256, 256, S.WAVELENGTHS_RGB, (0.0, 3e-3))
+    teacher = S.make_gaussians(3000, o.L, o.C, o.H, o.W, seed=3)
+    tdev = {k: torch.from_numpy(teacher[k]).cuda() for k in P.PARAM_NAMES}
+    vms = [torch.from_numpy(S.ring_cameras(4)[k:k + 1].astype(np.float32)).cuda() for k in range(4)]
+    it = torch.from_numpy(S.intrinsics(o.H, o.W).astype(np.float32)[None]).cuda()
+    targets = [focal_stack(ctx, tdev, v, it, o) for v in vms]
+    masks = [plane_masks(ctx, tdev, v, it, o, P.DEFAULT_OPTS) for v in vms]
+    student = dict(teacher)
+    student["phase"] = np.zeros_like(teacher["phase"])
+    kw = dict(objective="paper", optimizer="adan", total_steps=30, densify=dict(grad_threshold=1e-3),
+              densify_every=10, seed=5)
+    tr = HologramTrainer(ctx, {k: torch.from_numpy(np.ascontiguousarray(student[k])).cuda() for k in P.PARAM_NAMES},
+                         o, dict(P.DEFAULT_OPTS), **kw)
+    for s in range(12):
+        tr.step(vms[s % 4], it, targets[s % 4], masks[s % 4])
+    path = str(tmp_path / "ckpt.pt")
+    tr.save(path)
+    tr2 = HologramTrainer(ctx, {k: torch.from_numpy(np.ascontiguousarray(student[k])).cuda() for k in P.PARAM_NAMES},
+                          o, dict(P.DEFAULT_OPTS), **kw)
+    tr2.load(path)
+    assert tr2.t == 12 and tr2.p["means"].shape == tr.p["means"].shape
+    for k in P.PARAM_NAMES:
+        assert torch.equal(tr2.p[k], tr.p[k]) and torch.equal(tr2.n[k], tr.n[k]), k
+    for s in range(12, 18):
+        tr.step(vms[s % 4], it, targets[s % 4], masks[s % 4])
+        tr2.step(vms[s % 4], it, targets[s % 4], masks[s % 4])
+    torch.cuda.synchronize()
+    for k in P.PARAM_NAMES:
+        a, b = tr.p[k].cpu().numpy(), tr2.p[k].cpu().numpy()
+        assert rel(b, a) < 1e-4, (k, rel(b, a))
+    assert len(tr.densify_log) == 1 and tr2.densify_log == tr.densify_log
+    tr.saved.release()
+    tr2.saved.release()
+    ctx.close()
