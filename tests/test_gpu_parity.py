@@ -355,3 +355,28 @@ def test_bounded_wait_timeout_is_reported_and_context_recovers(P, ctx):
     ctx.render_view(gd, vmd, itd, o, P.DEFAULT_OPTS, holo)
     torch.cuda.synchronize()
     assert torch.equal(holo, ref)
+
+
+@pytest.mark.parametrize("footprint", [0, 1])
+def test_render_max_wavelengths_and_planes(P, ctx, footprint):
+    # the largest channel and plane counts the API takes (C = 4, L = 16):
+    # four-channel records (NR = 4) and sixteen plane lists, forward and adjoint
+    wl = (639e-9, 560e-9, 515e-9, 473e-9)
+    z = tuple(float(v) for v in np.linspace(0.0, 15e-3, 16))
+    o = S.Optics(40, 72, wl, z)
+    g = S.make_gaussians(400, o.L, o.C, o.H, o.W, seed=11, log_scale_mean=-2.8, log_scale_std=0.4)
+    g["means"][:, 2] += 0.5
+    opts = dict(P.DEFAULT_OPTS, footprint=footprint)
+    hp, Ug, Po, Uo, To, No, saved, (gd, vmd, itd, vm, it) = _render_both(P, ctx, g, o, 2, opts, seed=4)
+    tol_f = 1e-2 if footprint else 1e-4
+    assert rel(Ug, Uo) < tol_f and rel(hp, Po) < tol_f, (rel(Ug, Uo), rel(hp, Po))
+    gP = S.random_complex((2, o.C, o.H, o.W), seed=6)
+    grads = {k: torch.empty_like(gd[k]) for k in P.PARAM_NAMES}
+    ctx.render_view_backward(saved, gd, complex_dev(gP), grads)
+    saved.release()
+    ref = oracle.render_backward(g, vm.astype(np.float64), it.astype(np.float64), o, gP.astype(np.complex128),
+                                 oracle_opts(opts))
+    tol_g = 2e-2 if footprint else 1e-3
+    for k in P.PARAM_NAMES:
+        e = rel(grads[k].cpu().numpy(), ref[k])
+        assert e < tol_g, (k, e)
