@@ -220,18 +220,23 @@ __global__ void k_rs_hist(const uint32_t* __restrict__ keys, size_t seglen, int 
     hist[((size_t)seg * 256 + threadIdx.x) * nblk + blk] = h[threadIdx.x];
 }
 
-// One pass of the stable scatter.  The block's RS_KPB elements are ranked
-// within their digit (in input order: warp match, per-warp counts, running
-// totals over the rounds), staged in shared memory grouped by digit, and then
-// written out so that consecutive threads write consecutive addresses of a
-// digit's output run (instead of 4-byte writes scattered over 256 runs).
+// One pass of the stable scatter.  Warp w owns the block's elements
+// [256 w, 256 w + 256) and ranks them in input order, 32 at a time, against
+// its own digit counters (warp match; the leader of each digit group advances
+// the counter and broadcasts the old value), with no block barrier between
+// rounds.  One scan over (digit, warp) then gives every element its place in
+// the block's digit-sorted order; the elements are staged in shared memory in
+// that order and written out so that consecutive threads write consecutive
+// addresses of a digit's output run (instead of 4-byte writes scattered over
+// 256 runs).
 __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t* __restrict__ kin,
                                                            const uint32_t* __restrict__ vin,
                                                            uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                                            size_t seglen, int shift, int nblk,
                                                            const uint32_t* __restrict__ pos) {
-    __shared__ uint32_t wcnt[RS_THREADS / 32][256];
-    __shared__ uint32_t running[256], gbase[256], loff[256], wsum[RS_THREADS / 32];
+    constexpr int NW = RS_THREADS / 32, PW = RS_KPB / NW;  // warps, elements per warp
+    __shared__ uint32_t wh[NW][256];  // per-warp digit counters, then per-warp bases within a digit
+    __shared__ uint32_t gbase[256], loff[256], wsum[NW];
     __shared__ uint32_t sk[RS_KPB], sv[RS_KPB];
     const int seg = blockIdx.y, blk = blockIdx.x;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -239,22 +244,40 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t* __res
     const size_t beg = (size_t)blk * RS_KPB;
     const size_t so = (size_t)seg * seglen;
     const int nb = (int)min((size_t)RS_KPB, seglen - beg);  // elements of this block
-    running[t] = 0;
-    loff[t] = 0;
+    for (int e = t; e < NW * 256; e += RS_THREADS) (&wh[0][0])[e] = 0;
     gbase[t] = pos[((size_t)seg * 256 + t) * nblk + blk];
-    __syncthreads();
-    uint32_t key[RS_IPT], val[RS_IPT];
+    uint32_t key[RS_IPT], val[RS_IPT], rk[RS_IPT];
 #pragma unroll
     for (int r = 0; r < RS_IPT; r++) {
-        const int i = r * RS_THREADS + t;
+        const int i = warp * PW + r * 32 + lane;
         key[r] = i < nb ? kin[so + beg + i] : 0u;
         val[r] = i < nb ? vin[so + beg + i] : 0u;
-        if (i < nb) atomicAdd(&loff[(key[r] >> shift) & 255u], 1u);
     }
     __syncthreads();
-    // exclusive scan of the block's digit counts (thread t: digit t)
+#pragma unroll
+    for (int r = 0; r < RS_IPT; r++) {
+        const bool ok = warp * PW + r * 32 + lane < nb;
+        const uint32_t d = ok ? ((key[r] >> shift) & 255u) : 256u;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int leader = __ffs(peers) - 1;
+        const uint32_t lrank = __popc(peers & lt);
+        uint32_t old = (ok && lrank == 0) ? wh[warp][d] : 0u;
+        old = __shfl_sync(0xffffffffu, old, leader);
+        if (ok && lrank == 0) wh[warp][d] = old + __popc(peers);
+        rk[r] = old + lrank;
+        __syncwarp();
+    }
+    __syncthreads();
+    // thread t = digit t: bases of the warps within the digit, and the
+    // block's exclusive scan of the digit totals
     {
-        const uint32_t c = loff[t];
+        uint32_t c = 0;
+#pragma unroll
+        for (int w = 0; w < NW; w++) {
+            const uint32_t x = wh[w][t];
+            wh[w][t] = c;
+            c += x;
+        }
         uint32_t inc = c;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -267,30 +290,15 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t* __res
         for (int w = 0; w < warp; w++) wb += wsum[w];
         loff[t] = wb + inc - c;
     }
-    for (int r = 0; r < RS_IPT; r++) {
-        for (int e = t; e < (RS_THREADS / 32) * 256; e += RS_THREADS) (&wcnt[0][0])[e] = 0;
-        __syncthreads();
-        const bool ok = r * RS_THREADS + t < nb;
-        const uint32_t d = ok ? ((key[r] >> shift) & 255u) : 256u;
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
-        const uint32_t lrank = __popc(peers & lt);
-        if (ok && lrank == 0) wcnt[warp][d] = __popc(peers);
-        __syncthreads();
-        uint32_t tot = 0;
+    __syncthreads();
 #pragma unroll
-        for (int w = 0; w < RS_THREADS / 32; w++) {
-            const uint32_t c = wcnt[w][t];
-            wcnt[w][t] = tot;
-            tot += c;
-        }
-        __syncthreads();
-        if (ok) {
-            const uint32_t lp = loff[d] + running[d] + wcnt[warp][d] + lrank;
+    for (int r = 0; r < RS_IPT; r++) {
+        if (warp * PW + r * 32 + lane < nb) {
+            const uint32_t d = (key[r] >> shift) & 255u;
+            const uint32_t lp = loff[d] + wh[warp][d] + rk[r];
             sk[lp] = key[r];
             sv[lp] = val[r];
         }
-        __syncthreads();
-        running[t] += tot;
     }
     __syncthreads();
     for (int i = t; i < nb; i += RS_THREADS) {
