@@ -173,7 +173,9 @@ hcgs_status hcgs_saved_release(hcgs_ctx* ctx, hcgs_saved* saved);
 /* Self-test of the bounded waits: launches, on `stream`, one kernel that
  * waits on a shared-memory barrier nothing completes.  Its wait gives up
  * after about one second of SM clock and sets the context's status word, as
- * the row passes do when a bulk copy never arrives; the next hcgs_project or
+ * the FFT row passes and the SSIM passes of hcgs_paper_loss /
+ * hcgs_paper_loss_intensities / hcgs_phase_only_loss do when a bulk or tensor
+ * copy never arrives (they leave without writing); the next hcgs_project or
  * hcgs_render_view on the context then returns HCGS_ERR_TIMEOUT (and clears
  * the word), and the calls after it work again.  Returns HCGS_OK once the
  * kernel is launched; HCGS_ERR_INVALID_ARG for a null context. */
