@@ -504,15 +504,15 @@ def run_ours(args):
             configs[name] = measure_config(ctx, P, S, name, tiers, dev)
 
     # --- full optimisation step on the ring configuration (512^2 RGB, 8
-    # planes, 500k Gaussians, 50 views): FP32 path vs FP16x2 footprint tier ---
+    # planes, 500k Gaussians, 50 views): FP32 path vs the FP16x2 and BF16x2 footprint tiers ---
     training = None
     if args.train_steps > 0:
         from paper_2506_08350_b300.train import ring_run
         wt = S.workload("c3_512_L8_N500k")
         training = {"workload": wt.name, "unit": "steps/s",
                     "step": "render + inverse propagation + focal-stack loss + adjoint + Adam, one ring view per step"}
-        for fp in (0, 1):
-            training["fp16x2" if fp else "fp32"] = ring_run(ctx, wt.optics, wt.N, args.train_steps, footprint=fp)
+        for fp, tier in ((0, "fp32"), (1, "fp16x2"), (2, "bf16x2")):
+            training[tier] = ring_run(ctx, wt.optics, wt.N, args.train_steps, footprint=fp)
         # the paper's recipe: L_recon + L_SSIM with teacher plane masks, Adan,
         # cosine annealing of the means' and plane logits' learning rates
         training["fp32_paper_objective_adan"] = ring_run(ctx, wt.optics, wt.N, args.train_steps, footprint=0,

@@ -86,16 +86,22 @@ hcgs_status philox(hcgs_ctx* ctx, uint64_t seed, uint32_t stream_id, int64_t n, 
 // ---------------------------------------------------------------------------
 // statistics: per Gaussian, over the views of the last backward pass
 // ---------------------------------------------------------------------------
-__global__ void k_densify_accum(const uint32_t* __restrict__ rank, const float* __restrict__ g2d, int V, int N,
-                                int G, float hw, float hh, float* __restrict__ accum, float* __restrict__ denom) {
+__global__ void k_densify_accum(const uint32_t* __restrict__ rank, const float* __restrict__ g2d,
+                                const float4* __restrict__ rec, int NR, int V, int N, int G, float hw, float hh,
+                                float* __restrict__ accum, float* __restrict__ denom) {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
     float s = 0.f, d = 0.f;
     for (int v = 0; v < V; v++) {
         const uint32_t r = rank[(size_t)v * N + n];
         if (r == 0xFFFFFFFFu) continue;
-        const float* g = g2d + ((size_t)v * N + r) * G;
-        s += sqrtf(g[0] * hw * (g[0] * hw) + g[1] * hh * (g[1] * hh));
+        const size_t e = (size_t)v * N + r;
+        const float* g = g2d + e * G;
+        // dL/dmu from the pixel moments sum dx p, sum dy p and the conic A, B, C
+        // of the record: (A m0 + B m1, B m0 + C m1)
+        const float4 q0 = rec[e * NR], q1 = rec[e * NR + 1];
+        const float gx = fmaf(q0.z, g[0], q0.w * g[1]), gy = fmaf(q0.w, g[0], q1.x * g[1]);
+        s += sqrtf(gx * hw * (gx * hw) + gy * hh * (gy * hh));
         d += 1.f;
     }
     if (d > 0.f) {
@@ -108,7 +114,8 @@ hcgs_status densify_accumulate(hcgs_ctx* ctx, hcgs_saved* s, float* accum, float
     if (s->N == 0) return HCGS_OK;
     HCGS_KERNEL(ctx, "k_densify_accum", st,
                 k_densify_accum<<<(s->N + 255) / 256, 256, 0, st>>>(
-                    (const uint32_t*)s->rank.p, (const float*)s->g2d.p, s->V, s->N, g2d_count(s->C),
+                    (const uint32_t*)s->rank.p, (const float*)s->g2d.p, (const float4*)s->rec.p,
+                    rec_count(s->C), s->V, s->N, g2d_count(s->C),
                     0.5f * (float)s->W, 0.5f * (float)s->H, accum, denom));
     return HCGS_OK;
 }

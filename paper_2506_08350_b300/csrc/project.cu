@@ -590,7 +590,12 @@ __global__ void k_project_bwd(ProjArgs a, const float* __restrict__ means, const
         const float ogo = g[5];
         gol += ogo * (1.f - P.o);
         drho += ogo;
-        project_one_backward(a, P, cam + 20 * v, make_float2(g[0], g[1]), g[2], g[3], g[4], gm, gls, gq);
+        // the rasterizer's adjoint leaves the pixel moments of p = -dL/dpower
+        // (sum dx p, sum dy p, sum dx^2 p, sum dx dy p, sum dy^2 p); with
+        // power = 1/2 (A dx^2 + C dy^2) + B dx dy, d = pixel - mu:
+        const float A = P.conic[0], B = P.conic[1], Cc = P.conic[2];
+        const float2 gmu = make_float2(fmaf(A, g[0], B * g[1]), fmaf(B, g[0], Cc * g[1]));
+        project_one_backward(a, P, cam + 20 * v, gmu, -0.5f * g[2], -g[3], -0.5f * g[4], gm, gls, gq);
     }
     // appearance: w_c = a_c (cos phi_c, sin phi_c)
     for (int c = 0; c < C; c++) {

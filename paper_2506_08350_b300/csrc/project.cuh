@@ -29,7 +29,7 @@ inline ProjArgs make_proj_args(const hcgs_saved* s) {
 
 // float4s per rasterizer record: (mu, A, B), (C, o, w0), (w1, w2), (w3, -)
 __host__ __device__ inline int rec_count(int C) { return C <= 1 ? 2 : (C <= 3 ? 3 : 4); }
-// floats per 2D gradient record: mu 2, conic 3, opacity 1, w 2C
+// floats per 2D gradient record: pixel moments of -dL/dpower 5, o dL/do 1, dL/dw 2C
 __host__ __device__ inline int g2d_count(int C) { return 6 + 2 * C; }
 
 struct ProjF {

@@ -20,6 +20,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "project.cuh"
 
@@ -172,6 +174,13 @@ __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 // dx terms once per entry and thread (t0 = A' dx^2 + log2 o, bdx = B' dx);
 // alpha = min(alpha_max, o G).
 
+// alpha = min(alpha_max, o G) needs the clamp only for entries whose opacity
+// comes near alpha_max: below alpha_max (1 - 2^-10), o G <= o stays below
+// alpha_max up to the rounding of the evaluation, and alpha = o G as evaluated.
+// The choice is per entry (warp-uniform), so the forward and the adjoint
+// evaluate every entry the same way.
+__device__ __forceinline__ bool may_clamp(float o, float amax) { return o > amax * 0.9990234375f; }
+
 // Reduced-precision footprint (the FP16x2 tier): the same quantities, with the
 // exponent and exp() evaluated in packed half precision.  To stay well
 // conditioned for footprints of any size the quadratic is formed in the
@@ -196,7 +205,7 @@ struct Half2Of<2> {
     static __device__ __forceinline__ float2 to2(T x) { return __bfloat1622float2(x); }
 };
 
-template <int FT>
+template <int FT, bool CL>
 __device__ __forceinline__ void eval_pair_h(float2 py2, float4 r0, float sc, typename Half2Of<FT>::T nc,
                                             typename Half2Of<FT>::T a1, typename Half2Of<FT>::T a0, float o,
                                             float amax, float2& dy2, float2& og2, float2& a2) {
@@ -205,7 +214,7 @@ __device__ __forceinline__ void eval_pair_h(float2 py2, float4 r0, float sc, typ
     const auto e = __hfma2(__hfma2(nc, v, a1), v, a0);
     const float2 G2 = Half2Of<FT>::to2(h2exp2(e));
     og2 = __fmul2_rn(f2(o), G2);
-    a2 = make_float2(fminf(amax, og2.x), fminf(amax, og2.y));
+    a2 = CL ? make_float2(fminf(amax, og2.x), fminf(amax, og2.y)) : og2;
 }
 
 // Per-entry, per-thread part of the evaluation (the pixel column is fixed):
@@ -225,8 +234,9 @@ __device__ __forceinline__ EntryX entry_x(float px, float4 r0, float4 k) {
 // the FP32 tier the exponent is quadratic in dy, so the second pair follows
 // from the first by a linear correction: e(dy + 4) - e(dy) = 4 B' dx +
 // 16 C' + 8 C' dy (two packed operations instead of four).  Forward and
-// adjoint both evaluate through here, so they take identical decisions.
-template <int FT>
+// adjoint both evaluate through here, so they take identical decisions.  CL:
+// the entry may reach the clamp (may_clamp).
+template <int FT, bool CL>
 __device__ __forceinline__ void eval_entry(const EntryX& x, float2 pyA, float2 pyB, float4 r0, float4 r1, float4 k,
                                            float amax, float2& dyA, float2& ogA, float2& aA, float2& dyB,
                                            float2& ogB, float2& aB) {
@@ -238,8 +248,8 @@ __device__ __forceinline__ void eval_entry(const EntryX& x, float2 pyA, float2 p
         const float u = x.dx * k.x;
         constexpr float c = 0.72134752044448170f;  // log2(e) / 2
         const H2 nc = Half2Of<FT>::from(-c), a1 = Half2Of<FT>::from(-c * k.z * u), a0 = Half2Of<FT>::from(-c * u * u);
-        eval_pair_h<FT>(pyA, r0, k.y, nc, a1, a0, r1.y, amax, dyA, ogA, aA);
-        eval_pair_h<FT>(pyB, r0, k.y, nc, a1, a0, r1.y, amax, dyB, ogB, aB);
+        eval_pair_h<FT, CL>(pyA, r0, k.y, nc, a1, a0, r1.y, amax, dyA, ogA, aA);
+        eval_pair_h<FT, CL>(pyB, r0, k.y, nc, a1, a0, r1.y, amax, dyB, ogB, aB);
     } else {
         dyA = __fadd2_rn(pyA, f2(-r0.y));
         float2 e = __ffma2_rn(f2(x.bdx), dyA, f2(x.t0));
@@ -249,8 +259,8 @@ __device__ __forceinline__ void eval_entry(const EntryX& x, float2 pyA, float2 p
         dyB = __fadd2_rn(dyA, f2(4.f));
         ogA = make_float2(ex2_approx(e.x), ex2_approx(e.y));
         ogB = make_float2(ex2_approx(eB.x), ex2_approx(eB.y));
-        aA = make_float2(fminf(amax, ogA.x), fminf(amax, ogA.y));
-        aB = make_float2(fminf(amax, ogB.x), fminf(amax, ogB.y));
+        aA = CL ? make_float2(fminf(amax, ogA.x), fminf(amax, ogA.y)) : ogA;
+        aB = CL ? make_float2(fminf(amax, ogB.x), fminf(amax, ogB.y)) : ogB;
     }
 }
 
@@ -270,8 +280,6 @@ __device__ __forceinline__ float warp_reduce_scatter16(float (&v)[16], int lane)
     return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
-// Forward step of a pixel pair that takes it (c0/c1) for one record: a pixel
-// that does not take it gets alpha 0 (no add, T unchanged).
 // Forward step of a pixel pair that takes it (c0/c1) for one record: a pixel
 // that does not take it gets alpha 0 (no add, T unchanged).
 template <int C>
@@ -331,19 +339,23 @@ __global__ void __launch_bounds__(RT, 32) k_raster_fwd(RasterArgs a, float2* __r
             const float4* rec = srec[k];
             const float4 r0 = rec[0], r1 = rec[1], kk = rec[NR];
             const uint32_t pos1 = nkept + (uint32_t)k + 1u;  // staged index + 1
-            const EntryX x = entry_x(fpx, r0, kk);
-            float2 dyA, ogA, aA, dyB, ogB, aB;
-            eval_entry<FT>(x, pyA, pyB, r0, r1, kk, a.amax, dyA, ogA, aA, dyB, ogB, aB);
-            const bool c0 = TA.x >= teps && aA.x >= a.amin, c1 = TA.y >= teps && aA.y >= a.amin;
-            const bool c2 = TB.x >= teps && aB.x >= a.amin, c3 = TB.y >= teps && aB.y >= a.amin;
-            fwd_pair<C>(rec, aA, c0, c1, TA, aAX, aAY);
-            last[0] = c0 ? pos1 : last[0];
-            last[1] = c1 ? pos1 : last[1];
-            if (NCOUNT) { nc[0] += c0; nc[1] += c1; }
-            fwd_pair<C>(rec, aB, c2, c3, TB, aBX, aBY);
-            last[2] = c2 ? pos1 : last[2];
-            last[3] = c3 ? pos1 : last[3];
-            if (NCOUNT) { nc[2] += c2; nc[3] += c3; }
+            auto step = [&](auto cl) {
+                const EntryX x = entry_x(fpx, r0, kk);
+                float2 dyA, ogA, aA, dyB, ogB, aB;
+                eval_entry<FT, decltype(cl)::value>(x, pyA, pyB, r0, r1, kk, a.amax, dyA, ogA, aA, dyB, ogB, aB);
+                const bool c0 = TA.x >= teps && aA.x >= a.amin, c1 = TA.y >= teps && aA.y >= a.amin;
+                const bool c2 = TB.x >= teps && aB.x >= a.amin, c3 = TB.y >= teps && aB.y >= a.amin;
+                fwd_pair<C>(rec, aA, c0, c1, TA, aAX, aAY);
+                last[0] = c0 ? pos1 : last[0];
+                last[1] = c1 ? pos1 : last[1];
+                if (NCOUNT) { nc[0] += c0; nc[1] += c1; }
+                fwd_pair<C>(rec, aB, c2, c3, TB, aBX, aBY);
+                last[2] = c2 ? pos1 : last[2];
+                last[3] = c3 ? pos1 : last[3];
+                if (NCOUNT) { nc[2] += c2; nc[3] += c3; }
+            };
+            if (may_clamp(r1.y, a.amax)) step(std::true_type{});
+            else step(std::false_type{});
         }
         nkept += (uint32_t)nh;
         __syncwarp();
@@ -387,8 +399,10 @@ __device__ __forceinline__ float rcp_approx(float x) {
 // Syy = sum p dy^2; all pixels of a thread share dx, so the thread's
 // gradients of mu and the conic follow from the moments once per entry.
 // The reciprocal of 1 - alpha only scales gradients (no decision depends on
-// it), so the hardware approximation is used.
-template <int C, bool FIRST>
+// it), so the hardware approximation is used.  CL as in eval_entry: for an
+// entry that cannot reach the clamp the masked alpha is o G at the pixels that
+// took the step and 0 elsewhere, so p = dL/dalpha * alpha.
+template <int C, bool FIRST, bool CL>
 __device__ __forceinline__ void bwd_pair(const float4* rec, float2 dy2, float2 og2, float2 a2, bool c0, bool c1,
                                          float amax, float2& T2, float2& B2, const float2 (&gX)[C],
                                          const float2 (&gY)[C], float2 (&gw)[2 * C], float2& S0, float2& Sy,
@@ -409,9 +423,14 @@ __device__ __forceinline__ void bwd_pair(const float4* rec, float2 dy2, float2 o
     const float2 dLda = __ffma2_rn(Tk, Ak, __fmul2_rn(make_float2(-iom.x, -iom.y), B2));
     B2 = __ffma2_rn(aT, Ak, B2);
     T2 = Tk;
-    // a clamped alpha (o G > alpha_max) is flat in o G
-    const float2 dLa = make_float2(c0 && og2.x <= amax ? dLda.x : 0.f, c1 && og2.y <= amax ? dLda.y : 0.f);
-    const float2 p = __fmul2_rn(dLa, og2);  // -dL/dpower = o dL/do
+    // -dL/dpower = o dL/do; a clamped alpha (o G > alpha_max) is flat in o G
+    float2 p;
+    if (CL) {
+        const float2 dLa = make_float2(c0 && og2.x <= amax ? dLda.x : 0.f, c1 && og2.y <= amax ? dLda.y : 0.f);
+        p = __fmul2_rn(dLa, og2);
+    } else {
+        p = __fmul2_rn(dLda, al);
+    }
     const float2 pdy = __fmul2_rn(p, dy2);
     if (FIRST) {
         S0 = p;
@@ -424,21 +443,23 @@ __device__ __forceinline__ void bwd_pair(const float4* rec, float2 dy2, float2 o
     }
 }
 
-// The entry's 6 + 2C gradient values of one thread from its accumulators:
-// with power = 1/2 (A dx^2 + 2 B dx dy + C dy^2), d = pixel - mu, and the
-// thread's moments s0, sy, syy of p = -dL/dpower (dx is the same for its
-// pixels):  dL/dmu = (A dx s0 + B sy, B dx s0 + C sy), dL/dA = -dx^2 s0 / 2,
-// dL/dB = -dx sy, dL/dC = -syy / 2, o dL/do = s0; then dL/dw_c.
+// The entry's 6 + 2C sums of one thread, from its accumulators: the pixel
+// moments of p = -dL/dpower, d = pixel - mu (dx is the same for the thread's
+// pixels; s0, sy, syy its sums of p, p dy, p dy^2), then dL/dw_c:
+//   m = (sum dx p, sum dy p, sum dx^2 p, sum dx dy p, sum dy^2 p, sum p).
+// With power = 1/2 (A dx^2 + C dy^2) + B dx dy the 2D gradients are linear in
+// them: dL/dmu = (A m0 + B m1, B m0 + C m1), dL/dA = -m2 / 2, dL/dB = -m3,
+// dL/dC = -m4 / 2, o dL/do = m5 (formed once per Gaussian in the projection
+// adjoint, not per entry and thread).
 template <int C>
-__device__ __forceinline__ void entry_grads(float4 r0, float4 r1, float dx, float2 S0, float2 Sy, float2 Syy,
-                                            const float2 (&gw)[2 * C], float (&out)[6 + 2 * C]) {
-    const float s0 = S0.x + S0.y, sy = Sy.x + Sy.y, syy = Syy.x + Syy.y;
-    const float dxs0 = dx * s0;
-    out[0] = fmaf(r0.z, dxs0, r0.w * sy);
-    out[1] = fmaf(r0.w, dxs0, r1.x * sy);
-    out[2] = -0.5f * dx * dxs0;
-    out[3] = -dx * sy;
-    out[4] = -0.5f * syy;
+__device__ __forceinline__ void entry_moments(float dx, float2 S0, float2 Sy, float2 Syy, const float2 (&gw)[2 * C],
+                                              float (&out)[6 + 2 * C]) {
+    const float s0 = S0.x + S0.y, sy = Sy.x + Sy.y;
+    out[0] = dx * s0;
+    out[1] = sy;
+    out[2] = dx * out[0];
+    out[3] = dx * sy;
+    out[4] = Syy.x + Syy.y;
     out[5] = s0;
 #pragma unroll
     for (int e = 0; e < 2 * C; e++) out[6 + e] = gw[e].x + gw[e].y;
@@ -524,21 +545,22 @@ __global__ void __launch_bounds__(RT, 24) k_raster_bwd(RasterArgs a, const float
             const float4* rec = srec[k];
             const uint32_t pos = lo + (uint32_t)k;
             const float4 r0 = rec[0], r1 = rec[1], kk = rec[NR];
-            const EntryX x = entry_x(fpx, r0, kk);
-            float2 dyA, ogA, aA, dyB, ogB, aB;
-            eval_entry<FT>(x, pyA, pyB, r0, r1, kk, a.amax, dyA, ogA, aA, dyB, ogB, aB);
-            const bool c0 = pos < last[0] && aA.x >= a.amin, c1 = pos < last[1] && aA.y >= a.amin;
-            const bool c2 = pos < last[2] && aB.x >= a.amin, c3 = pos < last[3] && aB.y >= a.amin;
-            // no pixel of the strip took this step: zero gradient, T and B unchanged
-            if (!__any_sync(0xffffffffu, c0 || c1 || c2 || c3)) continue;
-            {
+            auto step = [&](auto cl) {
+                constexpr bool CL = decltype(cl)::value;
+                const EntryX x = entry_x(fpx, r0, kk);
+                float2 dyA, ogA, aA, dyB, ogB, aB;
+                eval_entry<FT, CL>(x, pyA, pyB, r0, r1, kk, a.amax, dyA, ogA, aA, dyB, ogB, aB);
+                const bool c0 = pos < last[0] && aA.x >= a.amin, c1 = pos < last[1] && aA.y >= a.amin;
+                const bool c2 = pos < last[2] && aB.x >= a.amin, c3 = pos < last[3] && aB.y >= a.amin;
+                // no pixel of the strip took this step: zero gradient, T and B unchanged
+                if (!__any_sync(0xffffffffu, c0 || c1 || c2 || c3)) return;
                 // branch-free: pixels that did not take the step carry alpha 0
                 // through the pair (T and B unchanged, zero gradient)
                 float2 gw[2 * C], S0, Sy, Syy;
-                bwd_pair<C, true>(rec, dyA, ogA, aA, c0, c1, a.amax, TA, BA, gAX, gAY, gw, S0, Sy, Syy);
-                bwd_pair<C, false>(rec, dyB, ogB, aB, c2, c3, a.amax, TB, BB, gBX, gBY, gw, S0, Sy, Syy);
+                bwd_pair<C, true, CL>(rec, dyA, ogA, aA, c0, c1, a.amax, TA, BA, gAX, gAY, gw, S0, Sy, Syy);
+                bwd_pair<C, false, CL>(rec, dyB, ogB, aB, c2, c3, a.amax, TB, BB, gBX, gBY, gw, S0, Sy, Syy);
                 float gv[G];
-                entry_grads<C>(r0, r1, x.dx, S0, Sy, Syy, gw, gv);
+                entry_moments<C>(x.dx, S0, Sy, Syy, gw, gv);
                 // warp sum of the G values: each lane writes its column of the
                 // G x 32 buffer, lane (e, h) adds the 16 values of row e in
                 // half h, one shuffle joins the halves
@@ -557,10 +579,12 @@ __global__ void __launch_bounds__(RT, 24) k_raster_bwd(RasterArgs a, const float
                 const float2 s4 = __fadd2_rn(__fadd2_rn(s0, s1), __fadd2_rn(s2, s3));
                 float sum = s4.x + s4.y;
                 sum += __shfl_xor_sync(0xffffffffu, sum, 1);
-                // slot 5 holds o dL/do (the projection adjoint needs no more)
+                // slot 5 holds o dL/do = sum p (the projection adjoint needs no more)
                 if (!h && e < G) atomicAdd(g2d + (vN + sid[k]) * G + e, sum);
                 __syncwarp();
-            }
+            };
+            if (may_clamp(r1.y, a.amax)) step(std::true_type{});
+            else step(std::false_type{});
         }
         __syncwarp();
         hi = lo;
@@ -619,7 +643,8 @@ __global__ void __launch_bounds__(RT) k_raster_rho_dense(RasterArgs a, const uin
                 const float4 r0 = rec[0], r1 = rec[1], kk = rec[NR];
                 const EntryX x = entry_x(fpx, r0, kk);
                 float2 dyA, ogA, aA, dyB, ogB, aB;
-                eval_entry<FT>(x, pyA, pyB, r0, r1, kk, a.amax, dyA, ogA, aA, dyB, ogB, aB);
+                if (may_clamp(r1.y, a.amax)) eval_entry<FT, true>(x, pyA, pyB, r0, r1, kk, a.amax, dyA, ogA, aA, dyB, ogB, aB);
+                else eval_entry<FT, false>(x, pyA, pyB, r0, r1, kk, a.amax, dyA, ogA, aA, dyB, ogB, aB);
                 const bool c0 = TA.x >= teps && aA.x >= a.amin, c1 = TA.y >= teps && aA.y >= a.amin;
                 const bool c2 = TB.x >= teps && aB.x >= a.amin, c3 = TB.y >= teps && aB.y >= a.amin;
                 fwd_pair<C>(rec, aA, c0, c1, TA, uAX, uAY);
@@ -659,7 +684,8 @@ __global__ void __launch_bounds__(RT) k_raster_rho_dense(RasterArgs a, const uin
             const bool own = planes[vN + srank] == l;  // warp-uniform
             const EntryX x = entry_x(fpx, r0, kk);
             float2 dyA, ogA, aA, dyB, ogB, aB;
-            eval_entry<FT>(x, pyA, pyB, r0, r1, kk, a.amax, dyA, ogA, aA, dyB, ogB, aB);
+            if (may_clamp(r1.y, a.amax)) eval_entry<FT, true>(x, pyA, pyB, r0, r1, kk, a.amax, dyA, ogA, aA, dyB, ogB, aB);
+            else eval_entry<FT, false>(x, pyA, pyB, r0, r1, kk, a.amax, dyA, ogA, aA, dyB, ogB, aB);
             const bool c0 = TA.x >= teps && aA.x >= a.amin, c1 = TA.y >= teps && aA.y >= a.amin;
             const bool c2 = TB.x >= teps && aB.x >= a.amin, c3 = TB.y >= teps && aB.y >= a.amin;
             if (own) {

@@ -268,7 +268,7 @@ def ring_run(ctx: Context, optics, N: int, steps: int, n_views: int = 50, footpr
     (amplitude U[0, 1], phase U[0, 2 pi), the plain initialisation) and is
     optimised one view per step (render, inverse propagation + loss, adjoint,
     optimiser step on every parameter array).  ``footprint`` selects the FP32
-    (0) or FP16x2 (1) footprint tier; ``objective``, ``optimizer`` and
+    (0), FP16x2 (1) or BF16x2 (2) footprint tier; ``objective``, ``optimizer`` and
     ``anneal`` (cosine schedule over ``steps``) as in HologramTrainer; with the
     "paper" objective the plane masks come from the teacher (plane_masks).
 
@@ -321,7 +321,7 @@ def ring_run(ctx: Context, optics, N: int, steps: int, n_views: int = 50, footpr
     p1 = psnr()
     tr.saved.release()
     out = {"steps_per_s": 1e3 / ms, "ms_per_step": ms, "psnr_start": p0, "psnr_end": p1, "steps": steps,
-           "views": n_views, "footprint": "fp16x2" if footprint else "fp32", "objective": objective,
+           "views": n_views, "footprint": ("fp32", "fp16x2", "bf16x2")[int(footprint)], "objective": objective,
            "optimizer": optimizer, "anneal": bool(anneal)}
     if densify is not None:
         out["densify"] = tr.densify_log

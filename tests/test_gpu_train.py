@@ -76,19 +76,22 @@ def test_optimisation_reduces_focal_stack_loss(P):
     assert last < 0.5 * first, (first, last)
 
 
-def test_ring_run_fp16_tier_tracks_fp32(P):
-    # The ring configuration at reduced size (100k Gaussians, 10 views): both
-    # footprint tiers optimise the appearance, and the FP16x2 tier ends within
-    # a small margin of the FP32 path after the same steps.
+def test_ring_run_reduced_precision_tiers_track_fp32(P):
+    # The ring configuration at reduced size (100k Gaussians, 10 views): all
+    # three footprint tiers optimise the appearance, and the FP16x2 and BF16x2
+    # tiers end within a small margin of the FP32 path after the same steps.
     from paper_2506_08350_b300.train import ring_run
     ctx = P.Context(0)
     o = S.workload("c3_512_L8_N500k").optics
     r32 = ring_run(ctx, o, 100_000, steps=300, n_views=10, footprint=0)
     r16 = ring_run(ctx, o, 100_000, steps=300, n_views=10, footprint=1)
-    print("ring run fp32", r32, "fp16x2", r16)
+    rb16 = ring_run(ctx, o, 100_000, steps=300, n_views=10, footprint=2)
+    print("ring run fp32", r32, "fp16x2", r16, "bf16x2", rb16)
     assert r32["psnr_end"] > r32["psnr_start"] + 2.0, r32
-    assert r16["psnr_end"] > r16["psnr_start"] + 2.0, r16
-    assert abs(r16["psnr_end"] - r32["psnr_end"]) < 0.5, (r32, r16)
+    for r in (r16, rb16):
+        assert r["psnr_end"] > r["psnr_start"] + 2.0, r
+        assert abs(r["psnr_end"] - r32["psnr_end"]) < 0.5, (r32, r)
+    assert rb16["footprint"] == "bf16x2"
     ctx.close()
 
 
