@@ -110,7 +110,7 @@ struct hcgs_saved {
     hcgs::DevBuf last;     // [V][L][H][W] uint32: staged index after the last contributor
     hcgs::DevBuf slist;    // [32 M] uint32: per 16x8 strip, the Gaussians its forward pass kept, in order
     hcgs::DevBuf U;        // [V][L][C][H][W] float2 when the caller gives no plane buffer
-    hcgs::DevBuf g2d;      // [V][N][G2D] float (visiting order): pixel moments of -dL/dpower 5, o dL/do, dL/dw 2C
+    hcgs::DevBuf g2d;      // [V][N][G2D] float (Gaussian order): pixel moments of -dL/dpower 5, o dL/do, dL/dw 2C
     hcgs::DevBuf gU;       // [V][L][C][H][W] float2 plane gradients
     hcgs::DevBuf cam;      // [V][20] float copies of the view matrices and intrinsics
     // dense plane-weight gradient (opts.rho_grad = 1 only)

@@ -96,7 +96,7 @@ __global__ void k_densify_accum(const uint32_t* __restrict__ rank, const float* 
         const uint32_t r = rank[(size_t)v * N + n];
         if (r == 0xFFFFFFFFu) continue;
         const size_t e = (size_t)v * N + r;
-        const float* g = g2d + e * G;
+        const float* g = g2d + ((size_t)v * N + n) * G;
         // dL/dmu from the pixel moments sum dx p, sum dy p and the conic A, B, C
         // of the record: (A m0 + B m1, B m0 + C m1)
         const float4 q0 = rec[e * NR], q1 = rec[e * NR + 1];

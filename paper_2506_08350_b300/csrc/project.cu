@@ -577,7 +577,7 @@ __global__ void k_project_bwd(ProjArgs a, const float* __restrict__ means, const
     for (int v = 0; v < a.V; v++) {
         const uint32_t s = rank[(size_t)v * a.N + n];
         if (s == 0xFFFFFFFFu) continue;
-        const float* g = g2d + ((size_t)v * a.N + s) * G;
+        const float* g = g2d + ((size_t)v * a.N + n) * G;
         for (int c = 0; c < C; c++) {
             gwr[c] += g[6 + 2 * c];
             gwi[c] += g[7 + 2 * c];

@@ -32,6 +32,7 @@ struct RasterArgs {
     const uint2* rects;
     const uint32_t* off;
     const uint32_t* list;
+    const uint32_t* sortid;  // [V][N] Gaussian id at visiting rank
     uint32_t* slist;
     int V, N, L, H, W, tilesX, tilesY, ctX, ctY;
     float amin, amax, teps;
@@ -43,6 +44,7 @@ static RasterArgs make_raster_args(const hcgs_saved* s) {
     a.rects = (const uint2*)s->rects.p;
     a.off = (const uint32_t*)s->bcount.p;
     a.list = s->list;
+    a.sortid = (const uint32_t*)s->sortid.p;
     a.slist = (uint32_t*)s->slist.p;
     a.V = s->V; a.N = s->N; a.L = s->L; a.H = s->H; a.W = s->W;
     a.tilesX = s->tilesX; a.tilesY = s->tilesY; a.ctX = s->ctX; a.ctY = s->ctY;
@@ -465,8 +467,10 @@ __device__ __forceinline__ void entry_moments(float dx, float2 S0, float2 Sy, fl
     for (int e = 0; e < 2 * C; e++) out[6 + e] = gw[e].x + gw[e].y;
 }
 
-// Loads kept entries [lo, lo + cnt) of a strip (Gaussian ids from the forward
-// pass) into the warp's slots: record and base-2 exponent coefficients.
+// Loads kept entries [lo, lo + cnt) of a strip (visiting ranks from the forward
+// pass) into the warp's slots: record, base-2 exponent coefficients and the
+// Gaussian id (the 2D gradients are stored in Gaussian order, so that the
+// projection adjoint reads them contiguously).
 template <int NR, int FT>
 __device__ __forceinline__ void stage_kept(const RasterArgs& a, size_t vN, const uint32_t* kept, uint32_t lo, int cnt,
                                            float4 (*wrec)[NR + 1], uint32_t* wid) {
@@ -480,7 +484,7 @@ __device__ __forceinline__ void stage_kept(const RasterArgs& a, size_t vN, const
 #pragma unroll
         for (int k = 2; k < NR; k++) wrec[lane][k] = r[k];
         wrec[lane][NR] = entry_coeffs<FT>(q0, q1);
-        wid[lane] = s;
+        wid[lane] = a.sortid[vN + s];
     }
     __syncwarp();
 }
