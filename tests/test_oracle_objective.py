@@ -105,6 +105,55 @@ def test_paper_loss_gradient_finite_differences():
         assert abs(fd - want) < 1e-6 * max(1.0, abs(fd)), (c, i, j, fd, want)
 
 
+def test_recon_loss_weights_reduce_to_scaled_plain_loss():
+    # L_recon = mean d^2 + mean (M d)^2 + mean (I_gt d)^2 with d = I - I_gt:
+    # with every mask 1 and zero targets it is twice the plain focal-stack
+    # loss; with zero masks and a constant target c it is (1 + c^2) times it
+    # (lambda_1 = 0 in both; the gradients scale the same way)
+    C, H, W = 1, 12, 14
+    z = (0.0, 2e-3)
+    P = _rng(12).normal(size=(C, H, W)) + 1j * _rng(13).normal(size=(C, H, W))
+    zero = np.zeros((len(z), C, H, W))
+    l0, g0, _ = oracle.focal_stack_loss(P, zero, PITCH, (515e-9,), z)
+    l1, g1, _ = oracle.paper_loss(P, zero, np.ones((len(z), H, W)), PITCH, (515e-9,), z, lam=0.0)
+    assert abs(l1 - 2.0 * l0) < 1e-12 * l0
+    assert np.max(np.abs(g1 - 2.0 * g0)) < 1e-12 * np.max(np.abs(g0))
+    c = 0.7
+    Igt = np.full((len(z), C, H, W), c)
+    l0, g0, _ = oracle.focal_stack_loss(P, Igt, PITCH, (515e-9,), z)
+    l2, g2, _ = oracle.paper_loss(P, Igt, np.zeros((len(z), H, W)), PITCH, (515e-9,), z, lam=0.0)
+    assert abs(l2 - (1 + c * c) * l0) < 1e-12 * l0
+    assert np.max(np.abs(g2 - (1 + c * c) * g0)) < 1e-12 * np.max(np.abs(g0))
+
+
+def test_adan_matches_the_algorithm_in_its_authors_notation():
+    # Adan as its authors state it (Xie et al., Algorithm 1), with small
+    # momentum coefficients a = 1 - beta:
+    #   m_k = (1 - a1) m + a1 g_k,  v_k = (1 - a2) v + a2 (g_k - g_{k-1}),
+    #   n_k = (1 - a3) n + a3 (g_k + (1 - a2)(g_k - g_{k-1}))^2,
+    #   theta <- theta - lr (m_k + (1 - a2) v_k) / (sqrt(n_k) + eps),
+    # started with m = g_0, v = 0, n = g_0^2 and v_1 = g_1 - g_0.
+    rng = _rng(14)
+    a1, a2, a3 = 0.1, 0.08, 0.01
+    lr, eps = 0.02, 1e-8
+    gs = [rng.normal(size=5) for _ in range(7)]
+    th = rng.normal(size=5)
+    m, v, n = gs[0].copy(), np.zeros(5), gs[0] ** 2
+    th_ref = [th - lr * m / (np.sqrt(n) + eps)]
+    for k in range(1, len(gs)):
+        dg = gs[k] - gs[k - 1]
+        m = (1 - a1) * m + a1 * gs[k]
+        v = dg if k == 1 else (1 - a2) * v + a2 * dg
+        n = (1 - a3) * n + a3 * (gs[k] + (1 - a2) * dg) ** 2
+        th_ref.append(th_ref[-1] - lr * (m + (1 - a2) * v) / (np.sqrt(n) + eps))
+    p, mo, vo, no = th.copy(), np.zeros(5), np.zeros(5), np.zeros(5)
+    prev = np.zeros(5)
+    for k, g in enumerate(gs):
+        p, mo, vo, no = oracle.adan_step(p, g, prev, mo, vo, no, k + 1, lr, 1 - a1, 1 - a2, 1 - a3, eps)
+        prev = g
+        assert np.allclose(p, th_ref[k], rtol=1e-13, atol=1e-15), k
+
+
 def test_adan_first_step_and_constant_gradient():
     # step 1: m = g, v = 0, n = g^2, so p moves by lr g / (|g| + eps); with a
     # constant gradient the difference terms vanish and every step does the same

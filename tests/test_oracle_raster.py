@@ -103,6 +103,36 @@ def test_projection_matches_numerical_jacobian():
         assert abs(pr["depth"][0] - (M[:3, :3] @ mean + M[:3, 3])[2]) < 1e-14
 
 
+def test_dilation_adds_to_the_2d_covariance():
+    # The 2D covariance gets + dilation * I (the low-pass the 3DGS rasterizer
+    # applies); the projected mean is untouched.
+    H, W = 40, 48
+    intr = np.array([300.0, 320.0, 23.5, 19.5])
+    g = _one([0.05, -0.03, 2.0], np.log([0.01, 0.02, 0.015]), [0.9, 0.1, -0.3, 0.2], 0.6, [1.0], [0.0], [0.0])
+    ex = oracle.project(g, np.eye(4), intr, H, W, oracle.EXACT_OPTS)
+    pr = oracle.project(g, np.eye(4), intr, H, W, dict(oracle.EXACT_OPTS, dilation=0.3))
+    assert np.allclose(pr["cov"][0] - ex["cov"][0], [0.3, 0.0, 0.3], rtol=0, atol=1e-12)
+    assert np.array_equal(pr["mu"][0], ex["mu"][0])
+
+
+def test_jacobian_clamp_closed_form():
+    # Beyond clip * tan(half field of view) the Jacobian of the pinhole map is
+    # taken at the clamped position t'_x = lim t_z, so the footprint of an
+    # axis-aligned Gaussian far off-axis is J' diag(s^2) J'^T with
+    # J' = [[f/z, 0, -f lim / z], [0, f/z, 0]]; the mean still projects exactly.
+    H, W, f = 40, 60, 100.0
+    intr = np.array([f, f, 29.5, 19.5])
+    z, x = 2.0, 1.5                      # x / z = 0.75 beyond lim = 1.3 * 30 / 100 = 0.39
+    s = np.array([0.03, 0.02, 0.01])
+    g = _one([x, 0.0, z], np.log(s), [1, 0, 0, 0], 0.5, [1.0], [0.0], [0.0])
+    pr = oracle.project(g, np.eye(4), intr, H, W, dict(oracle.EXACT_OPTS, clip=1.3))
+    lim = 1.3 * (W / 2) / f
+    J = np.array([[f / z, 0.0, -f * lim / z], [0.0, f / z, 0.0]])
+    Sig = J @ np.diag(s ** 2) @ J.T
+    assert np.allclose(pr["cov"][0], [Sig[0, 0], Sig[0, 1], Sig[1, 1]], rtol=1e-12)
+    assert abs(pr["mu"][0][0] - (f * x / z + 29.5)) < 1e-12
+
+
 def _golden():
     gs, ex = [], []
     with open(os.path.join(GOLDEN, "three_gaussians_one_pixel.txt")) as fh:
