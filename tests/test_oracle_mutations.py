@@ -90,6 +90,12 @@ C_CASES = [
      "gpl[(size_t)L * n + a] += drho;", GR.test_ste_plane_logit_gradient),
     ("dense plane-weight gradient without the opacity", "vg[K] = opac[n] * G;", "vg[K] = G;",
      RD.test_dense_gradient_matches_finite_differences),
+    ("support box too small", "double k = 2.0 * log(P.opac / opt[O_AMIN]);",
+     "double k = 0.5 * log(P.opac / opt[O_AMIN]);", R.test_reduces_to_textbook_alpha_blending),
+    ("support box axes swapped", "double rx = sqrt(k * P.cov[0]) + 1e-9, ry = sqrt(k * P.cov[2]) + 1e-9;",
+     "double rx = sqrt(k * P.cov[2]) + 1e-9, ry = sqrt(k * P.cov[0]) + 1e-9;",
+     R.test_reduces_to_textbook_alpha_blending),
+    ("back-to-front order not reversed", "if (order == 1)", "if (order == 2)", R.test_three_gaussians_golden_fixture),
 ]
 
 
