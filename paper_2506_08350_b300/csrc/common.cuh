@@ -95,6 +95,7 @@ struct hcgs_saved {
     hcgs::DevBuf dkey;     // [2][V][N] uint32 depth keys (sort ping-pong)
     hcgs::DevBuf dval;     // [2][V][N] uint32 Gaussian ids
     hcgs::DevBuf nvalid;   // [V] uint32 number of visible Gaussians per view
+    hcgs::DevBuf segoff;   // [V + 2] uint32 first instance of each view, M, the most instances of a view
     hcgs::DevBuf rank;     // [V][N] uint32 visiting rank of Gaussian n (~0u if culled)
     hcgs::DevBuf sortid;   // [V][N] uint32 Gaussian id at visiting rank s
     hcgs::DevBuf rec;      // [V][N][NR] float4 records in visiting order
@@ -235,11 +236,14 @@ hcgs_status raster_forward(hcgs_ctx* ctx, hcgs_saved* s, float2* U, float* T_out
 hcgs_status raster_backward(hcgs_ctx* ctx, hcgs_saved* s, const float2* gU, cudaStream_t st);
 hcgs_status project_backward(hcgs_ctx* ctx, hcgs_saved* s, const hcgs_gaussians* g,
                              const hcgs_gaussian_grads* gr, int accumulate, cudaStream_t st);
-// Stable LSD radix sort of nseg contiguous segments of seglen (key, value)
-// pairs on key bits [0, nbits); returns the buffer index (0 or 1) holding the
-// result.  keys/vals point at [2][nseg*seglen] ping-pong storage.
+// Stable LSD radix sort of nseg contiguous segments of (key, value) pairs on
+// key bits [0, nbits); returns the buffer index (0 or 1) holding the result.
+// keys/vals point at [2][total] ping-pong storage.  Without segoff the
+// segments are seglen long; with segoff (device, nseg + 1 offsets; seglen =
+// the longest segment) segment s is sorted on key - s keystep.
 hcgs_status radix_sort(hcgs_ctx* ctx, hcgs_saved* s, uint32_t* keys, uint32_t* vals, int nseg, size_t seglen,
-                       int nbits, int* which, cudaStream_t st);
+                       size_t total, const uint32_t* segoff, uint32_t keystep, int nbits, int* which,
+                       cudaStream_t st);
 // Exclusive scan of n uint32 counts (in place allowed); writes the total to
 // out[n] when with_total is set.  Totals must stay below 2^32.
 hcgs_status exclusive_scan(hcgs_ctx* ctx, hcgs_saved* s, const uint32_t* in, uint32_t* out, size_t n,

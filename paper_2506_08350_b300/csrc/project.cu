@@ -197,24 +197,48 @@ __global__ void k_bucket_bounds(const uint32_t* __restrict__ key, uint32_t M, ui
 }
 
 // ---------------------------------------------------------------------------
-// stable LSD radix sort (8-bit digits), segmented by fixed-length segments
+// stable LSD radix sort (8-bit digits), segmented: segments of a fixed length,
+// or (segoff given) segment s = [segoff[s], segoff[s + 1]) whose keys all lie
+// in [s keystep, (s + 1) keystep) and are sorted on key - s keystep.  The
+// segment is the most significant part of the order (the scan of the
+// histograms runs segment-major), so the result is the stable sort of the
+// whole array when the input is already grouped by segment.
 // ---------------------------------------------------------------------------
 constexpr int RS_THREADS = 256;
 constexpr int RS_IPT = 8;
 constexpr int RS_KPB = RS_THREADS * RS_IPT;
 
-__global__ void k_rs_hist(const uint32_t* __restrict__ keys, size_t seglen, int shift, int nblk,
-                          uint32_t* __restrict__ hist) {
+struct RsSeg {
+    size_t so, len;   // start and length of this block's segment
+    uint32_t kb;      // subtracted from the keys before the digit is taken
+};
+__device__ __forceinline__ RsSeg rs_segment(int seg, size_t seglen, const uint32_t* segoff, uint32_t keystep) {
+    RsSeg r;
+    if (segoff) {
+        r.so = segoff[seg];
+        r.len = segoff[seg + 1] - segoff[seg];
+        r.kb = (uint32_t)seg * keystep;
+    } else {
+        r.so = (size_t)seg * seglen;
+        r.len = seglen;
+        r.kb = 0u;
+    }
+    return r;
+}
+
+__global__ void k_rs_hist(const uint32_t* __restrict__ keys, size_t seglen, const uint32_t* __restrict__ segoff,
+                          uint32_t keystep, int shift, int nblk, uint32_t* __restrict__ hist) {
     __shared__ uint32_t h[256];
     const int seg = blockIdx.y, blk = blockIdx.x;
     h[threadIdx.x] = 0;
     __syncthreads();
+    const RsSeg sg = rs_segment(seg, seglen, segoff, keystep);
     const size_t beg = (size_t)blk * RS_KPB;
-    const uint32_t* k = keys + (size_t)seg * seglen;
+    const uint32_t* k = keys + sg.so;
 #pragma unroll
     for (int r = 0; r < RS_IPT; r++) {
         const size_t idx = beg + (size_t)r * RS_THREADS + threadIdx.x;
-        if (idx < seglen) atomicAdd(&h[(k[idx] >> shift) & 255u], 1u);
+        if (idx < sg.len) atomicAdd(&h[((k[idx] - sg.kb) >> shift) & 255u], 1u);
     }
     __syncthreads();
     hist[((size_t)seg * 256 + threadIdx.x) * nblk + blk] = h[threadIdx.x];
@@ -232,7 +256,8 @@ __global__ void k_rs_hist(const uint32_t* __restrict__ keys, size_t seglen, int 
 __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t* __restrict__ kin,
                                                            const uint32_t* __restrict__ vin,
                                                            uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
-                                                           size_t seglen, int shift, int nblk,
+                                                           size_t seglen, const uint32_t* __restrict__ segoff,
+                                                           uint32_t keystep, int shift, int nblk,
                                                            const uint32_t* __restrict__ pos) {
     constexpr int NW = RS_THREADS / 32, PW = RS_KPB / NW;  // warps, elements per warp
     __shared__ uint32_t wh[NW][256];  // per-warp digit counters, then per-warp bases within a digit
@@ -241,9 +266,12 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t* __res
     const int seg = blockIdx.y, blk = blockIdx.x;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const unsigned lt = (1u << lane) - 1u;
+    const RsSeg sg = rs_segment(seg, seglen, segoff, keystep);
     const size_t beg = (size_t)blk * RS_KPB;
-    const size_t so = (size_t)seg * seglen;
-    const int nb = (int)min((size_t)RS_KPB, seglen - beg);  // elements of this block
+    if (beg >= sg.len) return;  // past the end of a shorter segment (uniform over the block)
+    const size_t so = sg.so;
+    const uint32_t kb = sg.kb;
+    const int nb = (int)min((size_t)RS_KPB, sg.len - beg);  // elements of this block
     for (int e = t; e < NW * 256; e += RS_THREADS) (&wh[0][0])[e] = 0;
     gbase[t] = pos[((size_t)seg * 256 + t) * nblk + blk];
     uint32_t key[RS_IPT], val[RS_IPT], rk[RS_IPT];
@@ -257,7 +285,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t* __res
 #pragma unroll
     for (int r = 0; r < RS_IPT; r++) {
         const bool ok = warp * PW + r * 32 + lane < nb;
-        const uint32_t d = ok ? ((key[r] >> shift) & 255u) : 256u;
+        const uint32_t d = ok ? (((key[r] - kb) >> shift) & 255u) : 256u;
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         const int leader = __ffs(peers) - 1;
         const uint32_t lrank = __popc(peers & lt);
@@ -294,7 +322,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t* __res
 #pragma unroll
     for (int r = 0; r < RS_IPT; r++) {
         if (warp * PW + r * 32 + lane < nb) {
-            const uint32_t d = (key[r] >> shift) & 255u;
+            const uint32_t d = ((key[r] - kb) >> shift) & 255u;
             const uint32_t lp = loff[d] + wh[warp][d] + rk[r];
             sk[lp] = key[r];
             sv[lp] = val[r];
@@ -303,7 +331,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t* __res
     __syncthreads();
     for (int i = t; i < nb; i += RS_THREADS) {
         const uint32_t k = sk[i];
-        const uint32_t d = (k >> shift) & 255u;
+        const uint32_t d = ((k - kb) >> shift) & 255u;
         const uint32_t p = gbase[d] + (uint32_t)i - loff[d];
         kout[p] = k;
         vout[p] = sv[i];
@@ -425,15 +453,36 @@ static const unsigned long long* scan_total_ptr(hcgs_saved* s, size_t n) {
     return (const unsigned long long*)((char*)s->scan.p + scan_bsum_bytes(n));
 }
 
+// Segments of the bucket-instance array by view (instances are generated
+// view-major: view v owns [coff[v N], coff[(v + 1) N])): segoff[v] for
+// v < V, segoff[V] = M, and segoff[V + 1] = the most instances of one view.
+__global__ void k_view_segments(const uint32_t* __restrict__ coff, const unsigned long long* __restrict__ total,
+                                int V, int N, uint32_t* __restrict__ segoff) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    const uint32_t M = (uint32_t)*total;
+    uint32_t prev = 0, most = 0;
+    for (int v = 0; v <= V; v++) {
+        const uint32_t o = v < V ? coff[(size_t)v * N] : M;
+        segoff[v] = o;
+        if (v > 0) most = max(most, o - prev);
+        prev = o;
+    }
+    segoff[V + 1] = most;
+}
+
+// keys / vals hold two buffers of ``total`` elements each (the passes
+// ping-pong between them); *which tells the one holding the result.  Without
+// segoff: nseg segments of seglen elements; with segoff (device, nseg + 1
+// offsets): seglen is the longest segment.
 hcgs_status radix_sort(hcgs_ctx* ctx, hcgs_saved* s, uint32_t* keys, uint32_t* vals, int nseg, size_t seglen,
-                       int nbits, int* which, cudaStream_t st) {
+                       size_t total, const uint32_t* segoff, uint32_t keystep, int nbits, int* which,
+                       cudaStream_t st) {
     *which = 0;
     if (seglen == 0 || nseg == 0) return HCGS_OK;
     const int nblk = (int)((seglen + RS_KPB - 1) / RS_KPB);
     const size_t nh = (size_t)nseg * 256 * nblk;
     HCGS_CUDA(ctx, grow(ctx, s->hist, nh * sizeof(uint32_t), &s->bytes));
     uint32_t* hist = (uint32_t*)s->hist.p;
-    const size_t total = (size_t)nseg * seglen;
     int cur = 0;
     for (int shift = 0; shift < nbits; shift += 8) {
         uint32_t* kin = keys + (size_t)cur * total;
@@ -441,11 +490,14 @@ hcgs_status radix_sort(hcgs_ctx* ctx, hcgs_saved* s, uint32_t* keys, uint32_t* v
         uint32_t* kout = keys + (size_t)(1 - cur) * total;
         uint32_t* vout = vals + (size_t)(1 - cur) * total;
         dim3 grid(nblk, nseg);
-        HCGS_KERNEL(ctx, "k_rs_hist", st, k_rs_hist<<<grid, RS_THREADS, 0, st>>>(kin, seglen, shift, nblk, hist));
+        HCGS_KERNEL(ctx, "k_rs_hist", st,
+                    k_rs_hist<<<grid, RS_THREADS, 0, st>>>(kin, seglen, segoff, keystep, shift, nblk, hist));
         HCGS_LAUNCH(ctx, "k_rs_hist");
         hcgs_status e = exclusive_scan(ctx, s, hist, hist, nh, st);
         if (e) return e;
-        HCGS_KERNEL(ctx, "k_rs_scatter", st, k_rs_scatter<<<grid, RS_THREADS, 0, st>>>(kin, vin, kout, vout, seglen, shift, nblk, hist));
+        HCGS_KERNEL(ctx, "k_rs_scatter", st,
+                    k_rs_scatter<<<grid, RS_THREADS, 0, st>>>(kin, vin, kout, vout, seglen, segoff, keystep, shift,
+                                                              nblk, hist));
         HCGS_LAUNCH(ctx, "k_rs_scatter");
         cur = 1 - cur;
     }
@@ -499,7 +551,7 @@ hcgs_status project_and_bin(hcgs_ctx* ctx, hcgs_saved* s, const hcgs_gaussians* 
                                     (float4*)s->proj.p, (uint2*)s->rectn.p, dkey, dval));
     HCGS_LAUNCH(ctx, "k_project");
     int which = 0;
-    hcgs_status e = radix_sort(ctx, s, dkey, dval, V, N, 32, &which, st);
+    hcgs_status e = radix_sort(ctx, s, dkey, dval, V, N, VN, nullptr, 0u, 32, &which, st);
     if (e) return e;
     HCGS_KERNEL(ctx, "k_count_visible", st, k_count_visible<<<V, 1, 0, st>>>(dkey + (size_t)which * VN, N, (uint32_t*)s->nvalid.p));
     HCGS_KERNEL(ctx, "k_gather", st, k_gather<<<gridVN, T, 0, st>>>(a, dval + (size_t)which * VN, (const uint32_t*)s->nvalid.p,
@@ -509,8 +561,13 @@ hcgs_status project_and_bin(hcgs_ctx* ctx, hcgs_saved* s, const hcgs_gaussians* 
     HCGS_LAUNCH(ctx, "k_gather");
     uint32_t* coff = (uint32_t*)s->ccount.p;
     if ((e = exclusive_scan(ctx, s, coff, coff, VN, st))) return e;
-    // the instance count sizes the instance buffers: one readback
+    HCGS_CUDA(ctx, grow(ctx, s->segoff, (size_t)(V + 2) * sizeof(uint32_t), ob));
+    uint32_t* segoff = (uint32_t*)s->segoff.p;
+    HCGS_KERNEL(ctx, "k_view_segments", st, k_view_segments<<<1, 32, 0, st>>>(coff, scan_total_ptr(s, VN), V, N, segoff));
+    // the instance count sizes the instance buffers and the longest view the
+    // sort's grid: one readback
     HCGS_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, scan_total_ptr(s, VN), 8, cudaMemcpyDeviceToHost, st));
+    HCGS_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned + 3, segoff + V + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     // the device status word rides along: a bounded wait that ran out in an
     // earlier launch of this context is reported here
     HCGS_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned + 2, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -534,7 +591,12 @@ hcgs_status project_and_bin(hcgs_ctx* ctx, hcgs_saved* s, const hcgs_gaussians* 
     HCGS_KERNEL(ctx, "k_inst_gen", st, k_inst_gen<<<gridVN, T, 0, st>>>(a, coff, (const uint2*)s->rects.p, (const int*)s->planes.p,
                                      (const uint32_t*)s->nvalid.p, ikey, ival));
     HCGS_LAUNCH(ctx, "k_inst_gen");
-    if ((e = radix_sort(ctx, s, ikey, ival, 1, (size_t)M, bits_for(NB), &which, st))) return e;
+    // bucket ids are view-major (v L ctY ctX + within-view bucket) and the
+    // instances already grouped by view: each view's segment is sorted on its
+    // within-view bucket (fewer key bits, fewer passes than the whole id)
+    const uint32_t NBv = (uint32_t)(L * s->ctX * s->ctY);
+    const size_t most = ctx->h_pinned[3];
+    if ((e = radix_sort(ctx, s, ikey, ival, V, most, (size_t)M, segoff, NBv, bits_for(NBv), &which, st))) return e;
     const uint32_t* skey = ikey + (size_t)which * M;
     s->list = ival + (size_t)which * M;
     HCGS_KERNEL(ctx, "k_bucket_bounds", st, k_bucket_bounds<<<(unsigned)((M + 1 + T - 1) / T), T, 0, st>>>(skey, (uint32_t)M, (uint32_t)NB,
@@ -550,7 +612,9 @@ hcgs_status project_and_bin(hcgs_ctx* ctx, hcgs_saved* s, const hcgs_gaussians* 
         uint32_t* aval = (uint32_t*)s->aval.p;
         HCGS_KERNEL(ctx, "k_inst_gen_all", st, k_inst_gen_all<<<gridVN, T, 0, st>>>(a, coff, (const uint2*)s->rects.p,
                                                                              (const uint32_t*)s->nvalid.p, akey, aval));
-        if ((e = radix_sort(ctx, s, akey, aval, 1, (size_t)M, bits_for(NBA), &which, st))) return e;
+        const uint32_t NBAv = (uint32_t)(s->ctX * s->ctY);
+        if ((e = radix_sort(ctx, s, akey, aval, V, most, (size_t)M, segoff, NBAv, bits_for(NBAv), &which, st)))
+            return e;
         s->alist = aval + (size_t)which * M;
         HCGS_KERNEL(ctx, "k_bucket_bounds", st,
                     k_bucket_bounds<<<(unsigned)((M + 1 + T - 1) / T), T, 0, st>>>(akey + (size_t)which * M, (uint32_t)M,
