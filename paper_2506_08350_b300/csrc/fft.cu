@@ -591,7 +591,10 @@ struct RowSmem {
     static constexpr int W = RP::N, HS = hq_stride(RP::N);
     static constexpr int XS = (RP::smem_slots() + 1) & ~1;     // exchange (float2, even)
     static constexpr int IN = WITH_INPUT ? 2 * W : 0;          // input rows
-    static constexpr size_t bytes = (size_t)(XS + IN + 2 * HS) * sizeof(float2) + 2 * sizeof(uint64_t);
+    using SI = typename RP::template SB<true>;
+    // the row's spectrum, held across the planes (spread pass), thread-major
+    static constexpr int SP = WITH_INPUT ? 0 : ((SI::U * SI::RAD * RP::T + 1) & ~1);
+    static constexpr size_t bytes = (size_t)(XS + IN + 2 * HS + SP) * sizeof(float2) + 2 * sizeof(uint64_t);
 };
 
 // If a bulk copy for plane l does not arrive within the bounded wait, the CTA
@@ -703,7 +706,7 @@ __global__ void __launch_bounds__(RP::T, RP::N == 1920 ? 3 : RP::MINB)
 
 // out[b][l][c][i] = IDFT( Hsel_l * DFT(in[b][c][i]) )
 template <bool CONJ, class RP>
-__global__ void __launch_bounds__(RP::T, RP::MINB)
+__global__ void __launch_bounds__(RP::T, RP::N == 1920 ? 3 : RP::MINB)
     k_rows_spread_reg(const float2* __restrict__ in, float2* __restrict__ out, int L, int C, int H,
                       const float2* __restrict__ hq, const float2* __restrict__ tw, int* __restrict__ status) {
     using namespace rfft;
@@ -714,7 +717,8 @@ __global__ void __launch_bounds__(RP::T, RP::MINB)
     extern __shared__ __align__(16) float2 sm[];
     float2* xb = sm;
     float2* hb = sm + SM::XS;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(hb + 2 * HS);
+    float2* sp = hb + 2 * HS;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sp + SM::SP);
     const int b = blockIdx.x, i = blockIdx.y, c = blockIdx.z;
     const int ky = mirror(i, H);
     const float2* h0 = hq + ((size_t)c * L * (H / 2 + 1) + ky) * HS;
@@ -731,7 +735,9 @@ __global__ void __launch_bounds__(RP::T, RP::MINB)
         if (L > 1) issue(1, 1);
     }
     __syncthreads();
-    float2 spec[SI::U][SI::RAD];
+    // the row's spectrum stays in shared memory (each thread its own items,
+    // thread-major) rather than in registers across the plane loop
+    auto spec = [&](int a, int r) -> float2& { return sp[(a * SI::RAD + r) * RP::T + threadIdx.x]; };
     {
         float2 v[SF::U][SF::RAD];
         load_row<SF>(v, in + (((size_t)b * C + c) * H + i) * W);
@@ -739,7 +745,7 @@ __global__ void __launch_bounds__(RP::T, RP::MINB)
             static_assert(Shape<decltype(vo)>::R == SI::RAD && Shape<decltype(vo)>::U == SI::U,
                           "the inverse pass must start with the forward pass's last radix");
             sfor<SI::U>([&](auto a) {
-                sfor<SI::RAD>([&](auto r) { spec[HCGS_CI(a)][HCGS_CI(r)] = vo[HCGS_CI(a)][HCGS_CI(r)]; });
+                sfor<SI::RAD>([&](auto r) { spec(HCGS_CI(a), HCGS_CI(r)) = vo[HCGS_CI(a)][HCGS_CI(r)]; });
             });
         });
     }
@@ -760,7 +766,7 @@ __global__ void __launch_bounds__(RP::T, RP::MINB)
                 constexpr int r = HCGS_CI(rr);
                 float2 h = okj ? hrow[mirror(j + r * SI::M, W)] : make_float2(0.f, 0.f);
                 if (CONJ) h.y = -h.y;
-                v[u][r] = cmul(spec[u][r], h);
+                v[u][r] = cmul(spec(u, r), h);
             });
         });
         __syncthreads();  // the transfer-function row is consumed
