@@ -577,6 +577,11 @@ def run_ours(args):
             tr = traffic.get(name)
             if tr and tr.get("source_sha") == src_hash(KERNEL_SOURCE[name]) and tr.get("workload") == wl.name:
                 ent["traffic_bytes_per_launch"] = tr["dram_bytes_per_launch"]
+                # the DRAM rate those bytes make at the measured launch time,
+                # beside the kernel's own (ALU) roofline
+                ms_launch = ms_tot / max(cnt, 1)
+                ent["dram_gbs"] = tr["dram_bytes_per_launch"] / (ms_launch / 1e3) / 1e9
+                ent["dram_frac_of_hbm_peak"] = ent["dram_gbs"] / hbm_peak
         table[name] = ent
     dom = max((k for k in table if "bound" in table[k]), key=lambda k: table[k]["ms_per_step"], default=None)
     if dom:
@@ -586,6 +591,7 @@ def run_ours(args):
         result["roofline"] = {"kernel": dom, "bound": d["bound"], "achieved": ach_launch, "peak": d["peak"],
                               "unit": d["unit"], "frac": d["frac"],
                               "traffic": d.get("traffic_bytes_per_launch"),
+                              "traffic_gbs": d.get("dram_gbs"),
                               "peak_source": (hbm_src if d["bound"] == "hbm" else
                                               "148 SMs x 128 FP32 lanes x median SM clock %.0f MHz" % f_mhz),
                               "launches_per_step": lps}
