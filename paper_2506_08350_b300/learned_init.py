@@ -7,7 +7,7 @@ per wavelength.  It is trained, with the library's own kernels (forward,
 reverse mode, MSE loss, Adam on FP32 master weights, BF16 cast), on scenes
 that the plain optimiser produced; the plain initialisation (amplitude = RGB,
 phase uniform in [0, 2 pi)) stays as the fallback and as the baseline it is
-judged against.
+compared with.
 
 Python here only sequences library calls and keeps tensors; every
 arithmetic step runs in libhcgs kernels (``hcgs_init_*``, ``hcgs_mlp_*``,
