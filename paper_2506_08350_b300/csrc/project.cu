@@ -138,28 +138,77 @@ __global__ void k_gather(ProjArgs a, const uint32_t* __restrict__ sorted_id, con
     ccount[vn + s2] = cnt;
 }
 
-// One instance per (visible Gaussian, covered coarse bucket), in visiting order.
+// One instance per (visible Gaussian, covered coarse bucket), in visiting
+// order: entry i = (view, rank) owns positions [coff[i], coff[i] + n_i) for
+// its buckets [cx0, cx0 + cw) x [cy0, cy0 + ch), row by row.  A warp's 32
+// entries own one contiguous range, so the warp writes it 32 instances at a
+// time (coalesced), each lane finding the entry that owns its position by a
+// binary search over the warp's running counts, instead of one entry per lane.
+struct InstSrc {
+    uint32_t cnt = 0, start = 0, cw = 1, cx0 = 0, cy0 = 0, kb = 0, s = 0;
+};
+
+// The instance source of entry i (view v, visiting rank s): its bucket
+// rectangle; kb = the id of the entry's bucket row block (view, plane).
+__device__ __forceinline__ InstSrc inst_source(const ProjArgs& a, size_t i, const uint32_t* __restrict__ coff,
+                                               const uint2* __restrict__ rects, const int* __restrict__ planes,
+                                               const uint32_t* __restrict__ nvalid) {
+    InstSrc r;
+    if (i >= (size_t)a.V * a.N) return r;
+    const int v = (int)(i / a.N), s = (int)(i - (size_t)v * a.N);
+    if (s >= (int)nvalid[v]) return r;
+    const uint2 rc = rects[i];
+    const uint32_t tx0 = rc.x & 0xFFFFu, tx1 = rc.x >> 16, ty0 = rc.y & 0xFFFFu, ty1 = rc.y >> 16;
+    if (!(tx0 < tx1 && ty0 < ty1)) return r;
+    r.cx0 = tx0 / COARSE;
+    r.cy0 = ty0 / COARSE;
+    r.cw = (tx1 + COARSE - 1) / COARSE - r.cx0;
+    r.cnt = r.cw * ((ty1 + COARSE - 1) / COARSE - r.cy0);
+    r.start = coff[i];
+    // planes == nullptr: the all-plane lists (bucket id without the plane)
+    r.kb = planes ? ((uint32_t)v * a.L + (uint32_t)planes[i]) * a.ctY : (uint32_t)v * a.ctY;
+    r.s = (uint32_t)s;
+    return r;
+}
+
+__device__ __forceinline__ void emit_instances(const InstSrc& e, uint32_t ctX, uint32_t* __restrict__ ikey,
+                                               uint32_t* __restrict__ ival) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    uint32_t inc = e.cnt;  // inclusive running count over the warp's lanes
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(full, inc, o);
+        if (lane >= o) inc += y;
+    }
+    const uint32_t total = __shfl_sync(full, inc, 31);
+    const uint32_t excl = inc - e.cnt;
+    for (uint32_t b0 = 0; b0 < total; b0 += 32) {
+        const uint32_t idx = b0 + (uint32_t)lane;
+        int j = 0;  // the owner: the number of lanes whose running count is <= idx
+#pragma unroll
+        for (int b = 16; b > 0; b >>= 1) {
+            const uint32_t x = __shfl_sync(full, inc, j + b - 1);
+            if (x <= idx) j += b;
+        }
+        const uint32_t k = idx - __shfl_sync(full, excl, j);
+        const uint32_t start = __shfl_sync(full, e.start, j), w = __shfl_sync(full, e.cw, j);
+        const uint32_t x0 = __shfl_sync(full, e.cx0, j), y0 = __shfl_sync(full, e.cy0, j);
+        const uint32_t kb = __shfl_sync(full, e.kb, j), sv = __shfl_sync(full, e.s, j);
+        if (idx < total) {
+            const uint32_t dy = k / w, dx = k - dy * w;
+            ikey[start + k] = (kb + y0 + dy) * ctX + x0 + dx;
+            ival[start + k] = sv;
+        }
+    }
+}
+
 __global__ void k_inst_gen(ProjArgs a, const uint32_t* __restrict__ coff, const uint2* __restrict__ rects,
                            const int* __restrict__ planes, const uint32_t* __restrict__ nvalid,
                            uint32_t* __restrict__ ikey, uint32_t* __restrict__ ival) {
     const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    if (i >= (size_t)a.V * a.N) return;
-    const int v = (int)(i / a.N), s = (int)(i - (size_t)v * a.N);
-    if (s >= (int)nvalid[v]) return;
-    const uint2 rc = rects[i];
-    const uint32_t tx0 = rc.x & 0xFFFFu, tx1 = rc.x >> 16, ty0 = rc.y & 0xFFFFu, ty1 = rc.y >> 16;
-    if (!(tx0 < tx1 && ty0 < ty1)) return;
-    const uint32_t cx0 = tx0 / COARSE, cx1 = (tx1 + COARSE - 1) / COARSE;
-    const uint32_t cy0 = ty0 / COARSE, cy1 = (ty1 + COARSE - 1) / COARSE;
-    const uint32_t pl = (uint32_t)planes[i];
-    uint32_t pos = coff[i];
-    const uint32_t bb = ((uint32_t)v * a.L + pl) * a.ctY;
-    for (uint32_t cy = cy0; cy < cy1; cy++)
-        for (uint32_t cx = cx0; cx < cx1; cx++) {
-            ikey[pos] = (bb + cy) * a.ctX + cx;
-            ival[pos] = (uint32_t)s;
-            pos++;
-        }
+    if (i - (threadIdx.x & 31) >= (size_t)a.V * a.N) return;  // the whole warp is past the end
+    emit_instances(inst_source(a, i, coff, rects, planes, nvalid), (uint32_t)a.ctX, ikey, ival);
 }
 
 // The same instances with the plane left out of the bucket id (per view and
@@ -168,22 +217,8 @@ __global__ void k_inst_gen_all(ProjArgs a, const uint32_t* __restrict__ coff, co
                                const uint32_t* __restrict__ nvalid, uint32_t* __restrict__ ikey,
                                uint32_t* __restrict__ ival) {
     const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    if (i >= (size_t)a.V * a.N) return;
-    const int v = (int)(i / a.N), s = (int)(i - (size_t)v * a.N);
-    if (s >= (int)nvalid[v]) return;
-    const uint2 rc = rects[i];
-    const uint32_t tx0 = rc.x & 0xFFFFu, tx1 = rc.x >> 16, ty0 = rc.y & 0xFFFFu, ty1 = rc.y >> 16;
-    if (!(tx0 < tx1 && ty0 < ty1)) return;
-    const uint32_t cx0 = tx0 / COARSE, cx1 = (tx1 + COARSE - 1) / COARSE;
-    const uint32_t cy0 = ty0 / COARSE, cy1 = (ty1 + COARSE - 1) / COARSE;
-    uint32_t pos = coff[i];
-    const uint32_t bb = (uint32_t)v * a.ctY;
-    for (uint32_t cy = cy0; cy < cy1; cy++)
-        for (uint32_t cx = cx0; cx < cx1; cx++) {
-            ikey[pos] = (bb + cy) * a.ctX + cx;
-            ival[pos] = (uint32_t)s;
-            pos++;
-        }
+    if (i - (threadIdx.x & 31) >= (size_t)a.V * a.N) return;
+    emit_instances(inst_source(a, i, coff, rects, nullptr, nvalid), (uint32_t)a.ctX, ikey, ival);
 }
 
 // Bucket start offsets from the sorted bucket ids: off[b] = first position
