@@ -83,28 +83,37 @@ __device__ __forceinline__ size_t strip_list_base(uint32_t beg, uint32_t n, int 
 }
 
 // Can Gaussian (mu, conic A B C, opacity o) reach alpha >= alpha_min at any
-// pixel centre of the strip x in [x0, x0 + 15], y in [y0, y0 + 7]?  For each
-// row the footprint quadratic q = A dx^2 + 2 B dx dy + C dy^2 is minimised
-// over the row segment (a convex 1D problem: the unconstrained minimiser
-// clamped to the segment) and compared with 2 ln(o / alpha_min), with a
-// relative and absolute margin far above FP32 rounding.  Never rejects a
-// pixel that the per-pixel test would accept, so skipping is exact.
+// pixel centre of the strip x in [x0, x0 + 15], y in [y0, y0 + 7]?  The
+// footprint quadratic q = A dx^2 + 2 B dx dy + C dy^2 is minimised over the
+// strip's (continuous) box and compared with 2 ln(o / alpha_min), with a
+// relative and absolute margin far above FP32 rounding: zero when the centre
+// lies in the box, else the minimum of the convex q lies on an edge, where it
+// is a 1D convex problem (the unconstrained minimiser clamped to the edge).
+// The box contains every pixel centre of the strip, so this never rejects a
+// pixel that the per-pixel test would accept: skipping is exact.
 __device__ __forceinline__ bool strip_hits(float4 r0, float Cc, float o, float x0, float y0, float amin) {
     if (amin <= 0.f) return true;
     if (o < amin) return false;
+    const float x1 = x0 + 15.f, y1 = y0 + 7.f;
+    if (r0.x >= x0 && r0.x <= x1 && r0.y >= y0 && r0.y <= y1) return true;
     const float k2 = 2.f * __logf(o / amin) * 1.001f + 1e-3f;
-    const float x1 = x0 + 15.f;
-    const float slope = r0.w / r0.z;
-    bool hit = false;
-#pragma unroll
-    for (int r = 0; r < 8; r++) {
-        const float dy = (y0 + (float)r) - r0.y;
-        const float xs = fminf(fmaxf(r0.x - slope * dy, x0), x1);
-        const float dx = xs - r0.x;
-        const float q = r0.z * dx * dx + 2.f * r0.w * dx * dy + Cc * dy * dy;
-        hit |= q <= k2;
+    const float A = r0.z, B = r0.w;
+    const float sx = __fdividef(B, A), sy = __fdividef(B, Cc);
+    auto q = [&](float dx, float dy) { return fmaf(A * dx, dx, fmaf(2.f * B * dx, dy, Cc * dy * dy)); };
+    float m;
+    {   // horizontal edges y = y0, y1
+        const float d0 = y0 - r0.y, d1 = y1 - r0.y;
+        const float e0 = fminf(fmaxf(r0.x - sx * d0, x0), x1) - r0.x;
+        const float e1 = fminf(fmaxf(r0.x - sx * d1, x0), x1) - r0.x;
+        m = fminf(q(e0, d0), q(e1, d1));
     }
-    return hit;
+    {   // vertical edges x = x0, x1
+        const float d0 = x0 - r0.x, d1 = x1 - r0.x;
+        const float e0 = fminf(fmaxf(r0.y - sy * d0, y0), y1) - r0.y;
+        const float e1 = fminf(fmaxf(r0.y - sy * d1, y0), y1) - r0.y;
+        m = fminf(m, fminf(q(d0, e0), q(d1, e1)));
+    }
+    return m <= k2;
 }
 
 // Per-entry coefficients staged with the record.  FP32 tier: the base-2
