@@ -36,6 +36,7 @@ struct RasterArgs {
     uint32_t* slist;
     int V, N, L, H, W, tilesX, tilesY, ctX, ctY;
     float amin, amax, teps;
+    float inv_amin;  // 1 / alpha_min (0 when alpha_min = 0)
 };
 
 static RasterArgs make_raster_args(const hcgs_saved* s) {
@@ -49,6 +50,7 @@ static RasterArgs make_raster_args(const hcgs_saved* s) {
     a.V = s->V; a.N = s->N; a.L = s->L; a.H = s->H; a.W = s->W;
     a.tilesX = s->tilesX; a.tilesY = s->tilesY; a.ctX = s->ctX; a.ctY = s->ctY;
     a.amin = s->opts.alpha_min; a.amax = s->opts.alpha_max; a.teps = s->opts.T_eps;
+    a.inv_amin = a.amin > 0.f ? 1.f / a.amin : 0.f;
     return a;
 }
 
@@ -91,12 +93,13 @@ __device__ __forceinline__ size_t strip_list_base(uint32_t beg, uint32_t n, int 
 // is a 1D convex problem (the unconstrained minimiser clamped to the edge).
 // The box contains every pixel centre of the strip, so this never rejects a
 // pixel that the per-pixel test would accept: skipping is exact.
-__device__ __forceinline__ bool strip_hits(float4 r0, float Cc, float o, float x0, float y0, float amin) {
+__device__ __forceinline__ bool strip_hits(float4 r0, float Cc, float o, float x0, float y0, float amin,
+                                           float inv_amin) {
     if (amin <= 0.f) return true;
     if (o < amin) return false;
     const float x1 = x0 + 15.f, y1 = y0 + 7.f;
     if (r0.x >= x0 && r0.x <= x1 && r0.y >= y0 && r0.y <= y1) return true;
-    const float k2 = 2.f * __logf(o / amin) * 1.001f + 1e-3f;
+    const float k2 = 2.f * __logf(o * inv_amin) * 1.001f + 1e-3f;
     const float A = r0.z, B = r0.w;
     const float sx = __fdividef(B, A), sy = __fdividef(B, Cc);
     auto q = [&](float dx, float dy) { return fmaf(A * dx, dx, fmaf(2.f * B * dx, dy, Cc * dy * dy)); };
@@ -126,7 +129,7 @@ __device__ __forceinline__ float4 entry_coeffs(float4 q0, float4 q1) {
         return make_float4(sa, sc, 2.f * q0.w / (sa * sc), 0.f);
     }
     constexpr float L2E = 1.4426950408889634f;
-    return make_float4(-0.5f * L2E * q0.z, -L2E * q0.w, -0.5f * L2E * q1.x, log2f(q1.y));
+    return make_float4(-0.5f * L2E * q0.z, -L2E * q0.w, -0.5f * L2E * q1.x, __log2f(q1.y));
 }
 
 // Stream 32 list positions [p0, p0 + 32) of the bucket for one warp: keep the
@@ -151,7 +154,7 @@ __device__ __forceinline__ int stage_warp(const RasterArgs& a, size_t vN, uint32
             const float4* r = a.rec + (vN + s) * NR;
             q0 = r[0];
             q1 = r[1];
-            ok = strip_hits(q0, q1.x, q1.y, sx0, sy0, a.amin);
+            ok = strip_hits(q0, q1.x, q1.y, sx0, sy0, a.amin, a.inv_amin);
         }
     }
     const unsigned m = __ballot_sync(0xffffffffu, ok);
