@@ -200,8 +200,13 @@ __device__ __forceinline__ bool may_clamp(float o, float amax) { return o > amax
 // conditioned for footprints of any size the quadratic is formed in the
 // footprint's normalised frame, u = dx sqrt(A), v = dy sqrt(C),
 // q = u^2 + 2 rho u v + v^2 with rho = B / sqrt(A C) in (-1, 1), all O(1)
-// inside the support; the exponent -q log2(e) / 2 is a quadratic in v whose
-// coefficients are formed once per thread and entry.  Accumulation stays FP32.
+// inside the support.  The thread's pixels share a column, so u is fixed per
+// thread and entry, and completing the square in v splits the exponent
+// -q log2(e) / 2 = -c (1 - rho^2) u^2 - c w^2 (c = log2(e) / 2, w = v + rho u):
+// the first part, constant along the column, is taken in FP32 into the
+// factor o 2^(-c (1 - rho^2) u^2) once per thread and entry; only -c w^2,
+// never larger in magnitude than the whole exponent, and its exp() run in
+// packed half precision per pixel pair.  Accumulation stays FP32.
 template <int FT>
 struct Half2Of;
 template <>
@@ -219,15 +224,16 @@ struct Half2Of<2> {
     static __device__ __forceinline__ float2 to2(T x) { return __bfloat1622float2(x); }
 };
 
+// One pixel pair: w = dy sqrt(C) + rho u, then F 2^(-c w^2) with the
+// per-thread factor F = o 2^(-c (1 - rho^2) u^2).
 template <int FT, bool CL>
-__device__ __forceinline__ void eval_pair_h(float2 py2, float4 r0, float sc, typename Half2Of<FT>::T nc,
-                                            typename Half2Of<FT>::T a1, typename Half2Of<FT>::T a0, float o,
-                                            float amax, float2& dy2, float2& og2, float2& a2) {
+__device__ __forceinline__ void eval_pair_h(float2 py2, float4 r0, float sc, float ru, typename Half2Of<FT>::T nc,
+                                            float F, float amax, float2& dy2, float2& og2, float2& a2) {
     dy2 = __fadd2_rn(py2, f2(-r0.y));
-    const auto v = Half2Of<FT>::from2(__fmul2_rn(dy2, f2(sc)));
-    const auto e = __hfma2(__hfma2(nc, v, a1), v, a0);
+    const auto w = Half2Of<FT>::from2(__ffma2_rn(dy2, f2(sc), f2(ru)));
+    const auto e = __hmul2(__hmul2(nc, w), w);
     const float2 G2 = Half2Of<FT>::to2(h2exp2(e));
-    og2 = __fmul2_rn(f2(o), G2);
+    og2 = __fmul2_rn(f2(F), G2);
     a2 = CL ? make_float2(fminf(amax, og2.x), fminf(amax, og2.y)) : og2;
 }
 
@@ -255,15 +261,16 @@ __device__ __forceinline__ void eval_entry(const EntryX& x, float2 pyA, float2 p
                                            float amax, float2& dyA, float2& ogA, float2& aA, float2& dyB,
                                            float2& ogB, float2& aB) {
     if constexpr (FT != 0) {
-        // e = -(log2 e / 2)(u^2 + rho2 u v + v^2) = (nc v + a1) v + a0 in half
-        // (FT 1) or bfloat16 (FT 2) precision, with u = dx sqrt(A) fixed per
-        // thread and entry
+        // half (FT 1) or bfloat16 (FT 2) precision for -c w^2 and its exp();
+        // u = dx sqrt(A) and the factor F are fixed per thread and entry
         using H2 = typename Half2Of<FT>::T;
         const float u = x.dx * k.x;
         constexpr float c = 0.72134752044448170f;  // log2(e) / 2
-        const H2 nc = Half2Of<FT>::from(-c), a1 = Half2Of<FT>::from(-c * k.z * u), a0 = Half2Of<FT>::from(-c * u * u);
-        eval_pair_h<FT, CL>(pyA, r0, k.y, nc, a1, a0, r1.y, amax, dyA, ogA, aA);
-        eval_pair_h<FT, CL>(pyB, r0, k.y, nc, a1, a0, r1.y, amax, dyB, ogB, aB);
+        const float ru = 0.5f * k.z * u;            // rho u (k.z = 2 rho)
+        const float F = r1.y * ex2_approx(c * fmaf(ru, ru, -u * u));
+        const H2 nc = Half2Of<FT>::from(-c);
+        eval_pair_h<FT, CL>(pyA, r0, k.y, ru, nc, F, amax, dyA, ogA, aA);
+        eval_pair_h<FT, CL>(pyB, r0, k.y, ru, nc, F, amax, dyB, ogB, aB);
     } else {
         dyA = __fadd2_rn(pyA, f2(-r0.y));
         float2 e = __ffma2_rn(f2(x.bdx), dyA, f2(x.t0));

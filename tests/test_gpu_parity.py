@@ -210,12 +210,9 @@ def test_render_backward_vs_oracle(P, ctx, opts_name, order):
     base = {"default": P.DEFAULT_OPTS, "exact": P.EXACT_OPTS,
             "fp16": dict(P.DEFAULT_OPTS, footprint=1), "bf16": dict(P.DEFAULT_OPTS, footprint=2)}[opts_name]
     opts = dict(base, order=order)
-    # FP16x2 meets the 1e-2 bound of the reduced-precision tiers with margin
-    # (<= 4e-3); in BF16x2 the exponent is rounded to an 8-bit mantissa, which
-    # at the footprint's tails (|exponent| up to log2(o / alpha_min) ~ 8) is
-    # ~1 % of G, and the tail-weighted log-scale and rotation gradients sit
-    # at that level (1.0e-2)
-    tol = {"fp16": 1e-2, "bf16": 1.5e-2}.get(opts_name, 1e-3)
+    # the 1e-2 bound of the reduced-precision tiers (measured: FP16x2 <= 1.1e-3,
+    # BF16x2 <= 8e-3, the tail-weighted log-scale and rotation gradients)
+    tol = {"fp16": 1e-2, "bf16": 1e-2}.get(opts_name, 1e-3)
     V = 2
     vm, it = cams(V, o.H, o.W, seed=2)
     gd = dev(g)
