@@ -224,14 +224,15 @@ struct Half2Of<2> {
     static __device__ __forceinline__ float2 to2(T x) { return __bfloat1622float2(x); }
 };
 
-// One pixel pair: w = dy sqrt(C) + rho u, then F 2^(-c w^2) with the
-// per-thread factor F = o 2^(-c (1 - rho^2) u^2).
+// One pixel pair: w' = sqrt(c) (dy sqrt(C) + rho u), then F 2^(-w'^2) with
+// the per-thread factor F = o 2^(-c (1 - rho^2) u^2); scs = sqrt(c C),
+// rus = sqrt(c) rho u.
 template <int FT, bool CL>
-__device__ __forceinline__ void eval_pair_h(float2 py2, float4 r0, float sc, float ru, typename Half2Of<FT>::T nc,
-                                            float F, float amax, float2& dy2, float2& og2, float2& a2) {
+__device__ __forceinline__ void eval_pair_h(float2 py2, float4 r0, float scs, float rus, float F, float amax,
+                                            float2& dy2, float2& og2, float2& a2) {
     dy2 = __fadd2_rn(py2, f2(-r0.y));
-    const auto w = Half2Of<FT>::from2(__ffma2_rn(dy2, f2(sc), f2(ru)));
-    const auto e = __hmul2(__hmul2(nc, w), w);
+    const auto w = Half2Of<FT>::from2(__ffma2_rn(dy2, f2(scs), f2(rus)));
+    const auto e = __hmul2(__hneg2(w), w);
     const float2 G2 = Half2Of<FT>::to2(h2exp2(e));
     og2 = __fmul2_rn(f2(F), G2);
     a2 = CL ? make_float2(fminf(amax, og2.x), fminf(amax, og2.y)) : og2;
@@ -263,14 +264,13 @@ __device__ __forceinline__ void eval_entry(const EntryX& x, float2 pyA, float2 p
     if constexpr (FT != 0) {
         // half (FT 1) or bfloat16 (FT 2) precision for -c w^2 and its exp();
         // u = dx sqrt(A) and the factor F are fixed per thread and entry
-        using H2 = typename Half2Of<FT>::T;
         const float u = x.dx * k.x;
         constexpr float c = 0.72134752044448170f;  // log2(e) / 2
+        constexpr float sqc = 0.84932180028801904f;  // sqrt(c)
         const float ru = 0.5f * k.z * u;            // rho u (k.z = 2 rho)
         const float F = r1.y * ex2_approx(c * fmaf(ru, ru, -u * u));
-        const H2 nc = Half2Of<FT>::from(-c);
-        eval_pair_h<FT, CL>(pyA, r0, k.y, ru, nc, F, amax, dyA, ogA, aA);
-        eval_pair_h<FT, CL>(pyB, r0, k.y, ru, nc, F, amax, dyB, ogB, aB);
+        eval_pair_h<FT, CL>(pyA, r0, sqc * k.y, sqc * ru, F, amax, dyA, ogA, aA);
+        eval_pair_h<FT, CL>(pyB, r0, sqc * k.y, sqc * ru, F, amax, dyB, ogB, aB);
     } else {
         dyA = __fadd2_rn(pyA, f2(-r0.y));
         float2 e = __ffma2_rn(f2(x.bdx), dyA, f2(x.t0));

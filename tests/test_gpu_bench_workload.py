@@ -27,10 +27,10 @@ torch = pytest.importorskip("torch")
 
 V0, R0, R1 = 5, 480, 576  # sampled view and row band
 # relative L2 bounds: fields, gradients.  The reduced-precision tiers' bound
-# is 1e-2; FP16x2 meets it everywhere.  BF16x2 meets it on the fields, but at
-# this size its rotation gradient sits at it (1.03e-2): the 8-bit mantissa of
-# the exponent's per-pixel part is the format's limit at the footprint's
-# tails, so the bound checked for its gradients is 1.5e-2.
+# is 1e-2; FP16x2 meets it with margin.  BF16x2 meets it too, but at this
+# size its rotation gradient comes close (9.5e-3): the 8-bit mantissa of the
+# exponent's per-pixel part is the format's limit at the footprint's tails,
+# so the bound checked for its gradients leaves room for the draw: 1.5e-2.
 TOL = {0: (1e-4, 1e-3), 1: (1e-2, 1e-2), 2: (1e-2, 1.5e-2)}
 
 

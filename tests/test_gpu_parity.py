@@ -210,7 +210,7 @@ def test_render_backward_vs_oracle(P, ctx, opts_name, order):
     base = {"default": P.DEFAULT_OPTS, "exact": P.EXACT_OPTS,
             "fp16": dict(P.DEFAULT_OPTS, footprint=1), "bf16": dict(P.DEFAULT_OPTS, footprint=2)}[opts_name]
     opts = dict(base, order=order)
-    # the 1e-2 bound of the reduced-precision tiers (measured: FP16x2 <= 1.1e-3,
+    # the 1e-2 bound of the reduced-precision tiers (measured: FP16x2 <= 3.6e-3,
     # BF16x2 <= 8e-3, the tail-weighted log-scale and rotation gradients)
     tol = {"fp16": 1e-2, "bf16": 1e-2}.get(opts_name, 1e-3)
     V = 2
