@@ -671,6 +671,8 @@ __global__ void k_project_bwd(ProjArgs a, const float* __restrict__ means, const
     if (n >= a.N) return;
     const int C = a.C, G = g2d_count(C);
     float gm[3] = {0, 0, 0}, gls[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0};
+    float gsig[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // dL/dSigma summed over the views
+    bool any = false;
     float gol = 0.f, drho = 0.f;
     float gwr[MAX_C] = {0, 0, 0, 0}, gwi[MAX_C] = {0, 0, 0, 0};
     for (int v = 0; v < a.V; v++) {
@@ -694,7 +696,13 @@ __global__ void k_project_bwd(ProjArgs a, const float* __restrict__ means, const
         // power = 1/2 (A dx^2 + C dy^2) + B dx dy, d = pixel - mu:
         const float A = P.conic[0], B = P.conic[1], Cc = P.conic[2];
         const float2 gmu = make_float2(fmaf(A, g[0], B * g[1]), fmaf(B, g[0], Cc * g[1]));
-        project_one_backward(a, P, cam + 20 * v, gmu, -0.5f * g[2], -g[3], -0.5f * g[4], gm, gls, gq);
+        project_one_backward(a, P, cam + 20 * v, gmu, -0.5f * g[2], -g[3], -0.5f * g[4], gm, gsig);
+        any = true;
+    }
+    if (any) {
+        ProjF Q;
+        sigma_factors(log_scales + 3 * n, quats + 4 * n, Q);
+        sigma_backward(Q, gsig, gls, gq);
     }
     // appearance: w_c = a_c (cos phi_c, sin phi_c)
     for (int c = 0; c < C; c++) {

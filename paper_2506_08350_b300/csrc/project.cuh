@@ -43,6 +43,19 @@ struct ProjF {
     float o, depth;
 };
 
+// The view-independent factors of the 3D covariance: the normalised
+// quaternion, its rotation R and the scales s = exp(log_scale).
+__device__ __forceinline__ void sigma_factors(const float* ls, const float* q, ProjF& P) {
+    const float qq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+    P.qnorm = sqrtf(qq);
+    for (int i = 0; i < 4; i++) P.qn[i] = q[i] / P.qnorm;
+    const float w = P.qn[0], x = P.qn[1], y = P.qn[2], z = P.qn[3];
+    P.R[0] = 1.f - 2.f * (y * y + z * z); P.R[1] = 2.f * (x * y - w * z); P.R[2] = 2.f * (x * z + w * y);
+    P.R[3] = 2.f * (x * y + w * z); P.R[4] = 1.f - 2.f * (x * x + z * z); P.R[5] = 2.f * (y * z - w * x);
+    P.R[6] = 2.f * (x * z - w * y); P.R[7] = 2.f * (y * z + w * x); P.R[8] = 1.f - 2.f * (x * x + y * y);
+    for (int i = 0; i < 3; i++) P.s[i] = expf(ls[i]);
+}
+
 __device__ __forceinline__ void project_one(const ProjArgs& a, const float* mean, const float* ls, const float* q,
                                             float logit, const float* cam, ProjF& P) {
     const float* Vm = cam;
@@ -56,14 +69,7 @@ __device__ __forceinline__ void project_one(const ProjArgs& a, const float* mean
     P.conic[0] = P.conic[1] = P.conic[2] = 0.f;
     P.cov[0] = P.cov[1] = P.cov[2] = 0.f;
     if (!(P.t[2] >= a.near_z)) return;
-    const float qq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
-    P.qnorm = sqrtf(qq);
-    for (int i = 0; i < 4; i++) P.qn[i] = q[i] / P.qnorm;
-    const float w = P.qn[0], x = P.qn[1], y = P.qn[2], z = P.qn[3];
-    P.R[0] = 1.f - 2.f * (y * y + z * z); P.R[1] = 2.f * (x * y - w * z); P.R[2] = 2.f * (x * z + w * y);
-    P.R[3] = 2.f * (x * y + w * z); P.R[4] = 1.f - 2.f * (x * x + z * z); P.R[5] = 2.f * (y * z - w * x);
-    P.R[6] = 2.f * (x * z - w * y); P.R[7] = 2.f * (y * z + w * x); P.R[8] = 1.f - 2.f * (x * x + y * y);
-    for (int i = 0; i < 3; i++) P.s[i] = expf(ls[i]);
+    sigma_factors(ls, q, P);
     for (int i = 0; i < 3; i++)
         for (int j = 0; j < 3; j++) {
             float acc = 0.f;
@@ -106,11 +112,13 @@ __device__ __forceinline__ void project_one(const ProjArgs& a, const float* mean
     P.valid = true;
 }
 
-// Accumulates dL/d(mean, log_scale, quat) from dL/dmu and dL/d(A, B, C) of the
-// conic (A, B; B, C), B counted once.
+// One view's part of the projection adjoint: accumulates dL/dmean and
+// dL/dSigma (the 3D covariance, 3 x 3) from dL/dmu and dL/d(A, B, C) of the
+// conic (A, B; B, C), B counted once.  Sigma does not depend on the view, so
+// its gradient is summed over the views and mapped to the log-scales and the
+// rotation once (sigma_backward).
 __device__ __forceinline__ void project_one_backward(const ProjArgs& a, const ProjF& P, const float* cam, float2 gmu,
-                                                     float gA, float gB, float gC, float* gm, float* gls,
-                                                     float* gq) {
+                                                     float gA, float gB, float gC, float* gm, float* gsig) {
     const float* Vm = cam;
     const float fx = cam[16], fy = cam[17];
     // conic -> Sigma': G_S = -K G_K K with G_K = [[gA, gB/2], [gB/2, gC]]
@@ -122,13 +130,13 @@ __device__ __forceinline__ void project_one_backward(const ProjArgs& a, const Pr
     const float S10 = -(t10 * K0 + t11 * K1), S11 = -(t10 * K1 + t11 * K2);
     const float GS[4] = {S00, 0.5f * (S01 + S10), 0.5f * (S01 + S10), S11};
     // Sigma' = T Sigma T^T: dL/dSigma = T^T G T, dL/dT = 2 G T Sigma
-    float GSig[9], GT[6];
+    float GT[6];
     for (int i = 0; i < 3; i++)
         for (int j = 0; j < 3; j++) {
             float acc = 0.f;
             for (int p = 0; p < 2; p++)
                 for (int r = 0; r < 2; r++) acc += P.T[3 * p + i] * GS[2 * p + r] * P.T[3 * r + j];
-            GSig[3 * i + j] = acc;
+            gsig[3 * i + j] += acc;
         }
     float TSig[6];
     for (int r = 0; r < 2; r++)
@@ -151,6 +159,11 @@ __device__ __forceinline__ void project_one_backward(const ProjArgs& a, const Pr
     if (P.cly == 0) { gt1 += -GJ[5] * fy * iz2; gt2 += GJ[5] * 2.f * fy * ty * iz3; }
     else            { gt2 += GJ[5] * fy * P.tcy * iz3; }
     for (int k = 0; k < 3; k++) gm[k] += Vm[k] * gt0 + Vm[4 + k] * gt1 + Vm[8 + k] * gt2;
+}
+
+// dL/d(log_scale, quat) from dL/dSigma (summed over the views), with the
+// view-independent rotation and scales of P.
+__device__ __forceinline__ void sigma_backward(const ProjF& P, const float* GSig, float* gls, float* gq) {
     // Sigma = M M^T, M = R diag(s): dL/dM = 2 GSig M
     float GR[9];
     for (int j = 0; j < 3; j++) {
