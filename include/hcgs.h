@@ -110,7 +110,10 @@ typedef struct {
 typedef struct {
     int tile;                 /* must be 16 (Sec. 4.2: 16x16 tiles)             */
     float alpha_min;          /* skip a Gaussian at a pixel when alpha < this (1/255) */
-    float alpha_max;          /* alpha = min(alpha_max, o G) (0.99)             */
+    float alpha_max;          /* alpha = min(alpha_max, o G) (0.99); the min is
+                                 taken for Gaussians whose opacity exceeds
+                                 alpha_max (1 - 2^-10), below which o G <= o
+                                 cannot reach it up to rounding               */
     float T_eps;              /* stop a pixel once T < T_eps, after the add (1e-4) */
     float cov2d_dilation;     /* added to the diagonal of Sigma' (0.3 px^2)     */
     float near_z;             /* cull when camera-space z < near_z (0.2 m)      */
@@ -118,9 +121,11 @@ typedef struct {
     float ste_tau;            /* softmax temperature of Eq. ste (1e-3)          */
     int order;                /* 0 front-to-back (nearest first), 1 back-to-front */
     int footprint;            /* 0 FP32 footprint; 1 FP16x2 and 2 BF16x2 footprint
-                                 (exponent and exp() in packed half / bfloat16
-                                 precision in the footprint's normalised frame)
-                                 with FP32 accumulation                         */
+                                 (in the footprint's normalised frame the part
+                                 of the exponent that varies along a pixel
+                                 column and its exp() in packed half / bfloat16
+                                 precision, the part constant along the column
+                                 in FP32) with FP32 accumulation               */
     int rho_grad;             /* 0: only the assigned plane's rho gets gradient
                                  (the forward skips the other planes);
                                  1: dense plane-weight gradient: every plane's
