@@ -135,18 +135,19 @@ __device__ __forceinline__ float4 entry_coeffs(float4 q0, float4 q1) {
 // Stream 32 list positions [p0, p0 + 32) of the bucket for one warp: keep the
 // entries whose rectangle covers tile (tx, ty) and whose footprint can reach
 // the warp's strip, and compact them, in list order, into the warp's slots.
-// Returns the number kept.
-template <int NR, int FT>
+// Returns the number kept.  PF: the caller has already loaded the lane's
+// list entry (s_pf) for position p0 + lane.
+template <int NR, int FT, bool PF = false>
 __device__ __forceinline__ int stage_warp(const RasterArgs& a, size_t vN, uint32_t beg, uint32_t p0, uint32_t n,
                                           int tx, int ty, float sx0, float sy0, float4 (*wrec)[NR + 1],
-                                          uint32_t* wpos, uint32_t* wid, uint32_t* kept) {
+                                          uint32_t* wpos, uint32_t* wid, uint32_t* kept, uint32_t s_pf = 0u) {
     const int lane = threadIdx.x & 31;
     const uint32_t p = p0 + (uint32_t)lane;
     bool ok = false;
     uint32_t s = 0;
     float4 q0, q1;
     if (p < n) {
-        s = a.list[beg + p];
+        s = PF ? s_pf : a.list[beg + p];
         const uint2 rc = a.rects[vN + s];
         ok = (uint32_t)tx >= (rc.x & 0xFFFFu) && (uint32_t)tx < (rc.x >> 16) && (uint32_t)ty >= (rc.y & 0xFFFFu) &&
              (uint32_t)ty < (rc.y >> 16);
@@ -352,10 +353,15 @@ __global__ void __launch_bounds__(RT, 32) k_raster_fwd(RasterArgs a, float2* __r
     for (int c = 0; c < C; c++) aAX[c] = aAY[c] = aBX[c] = aBY[c] = f2(0.f);
     uint32_t last[4] = {0, 0, 0, 0};
     int nc[4] = {0, 0, 0, 0};
+    // the list entry of the next batch is loaded one batch ahead
+    uint32_t s_pf = (uint32_t)lane < n ? a.list[beg + lane] : 0u;
     for (uint32_t p0 = 0; p0 < n; p0 += 32) {
         const bool live = TA.x >= teps || TA.y >= teps || TB.x >= teps || TB.y >= teps;
         if (!__any_sync(0xffffffffu, live)) break;
-        const int nh = stage_warp<NR, FT>(a, vN, beg, p0, n, tx, ty, sx0, sy0, srec, spos, sid, kept + nkept);
+        const uint32_t s_cur = s_pf;
+        if (p0 + 32u + (uint32_t)lane < n) s_pf = a.list[beg + p0 + 32u + (uint32_t)lane];
+        const int nh = stage_warp<NR, FT, true>(a, vN, beg, p0, n, tx, ty, sx0, sy0, srec, spos, sid, kept + nkept,
+                                                s_cur);
         for (int k = 0; k < nh; k++) {
             const float4* rec = srec[k];
             const float4 r0 = rec[0], r1 = rec[1], kk = rec[NR];
