@@ -96,6 +96,8 @@ C_CASES = [
      "double rx = sqrt(k * P.cov[2]) + 1e-9, ry = sqrt(k * P.cov[0]) + 1e-9;",
      R.test_reduces_to_textbook_alpha_blending),
     ("back-to-front order not reversed", "if (order == 1)", "if (order == 2)", R.test_three_gaussians_golden_fixture),
+    ("dense plane-weight gradient: suffix sign", "double Sr = pre[2 * c] - vP[(size_t)k * 32 + 2 * c];",
+     "double Sr = vP[(size_t)k * 32 + 2 * c] - pre[2 * c];", RD.test_dense_gradient_matches_finite_differences),
 ]
 
 
@@ -157,9 +159,26 @@ PY_CASES = [
      GR.test_adam_first_step_closed_form),
     ("network activation not a ReLU", "mlp_forward", "h = np.maximum(z, 0.0)", "h = np.abs(z)",
      GR.test_mlp_reverse_mode),
+    ("network adjoint without the ReLU mask", "mlp_backward", "g = g * (z > 0)", "g = g",
+     GR.test_mlp_reverse_mode),
+    ("bfloat16 rounding without ties to even", "round_bf16", "u = (u + 0x7FFF + ((u >> 16) & 1)) >> 16 << 16",
+     "u = (u + 0x8000) >> 16 << 16", GR.test_bf16_rounding_matches_torch),
+    ("Adam second moment of g, not g^2", "adam_step", "v = beta2 * v + (1 - beta2) * g * g",
+     "v = beta2 * v + (1 - beta2) * g", GR.test_adam_first_step_closed_form),
+    ("paper loss gradient through |V|^2 halved", "paper_loss", "gV = 2.0 * gI * V", "gV = gI * V",
+     OB.test_paper_loss_gradient_finite_differences),
+    ("phase-only objective compares the real part twice", "phase_only_loss",
+     "X = np.stack([Uphi.real, Uphi.imag])", "X = np.stack([Uphi.real, Uphi.real])",
+     OB.test_phase_only_loss_without_ssim_is_the_field_mse),
+    ("inverse-propagation adjoint without the conjugate", "inverse_propagate_adjoint",
+     "r = np.fft.ifft2(np.conj(Hm) * np.fft.fft2(g))", "r = np.fft.ifft2(Hm * np.fft.fft2(g))",
+     OB.test_paper_loss_gradient_finite_differences),
+    ("clone copy without the phase-noise scale", "densify", 'o["phase_noise"] * z[n, 0, 3:]', "z[n, 0, 3:]",
+     D.test_densify_counts_order_and_copies),
 ]
 
 
+@pytest.mark.filterwarnings("ignore::RuntimeWarning")  # a mutant may take the sqrt of a negative number
 @pytest.mark.parametrize("what,name,old,new,pin", PY_CASES, ids=[c[0] for c in PY_CASES])
 def test_python_mistake_fails_its_pin(monkeypatch, what, name, old, new, pin):
     _plant_py(monkeypatch, name, old, new)
