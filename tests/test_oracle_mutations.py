@@ -98,6 +98,17 @@ C_CASES = [
     ("back-to-front order not reversed", "if (order == 1)", "if (order == 2)", R.test_three_gaussians_golden_fixture),
     ("dense plane-weight gradient: suffix sign", "double Sr = pre[2 * c] - vP[(size_t)k * 32 + 2 * c];",
      "double Sr = vP[(size_t)k * 32 + 2 * c] - pre[2 * c];", RD.test_dense_gradient_matches_finite_differences),
+    ("quaternion adjoint without the normalisation's projection",
+     "gq[4 * n + k] += (gqn[k] - P.qn[k] * dot) / P.qnorm;", "gq[4 * n + k] += gqn[k] / P.qnorm;",
+     GR.test_fd_exact_preset),
+    ("rotation adjoint entry sign", "gqn[0] = 2 * (-z * GR[1] + y * GR[2]", "gqn[0] = 2 * (z * GR[1] + y * GR[2]",
+     GR.test_fd_exact_preset),
+    ("log-scale adjoint without the exp chain factor", "gls[3 * n + j] += gs * P.s[j];",
+     "gls[3 * n + j] += gs;", GR.test_fd_exact_preset),
+    ("opacity logit adjoint without the sigmoid derivative", "gol[n] += g_opac[n] * o * (1.0 - o);",
+     "gol[n] += g_opac[n] * o;", GR.test_fd_exact_preset),
+    ("phase adjoint sign", "gph[C * n + c] += am * (-gr * sin(ph) + gi * cos(ph));",
+     "gph[C * n + c] += am * (gr * sin(ph) + gi * cos(ph));", GR.test_fd_exact_preset),
 ]
 
 
