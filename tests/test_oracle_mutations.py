@@ -109,6 +109,10 @@ C_CASES = [
      "gol[n] += g_opac[n] * o;", GR.test_fd_exact_preset),
     ("phase adjoint sign", "gph[C * n + c] += am * (-gr * sin(ph) + gi * cos(ph));",
      "gph[C * n + c] += am * (gr * sin(ph) + gi * cos(ph));", GR.test_fd_exact_preset),
+    ("alpha_max clamp not applied", "if (a > amax) { a = amax; *clamped = 1; }",
+     "if (0) { a = amax; *clamped = 1; }", R.test_alpha_max_clamp_and_its_flat_adjoint),
+    ("clamped alpha not flat in the adjoint", "if (kcl[k]) continue; /* alpha = alpha_max: flat in o G */",
+     "/* (planted: the clamp's flatness dropped) */", R.test_alpha_max_clamp_and_its_flat_adjoint),
 ]
 
 

@@ -133,6 +133,39 @@ def test_jacobian_clamp_closed_form():
     assert abs(pr["mu"][0][0] - (f * x / z + 29.5)) < 1e-12
 
 
+def test_alpha_max_clamp_and_its_flat_adjoint():
+    # alpha = min(alpha_max, o G): a near-opaque Gaussian is clamped around its
+    # centre, where the field is c alpha_max e^{j phi}; there alpha does not
+    # depend on o or mu, so the adjoint (checked against central differences
+    # of the compositing) takes nothing from those pixels.
+    H, W, f, z = 24, 28, 300.0, 2.0
+    intr = np.array([f, f, 14.0, 11.0])  # the centre falls on pixel (14, 11)
+    g = _one([0, 0, z], np.log([0.05, 0.06, 0.02]), [1, 0, 0, 0], 0.999, [0.8], [0.5], [0.0])
+    opts = dict(oracle.EXACT_OPTS, alpha_max=0.99)
+    pr = oracle.project(g, np.eye(4), intr, H, W, opts)
+    U, _, _ = oracle.composite(pr, opts)
+    a, b = (f / z * 0.05) ** 2, (f / z * 0.06) ** 2
+    i = np.arange(H)[:, None] - 11.0
+    j = np.arange(W)[None, :] - 14.0
+    G = np.exp(-0.5 * (j ** 2 / a + i ** 2 / b))
+    assert np.sum(0.999 * G > 0.99) >= 4  # the clamp is active at some pixels
+    assert np.max(np.abs(U[0, 0] - 0.8 * np.minimum(0.99, 0.999 * G) * np.exp(0.5j))) < 1e-14
+    gU = S.random_complex(U.shape, seed=4).astype(np.complex128)
+    g2 = oracle.composite_backward(pr, gU, opts)
+
+    def loss(key, idx, d):
+        p2 = dict(pr)
+        p2[key] = pr[key].copy()
+        p2[key][idx] += d
+        U2, _, _ = oracle.composite(p2, opts)
+        return float(np.sum(np.real(np.conj(gU) * U2)))
+
+    h = 1e-7
+    for key, idx in (("opac", (0,)), ("mu", (0, 0)), ("mu", (0, 1))):
+        fd = (loss(key, idx, h) - loss(key, idx, -h)) / (2 * h)
+        assert abs(fd - g2[key][idx]) < 1e-6 * max(1.0, abs(fd)), (key, idx, fd, g2[key][idx])
+
+
 def _golden():
     gs, ex = [], []
     with open(os.path.join(GOLDEN, "three_gaussians_one_pixel.txt")) as fh:
