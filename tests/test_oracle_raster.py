@@ -166,6 +166,50 @@ def test_alpha_max_clamp_and_its_flat_adjoint():
         assert abs(fd - g2[key][idx]) < 1e-6 * max(1.0, abs(fd)), (key, idx, fd, g2[key][idx])
 
 
+def test_near_plane_cull():
+    # a Gaussian whose camera-space depth is below near_z is culled (it
+    # contributes nothing); one just beyond it is projected
+    H, W = 16, 16
+    intr = np.array([100.0, 100.0, 7.5, 7.5])
+    g = _cat([_one([0, 0, 0.15], np.log([0.01] * 3), [1, 0, 0, 0], 0.5, [1.0], [0.0], [0.0]),
+              _one([0, 0, 0.25], np.log([0.01] * 3), [1, 0, 0, 0], 0.5, [1.0], [0.0], [0.0])])
+    pr = oracle.project(g, np.eye(4), intr, H, W, dict(oracle.EXACT_OPTS, near_z=0.2))
+    assert list(pr["valid"]) == [0, 1]
+    pr = oracle.project(g, np.eye(4), intr, H, W, dict(oracle.EXACT_OPTS, near_z=0.1))
+    assert list(pr["valid"]) == [1, 1]
+
+
+def test_stop_rule_in_the_adjoint():
+    # six Gaussians stacked on the optical axis, o = 0.9 each: at the centre
+    # pixel T falls to 1e-5 after the fifth, which stops the walk (T_eps =
+    # 1e-4, after the add); the sixth never contributes there.  U is linear in
+    # w, so the adjoint's dL/dw must equal the central differences exactly:
+    # the fifth Gaussian's is nonzero at the centre, the sixth's only from
+    # the pixels its neighbours leave open.
+    H, W = 9, 9
+    intr = np.array([100.0, 100.0, 4.0, 4.0])
+    g = _cat([_one([0, 0, 1.0 + 0.1 * k], np.log([0.01] * 3), [1, 0, 0, 0], 0.9, [0.5 + 0.1 * k], [0.3 * k], [0.0])
+              for k in range(6)])
+    opts = dict(oracle.EXACT_OPTS, T_eps=1e-4)
+    pr = oracle.project(g, np.eye(4), intr, H, W, opts)
+    U, T, nc = oracle.composite(pr, opts)
+    assert nc[0, 4, 4] == 5 and T[0, 4, 4] < 1e-4
+    gU = S.random_complex(U.shape, seed=6).astype(np.complex128)
+    g2 = oracle.composite_backward(pr, gU, opts)
+
+    def loss(n, part, d):
+        p2 = dict(pr)
+        p2["w"] = pr["w"].copy()
+        p2["w"][n, 0, part] += d
+        U2, _, _ = oracle.composite(p2, opts)
+        return float(np.sum(np.real(np.conj(gU) * U2)))
+
+    for n in range(6):
+        for part in (0, 1):
+            fd = (loss(n, part, 1e-6) - loss(n, part, -1e-6)) / 2e-6
+            assert abs(fd - g2["w"][n, 0, part]) < 1e-8 * max(1.0, abs(fd)), (n, part, fd, g2["w"][n, 0, part])
+
+
 def _golden():
     gs, ex = [], []
     with open(os.path.join(GOLDEN, "three_gaussians_one_pixel.txt")) as fh:
