@@ -115,6 +115,8 @@ C_CASES = [
      "/* (planted: the clamp's flatness dropped) */", R.test_alpha_max_clamp_and_its_flat_adjoint),
     ("near-plane cull at z > 0", "if (!(P->t[2] >= opt[O_NEAR])) { P->valid = 0; return; }",
      "if (!(P->t[2] > 0)) { P->valid = 0; return; }", R.test_near_plane_cull),
+    ("equal depths visited by descending index", "return (i > j) - (i < j);", "return (i < j) - (i > j);",
+     R.test_equal_depths_visit_in_index_order),
     ("adjoint's replay stops at ten times T_eps", "T *= (1.0 - a);\n                        if (T < teps) break;",
      "T *= (1.0 - a);\n                        if (T < 10.0 * teps) break;", R.test_stop_rule_in_the_adjoint),
 ]

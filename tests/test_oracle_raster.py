@@ -210,6 +210,23 @@ def test_stop_rule_in_the_adjoint():
             assert abs(fd - g2["w"][n, 0, part]) < 1e-8 * max(1.0, abs(fd)), (n, part, fd, g2["w"][n, 0, part])
 
 
+def test_equal_depths_visit_in_index_order():
+    # Reading R1: the visiting order is (depth, index) ascending front to back
+    # and its exact reverse back to front.  Two Gaussians at the same depth on
+    # the same pixel: U = w_a alpha_a + w_b alpha_b (1 - alpha_a) with a the
+    # one visited first.
+    H, W = 9, 9
+    intr = np.array([100.0, 100.0, 4.0, 4.0])
+    g = _cat([_one([0, 0, 1.5], np.log([0.01] * 3), [1, 0, 0, 0], 0.6, [1.0], [0.0], [0.0]),
+              _one([0, 0, 1.5], np.log([0.01] * 3), [1, 0, 0, 0], 0.3, [0.5], [np.pi / 2], [0.0])])
+    w0, w1 = 1.0, 0.5j
+    for order, (first, second) in ((0, ((w0, 0.6), (w1, 0.3))), (1, ((w1, 0.3), (w0, 0.6)))):
+        opts = dict(oracle.EXACT_OPTS, order=order)
+        U, _, _ = oracle.composite(oracle.project(g, np.eye(4), intr, H, W, opts), opts)
+        want = first[0] * first[1] + second[0] * second[1] * (1 - first[1])
+        assert abs(U[0, 0, 4, 4] - want) < 1e-12, (order, U[0, 0, 4, 4], want)
+
+
 def _golden():
     gs, ex = [], []
     with open(os.path.join(GOLDEN, "three_gaussians_one_pixel.txt")) as fh:
