@@ -272,6 +272,19 @@ def test_band_limit_is_the_unaliased_phase_region():
     assert np.array_equal(kept, kept[(-np.arange(n)) % n])
 
 
+def test_band_limit_applies_per_axis():
+    # the limit on f_y comes from the grid's own frequency spacing along y:
+    # on a 96 x 48 grid the kept f_y (column f_x = 0) are those of a 96-sample
+    # axis and the kept f_x (row f_y = 0) those of a 48-sample axis
+    z = 30e-3
+    Hb = oracle.transfer_function(96, 48, PITCH, LAM, z, band_limit=1)
+    ky = np.abs(Hb[:, 0]) > 0
+    kx = np.abs(Hb[0, :]) > 0
+    assert np.array_equal(ky, np.abs(oracle.transfer_function(1, 96, PITCH, LAM, z, band_limit=1)[0]) > 0)
+    assert np.array_equal(kx, np.abs(oracle.transfer_function(1, 48, PITCH, LAM, z, band_limit=1)[0]) > 0)
+    assert ky.sum() < 96 and kx.sum() < 48
+
+
 def test_band_limit_inactive_on_the_paper_shaped_grids():
     # At 8 um pitch the limit lies above the grid's highest frequency for the
     # workloads' sizes and distances, so band_limit = 1 changes nothing there.

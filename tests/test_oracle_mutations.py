@@ -196,6 +196,15 @@ PY_CASES = [
      OB.test_paper_loss_gradient_finite_differences),
     ("clone copy without the phase-noise scale", "densify", 'o["phase_noise"] * z[n, 0, 3:]', "z[n, 0, 3:]",
      D.test_densify_counts_order_and_copies),
+    ("band limit along y from the x spacing", "transfer_function",
+     "lim_y = 1.0 / (wavelength * np.sqrt((2.0 * duy * z) ** 2 + 1.0))",
+     "lim_y = 1.0 / (wavelength * np.sqrt((2.0 * dux * z) ** 2 + 1.0))", A.test_band_limit_applies_per_axis),
+    ("SSIM gradient normalised over planes only", "paper_loss_intensities",
+     "g[l, c] -= lam / (L * C) * ssim_grad", "g[l, c] -= lam / L * ssim_grad",
+     OB.test_paper_loss_is_a_mean_over_planes_and_channels),
+    ("SSIM loss normalised over planes only", "paper_loss_intensities",
+     "loss += lam * (1.0 - s_sum / (L * C))", "loss += lam * (1.0 - s_sum / L)",
+     OB.test_paper_loss_is_a_mean_over_planes_and_channels),
 ]
 
 

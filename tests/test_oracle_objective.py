@@ -154,6 +154,21 @@ def test_adan_matches_the_algorithm_in_its_authors_notation():
         assert np.allclose(p, th_ref[k], rtol=1e-13, atol=1e-15), k
 
 
+def test_paper_loss_is_a_mean_over_planes_and_channels():
+    # both terms are means over (planes, channels): repeating every image
+    # along the plane and channel axes leaves the loss unchanged and spreads
+    # the gradient evenly over the copies
+    rng = _rng(15)
+    I = rng.random((2, 1, 12, 14)) * 2.0
+    Igt = rng.random((2, 1, 12, 14)) * 2.0
+    M = (rng.random((2, 12, 14)) < 0.5).astype(np.float64)
+    l1, g1 = oracle.paper_loss_intensities(I, Igt, M, lam=0.7)
+    rep = lambda a: np.concatenate([np.concatenate([a, a], axis=1)] * 3, axis=0)
+    l6, g6 = oracle.paper_loss_intensities(rep(I), rep(Igt), np.concatenate([M] * 3, axis=0), lam=0.7)
+    assert abs(l6 - l1) < 1e-12 * abs(l1)
+    assert np.max(np.abs(g6 - rep(g1) / 6.0)) < 1e-12 * np.max(np.abs(g1))
+
+
 def test_adan_first_step_and_constant_gradient():
     # step 1: m = g, v = 0, n = g^2, so p moves by lr g / (|g| + eps); with a
     # constant gradient the difference terms vanish and every step does the same
