@@ -115,6 +115,12 @@ C_CASES = [
      "/* (planted: the clamp's flatness dropped) */", R.test_alpha_max_clamp_and_its_flat_adjoint),
     ("near-plane cull at z > 0", "if (!(P->t[2] >= opt[O_NEAR])) { P->valid = 0; return; }",
      "if (!(P->t[2] > 0)) { P->valid = 0; return; }", R.test_near_plane_cull),
+    ("plane argmax ties keep the highest index", "if (logits[l] > logits[best]) best = l;",
+     "if (logits[l] >= logits[best]) best = l;", GR.test_ste_plane_logit_gradient),
+    ("adjoint suffix accumulated without T", "S[2 * c] += wr * a * Tk;", "S[2 * c] += wr * a;",
+     GR.test_fd_exact_preset),
+    ("support radius from 1.5 ln(o / alpha_min)", "double k = 2.0 * log(P.opac / opt[O_AMIN]);",
+     "double k = 1.5 * log(P.opac / opt[O_AMIN]);", R.test_reduces_to_textbook_alpha_blending),
     ("equal depths visited by descending index", "return (i > j) - (i < j);", "return (i < j) - (i > j);",
      R.test_equal_depths_visit_in_index_order),
     ("adjoint's replay stops at ten times T_eps", "T *= (1.0 - a);\n                        if (T < teps) break;",
