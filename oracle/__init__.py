@@ -26,6 +26,8 @@ What each function follows (arXiv 2506.08350):
 * ``philox4x32_10``, ``philox_normals``  the counter-based generator that
                          draws the densification noise (Salmon et al. 2011)
                          and standard normals from it by Box-Muller;
+                         ``philox_uniforms``' half-word offset (w + 1/2) 2^-32
+                         is a convention: parity unpinned;
 * ``densify_accumulate``, ``densify``  Algorithm 1's pruning and phase-aware
                          clone / split (the 3DGS densification rules);
 * ``mlp_*``              the learned-initialisation network (no counterpart in

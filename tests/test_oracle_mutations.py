@@ -202,6 +202,12 @@ PY_CASES = [
      OB.test_paper_loss_gradient_finite_differences),
     ("clone copy without the phase-noise scale", "densify", 'o["phase_noise"] * z[n, 0, 3:]', "z[n, 0, 3:]",
      D.test_densify_counts_order_and_copies),
+    ("straight-through weights without the temperature", "ste_softmax", "/ tau", "/ 1.0",
+     RD.test_ste_weights_are_the_tempered_softmax),
+    ("split log-scale shift by ln 2", "densify", 'shrink = np.log(o["split_shrink"])', "shrink = np.log(2.0)",
+     D.test_densify_counts_order_and_copies),
+    ("crop window off by one column", "crop", "return u[..., H // 2:H // 2 + H, W // 2:W // 2 + W]",
+     "return u[..., H // 2:H // 2 + H, W // 2 + 1:W // 2 + 1 + W]", A.test_zero_padding_is_the_embedding_done_by_hand),
     ("band limit along y from the x spacing", "transfer_function",
      "lim_y = 1.0 / (wavelength * np.sqrt((2.0 * duy * z) ** 2 + 1.0))",
      "lim_y = 1.0 / (wavelength * np.sqrt((2.0 * dux * z) ** 2 + 1.0))", A.test_band_limit_applies_per_axis),

@@ -62,6 +62,15 @@ def test_dense_gradient_matches_finite_differences():
         assert abs(fd - d[n, l]) < 1e-6 * max(1.0, abs(fd)), (n, l, fd, d[n, l])
 
 
+def test_ste_weights_are_the_tempered_softmax():
+    # the straight-through weights of the dense mode: softmax(rho' / tau) per
+    # Gaussian, against scipy's softmax
+    from scipy.special import softmax
+    r = np.random.default_rng(3).normal(size=(7, 5))
+    for tau in (1e-3, 0.5, 2.0):
+        assert np.allclose(oracle.ste_softmax(r, tau), softmax(r / tau, axis=1), rtol=1e-12, atol=1e-300)
+
+
 def test_dense_mode_adds_the_unassigned_planes_to_the_logits():
     g, pr, gU = _setup(seed=1)
     optics = S.Optics(28, 36, (639e-9, 473e-9), (0.0, 3e-3, 6e-3))
