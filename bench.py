@@ -41,18 +41,23 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.json")
 
 # Arithmetic operations per contributing (pixel, Gaussian) pair for C channels
-# (an FMA, a compare, an exp and a reciprocal count one each), from what the
-# step computes, not from the instructions the kernels issue:
-#   forward: d = p - mu (2), power from dx^2, dy^2, dx dy and the conic (6),
-#     exp and its scaling (2), alpha = min(alpha_max, o G) (2), threshold (1),
-#     weight alpha T (1), w_c alpha T into the field (2C), T (1 - alpha) (2)
-#     = 16 + 2C;
-#   adjoint: the forward quantities again (12), T_k = T_{k+1} / (1 - alpha)
-#     (2), alpha T (1), A = sum_c Re(conj g_c w_c) (2C), dL/dalpha (2), the
-#     suffix update (1), dL/dw_c (2C), clamp test (1), dL/dpower (1),
-#     dL/dmu (6), dL/dconic (4), dL/do (1), the per-Gaussian sum over pixels
-#     of the 6 + 2C gradient values (6 + 2C) = 43 + 6C.
-OPS_PER_PAIR = {"k_raster_fwd": lambda C: 16 + 2 * C, "k_raster_bwd": lambda C: 43 + 6 * C}
+# (an FMA, a multiply, an add, a compare, an exp and a reciprocal count one
+# each), counting only what the method needs per pair, not the instructions
+# the kernels issue:
+#   forward (the count of the rasterizer's FP32-issue roofline): d = p - mu
+#     (2), the power from the conic (5), exp (1), alpha = min(alpha_max, o G)
+#     (2), alpha T (1), w_c alpha T into the field (2C), T (1 - alpha) (1)
+#     = 12 + 2C;
+#   adjoint (Sec. 4.2, back to front, T by division): alpha recomputed as
+#     above (10), 1 - alpha and T_k = T_{k+1} / (1 - alpha) (2), alpha T (1),
+#     A = sum_c Re(conj g_c w_c) (2C), dL/dalpha = T A - B / (1 - alpha) (3),
+#     the suffix B += alpha T A (1), dL/dw_c = g_c alpha T summed over the
+#     pixels (2C), the clamp test (1), p = -dL/dpower = dL/dalpha o G (1), the
+#     five pixel moments of p (sum p dx, p dy, p dx^2, p dx dy, p dy^2) (5),
+#     o dL/do = sum p (1) = 25 + 4C.
+#   The gradients of mu and of the conic follow from the moments once per
+#   Gaussian (not per pair), so they are not counted here.
+OPS_PER_PAIR = {"k_raster_fwd": lambda C: 12 + 2 * C, "k_raster_bwd": lambda C: 25 + 4 * C}
 KERNEL_SOURCE = {"k_fft_cols": "fft.cu", "k_rows_sum": "fft.cu", "k_rows_spread": "fft.cu",
                  "k_raster_fwd": "raster.cu", "k_raster_bwd": "raster.cu", "k_project": "project.cu",
                  "k_project_bwd": "project.cu", "k_rs_scatter": "project.cu", "k_rs_hist": "project.cu",
@@ -138,41 +143,54 @@ class ClockSampler:
 # the CPU oracle on a bounded sample (cpu_baseline leg and the reference arm)
 # ---------------------------------------------------------------------------
 def oracle_sample(wl, rows=16, seed=0):
-    """Times the FP64 oracle on one view of the workload: projection of all N
-    Gaussians, compositing and its adjoint on a band of `rows` image rows (all
-    planes), and one plane-channel of the propagation and of its adjoint;
-    scales each part to a full view.  Returns (views/s for fwd+bwd, s/view,
-    description)."""
+    """Times the FP64 oracle on one view of the workload and scales it to a
+    full view: the projection of all N Gaussians and its adjoint (once per
+    view), the compositing and its adjoint, and one plane-channel of the
+    propagation and of its adjoint (scaled by the L C plane-channels).
+
+    The compositing calls have a per-view part that does not depend on the
+    rows (the depth sort of all N Gaussians and the candidate grid) and a
+    per-row part.  Each is timed twice, on an empty band (the per-view part
+    alone) and on a band of `rows` rows at the image centre; only the
+    difference is scaled by H / rows.  Returns (views/s for fwd + bwd,
+    s/view, description, wall seconds)."""
     import oracle
     o = wl.optics
     g = S.make_gaussians(wl.N, o.L, o.C, o.H, o.W, seed=seed)
     vm, it = S.view_batch(1, o.H, o.W, seed=seed)
     vm, it = vm.astype(np.float32).astype(np.float64), it.astype(np.float32).astype(np.float64)
     r0 = o.H // 2 - rows // 2
-    t0 = time.perf_counter()
-    pr = oracle.project(g, vm[0], it[0], o.H, o.W)
-    t1 = time.perf_counter()
-    U, T, nc = oracle.composite(pr, rows=(r0, r0 + rows))
-    t2 = time.perf_counter()
-    u = np.asarray(U[0, 0])
-    oracle.propagate(u, o.pitch, o.wavelengths[0], o.plane_z[-1])
-    t3 = time.perf_counter()
+    w0 = time.perf_counter()
+
+    def clock(fn):
+        t = time.perf_counter()
+        out = fn()
+        return time.perf_counter() - t, out
+
+    t_proj, pr = clock(lambda: oracle.project(g, vm[0], it[0], o.H, o.W))
+    t_c0, _ = clock(lambda: oracle.composite(pr, rows=(r0, r0)))
+    t_c1, _ = clock(lambda: oracle.composite(pr, rows=(r0, r0 + rows)))
+    u = np.asarray(S.random_complex((o.H, o.W), seed=3), dtype=np.complex128)
+    t_prop, _ = clock(lambda: oracle.propagate(u, o.pitch, o.wavelengths[0], o.plane_z[-1]))
     gP = S.random_complex((1, o.H, o.W), seed=2).astype(np.complex128)
-    oracle.propagate_planes_adjoint(gP, o.pitch, o.wavelengths[:1], o.plane_z[-1:])
-    t4 = time.perf_counter()
+    t_adj, _ = clock(lambda: oracle.propagate_planes_adjoint(gP, o.pitch, o.wavelengths[:1], o.plane_z[-1:]))
     gU = np.zeros((o.L, o.C, o.H, o.W), dtype=np.complex128)
     gU[:, :, r0:r0 + rows] = S.random_complex((o.L, o.C, rows, o.W), seed=3)
-    g2 = oracle.composite_backward(pr, gU, rows=(r0, r0 + rows))
-    t5 = time.perf_counter()
-    oracle.project_backward(g, vm[0], it[0], o.H, o.W, g2)
-    t6 = time.perf_counter()
-    frac = rows / o.H
+    t_b0, _ = clock(lambda: oracle.composite_backward(pr, gU, rows=(r0, r0)))
+    t_b1, g2 = clock(lambda: oracle.composite_backward(pr, gU, rows=(r0, r0 + rows)))
+    t_pb, _ = clock(lambda: oracle.project_backward(g, vm[0], it[0], o.H, o.W, g2))
+    scale = o.H / rows
     LC = o.L * o.C
-    per_view = ((t1 - t0) + (t2 - t1) / frac + (t3 - t2) * LC + (t4 - t3) * LC + (t5 - t4) / frac + (t6 - t5))
-    desc = ("one view of %s: projection and projection adjoint of all %d Gaussians, compositing and its "
-            "adjoint on %d of %d rows (all %d planes), one of %d plane-channel propagations and adjoints; "
-            "each part scaled to a full view" % (wl.name, wl.N, rows, o.H, o.L, LC))
-    return 1.0 / per_view, per_view, desc, time.perf_counter() - t0
+    fixed = t_proj + t_c0 + t_b0 + t_pb
+    per_rows = max(t_c1 - t_c0, 0.0) + max(t_b1 - t_b0, 0.0)
+    per_view = fixed + per_rows * scale + (t_prop + t_adj) * LC
+    desc = ("one view of %s: projection and projection adjoint of all %d Gaussians; compositing and its "
+            "adjoint timed on an empty band (depth sort and candidate grid, once per view: %.2f s) and on %d "
+            "of %d rows at the centre (all %d planes), the difference scaled by %.1f; one of %d "
+            "plane-channel propagations and adjoints, scaled by %d" %
+            (wl.name, wl.N, t_c0 + t_b0, rows, o.H, o.L, scale, LC, LC))
+    parts = {"fixed_s": fixed, "rows_s": per_rows, "rows": rows, "propagation_s": t_prop + t_adj}
+    return 1.0 / per_view, per_view, desc, time.perf_counter() - w0, parts
 
 
 def omp_threads():
@@ -190,10 +208,10 @@ def run_reference(args):
     if rank != 0:
         return
     wl = S.workload(args.workload)
-    rows = 8
+    rows = 24
     times = []
     for k in range(args.warmup + args.steps):
-        _, per_view, desc, _ = oracle_sample(wl, rows=rows, seed=k)
+        _, per_view, desc, _, _ = oracle_sample(wl, rows=rows, seed=k)
         if k >= args.warmup:
             times.append(per_view)
     per_view = statistics.median(times)
@@ -601,9 +619,9 @@ def run_ours(args):
             json.dump({"workload": wl.name, "pairs": pairs, "kernels": table, "clocks": clocks}, fh, indent=1)
     # --- CPU oracle baseline (rank 0, N = 1 only) ---
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, per_view, desc, wall = oracle_sample(wl, rows=48)
+        v, per_view, desc, wall, parts = oracle_sample(wl, rows=48)
         result["cpu_baseline"] = {"value": v, "unit": "views/s", "cores": omp_threads(), "kind": "oracle",
-                                  "sample": desc, "wall_s": wall}
+                                  "sample": desc, "wall_s": wall, "parts": parts}
     saved.release()
     ctx.close()
     if rank == 0:

@@ -8,8 +8,9 @@
  * 3D Gaussians in four steps:
  *   1. project      (Sec. 3 Eq. gaussian_projection / gaussian_projection_2d,
  *                    Eq. hard_assignment)                      -> hcgs_project
- *   2. depth-sort and bin into 16x16 tiles per plane (Sec. 4.2,
- *                    Algorithm 2 preprocessing)               -> hcgs_project
+ *   2. depth-sort and bin per plane into 64x64-pixel buckets, each bucket's
+ *                    list in visiting order (Sec. 4.2, Algorithm 2
+ *                    preprocessing)                          -> hcgs_project
  *   3. composite complex footprints into L plane fields (Sec. 4.1 per-plane
  *                    field equation, Algorithm 2)             -> hcgs_rasterize_planes
  *   4. propagate each plane by the band-limited angular spectrum method and
@@ -374,18 +375,20 @@ hcgs_status hcgs_init_apply(hcgs_ctx* ctx, const float* y, int N, int C, float* 
  * Result: the same as hcgs_asm_propagate(ctx, in, B, optics, -1, 0, out,
  * stream), i.e. out[b][l][c] = IDFT(H_{-Z_l} DFT(in[b][c])):
  *   in   device [B][C][H][W] complex64, not modified
- *   out  device [B][L][C][H][W] complex64, must not alias `in`
+ *   out  device [B][L][C][H][W] complex64, must share no byte with `in`
  * Working memory (column spectrum, transfer-function table, twiddles) lives
  * in one static device array of 4 Mi complex64 values (32 MiB) that every GPU
  * loading the library holds until exit.  Requests needing more, i.e.
  *   B*C*H*W + C*L*(H/2+1)*S + H + W (each rounded up to 64) > 4194304, with
  *   S = W/2 + 1 rounded up to even (the table's row stride),
  * return HCGS_ERR_CAPACITY before any launch.  The first call on a device
- * looks up that device's address of the array (cudaGetSymbolAddress); make
- * that first call before any stream capture.  All calls share the array and
+ * (and again the first after that device's context was destroyed and made
+ * anew, e.g. by cudaDeviceReset) looks up that device's address of the array
+ * (cudaGetSymbolAddress); make that first call before any stream capture.  All calls share the array and
  * it keeps the last call's contents (each call rewrites what it reads), so
  * calls whose kernels overlap on the GPU race: serialise them.  Errors:
- * HCGS_ERR_INVALID_ARG (NULL/aliased pointers, B < 1, bad optics),
+ * HCGS_ERR_INVALID_ARG (NULL pointers, `in` and `out` overlapping, B < 1,
+ * bad optics),
  * HCGS_ERR_UNSUPPORTED_SIZE (H or W not 2^a 3^b 5^c <= 4096),
  * HCGS_ERR_CAPACITY (too large), HCGS_ERR_CUDA (a CUDA call failed). */
 hcgs_status hcgs_asm_propagate_noalloc(const float* in, int B, const hcgs_optics* optics, float* out,

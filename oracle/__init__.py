@@ -574,17 +574,24 @@ def philox_normals(seed: int, n: int, stream: int = 0) -> np.ndarray:
     word pair (a, b) gives u = (a + 1/2) 2^-32, v = (b + 1/2) 2^-32 and, by
     Box-Muller, sqrt(-2 ln u) (cos 2 pi v, sin 2 pi v)."""
     m = (n + 1) // 2
-    w = philox_words(seed, 2 * m, stream).astype(np.float64).reshape(m, 2)
-    u = (w[:, 0] + 0.5) * 2.0 ** -32
-    v = (w[:, 1] + 0.5) * 2.0 ** -32
+    w = uniform_of_words(philox_words(seed, 2 * m, stream)).reshape(m, 2)
+    u, v = w[:, 0], w[:, 1]
     r = np.sqrt(-2.0 * np.log(u))
     z = np.stack([r * np.cos(2 * np.pi * v), r * np.sin(2 * np.pi * v)], axis=1).reshape(-1)
     return z[:n]
 
 
+def uniform_of_words(w) -> np.ndarray:
+    """The map from 32-bit words to uniforms: u = (w + 1/2) 2^-32, the centre
+    of the word's cell of width 2^-32 in [0, 1), so that u lies in the open
+    interval (0, 1) (ln u stays finite in Box-Muller) and the map is symmetric
+    about 1/2: u(w) + u(2^32 - 1 - w) = 1.  Exact in float64 (33 bits)."""
+    return (np.asarray(w, dtype=np.uint32).astype(np.float64) + 0.5) * 2.0 ** -32
+
+
 def philox_uniforms(seed: int, n: int, stream: int = 0) -> np.ndarray:
-    """n uniforms (w + 1/2) 2^-32 in (0, 1) from the words of ``philox_words``."""
-    return (philox_words(seed, n, stream).astype(np.float64) + 0.5) * 2.0 ** -32
+    """n uniforms in (0, 1) from the words of ``philox_words`` (``uniform_of_words``)."""
+    return uniform_of_words(philox_words(seed, n, stream))
 
 
 DENSIFY_OPTS = dict(grad_threshold=2e-4, split_scale=0.02, prune_opacity=5e-3, prune_scale=0.0,

@@ -33,7 +33,46 @@ static __device__ __align__(256) float2 g_noalloc_scratch[NOALLOC_SCRATCH_COMPLE
 
 constexpr int NOALLOC_MAX_DEVICES = 64;
 std::mutex g_noalloc_mu;
-float2* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {nullptr};
+// The array's device address, looked up once per device and CUDA context: a
+// context that is destroyed and created again (cudaDeviceReset) reloads the
+// module, so the address is keyed on the context's process-unique id (a new
+// context never reuses an old id, unlike its handle).
+struct NoallocAddr {
+    unsigned long long ctx_id;
+    float2* p;
+};
+NoallocAddr g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
+
+// Id of the calling thread's current context, through the driver entry
+// points the runtime hands out (no link-time dependency on libcuda).
+typedef int (*CtxGetCurrentFn)(void**);
+typedef int (*CtxGetIdFn)(void*, unsigned long long*);
+bool current_context_id(unsigned long long* id) {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    if (!get_current || !get_id) {
+        void* f0 = nullptr;
+        void* f1 = nullptr;
+        cudaDriverEntryPointQueryResult q0, q1;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f0, 12000, cudaEnableDefault, &q0) != cudaSuccess ||
+            q0 != cudaDriverEntryPointSuccess || !f0)
+            return false;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess || !f1)
+            return false;
+        get_current = (CtxGetCurrentFn)f0;
+        get_id = (CtxGetIdFn)f1;
+    }
+    void* ctx = nullptr;
+    if (get_current(&ctx) != 0 || !ctx) return false;
+    return get_id(ctx, id) == 0;
+}
+
+// do the byte ranges [a, a + na) and [b, b + nb) share a byte?
+bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+    const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+    return x < y + nb && y < x + na;
+}
 
 // exp(-2 pi i m / n), formed in FP64 and rounded to FP32
 __global__ void k_noalloc_twiddles(float2* __restrict__ tw, int n) {
@@ -72,27 +111,36 @@ using namespace hcgs;
 
 extern "C" hcgs_status hcgs_asm_propagate_noalloc(const float* in, int B, const hcgs_optics* o, float* out,
                                                   void* stream) {
-    if (!in || !out || in == out || B < 1 || !optics_ok(o)) return HCGS_ERR_INVALID_ARG;
-    if (!fft_supported(o->H) || !fft_supported(o->W)) return HCGS_ERR_UNSUPPORTED_SIZE;
+    if (!in || !out || B < 1 || !optics_ok(o)) return HCGS_ERR_INVALID_ARG;
     const int H = o->H, W = o->W, C = o->C, L = o->L;
     const size_t nS = (size_t)B * C * H * W;
+    // `out` is written while `in` is still being read: no shared byte
+    if (overlaps(in, nS * sizeof(float2), out, nS * L * sizeof(float2))) return HCGS_ERR_INVALID_ARG;
+    if (!fft_supported(o->H) || !fft_supported(o->W)) return HCGS_ERR_UNSUPPORTED_SIZE;
     const size_t nH = (size_t)C * L * (H / 2 + 1) * hq_stride(W);
     const size_t need = round64(nS) + round64(nH) + round64(H) + round64(W);
     if (need > NOALLOC_SCRATCH_COMPLEX) return HCGS_ERR_CAPACITY;
 
-    // set-up, once per device, with that device current: the device address
-    // of the static array (its host-side name is only a stand-in)
+    // set-up, once per device and context, with that device current: the
+    // device address of the static array (its host-side name is only a
+    // stand-in)
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) return HCGS_ERR_CUDA;
     float2* base = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_noalloc_mu);
-        if (!g_noalloc_addr[dev]) {
+        unsigned long long cid = 0;
+        // no context current yet on this thread: cudaSetDevice makes the
+        // device's primary context current (it allocates nothing)
+        if (!current_context_id(&cid) && (cudaSetDevice(dev) != cudaSuccess || !current_context_id(&cid)))
+            return HCGS_ERR_CUDA;
+        if (!g_noalloc_addr[dev].p || g_noalloc_addr[dev].ctx_id != cid) {
             void* p = nullptr;
             if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return HCGS_ERR_CUDA;
-            g_noalloc_addr[dev] = (float2*)p;
+            g_noalloc_addr[dev].p = (float2*)p;
+            g_noalloc_addr[dev].ctx_id = cid;
         }
-        base = g_noalloc_addr[dev];
+        base = g_noalloc_addr[dev].p;
     }
     float2* S1 = base;
     float2* hq = S1 + round64(nS);

@@ -2,18 +2,18 @@
 // (Sec. 4.1 per-plane field equation; Algorithm 2) and its adjoint (Supp. D.4;
 // Sec. 4.2: back-to-front walk, transmittance recovered by division).
 //
-// One CTA of 128 threads per (16 x 32 pixel region = two vertically adjacent
-// 16x16 tiles, plane, view); four pixels per thread (one column, rows r,
-// r + 2, r + 4, r + 6 of the warp's 16 x 8 strip), evaluated as two packed
-// FP32x2 pairs.  Both tiles lie in the same 64x64 bucket.  The four warps
-// are independent (no block barrier): each streams the bucket's list (in
-// visiting order) 32 entries at a time, keeps the entries whose tile
-// rectangle covers its tile and whose footprint can reach its 16 x 8 strip
-// (exact superset test), compacts them in order into its own shared-memory
-// slots (warp ballot), and every pixel of the warp takes the step of
-// Algorithm 2 for each of them: alpha = min(alpha_max, o exp(-power)); skip
-// when alpha < alpha_min; U += w alpha T; T *= 1 - alpha; stop once T < T_eps.
-// A warp leaves the list as soon as its own pixels have all stopped.
+// One CTA of one warp per (16 x 8 pixel strip, plane, view): a 16x16 tile
+// is two strips, and a strip's tile lies in one 64x64 bucket of the plane's
+// binning.  Four pixels per thread (one column, rows r, r + 2, r + 4, r + 6
+// of the strip), evaluated as two packed FP32x2 pairs.  The warp streams the
+// bucket's list (in visiting order) 32 entries at a time, keeps the entries
+// whose tile rectangle covers its tile and whose footprint can reach its
+// strip (exact superset test), compacts them in order into shared-memory
+// slots (warp ballot), and every pixel takes the step of Algorithm 2 for
+// each of them: alpha = min(alpha_max, o exp(-power)); skip when alpha <
+// alpha_min; U += w alpha T; T *= 1 - alpha; stop once T < T_eps.  The warp
+// leaves the list as soon as its pixels have all stopped, and writes the ids
+// it kept (the strip's list) for the adjoint.
 //
 // The alpha arithmetic uses explicitly rounded intrinsics so that the forward
 // and backward kernels take identical skip/stop decisions.

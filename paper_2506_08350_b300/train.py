@@ -106,7 +106,18 @@ class HologramTrainer:
     def step(self, viewmat, intr, I_gt, mask=None):
         """One optimisation step on one view; returns the loss before the update
         (a device tensor).  mask: the view's plane masks [1, L, H, W] (objective
-        "paper"; None = all zero)."""
+        "paper"; None = all zero).  With data_parallel the gradients are summed
+        over the ranks of the process group before the update."""
+        self.gradients(viewmat, intr, I_gt, mask)
+        if self.data_parallel:
+            from .parallel import allreduce_gradients
+            allreduce_gradients(self.g)
+        self.apply_gradients()
+        return self.loss
+
+    def gradients(self, viewmat, intr, I_gt, mask=None):
+        """The loss of one view and its gradients w.r.t. every parameter array
+        (into ``self.g``, overwritten), and the densification statistics."""
         self.ctx.render_view(self.p, viewmat, intr, self.optics, self.opts, self.holo, None, self.saved)
         if self.objective == "paper":
             self.ctx.paper_loss(self.holo, I_gt, mask, 1, self.optics, self.loss, self.gholo, None,
@@ -116,9 +127,11 @@ class HologramTrainer:
         self.ctx.render_view_backward(self.saved, self.p, self.gholo, self.g)
         if self.densify_opts is not None:
             self.ctx.densify_accumulate(self.saved, self.accum, self.denom)
-        if self.data_parallel:
-            from .parallel import allreduce_gradients
-            allreduce_gradients(self.g)
+        return self.loss
+
+    def apply_gradients(self):
+        """The optimiser step with the gradients in ``self.g`` (and the
+        densification, when its period comes round)."""
         self.t += 1
         for k in PARAM_NAMES:
             lr = self.lr(k)
@@ -134,7 +147,6 @@ class HologramTrainer:
         if (self.densify_opts is not None and self.t % self.densify_every == 0
                 and (self.densify_until is None or self.t <= self.densify_until)):
             self.densify()
-        return self.loss
 
     # ---- checkpoint / resume ----
     STATE_KEYS = ("m", "v", "n", "g_prev")

@@ -378,7 +378,8 @@ def test_render_max_wavelengths_and_planes(P, ctx, footprint):
     saved.release()
     ref = oracle.render_backward(g, vm.astype(np.float64), it.astype(np.float64), o, gP.astype(np.complex128),
                                  oracle_opts(opts))
-    tol_g = 2e-2 if footprint else 1e-3
-    for k in P.PARAM_NAMES:
-        e = rel(grads[k].cpu().numpy(), ref[k])
+    tol_g = 1e-2 if footprint else 1e-3
+    errs = {k: rel(grads[k].cpu().numpy(), ref[k]) for k in P.PARAM_NAMES}
+    print("C = 4, L = 16, footprint tier %d: gradients" % footprint, {k: "%.2e" % e for k, e in errs.items()})
+    for k, e in errs.items():
         assert e < tol_g, (k, e)

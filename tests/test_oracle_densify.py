@@ -35,6 +35,20 @@ def test_philox_streams_are_distinct_and_uniform():
     assert stats.chisquare(counts).pvalue > 1e-4
 
 
+def test_uniform_map_is_the_open_interval_symmetric_about_one_half():
+    # the word -> uniform map: centres of the 2^32 cells of [0, 1).  The ends
+    # stay inside (0, 1), and u(w) + u(2^32 - 1 - w) = 1 exactly, which the
+    # map w 2^-32 (or (w + 1) 2^-32) breaks by 2^-32
+    top = 2 ** 32 - 1
+    w = np.array([0, 1, 2 ** 23 - 1, 2 ** 31 - 1, 2 ** 31, top - 5, top], dtype=np.uint32)
+    u = oracle.uniform_of_words(w)
+    assert u[0] == 2.0 ** -33 and u[-1] == 1.0 - 2.0 ** -33
+    assert np.all((u > 0) & (u < 1)) and np.all(np.diff(u) > 0)
+    assert np.array_equal(u + oracle.uniform_of_words(top - w.astype(np.int64)), np.ones(w.size))
+    # and it is what the uniforms of a stream are made of
+    assert np.array_equal(oracle.philox_uniforms(3, 9, 2), oracle.uniform_of_words(oracle.philox_words(3, 9, 2)))
+
+
 def test_philox_normals_are_standard_normal():
     z = oracle.philox_normals(11, 400_000)
     assert abs(z.mean()) < 5 * 1.0 / math.sqrt(z.size)

@@ -173,6 +173,10 @@ PY_CASES = [
      "c0, c1, c2, c3 = hi0 ^ c1 ^ k0, lo1, hi1 ^ c3 ^ k1, lo0", D.test_philox_known_answers),
     ("Box-Muller radius", "philox_normals", "r = np.sqrt(-2.0 * np.log(u))", "r = np.sqrt(-np.log(u))",
      D.test_philox_normals_are_standard_normal),
+    ("uniforms without the half-cell offset", "uniform_of_words", "astype(np.float64) + 0.5)", "astype(np.float64) + 0.0)",
+     D.test_uniform_map_is_the_open_interval_symmetric_about_one_half),
+    ("uniforms offset by a whole cell", "uniform_of_words", "astype(np.float64) + 0.5)", "astype(np.float64) + 1.0)",
+     D.test_uniform_map_is_the_open_interval_symmetric_about_one_half),
     ("densification: small Gaussians split", "densify_actions",
      'act[dens & (smax <= f(o["split_scale"]))] = CLONE', 'act[dens & (smax <= f(o["split_scale"]))] = SPLIT',
      D.test_actions_follow_the_thresholds),

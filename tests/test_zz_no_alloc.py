@@ -60,3 +60,22 @@ def test_noalloc_rejects_requests_beyond_its_scratch():
     x = torch.zeros((B, C, H, W), dtype=torch.complex64, device="cuda")
     out = torch.zeros((B, L, C, H, W), dtype=torch.complex64, device="cuda")
     assert _call(P, x, B, o, out) == -3  # HCGS_ERR_CAPACITY, before any launch
+
+
+def test_noalloc_rejects_overlapping_input_and_output():
+    # `out` is written while `in` is still being read, so a partial overlap is
+    # as wrong as `in == out`: both are refused before any launch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2506_08350_b300 as P
+    H, W, L, C, B = 64, 64, 2, 1, 1
+    o = S.Optics(H, W, (515e-9,), (0.0, 1e-3))
+    n = B * C * H * W
+    buf = torch.zeros(n * (L + 2), dtype=torch.complex64, device="cuda")
+    x = buf[:n]
+    for start in (0, n // 2, n - 1):
+        out = buf[start:start + n * L]
+        assert _call(P, x, B, o, out) == -1  # HCGS_ERR_INVALID_ARG
+    # adjacent, not overlapping: accepted
+    assert _call(P, x, B, o, buf[n:n + n * L]) == 0
+    torch.cuda.synchronize()
