@@ -347,6 +347,65 @@ def measure_losses(ctx, P, S, o, dev, peak_gbs, steps=10, warmup=3):
     return out
 
 
+# Algorithmic FLOPs per row of the learned-initialisation network
+# (16 -> 128 -> 128 -> 128 -> 16): the forward's four products, 2 x 36 864
+# multiply-adds; the reverse mode's weight gradients (the same 36 864 MACs)
+# and input gradients of layers 4, 3, 2 (34 816 MACs; the input features need
+# none).  The reverse kernel's recomputation of the forward is not counted.
+MLP_FWD_FLOP = 2 * (16 * 128 + 128 * 128 + 128 * 128 + 128 * 16)
+MLP_BWD_FLOP = MLP_FWD_FLOP + 2 * (128 * 16 + 128 * 128 + 128 * 128)
+
+
+def measure_mlp(ctx, P, dev, peaks, steps=20, warmup=3):
+    """Forward and reverse mode of the learned-initialisation network on the
+    tensor cores: inference over 1 048 576 rows (one row per Gaussian of the
+    bench scene) and the reverse mode over the same rows, CUDA events on the
+    current stream, with their rate against the measured BF16 tensor peak;
+    and one fit step of the network's training (forward, MSE, reverse mode,
+    Adam on the FP32 master weights, BF16 cast) on a 65 536-row batch."""
+    import torch
+    from paper_2506_08350_b300.learned_init import InitNet
+    st = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(steps):
+            fn()
+        e1.record(st)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    net = InitNet(ctx, seed=0, device=dev)
+    N = 1 << 20
+    rng = np.random.default_rng(7)
+    xf = torch.from_numpy(rng.uniform(-1, 1, size=(N, 16)).astype(np.float32)).to(dev)
+    x = torch.empty((N, 16), dtype=torch.int16, device=dev)
+    ctx.cast_bf16(xf, x)
+    y = torch.empty((N, 16), dtype=torch.float32, device=dev)
+    gy = torch.from_numpy(rng.normal(size=(N, 16)).astype(np.float32)).to(dev)
+    ms_f = timed(lambda: ctx.mlp_forward(x, net.W16, net.b32, y))
+    ms_b = timed(lambda: ctx.mlp_backward(x, net.W16, net.b32, gy, net.gW, net.gb))
+    B = 1 << 16
+    tgt = torch.from_numpy(rng.normal(size=(B, 16)).astype(np.float32)).to(dev)
+    yb, gyb = torch.empty((B, 16), dtype=torch.float32, device=dev), torch.empty((B, 16), dtype=torch.float32, device=dev)
+    ms_fit = timed(lambda: net.train_step(x[:B], tgt, 6, 1e-4, yb, gyb))
+    peak = (peaks or {}).get("bf16_tflops", 1800.0)
+    tf_f = N * MLP_FWD_FLOP / (ms_f * 1e-3) / 1e12
+    tf_b = N * MLP_BWD_FLOP / (ms_b * 1e-3) / 1e12
+    out = {"rows": N, "flop_per_row_fwd": MLP_FWD_FLOP, "flop_per_row_bwd": MLP_BWD_FLOP,
+           "k_mlp_fwd": {"ms": ms_f, "tflops": tf_f, "frac": tf_f / peak},
+           "k_mlp_bwd": {"ms": ms_b, "tflops": tf_b, "frac": tf_b / peak},
+           "peak_tflops": peak, "peak_source": "measured bf16 burst (cuBLAS) of MEASURED_PEAKS.json"
+           if peaks else "fallback",
+           "fit_step_65536_rows_ms": ms_fit}
+    del xf, x, y, gy, tgt, yb, gyb, net
+    return out
+
+
 def run_ours(args):
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -540,6 +599,12 @@ def run_ours(args):
                                                                  objective="paper", optimizer="adan", anneal=True,
                                                                  densify=dict(P.DEFAULT_DENSIFY))
 
+    # --- the learned-initialisation network on the tensor cores ---
+    mlp = None
+    if not args.no_configs and rank == 0:
+        pk = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else None
+        mlp = measure_mlp(ctx, P, dev, pk)
+
     # --- the two objectives on one view of this workload's optics ---
     objective = None
     if not args.no_configs and rank == 0:
@@ -568,6 +633,8 @@ def run_ours(args):
         result["configs"] = configs
     if objective is not None:
         result["objective"] = objective
+    if mlp is not None:
+        result["learned_init_mlp"] = mlp
     # --- roofline of the dominant kernel ---
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else None
     hbm_peak = peaks["hbm_gbs"] if peaks else 6400.0

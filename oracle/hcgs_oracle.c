@@ -187,15 +187,19 @@ void oracle_project(int N, int L, int C, int H, int W,
 }
 
 /* ---------- depth order ---------- */
+/* The visiting order compares depth keys: the camera-space depth rounded
+ * once to FP32 (the precision in which the order is decided; Gaussians whose
+ * keys are equal are visited by index). */
 static const double* g_sort_depth;
 static int cmp_front(const void* a, const void* b) {
     int i = *(const int*)a, j = *(const int*)b;
-    if (g_sort_depth[i] < g_sort_depth[j]) return -1;
-    if (g_sort_depth[i] > g_sort_depth[j]) return 1;
+    const float di = (float)g_sort_depth[i], dj = (float)g_sort_depth[j];
+    if (di < dj) return -1;
+    if (di > dj) return 1;
     return (i > j) - (i < j);
 }
 
-/* Writes the visiting order: ascending (depth, index) for front-to-back,
+/* Writes the visiting order: ascending (depth key, index) for front-to-back,
  * the exact reverse for back-to-front.  Only valid Gaussians are listed. */
 int oracle_sort(int N, const double* depth, const int* valid, int order, int* out) {
     int m = 0;

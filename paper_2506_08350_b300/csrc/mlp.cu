@@ -1,28 +1,34 @@
 // Learned-initialisation network (no counterpart in the paper): a 4-layer
 // ReLU MLP 16 -> 128 -> 128 -> 128 -> 16 with BF16 operands and FP32
-// accumulation on the tensor cores (mma.m16n8k16), forward and reverse mode.
+// accumulation on the fifth-generation tensor cores (tcgen05.mma, kind::f16,
+// accumulators in tensor memory), forward and reverse mode.
 //
-// Forward: each warp owns 16 rows; activations stay in shared memory as BF16;
-// weights are read as B fragments through L1.  Reverse mode: a CTA owns 128
-// rows, recomputes the forward into shared memory, then per layer computes
-// the bias and weight gradients over its 128 rows (weight gradient = a
-// tensor-core product with k = 128 rows, added once per CTA) and the input
-// gradient of the next layer down.
+// One CTA of 128 threads (one warpgroup) per SM slot, persistent over tiles
+// of 128 rows; thread t owns row t of the tile in every epilogue (TMEM lane t
+// holds row t of an M = 128 accumulator).  The weights stay in shared memory
+// for the CTA's lifetime, in core-matrix form: 8 x 8 blocks of BF16 (8 rows,
+// 16 contiguous bytes each) that serve as K-major operands (features along K)
+// and, read through the other descriptor mode, as MN-major operands (features
+// along M or N), so one copy of W is both W^T in the forward and W in the
+// input gradients.  One elected thread issues the MMAs and commits them to an
+// mbarrier; every thread waits on it (bounded), reads its accumulator row
+// with tcgen05.ld, applies bias / ReLU / the ReLU mask in FP32, rounds to
+// BF16 and writes the next operand back to shared memory.
+//
+// Reverse mode recomputes the forward of the tile (the activations H1..H3
+// stay in shared memory), then per layer l: the weight gradient
+// dW_l += dZ_l^T H_{l-1} accumulates in TMEM over all tiles of the CTA (the
+// bias gradient rides along as one extra column: H_{l-1} carries a block of
+// ones, so that column is sum_rows dZ_l), and the input gradient dZ_l W_l,
+// masked by the ReLU decisions kept from the forward, gives dZ_{l-1}.  At the
+// end each CTA adds its accumulators to the outputs once.
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace hcgs {
 
 constexpr int MLP_IN = 16, MLP_HID = 128, MLP_OUT = 16;
-constexpr int LDI = MLP_IN + 8;    // padded row strides (bf16 elements) against bank conflicts
-constexpr int LDH = MLP_HID + 8;
-
-__device__ __forceinline__ void mma16816(float* d, const uint32_t* a, const uint32_t* b) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
 
 __device__ __forceinline__ uint16_t f2bf(float x) {
     // round to nearest even
@@ -31,52 +37,172 @@ __device__ __forceinline__ uint16_t f2bf(float x) {
     u += 0x7fffu + ((u >> 16) & 1u);
     return (uint16_t)(u >> 16);
 }
-__device__ __forceinline__ float bf2f(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
-__device__ __forceinline__ uint32_t pack2(uint16_t lo, uint16_t hi) { return (uint32_t)lo | ((uint32_t)hi << 16); }
-__device__ __forceinline__ uint32_t ld32(const uint16_t* p) { return *reinterpret_cast<const uint32_t*>(p); }
-
-// A fragment of a row-major 16 x 16 block at X (leading dimension ld).
-__device__ __forceinline__ void frag_a(uint32_t* a, const uint16_t* X, int ld, int k0, int gid, int tig) {
-    a[0] = ld32(X + gid * ld + k0 + 2 * tig);
-    a[1] = ld32(X + (gid + 8) * ld + k0 + 2 * tig);
-    a[2] = ld32(X + gid * ld + k0 + 8 + 2 * tig);
-    a[3] = ld32(X + (gid + 8) * ld + k0 + 8 + 2 * tig);
-}
-// B fragment for y = x W^T with W row-major [nout][K]: B(k, n) = W[n0 + n][k0 + k].
-__device__ __forceinline__ void frag_b(uint32_t* b, const uint16_t* W, int K, int n0, int k0, int gid, int tig) {
-    b[0] = __ldg(reinterpret_cast<const unsigned int*>(W + (size_t)(n0 + gid) * K + k0 + 2 * tig));
-    b[1] = __ldg(reinterpret_cast<const unsigned int*>(W + (size_t)(n0 + gid) * K + k0 + 8 + 2 * tig));
+// (lo, hi) -> packed bf16x2, round to nearest even
+__device__ __forceinline__ uint32_t pack_bf2(float lo, float hi) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-// One layer for the warp's 16 rows: Y = act(X W^T + b), Y as BF16 in smem.
-template <int K, int NOUT, bool RELU>
-__device__ __forceinline__ void layer_smem(const uint16_t* X, int ldx, const uint16_t* W, const float* bias,
-                                           uint16_t* Y, int ldy, int gid, int tig) {
-#pragma unroll 2
-    for (int nt = 0; nt < NOUT / 8; nt++) {
-        const int n0 = nt * 8;
-        const float b0 = bias[n0 + 2 * tig], b1 = bias[n0 + 2 * tig + 1];
-        float d[4] = {b0, b1, b0, b1};
+// ---- tcgen05 (inline PTX) ----
+__device__ __forceinline__ void tc_alloc(uint32_t* slot, uint32_t ncols) {  // whole warp
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tc_dealloc(uint32_t taddr, uint32_t ncols) {  // whole warp
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// D[tmem] (+)= A B^T, A from descriptor a (M x 16), B from descriptor b (N x 16)
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, int acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+// the mbarrier's phase completes once every MMA issued so far by this thread is done
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// 32 (16) consecutive FP32 columns of this thread's TMEM lane from taddr
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+    tc_wait_ld();
 #pragma unroll
-        for (int kt = 0; kt < K / 16; kt++) {
-            uint32_t a[4], b[2];
-            frag_a(a, X, ldx, kt * 16, gid, tig);
-            frag_b(b, W, K, n0, kt * 16, gid, tig);
-            mma16816(d, a, b);
-        }
-        if (RELU)
-            for (int e = 0; e < 4; e++) d[e] = fmaxf(d[e], 0.f);
-        *reinterpret_cast<uint32_t*>(Y + gid * ldy + n0 + 2 * tig) = pack2(f2bf(d[0]), f2bf(d[1]));
-        *reinterpret_cast<uint32_t*>(Y + (gid + 8) * ldy + n0 + 2 * tig) = pack2(f2bf(d[2]), f2bf(d[3]));
+    for (int j = 0; j < 32; j++) v[j] = __uint_as_float(r[j]);
+}
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    tc_wait_ld();
+#pragma unroll
+    for (int j = 0; j < 16; j++) v[j] = __uint_as_float(r[j]);
+}
+
+// Core-matrix layout of an R x F BF16 matrix (F features per row, both
+// multiples of 8): element (r, f) at byte ((r / 8) (F / 8) + f / 8) 128 +
+// (r % 8) 16 + (f % 8) 2, i.e. 8-row groups, each a run of F / 8 blocks of
+// 8 x 8 elements.
+__host__ __device__ constexpr uint32_t cm_off(int r, int f, int F) {
+    return (uint32_t)((((r >> 3) * (F >> 3) + (f >> 3)) << 7) + ((r & 7) << 4) + ((f & 7) << 1));
+}
+// Shared-memory matrix descriptor without swizzling: start address, the
+// stride between core matrices along K (lbo) and along M / N (sbo), in bytes.
+__device__ __forceinline__ uint64_t sm_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// Operand views of a core-matrix buffer at saddr with F features, for the
+// MMA's K-step s (16 elements of K):
+//  K-major: rows along M / N, features along K (features 16 s .. 16 s + 15);
+//  MN-major: features along M / N, rows along K (rows 16 s .. 16 s + 15).
+__device__ __forceinline__ uint64_t op_k(uint32_t saddr, int F, int s) {
+    return sm_desc(saddr + (uint32_t)s * 256u, 128u, (uint32_t)F * 16u);
+}
+__device__ __forceinline__ uint64_t op_mn(uint32_t saddr, int F, int s) {
+    return sm_desc(saddr + (uint32_t)s * (uint32_t)F * 32u, (uint32_t)F * 16u, 128u);
+}
+// Instruction descriptor of kind::f16: BF16 A and B, FP32 D, M x N, each
+// operand K-major (0) or MN-major (1).
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N, int a_mn, int b_mn) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Copy an R x F row-major BF16 matrix (16-byte aligned rows) into core-matrix form.
+__device__ __forceinline__ void load_cm(uint8_t* dst, const uint16_t* __restrict__ src, int R, int F) {
+    const int chunks = R * (F >> 3);
+    for (int i = threadIdx.x; i < chunks; i += blockDim.x) {
+        const int r = i / (F >> 3), j = i % (F >> 3);
+        *reinterpret_cast<uint4*>(dst + cm_off(r, 8 * j, F)) =
+            __ldg(reinterpret_cast<const uint4*>(src + (size_t)r * F + 8 * j));
     }
 }
 
-__device__ __forceinline__ void load_x(uint16_t* xs, const uint16_t* x, int row0, int N, int lane) {
-    for (int e = lane; e < 16 * MLP_IN; e += 32) {
-        const int r = e / MLP_IN, c = e % MLP_IN;
-        xs[r * LDI + c] = row0 + r < N ? x[(size_t)(row0 + r) * MLP_IN + c] : (uint16_t)0;
+// Make the threads' shared-memory writes visible to the tensor cores and
+// order everything before the next MMA issue.
+__device__ __forceinline__ void sync_for_mma() {
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+}
+
+// Bounded wait of every thread for the MMA phase; all threads agree on the
+// outcome.  On a timeout the status word records it.
+__device__ __forceinline__ bool wait_mma(uint64_t* bar, uint32_t& phase, int* status) {
+    const bool ok = mbar_wait(bar, phase);
+    phase ^= 1u;
+    const int bad = __syncthreads_or(!ok);
+    if (bad && threadIdx.x == 0) atomicOr(status, STATUS_WAIT_TIMEOUT);
+    tc_fence_after();
+    return !bad;
+}
+
+// Hidden-layer epilogue of this thread's row: h = bf16(relu(z + b)) for the
+// 128 accumulator columns at taddr, written to the core-matrix buffer H (F
+// features per row) at row r; mask bit j of word c = (h_{32c + j} > 0).
+__device__ __forceinline__ void epi_hidden(uint32_t taddr, const float* b, uint8_t* H, int F, int r,
+                                           uint32_t (&mask)[4]) {
+#pragma unroll 1
+    for (int c = 0; c < 4; c++) {
+        float v[32];
+        tc_ld32(taddr + 32 * c, v);
+        uint32_t p[16], m = 0;
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+            const float lo = fmaxf(v[2 * j] + b[32 * c + 2 * j], 0.f);
+            const float hi = fmaxf(v[2 * j + 1] + b[32 * c + 2 * j + 1], 0.f);
+            p[j] = pack_bf2(lo, hi);
+            m |= ((p[j] & 0xFFFFu) != 0u ? 1u : 0u) << (2 * j);
+            m |= ((p[j] >> 16) != 0u ? 1u : 0u) << (2 * j + 1);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+            *reinterpret_cast<uint4*>(H + cm_off(r, 32 * c + 8 * q, F)) =
+                make_uint4(p[4 * q], p[4 * q + 1], p[4 * q + 2], p[4 * q + 3]);
+        mask[c] = m;
     }
-    __syncwarp();
+}
+
+// Gradient epilogue: dZ = bf16(dH masked by the ReLU decisions) into G (128 features).
+__device__ __forceinline__ void epi_grad(uint32_t taddr, const uint32_t (&mask)[4], uint8_t* G, int r) {
+#pragma unroll 1
+    for (int c = 0; c < 4; c++) {
+        float v[32];
+        tc_ld32(taddr + 32 * c, v);
+        uint32_t p[16];
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+            const float lo = (mask[c] >> (2 * j)) & 1u ? v[2 * j] : 0.f;
+            const float hi = (mask[c] >> (2 * j + 1)) & 1u ? v[2 * j + 1] : 0.f;
+            p[j] = pack_bf2(lo, hi);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+            *reinterpret_cast<uint4*>(G + cm_off(r, 32 * c + 8 * q, MLP_HID)) =
+                make_uint4(p[4 * q], p[4 * q + 1], p[4 * q + 2], p[4 * q + 3]);
+    }
 }
 
 struct MlpW {
@@ -84,167 +210,306 @@ struct MlpW {
     const float *b1, *b2, *b3, *b4;
 };
 
-constexpr size_t MLP_FWD_SMEM = (size_t)8 * 16 * (LDI + 2 * LDH) * sizeof(uint16_t);
+// ---------------------------------------------------------------------------
+// forward: y = W4 relu(W3 relu(W2 relu(W1 x + b1) + b2) + b3) + b4
+// ---------------------------------------------------------------------------
+// shared memory (bytes): W1 [128][16], W2, W3 [128][128], W4 [16][128], the
+// X tile [128][16], one hidden tile [128][128] (reused by every layer), biases
+constexpr uint32_t FS_W1 = 0, FS_W2 = FS_W1 + 128 * 16 * 2, FS_W3 = FS_W2 + 128 * 128 * 2,
+                   FS_W4 = FS_W3 + 128 * 128 * 2, FS_X = FS_W4 + 16 * 128 * 2, FS_H = FS_X + 128 * 16 * 2,
+                   FS_B = FS_H + 128 * 128 * 2, FS_BAR = FS_B + (3 * 128 + 16) * 4, FS_END = FS_BAR + 16;
+constexpr uint32_t F_TMEM_COLS = 256;  // [0, 128) hidden accumulator, [128, 144) output
 
-__global__ void __launch_bounds__(256) k_mlp_fwd(MlpW w, const uint16_t* __restrict__ x, int N,
-                                                 float* __restrict__ y) {
-    extern __shared__ __align__(16) uint16_t fsm[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
-    uint16_t* sx = fsm + warp * 16 * (LDI + 2 * LDH);
-    uint16_t* sa = sx + 16 * LDI;
-    uint16_t* sb = sa + 16 * LDH;
-    const int row0 = (blockIdx.x * 8 + warp) * 16;
-    if (row0 >= N) return;
-    load_x(sx, x, row0, N, lane);
-    layer_smem<MLP_IN, MLP_HID, true>(sx, LDI, w.W1, w.b1, sa, LDH, gid, tig);
-    __syncwarp();
-    layer_smem<MLP_HID, MLP_HID, true>(sa, LDH, w.W2, w.b2, sb, LDH, gid, tig);
-    __syncwarp();
-    layer_smem<MLP_HID, MLP_HID, true>(sb, LDH, w.W3, w.b3, sa, LDH, gid, tig);
-    __syncwarp();
-    // output layer, FP32
-    for (int nt = 0; nt < MLP_OUT / 8; nt++) {
-        const int n0 = nt * 8;
-        const float b0 = w.b4[n0 + 2 * tig], b1 = w.b4[n0 + 2 * tig + 1];
-        float d[4] = {b0, b1, b0, b1};
+__global__ void __launch_bounds__(128, 2) k_mlp_fwd(MlpW w, const uint16_t* __restrict__ x, int N,
+                                                    float* __restrict__ y, int* __restrict__ status) {
+    extern __shared__ __align__(1024) uint8_t sm[];
+    const int tid = threadIdx.x, warp = tid >> 5;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + FS_BAR);
+    uint32_t* slot = reinterpret_cast<uint32_t*>(sm + FS_BAR + 8);
+    float* sb = reinterpret_cast<float*>(sm + FS_B);
+    if (warp == 0) tc_alloc(slot, F_TMEM_COLS);
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        mbar_init_fence();
+    }
+    load_cm(sm + FS_W1, w.W1, MLP_HID, MLP_IN);
+    load_cm(sm + FS_W2, w.W2, MLP_HID, MLP_HID);
+    load_cm(sm + FS_W3, w.W3, MLP_HID, MLP_HID);
+    load_cm(sm + FS_W4, w.W4, MLP_OUT, MLP_HID);
+    sb[tid] = w.b1[tid];
+    sb[128 + tid] = w.b2[tid];
+    sb[256 + tid] = w.b3[tid];
+    if (tid < MLP_OUT) sb[384 + tid] = w.b4[tid];
+    sync_for_mma();
+    const uint32_t tm = *slot;
+    const uint32_t tl = tm + ((uint32_t)(warp * 32) << 16);  // this warp's TMEM lanes
+    const uint32_t sa = smem_addr(sm);
+    constexpr uint32_t ID_H = tc_idesc(128, 128, 0, 0), ID_O = tc_idesc(128, 16, 0, 0);
+    uint32_t phase = 0, mask[4];
+    const int ntiles = (N + 127) / 128;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int row = t * 128 + tid;
+        uint4 x0 = make_uint4(0, 0, 0, 0), x1 = x0;
+        if (row < N) {
+            const uint4* xr = reinterpret_cast<const uint4*>(x + (size_t)row * MLP_IN);
+            x0 = __ldg(xr);
+            x1 = __ldg(xr + 1);
+        }
+        *reinterpret_cast<uint4*>(sm + FS_X + cm_off(tid, 0, MLP_IN)) = x0;
+        *reinterpret_cast<uint4*>(sm + FS_X + cm_off(tid, 8, MLP_IN)) = x1;
+        sync_for_mma();
+        if (tid == 0) {
+            tc_mma(tm, op_k(sa + FS_X, MLP_IN, 0), op_k(sa + FS_W1, MLP_IN, 0), ID_H, 0);
+            tc_commit(bar);
+        }
+        if (!wait_mma(bar, phase, status)) break;
+        epi_hidden(tl, sb, sm + FS_H, MLP_HID, tid, mask);
+        bool ok = true;
+#pragma unroll 1
+        for (int layer = 0; layer < 2 && ok; layer++) {
+            const uint32_t Wl = layer == 0 ? FS_W2 : FS_W3;
+            sync_for_mma();
+            if (tid == 0) {
 #pragma unroll
-        for (int kt = 0; kt < MLP_HID / 16; kt++) {
-            uint32_t a[4], b[2];
-            frag_a(a, sa, LDH, kt * 16, gid, tig);
-            frag_b(b, w.W4, MLP_HID, n0, kt * 16, gid, tig);
-            mma16816(d, a, b);
+                for (int s = 0; s < 8; s++) tc_mma(tm, op_k(sa + FS_H, MLP_HID, s), op_k(sa + Wl, MLP_HID, s), ID_H, s);
+                tc_commit(bar);
+            }
+            ok = wait_mma(bar, phase, status);
+            if (ok) epi_hidden(tl, sb + 128 * (layer + 1), sm + FS_H, MLP_HID, tid, mask);
         }
-        const int r0 = row0 + gid, r1 = row0 + gid + 8;
-        if (r0 < N) { y[(size_t)r0 * MLP_OUT + n0 + 2 * tig] = d[0]; y[(size_t)r0 * MLP_OUT + n0 + 2 * tig + 1] = d[1]; }
-        if (r1 < N) { y[(size_t)r1 * MLP_OUT + n0 + 2 * tig] = d[2]; y[(size_t)r1 * MLP_OUT + n0 + 2 * tig + 1] = d[3]; }
-    }
-}
-
-// W [rows][cols] -> Wt [cols][rows] (bf16)
-__global__ void k_transpose_bf16(const uint16_t* __restrict__ W, uint16_t* __restrict__ Wt, int rows, int cols) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= rows * cols) return;
-    const int r = i / cols, c = i % cols;
-    Wt[(size_t)c * rows + r] = W[i];
-}
-
-// CTA-level weight gradient over 128 rows: gW[o][i] += sum_r gZ[r][o] X[r][i].
-// gZ: smem [128][ldz] bf16, X: smem [128][ldx] bf16.
-template <int NOUT, int K>
-__device__ void weight_grad(const uint16_t* gZ, int ldz, const uint16_t* X, int ldx, float* gW, int warp, int gid,
-                            int tig) {
-    constexpr int MT = NOUT / 16, NT = K / 8;
-    for (int p = warp; p < MT * NT; p += 8) {
-        const int m0 = (p / NT) * 16, n0 = (p % NT) * 8;
-        float d[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 4
-        for (int k0 = 0; k0 < 128; k0 += 16) {
-            uint32_t a[4], b[2];
-            // A(m, k) = gZ[k0 + k][m0 + m]
-            a[0] = pack2(gZ[(k0 + 2 * tig) * ldz + m0 + gid], gZ[(k0 + 2 * tig + 1) * ldz + m0 + gid]);
-            a[1] = pack2(gZ[(k0 + 2 * tig) * ldz + m0 + gid + 8], gZ[(k0 + 2 * tig + 1) * ldz + m0 + gid + 8]);
-            a[2] = pack2(gZ[(k0 + 2 * tig + 8) * ldz + m0 + gid], gZ[(k0 + 2 * tig + 9) * ldz + m0 + gid]);
-            a[3] = pack2(gZ[(k0 + 2 * tig + 8) * ldz + m0 + gid + 8], gZ[(k0 + 2 * tig + 9) * ldz + m0 + gid + 8]);
-            // B(k, n) = X[k0 + k][n0 + n]
-            b[0] = pack2(X[(k0 + 2 * tig) * ldx + n0 + gid], X[(k0 + 2 * tig + 1) * ldx + n0 + gid]);
-            b[1] = pack2(X[(k0 + 2 * tig + 8) * ldx + n0 + gid], X[(k0 + 2 * tig + 9) * ldx + n0 + gid]);
-            mma16816(d, a, b);
-        }
-        atomicAdd(gW + (m0 + gid) * K + n0 + 2 * tig, d[0]);
-        atomicAdd(gW + (m0 + gid) * K + n0 + 2 * tig + 1, d[1]);
-        atomicAdd(gW + (m0 + gid + 8) * K + n0 + 2 * tig, d[2]);
-        atomicAdd(gW + (m0 + gid + 8) * K + n0 + 2 * tig + 1, d[3]);
-    }
-}
-
-// Column sums of gZ[128][ldz] (first NOUT columns) into gb.
-template <int NOUT>
-__device__ void bias_grad(const uint16_t* gZ, int ldz, float* gb, int rows) {
-    for (int c = threadIdx.x; c < NOUT; c += blockDim.x) {
-        float s = 0.f;
-        for (int r = 0; r < rows; r++) s += bf2f(gZ[r * ldz + c]);
-        atomicAdd(gb + c, s);
-    }
-}
-
-// Input gradient for the warp's 16 rows: gX = (gZ W) masked by (H > 0),
-// written as BF16.  Wt is W transposed: [K][NOUT] row-major.
-template <int NOUT, int K>
-__device__ __forceinline__ void input_grad(const uint16_t* gZ, int ldz, const uint16_t* Wt, const uint16_t* Hm,
-                                           int ldh, uint16_t* gX, int ldg, int gid, int tig) {
-    for (int nt = 0; nt < K / 8; nt++) {
-        const int n0 = nt * 8;
-        float d[4] = {0.f, 0.f, 0.f, 0.f};
+        if (!ok) break;
+        sync_for_mma();
+        if (tid == 0) {
 #pragma unroll
-        for (int kt = 0; kt < NOUT / 16; kt++) {
-            uint32_t a[4], b[2];
-            frag_a(a, gZ, ldz, kt * 16, gid, tig);
-            frag_b(b, Wt, NOUT, n0, kt * 16, gid, tig);
-            mma16816(d, a, b);
+            for (int s = 0; s < 8; s++)
+                tc_mma(tm + 128, op_k(sa + FS_H, MLP_HID, s), op_k(sa + FS_W4, MLP_HID, s), ID_O, s);
+            tc_commit(bar);
         }
-        const int c = n0 + 2 * tig;
-        const float m0 = bf2f(Hm[gid * ldh + c]) > 0.f ? 1.f : 0.f, m1 = bf2f(Hm[gid * ldh + c + 1]) > 0.f ? 1.f : 0.f;
-        const float m2 = bf2f(Hm[(gid + 8) * ldh + c]) > 0.f ? 1.f : 0.f, m3 = bf2f(Hm[(gid + 8) * ldh + c + 1]) > 0.f ? 1.f : 0.f;
-        *reinterpret_cast<uint32_t*>(gX + gid * ldg + c) = pack2(f2bf(d[0] * m0), f2bf(d[1] * m1));
-        *reinterpret_cast<uint32_t*>(gX + (gid + 8) * ldg + c) = pack2(f2bf(d[2] * m2), f2bf(d[3] * m3));
+        if (!wait_mma(bar, phase, status)) break;
+        float o[16];
+        tc_ld16(tl + 128, o);
+        if (row < N) {
+            float4* yr = reinterpret_cast<float4*>(y + (size_t)row * MLP_OUT);
+#pragma unroll
+            for (int q = 0; q < 4; q++)
+                yr[q] = make_float4(o[4 * q] + sb[384 + 4 * q], o[4 * q + 1] + sb[385 + 4 * q],
+                                    o[4 * q + 2] + sb[386 + 4 * q], o[4 * q + 3] + sb[387 + 4 * q]);
+        }
     }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tc_dealloc(tm, F_TMEM_COLS);
 }
+
+// ---------------------------------------------------------------------------
+// reverse mode
+// ---------------------------------------------------------------------------
+// shared memory (bytes): the weights as in the forward; X extended to 32
+// features (x | 1 0 ... 0); H1, H2 extended to 144 (h | 1 0 ... 0); H3; the
+// output gradient tile dZ4 [128][16]; one gradient tile dZ [128][128]; biases
+constexpr int FX = 32, FHE = 144;
+constexpr uint32_t BS_W1 = 0, BS_W2 = BS_W1 + 128 * 16 * 2, BS_W3 = BS_W2 + 128 * 128 * 2,
+                   BS_W4 = BS_W3 + 128 * 128 * 2, BS_X = BS_W4 + 16 * 128 * 2, BS_H1 = BS_X + 128 * FX * 2,
+                   BS_H2 = BS_H1 + 128 * FHE * 2, BS_H3 = BS_H2 + 128 * FHE * 2, BS_G4 = BS_H3 + 128 * 128 * 2,
+                   BS_GZ = BS_G4 + 128 * 16 * 2, BS_B = BS_GZ + 128 * 128 * 2, BS_BAR = BS_B + 3 * 128 * 4,
+                   BS_END = BS_BAR + 16;
+// TMEM columns: per-tile accumulator, then the gradients kept over all tiles
+constexpr uint32_t BT_Z = 0, BT_GW3 = 128, BT_GW2 = 288, BT_GW1 = 448, BT_GW4 = 480, B_TMEM_COLS = 512;
 
 struct MlpG {
     float *gW1, *gW2, *gW3, *gW4, *gb1, *gb2, *gb3, *gb4;
-    const uint16_t *W2t, *W3t, *W4t;
 };
 
-constexpr size_t MLP_BWD_SMEM = (size_t)128 * (LDI + 3 * LDH + LDH + LDI) * sizeof(uint16_t);
+// the ones block of an extended buffer: feature F0 = 1, F0 + 1 .. F0 + 15 = 0
+__device__ __forceinline__ void ones_block(uint8_t* buf, int F, int F0, int r) {
+    const uint32_t one = 0x3F80u;  // bf16 1.0
+    *reinterpret_cast<uint4*>(buf + cm_off(r, F0, F)) = make_uint4(one, 0u, 0u, 0u);
+    *reinterpret_cast<uint4*>(buf + cm_off(r, F0 + 8, F)) = make_uint4(0u, 0u, 0u, 0u);
+}
 
-__global__ void __launch_bounds__(256) k_mlp_bwd(MlpW w, MlpG g, const uint16_t* __restrict__ x, int N,
-                                                 const float* __restrict__ gy) {
-    extern __shared__ __align__(16) uint16_t smem[];
-    uint16_t* sx = smem;                    // [128][LDI]
-    uint16_t* h1 = sx + 128 * LDI;          // [128][LDH]
-    uint16_t* h2 = h1 + 128 * LDH;
-    uint16_t* h3 = h2 + 128 * LDH;
-    uint16_t* gz = h3 + 128 * LDH;          // [128][LDH] current layer's dL/dZ
-    uint16_t* gz4 = gz + 128 * LDH;         // [128][LDI] output layer's dL/dZ
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
-    const int row0 = blockIdx.x * 128 + warp * 16;
-    const int rows = min(128, N - (int)blockIdx.x * 128);
-    // forward recompute for this warp's rows
-    load_x(sx + warp * 16 * LDI, x, row0, N, lane);
-    layer_smem<MLP_IN, MLP_HID, true>(sx + warp * 16 * LDI, LDI, w.W1, w.b1, h1 + warp * 16 * LDH, LDH, gid, tig);
-    __syncwarp();
-    layer_smem<MLP_HID, MLP_HID, true>(h1 + warp * 16 * LDH, LDH, w.W2, w.b2, h2 + warp * 16 * LDH, LDH, gid, tig);
-    __syncwarp();
-    layer_smem<MLP_HID, MLP_HID, true>(h2 + warp * 16 * LDH, LDH, w.W3, w.b3, h3 + warp * 16 * LDH, LDH, gid, tig);
-    // output-layer gradient (rows past N are zero)
-    for (int e = lane; e < 16 * MLP_OUT; e += 32) {
-        const int r = e / MLP_OUT, c = e % MLP_OUT;
-        gz4[(warp * 16 + r) * LDI + c] = row0 + r < N ? f2bf(gy[(size_t)(row0 + r) * MLP_OUT + c]) : (uint16_t)0;
+// 32 FP32 values of a TMEM row added to global memory (16-byte aligned)
+__device__ __forceinline__ void red_add32(float* dst, const float (&v)[32]) {
+#pragma unroll
+    for (int q = 0; q < 8; q++)
+        atomicAdd(reinterpret_cast<float4*>(dst) + q, make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
+}
+
+__global__ void __launch_bounds__(128, 1) k_mlp_bwd(MlpW w, MlpG g, const uint16_t* __restrict__ x, int N,
+                                                    const float* __restrict__ gy, int* __restrict__ status) {
+    extern __shared__ __align__(1024) uint8_t sm[];
+    const int tid = threadIdx.x, warp = tid >> 5;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + BS_BAR);
+    uint32_t* slot = reinterpret_cast<uint32_t*>(sm + BS_BAR + 8);
+    float* sb = reinterpret_cast<float*>(sm + BS_B);
+    if (warp == 0) tc_alloc(slot, B_TMEM_COLS);
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        mbar_init_fence();
+    }
+    load_cm(sm + BS_W1, w.W1, MLP_HID, MLP_IN);
+    load_cm(sm + BS_W2, w.W2, MLP_HID, MLP_HID);
+    load_cm(sm + BS_W3, w.W3, MLP_HID, MLP_HID);
+    load_cm(sm + BS_W4, w.W4, MLP_OUT, MLP_HID);
+    sb[tid] = w.b1[tid];
+    sb[128 + tid] = w.b2[tid];
+    sb[256 + tid] = w.b3[tid];
+    ones_block(sm + BS_X, FX, MLP_IN, tid);
+    ones_block(sm + BS_H1, FHE, MLP_HID, tid);
+    ones_block(sm + BS_H2, FHE, MLP_HID, tid);
+    sync_for_mma();
+    const uint32_t tm = *slot;
+    const uint32_t tl = tm + ((uint32_t)(warp * 32) << 16);
+    const uint32_t sa = smem_addr(sm);
+    constexpr uint32_t ID_FWD = tc_idesc(128, 128, 0, 0);   // Z = H W^T
+    constexpr uint32_t ID_IN = tc_idesc(128, 128, 0, 1);    // dH = dZ W
+    constexpr uint32_t ID_W4 = tc_idesc(128, 16, 1, 1);     // dW4^T = H3^T dZ4
+    constexpr uint32_t ID_WH = tc_idesc(128, FHE, 1, 1);    // [dW | db] = dZ^T [H | 1]
+    constexpr uint32_t ID_W1 = tc_idesc(128, FX, 1, 1);     // [dW1 | db1] = dZ1^T [X | 1]
+    uint32_t phase = 0, m1[4], m2[4], m3[4];
+    float gb4[16];
+#pragma unroll
+    for (int j = 0; j < 16; j++) gb4[j] = 0.f;
+    bool ok = true;
+    int ntile_cta = 0;
+    const int ntiles = (N + 127) / 128;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const int acc = ntile_cta > 0;  // accumulate onto the earlier tiles' weight gradients
+        const int row = t * 128 + tid;
+        uint4 x0 = make_uint4(0, 0, 0, 0), x1 = x0;
+        float gr[16];
+#pragma unroll
+        for (int j = 0; j < 16; j++) gr[j] = 0.f;
+        if (row < N) {
+            const uint4* xr = reinterpret_cast<const uint4*>(x + (size_t)row * MLP_IN);
+            x0 = __ldg(xr);
+            x1 = __ldg(xr + 1);
+            const float4* gq = reinterpret_cast<const float4*>(gy + (size_t)row * MLP_OUT);
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const float4 v = __ldg(gq + q);
+                gr[4 * q] = v.x; gr[4 * q + 1] = v.y; gr[4 * q + 2] = v.z; gr[4 * q + 3] = v.w;
+            }
+        }
+        *reinterpret_cast<uint4*>(sm + BS_X + cm_off(tid, 0, FX)) = x0;
+        *reinterpret_cast<uint4*>(sm + BS_X + cm_off(tid, 8, FX)) = x1;
+        // dZ4 = gy as BF16 (the tensor-core operand); the bias gradient of the
+        // output layer sums the same rounded values
+        uint32_t p[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            p[j] = pack_bf2(gr[2 * j], gr[2 * j + 1]);
+            gb4[2 * j] += __uint_as_float(p[j] << 16);
+            gb4[2 * j + 1] += __uint_as_float(p[j] & 0xFFFF0000u);
+        }
+        *reinterpret_cast<uint4*>(sm + BS_G4 + cm_off(tid, 0, 16)) = make_uint4(p[0], p[1], p[2], p[3]);
+        *reinterpret_cast<uint4*>(sm + BS_G4 + cm_off(tid, 8, 16)) = make_uint4(p[4], p[5], p[6], p[7]);
+        // forward recompute: H1, H2 (extended), H3 and the ReLU masks
+        sync_for_mma();
+        if (tid == 0) {
+            tc_mma(tm + BT_Z, op_k(sa + BS_X, FX, 0), op_k(sa + BS_W1, MLP_IN, 0), ID_FWD, 0);
+            tc_commit(bar);
+        }
+        if (!(ok = wait_mma(bar, phase, status))) break;
+        epi_hidden(tl + BT_Z, sb, sm + BS_H1, FHE, tid, m1);
+        sync_for_mma();
+        if (tid == 0) {
+#pragma unroll
+            for (int s = 0; s < 8; s++)
+                tc_mma(tm + BT_Z, op_k(sa + BS_H1, FHE, s), op_k(sa + BS_W2, MLP_HID, s), ID_FWD, s);
+            tc_commit(bar);
+        }
+        if (!(ok = wait_mma(bar, phase, status))) break;
+        epi_hidden(tl + BT_Z, sb + 128, sm + BS_H2, FHE, tid, m2);
+        sync_for_mma();
+        if (tid == 0) {
+#pragma unroll
+            for (int s = 0; s < 8; s++)
+                tc_mma(tm + BT_Z, op_k(sa + BS_H2, FHE, s), op_k(sa + BS_W3, MLP_HID, s), ID_FWD, s);
+            tc_commit(bar);
+        }
+        if (!(ok = wait_mma(bar, phase, status))) break;
+        epi_hidden(tl + BT_Z, sb + 256, sm + BS_H3, MLP_HID, tid, m3);
+        // layer 4: dW4^T += H3^T dZ4; dH3 = dZ4 W4
+        sync_for_mma();
+        if (tid == 0) {
+#pragma unroll
+            for (int s = 0; s < 8; s++)
+                tc_mma(tm + BT_GW4, op_mn(sa + BS_H3, MLP_HID, s), op_mn(sa + BS_G4, 16, s), ID_W4, acc | s);
+            tc_mma(tm + BT_Z, op_k(sa + BS_G4, 16, 0), op_mn(sa + BS_W4, MLP_HID, 0), ID_IN, 0);
+            tc_commit(bar);
+        }
+        if (!(ok = wait_mma(bar, phase, status))) break;
+        epi_grad(tl + BT_Z, m3, sm + BS_GZ, tid);
+        // layers 3, 2: [dW | db] += dZ^T [H | 1]; dH = dZ W
+#pragma unroll 1
+        for (int layer = 3; layer >= 2 && ok; layer--) {
+            const uint32_t Hprev = layer == 3 ? BS_H2 : BS_H1;
+            const uint32_t Wl = layer == 3 ? BS_W3 : BS_W2;
+            const uint32_t Dw = layer == 3 ? BT_GW3 : BT_GW2;
+            sync_for_mma();
+            if (tid == 0) {
+#pragma unroll
+                for (int s = 0; s < 8; s++)
+                    tc_mma(tm + Dw, op_mn(sa + BS_GZ, MLP_HID, s), op_mn(sa + Hprev, FHE, s), ID_WH, acc | s);
+#pragma unroll
+                for (int s = 0; s < 8; s++)
+                    tc_mma(tm + BT_Z, op_k(sa + BS_GZ, MLP_HID, s), op_mn(sa + Wl, MLP_HID, s), ID_IN, s);
+                tc_commit(bar);
+            }
+            if ((ok = wait_mma(bar, phase, status))) epi_grad(tl + BT_Z, layer == 3 ? m2 : m1, sm + BS_GZ, tid);
+        }
+        if (!ok) break;
+        // layer 1: [dW1 | db1] += dZ1^T [X | 1]
+        sync_for_mma();
+        if (tid == 0) {
+#pragma unroll
+            for (int s = 0; s < 8; s++)
+                tc_mma(tm + BT_GW1, op_mn(sa + BS_GZ, MLP_HID, s), op_mn(sa + BS_X, FX, s), ID_W1, acc | s);
+            tc_commit(bar);
+        }
+        if (!(ok = wait_mma(bar, phase, status))) break;
+        ntile_cta++;
+    }
+    if (ok && ntile_cta > 0) {
+        // this CTA's sums, added once: thread t holds row t of every accumulator
+        float v[32];
+        const int o = tid;
+#pragma unroll 1
+        for (int c = 0; c < 4; c++) {
+            tc_ld32(tl + BT_GW3 + 32 * c, v);
+            red_add32(g.gW3 + (size_t)o * MLP_HID + 32 * c, v);
+            tc_ld32(tl + BT_GW2 + 32 * c, v);
+            red_add32(g.gW2 + (size_t)o * MLP_HID + 32 * c, v);
+        }
+        float u[16];
+        tc_ld16(tl + BT_GW3 + 128, u);
+        atomicAdd(g.gb3 + o, u[0]);
+        tc_ld16(tl + BT_GW2 + 128, u);
+        atomicAdd(g.gb2 + o, u[0]);
+        tc_ld32(tl + BT_GW1, v);  // columns 0..15: dW1[o][:], column 16: db1[o]
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+            atomicAdd(reinterpret_cast<float4*>(g.gW1 + (size_t)o * MLP_IN) + q,
+                      make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
+        atomicAdd(g.gb1 + o, v[16]);
+        tc_ld16(tl + BT_GW4, u);  // row i = tid of dW4^T: dW4[k][i] for k = 0..15
+#pragma unroll
+        for (int k = 0; k < 16; k++) atomicAdd(g.gW4 + (size_t)k * MLP_HID + tid, u[k]);
+    }
+    // the output layer's bias gradient: the threads' sums, reduced through shared memory
+    tc_fence_before();
+    __syncthreads();
+    float* red = reinterpret_cast<float*>(sm + BS_GZ);
+#pragma unroll
+    for (int j = 0; j < 16; j++) red[j * 128 + tid] = gb4[j];
+    __syncthreads();
+    if (tid < 16) {
+        float s = 0.f;
+        for (int k = 0; k < 128; k++) s += red[tid * 128 + k];
+        if (ntile_cta > 0) atomicAdd(g.gb4 + tid, s);
     }
     __syncthreads();
-    // layer 4
-    bias_grad<MLP_OUT>(gz4, LDI, g.gb4, rows);
-    weight_grad<MLP_OUT, MLP_HID>(gz4, LDI, h3, LDH, g.gW4, warp, gid, tig);
-    input_grad<MLP_OUT, MLP_HID>(gz4 + warp * 16 * LDI, LDI, g.W4t, h3 + warp * 16 * LDH, LDH, gz + warp * 16 * LDH,
-                                 LDH, gid, tig);
-    __syncthreads();
-    // layer 3
-    bias_grad<MLP_HID>(gz, LDH, g.gb3, rows);
-    weight_grad<MLP_HID, MLP_HID>(gz, LDH, h2, LDH, g.gW3, warp, gid, tig);
-    __syncthreads();
-    // gz (layer 3) -> gz (layer 2): compute into h3's space, which is no longer needed
-    input_grad<MLP_HID, MLP_HID>(gz + warp * 16 * LDH, LDH, g.W3t, h2 + warp * 16 * LDH, LDH, h3 + warp * 16 * LDH,
-                                 LDH, gid, tig);
-    __syncthreads();
-    uint16_t* gz2 = h3;
-    bias_grad<MLP_HID>(gz2, LDH, g.gb2, rows);
-    weight_grad<MLP_HID, MLP_HID>(gz2, LDH, h1, LDH, g.gW2, warp, gid, tig);
-    __syncthreads();
-    input_grad<MLP_HID, MLP_HID>(gz2 + warp * 16 * LDH, LDH, g.W2t, h1 + warp * 16 * LDH, LDH, gz + warp * 16 * LDH,
-                                 LDH, gid, tig);
-    __syncthreads();
-    bias_grad<MLP_HID>(gz, LDH, g.gb1, rows);
-    weight_grad<MLP_HID, MLP_IN>(gz, LDH, sx, LDI, g.gW1, warp, gid, tig);
+    if (warp == 0) tc_dealloc(tm, B_TMEM_COLS);
 }
 
 // Mean squared error of the first K of the 16 output columns against
@@ -304,12 +569,18 @@ static MlpW make_w(const uint16_t* const* W, const float* const* b) {
     return w;
 }
 
+static int sm_count(hcgs_ctx* ctx) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess || n < 1) n = 148;
+    return n;
+}
+
 hcgs_status mlp_fwd(hcgs_ctx* ctx, const uint16_t* x, int N, const uint16_t* const* W, const float* const* b,
                     float* y, cudaStream_t st) {
-    const int rows_per_cta = 128;
-    HCGS_CUDA(ctx, cudaFuncSetAttribute(k_mlp_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MLP_FWD_SMEM));
-    HCGS_KERNEL(ctx, "k_mlp_fwd", st, k_mlp_fwd<<<(N + rows_per_cta - 1) / rows_per_cta, 256, MLP_FWD_SMEM, st>>>(make_w(W, b), x, N, y));
-    HCGS_LAUNCH(ctx, "k_mlp_fwd");
+    const int tiles = (N + 127) / 128;
+    const int grid = tiles < 2 * sm_count(ctx) ? tiles : 2 * sm_count(ctx);  // two CTAs per SM
+    HCGS_CUDA(ctx, cudaFuncSetAttribute(k_mlp_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FS_END));
+    HCGS_KERNEL(ctx, "k_mlp_fwd", st, k_mlp_fwd<<<grid, 128, FS_END, st>>>(make_w(W, b), x, N, y, ctx->d_status));
     return HCGS_OK;
 }
 
@@ -323,23 +594,13 @@ hcgs_status mlp_bwd(hcgs_ctx* ctx, const uint16_t* x, int N, const uint16_t* con
         HCGS_CUDA(ctx, cudaMemsetAsync(gb[k], 0, nb[k] * sizeof(float), st));
     }
     if (N == 0) return HCGS_OK;
-    // transposed W2, W3, W4 for the input gradients
-    const size_t nt = nW[1] + nW[2] + nW[3];
-    HCGS_CUDA(ctx, grow(ctx, ctx->ws[4], nt * sizeof(uint16_t), &ctx->bytes));
-    uint16_t* W2t = (uint16_t*)ctx->ws[4].p;
-    uint16_t* W3t = W2t + nW[1];
-    uint16_t* W4t = W3t + nW[2];
-    HCGS_KERNEL(ctx, "k_transpose_bf16", st, k_transpose_bf16<<<(int)((nW[1] + 255) / 256), 256, 0, st>>>(W[1], W2t, MLP_HID, MLP_HID));
-    HCGS_KERNEL(ctx, "k_transpose_bf16", st, k_transpose_bf16<<<(int)((nW[2] + 255) / 256), 256, 0, st>>>(W[2], W3t, MLP_HID, MLP_HID));
-    HCGS_KERNEL(ctx, "k_transpose_bf16", st, k_transpose_bf16<<<(int)((nW[3] + 255) / 256), 256, 0, st>>>(W[3], W4t, MLP_OUT, MLP_HID));
-    HCGS_LAUNCH(ctx, "k_transpose_bf16");
     MlpG g;
     g.gW1 = gW[0]; g.gW2 = gW[1]; g.gW3 = gW[2]; g.gW4 = gW[3];
     g.gb1 = gb[0]; g.gb2 = gb[1]; g.gb3 = gb[2]; g.gb4 = gb[3];
-    g.W2t = W2t; g.W3t = W3t; g.W4t = W4t;
-    HCGS_CUDA(ctx, cudaFuncSetAttribute(k_mlp_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MLP_BWD_SMEM));
-    HCGS_KERNEL(ctx, "k_mlp_bwd", st, k_mlp_bwd<<<(N + 127) / 128, 256, MLP_BWD_SMEM, st>>>(make_w(W, b), g, x, N, gy));
-    HCGS_LAUNCH(ctx, "k_mlp_bwd");
+    const int tiles = (N + 127) / 128;
+    const int grid = tiles < sm_count(ctx) ? tiles : sm_count(ctx);  // one CTA per SM (all of TMEM)
+    HCGS_CUDA(ctx, cudaFuncSetAttribute(k_mlp_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BS_END));
+    HCGS_KERNEL(ctx, "k_mlp_bwd", st, k_mlp_bwd<<<grid, 128, BS_END, st>>>(make_w(W, b), g, x, N, gy, ctx->d_status));
     return HCGS_OK;
 }
 

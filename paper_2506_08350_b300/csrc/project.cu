@@ -76,8 +76,20 @@ __global__ void k_project(ProjArgs a, const float* __restrict__ means, const flo
     proj[2 * i] = make_float4(P.mu.x, P.mu.y, P.conic[0], P.conic[1]);
     proj[2 * i + 1] = make_float4(P.conic[2], P.o, P.depth, __int_as_float(plane));
     rectn[i] = rect;
-    // depth >= near_z > 0, so the float bits order like the values
-    dkey[i] = P.valid ? __float_as_uint(P.depth) : 0xFFFFFFFFu;
+    // The visiting order's key: the camera-space depth rounded once to FP32.
+    // It is formed in FP64 from the FP32 inputs (each product exact), so that
+    // Gaussians closer in depth than the rounding error of an FP32 evaluation
+    // are still ordered by their depths; equal keys go by index (the sort is
+    // stable).  depth >= near_z > 0, so the float bits order like the values.
+    if (P.valid) {
+        const float* Vm = cam + 20 * v;
+        const float* mn = means + 3 * n;
+        const double zd = fma((double)Vm[8], (double)mn[0],
+                              fma((double)Vm[9], (double)mn[1], fma((double)Vm[10], (double)mn[2], (double)Vm[11])));
+        dkey[i] = __float_as_uint(__double2float_rn(zd));
+    } else {
+        dkey[i] = 0xFFFFFFFFu;
+    }
     dval[i] = (uint32_t)n;
 }
 

@@ -283,9 +283,11 @@ def _bf16(a):
     return t
 
 
-def test_mlp_forward_backward(P, ctx):
-    rng = np.random.default_rng(1)
-    N = 1000  # ragged: not a multiple of 128
+@pytest.mark.parametrize("N", [1, 128, 1000, 150001])
+def test_mlp_forward_backward(P, ctx, N):
+    # one row; one whole tile of 128 rows; a ragged count; and enough rows
+    # that every CTA of the reverse mode accumulates several tiles
+    rng = np.random.default_rng(N)
     dims = [16, 128, 128, 128, 16]
     Ws = [_bf16(rng.normal(size=(dims[k + 1], dims[k])) / math.sqrt(dims[k])) for k in range(4)]
     bs = [torch.from_numpy((rng.normal(size=dims[k + 1]) * 0.1).astype(np.float32)) for k in range(4)]
@@ -299,15 +301,19 @@ def test_mlp_forward_backward(P, ctx):
     b64 = [b.numpy().astype(np.float64) for b in bs]
     x64 = x.float().numpy().astype(np.float64)
     y_ref, _ = oracle.mlp_forward(x64, W64, b64, act_round="bf16")
-    assert rel(y.cpu().numpy(), y_ref) < 1e-2
+    e_y = rel(y.cpu().numpy(), y_ref)
+    assert e_y < 1e-2, e_y
     gy = rng.normal(size=(N, 16)).astype(np.float32)
     gW = [torch.empty(tuple(w.shape), dtype=torch.float32, device="cuda") for w in Ws]
     gb = [torch.empty(tuple(b.shape), dtype=torch.float32, device="cuda") for b in bs]
     ctx.mlp_backward(xd, Wd, bd, torch.from_numpy(gy).cuda(), gW, gb)
     gW_ref, gb_ref, _ = oracle.mlp_backward(x64, W64, b64, gy.astype(np.float64), act_round="bf16")
-    for k in range(4):
-        assert rel(gW[k].cpu().numpy(), gW_ref[k]) < 1e-2, ("W", k, rel(gW[k].cpu().numpy(), gW_ref[k]))
-        assert rel(gb[k].cpu().numpy(), gb_ref[k]) < 1e-2, ("b", k)
+    errs = [(rel(gW[k].cpu().numpy(), gW_ref[k]), rel(gb[k].cpu().numpy(), gb_ref[k])) for k in range(4)]
+    print("network, %d rows: output %.2e, (weight, bias) gradients per layer %s" %
+          (N, e_y, ["(%.2e, %.2e)" % e for e in errs]))
+    for k, (ew, eb) in enumerate(errs):
+        assert ew < 1e-2, ("W", k, ew)
+        assert eb < 1e-2, ("b", k, eb)
 
 
 @pytest.mark.parametrize("H,W", [(64, 96), (120, 200)])

@@ -49,6 +49,11 @@ def _plant_py(monkeypatch, name, old, new):
 
 # (what is wrong, original expression, planted expression, the pin that must fail)
 C_CASES = [
+    ("depth key compared in FP64 instead of rounded to FP32",
+     "const float di = (float)g_sort_depth[i], dj = (float)g_sort_depth[j];",
+     "const double di = g_sort_depth[i], dj = g_sort_depth[j];", R.test_depth_key_is_rounded_once_to_fp32),
+    ("depth key ignored (index order only)", "if (di < dj) return -1;\n    if (di > dj) return 1;",
+     "", R.test_depth_key_is_rounded_once_to_fp32),
     ("transmittance update 1 + alpha", "T *= (1.0 - a);", "T *= (1.0 + a);", R.test_weights_sum_to_one_minus_T),
     ("transmittance update in the golden pixel", "T *= (1.0 - a);", "T *= (1.0 - 0.5 * a);",
      R.test_three_gaussians_golden_fixture),

@@ -227,6 +227,25 @@ def test_equal_depths_visit_in_index_order():
         assert abs(U[0, 0, 4, 4] - want) < 1e-12, (order, U[0, 0, 4, 4], want)
 
 
+def test_depth_key_is_rounded_once_to_fp32():
+    # Reading R14: the visiting order compares the camera-space depth rounded
+    # to FP32, ties by index.  Gaussian 0 sits 2e-8 m behind Gaussian 1 at
+    # 1.5 m (FP32 spacing there 1.2e-7 m): equal keys, so index order, 0
+    # first.  5e-7 m behind (four FP32 steps): depth order, 1 first.
+    H, W = 9, 9
+    intr = np.array([100.0, 100.0, 4.0, 4.0])
+    opts = dict(oracle.EXACT_OPTS, order=0)
+    for dz, first_is_0 in ((2e-8, True), (5e-7, False)):
+        g = _cat([_one([0, 0, 1.5 + dz], np.log([0.01] * 3), [1, 0, 0, 0], 0.6, [1.0], [0.0], [0.0]),
+                  _one([0, 0, 1.5], np.log([0.01] * 3), [1, 0, 0, 0], 0.3, [0.5], [np.pi / 2], [0.0])])
+        pr = oracle.project(g, np.eye(4), intr, H, W, opts)
+        U, _, _ = oracle.composite(pr, opts)
+        (wa, aa), (wb, ab) = ((1.0, 0.6), (0.5j, 0.3)) if first_is_0 else ((0.5j, 0.3), (1.0, 0.6))
+        want = wa * aa + wb * ab * (1 - aa)
+        assert abs(U[0, 0, 4, 4] - want) < 1e-9, (dz, U[0, 0, 4, 4], want)
+        assert list(oracle.visiting_order(pr)) == ([0, 1] if first_is_0 else [1, 0])
+
+
 def _golden():
     gs, ex = [], []
     with open(os.path.join(GOLDEN, "three_gaussians_one_pixel.txt")) as fh:
