@@ -177,7 +177,7 @@ hcgs_status hcgs_ctx_create(hcgs_ctx** out, int device) {
 static void saved_free(hcgs_saved* s) {
     DevBuf* bufs[] = {&s->w, &s->proj, &s->rectn, &s->dkey, &s->dval, &s->nvalid, &s->rank, &s->sortid, &s->rec,
                       &s->rects, &s->planes, &s->ccount, &s->bcount, &s->ikey, &s->ival, &s->hist, &s->scan,
-                      &s->Tfin, &s->last, &s->slist, &s->U, &s->g2d, &s->gU, &s->cam, &s->akey, &s->aval,
+                      &s->Tfin, &s->last, &s->skmax, &s->slist, &s->U, &s->g2d, &s->gU, &s->cam, &s->akey, &s->aval,
                       &s->abcount, &s->drho, &s->segoff};
     for (DevBuf* b : bufs) free_buf(*b);
     s->bytes = 0;

@@ -108,7 +108,8 @@ struct hcgs_saved {
     hcgs::DevBuf hist;     // radix-sort block histograms
     hcgs::DevBuf scan;     // scan partials
     hcgs::DevBuf Tfin;     // [V][L][H][W] float
-    hcgs::DevBuf last;     // [V][L][H][W] uint32: staged index after the last contributor
+    hcgs::DevBuf last;     // [V][L][H][W] uint32: 1 + visiting rank of the last contributor (0: none)
+    hcgs::DevBuf skmax;    // [V][L][2 tilesY][tilesX] uint32: per 16x8 strip, kept entries up to its last contribution
     hcgs::DevBuf slist;    // [32 M] uint32: per 16x8 strip, the Gaussians its forward pass kept, in order
     hcgs::DevBuf U;        // [V][L][C][H][W] float2 when the caller gives no plane buffer
     hcgs::DevBuf g2d;      // [V][N][G2D] float (Gaussian order): pixel moments of -dL/dpower 5, o dL/do, dL/dw 2C
