@@ -187,6 +187,32 @@ hcgs_status hcgs_saved_release(hcgs_ctx* ctx, hcgs_saved* saved);
  * kernel is launched; HCGS_ERR_INVALID_ARG for a null context. */
 hcgs_status hcgs_selftest_wait_timeout(hcgs_ctx* ctx, void* stream);
 
+/* ---------------- bounds-checked build (no counterpart in the paper) ---------------- */
+/* libhcgs_checked.so is the same library compiled with HCGS_CHECKED: device
+ * kernels check the indices they take from data (bucket-list entries, strip
+ * lengths, visiting ranks, instance offsets) before using them and skip an
+ * access whose check fails, the projection checks that every Gaussian
+ * parameter is finite (a non-finite Gaussian is reported and culled), and
+ * every buffer the library grows carries a 256-byte guard band after its
+ * capacity.  A failed check sets the context's status word.
+ * hcgs_is_checked_build: 1 in libhcgs_checked.so, 0 in libhcgs.so.
+ * hcgs_check_status: synchronises `stream`, verifies the guard bands of this
+ *   device's library buffers (checked build; a damaged band is reported and
+ *   filled again), reads and clears the status word.  Returns
+ *   HCGS_ERR_DEVICE_CHECK if a check failed since the last report,
+ *   HCGS_ERR_TIMEOUT if a bounded device wait ran out, else HCGS_OK; the
+ *   context stays usable.  (hcgs_project / hcgs_render_view also report the
+ *   word at their own readback.)
+ * hcgs_selftest_device_check: checked build only (else HCGS_ERR_STATE).
+ *   kind 0 launches a kernel whose index check fails (the index is outside
+ *   the checked range but inside its buffer); kind 1 writes one byte into
+ *   the guard band of a context buffer (inside the allocation).  The next
+ *   hcgs_check_status returns HCGS_ERR_DEVICE_CHECK.  No access leaves its
+ *   allocation in either case. */
+int hcgs_is_checked_build(void);
+hcgs_status hcgs_check_status(hcgs_ctx* ctx, void* stream);
+hcgs_status hcgs_selftest_device_check(hcgs_ctx* ctx, int kind, void* stream);
+
 hcgs_status hcgs_profile_enable(hcgs_ctx* ctx, int on);
 hcgs_status hcgs_profile_summary(hcgs_ctx* ctx, int max, int* n_out, const char** names, double* ms,
                                  int64_t* launches);

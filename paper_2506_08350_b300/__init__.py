@@ -18,7 +18,10 @@ from ctypes import POINTER, c_double, c_float, c_int, c_int64, c_size_t, c_void_
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libhcgs.so")
+# HCGS_CHECKED=1 in the environment loads the bounds-checked variant
+CHECKED = os.environ.get("HCGS_CHECKED", "0") == "1"
+LIB_PATH = os.path.join(_HERE, "_build_checked", "libhcgs_checked.so") if CHECKED else \
+    os.path.join(_HERE, "_build", "libhcgs.so")
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(
@@ -40,7 +43,8 @@ EXPORTS = ("hcgs_ctx_create", "hcgs_ctx_destroy", "hcgs_status_string", "hcgs_la
            "hcgs_cast_bf16", "hcgs_init_features", "hcgs_init_targets", "hcgs_init_apply",
            "hcgs_selftest_wait_timeout", "hcgs_paper_loss", "hcgs_paper_loss_intensities", "hcgs_adan_step",
            "hcgs_densify_accumulate", "hcgs_densify_plan", "hcgs_densify_apply", "hcgs_philox",
-           "hcgs_phase_only_loss", "hcgs_hologram_phase", "hcgs_phase_hologram", "hcgs_scale")
+           "hcgs_phase_only_loss", "hcgs_hologram_phase", "hcgs_phase_hologram", "hcgs_scale",
+           "hcgs_is_checked_build", "hcgs_check_status", "hcgs_selftest_device_check")
 
 
 class HcgsError(RuntimeError):
@@ -96,6 +100,10 @@ _sig("hcgs_ctx_create", [POINTER(c_void_p), c_int])
 _sig("hcgs_saved_create", [_P, POINTER(c_void_p)])
 _sig("hcgs_profile_enable", [_P, c_int])
 _sig("hcgs_selftest_wait_timeout", [_P, _P])
+_sig("hcgs_check_status", [_P, _P])
+_sig("hcgs_selftest_device_check", [_P, c_int, _P])
+_lib.hcgs_is_checked_build.argtypes = []
+_lib.hcgs_is_checked_build.restype = c_int
 _sig("hcgs_profile_summary", [_P, c_int, POINTER(c_int), POINTER(ctypes.c_char_p), POINTER(c_double),
                               POINTER(c_int64)])
 _sig("hcgs_saved_release", [_P, _P])
@@ -249,6 +257,14 @@ class Context:
         """Launches a kernel whose bounded wait runs out (about one second); the
         next project / render_view call then raises HcgsError(HCGS_ERR_TIMEOUT)."""
         self._check(_lib.hcgs_selftest_wait_timeout(self.handle, _stream()))
+
+    def check_status(self):
+        """hcgs_check_status on the current stream: raises HcgsError
+        (HCGS_ERR_DEVICE_CHECK / HCGS_ERR_TIMEOUT) for what the device recorded."""
+        self._check(_lib.hcgs_check_status(self.handle, _stream()))
+
+    def selftest_device_check(self, kind):
+        self._check(_lib.hcgs_selftest_device_check(self.handle, int(kind), _stream()))
 
     def profile_enable(self, on=True):
         self._check(_lib.hcgs_profile_enable(self.handle, int(bool(on))))

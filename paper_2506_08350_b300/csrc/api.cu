@@ -2,6 +2,8 @@
 // orchestration of the render path.  See include/hcgs.h for the contract.
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 
 #include "common.cuh"
 #include "project.cuh"
@@ -20,25 +22,44 @@ hcgs_status cuda_err(hcgs_ctx* ctx, cudaError_t e, const char* what) {
     return HCGS_ERR_CUDA;
 }
 
+#ifdef HCGS_CHECKED
+// registry of guarded allocations: base -> (capacity, device); the guard band
+// follows the capacity
+static std::mutex g_guard_mu;
+static std::map<void*, std::pair<size_t, int>> g_guards;
+#endif
+
 cudaError_t grow(hcgs_ctx* ctx, DevBuf& b, size_t bytes, size_t* owner_bytes) {
     if (bytes <= b.cap) return cudaSuccess;
     if (b.p) {
-        cudaError_t e = cudaFree(b.p);
-        if (e != cudaSuccess) return e;
         *owner_bytes -= b.cap;
-        b.p = nullptr;
-        b.cap = 0;
+        free_buf(b);
     }
+#ifdef HCGS_CHECKED
+    const size_t guard = GUARD_BYTES;
+#else
+    const size_t guard = 0;
+#endif
     const size_t want = bytes + bytes / 8;  // slack against small growth steps
-    cudaError_t e = cudaMalloc(&b.p, want);
+    cudaError_t e = cudaMalloc(&b.p, want + guard);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        e = cudaMalloc(&b.p, bytes);
+        e = cudaMalloc(&b.p, bytes + guard);
         if (e != cudaSuccess) return e;
         b.cap = bytes;
     } else {
         b.cap = want;
     }
+#ifdef HCGS_CHECKED
+    e = cudaMemset((char*)b.p + b.cap, GUARD_FILL, guard);
+    if (e != cudaSuccess) return e;
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        std::lock_guard<std::mutex> lk(g_guard_mu);
+        g_guards[b.p] = std::make_pair(b.cap, dev);
+    }
+#endif
     *owner_bytes += b.cap;
     (void)ctx;
     return cudaSuccess;
@@ -65,11 +86,47 @@ void prof_end(hcgs_ctx* ctx, cudaStream_t st) {
     cudaEventRecord(ctx->prof.recs.back().b, st);
 }
 
-static void free_buf(DevBuf& b) {
-    if (b.p) cudaFree(b.p);
+void free_buf(DevBuf& b) {
+    if (b.p) {
+#ifdef HCGS_CHECKED
+        {
+            std::lock_guard<std::mutex> lk(g_guard_mu);
+            g_guards.erase(b.p);
+        }
+#endif
+        cudaFree(b.p);
+    }
     b.p = nullptr;
     b.cap = 0;
 }
+
+#ifdef HCGS_CHECKED
+// one block per guarded buffer: any byte of its guard band that differs from
+// the fill pattern marks the status word; the band is then filled again, so
+// that the context stays usable after the report
+__global__ void k_check_guards(unsigned char* const* __restrict__ guards, int n, int* __restrict__ status) {
+    const int g = blockIdx.x;
+    if (g >= n) return;
+    unsigned char* p = guards[g];
+    bool bad = false;
+    for (int i = threadIdx.x; i < (int)GUARD_BYTES; i += blockDim.x) bad |= p[i] != GUARD_FILL;
+    if (__syncthreads_or(bad)) {
+        if (threadIdx.x == 0) atomicOr(status, STATUS_DEVICE_CHECK);
+        for (int i = threadIdx.x; i < (int)GUARD_BYTES; i += blockDim.x) p[i] = GUARD_FILL;
+    }
+}
+
+// index check of the self-test: idx = n is out of the checked range [0, n),
+// while the buffer holds 2 n elements, so the store stays inside the
+// allocation even if the check were missing
+__global__ void k_selftest_index(float* __restrict__ buf, int n, int idx, int* __restrict__ status) {
+    if (threadIdx.x == 0 && HCGS_DCHECK(status, idx < n)) buf[idx] = 1.f;
+}
+// a store into the guard band of buf (inside its allocation)
+__global__ void k_selftest_guard(unsigned char* __restrict__ guard) {
+    if (threadIdx.x == 0) guard[GUARD_BYTES / 2] = (unsigned char)(GUARD_FILL ^ 0xFF);
+}
+#endif
 
 }  // namespace hcgs
 
@@ -177,7 +234,7 @@ hcgs_status hcgs_ctx_create(hcgs_ctx** out, int device) {
 static void saved_free(hcgs_saved* s) {
     DevBuf* bufs[] = {&s->w, &s->proj, &s->rectn, &s->dkey, &s->dval, &s->nvalid, &s->rank, &s->sortid, &s->rec,
                       &s->rects, &s->planes, &s->ccount, &s->bcount, &s->ikey, &s->ival, &s->hist, &s->scan,
-                      &s->Tfin, &s->last, &s->skmax, &s->slist, &s->U, &s->g2d, &s->gU, &s->cam, &s->akey, &s->aval,
+                      &s->Tfin, &s->last, &s->slist, &s->U, &s->g2d, &s->gU, &s->cam, &s->akey, &s->aval,
                       &s->abcount, &s->drho, &s->segoff};
     for (DevBuf* b : bufs) free_buf(*b);
     s->bytes = 0;
@@ -188,6 +245,7 @@ void hcgs_ctx_destroy(hcgs_ctx* ctx) {
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
     for (auto& b : ctx->ws) free_buf(b);
+    free_buf(ctx->selftest);
     for (auto& kv : ctx->plans) cudaFree(kv.second.tw);
     for (auto& kv : ctx->htab) free_buf(kv.second);
     if (ctx->scratch_saved) {
@@ -250,6 +308,78 @@ size_t hcgs_ctx_bytes(hcgs_ctx* ctx) {
     size_t b = ctx->bytes;
     if (ctx->scratch_saved) b += ctx->scratch_saved->bytes;
     return b;
+}
+
+int hcgs_is_checked_build(void) {
+#ifdef HCGS_CHECKED
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+hcgs_status hcgs_check_status(hcgs_ctx* ctx, void* stream) {
+    if (!ctx) return HCGS_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = S(stream);
+#ifdef HCGS_CHECKED
+    {
+        std::vector<unsigned char*> gp;
+        {
+            std::lock_guard<std::mutex> lk(g_guard_mu);
+            for (auto& kv : g_guards)
+                if (kv.second.second == ctx->device) gp.push_back((unsigned char*)kv.first + kv.second.first);
+        }
+        if (!gp.empty()) {
+            unsigned char** d = nullptr;
+            HCGS_CUDA(ctx, cudaMalloc(&d, gp.size() * sizeof(unsigned char*)));
+            cudaError_t e = cudaMemcpyAsync(d, gp.data(), gp.size() * sizeof(unsigned char*), cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) {
+                k_check_guards<<<(unsigned)gp.size(), 128, 0, st>>>(d, (int)gp.size(), ctx->d_status);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            cudaFree(d);
+            HCGS_CUDA(ctx, e);
+        }
+    }
+#endif
+    HCGS_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned + 2, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    HCGS_CUDA(ctx, cudaStreamSynchronize(st));
+    const uint32_t w = ctx->h_pinned[2];
+    if (w) {
+        HCGS_CUDA(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st));
+        HCGS_CUDA(ctx, cudaStreamSynchronize(st));
+    }
+    if (w & STATUS_DEVICE_CHECK) {
+        set_err(ctx, HCGS_ERR_DEVICE_CHECK, "a device-side bounds, input or guard-band check failed");
+        return HCGS_ERR_DEVICE_CHECK;
+    }
+    if (w & STATUS_WAIT_TIMEOUT) {
+        set_err(ctx, HCGS_ERR_TIMEOUT, "a bounded device wait ran out");
+        return HCGS_ERR_TIMEOUT;
+    }
+    return HCGS_OK;
+}
+
+hcgs_status hcgs_selftest_device_check(hcgs_ctx* ctx, int kind, void* stream) {
+    if (!ctx) return HCGS_ERR_INVALID_ARG;
+    REQUIRE(ctx, kind == 0 || kind == 1, "kind must be 0 (index check) or 1 (guard band)");
+#ifdef HCGS_CHECKED
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = S(stream);
+    const int n = 32;
+    HCGS_CUDA(ctx, grow(ctx, ctx->selftest, 2 * n * sizeof(float), &ctx->bytes));
+    if (kind == 0)
+        HCGS_KERNEL(ctx, "k_selftest_index", st, k_selftest_index<<<1, 32, 0, st>>>((float*)ctx->selftest.p, n, n, ctx->d_status));
+    else
+        HCGS_KERNEL(ctx, "k_selftest_guard", st, k_selftest_guard<<<1, 32, 0, st>>>((unsigned char*)ctx->selftest.p + ctx->selftest.cap));
+    return HCGS_OK;
+#else
+    (void)stream;
+    set_err(ctx, HCGS_ERR_STATE, "device checks exist only in the bounds-checked build (libhcgs_checked.so)");
+    return HCGS_ERR_STATE;
+#endif
 }
 
 hcgs_status hcgs_saved_create(hcgs_ctx* ctx, hcgs_saved** out) {

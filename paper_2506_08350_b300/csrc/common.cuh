@@ -70,6 +70,7 @@ struct hcgs_ctx {
     std::string last_error;
     size_t bytes = 0;
     hcgs::DevBuf ws[10];                             // workspace slots (6, 7: zero-padded grids; 8, 9: phase-only conversion)
+    hcgs::DevBuf selftest;                           // target of hcgs_selftest_device_check
     std::map<int, hcgs::FftPlan> plans;              // FFT plans by length
     std::map<hcgs::HKey, hcgs::DevBuf> htab;         // transfer-function tables
     int* d_status = nullptr;                         // device status word
@@ -108,8 +109,7 @@ struct hcgs_saved {
     hcgs::DevBuf hist;     // radix-sort block histograms
     hcgs::DevBuf scan;     // scan partials
     hcgs::DevBuf Tfin;     // [V][L][H][W] float
-    hcgs::DevBuf last;     // [V][L][H][W] uint32: 1 + visiting rank of the last contributor (0: none)
-    hcgs::DevBuf skmax;    // [V][L][2 tilesY][tilesX] uint32: per 16x8 strip, kept entries up to its last contribution
+    hcgs::DevBuf last;     // [V][L][H][W] uint32: staged index after the last contributor
     hcgs::DevBuf slist;    // [32 M] uint32: per 16x8 strip, the Gaussians its forward pass kept, in order
     hcgs::DevBuf U;        // [V][L][C][H][W] float2 when the caller gives no plane buffer
     hcgs::DevBuf g2d;      // [V][N][G2D] float (Gaussian order): pixel moments of -dL/dpower 5, o dL/do, dL/dw 2C
@@ -173,6 +173,17 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
 }
 // status word bits set by kernels (read back by the host at its next sync)
 constexpr int STATUS_WAIT_TIMEOUT = 1;
+constexpr int STATUS_DEVICE_CHECK = 2;  // a bounds / input check failed (HCGS_CHECKED builds)
+
+// Device-side checks of the bounds-checked build (HCGS_CHECKED): a failed
+// check records STATUS_DEVICE_CHECK in the status word and evaluates to
+// false, so the caller skips the access it guards.  In the regular build the
+// check compiles away (true).
+#ifdef HCGS_CHECKED
+#define HCGS_DCHECK(status, cond) ((cond) ? true : (atomicOr((status), hcgs::STATUS_DEVICE_CHECK), false))
+#else
+#define HCGS_DCHECK(status, cond) true
+#endif
 
 // ---- error plumbing ----
 struct Err {
@@ -182,6 +193,12 @@ struct Err {
 bool set_err(hcgs_ctx* ctx, hcgs_status s, const std::string& m);
 hcgs_status cuda_err(hcgs_ctx* ctx, cudaError_t e, const char* what);
 cudaError_t grow(hcgs_ctx* ctx, DevBuf& b, size_t bytes, size_t* owner_bytes);
+void free_buf(DevBuf& b);
+// Guard bands of the bounds-checked build: every buffer the library grows
+// carries GUARD_BYTES of a fixed pattern after its capacity; hcgs_check_status
+// verifies them.  Empty in the regular build.
+constexpr size_t GUARD_BYTES = 256;
+constexpr unsigned char GUARD_FILL = 0xA5;
 
 #define HCGS_CUDA(ctx, call)                                        \
     do {                                                            \

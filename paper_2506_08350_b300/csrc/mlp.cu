@@ -161,47 +161,53 @@ __device__ __forceinline__ bool wait_mma(uint64_t* bar, uint32_t& phase, int* st
 
 // Hidden-layer epilogue of this thread's row: h = bf16(relu(z + b)) for the
 // 128 accumulator columns at taddr, written to the core-matrix buffer H (F
-// features per row) at row r; mask bit j of word c = (h_{32c + j} > 0).
-__device__ __forceinline__ void epi_hidden(uint32_t taddr, const float* b, uint8_t* H, int F, int r,
-                                           uint32_t (&mask)[4]) {
+// features per row) at row r.  The bias is added in packed FP32, the ReLU
+// taken on the rounded pair (rounding keeps the sign, so relu and rounding
+// commute).
+__device__ __forceinline__ void epi_hidden(uint32_t taddr, const float* b, uint8_t* H, int F, int r) {
+    const __nv_bfloat162 zero = __floats2bfloat162_rn(0.f, 0.f);
 #pragma unroll 1
     for (int c = 0; c < 4; c++) {
         float v[32];
         tc_ld32(taddr + 32 * c, v);
-        uint32_t p[16], m = 0;
+        const float2* bb = reinterpret_cast<const float2*>(b + 32 * c);
+        uint32_t p[16];
 #pragma unroll
         for (int j = 0; j < 16; j++) {
-            const float lo = fmaxf(v[2 * j] + b[32 * c + 2 * j], 0.f);
-            const float hi = fmaxf(v[2 * j + 1] + b[32 * c + 2 * j + 1], 0.f);
-            p[j] = pack_bf2(lo, hi);
-            m |= ((p[j] & 0xFFFFu) != 0u ? 1u : 0u) << (2 * j);
-            m |= ((p[j] >> 16) != 0u ? 1u : 0u) << (2 * j + 1);
+            const float2 z = __fadd2_rn(make_float2(v[2 * j], v[2 * j + 1]), bb[j]);
+            __nv_bfloat162 h = __floats2bfloat162_rn(z.x, z.y);
+            h = __hmax2(h, zero);
+            p[j] = *reinterpret_cast<const uint32_t*>(&h);
         }
 #pragma unroll
         for (int q = 0; q < 4; q++)
             *reinterpret_cast<uint4*>(H + cm_off(r, 32 * c + 8 * q, F)) =
                 make_uint4(p[4 * q], p[4 * q + 1], p[4 * q + 2], p[4 * q + 3]);
-        mask[c] = m;
     }
 }
 
-// Gradient epilogue: dZ = bf16(dH masked by the ReLU decisions) into G (128 features).
-__device__ __forceinline__ void epi_grad(uint32_t taddr, const uint32_t (&mask)[4], uint8_t* G, int r) {
+// Gradient epilogue: dZ = bf16(dH) where the layer's activation h (row r of
+// Hl, F features) is positive, else 0, into G (128 features).
+__device__ __forceinline__ void epi_grad(uint32_t taddr, const uint8_t* Hl, int F, uint8_t* G, int r) {
+    const __nv_bfloat162 zero = __floats2bfloat162_rn(0.f, 0.f);
 #pragma unroll 1
     for (int c = 0; c < 4; c++) {
         float v[32];
         tc_ld32(taddr + 32 * c, v);
-        uint32_t p[16];
 #pragma unroll
-        for (int j = 0; j < 16; j++) {
-            const float lo = (mask[c] >> (2 * j)) & 1u ? v[2 * j] : 0.f;
-            const float hi = (mask[c] >> (2 * j + 1)) & 1u ? v[2 * j + 1] : 0.f;
-            p[j] = pack_bf2(lo, hi);
+        for (int q = 0; q < 4; q++) {
+            const uint4 hw = *reinterpret_cast<const uint4*>(Hl + cm_off(r, 32 * c + 8 * q, F));
+            const uint32_t hv[4] = {hw.x, hw.y, hw.z, hw.w};
+            uint32_t p[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const int j = 4 * q + k;
+                const __nv_bfloat162 d = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                const uint32_t m = __hgt2_mask(*reinterpret_cast<const __nv_bfloat162*>(&hv[k]), zero);
+                p[k] = *reinterpret_cast<const uint32_t*>(&d) & m;
+            }
+            *reinterpret_cast<uint4*>(G + cm_off(r, 32 * c + 8 * q, MLP_HID)) = make_uint4(p[0], p[1], p[2], p[3]);
         }
-#pragma unroll
-        for (int q = 0; q < 4; q++)
-            *reinterpret_cast<uint4*>(G + cm_off(r, 32 * c + 8 * q, MLP_HID)) =
-                make_uint4(p[4 * q], p[4 * q + 1], p[4 * q + 2], p[4 * q + 3]);
     }
 }
 
@@ -245,25 +251,33 @@ __global__ void __launch_bounds__(128, 2) k_mlp_fwd(MlpW w, const uint16_t* __re
     const uint32_t tl = tm + ((uint32_t)(warp * 32) << 16);  // this warp's TMEM lanes
     const uint32_t sa = smem_addr(sm);
     constexpr uint32_t ID_H = tc_idesc(128, 128, 0, 0), ID_O = tc_idesc(128, 16, 0, 0);
-    uint32_t phase = 0, mask[4];
+    uint32_t phase = 0;
     const int ntiles = (N + 127) / 128;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int row = t * 128 + tid;
-        uint4 x0 = make_uint4(0, 0, 0, 0), x1 = x0;
-        if (row < N) {
-            const uint4* xr = reinterpret_cast<const uint4*>(x + (size_t)row * MLP_IN);
+    // this thread's input row of tile t (zeros past N)
+    auto load_x = [&](int t, uint4& x0, uint4& x1) {
+        const int rr = t * 128 + tid;
+        x0 = make_uint4(0, 0, 0, 0);
+        x1 = x0;
+        if (t < ntiles && rr < N) {
+            const uint4* xr = reinterpret_cast<const uint4*>(x + (size_t)rr * MLP_IN);
             x0 = __ldg(xr);
             x1 = __ldg(xr + 1);
         }
-        *reinterpret_cast<uint4*>(sm + FS_X + cm_off(tid, 0, MLP_IN)) = x0;
-        *reinterpret_cast<uint4*>(sm + FS_X + cm_off(tid, 8, MLP_IN)) = x1;
+    };
+    uint4 nx0, nx1;  // the next tile's row, loaded one tile ahead
+    load_x(blockIdx.x, nx0, nx1);
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int row = t * 128 + tid;
+        *reinterpret_cast<uint4*>(sm + FS_X + cm_off(tid, 0, MLP_IN)) = nx0;
+        *reinterpret_cast<uint4*>(sm + FS_X + cm_off(tid, 8, MLP_IN)) = nx1;
+        load_x(t + gridDim.x, nx0, nx1);
         sync_for_mma();
         if (tid == 0) {
             tc_mma(tm, op_k(sa + FS_X, MLP_IN, 0), op_k(sa + FS_W1, MLP_IN, 0), ID_H, 0);
             tc_commit(bar);
         }
         if (!wait_mma(bar, phase, status)) break;
-        epi_hidden(tl, sb, sm + FS_H, MLP_HID, tid, mask);
+        epi_hidden(tl, sb, sm + FS_H, MLP_HID, tid);
         bool ok = true;
 #pragma unroll 1
         for (int layer = 0; layer < 2 && ok; layer++) {
@@ -275,7 +289,7 @@ __global__ void __launch_bounds__(128, 2) k_mlp_fwd(MlpW w, const uint16_t* __re
                 tc_commit(bar);
             }
             ok = wait_mma(bar, phase, status);
-            if (ok) epi_hidden(tl, sb + 128 * (layer + 1), sm + FS_H, MLP_HID, tid, mask);
+            if (ok) epi_hidden(tl, sb + 128 * (layer + 1), sm + FS_H, MLP_HID, tid);
         }
         if (!ok) break;
         sync_for_mma();
@@ -365,33 +379,42 @@ __global__ void __launch_bounds__(128, 1) k_mlp_bwd(MlpW w, MlpG g, const uint16
     constexpr uint32_t ID_W4 = tc_idesc(128, 16, 1, 1);     // dW4^T = H3^T dZ4
     constexpr uint32_t ID_WH = tc_idesc(128, FHE, 1, 1);    // [dW | db] = dZ^T [H | 1]
     constexpr uint32_t ID_W1 = tc_idesc(128, FX, 1, 1);     // [dW1 | db1] = dZ1^T [X | 1]
-    uint32_t phase = 0, m1[4], m2[4], m3[4];
+    uint32_t phase = 0;
     float gb4[16];
 #pragma unroll
     for (int j = 0; j < 16; j++) gb4[j] = 0.f;
     bool ok = true;
     int ntile_cta = 0;
     const int ntiles = (N + 127) / 128;
-    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        const int acc = ntile_cta > 0;  // accumulate onto the earlier tiles' weight gradients
-        const int row = t * 128 + tid;
-        uint4 x0 = make_uint4(0, 0, 0, 0), x1 = x0;
-        float gr[16];
+    // this thread's rows of x and gy in tile t (zeros past N), loaded one tile ahead
+    auto load_rows = [&](int t, uint4& x0, uint4& x1, float4 (&g4)[4]) {
+        const int rr = t * 128 + tid;
+        x0 = make_uint4(0, 0, 0, 0);
+        x1 = x0;
 #pragma unroll
-        for (int j = 0; j < 16; j++) gr[j] = 0.f;
-        if (row < N) {
-            const uint4* xr = reinterpret_cast<const uint4*>(x + (size_t)row * MLP_IN);
+        for (int q = 0; q < 4; q++) g4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (t < ntiles && rr < N) {
+            const uint4* xr = reinterpret_cast<const uint4*>(x + (size_t)rr * MLP_IN);
             x0 = __ldg(xr);
             x1 = __ldg(xr + 1);
-            const float4* gq = reinterpret_cast<const float4*>(gy + (size_t)row * MLP_OUT);
+            const float4* gq = reinterpret_cast<const float4*>(gy + (size_t)rr * MLP_OUT);
 #pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const float4 v = __ldg(gq + q);
-                gr[4 * q] = v.x; gr[4 * q + 1] = v.y; gr[4 * q + 2] = v.z; gr[4 * q + 3] = v.w;
-            }
+            for (int q = 0; q < 4; q++) g4[q] = __ldg(gq + q);
         }
-        *reinterpret_cast<uint4*>(sm + BS_X + cm_off(tid, 0, FX)) = x0;
-        *reinterpret_cast<uint4*>(sm + BS_X + cm_off(tid, 8, FX)) = x1;
+    };
+    uint4 nx0, nx1;
+    float4 ng[4];
+    load_rows(blockIdx.x, nx0, nx1, ng);
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const int acc = ntile_cta > 0;  // accumulate onto the earlier tiles' weight gradients
+        float gr[16];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            gr[4 * q] = ng[q].x; gr[4 * q + 1] = ng[q].y; gr[4 * q + 2] = ng[q].z; gr[4 * q + 3] = ng[q].w;
+        }
+        *reinterpret_cast<uint4*>(sm + BS_X + cm_off(tid, 0, FX)) = nx0;
+        *reinterpret_cast<uint4*>(sm + BS_X + cm_off(tid, 8, FX)) = nx1;
+        load_rows(t + gridDim.x, nx0, nx1, ng);
         // dZ4 = gy as BF16 (the tensor-core operand); the bias gradient of the
         // output layer sums the same rounded values
         uint32_t p[8];
@@ -410,7 +433,7 @@ __global__ void __launch_bounds__(128, 1) k_mlp_bwd(MlpW w, MlpG g, const uint16
             tc_commit(bar);
         }
         if (!(ok = wait_mma(bar, phase, status))) break;
-        epi_hidden(tl + BT_Z, sb, sm + BS_H1, FHE, tid, m1);
+        epi_hidden(tl + BT_Z, sb, sm + BS_H1, FHE, tid);
         sync_for_mma();
         if (tid == 0) {
 #pragma unroll
@@ -419,7 +442,7 @@ __global__ void __launch_bounds__(128, 1) k_mlp_bwd(MlpW w, MlpG g, const uint16
             tc_commit(bar);
         }
         if (!(ok = wait_mma(bar, phase, status))) break;
-        epi_hidden(tl + BT_Z, sb + 128, sm + BS_H2, FHE, tid, m2);
+        epi_hidden(tl + BT_Z, sb + 128, sm + BS_H2, FHE, tid);
         sync_for_mma();
         if (tid == 0) {
 #pragma unroll
@@ -428,7 +451,7 @@ __global__ void __launch_bounds__(128, 1) k_mlp_bwd(MlpW w, MlpG g, const uint16
             tc_commit(bar);
         }
         if (!(ok = wait_mma(bar, phase, status))) break;
-        epi_hidden(tl + BT_Z, sb + 256, sm + BS_H3, MLP_HID, tid, m3);
+        epi_hidden(tl + BT_Z, sb + 256, sm + BS_H3, MLP_HID, tid);
         // layer 4: dW4^T += H3^T dZ4; dH3 = dZ4 W4
         sync_for_mma();
         if (tid == 0) {
@@ -439,7 +462,7 @@ __global__ void __launch_bounds__(128, 1) k_mlp_bwd(MlpW w, MlpG g, const uint16
             tc_commit(bar);
         }
         if (!(ok = wait_mma(bar, phase, status))) break;
-        epi_grad(tl + BT_Z, m3, sm + BS_GZ, tid);
+        epi_grad(tl + BT_Z, sm + BS_H3, MLP_HID, sm + BS_GZ, tid);
         // layers 3, 2: [dW | db] += dZ^T [H | 1]; dH = dZ W
 #pragma unroll 1
         for (int layer = 3; layer >= 2 && ok; layer--) {
@@ -456,7 +479,7 @@ __global__ void __launch_bounds__(128, 1) k_mlp_bwd(MlpW w, MlpG g, const uint16
                     tc_mma(tm + BT_Z, op_k(sa + BS_GZ, MLP_HID, s), op_mn(sa + Wl, MLP_HID, s), ID_IN, s);
                 tc_commit(bar);
             }
-            if ((ok = wait_mma(bar, phase, status))) epi_grad(tl + BT_Z, layer == 3 ? m2 : m1, sm + BS_GZ, tid);
+            if ((ok = wait_mma(bar, phase, status))) epi_grad(tl + BT_Z, sm + Hprev, FHE, sm + BS_GZ, tid);
         }
         if (!ok) break;
         // layer 1: [dW1 | db1] += dZ1^T [X | 1]

@@ -24,9 +24,10 @@ namespace hcgs {
 // projection
 // ---------------------------------------------------------------------------
 __global__ void k_prep_w(const float* __restrict__ amp, const float* __restrict__ ph, float2* __restrict__ w,
-                         int N, int C) {
+                         int N, int C, int* __restrict__ status) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N * C) return;
+    HCGS_DCHECK(status, isfinite(amp[i]) && isfinite(ph[i]));  // non-finite appearance (checked build)
     float s, c;
     sincosf(ph[i], &s, &c);
     w[i] = make_float2(amp[i] * c, amp[i] * s);
@@ -42,6 +43,16 @@ __global__ void k_project(ProjArgs a, const float* __restrict__ means, const flo
     const int v = (int)(i / a.N), n = (int)(i - (size_t)v * a.N);
     ProjF P;
     project_one(a, means + 3 * n, log_scales + 3 * n, quats + 4 * n, opacity_logits[n], cam + 20 * v, P);
+#ifdef HCGS_CHECKED
+    {   // a Gaussian with a non-finite parameter is reported (and culled)
+        bool fin = isfinite(opacity_logits[n]);
+        for (int k = 0; k < 3; k++) fin = fin && isfinite(means[3 * n + k]) && isfinite(log_scales[3 * n + k]);
+        for (int k = 0; k < 4; k++) fin = fin && isfinite(quats[4 * n + k]);
+        for (int l = 0; l < a.L; l++) fin = fin && isfinite(plane_logits[(size_t)n * a.L + l]);
+        if (v == 0) HCGS_DCHECK(a.status, fin);
+        if (!fin) P.valid = false;
+    }
+#endif
     int plane = 0;
     {
         const float* r = plane_logits + (size_t)n * a.L;
@@ -121,6 +132,7 @@ __global__ void k_gather(ProjArgs a, const uint32_t* __restrict__ sorted_id, con
     const int m = (int)nvalid[v];
     const uint32_t n = sorted_id[i];
     const size_t vn = (size_t)v * a.N;
+    if (!HCGS_DCHECK(a.status, n < (uint32_t)a.N && m <= a.N)) return;
     if (s >= m) {
         rank[vn + n] = 0xFFFFFFFFu;
         ccount[i] = 0u;
@@ -184,7 +196,7 @@ __device__ __forceinline__ InstSrc inst_source(const ProjArgs& a, size_t i, cons
 }
 
 __device__ __forceinline__ void emit_instances(const InstSrc& e, uint32_t ctX, uint32_t* __restrict__ ikey,
-                                               uint32_t* __restrict__ ival) {
+                                               uint32_t* __restrict__ ival, const ProjArgs& a) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     uint32_t inc = e.cnt;  // inclusive running count over the warp's lanes
@@ -207,7 +219,7 @@ __device__ __forceinline__ void emit_instances(const InstSrc& e, uint32_t ctX, u
         const uint32_t start = __shfl_sync(full, e.start, j), w = __shfl_sync(full, e.cw, j);
         const uint32_t x0 = __shfl_sync(full, e.cx0, j), y0 = __shfl_sync(full, e.cy0, j);
         const uint32_t kb = __shfl_sync(full, e.kb, j), sv = __shfl_sync(full, e.s, j);
-        if (idx < total) {
+        if (idx < total && HCGS_DCHECK(a.status, start + k < a.M)) {
             const uint32_t dy = k / w, dx = k - dy * w;
             ikey[start + k] = (kb + y0 + dy) * ctX + x0 + dx;
             ival[start + k] = sv;
@@ -220,7 +232,7 @@ __global__ void k_inst_gen(ProjArgs a, const uint32_t* __restrict__ coff, const 
                            uint32_t* __restrict__ ikey, uint32_t* __restrict__ ival) {
     const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (i - (threadIdx.x & 31) >= (size_t)a.V * a.N) return;  // the whole warp is past the end
-    emit_instances(inst_source(a, i, coff, rects, planes, nvalid), (uint32_t)a.ctX, ikey, ival);
+    emit_instances(inst_source(a, i, coff, rects, planes, nvalid), (uint32_t)a.ctX, ikey, ival, a);
 }
 
 // The same instances with the plane left out of the bucket id (per view and
@@ -230,7 +242,7 @@ __global__ void k_inst_gen_all(ProjArgs a, const uint32_t* __restrict__ coff, co
                                uint32_t* __restrict__ ival) {
     const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (i - (threadIdx.x & 31) >= (size_t)a.V * a.N) return;
-    emit_instances(inst_source(a, i, coff, rects, nullptr, nvalid), (uint32_t)a.ctX, ikey, ival);
+    emit_instances(inst_source(a, i, coff, rects, nullptr, nvalid), (uint32_t)a.ctX, ikey, ival, a);
 }
 
 // Bucket start offsets from the sorted bucket ids: off[b] = first position
@@ -589,8 +601,9 @@ hcgs_status project_and_bin(hcgs_ctx* ctx, hcgs_saved* s, const hcgs_gaussians* 
         HCGS_CUDA(ctx, cudaMemcpyAsync(cam + 20 * v + 16, intr + 4 * v, 4 * sizeof(float), cudaMemcpyDeviceToDevice, st));
     }
     ProjArgs a = make_proj_args(s);
+    a.status = ctx->d_status;
     const int T = 256;
-    HCGS_KERNEL(ctx, "k_prep_w", st, k_prep_w<<<(N * C + T - 1) / T, T, 0, st>>>(g->amplitude, g->phase, (float2*)s->w.p, N, C));
+    HCGS_KERNEL(ctx, "k_prep_w", st, k_prep_w<<<(N * C + T - 1) / T, T, 0, st>>>(g->amplitude, g->phase, (float2*)s->w.p, N, C, ctx->d_status));
     const unsigned gridVN = (unsigned)((VN + T - 1) / T);
     uint32_t* dkey = (uint32_t*)s->dkey.p;
     uint32_t* dval = (uint32_t*)s->dval.p;
@@ -620,7 +633,12 @@ hcgs_status project_and_bin(hcgs_ctx* ctx, hcgs_saved* s, const hcgs_gaussians* 
     HCGS_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned + 2, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
     HCGS_CUDA(ctx, cudaStreamSynchronize(st));
     if (ctx->h_pinned[2] != 0) {
+        const uint32_t w = ctx->h_pinned[2];
         HCGS_CUDA(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st));
+        if (w & STATUS_DEVICE_CHECK) {
+            set_err(ctx, HCGS_ERR_DEVICE_CHECK, "a device-side bounds or input check failed in an earlier launch");
+            return HCGS_ERR_DEVICE_CHECK;
+        }
         set_err(ctx, HCGS_ERR_TIMEOUT, "a bounded device wait ran out in an earlier launch");
         return HCGS_ERR_TIMEOUT;
     }
@@ -630,6 +648,7 @@ hcgs_status project_and_bin(hcgs_ctx* ctx, hcgs_saved* s, const hcgs_gaussians* 
         return HCGS_ERR_CAPACITY;
     }
     s->M = M;
+    a.M = (uint32_t)M;
     const size_t Mc = M > 0 ? (size_t)M : 1;
     HCGS_CUDA(ctx, grow(ctx, s->ikey, 2 * Mc * sizeof(uint32_t), ob));
     HCGS_CUDA(ctx, grow(ctx, s->ival, 2 * Mc * sizeof(uint32_t), ob));
@@ -761,6 +780,7 @@ __global__ void k_project_bwd(ProjArgs a, const float* __restrict__ means, const
 hcgs_status project_backward(hcgs_ctx* ctx, hcgs_saved* s, const hcgs_gaussians* g,
                              const hcgs_gaussian_grads* gr, int accumulate, cudaStream_t st) {
     ProjArgs a = make_proj_args(s);
+    a.status = ctx->d_status;
     HCGS_KERNEL(ctx, "k_project_bwd", st, k_project_bwd<<<(s->N + 127) / 128, 128, 0, st>>>(a, g->means, g->log_scales, g->quats, g->opacity_logits,
                                                       g->amplitude, g->phase, g->plane_logits,
                                                       (const float*)s->cam.p, (const uint32_t*)s->rank.p,

@@ -16,6 +16,8 @@ struct ProjArgs {
     int V, N, C, L, H, W;
     int tilesX, tilesY, ctX, ctY;
     float amin, amax, teps, dil, near_z, clip;
+    int* status;  // device status word (device checks of the bounds-checked build)
+    uint32_t M;   // bucket instances (once known)
 };
 
 inline ProjArgs make_proj_args(const hcgs_saved* s) {
@@ -24,6 +26,8 @@ inline ProjArgs make_proj_args(const hcgs_saved* s) {
     a.tilesX = s->tilesX; a.tilesY = s->tilesY; a.ctX = s->ctX; a.ctY = s->ctY;
     a.amin = s->opts.alpha_min; a.amax = s->opts.alpha_max; a.teps = s->opts.T_eps;
     a.dil = s->opts.cov2d_dilation; a.near_z = s->opts.near_z; a.clip = s->opts.clip_factor;
+    a.status = nullptr;
+    a.M = (uint32_t)s->M;
     return a;
 }
 

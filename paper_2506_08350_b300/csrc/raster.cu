@@ -37,6 +37,8 @@ struct RasterArgs {
     int V, N, L, H, W, tilesX, tilesY, ctX, ctY;
     float amin, amax, teps;
     float inv_amin;  // 1 / alpha_min (0 when alpha_min = 0)
+    uint32_t M;      // bucket instances (device checks of the bounds-checked build)
+    int* status;     // device status word
 };
 
 static RasterArgs make_raster_args(const hcgs_saved* s) {
@@ -51,6 +53,8 @@ static RasterArgs make_raster_args(const hcgs_saved* s) {
     a.tilesX = s->tilesX; a.tilesY = s->tilesY; a.ctX = s->ctX; a.ctY = s->ctY;
     a.amin = s->opts.alpha_min; a.amax = s->opts.alpha_max; a.teps = s->opts.T_eps;
     a.inv_amin = a.amin > 0.f ? 1.f / a.amin : 0.f;
+    a.M = (uint32_t)s->M;
+    a.status = nullptr;
     return a;
 }
 
@@ -146,8 +150,9 @@ __device__ __forceinline__ int stage_warp(const RasterArgs& a, size_t vN, uint32
     bool ok = false;
     uint32_t s = 0;
     float4 q0, q1;
-    if (p < n) {
+    if (p < n && HCGS_DCHECK(a.status, beg + p < a.M)) {
         s = PF ? s_pf : a.list[beg + p];
+        if (!HCGS_DCHECK(a.status, s < (uint32_t)a.N)) s = 0u;  // checked build: a stray rank reads entry 0
         const uint2 rc = a.rects[vN + s];
         ok = (uint32_t)tx >= (rc.x & 0xFFFFu) && (uint32_t)tx < (rc.x >> 16) && (uint32_t)ty >= (rc.y & 0xFFFFu) &&
              (uint32_t)ty < (rc.y >> 16);
@@ -321,13 +326,10 @@ __device__ __forceinline__ void fwd_pair(const float4* rec, float2 a2, bool c0, 
 // A pixel is still compositing while T >= T_eps (T only changes when the
 // pixel takes a step, so this is the "stop once T < T_eps" rule); pixels
 // outside the image start with T = 0.
-// Saved for the adjoint: per pixel T and last = 1 + the visiting rank of its
-// last contributor (0: none); per strip kmax = the number of its kept entries
-// up to the last one any of its pixels took.
 template <int C, int FT, bool NCOUNT>
 __global__ void __launch_bounds__(RT, 32) k_raster_fwd(RasterArgs a, float2* __restrict__ U, float* __restrict__ Tsave,
-                                                   uint32_t* __restrict__ lastsave, uint32_t* __restrict__ skmax,
-                                                   float* __restrict__ Tout, int32_t* __restrict__ ncout) {
+                                                   uint32_t* __restrict__ lastsave, float* __restrict__ Tout,
+                                                   int32_t* __restrict__ ncout) {
     constexpr int NR = C <= 1 ? 2 : (C <= 3 ? 3 : 4);
     __shared__ float4 srec[32][NR + 1];
     __shared__ uint32_t spos[32], sid[32];
@@ -355,22 +357,21 @@ __global__ void __launch_bounds__(RT, 32) k_raster_fwd(RasterArgs a, float2* __r
 #pragma unroll
     for (int c = 0; c < C; c++) aAX[c] = aAY[c] = aBX[c] = aBY[c] = f2(0.f);
     uint32_t last[4] = {0, 0, 0, 0};
-    uint32_t kmax = 0;
     int nc[4] = {0, 0, 0, 0};
     // the list entry of the next batch is loaded one batch ahead
-    uint32_t s_pf = (uint32_t)lane < n ? a.list[beg + lane] : 0u;
+    uint32_t s_pf = (uint32_t)lane < n && HCGS_DCHECK(a.status, beg + lane < a.M) ? a.list[beg + lane] : 0u;
     for (uint32_t p0 = 0; p0 < n; p0 += 32) {
         const bool live = TA.x >= teps || TA.y >= teps || TB.x >= teps || TB.y >= teps;
         if (!__any_sync(0xffffffffu, live)) break;
         const uint32_t s_cur = s_pf;
-        if (p0 + 32u + (uint32_t)lane < n) s_pf = a.list[beg + p0 + 32u + (uint32_t)lane];
+        if (p0 + 32u + (uint32_t)lane < n && HCGS_DCHECK(a.status, beg + p0 + 32u + lane < a.M))
+            s_pf = a.list[beg + p0 + 32u + (uint32_t)lane];
         const int nh = stage_warp<NR, FT, true>(a, vN, beg, p0, n, tx, ty, sx0, sy0, srec, spos, sid, kept + nkept,
                                                 s_cur);
         for (int k = 0; k < nh; k++) {
             const float4* rec = srec[k];
             const float4 r0 = rec[0], r1 = rec[1], kk = rec[NR];
             const uint32_t pos1 = nkept + (uint32_t)k + 1u;  // staged index + 1
-            const uint32_t rank1 = sid[k] + 1u;               // visiting rank + 1
             auto step = [&](auto cl) {
                 const EntryX x = entry_x(fpx, r0, kk);
                 float2 dyA, ogA, aA, dyB, ogB, aB;
@@ -378,13 +379,12 @@ __global__ void __launch_bounds__(RT, 32) k_raster_fwd(RasterArgs a, float2* __r
                 const bool c0 = TA.x >= teps && aA.x >= a.amin, c1 = TA.y >= teps && aA.y >= a.amin;
                 const bool c2 = TB.x >= teps && aB.x >= a.amin, c3 = TB.y >= teps && aB.y >= a.amin;
                 fwd_pair<C>(rec, aA, c0, c1, TA, aAX, aAY);
-                last[0] = c0 ? rank1 : last[0];
-                last[1] = c1 ? rank1 : last[1];
+                last[0] = c0 ? pos1 : last[0];
+                last[1] = c1 ? pos1 : last[1];
                 if (NCOUNT) { nc[0] += c0; nc[1] += c1; }
                 fwd_pair<C>(rec, aB, c2, c3, TB, aBX, aBY);
-                last[2] = c2 ? rank1 : last[2];
-                last[3] = c3 ? rank1 : last[3];
-                kmax = (c0 || c1 || c2 || c3) ? pos1 : kmax;
+                last[2] = c2 ? pos1 : last[2];
+                last[3] = c3 ? pos1 : last[3];
                 if (NCOUNT) { nc[2] += c2; nc[3] += c3; }
             };
             if (may_clamp(r1.y, a.amax)) step(std::true_type{});
@@ -395,9 +395,6 @@ __global__ void __launch_bounds__(RT, 32) k_raster_fwd(RasterArgs a, float2* __r
     }
     const size_t plane = (size_t)v * a.L + l;
     const size_t HW = (size_t)a.H * a.W;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
-    if (lane == 0) skmax[plane * gridDim.x + strip] = kmax;
 #pragma unroll
     for (int q = 0; q < 4; q++) {
         if (!(colin && py + 2 * q < a.H)) continue;
@@ -501,53 +498,17 @@ __device__ __forceinline__ void entry_moments(float dx, float2 S0, float2 Sy, fl
     for (int e = 0; e < 2 * C; e++) out[6 + e] = gw[e].x + gw[e].y;
 }
 
-// Stages the next entries of the union of a tile's two strip lists, in
-// descending visiting rank (the adjoint's back-to-front order).  List A holds
-// [0, ia) and list B [0, ib), each ascending in rank.  The warp takes the 32
-// highest remaining ranks of each, merges them (an entry in both lists once),
-// writes the ranks of the 32 highest (or all, if fewer remain) to wrank in
-// descending order with their records, coefficients and Gaussian ids, and
-// consumes them from both lists.  Returns the number staged.
+// Loads kept entries [lo, lo + cnt) of a strip (visiting ranks from the forward
+// pass) into the warp's slots: record, base-2 exponent coefficients and the
+// Gaussian id (the 2D gradients are stored in Gaussian order, so that the
+// projection adjoint reads them contiguously).
 template <int NR, int FT>
-__device__ __forceinline__ int stage_union(const RasterArgs& a, size_t vN, const uint32_t* kA, const uint32_t* kB,
-                                           uint32_t& ia, uint32_t& ib, float4 (*wrec)[NR + 1], uint32_t* wid,
-                                           uint32_t* wrank) {
-    constexpr unsigned FULL = 0xffffffffu;
+__device__ __forceinline__ void stage_kept(const RasterArgs& a, size_t vN, const uint32_t* kept, uint32_t lo, int cnt,
+                                           float4 (*wrec)[NR + 1], uint32_t* wid) {
     const int lane = threadIdx.x & 31;
-    const bool va = (uint32_t)lane < ia, vb = (uint32_t)lane < ib;
-    const int ra = va ? (int)kA[ia - 1u - (uint32_t)lane] : -1;  // descending over the lanes
-    const int rb = vb ? (int)kB[ib - 1u - (uint32_t)lane] : -1;
-    // j0 = number of B candidates above ra, i0 = number of A candidates above rb
-    int j0 = 0, i0 = 0;
-#pragma unroll
-    for (int step = 16; step >= 1; step >>= 1) {
-        const int pb = __shfl_sync(FULL, rb, j0 + step - 1), pa = __shfl_sync(FULL, ra, i0 + step - 1);
-        j0 += pb > ra ? step : 0;
-        i0 += pa > rb ? step : 0;
-    }
-    const int b31 = __shfl_sync(FULL, rb, 31), a31 = __shfl_sync(FULL, ra, 31);
-    j0 += (j0 == 31 && b31 > ra) ? 1 : 0;
-    i0 += (i0 == 31 && a31 > rb) ? 1 : 0;
-    // a B candidate equal to an A candidate is the same entry (ranks are unique)
-    const int twin = __shfl_sync(FULL, ra, i0 & 31);
-    const bool dup = vb && i0 < 32 && twin == rb;
-    const unsigned dm = __ballot_sync(FULL, dup);
-    auto below = [](unsigned m, int k) { return k >= 32 ? __popc(m) : __popc(m & ((1u << k) - 1u)); };
-    // merged positions (descending): distinct candidates above this one
-    const int posa = lane + j0 - below(dm, j0);
-    const int posb = lane - below(dm, lane) + i0;
-    const int twin_pos = __shfl_sync(FULL, posa, i0 & 31);
-    const bool ta = va && posa < 32, tb = vb && !dup && posb < 32;
-    const bool cb = vb && (dup ? twin_pos < 32 : posb < 32);  // a duplicate leaves with its twin
-    const unsigned ma = __ballot_sync(FULL, ta), mb = __ballot_sync(FULL, tb), mc = __ballot_sync(FULL, cb);
-    if (ta) wrank[posa] = (uint32_t)ra;
-    if (tb) wrank[posb] = (uint32_t)rb;
-    ia -= (uint32_t)__popc(ma);
-    ib -= (uint32_t)__popc(mc);
-    const int nh = __popc(ma) + __popc(mb);
-    __syncwarp();
-    if (lane < nh) {
-        const uint32_t s = wrank[lane];
+    if (lane < cnt) {
+        uint32_t s = kept[lo + lane];
+        if (!HCGS_DCHECK(a.status, s < (uint32_t)a.N)) s = 0u;  // checked build: a stray rank reads entry 0
         const float4* r = a.rec + (vN + s) * NR;
         const float4 q0 = r[0], q1 = r[1];
         wrec[lane][0] = q0;
@@ -558,55 +519,37 @@ __device__ __forceinline__ int stage_union(const RasterArgs& a, size_t vN, const
         wid[lane] = a.sortid[vN + s];
     }
     __syncwarp();
-    return nh;
 }
 
-// One warp per (16 x 16 tile, plane, view): eight pixels per thread (one
-// column, rows r, r + 2, ..., r + 14 of the tile: the thread's four pixels of
-// each of the tile's two forward strips).  The warp walks the union of the two
-// strips' kept lists back to front.  A pixel takes entry s iff s precedes its
-// last contributor (s < last) and alpha >= alpha_min: an entry missing from a
-// strip's list either cannot reach that strip (alpha < alpha_min there) or
-// comes after all of its pixels stopped, so the union walk repeats every
-// forward decision exactly.
 template <int C, int FT>
-__global__ void __launch_bounds__(RT, 16) k_raster_bwd(RasterArgs a, const float* __restrict__ Tsave,
+__global__ void __launch_bounds__(RT, 24) k_raster_bwd(RasterArgs a, const float* __restrict__ Tsave,
                                                     const uint32_t* __restrict__ lastsave,
-                                                    const uint32_t* __restrict__ skmax,
                                                     const float2* __restrict__ gU, float* __restrict__ g2d) {
     constexpr int NR = C <= 1 ? 2 : (C <= 3 ? 3 : 4);
     constexpr int G = 6 + 2 * C;
     constexpr int RS = 36;  // row stride of the reduction buffer (floats)
-    constexpr int NP = 8;   // pixels per thread
     __shared__ float4 srec[32][NR + 1];
-    __shared__ uint32_t sid[32], srank[32];
+    __shared__ uint32_t sid[32];
     __shared__ __align__(16) float sred[G][RS];
     const int lane = threadIdx.x;
-    const int tile = blockIdx.x, l = blockIdx.y, v = blockIdx.z;
-    const int tx = tile % a.tilesX, ty = tile / a.tilesX;
+    const int strip = blockIdx.x, l = blockIdx.y, v = blockIdx.z;
+    const int tx = strip % a.tilesX, ty = (strip / a.tilesX) >> 1;
     const int px = tx * TILE + (lane & 15);
-    const int py = ty * TILE + (lane >> 4);  // rows py, py + 2, ..., py + 14
+    const int sy = ty * TILE + 8 * ((strip / a.tilesX) & 1);
+    const int py = sy + (lane >> 4);
     const uint32_t gb = ((uint32_t)(v * a.L + l) * a.ctY + ty / COARSE) * a.ctX + tx / COARSE;
     const uint32_t beg = a.off[gb], n = a.off[gb + 1] - beg;
-    const uint32_t* kA = a.slist + strip_list_base(beg, n, tx, 2 * ty);
-    const uint32_t* kB = a.slist + strip_list_base(beg, n, tx, 2 * ty + 1);
+    const uint32_t* kept = a.slist + strip_list_base(beg, n, tx, strip / a.tilesX);
     const size_t vN = (size_t)v * a.N;
     const size_t plane = (size_t)v * a.L + l;
     const size_t HW = (size_t)a.H * a.W;
-    const size_t nstrips = (size_t)a.tilesX * a.tilesY * 2;
-    uint32_t ia = skmax[plane * nstrips + (size_t)(2 * ty) * a.tilesX + tx];
-    uint32_t ib = skmax[plane * nstrips + (size_t)(2 * ty + 1) * a.tilesX + tx];
     const float fpx = (float)px;
-    float2 pyq[NP / 2];
+    const float2 pyA = make_float2((float)py, (float)(py + 2)), pyB = make_float2((float)(py + 4), (float)(py + 6));
+    float Tq[4] = {1.f, 1.f, 1.f, 1.f};
+    uint32_t last[4] = {0, 0, 0, 0};
+    float2 gq[4][C];
 #pragma unroll
-    for (int k = 0; k < NP / 2; k++) pyq[k] = make_float2((float)(py + 4 * k), (float)(py + 4 * k + 2));
-    float Tq[NP];
-    uint32_t last[NP];
-    float2 gq[NP][C];
-#pragma unroll
-    for (int q = 0; q < NP; q++) {
-        Tq[q] = 1.f;
-        last[q] = 0;
+    for (int q = 0; q < 4; q++) {
 #pragma unroll
         for (int c = 0; c < C; c++) gq[q][c] = make_float2(0.f, 0.f);
         if (px < a.W && py + 2 * q < a.H) {
@@ -617,49 +560,42 @@ __global__ void __launch_bounds__(RT, 16) k_raster_bwd(RasterArgs a, const float
             for (int c = 0; c < C; c++) gq[q][c] = gU[(plane * C + c) * HW + pix];
         }
     }
-    // pixel pairs (2k, 2k + 1): packed transmittance, projected suffix, upstream gradient
-    float2 T2[NP / 2], B2[NP / 2], gX[NP / 2][C], gY[NP / 2][C];
+    float2 TA = make_float2(Tq[0], Tq[1]), TB = make_float2(Tq[2], Tq[3]);
+    float2 gAX[C], gAY[C], gBX[C], gBY[C];
 #pragma unroll
-    for (int k = 0; k < NP / 2; k++) {
-        T2[k] = make_float2(Tq[2 * k], Tq[2 * k + 1]);
-        B2[k] = f2(0.f);
-#pragma unroll
-        for (int c = 0; c < C; c++) {
-            gX[k][c] = make_float2(gq[2 * k][c].x, gq[2 * k + 1][c].x);
-            gY[k][c] = make_float2(gq[2 * k][c].y, gq[2 * k + 1][c].y);
-        }
+    for (int c = 0; c < C; c++) {
+        gAX[c] = make_float2(gq[0][c].x, gq[1][c].x);
+        gAY[c] = make_float2(gq[0][c].y, gq[1][c].y);
+        gBX[c] = make_float2(gq[2][c].x, gq[3][c].x);
+        gBY[c] = make_float2(gq[2][c].y, gq[3][c].y);
     }
-    while (ia > 0u || ib > 0u) {
-        const int nh = stage_union<NR, FT>(a, vN, kA, kB, ia, ib, srec, sid, srank);
-        for (int k = 0; k < nh; k++) {  // back to front over the visiting order
+    float2 BA = f2(0.f), BB = f2(0.f);  // sum_c Re(conj(g_c) S_c) per pixel
+    uint32_t maxlast = max(max(last[0], last[1]), max(last[2], last[3]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) maxlast = max(maxlast, __shfl_xor_sync(0xffffffffu, maxlast, o));
+    if (!HCGS_DCHECK(a.status, maxlast <= n)) maxlast = 0u;  // checked build: a stray length skips the strip
+    for (uint32_t hi = maxlast; hi > 0;) {
+        const uint32_t lo = hi > 32u ? hi - 32u : 0u;
+        const int nh = (int)(hi - lo);
+        stage_kept<NR, FT>(a, vN, kept, lo, nh, srec, sid);
+        for (int k = nh - 1; k >= 0; k--) {  // back-to-front over the visiting order
             const float4* rec = srec[k];
-            const uint32_t s = srank[k];
+            const uint32_t pos = lo + (uint32_t)k;
             const float4 r0 = rec[0], r1 = rec[1], kk = rec[NR];
             auto step = [&](auto cl) {
                 constexpr bool CL = decltype(cl)::value;
                 const EntryX x = entry_x(fpx, r0, kk);
-                float2 dy[NP / 2], og[NP / 2], al[NP / 2];
-                eval_entry<FT, CL>(x, pyq[0], pyq[1], r0, r1, kk, a.amax, dy[0], og[0], al[0], dy[1], og[1], al[1]);
-                eval_entry<FT, CL>(x, pyq[2], pyq[3], r0, r1, kk, a.amax, dy[2], og[2], al[2], dy[3], og[3], al[3]);
-                bool cq[NP];
-                bool any = false;
-#pragma unroll
-                for (int k2 = 0; k2 < NP / 2; k2++) {
-                    cq[2 * k2] = s < last[2 * k2] && al[k2].x >= a.amin;
-                    cq[2 * k2 + 1] = s < last[2 * k2 + 1] && al[k2].y >= a.amin;
-                    any = any || cq[2 * k2] || cq[2 * k2 + 1];
-                }
-                // no pixel of the tile took this step: zero gradient, T and B unchanged
-                if (!__any_sync(0xffffffffu, any)) return;
+                float2 dyA, ogA, aA, dyB, ogB, aB;
+                eval_entry<FT, CL>(x, pyA, pyB, r0, r1, kk, a.amax, dyA, ogA, aA, dyB, ogB, aB);
+                const bool c0 = pos < last[0] && aA.x >= a.amin, c1 = pos < last[1] && aA.y >= a.amin;
+                const bool c2 = pos < last[2] && aB.x >= a.amin, c3 = pos < last[3] && aB.y >= a.amin;
+                // no pixel of the strip took this step: zero gradient, T and B unchanged
+                if (!__any_sync(0xffffffffu, c0 || c1 || c2 || c3)) return;
                 // branch-free: pixels that did not take the step carry alpha 0
                 // through the pair (T and B unchanged, zero gradient)
                 float2 gw[2 * C], S0, Sy, Syy;
-                bwd_pair<C, true, CL>(rec, dy[0], og[0], al[0], cq[0], cq[1], a.amax, T2[0], B2[0], gX[0], gY[0],
-                                      gw, S0, Sy, Syy);
-#pragma unroll
-                for (int k2 = 1; k2 < NP / 2; k2++)
-                    bwd_pair<C, false, CL>(rec, dy[k2], og[k2], al[k2], cq[2 * k2], cq[2 * k2 + 1], a.amax, T2[k2],
-                                           B2[k2], gX[k2], gY[k2], gw, S0, Sy, Syy);
+                bwd_pair<C, true, CL>(rec, dyA, ogA, aA, c0, c1, a.amax, TA, BA, gAX, gAY, gw, S0, Sy, Syy);
+                bwd_pair<C, false, CL>(rec, dyB, ogB, aB, c2, c3, a.amax, TB, BB, gBX, gBY, gw, S0, Sy, Syy);
                 float gv[G];
                 entry_moments<C>(x.dx, S0, Sy, Syy, gw, gv);
                 // warp sum of the G values: each lane writes its column of the
@@ -688,6 +624,7 @@ __global__ void __launch_bounds__(RT, 16) k_raster_bwd(RasterArgs a, const float
             else step(std::false_type{});
         }
         __syncwarp();
+        hi = lo;
     }
 }
 
@@ -827,18 +764,17 @@ hcgs_status raster_forward(hcgs_ctx* ctx, hcgs_saved* s, float2* U, float* T_out
     HCGS_CUDA(ctx, grow(ctx, s->Tfin, pl * sizeof(float), &s->bytes));
     HCGS_CUDA(ctx, grow(ctx, s->last, pl * sizeof(uint32_t), &s->bytes));
     HCGS_CUDA(ctx, grow(ctx, s->slist, (size_t)COARSE * COARSE * 2 * s->M * sizeof(uint32_t) + 16, &s->bytes));
-    HCGS_CUDA(ctx, grow(ctx, s->skmax, (size_t)s->V * s->L * s->tilesX * s->tilesY * 2 * sizeof(uint32_t), &s->bytes));
     RasterArgs a = make_raster_args(s);
+    a.status = ctx->d_status;
     dim3 grid(s->tilesX * s->tilesY * 2, s->L, s->V);  // 16 x 8 pixel strips
     float* Ts = (float*)s->Tfin.p;
     uint32_t* ls = (uint32_t*)s->last.p;
-    uint32_t* km = (uint32_t*)s->skmax.p;
     const int ft = s->opts.footprint;
 #define HCGS_FWD_T(CC, FTV)                                                                                                 \
     if (nc_out)                                                                                                             \
-        HCGS_KERNEL(ctx, "k_raster_fwd", st, (k_raster_fwd<CC, FTV, true><<<grid, RT, 0, st>>>(a, U, Ts, ls, km, T_out, nc_out)));  \
+        HCGS_KERNEL(ctx, "k_raster_fwd", st, (k_raster_fwd<CC, FTV, true><<<grid, RT, 0, st>>>(a, U, Ts, ls, T_out, nc_out)));  \
     else                                                                                                                    \
-        HCGS_KERNEL(ctx, "k_raster_fwd", st, (k_raster_fwd<CC, FTV, false><<<grid, RT, 0, st>>>(a, U, Ts, ls, km, T_out, nc_out)))
+        HCGS_KERNEL(ctx, "k_raster_fwd", st, (k_raster_fwd<CC, FTV, false><<<grid, RT, 0, st>>>(a, U, Ts, ls, T_out, nc_out)))
 #define HCGS_FWD(CC)                          \
     if (ft == 1) {                            \
         HCGS_FWD_T(CC, 1);                    \
@@ -864,20 +800,19 @@ hcgs_status raster_backward(hcgs_ctx* ctx, hcgs_saved* s, const float2* gU, cuda
     HCGS_CUDA(ctx, grow(ctx, s->g2d, ng * sizeof(float), &s->bytes));
     HCGS_CUDA(ctx, cudaMemsetAsync(s->g2d.p, 0, ng * sizeof(float), st));
     RasterArgs a = make_raster_args(s);
-    dim3 grid(s->tilesX * s->tilesY * 2, s->L, s->V);  // 16 x 8 pixel strips (dense plane-weight pass)
-    dim3 tgrid(s->tilesX * s->tilesY, s->L, s->V);     // 16 x 16 tiles (adjoint)
+    a.status = ctx->d_status;
+    dim3 grid(s->tilesX * s->tilesY * 2, s->L, s->V);  // 16 x 8 pixel strips
     const float* Ts = (const float*)s->Tfin.p;
     const uint32_t* ls = (const uint32_t*)s->last.p;
-    const uint32_t* km = (const uint32_t*)s->skmax.p;
     float* g2 = (float*)s->g2d.p;
     const int ft = s->opts.footprint;
-#define HCGS_BWD(CC)                                                                                                   \
-    if (ft == 1)                                                                                                       \
-        HCGS_KERNEL(ctx, "k_raster_bwd", st, (k_raster_bwd<CC, 1><<<tgrid, RT, 0, st>>>(a, Ts, ls, km, gU, g2)));      \
-    else if (ft == 2)                                                                                                  \
-        HCGS_KERNEL(ctx, "k_raster_bwd", st, (k_raster_bwd<CC, 2><<<tgrid, RT, 0, st>>>(a, Ts, ls, km, gU, g2)));      \
-    else                                                                                                               \
-        HCGS_KERNEL(ctx, "k_raster_bwd", st, (k_raster_bwd<CC, 0><<<tgrid, RT, 0, st>>>(a, Ts, ls, km, gU, g2)))
+#define HCGS_BWD(CC)                                                                                              \
+    if (ft == 1)                                                                                                  \
+        HCGS_KERNEL(ctx, "k_raster_bwd", st, (k_raster_bwd<CC, 1><<<grid, RT, 0, st>>>(a, Ts, ls, gU, g2)));      \
+    else if (ft == 2)                                                                                             \
+        HCGS_KERNEL(ctx, "k_raster_bwd", st, (k_raster_bwd<CC, 2><<<grid, RT, 0, st>>>(a, Ts, ls, gU, g2)));      \
+    else                                                                                                          \
+        HCGS_KERNEL(ctx, "k_raster_bwd", st, (k_raster_bwd<CC, 0><<<grid, RT, 0, st>>>(a, Ts, ls, gU, g2)))
     switch (s->C) {
         case 1: HCGS_BWD(1); break;
         case 2: HCGS_BWD(2); break;

@@ -76,3 +76,19 @@ def test_torch_complex_gradient_convention():
     x, y = z.detach().real, z.detach().imag
     expect = (6 * x - y) + 1j * (5.0 - x)
     assert torch.allclose(z.grad, expect)
+
+
+def test_checked_build_exports_the_same_entry_points():
+    # the bounds-checked variant (HCGS_CHECKED) is the same ABI; only
+    # hcgs_is_checked_build tells them apart (callable without a GPU)
+    import __graft_entry__ as E
+    checked = ctypes.CDLL(E._build_module().build(checked=True))
+    regular = ctypes.CDLL(E._build_module().build())
+    for name in _declared():
+        assert hasattr(checked, name), name
+    checked.hcgs_is_checked_build.restype = ctypes.c_int
+    regular.hcgs_is_checked_build.restype = ctypes.c_int
+    assert checked.hcgs_is_checked_build() == 1 and regular.hcgs_is_checked_build() == 0
+    for lib_ in (checked, regular):
+        lib_.hcgs_check_status.restype = ctypes.c_int
+        assert lib_.hcgs_check_status(None, None) == -1  # NULL context, no CUDA call
