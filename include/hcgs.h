@@ -158,7 +158,10 @@ typedef struct {
 } hcgs_gaussian_grads;
 
 /* ---------------- context ---------------- */
-/* Creates a context on `device` (made current for the call). */
+/* Creates a context on `device` (made current for the call).  Destroying it
+ * (and releasing a saved state) first waits for the work the context's
+ * launches enqueued, on every stream they used (not for the whole device),
+ * then frees its buffers. */
 hcgs_status hcgs_ctx_create(hcgs_ctx** ctx, int device);
 void hcgs_ctx_destroy(hcgs_ctx* ctx);
 const char* hcgs_status_string(hcgs_status s);
@@ -202,7 +205,8 @@ hcgs_status hcgs_selftest_wait_timeout(hcgs_ctx* ctx, void* stream);
  *   HCGS_ERR_DEVICE_CHECK if a check failed since the last report,
  *   HCGS_ERR_TIMEOUT if a bounded device wait ran out, else HCGS_OK; the
  *   context stays usable.  (hcgs_project / hcgs_render_view also report the
- *   word at their own readback.)
+ *   word at their own readback, which follows the projection: a non-finite
+ *   Gaussian makes that very call return HCGS_ERR_DEVICE_CHECK.)
  * hcgs_selftest_device_check: checked build only (else HCGS_ERR_STATE).
  *   kind 0 launches a kernel whose index check fails (the index is outside
  *   the checked range but inside its buffer); kind 1 writes one byte into

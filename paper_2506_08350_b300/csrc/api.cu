@@ -66,7 +66,15 @@ cudaError_t grow(hcgs_ctx* ctx, DevBuf& b, size_t bytes, size_t* owner_bytes) {
 }
 
 void prof_begin(hcgs_ctx* ctx, const char* name, cudaStream_t st) {
-    if (!ctx || !ctx->prof.on) return;
+    if (!ctx) return;
+    // the streams this context's work was enqueued on: releasing a saved
+    // state or the context waits for them, not for the whole device
+    if (ctx->streams.empty() || ctx->streams.back() != st) {
+        bool seen = false;
+        for (cudaStream_t x : ctx->streams) seen = seen || x == st;
+        if (!seen) ctx->streams.push_back(st);
+    }
+    if (!ctx->prof.on) return;
     Prof& P = ctx->prof;
     if (P.used + 2 > P.pool.size()) {
         for (int k = 0; k < 64; k++) {
@@ -240,10 +248,16 @@ static void saved_free(hcgs_saved* s) {
     s->bytes = 0;
 }
 
+// waits for the work this context enqueued (on every stream it used)
+static void wait_ctx_streams(hcgs_ctx* ctx) {
+    for (cudaStream_t st : ctx->streams)
+        if (cudaStreamSynchronize(st) != cudaSuccess) cudaGetLastError();  // a stream destroyed since: nothing to wait for
+}
+
 void hcgs_ctx_destroy(hcgs_ctx* ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
-    cudaDeviceSynchronize();
+    wait_ctx_streams(ctx);
     for (auto& b : ctx->ws) free_buf(b);
     free_buf(ctx->selftest);
     for (auto& kv : ctx->plans) cudaFree(kv.second.tw);
@@ -390,8 +404,12 @@ hcgs_status hcgs_saved_create(hcgs_ctx* ctx, hcgs_saved** out) {
 
 hcgs_status hcgs_saved_release(hcgs_ctx* ctx, hcgs_saved* s) {
     if (!s) return HCGS_OK;
-    if (ctx) cudaSetDevice(ctx->device);
-    cudaDeviceSynchronize();
+    if (ctx) {
+        cudaSetDevice(ctx->device);
+        wait_ctx_streams(ctx);  // the saved state's buffers are used only by this context's launches
+    } else {
+        cudaDeviceSynchronize();  // no context to ask which streams used it
+    }
     saved_free(s);
     delete s;
     return HCGS_OK;

@@ -71,6 +71,7 @@ struct hcgs_ctx {
     size_t bytes = 0;
     hcgs::DevBuf ws[10];                             // workspace slots (6, 7: zero-padded grids; 8, 9: phase-only conversion)
     hcgs::DevBuf selftest;                           // target of hcgs_selftest_device_check
+    std::vector<cudaStream_t> streams;               // streams this context's kernels were launched on
     std::map<int, hcgs::FftPlan> plans;              // FFT plans by length
     std::map<hcgs::HKey, hcgs::DevBuf> htab;         // transfer-function tables
     int* d_status = nullptr;                         // device status word
