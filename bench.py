@@ -78,6 +78,10 @@ def parse():
     ap.add_argument("--kernels-out", default=None, help="write the per-kernel table (JSON) here")
     ap.add_argument("--objective-only", action="store_true",
                     help="time only the two objectives on one view of the workload's optics and print them")
+    ap.add_argument("--mlp-only", action="store_true",
+                    help="time only the learned-initialisation network (forward, reverse mode, fit step) and print it")
+    ap.add_argument("--footprint", type=int, default=0, choices=[0, 1, 2],
+                    help="footprint tier of the timed step: 0 FP32 (the headline), 1 FP16x2, 2 BF16x2")
     return ap.parse_args()
 
 
@@ -439,7 +443,7 @@ def run_ours(args):
     grads = {k: torch.empty_like(g[k]) for k in P.PARAM_NAMES}
     ctx = P.Context(dev.index)
     saved = P.Saved(ctx)
-    opts = dict(P.DEFAULT_OPTS)
+    opts = dict(P.DEFAULT_OPTS, footprint=args.footprint)
     stream = torch.cuda.current_stream()
 
     def fwd():
@@ -615,9 +619,12 @@ def run_ours(args):
     value = views / (ms_step / 1e3)
     result = {"metric": METRIC, "value": value, "unit": "views/s", "n_gpus": world, "steps": args.steps,
               "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-              "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+              "vs_baseline": None,
+              "dtype": {0: "f32", 1: "f16x2 footprint, f32 accumulate", 2: "bf16x2 footprint, f32 accumulate"}[args.footprint],
+              "data": "synthetic",
               "config": {"workload": wl.name, "H": o.H, "W": o.W, "C": o.C, "L": o.L, "N": wl.N,
                          "views_per_step_per_gpu": V, "step": "render forward + adjoint from a fixed dL/dP",
+                         "footprint": args.footprint,
                          "l2": "inputs larger than L2 (~30 GB per step working set), no flush"},
               "steps_per_s": 1e3 / ms_step, "fwd_views_per_s": views / (ms_fwd / 1e3),
               "ms_per_fwd": ms_fwd, "clocks": clocks,
@@ -710,10 +717,23 @@ def run_objective_only(args):
     print(json.dumps({"workload": args.workload, "objective": out}), flush=True)
 
 
+def run_mlp_only(args):
+    import torch
+    torch.cuda.set_device(0)
+    import paper_2506_08350_b300 as P
+    ctx = P.Context(0)
+    pk = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else None
+    out = measure_mlp(ctx, P, torch.device("cuda", 0), pk, steps=args.steps, warmup=args.warmup)
+    ctx.close()
+    print(json.dumps({"learned_init_mlp": out}), flush=True)
+
+
 def main():
     args = parse()
     if args.objective_only:
         run_objective_only(args)
+    elif args.mlp_only:
+        run_mlp_only(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
