@@ -676,7 +676,13 @@ def run_ours(args):
                 ent.update(bound="alu", achieved=ach, peak=alu_peak_tops, unit="Top/s", frac=ach / alu_peak_tops,
                            pairs_per_step=pairs, ops_per_pair=OPS_PER_PAIR[name](o.C))
             tr = traffic.get(name)
-            if tr and tr.get("source_sha") == src_hash(KERNEL_SOURCE[name]) and tr.get("workload") == wl.name:
+            if tr and tr.get("source_sha") == src_hash(KERNEL_SOURCE[name]):
+                # ncu's pipe counters of the same source, beside the ALU roofline
+                for key in ("fma_pipe_active_pct", "issue_active_pct", "warps_active_per_sm"):
+                    if key in tr:
+                        ent["ncu_" + key] = tr[key]
+            if tr and tr.get("source_sha") == src_hash(KERNEL_SOURCE[name]) and tr.get("workload") == wl.name \
+                    and "dram_bytes_per_launch" in tr:
                 ent["traffic_bytes_per_launch"] = tr["dram_bytes_per_launch"]
                 # the DRAM rate those bytes make at the measured launch time,
                 # beside the kernel's own (ALU) roofline
@@ -691,6 +697,8 @@ def run_ours(args):
         ach_launch = d["achieved"]
         result["roofline"] = {"kernel": dom, "bound": d["bound"], "achieved": ach_launch, "peak": d["peak"],
                               "unit": d["unit"], "frac": d["frac"],
+                              "ncu_fma_pipe_active_pct": d.get("ncu_fma_pipe_active_pct"),
+                              "ncu_issue_active_pct": d.get("ncu_issue_active_pct"),
                               "traffic": d.get("traffic_bytes_per_launch"),
                               "traffic_gbs": d.get("dram_gbs"),
                               "peak_source": (hbm_src if d["bound"] == "hbm" else
