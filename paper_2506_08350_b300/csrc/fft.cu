@@ -361,12 +361,18 @@ struct Stages<N, INV, NTRANS, T, NS, Seq<R>, Lays<>> {
     using It = Items<M, NTRANS, T>;
     static constexpr int U = It::U, RAD = R;
     static constexpr int smem(int) { return 0; }
+    static constexpr int exchanges() { return 0; }
     // v: this stage's inputs (element j + r M of item j); out(v) receives
     // the outputs (element j + r M of the transform again)
     template <class Out>
     static __device__ __forceinline__ void run(float2 (&v)[U][R], float2*, const float2* __restrict__ tw, Out&& out) {
         sfor<U>([&](auto a) { stage_math<N, NS, R, INV>(v[HCGS_CI(a)], It::j(HCGS_CI(a)), tw); });
         out(v);
+    }
+    template <class Out>
+    static __device__ __forceinline__ void run2(float2 (&v)[U][R], float2*, float2*, const float2* __restrict__ tw,
+                                                Out&& out) {
+        run(v, nullptr, tw, out);
     }
 };
 
@@ -410,6 +416,41 @@ struct Stages<N, INV, NTRANS, T, NS, Seq<R, R2, RS...>, Lays<L, LS...>> {
         });
         Next::run(v2, sm, tw, out);
     }
+    // The same with the exchanges alternating between two buffers (a, then
+    // b for the next exchange, ...): a buffer's earlier readers are then
+    // always past the barrier that followed the other buffer's writes, so the
+    // barrier before each write is not needed.  Requires at least two
+    // exchanges per transform between two uses of the same buffer.
+    template <class Out>
+    static __device__ __forceinline__ void run2(float2 (&v)[U][R], float2* sa, float2* sb,
+                                                const float2* __restrict__ tw, Out&& out) {
+        sfor<U>([&](auto a) { stage_math<N, NS, R, INV>(v[HCGS_CI(a)], It::j(HCGS_CI(a)), tw); });
+        sfor<U>([&](auto a) {
+            constexpr int u = HCGS_CI(a);
+            if (It::valid(u)) {
+                const int j = It::j(u), t = It::t(u);
+                const int base = (j / NS) * NS * R + j % NS;
+                sfor<R>([&](auto b) {
+                    constexpr int r = HCGS_CI(b);
+                    sa[L::at((base + r * NS) * NTRANS + t)] = v[u][r];
+                });
+            }
+        });
+        __syncthreads();
+        using Nt = typename Next::It;
+        float2 v2[Next::U][R2];
+        sfor<Next::U>([&](auto a) {
+            constexpr int u = HCGS_CI(a);
+            const bool ok = Nt::valid(u);
+            const int j = Nt::j(u), t = Nt::t(u);
+            sfor<R2>([&](auto b) {
+                constexpr int r = HCGS_CI(b);
+                v2[u][r] = ok ? sa[L::at((j + r * Next::M) * NTRANS + t)] : make_float2(0.f, 0.f);
+            });
+        });
+        Next::run2(v2, sb, sa, tw, out);
+    }
+    static constexpr int exchanges() { return 1 + Next::exchanges(); }
 };
 
 template <class V>
@@ -586,15 +627,34 @@ __global__ void __launch_bounds__(CP::T, CP::MINB)
 // shared-memory buffer by bulk copies while the current plane is transformed
 // (two buffers, one mbarrier each).  Shared memory: the exchange buffer, then
 // the row buffers, then the barriers.
+// Exchange buffers of the row passes: with two (ALT), consecutive exchanges
+// alternate between them and each exchange needs one barrier instead of two.
+#ifndef HCGS_ROWS_SUM_ALT
+#define HCGS_ROWS_SUM_ALT 0
+#endif
+#ifndef HCGS_ROWS_SPREAD_ALT
+#define HCGS_ROWS_SPREAD_ALT 1
+#endif
 template <class RP, bool WITH_INPUT>
 struct RowSmem {
     static constexpr int W = RP::N, HS = hq_stride(RP::N);
-    static constexpr int XS = (RP::smem_slots() + 1) & ~1;     // exchange (float2, even)
+    static constexpr bool ALT = WITH_INPUT ? HCGS_ROWS_SUM_ALT : HCGS_ROWS_SPREAD_ALT;
+    static constexpr int XS = (RP::smem_slots() + 1) & ~1;     // one exchange buffer (float2, even)
+    static constexpr int XB = ALT ? 2 * XS : XS;               // all exchange buffers
     static constexpr int IN = WITH_INPUT ? 2 * W : 0;          // input rows
     using SI = typename RP::template SB<true>;
+    using SF = typename RP::template SA<false>;
+    static_assert(!ALT || (SI::exchanges() >= 2 && SF::exchanges() >= 2),
+                  "alternating exchange buffers need two exchanges per transform");
     // the row's spectrum, held across the planes (spread pass), thread-major
     static constexpr int SP = WITH_INPUT ? 0 : ((SI::U * SI::RAD * RP::T + 1) & ~1);
-    static constexpr size_t bytes = (size_t)(XS + IN + 2 * HS + SP) * sizeof(float2) + 2 * sizeof(uint64_t);
+    static constexpr size_t bytes = (size_t)(XB + IN + 2 * HS + SP) * sizeof(float2) + 2 * sizeof(uint64_t);
+    // runs transform S on v through the exchange buffers at xb
+    template <class S, class V, class Out>
+    static __device__ __forceinline__ void run(V& v, float2* xb, const float2* __restrict__ tw, Out&& out) {
+        if constexpr (ALT) S::run2(v, xb, xb + XS, tw, out);
+        else S::run(v, xb, tw, out);
+    }
 };
 
 // If a bulk copy for plane l does not arrive within the bounded wait, the CTA
@@ -635,7 +695,7 @@ __global__ void __launch_bounds__(RP::T, RP::N == 1920 ? 3 : RP::MINB)
     using SI = typename RP::template SB<true>;
     extern __shared__ __align__(16) float2 sm[];
     float2* xb = sm;
-    float2* rowb = sm + SM::XS;
+    float2* rowb = sm + SM::XB;
     float2* hb = rowb + SM::IN;
     uint64_t* bar = reinterpret_cast<uint64_t*>(hb + 2 * HS);
     const int b = blockIdx.x, i = blockIdx.y, c = blockIdx.z;
@@ -676,7 +736,7 @@ __global__ void __launch_bounds__(RP::T, RP::N == 1920 ? 3 : RP::MINB)
                 v[u][HCGS_CI(r)] = okj ? srow[j + HCGS_CI(r) * SF::M] : make_float2(0.f, 0.f);
             });
         });
-        SF::run(v, xb, tw, [&](auto& vo) {
+        SM::template run<SF>(v, xb, tw, [&](auto& vo) {
             static_assert(Shape<decltype(vo)>::R == SI::RAD && Shape<decltype(vo)>::U == SI::U,
                           "the inverse pass must start with the forward pass's last radix");
             sfor<SI::U>([&](auto a) {
@@ -699,7 +759,7 @@ __global__ void __launch_bounds__(RP::T, RP::N == 1920 ? 3 : RP::MINB)
         }
     }
     float2* dst = out + (((size_t)b * C + c) * H + i) * W;
-    SI::run(acc, xb, tw, [&](auto& vo) {
+    SM::template run<SI>(acc, xb, tw, [&](auto& vo) {
         for_outputs<W, 1, RP::T>(vo, [&](float2 x, int pos, int) { dst[pos] = x; });
     });
 }
@@ -716,7 +776,7 @@ __global__ void __launch_bounds__(RP::T, RP::N == 1920 ? 3 : RP::MINB)
     using SI = typename RP::template SB<true>;
     extern __shared__ __align__(16) float2 sm[];
     float2* xb = sm;
-    float2* hb = sm + SM::XS;
+    float2* hb = sm + SM::XB;
     float2* sp = hb + 2 * HS;
     uint64_t* bar = reinterpret_cast<uint64_t*>(sp + SM::SP);
     const int b = blockIdx.x, i = blockIdx.y, c = blockIdx.z;
@@ -741,7 +801,7 @@ __global__ void __launch_bounds__(RP::T, RP::N == 1920 ? 3 : RP::MINB)
     {
         float2 v[SF::U][SF::RAD];
         load_row<SF>(v, in + (((size_t)b * C + c) * H + i) * W);
-        SF::run(v, xb, tw, [&](auto& vo) {
+        SM::template run<SF>(v, xb, tw, [&](auto& vo) {
             static_assert(Shape<decltype(vo)>::R == SI::RAD && Shape<decltype(vo)>::U == SI::U,
                           "the inverse pass must start with the forward pass's last radix");
             sfor<SI::U>([&](auto a) {
@@ -775,7 +835,7 @@ __global__ void __launch_bounds__(RP::T, RP::N == 1920 ? 3 : RP::MINB)
             issue(l + 2, buf);
         }
         float2* dst = out + ((((size_t)b * L + l) * C + c) * H + i) * W;
-        SI::run(v, xb, tw, [&](auto& vo) {
+        SM::template run<SI>(v, xb, tw, [&](auto& vo) {
             for_outputs<W, 1, RP::T>(vo, [&](float2 x, int pos, int) { dst[pos] = x; });
         });
     }
