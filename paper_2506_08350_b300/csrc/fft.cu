@@ -361,18 +361,12 @@ struct Stages<N, INV, NTRANS, T, NS, Seq<R>, Lays<>> {
     using It = Items<M, NTRANS, T>;
     static constexpr int U = It::U, RAD = R;
     static constexpr int smem(int) { return 0; }
-    static constexpr int exchanges() { return 0; }
     // v: this stage's inputs (element j + r M of item j); out(v) receives
     // the outputs (element j + r M of the transform again)
     template <class Out>
     static __device__ __forceinline__ void run(float2 (&v)[U][R], float2*, const float2* __restrict__ tw, Out&& out) {
         sfor<U>([&](auto a) { stage_math<N, NS, R, INV>(v[HCGS_CI(a)], It::j(HCGS_CI(a)), tw); });
         out(v);
-    }
-    template <class Out>
-    static __device__ __forceinline__ void run2(float2 (&v)[U][R], float2*, float2*, const float2* __restrict__ tw,
-                                                Out&& out) {
-        run(v, nullptr, tw, out);
     }
 };
 
@@ -416,41 +410,6 @@ struct Stages<N, INV, NTRANS, T, NS, Seq<R, R2, RS...>, Lays<L, LS...>> {
         });
         Next::run(v2, sm, tw, out);
     }
-    // The same with the exchanges alternating between two buffers (a, then
-    // b for the next exchange, ...): a buffer's earlier readers are then
-    // always past the barrier that followed the other buffer's writes, so the
-    // barrier before each write is not needed.  Requires at least two
-    // exchanges per transform between two uses of the same buffer.
-    template <class Out>
-    static __device__ __forceinline__ void run2(float2 (&v)[U][R], float2* sa, float2* sb,
-                                                const float2* __restrict__ tw, Out&& out) {
-        sfor<U>([&](auto a) { stage_math<N, NS, R, INV>(v[HCGS_CI(a)], It::j(HCGS_CI(a)), tw); });
-        sfor<U>([&](auto a) {
-            constexpr int u = HCGS_CI(a);
-            if (It::valid(u)) {
-                const int j = It::j(u), t = It::t(u);
-                const int base = (j / NS) * NS * R + j % NS;
-                sfor<R>([&](auto b) {
-                    constexpr int r = HCGS_CI(b);
-                    sa[L::at((base + r * NS) * NTRANS + t)] = v[u][r];
-                });
-            }
-        });
-        __syncthreads();
-        using Nt = typename Next::It;
-        float2 v2[Next::U][R2];
-        sfor<Next::U>([&](auto a) {
-            constexpr int u = HCGS_CI(a);
-            const bool ok = Nt::valid(u);
-            const int j = Nt::j(u), t = Nt::t(u);
-            sfor<R2>([&](auto b) {
-                constexpr int r = HCGS_CI(b);
-                v2[u][r] = ok ? sa[L::at((j + r * Next::M) * NTRANS + t)] : make_float2(0.f, 0.f);
-            });
-        });
-        Next::run2(v2, sb, sa, tw, out);
-    }
-    static constexpr int exchanges() { return 1 + Next::exchanges(); }
 };
 
 template <class V>
@@ -475,9 +434,10 @@ struct ColPlan {
     }
 };
 // Row plan: one row per CTA of T threads.
-template <int N_, int T_, int MINB_, class A_, class LA_, class B_, class LB_>
+// MINB_ / MINBS_: resident CTAs per SM the spread / sum pass's registers are capped for
+template <int N_, int T_, int MINB_, class A_, class LA_, class B_, class LB_, int MINBS_ = MINB_>
 struct RowPlan {
-    static constexpr int N = N_, T = T_, MINB = MINB_;
+    static constexpr int N = N_, T = T_, MINB = MINB_, MINBS = MINBS_;
     template <bool INV> using SA = Stages<N, INV, 1, T, 1, A_, LA_>;
     template <bool INV> using SB = Stages<N, INV, 1, T, 1, B_, LB_>;
     static constexpr int smem_slots() {
@@ -493,8 +453,11 @@ using Cols512 = ColPlan<512, 16, 512, 2, Seq<8, 8, 8>, Lays<Pad<1, 0>, Pad<1, 0>
                         Lays<Pad<1, 0>, Pad<1, 0>>>;
 using Cols256 = ColPlan<256, 16, 256, 3, Seq<16, 16>, Lays<Pad<1, 0>>, Seq<16, 16>, Lays<Pad<1, 0>>>;
 
-using Rows1920 = RowPlan<1920, 192, 2, Seq<16, 12, 10>, Lays<Pad<16, 1>, Pad<128, 1>>, Seq<10, 12, 16>,
-                         Lays<Pad<80, 1>, Pad<120, 2>>>;
+// 1920 = 8 x 15 x 16 on 128 threads: the stages have 240, 128 and 120 work
+// items, so few threads idle at the exchange barriers (16 x 12 x 10 on 192
+// threads left 37 % of them without a butterfly in the radix-16 stage)
+using Rows1920 = RowPlan<1920, 128, 4, Seq<8, 15, 16>, Lays<Pad<16, 1>, Pad<128, 1>>, Seq<16, 15, 8>,
+                         Lays<Pad<16, 1>, Pad<1, 0>>, 3>;
 using Rows1080 = RowPlan<1080, 128, 4, Seq<12, 10, 9>, Lays<Pad<48, 1>, Pad<120, 4>>, Seq<9, 10, 12>,
                          Lays<Pad<1, 0>, Pad<1, 0>>>;
 using Rows512 = RowPlan<512, 64, 8, Seq<8, 8, 8>, Lays<Pad<16, 1>, Pad<16, 2>>, Seq<8, 8, 8>,
@@ -627,34 +590,15 @@ __global__ void __launch_bounds__(CP::T, CP::MINB)
 // shared-memory buffer by bulk copies while the current plane is transformed
 // (two buffers, one mbarrier each).  Shared memory: the exchange buffer, then
 // the row buffers, then the barriers.
-// Exchange buffers of the row passes: with two (ALT), consecutive exchanges
-// alternate between them and each exchange needs one barrier instead of two.
-#ifndef HCGS_ROWS_SUM_ALT
-#define HCGS_ROWS_SUM_ALT 0
-#endif
-#ifndef HCGS_ROWS_SPREAD_ALT
-#define HCGS_ROWS_SPREAD_ALT 1
-#endif
 template <class RP, bool WITH_INPUT>
 struct RowSmem {
     static constexpr int W = RP::N, HS = hq_stride(RP::N);
-    static constexpr bool ALT = WITH_INPUT ? HCGS_ROWS_SUM_ALT : HCGS_ROWS_SPREAD_ALT;
-    static constexpr int XS = (RP::smem_slots() + 1) & ~1;     // one exchange buffer (float2, even)
-    static constexpr int XB = ALT ? 2 * XS : XS;               // all exchange buffers
+    static constexpr int XS = (RP::smem_slots() + 1) & ~1;     // exchange (float2, even)
     static constexpr int IN = WITH_INPUT ? 2 * W : 0;          // input rows
     using SI = typename RP::template SB<true>;
-    using SF = typename RP::template SA<false>;
-    static_assert(!ALT || (SI::exchanges() >= 2 && SF::exchanges() >= 2),
-                  "alternating exchange buffers need two exchanges per transform");
     // the row's spectrum, held across the planes (spread pass), thread-major
     static constexpr int SP = WITH_INPUT ? 0 : ((SI::U * SI::RAD * RP::T + 1) & ~1);
-    static constexpr size_t bytes = (size_t)(XB + IN + 2 * HS + SP) * sizeof(float2) + 2 * sizeof(uint64_t);
-    // runs transform S on v through the exchange buffers at xb
-    template <class S, class V, class Out>
-    static __device__ __forceinline__ void run(V& v, float2* xb, const float2* __restrict__ tw, Out&& out) {
-        if constexpr (ALT) S::run2(v, xb, xb + XS, tw, out);
-        else S::run(v, xb, tw, out);
-    }
+    static constexpr size_t bytes = (size_t)(XS + IN + 2 * HS + SP) * sizeof(float2) + 2 * sizeof(uint64_t);
 };
 
 // If a bulk copy for plane l does not arrive within the bounded wait, the CTA
@@ -682,10 +626,9 @@ __global__ void k_wait_selftest(int* __restrict__ status) {
 }
 
 // out[b][c][i] = IDFT( sum_l Hsel_l * DFT(in[b][l][c][i]) )
-// (1920-point rows: three CTAs per SM fit the register file without spills
-// here, unlike the spread pass, and hide more of the row loads)
+// (the row plan's MINB caps the registers; shared memory sets the CTAs per SM)
 template <bool CONJ, class RP>
-__global__ void __launch_bounds__(RP::T, RP::N == 1920 ? 3 : RP::MINB)
+__global__ void __launch_bounds__(RP::T, RP::MINBS)
     k_rows_sum_reg(const float2* __restrict__ in, float2* __restrict__ out, int L, int C, int H,
                    const float2* __restrict__ hq, const float2* __restrict__ tw, int* __restrict__ status) {
     using namespace rfft;
@@ -695,7 +638,7 @@ __global__ void __launch_bounds__(RP::T, RP::N == 1920 ? 3 : RP::MINB)
     using SI = typename RP::template SB<true>;
     extern __shared__ __align__(16) float2 sm[];
     float2* xb = sm;
-    float2* rowb = sm + SM::XB;
+    float2* rowb = sm + SM::XS;
     float2* hb = rowb + SM::IN;
     uint64_t* bar = reinterpret_cast<uint64_t*>(hb + 2 * HS);
     const int b = blockIdx.x, i = blockIdx.y, c = blockIdx.z;
@@ -736,7 +679,7 @@ __global__ void __launch_bounds__(RP::T, RP::N == 1920 ? 3 : RP::MINB)
                 v[u][HCGS_CI(r)] = okj ? srow[j + HCGS_CI(r) * SF::M] : make_float2(0.f, 0.f);
             });
         });
-        SM::template run<SF>(v, xb, tw, [&](auto& vo) {
+        SF::run(v, xb, tw, [&](auto& vo) {
             static_assert(Shape<decltype(vo)>::R == SI::RAD && Shape<decltype(vo)>::U == SI::U,
                           "the inverse pass must start with the forward pass's last radix");
             sfor<SI::U>([&](auto a) {
@@ -759,14 +702,14 @@ __global__ void __launch_bounds__(RP::T, RP::N == 1920 ? 3 : RP::MINB)
         }
     }
     float2* dst = out + (((size_t)b * C + c) * H + i) * W;
-    SM::template run<SI>(acc, xb, tw, [&](auto& vo) {
+    SI::run(acc, xb, tw, [&](auto& vo) {
         for_outputs<W, 1, RP::T>(vo, [&](float2 x, int pos, int) { dst[pos] = x; });
     });
 }
 
 // out[b][l][c][i] = IDFT( Hsel_l * DFT(in[b][c][i]) )
 template <bool CONJ, class RP>
-__global__ void __launch_bounds__(RP::T, RP::N == 1920 ? 3 : RP::MINB)
+__global__ void __launch_bounds__(RP::T, RP::MINB)
     k_rows_spread_reg(const float2* __restrict__ in, float2* __restrict__ out, int L, int C, int H,
                       const float2* __restrict__ hq, const float2* __restrict__ tw, int* __restrict__ status) {
     using namespace rfft;
@@ -776,7 +719,7 @@ __global__ void __launch_bounds__(RP::T, RP::N == 1920 ? 3 : RP::MINB)
     using SI = typename RP::template SB<true>;
     extern __shared__ __align__(16) float2 sm[];
     float2* xb = sm;
-    float2* hb = sm + SM::XB;
+    float2* hb = sm + SM::XS;
     float2* sp = hb + 2 * HS;
     uint64_t* bar = reinterpret_cast<uint64_t*>(sp + SM::SP);
     const int b = blockIdx.x, i = blockIdx.y, c = blockIdx.z;
@@ -801,7 +744,7 @@ __global__ void __launch_bounds__(RP::T, RP::N == 1920 ? 3 : RP::MINB)
     {
         float2 v[SF::U][SF::RAD];
         load_row<SF>(v, in + (((size_t)b * C + c) * H + i) * W);
-        SM::template run<SF>(v, xb, tw, [&](auto& vo) {
+        SF::run(v, xb, tw, [&](auto& vo) {
             static_assert(Shape<decltype(vo)>::R == SI::RAD && Shape<decltype(vo)>::U == SI::U,
                           "the inverse pass must start with the forward pass's last radix");
             sfor<SI::U>([&](auto a) {
@@ -835,7 +778,7 @@ __global__ void __launch_bounds__(RP::T, RP::N == 1920 ? 3 : RP::MINB)
             issue(l + 2, buf);
         }
         float2* dst = out + ((((size_t)b * L + l) * C + c) * H + i) * W;
-        SM::template run<SI>(v, xb, tw, [&](auto& vo) {
+        SI::run(v, xb, tw, [&](auto& vo) {
             for_outputs<W, 1, RP::T>(vo, [&](float2 x, int pos, int) { dst[pos] = x; });
         });
     }
