@@ -86,6 +86,19 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32]) {
 #pragma unroll
     for (int j = 0; j < 32; j++) v[j] = __uint_as_float(r[j]);
 }
+// 64 consecutive FP32 columns of this thread's TMEM lane from taddr (one
+// round trip instead of two 32-column loads)
+__device__ __forceinline__ void tc_ld64(uint32_t taddr, float (&v)[64]) {
+    uint32_t r[64];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+        : "r"(taddr)
+        : "memory");
+    tc_wait_ld();
+#pragma unroll
+    for (int j = 0; j < 64; j++) v[j] = __uint_as_float(r[j]);
+}
 __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
     uint32_t r[16];
     asm volatile(
@@ -167,21 +180,21 @@ __device__ __forceinline__ bool wait_mma(uint64_t* bar, uint32_t& phase, int* st
 __device__ __forceinline__ void epi_hidden(uint32_t taddr, const float* b, uint8_t* H, int F, int r) {
     const __nv_bfloat162 zero = __floats2bfloat162_rn(0.f, 0.f);
 #pragma unroll 1
-    for (int c = 0; c < 4; c++) {
-        float v[32];
-        tc_ld32(taddr + 32 * c, v);
-        const float2* bb = reinterpret_cast<const float2*>(b + 32 * c);
-        uint32_t p[16];
+    for (int c = 0; c < 2; c++) {
+        float v[64];
+        tc_ld64(taddr + 64 * c, v);
+        const float2* bb = reinterpret_cast<const float2*>(b + 64 * c);
+        uint32_t p[32];
 #pragma unroll
-        for (int j = 0; j < 16; j++) {
+        for (int j = 0; j < 32; j++) {
             const float2 z = __fadd2_rn(make_float2(v[2 * j], v[2 * j + 1]), bb[j]);
             __nv_bfloat162 h = __floats2bfloat162_rn(z.x, z.y);
             h = __hmax2(h, zero);
             p[j] = *reinterpret_cast<const uint32_t*>(&h);
         }
 #pragma unroll
-        for (int q = 0; q < 4; q++)
-            *reinterpret_cast<uint4*>(H + cm_off(r, 32 * c + 8 * q, F)) =
+        for (int q = 0; q < 8; q++)
+            *reinterpret_cast<uint4*>(H + cm_off(r, 64 * c + 8 * q, F)) =
                 make_uint4(p[4 * q], p[4 * q + 1], p[4 * q + 2], p[4 * q + 3]);
     }
 }
@@ -191,12 +204,12 @@ __device__ __forceinline__ void epi_hidden(uint32_t taddr, const float* b, uint8
 __device__ __forceinline__ void epi_grad(uint32_t taddr, const uint8_t* Hl, int F, uint8_t* G, int r) {
     const __nv_bfloat162 zero = __floats2bfloat162_rn(0.f, 0.f);
 #pragma unroll 1
-    for (int c = 0; c < 4; c++) {
-        float v[32];
-        tc_ld32(taddr + 32 * c, v);
+    for (int c = 0; c < 2; c++) {
+        float v[64];
+        tc_ld64(taddr + 64 * c, v);
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const uint4 hw = *reinterpret_cast<const uint4*>(Hl + cm_off(r, 32 * c + 8 * q, F));
+        for (int q = 0; q < 8; q++) {
+            const uint4 hw = *reinterpret_cast<const uint4*>(Hl + cm_off(r, 64 * c + 8 * q, F));
             const uint32_t hv[4] = {hw.x, hw.y, hw.z, hw.w};
             uint32_t p[4];
 #pragma unroll
@@ -206,7 +219,7 @@ __device__ __forceinline__ void epi_grad(uint32_t taddr, const uint8_t* Hl, int 
                 const uint32_t m = __hgt2_mask(*reinterpret_cast<const __nv_bfloat162*>(&hv[k]), zero);
                 p[k] = *reinterpret_cast<const uint32_t*>(&d) & m;
             }
-            *reinterpret_cast<uint4*>(G + cm_off(r, 32 * c + 8 * q, MLP_HID)) = make_uint4(p[0], p[1], p[2], p[3]);
+            *reinterpret_cast<uint4*>(G + cm_off(r, 64 * c + 8 * q, MLP_HID)) = make_uint4(p[0], p[1], p[2], p[3]);
         }
     }
 }
