@@ -224,9 +224,12 @@ hcgs_status hcgs_profile_summary(hcgs_ctx* ctx, int max, int* n_out, const char*
 /* ---------------- step 1+2: projection, depth sort, tile binning ---------------- */
 /* Projects the N Gaussians for V views (Eq. gaussian_projection:
  * Sigma' = J W Sigma W^T J^T, mu = projection of the mean; Eq. hard_assignment
- * for the plane), culls (z < near_z), sorts by camera-space depth (ties by
- * index) and bins every Gaussian into the 16x16 tiles of its plane that its
- * support {p : o G(p) >= alpha_min} can touch.
+ * for the plane), culls (z < near_z), sorts by camera-space depth (the
+ * depth z of the mean formed in FP64 from the FP32 inputs and rounded once
+ * to FP32; equal keys by index) and bins every Gaussian into the 64x64-pixel
+ * buckets of its plane that the 16x16 tiles its support
+ * {p : o G(p) >= alpha_min} can touch lie in; the compositing tests the tile
+ * rectangle and the support again per 16x8 strip.
  *   viewmats   device [V][4][4] world -> camera, row-major
  *   intrinsics device [V][4]    (f_x, f_y, c_x, c_y) in pixels
  * The result lives in `saved` (must come from hcgs_saved_create). */
