@@ -27,7 +27,7 @@ __global__ void k_prep_w(const float* __restrict__ amp, const float* __restrict_
                          int N, int C, int* __restrict__ status) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N * C) return;
-    HCGS_DCHECK(status, isfinite(amp[i]) && isfinite(ph[i]));  // non-finite appearance (checked build)
+    (void)HCGS_DCHECK(status, isfinite(amp[i]) && isfinite(ph[i]));  // non-finite appearance (checked build)
     float s, c;
     sincosf(ph[i], &s, &c);
     w[i] = make_float2(amp[i] * c, amp[i] * s);
