@@ -3,9 +3,10 @@
 // accumulation on the fifth-generation tensor cores (tcgen05.mma, kind::f16,
 // accumulators in tensor memory), forward and reverse mode.
 //
-// One CTA of 128 threads (one warpgroup) per SM slot, persistent over tiles
-// of 128 rows; thread t owns row t of the tile in every epilogue (TMEM lane t
-// holds row t of an M = 128 accumulator).  The weights stay in shared memory
+// Persistent CTAs over tiles of 128 rows, one per SM: the forward runs four
+// warpgroups per CTA, each on its own tiles, the reverse mode one warpgroup;
+// thread t of a warpgroup owns row t of its tile in every epilogue (TMEM lane
+// t holds row t of an M = 128 accumulator).  The weights stay in shared memory
 // for the CTA's lifetime, in core-matrix form: 8 x 8 blocks of BF16 (8 rows,
 // 16 contiguous bytes each) that serve as K-major operands (features along K)
 // and, read through the other descriptor mode, as MN-major operands (features
@@ -172,29 +173,37 @@ __device__ __forceinline__ bool wait_mma(uint64_t* bar, uint32_t& phase, int* st
     return !bad;
 }
 
+// CH consecutive FP32 columns (32 or 64) of this thread's TMEM lane
+template <int CH>
+__device__ __forceinline__ void tc_ldn(uint32_t taddr, float (&v)[CH]) {
+    if constexpr (CH == 64) tc_ld64(taddr, v);
+    else tc_ld32(taddr, v);
+}
+
 // Hidden-layer epilogue of this thread's row: h = bf16(relu(z + b)) for the
-// 128 accumulator columns at taddr, written to the core-matrix buffer H (F
-// features per row) at row r.  The bias is added in packed FP32, the ReLU
-// taken on the rounded pair (rounding keeps the sign, so relu and rounding
-// commute).
+// 128 accumulator columns at taddr, read CH at a time, written to the
+// core-matrix buffer H (F features per row) at row r.  The bias is added in
+// packed FP32, the ReLU taken on the rounded pair (rounding keeps the sign,
+// so relu and rounding commute).
+template <int CH = 64>
 __device__ __forceinline__ void epi_hidden(uint32_t taddr, const float* b, uint8_t* H, int F, int r) {
     const __nv_bfloat162 zero = __floats2bfloat162_rn(0.f, 0.f);
 #pragma unroll 1
-    for (int c = 0; c < 2; c++) {
-        float v[64];
-        tc_ld64(taddr + 64 * c, v);
-        const float2* bb = reinterpret_cast<const float2*>(b + 64 * c);
-        uint32_t p[32];
+    for (int c = 0; c < 128 / CH; c++) {
+        float v[CH];
+        tc_ldn<CH>(taddr + CH * c, v);
+        const float2* bb = reinterpret_cast<const float2*>(b + CH * c);
+        uint32_t p[CH / 2];
 #pragma unroll
-        for (int j = 0; j < 32; j++) {
+        for (int j = 0; j < CH / 2; j++) {
             const float2 z = __fadd2_rn(make_float2(v[2 * j], v[2 * j + 1]), bb[j]);
             __nv_bfloat162 h = __floats2bfloat162_rn(z.x, z.y);
             h = __hmax2(h, zero);
             p[j] = *reinterpret_cast<const uint32_t*>(&h);
         }
 #pragma unroll
-        for (int q = 0; q < 8; q++)
-            *reinterpret_cast<uint4*>(H + cm_off(r, 64 * c + 8 * q, F)) =
+        for (int q = 0; q < CH / 8; q++)
+            *reinterpret_cast<uint4*>(H + cm_off(r, CH * c + 8 * q, F)) =
                 make_uint4(p[4 * q], p[4 * q + 1], p[4 * q + 2], p[4 * q + 3]);
     }
 }
@@ -232,22 +241,68 @@ struct MlpW {
 // ---------------------------------------------------------------------------
 // forward: y = W4 relu(W3 relu(W2 relu(W1 x + b1) + b2) + b3) + b4
 // ---------------------------------------------------------------------------
-// shared memory (bytes): W1 [128][16], W2, W3 [128][128], W4 [16][128], the
-// X tile [128][16], one hidden tile [128][128] (reused by every layer), biases
+// One CTA of F_WG warpgroups per SM.  The weights and biases are staged once
+// per CTA and shared; each warpgroup runs its own stream of 128-row tiles
+// with its own X and H tiles in shared memory, its own 128 TMEM columns
+// (hidden accumulator; the 16 output columns reuse the first 16 of them once
+// the last hidden epilogue has read them), its own mbarrier and its own named
+// barrier.  While one warpgroup reads back and rounds an accumulator, the
+// tensor cores run the MMAs the other warpgroups have issued, so the MMAs of
+// a tile no longer wait for their own epilogues alone.
+//
+// shared memory (bytes): W1 [128][16], W2, W3 [128][128], W4 [16][128],
+// biases, then per warpgroup the X tile [128][16] and the hidden tile
+// [128][128] (reused by every layer), then the mbarriers and the TMEM slot.
+constexpr int F_WG = 4;
+constexpr int F_EPI = 32;  // accumulator columns per tcgen05.ld in the forward's epilogues
 constexpr uint32_t FS_W1 = 0, FS_W2 = FS_W1 + 128 * 16 * 2, FS_W3 = FS_W2 + 128 * 128 * 2,
-                   FS_W4 = FS_W3 + 128 * 128 * 2, FS_X = FS_W4 + 16 * 128 * 2, FS_H = FS_X + 128 * 16 * 2,
-                   FS_B = FS_H + 128 * 128 * 2, FS_BAR = FS_B + (3 * 128 + 16) * 4, FS_END = FS_BAR + 16;
-constexpr uint32_t F_TMEM_COLS = 256;  // [0, 128) hidden accumulator, [128, 144) output
+                   FS_W4 = FS_W3 + 128 * 128 * 2, FS_B = FS_W4 + 16 * 128 * 2,
+                   FS_TILES = (FS_B + (3 * 128 + 16) * 4 + 1023) & ~1023u, FS_X = 0, FS_H = 128 * 16 * 2,
+                   FS_WG = FS_H + 128 * 128 * 2, FS_BAR = FS_TILES + F_WG * FS_WG, FS_END = FS_BAR + 8 * F_WG + 16;
+static_assert(FS_END <= 232448, "forward shared memory above the per-CTA limit");
+constexpr uint32_t F_TMEM_COLS = 512;  // all of the SM's TMEM (one CTA per SM), 128 columns per warpgroup
+static_assert(128 * F_WG <= F_TMEM_COLS, "forward TMEM above the per-SM 512 columns");
 
-__global__ void __launch_bounds__(128, 2) k_mlp_fwd(MlpW w, const uint16_t* __restrict__ x, int N,
-                                                    float* __restrict__ y, int* __restrict__ status) {
+// Named barrier of one warpgroup (id 1 + warpgroup; 0 is the CTA barrier).
+__device__ __forceinline__ void wg_bar(int id) { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
+// Named-barrier OR over the warpgroup's 128 threads.
+__device__ __forceinline__ bool wg_bar_or(int id, bool p) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred a, b;\n setp.ne.u32 a, %1, 0;\n bar.red.or.pred b, %2, 128, a;\n selp.u32 %0, 1, 0, b;\n}\n"
+        : "=r"(r)
+        : "r"((uint32_t)p), "r"(id)
+        : "memory");
+    return r != 0;
+}
+// sync_for_mma / wait_mma for one warpgroup
+__device__ __forceinline__ void wg_sync_for_mma(int id) {
+    fence_proxy_async_smem();
+    tc_fence_before();
+    wg_bar(id);
+    tc_fence_after();
+}
+__device__ __forceinline__ bool wg_wait_mma(uint64_t* bar, uint32_t& phase, int* status, int id) {
+    const bool ok = mbar_wait(bar, phase);
+    phase ^= 1u;
+    const bool bad = wg_bar_or(id, !ok);
+    if (bad && (threadIdx.x & 127) == 0) atomicOr(status, STATUS_WAIT_TIMEOUT);
+    tc_fence_after();
+    return !bad;
+}
+
+__global__ void __launch_bounds__(128 * F_WG, 1) k_mlp_fwd(MlpW w, const uint16_t* __restrict__ x, int N,
+                                                         float* __restrict__ y, int* __restrict__ status) {
     extern __shared__ __align__(1024) uint8_t sm[];
-    const int tid = threadIdx.x, warp = tid >> 5;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + FS_BAR);
-    uint32_t* slot = reinterpret_cast<uint32_t*>(sm + FS_BAR + 8);
+    const int wg = threadIdx.x >> 7, t = threadIdx.x & 127, warp = threadIdx.x >> 5;
+    const int bid = 1 + wg;  // this warpgroup's named barrier
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + FS_BAR) + wg;
+    uint32_t* slot = reinterpret_cast<uint32_t*>(sm + FS_BAR + 8 * F_WG);
     float* sb = reinterpret_cast<float*>(sm + FS_B);
+    uint8_t* sx = sm + FS_TILES + wg * FS_WG + FS_X;
+    uint8_t* sh = sm + FS_TILES + wg * FS_WG + FS_H;
     if (warp == 0) tc_alloc(slot, F_TMEM_COLS);
-    if (tid == 0) {
+    if (t == 0) {
         mbar_init(bar, 1);
         mbar_init_fence();
     }
@@ -255,66 +310,65 @@ __global__ void __launch_bounds__(128, 2) k_mlp_fwd(MlpW w, const uint16_t* __re
     load_cm(sm + FS_W2, w.W2, MLP_HID, MLP_HID);
     load_cm(sm + FS_W3, w.W3, MLP_HID, MLP_HID);
     load_cm(sm + FS_W4, w.W4, MLP_OUT, MLP_HID);
-    sb[tid] = w.b1[tid];
-    sb[128 + tid] = w.b2[tid];
-    sb[256 + tid] = w.b3[tid];
-    if (tid < MLP_OUT) sb[384 + tid] = w.b4[tid];
+    for (int i = threadIdx.x; i < 3 * MLP_HID + MLP_OUT; i += blockDim.x)
+        sb[i] = i < 128 ? w.b1[i] : i < 256 ? w.b2[i - 128] : i < 384 ? w.b3[i - 256] : w.b4[i - 384];
     sync_for_mma();
-    const uint32_t tm = *slot;
-    const uint32_t tl = tm + ((uint32_t)(warp * 32) << 16);  // this warp's TMEM lanes
-    const uint32_t sa = smem_addr(sm);
+    const uint32_t tm = *slot + 128u * (uint32_t)wg;                 // this warpgroup's columns
+    const uint32_t tl = tm + ((uint32_t)((warp & 3) * 32) << 16);   // this warp's TMEM lanes
+    const uint32_t sa = smem_addr(sm), sxa = smem_addr(sx), sha = smem_addr(sh);
     constexpr uint32_t ID_H = tc_idesc(128, 128, 0, 0), ID_O = tc_idesc(128, 16, 0, 0);
     uint32_t phase = 0;
     const int ntiles = (N + 127) / 128;
-    // this thread's input row of tile t (zeros past N)
-    auto load_x = [&](int t, uint4& x0, uint4& x1) {
-        const int rr = t * 128 + tid;
+    const int first = blockIdx.x * F_WG + wg, stride = gridDim.x * F_WG;
+    // this thread's input row of tile i (zeros past N)
+    auto load_x = [&](int i, uint4& x0, uint4& x1) {
+        const int rr = i * 128 + t;
         x0 = make_uint4(0, 0, 0, 0);
         x1 = x0;
-        if (t < ntiles && rr < N) {
+        if (i < ntiles && rr < N) {
             const uint4* xr = reinterpret_cast<const uint4*>(x + (size_t)rr * MLP_IN);
             x0 = __ldg(xr);
             x1 = __ldg(xr + 1);
         }
     };
     uint4 nx0, nx1;  // the next tile's row, loaded one tile ahead
-    load_x(blockIdx.x, nx0, nx1);
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int row = t * 128 + tid;
-        *reinterpret_cast<uint4*>(sm + FS_X + cm_off(tid, 0, MLP_IN)) = nx0;
-        *reinterpret_cast<uint4*>(sm + FS_X + cm_off(tid, 8, MLP_IN)) = nx1;
-        load_x(t + gridDim.x, nx0, nx1);
-        sync_for_mma();
-        if (tid == 0) {
-            tc_mma(tm, op_k(sa + FS_X, MLP_IN, 0), op_k(sa + FS_W1, MLP_IN, 0), ID_H, 0);
+    load_x(first, nx0, nx1);
+    for (int i = first; i < ntiles; i += stride) {
+        const int row = i * 128 + t;
+        *reinterpret_cast<uint4*>(sx + cm_off(t, 0, MLP_IN)) = nx0;
+        *reinterpret_cast<uint4*>(sx + cm_off(t, 8, MLP_IN)) = nx1;
+        load_x(i + stride, nx0, nx1);
+        wg_sync_for_mma(bid);
+        if (t == 0) {
+            tc_mma(tm, op_k(sxa, MLP_IN, 0), op_k(sa + FS_W1, MLP_IN, 0), ID_H, 0);
             tc_commit(bar);
         }
-        if (!wait_mma(bar, phase, status)) break;
-        epi_hidden(tl, sb, sm + FS_H, MLP_HID, tid);
+        if (!wg_wait_mma(bar, phase, status, bid)) break;
+        epi_hidden<F_EPI>(tl, sb, sh, MLP_HID, t);
         bool ok = true;
 #pragma unroll 1
         for (int layer = 0; layer < 2 && ok; layer++) {
             const uint32_t Wl = layer == 0 ? FS_W2 : FS_W3;
-            sync_for_mma();
-            if (tid == 0) {
+            wg_sync_for_mma(bid);
+            if (t == 0) {
 #pragma unroll
-                for (int s = 0; s < 8; s++) tc_mma(tm, op_k(sa + FS_H, MLP_HID, s), op_k(sa + Wl, MLP_HID, s), ID_H, s);
+                for (int s = 0; s < 8; s++) tc_mma(tm, op_k(sha, MLP_HID, s), op_k(sa + Wl, MLP_HID, s), ID_H, s);
                 tc_commit(bar);
             }
-            ok = wait_mma(bar, phase, status);
-            if (ok) epi_hidden(tl, sb + 128 * (layer + 1), sm + FS_H, MLP_HID, tid);
+            ok = wg_wait_mma(bar, phase, status, bid);
+            if (ok) epi_hidden<F_EPI>(tl, sb + 128 * (layer + 1), sh, MLP_HID, t);
         }
         if (!ok) break;
-        sync_for_mma();
-        if (tid == 0) {
+        // output layer into the first 16 columns (the last epilogue has read them)
+        wg_sync_for_mma(bid);
+        if (t == 0) {
 #pragma unroll
-            for (int s = 0; s < 8; s++)
-                tc_mma(tm + 128, op_k(sa + FS_H, MLP_HID, s), op_k(sa + FS_W4, MLP_HID, s), ID_O, s);
+            for (int s = 0; s < 8; s++) tc_mma(tm, op_k(sha, MLP_HID, s), op_k(sa + FS_W4, MLP_HID, s), ID_O, s);
             tc_commit(bar);
         }
-        if (!wait_mma(bar, phase, status)) break;
+        if (!wg_wait_mma(bar, phase, status, bid)) break;
         float o[16];
-        tc_ld16(tl + 128, o);
+        tc_ld16(tl, o);
         if (row < N) {
             float4* yr = reinterpret_cast<float4*>(y + (size_t)row * MLP_OUT);
 #pragma unroll
@@ -325,7 +379,7 @@ __global__ void __launch_bounds__(128, 2) k_mlp_fwd(MlpW w, const uint16_t* __re
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tc_dealloc(tm, F_TMEM_COLS);
+    if (warp == 0) tc_dealloc(*slot, F_TMEM_COLS);
 }
 
 // ---------------------------------------------------------------------------
@@ -614,9 +668,11 @@ static int sm_count(hcgs_ctx* ctx) {
 hcgs_status mlp_fwd(hcgs_ctx* ctx, const uint16_t* x, int N, const uint16_t* const* W, const float* const* b,
                     float* y, cudaStream_t st) {
     const int tiles = (N + 127) / 128;
-    const int grid = tiles < 2 * sm_count(ctx) ? tiles : 2 * sm_count(ctx);  // two CTAs per SM
+    const int wgs = (tiles + F_WG - 1) / F_WG;  // CTAs that have a tile for every warpgroup
+    const int grid = wgs < sm_count(ctx) ? wgs : sm_count(ctx);  // one CTA per SM
     HCGS_CUDA(ctx, cudaFuncSetAttribute(k_mlp_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FS_END));
-    HCGS_KERNEL(ctx, "k_mlp_fwd", st, k_mlp_fwd<<<grid, 128, FS_END, st>>>(make_w(W, b), x, N, y, ctx->d_status));
+    HCGS_KERNEL(ctx, "k_mlp_fwd", st,
+                k_mlp_fwd<<<grid, 128 * F_WG, FS_END, st>>>(make_w(W, b), x, N, y, ctx->d_status));
     return HCGS_OK;
 }
 
