@@ -4,7 +4,8 @@ and differentiated in one batch, at 1M Gaussians (the bench workload; FP32
 path, FP16x2 and BF16x2 footprint tiers) and at 2M Gaussians (configuration
 c4; FP32 path and FP16x2 tier), so that the instance buffers sized from the
 device's instance count and the strip lists are exercised at the largest
-configuration.
+configuration; and the training configuration's render (c3: one view of
+512 x 512, three wavelengths, 8 planes, 500k Gaussians; all three tiers).
 
 The FP64 oracle cannot composite 16 full views in a test's time, so the
 outputs are sampled where it can compute them exactly:
@@ -28,13 +29,15 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-V0, R0, R1 = 5, 480, 576  # sampled view and row band
 # relative L2 bounds (fields, gradients): 1e-4 / 1e-3 for the FP32 path
 # (gradients are sums of many FP32 terms accumulated by atomics), 1e-2 for
 # both reduced-precision tiers
 TOL = {0: (1e-4, 1e-3), 1: (1e-2, 1e-2), 2: (1e-2, 1e-2)}
-WORKLOADS = {"1080p_rgb_L12_N1M_V16": (0, 1, 2), "c4_1080p_L12_N2M_V16": (0, 1)}
-CASES = [(w, fp) for w, tiers in WORKLOADS.items() for fp in tiers]
+# workload: (footprint tiers, sampled view, row band)
+WORKLOADS = {"1080p_rgb_L12_N1M_V16": ((0, 1, 2), 5, 480, 576),
+             "c4_1080p_L12_N2M_V16": ((0, 1), 5, 480, 576),
+             "c3_512_L8_N500k": ((0, 1, 2), 0, 224, 288)}
+CASES = [(w, fp) for w, spec in WORKLOADS.items() for fp in spec[0]]
 
 
 @pytest.fixture(scope="module")
@@ -53,6 +56,7 @@ def _case(P, name):
     if name in _CASES:
         return _CASES[name]
     _CASES.clear()
+    _, V0, R0, R1 = WORKLOADS[name]
     wl = S.workload(name)
     o = wl.optics
     g = S.make_gaussians(wl.N, o.L, o.C, o.H, o.W, seed=0)
@@ -74,7 +78,7 @@ def _case(P, name):
     bb = pr["bbox"]  # x0, x1, y0, y1 of the support ellipse
     sel = (pr["valid"] == 1) & np.all(np.isfinite(bb), axis=1) & (bb[:, 1] > bb[:, 0]) & (bb[:, 3] > bb[:, 2])
     sel &= (bb[:, 1] >= 0) & (bb[:, 0] < o.W - 1) & (bb[:, 2] >= R0) & (bb[:, 3] <= R1 - 1)
-    _CASES[name] = dict(wl=wl, o=o, g=g, vm=vm, it=it, gP=gP, band=band, go=go, sel=sel)
+    _CASES[name] = dict(wl=wl, o=o, g=g, vm=vm, it=it, gP=gP, band=band, go=go, sel=sel, V0=V0, R0=R0, R1=R1)
     return _CASES[name]
 
 
@@ -82,6 +86,7 @@ def _case(P, name):
 def test_full_size_sampled_parity(P, workload, footprint):
     case = _case(P, workload)
     wl, o = case["wl"], case["o"]
+    V0, R0, R1 = case["V0"], case["R0"], case["R1"]
     opts = dict(P.DEFAULT_OPTS, footprint=footprint)
     ctx = P.Context(0)
     gd = dev(case["g"])
