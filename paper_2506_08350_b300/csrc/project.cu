@@ -264,7 +264,7 @@ __global__ void k_bucket_bounds(const uint32_t* __restrict__ key, uint32_t M, ui
 // whole array when the input is already grouped by segment.
 // ---------------------------------------------------------------------------
 constexpr int RS_THREADS = 256;
-constexpr int RS_IPT = 8;
+constexpr int RS_IPT = 16;
 constexpr int RS_KPB = RS_THREADS * RS_IPT;
 
 struct RsSeg {
