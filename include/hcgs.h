@@ -354,6 +354,22 @@ hcgs_status hcgs_adan_step(hcgs_ctx* ctx, float* p, const float* g, float* g_pre
  * m^ = m/(1-b1^step), v^ = v/(1-b2^step).  All arrays device [n]. */
 hcgs_status hcgs_adam_step(hcgs_ctx* ctx, float* p, const float* g, float* m, float* v, int64_t n,
                            int step, float lr, float beta1, float beta2, float eps, void* stream);
+/* hcgs_adam_step on k parameter arrays in one launch (0 <= k <= 16): array a
+ * is p[a], g[a], m[a], v[a] (device [count[a]] float) with learning rate
+ * lr[a]; the pointer tables p, g, m, v and count, lr are host [k] arrays,
+ * read during the call.  Each element is updated exactly as by
+ * hcgs_adam_step.  The arrays must not overlap.  Errors as hcgs_adam_step;
+ * k outside [0, 16] -> HCGS_ERR_INVALID_ARG. */
+hcgs_status hcgs_adam_step_multi(hcgs_ctx* ctx, int k, float* const* p, const float* const* g, float* const* m,
+                                 float* const* v, const int64_t* count, const float* lr, int step, float beta1,
+                                 float beta2, float eps, void* stream);
+/* hcgs_adan_step on k parameter arrays in one launch (0 <= k <= 16), tables
+ * as in hcgs_adam_step_multi (g_prev, n: the Adan state of each array);
+ * each element is updated exactly as by hcgs_adan_step with lr[a]. */
+hcgs_status hcgs_adan_step_multi(hcgs_ctx* ctx, int k, float* const* p, const float* const* g, float* const* g_prev,
+                                 float* const* m, float* const* v, float* const* n, const int64_t* count,
+                                 const float* lr, int step, float beta1, float beta2, float beta3, float eps,
+                                 float weight_decay, void* stream);
 
 /* ---------------- learned initialisation network (no counterpart in the paper) ---------------- */
 /* 4-layer ReLU MLP, width 128, BF16 operands with FP32 accumulation:

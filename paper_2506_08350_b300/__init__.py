@@ -44,7 +44,8 @@ EXPORTS = ("hcgs_ctx_create", "hcgs_ctx_destroy", "hcgs_status_string", "hcgs_la
            "hcgs_selftest_wait_timeout", "hcgs_paper_loss", "hcgs_paper_loss_intensities", "hcgs_adan_step",
            "hcgs_densify_accumulate", "hcgs_densify_plan", "hcgs_densify_apply", "hcgs_philox",
            "hcgs_phase_only_loss", "hcgs_hologram_phase", "hcgs_phase_hologram", "hcgs_scale",
-           "hcgs_is_checked_build", "hcgs_check_status", "hcgs_selftest_device_check")
+           "hcgs_is_checked_build", "hcgs_check_status", "hcgs_selftest_device_check",
+           "hcgs_adam_step_multi", "hcgs_adan_step_multi")
 
 
 class HcgsError(RuntimeError):
@@ -131,6 +132,11 @@ _sig("hcgs_paper_loss", [_P, _P, _P, _P, c_int, POINTER(_Optics), c_float, _P, _
 _sig("hcgs_paper_loss_intensities", [_P, _P, _P, _P, c_int, c_int, c_int, c_int, c_int, c_float, _P, _P, _P])
 _sig("hcgs_adan_step", [_P, _P, _P, _P, _P, _P, _P, c_int64, c_int, c_float, c_float, c_float, c_float, c_float,
                         c_float, _P])
+_PP = POINTER(c_void_p)
+_sig("hcgs_adam_step_multi", [_P, c_int, _PP, _PP, _PP, _PP, POINTER(c_int64), POINTER(c_float), c_int, c_float,
+                              c_float, c_float, _P])
+_sig("hcgs_adan_step_multi", [_P, c_int, _PP, _PP, _PP, _PP, _PP, _PP, POINTER(c_int64), POINTER(c_float), c_int,
+                              c_float, c_float, c_float, c_float, c_float, _P])
 _sig("hcgs_mlp_forward", [_P, _P, c_int] + [_P] * 8 + [_P, _P])
 _sig("hcgs_asm_propagate_noalloc", [_P, c_int, POINTER(_Optics), _P, _P])
 _sig("hcgs_mlp_mse_loss", [_P, _P, _P, c_int, c_int, _P, _P, _P])
@@ -152,6 +158,11 @@ PARAM_NAMES = ("means", "log_scales", "quats", "opacity_logits", "amplitude", "p
 DEFAULT_OPTS = dict(tile=16, alpha_min=1.0 / 255.0, alpha_max=0.99, T_eps=1e-4, cov2d_dilation=0.3,
                     near_z=0.2, clip_factor=1.3, ste_tau=1e-3, order=0, footprint=0, rho_grad=0)
 EXACT_OPTS = dict(DEFAULT_OPTS, alpha_min=0.0, alpha_max=1.0, T_eps=0.0, cov2d_dilation=0.0, clip_factor=0.0)
+
+
+def _ptrs(ts):
+    """A host array of the device pointers of a list of tensors."""
+    return (c_void_p * len(ts))(*[_ptr(t) for t in ts])
 
 
 def _ptr(t):
@@ -342,6 +353,24 @@ class Context:
     def adam_step(self, p, g, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
         self._check(_lib.hcgs_adam_step(self.handle, _ptr(p), _ptr(g), _ptr(m), _ptr(v), p.numel(), int(step),
                                         float(lr), float(beta1), float(beta2), float(eps), _stream()))
+
+    def adam_step_multi(self, ps, gs, ms, vs, step, lrs, beta1=0.9, beta2=0.999, eps=1e-8):
+        """adam_step on several parameter arrays (lists of equal length) in one launch."""
+        k = len(ps)
+        self._check(_lib.hcgs_adam_step_multi(self.handle, k, _ptrs(ps), _ptrs(gs), _ptrs(ms), _ptrs(vs),
+                                              (c_int64 * k)(*[t.numel() for t in ps]),
+                                              (c_float * k)(*[float(x) for x in lrs]), int(step), float(beta1),
+                                              float(beta2), float(eps), _stream()))
+
+    def adan_step_multi(self, ps, gs, g_prevs, ms, vs, ns, step, lrs, beta1=0.9, beta2=0.92, beta3=0.99,
+                        eps=1e-8, weight_decay=0.0):
+        """adan_step on several parameter arrays (lists of equal length) in one launch."""
+        k = len(ps)
+        self._check(_lib.hcgs_adan_step_multi(self.handle, k, _ptrs(ps), _ptrs(gs), _ptrs(g_prevs), _ptrs(ms),
+                                              _ptrs(vs), _ptrs(ns), (c_int64 * k)(*[t.numel() for t in ps]),
+                                              (c_float * k)(*[float(x) for x in lrs]), int(step), float(beta1),
+                                              float(beta2), float(beta3), float(eps), float(weight_decay),
+                                              _stream()))
 
     def phase_only_loss(self, U_target, phase, B, optics, loss, g_phase=None, lambda_ssim=SSIM_LAMBDA):
         self._check(_lib.hcgs_phase_only_loss(self.handle, _ptr(U_target), _ptr(phase), int(B),

@@ -895,6 +895,53 @@ hcgs_status hcgs_adam_step(hcgs_ctx* ctx, float* p, const float* g, float* m, fl
     return adam(ctx, p, g, m, v, n, step, lr, beta1, beta2, eps, S(stream));
 }
 
+hcgs_status hcgs_adam_step_multi(hcgs_ctx* ctx, int k, float* const* p, const float* const* g, float* const* m,
+                                 float* const* v, const int64_t* count, const float* lr, int step, float beta1,
+                                 float beta2, float eps, void* stream) {
+    if (!ctx) return HCGS_ERR_INVALID_ARG;
+    REQUIRE(ctx, k >= 0 && k <= OPT_MAX, "k must be in [0, 16]");
+    if (k == 0) return HCGS_OK;
+    REQUIRE(ctx, p && g && m && v && count && lr, "NULL argument");
+    REQUIRE(ctx, step >= 1, "step counts from 1");
+    REQUIRE(ctx, beta1 >= 0.f && beta1 < 1.f && beta2 >= 0.f && beta2 < 1.f && eps >= 0.f, "bad Adam constants");
+    OptArrays A{};
+    A.k = k;
+    for (int a = 0; a < k; a++) {
+        REQUIRE(ctx, count[a] >= 0, "count must be >= 0");
+        REQUIRE(ctx, count[a] == 0 || (p[a] && g[a] && m[a] && v[a]), "NULL array");
+        A.p[a] = p[a]; A.g[a] = g[a]; A.m[a] = m[a]; A.v[a] = v[a];
+        A.count[a] = count[a];
+        A.lr[a] = lr[a];
+    }
+    cudaSetDevice(ctx->device);
+    return adam_multi(ctx, A, step, beta1, beta2, eps, S(stream));
+}
+
+hcgs_status hcgs_adan_step_multi(hcgs_ctx* ctx, int k, float* const* p, const float* const* g, float* const* g_prev,
+                                 float* const* m, float* const* v, float* const* n, const int64_t* count,
+                                 const float* lr, int step, float beta1, float beta2, float beta3, float eps,
+                                 float weight_decay, void* stream) {
+    if (!ctx) return HCGS_ERR_INVALID_ARG;
+    REQUIRE(ctx, k >= 0 && k <= OPT_MAX, "k must be in [0, 16]");
+    if (k == 0) return HCGS_OK;
+    REQUIRE(ctx, p && g && g_prev && m && v && n && count && lr, "NULL argument");
+    REQUIRE(ctx, step >= 1, "step counts from 1");
+    REQUIRE(ctx, beta1 >= 0.f && beta1 < 1.f && beta2 >= 0.f && beta2 < 1.f && beta3 >= 0.f && beta3 < 1.f &&
+                     eps >= 0.f && weight_decay >= 0.f,
+            "bad Adan constants");
+    OptArrays A{};
+    A.k = k;
+    for (int a = 0; a < k; a++) {
+        REQUIRE(ctx, count[a] >= 0, "count must be >= 0");
+        REQUIRE(ctx, count[a] == 0 || (p[a] && g[a] && g_prev[a] && m[a] && v[a] && n[a]), "NULL array");
+        A.p[a] = p[a]; A.g[a] = g[a]; A.gp[a] = g_prev[a]; A.m[a] = m[a]; A.v[a] = v[a]; A.n[a] = n[a];
+        A.count[a] = count[a];
+        A.lr[a] = lr[a];
+    }
+    cudaSetDevice(ctx->device);
+    return adan_multi(ctx, A, step, beta1, beta2, beta3, eps, weight_decay, S(stream));
+}
+
 hcgs_status hcgs_mlp_forward(hcgs_ctx* ctx, const uint16_t* x, int N, const uint16_t* W1, const uint16_t* W2,
                              const uint16_t* W3, const uint16_t* W4, const float* b1, const float* b2,
                              const float* b3, const float* b4, float* y, void* stream) {

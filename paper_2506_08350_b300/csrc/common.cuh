@@ -271,6 +271,23 @@ hcgs_status exclusive_scan(hcgs_ctx* ctx, hcgs_saved* s, const uint32_t* in, uin
 // ---- training pieces (train.cu) ----
 hcgs_status adam(hcgs_ctx* ctx, float* p, const float* g, float* m, float* v, int64_t n, int step, float lr,
                  float b1, float b2, float eps, cudaStream_t st);
+// Up to OPT_MAX parameter arrays updated by one optimiser launch (the unused
+// pointers of an array are NULL: gp and n for Adam).
+constexpr int OPT_MAX = 16, OPT_THREADS = 256, OPT_EPB = 4 * OPT_THREADS;
+struct OptArrays {
+    float* p[OPT_MAX];
+    const float* g[OPT_MAX];
+    float* m[OPT_MAX];
+    float* v[OPT_MAX];
+    float* gp[OPT_MAX];
+    float* n[OPT_MAX];
+    int64_t count[OPT_MAX];
+    float lr[OPT_MAX];
+    int64_t first[OPT_MAX + 1];  // first block of each array (filled by opt_blocks)
+    int k;
+};
+int64_t opt_blocks(OptArrays& A);
+hcgs_status adam_multi(hcgs_ctx* ctx, OptArrays& A, int step, float b1, float b2, float eps, cudaStream_t st);
 hcgs_status reduce_sum(hcgs_ctx* ctx, const float* partials, int n, float scale, float* out, cudaStream_t st);
 hcgs_status mlp_fwd(hcgs_ctx* ctx, const uint16_t* x, int N, const uint16_t* const* W, const float* const* b,
                     float* y, cudaStream_t st);
@@ -307,5 +324,7 @@ hcgs_status focal_field(hcgs_ctx* ctx, float2* V, const float* Igt, float* Iout,
                         cudaStream_t st);
 hcgs_status adan(hcgs_ctx* ctx, float* p, const float* g, float* gp, float* m, float* v, float* n, int64_t count,
                  int step, float lr, float b1, float b2, float b3, float eps, float wd, cudaStream_t st);
+hcgs_status adan_multi(hcgs_ctx* ctx, OptArrays& A, int step, float b1, float b2, float b3, float eps, float wd,
+                       cudaStream_t st);
 
 }  // namespace hcgs

@@ -659,31 +659,62 @@ hcgs_status phase_of(hcgs_ctx* ctx, const float2* P, float* phi, int64_t n, cuda
 //   n <- b3 n + (1 - b3)(g + b2 (g - g_prev))^2;
 // p <- (p - lr (m + b2 v) / (sqrt(n) + eps)) / (1 + wd lr); g_prev <- g.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void adan_elem(float* __restrict__ p, const float* __restrict__ g,
+                                          float* __restrict__ gp, float* __restrict__ m, float* __restrict__ v,
+                                          float* __restrict__ nn, int64_t i, int step, float lr, float b1,
+                                          float b2, float b3, float eps, float shrink) {
+    const float gi = g[i];
+    float mi, vi, ni;
+    if (step == 1) {
+        mi = gi;
+        vi = 0.f;
+        ni = gi * gi;
+    } else {
+        const float dg = gi - gp[i];
+        mi = fmaf(b1, m[i], (1.f - b1) * gi);
+        vi = step == 2 ? dg : fmaf(b2, v[i], (1.f - b2) * dg);
+        const float u = fmaf(b2, dg, gi);
+        ni = fmaf(b3, nn[i], (1.f - b3) * u * u);
+    }
+    m[i] = mi;
+    v[i] = vi;
+    nn[i] = ni;
+    gp[i] = gi;
+    p[i] = (p[i] - lr * fmaf(b2, vi, mi) / (sqrtf(ni) + eps)) * shrink;
+}
+
 __global__ void k_adan(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ gp,
                        float* __restrict__ m, float* __restrict__ v, float* __restrict__ nn, int64_t count,
                        int step, float lr, float b1, float b2, float b3, float eps, float wd) {
     const float shrink = 1.f / (1.f + wd * lr);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const float gi = g[i];
-        float mi, vi, ni;
-        if (step == 1) {
-            mi = gi;
-            vi = 0.f;
-            ni = gi * gi;
-        } else {
-            const float dg = gi - gp[i];
-            mi = fmaf(b1, m[i], (1.f - b1) * gi);
-            vi = step == 2 ? dg : fmaf(b2, v[i], (1.f - b2) * dg);
-            const float u = fmaf(b2, dg, gi);
-            ni = fmaf(b3, nn[i], (1.f - b3) * u * u);
-        }
-        m[i] = mi;
-        v[i] = vi;
-        nn[i] = ni;
-        gp[i] = gi;
-        p[i] = (p[i] - lr * fmaf(b2, vi, mi) / (sqrtf(ni) + eps)) * shrink;
+         i += (int64_t)gridDim.x * blockDim.x)
+        adan_elem(p, g, gp, m, v, nn, i, step, lr, b1, b2, b3, eps, shrink);
+}
+
+// Several parameter arrays in one launch (block layout as k_adam_multi; the
+// arithmetic is adan_elem's, so the result equals one k_adan per array).
+__global__ void __launch_bounds__(OPT_THREADS) k_adan_multi(OptArrays A, int step, float b1, float b2, float b3,
+                                                            float eps, float wd) {
+    int a = 0;
+    while (a + 1 < A.k && (int64_t)blockIdx.x >= A.first[a + 1]) a++;
+    const float lr = A.lr[a];
+    const float shrink = 1.f / (1.f + wd * lr);
+    const int64_t base = ((int64_t)blockIdx.x - A.first[a]) * OPT_EPB;
+    for (int e = threadIdx.x; e < OPT_EPB; e += OPT_THREADS) {
+        const int64_t i = base + e;
+        if (i < A.count[a])
+            adan_elem(A.p[a], A.g[a], A.gp[a], A.m[a], A.v[a], A.n[a], i, step, lr, b1, b2, b3, eps, shrink);
     }
+}
+
+hcgs_status adan_multi(hcgs_ctx* ctx, OptArrays& A, int step, float b1, float b2, float b3, float eps, float wd,
+                       cudaStream_t st) {
+    const int64_t blocks = opt_blocks(A);
+    if (blocks == 0) return HCGS_OK;
+    HCGS_KERNEL(ctx, "k_adan", st,
+                k_adan_multi<<<(unsigned)blocks, OPT_THREADS, 0, st>>>(A, step, b1, b2, b3, eps, wd));
+    return HCGS_OK;
 }
 
 hcgs_status adan(hcgs_ctx* ctx, float* p, const float* g, float* gp, float* m, float* v, float* n, int64_t count,

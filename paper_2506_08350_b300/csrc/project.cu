@@ -443,33 +443,28 @@ __global__ void k_scan_reduce(const uint32_t* __restrict__ in, size_t n, uint32_
     if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
 }
 
-// single block: exclusive scan of nb block sums; 64-bit total to *total64
-__global__ void k_scan_top(uint32_t* __restrict__ bsum, int nb, unsigned long long* __restrict__ total64) {
-    const int per = (nb + SC_THREADS - 1) / SC_THREADS;
-    const int beg = threadIdx.x * per;
-    unsigned long long s = 0;
-    for (int k = 0; k < per; k++)
-        if (beg + k < nb) s += bsum[beg + k];
-    __shared__ uint32_t tot;
-    const uint32_t ex = block_exclusive_scan((uint32_t)s, &tot);
-    uint32_t run = ex;
-    for (int k = 0; k < per; k++)
-        if (beg + k < nb) {
-            const uint32_t c = bsum[beg + k];
-            bsum[beg + k] = run;
-            run += c;
-        }
-    // 64-bit total for overflow detection
-    __shared__ unsigned long long t64;
-    if (threadIdx.x == 0) t64 = 0;
-    __syncthreads();
-    atomicAdd(&t64, s);
-    __syncthreads();
-    if (threadIdx.x == 0) *total64 = t64;
-}
-
+// Second pass: block b starts from the sum of the block sums before it
+// (summed here, in 64 bits, by the whole block: no separate pass over the
+// block sums), scans its own elements and writes them; the last block also
+// writes the 64-bit total (for overflow detection).
 __global__ void k_scan_apply(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, size_t n,
-                             const uint32_t* __restrict__ bsum) {
+                             const uint32_t* __restrict__ bsum, int nb, unsigned long long* __restrict__ total64) {
+    __shared__ unsigned long long red[SC_THREADS / 32];
+    __shared__ unsigned long long base_s;
+    unsigned long long part = 0;
+    for (int j = threadIdx.x; j < (int)blockIdx.x; j += SC_THREADS) part += bsum[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < SC_THREADS / 32; w++) t += red[w];
+        base_s = t;
+        if ((int)blockIdx.x == nb - 1) *total64 = t + bsum[nb - 1];
+    }
+    __syncthreads();
+    const uint32_t base = (uint32_t)base_s;
     const size_t beg = (size_t)blockIdx.x * SC_EPB + (size_t)threadIdx.x * SC_IPT;
     uint32_t v[SC_IPT];
     uint32_t s = 0;
@@ -479,7 +474,7 @@ __global__ void k_scan_apply(const uint32_t* __restrict__ in, uint32_t* __restri
         s += v[k];
     }
     __shared__ uint32_t tot;
-    uint32_t run = block_exclusive_scan(s, &tot) + bsum[blockIdx.x];
+    uint32_t run = block_exclusive_scan(s, &tot) + base;
 #pragma unroll
     for (int k = 0; k < SC_IPT; k++)
         if (beg + k < n) {
@@ -501,8 +496,8 @@ hcgs_status exclusive_scan(hcgs_ctx* ctx, hcgs_saved* s, const uint32_t* in, uin
     uint32_t* bsum = (uint32_t*)s->scan.p;
     unsigned long long* t64 = (unsigned long long*)((char*)s->scan.p + scan_bsum_bytes(n));
     HCGS_KERNEL(ctx, "k_scan_reduce", st, k_scan_reduce<<<(unsigned)nb, SC_THREADS, 0, st>>>(in, n, bsum));
-    HCGS_KERNEL(ctx, "k_scan_top", st, k_scan_top<<<1, SC_THREADS, 0, st>>>(bsum, (int)nb, t64));
-    HCGS_KERNEL(ctx, "k_scan_apply", st, k_scan_apply<<<(unsigned)nb, SC_THREADS, 0, st>>>(in, out, n, bsum));
+    HCGS_KERNEL(ctx, "k_scan_apply", st,
+                k_scan_apply<<<(unsigned)nb, SC_THREADS, 0, st>>>(in, out, n, bsum, (int)nb, t64));
     HCGS_LAUNCH(ctx, "exclusive_scan");
     return HCGS_OK;
 }

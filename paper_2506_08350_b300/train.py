@@ -133,17 +133,17 @@ class HologramTrainer:
         """The optimiser step with the gradients in ``self.g`` (and the
         densification, when its period comes round)."""
         self.t += 1
-        for k in PARAM_NAMES:
-            lr = self.lr(k)
-            if lr <= 0:
-                continue
-            if self.optimizer == "adan":
-                b1, b2, b3 = self.betas
-                self.ctx.adan_step(self.p[k], self.g[k], self.g_prev[k], self.m[k], self.v[k], self.n[k], self.t,
-                                   lr, b1, b2, b3, self.eps, self.weight_decay)
-            else:
-                self.ctx.adam_step(self.p[k], self.g[k], self.m[k], self.v[k], self.t, lr, self.betas[0],
-                                   self.betas[1], self.eps)
+        # every parameter array with a positive learning rate, in one launch
+        ks = [k for k in PARAM_NAMES if self.lr(k) > 0]
+        sel = lambda d: [d[k] for k in ks]
+        if ks and self.optimizer == "adan":
+            b1, b2, b3 = self.betas
+            self.ctx.adan_step_multi(sel(self.p), sel(self.g), sel(self.g_prev), sel(self.m), sel(self.v),
+                                     sel(self.n), self.t, [self.lr(k) for k in ks], b1, b2, b3, self.eps,
+                                     self.weight_decay)
+        elif ks:
+            self.ctx.adam_step_multi(sel(self.p), sel(self.g), sel(self.m), sel(self.v), self.t,
+                                     [self.lr(k) for k in ks], self.betas[0], self.betas[1], self.eps)
         if (self.densify_opts is not None and self.t % self.densify_every == 0
                 and (self.densify_until is None or self.t <= self.densify_until)):
             self.densify()

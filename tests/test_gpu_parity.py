@@ -278,6 +278,46 @@ def test_adam_step(P, ctx):
     assert rel(mt.cpu().numpy(), mr) < 1e-6 and rel(vt.cpu().numpy(), vr) < 1e-6
 
 
+@pytest.mark.parametrize("opt", ["adam", "adan"])
+def test_optimiser_step_on_several_arrays(P, ctx, opt):
+    # One launch over arrays of ragged sizes (an empty one, one below and
+    # several above the 1024 elements a block takes) updates every element
+    # exactly as one call per array does, with each array's own learning rate;
+    # the Adam result also matches the oracle's update.
+    rng = np.random.default_rng(5)
+    sizes = [1, 0, 1023, 1025, 100003, 7]
+    lrs = [1e-2, 3e-3, 5e-4, 2e-2, 1e-3, 0.1]
+    nstate = 2 if opt == "adam" else 4
+    # p, g, then the state (Adam's second moment non-negative)
+    host = [[np.abs(x) if opt == "adam" and j == 3 else x
+             for j, x in enumerate(rng.normal(size=n).astype(np.float32) for _ in range(2 + nstate))]
+            for n in sizes]
+    a = [[torch.from_numpy(x.copy()).cuda() for x in arrs] for arrs in host]
+    b = [[torch.from_numpy(x.copy()).cuda() for x in arrs] for arrs in host]
+    for step in (1, 2, 3):  # Adan's first two steps take their own branches
+        cols = list(zip(*a))
+        if opt == "adam":
+            ctx.adam_step_multi(list(cols[0]), list(cols[1]), list(cols[2]), list(cols[3]), step, lrs)
+            for (pb, gb, mb, vb), lr in zip(b, lrs):
+                ctx.adam_step(pb, gb, mb, vb, step, lr)
+        else:
+            ctx.adan_step_multi(list(cols[0]), list(cols[1]), list(cols[2]), list(cols[3]), list(cols[4]),
+                                list(cols[5]), step, lrs, weight_decay=0.01)
+            for (pb, gb, gpb, mb, vb, nb), lr in zip(b, lrs):
+                ctx.adan_step(pb, gb, gpb, mb, vb, nb, step, lr, weight_decay=0.01)
+    torch.cuda.synchronize()
+    for arrs_a, arrs_b in zip(a, b):
+        for xa, xb in zip(arrs_a, arrs_b):
+            assert torch.equal(xa, xb)
+    if opt == "adam":
+        n = sizes[4]
+        p0, g0, m0, v0 = (x.astype(np.float64) for x in host[4])
+        pr, mr, vr = p0, m0, v0
+        for step in (1, 2, 3):
+            pr, mr, vr = oracle.adam_step(pr, g0, mr, vr, step, lrs[4])
+        assert rel(a[4][0].cpu().numpy(), pr) < 1e-6 and a[4][0].numel() == n
+
+
 def _bf16(a):
     t = torch.from_numpy(np.asarray(a, dtype=np.float32)).to(torch.bfloat16)
     return t
