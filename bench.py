@@ -80,6 +80,9 @@ def parse():
                     help="time only the two objectives on one view of the workload's optics and print them")
     ap.add_argument("--mlp-only", action="store_true",
                     help="time only the learned-initialisation network (forward, reverse mode, fit step) and print it")
+    ap.add_argument("--profile-train-step", action="store_true",
+                    help="run five training steps at the ring configuration, then one between "
+                         "cudaProfilerStart/Stop (for a profiler's launch list); prints nothing else")
     ap.add_argument("--footprint", type=int, default=0, choices=[0, 1, 2],
                     help="footprint tier of the timed step: 0 FP32 (the headline), 1 FP16x2, 2 BF16x2")
     return ap.parse_args()
@@ -721,6 +724,34 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_profile_train_step(args):
+    """Five training steps of the ring configuration (Adam, focal-stack loss,
+    one view per step), then one more inside cudaProfilerStart/Stop, so that
+    a profiler started with profiling off records exactly one step."""
+    import torch
+    torch.cuda.set_device(0)
+    import paper_2506_08350_b300 as P
+    from paper_2506_08350_b300.train import HologramTrainer, focal_stack
+    wl = S.workload("c3_512_L8_N500k")
+    o = wl.optics
+    vms = [torch.from_numpy(v[None].copy()).cuda() for v in S.ring_cameras(4).astype(np.float32)]
+    it = torch.from_numpy(S.intrinsics(o.H, o.W).astype(np.float32)[None]).cuda()
+    ctx = P.Context(0)
+    teacher = S.make_gaussians(wl.N, o.L, o.C, o.H, o.W, seed=3)
+    tdev = {k: torch.from_numpy(teacher[k]).cuda() for k in P.PARAM_NAMES}
+    targets = [focal_stack(ctx, tdev, vm, it, o) for vm in vms]
+    p = {k: t.clone() for k, t in tdev.items()}
+    tr = HologramTrainer(ctx, p, o, dict(P.DEFAULT_OPTS))
+    for s in range(5):
+        tr.step(vms[s % 4], it, targets[s % 4])
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    tr.step(vms[1], it, targets[1])
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    ctx.close()
+
+
 def run_objective_only(args):
     import torch
     torch.cuda.set_device(0)
@@ -751,6 +782,8 @@ def main():
         run_objective_only(args)
     elif args.mlp_only:
         run_mlp_only(args)
+    elif args.profile_train_step:
+        run_profile_train_step(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
