@@ -55,7 +55,7 @@ def test_null_context_is_rejected_without_cuda(lib):
     for name in ("hcgs_project", "hcgs_rasterize_planes", "hcgs_asm_propagate", "hcgs_render_view",
                  "hcgs_rasterize_planes_backward", "hcgs_project_backward", "hcgs_render_view_backward",
                  "hcgs_focal_stack_loss", "hcgs_adam_step", "hcgs_mlp_forward", "hcgs_mlp_backward",
-                 "hcgs_asm_propagate_backward"):
+                 "hcgs_asm_propagate_backward", "hcgs_adam_step_multi", "hcgs_adan_step_multi"):
         f = getattr(lib, name)
         f.restype = ctypes.c_int
         args = [None] * 20
