@@ -135,7 +135,10 @@ class HologramTrainer:
         self.t += 1
         # every parameter array with a positive learning rate, in one launch
         ks = [k for k in PARAM_NAMES if self.lr(k) > 0]
-        sel = lambda d: [d[k] for k in ks]
+
+        def sel(d):
+            return [d[k] for k in ks]
+
         if ks and self.optimizer == "adan":
             b1, b2, b3 = self.betas
             self.ctx.adan_step_multi(sel(self.p), sel(self.g), sel(self.g_prev), sel(self.m), sel(self.v),
