@@ -11,7 +11,7 @@ compared with.
 
 Python here only sequences library calls and keeps tensors; every
 arithmetic step runs in libhcgs kernels (``hcgs_init_*``, ``hcgs_mlp_*``,
-``hcgs_adam_step``, ``hcgs_cast_bf16`` and the render path).
+``hcgs_adam_step_multi``, ``hcgs_cast_bf16`` and the render path).
 """
 from __future__ import annotations
 
@@ -64,9 +64,9 @@ class InitNet:
         self.ctx.mlp_mse_loss(y, target, K, self.loss, gy)
         self.ctx.mlp_backward(x, self.W16, self.b32, gy, self.gW, self.gb)
         self.t += 1
-        for k in range(len(DIMS)):
-            self.ctx.adam_step(self.W32[k], self.gW[k], self.mW[k], self.vW[k], self.t, lr)
-            self.ctx.adam_step(self.b32[k], self.gb[k], self.mb[k], self.vb[k], self.t, lr)
+        # the eight weight and bias arrays in one launch
+        self.ctx.adam_step_multi(self.W32 + self.b32, self.gW + self.gb, self.mW + self.mb, self.vW + self.vb,
+                                 self.t, [lr] * (2 * len(DIMS)))
         self._sync()
         return self.loss
 
