@@ -378,7 +378,9 @@ hcgs_status hcgs_adan_step_multi(hcgs_ctx* ctx, int k, float* const* p, const fl
  *       opacity logit 1, RGB 3, padding 2)
  *   W1  device [128][16], W2, W3 [128][128], W4 [16][128] bf16 (row = output)
  *   b1, b2, b3 device [128], b4 [16] float
- *   y   device [N][16] float (output) */
+ *   y   device [N][16] float (output)
+ * 0 <= N <= 2^30 (row indices stay in 32-bit arithmetic), else
+ * HCGS_ERR_INVALID_ARG; the same bound holds for hcgs_mlp_backward. */
 hcgs_status hcgs_mlp_forward(hcgs_ctx* ctx, const uint16_t* x, int N, const uint16_t* W1,
                              const uint16_t* W2, const uint16_t* W3, const uint16_t* W4,
                              const float* b1, const float* b2, const float* b3, const float* b4,

@@ -946,7 +946,7 @@ hcgs_status hcgs_mlp_forward(hcgs_ctx* ctx, const uint16_t* x, int N, const uint
                              const uint16_t* W3, const uint16_t* W4, const float* b1, const float* b2,
                              const float* b3, const float* b4, float* y, void* stream) {
     if (!ctx) return HCGS_ERR_INVALID_ARG;
-    REQUIRE(ctx, N >= 0, "N must be >= 0");
+    REQUIRE(ctx, N >= 0 && N <= (1 << 30), "N must be in [0, 2^30]");
     if (N == 0) return HCGS_OK;
     REQUIRE(ctx, x && W1 && W2 && W3 && W4 && b1 && b2 && b3 && b4 && y, "NULL argument");
     cudaSetDevice(ctx->device);
@@ -961,7 +961,7 @@ hcgs_status hcgs_mlp_backward(hcgs_ctx* ctx, const uint16_t* x, int N, const uin
                               float* gW3, float* gW4, float* gb1, float* gb2, float* gb3, float* gb4,
                               void* stream) {
     if (!ctx) return HCGS_ERR_INVALID_ARG;
-    REQUIRE(ctx, N >= 0, "N must be >= 0");
+    REQUIRE(ctx, N >= 0 && N <= (1 << 30), "N must be in [0, 2^30]");
     REQUIRE(ctx, x && W1 && W2 && W3 && W4 && b1 && b2 && b3 && b4 && gy, "NULL argument");
     REQUIRE(ctx, gW1 && gW2 && gW3 && gW4 && gb1 && gb2 && gb3 && gb4, "NULL gradient argument");
     cudaSetDevice(ctx->device);
