@@ -286,7 +286,7 @@ __device__ __forceinline__ RsSeg rs_segment(int seg, size_t seglen, const uint32
 }
 
 __global__ void k_rs_hist(const uint32_t* __restrict__ keys, size_t seglen, const uint32_t* __restrict__ segoff,
-                          uint32_t keystep, int shift, int nblk, uint32_t* __restrict__ hist) {
+                          uint32_t keystep, int shift, uint32_t mask, int nblk, uint32_t* __restrict__ hist) {
     __shared__ uint32_t h[256];
     const int seg = blockIdx.y, blk = blockIdx.x;
     h[threadIdx.x] = 0;
@@ -297,7 +297,7 @@ __global__ void k_rs_hist(const uint32_t* __restrict__ keys, size_t seglen, cons
 #pragma unroll
     for (int r = 0; r < RS_IPT; r++) {
         const size_t idx = beg + (size_t)r * RS_THREADS + threadIdx.x;
-        if (idx < sg.len) atomicAdd(&h[((k[idx] - sg.kb) >> shift) & 255u], 1u);
+        if (idx < sg.len) atomicAdd(&h[((k[idx] - sg.kb) >> shift) & mask], 1u);
     }
     __syncthreads();
     hist[((size_t)seg * 256 + threadIdx.x) * nblk + blk] = h[threadIdx.x];
@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t* __res
                                                            const uint32_t* __restrict__ vin,
                                                            uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                                            size_t seglen, const uint32_t* __restrict__ segoff,
-                                                           uint32_t keystep, int shift, int nblk,
+                                                           uint32_t keystep, int shift, uint32_t mask, int nblk,
                                                            const uint32_t* __restrict__ pos) {
     constexpr int NW = RS_THREADS / 32, PW = RS_KPB / NW;  // warps, elements per warp
     __shared__ uint32_t wh[NW][256];  // per-warp digit counters, then per-warp bases within a digit
@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t* __res
 #pragma unroll
     for (int r = 0; r < RS_IPT; r++) {
         const bool ok = warp * PW + r * 32 + lane < nb;
-        const uint32_t d = ok ? (((key[r] - kb) >> shift) & 255u) : 256u;
+        const uint32_t d = ok ? (((key[r] - kb) >> shift) & mask) : 256u;
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         const int leader = __ffs(peers) - 1;
         const uint32_t lrank = __popc(peers & lt);
@@ -381,7 +381,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t* __res
 #pragma unroll
     for (int r = 0; r < RS_IPT; r++) {
         if (warp * PW + r * 32 + lane < nb) {
-            const uint32_t d = ((key[r] - kb) >> shift) & 255u;
+            const uint32_t d = ((key[r] - kb) >> shift) & mask;
             const uint32_t lp = loff[d] + wh[warp][d] + rk[r];
             sk[lp] = key[r];
             sv[lp] = val[r];
@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t* __res
     __syncthreads();
     for (int i = t; i < nb; i += RS_THREADS) {
         const uint32_t k = sk[i];
-        const uint32_t d = ((k - kb) >> shift) & 255u;
+        const uint32_t d = ((k - kb) >> shift) & mask;
         const uint32_t p = gbase[d] + (uint32_t)i - loff[d];
         kout[p] = k;
         vout[p] = sv[i];
@@ -538,20 +538,26 @@ hcgs_status radix_sort(hcgs_ctx* ctx, hcgs_saved* s, uint32_t* keys, uint32_t* v
     HCGS_CUDA(ctx, grow(ctx, s->hist, nh * sizeof(uint32_t), &s->bytes));
     uint32_t* hist = (uint32_t*)s->hist.p;
     int cur = 0;
-    for (int shift = 0; shift < nbits; shift += 8) {
+    // as few passes of at most 8 bits as cover nbits, the bits split evenly
+    // between them (13 bits: 7 + 6 rather than 8 + 5, so that the first
+    // pass scatters into fewer, longer runs)
+    const int npass = (nbits + 7) / 8;
+    const int width = (nbits + npass - 1) / npass;
+    for (int shift = 0; shift < nbits; shift += width) {
+        const uint32_t mask = (1u << width) - 1u;
         uint32_t* kin = keys + (size_t)cur * total;
         uint32_t* vin = vals + (size_t)cur * total;
         uint32_t* kout = keys + (size_t)(1 - cur) * total;
         uint32_t* vout = vals + (size_t)(1 - cur) * total;
         dim3 grid(nblk, nseg);
         HCGS_KERNEL(ctx, "k_rs_hist", st,
-                    k_rs_hist<<<grid, RS_THREADS, 0, st>>>(kin, seglen, segoff, keystep, shift, nblk, hist));
+                    k_rs_hist<<<grid, RS_THREADS, 0, st>>>(kin, seglen, segoff, keystep, shift, mask, nblk, hist));
         HCGS_LAUNCH(ctx, "k_rs_hist");
         hcgs_status e = exclusive_scan(ctx, s, hist, hist, nh, st);
         if (e) return e;
         HCGS_KERNEL(ctx, "k_rs_scatter", st,
                     k_rs_scatter<<<grid, RS_THREADS, 0, st>>>(kin, vin, kout, vout, seglen, segoff, keystep, shift,
-                                                              nblk, hist));
+                                                              mask, nblk, hist));
         HCGS_LAUNCH(ctx, "k_rs_scatter");
         cur = 1 - cur;
     }
