@@ -123,12 +123,24 @@ __device__ __forceinline__ bool strip_hits(float4 r0, float Cc, float o, float x
     return m <= k2;
 }
 
-// Per-entry coefficients staged with the record.  FP32 tier: the base-2
-// exponent of o G = 2^(A' dx^2 + B' dx dy + C' dy^2 + log2 o).  FP16x2 tier:
-// the normalised-frame factors sqrt(A), sqrt(C) and rho2 = 2 B / sqrt(A C).
+// In the reduced-precision tiers, entries of opacity above this are still
+// evaluated in FP32: the adjoint's dL/dalpha carries S / (1 - alpha), which
+// multiplies the relative error of a reduced-precision alpha by
+// alpha / (1 - alpha) (3 at alpha = 0.75, 99 at 0.99).  The choice depends
+// on the record alone, so the forward and the adjoint make it alike.
+constexpr float TIER_FP32_OPACITY = 0.75f;
+template <int FT>
+__device__ __forceinline__ bool tier_half(float o) {
+    return FT != 0 && o <= TIER_FP32_OPACITY;
+}
+
+// Per-entry coefficients staged with the record.  FP32 evaluation: the
+// base-2 exponent of o G = 2^(A' dx^2 + B' dx dy + C' dy^2 + log2 o).
+// Reduced precision (tier_half): the normalised-frame factors sqrt(A),
+// sqrt(C) and rho2 = 2 B / sqrt(A C).
 template <int FT>
 __device__ __forceinline__ float4 entry_coeffs(float4 q0, float4 q1) {
-    if (FT) {
+    if (tier_half<FT>(q1.y)) {
         const float sa = sqrtf(q0.z), sc = sqrtf(q1.x);
         return make_float4(sa, sc, 2.f * q0.w / (sa * sc), 0.f);
     }
@@ -267,7 +279,7 @@ template <int FT, bool CL>
 __device__ __forceinline__ void eval_entry(const EntryX& x, float2 pyA, float2 pyB, float4 r0, float4 r1, float4 k,
                                            float amax, float2& dyA, float2& ogA, float2& aA, float2& dyB,
                                            float2& ogB, float2& aB) {
-    if constexpr (FT != 0) {
+    if (tier_half<FT>(r1.y)) {
         // half (FT 1) or bfloat16 (FT 2) precision for -c w^2 and its exp();
         // u = dx sqrt(A) and the factor F are fixed per thread and entry
         const float u = x.dx * k.x;
@@ -275,8 +287,8 @@ __device__ __forceinline__ void eval_entry(const EntryX& x, float2 pyA, float2 p
         constexpr float sqc = 0.84932180028801904f;  // sqrt(c)
         const float ru = 0.5f * k.z * u;            // rho u (k.z = 2 rho)
         const float F = r1.y * ex2_approx(c * fmaf(ru, ru, -u * u));
-        eval_pair_h<FT, CL>(pyA, r0, sqc * k.y, sqc * ru, F, amax, dyA, ogA, aA);
-        eval_pair_h<FT, CL>(pyB, r0, sqc * k.y, sqc * ru, F, amax, dyB, ogB, aB);
+        eval_pair_h<FT == 0 ? 1 : FT, CL>(pyA, r0, sqc * k.y, sqc * ru, F, amax, dyA, ogA, aA);
+        eval_pair_h<FT == 0 ? 1 : FT, CL>(pyB, r0, sqc * k.y, sqc * ru, F, amax, dyB, ogB, aB);
     } else {
         dyA = __fadd2_rn(pyA, f2(-r0.y));
         float2 e = __ffma2_rn(f2(x.bdx), dyA, f2(x.t0));

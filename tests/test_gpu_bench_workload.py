@@ -2,7 +2,7 @@
 views of 1080 x 1920, three wavelengths, 12 planes over 0-12 mm, rendered
 and differentiated in one batch, at 1M Gaussians (the bench workload; FP32
 path, FP16x2 and BF16x2 footprint tiers) and at 2M Gaussians (configuration
-c4; FP32 path and FP16x2 tier), so that the instance buffers sized from the
+c4; all three tiers), so that the instance buffers sized from the
 device's instance count and the strip lists are exercised at the largest
 configuration; and the training configuration's render (c3: one view of
 512 x 512, three wavelengths, 8 planes, 500k Gaussians; all three tiers).
@@ -35,7 +35,7 @@ torch = pytest.importorskip("torch")
 TOL = {0: (1e-4, 1e-3), 1: (1e-2, 1e-2), 2: (1e-2, 1e-2)}
 # workload: (footprint tiers, sampled view, row band)
 WORKLOADS = {"1080p_rgb_L12_N1M_V16": ((0, 1, 2), 5, 480, 576),
-             "c4_1080p_L12_N2M_V16": ((0, 1), 5, 480, 576),
+             "c4_1080p_L12_N2M_V16": ((0, 1, 2), 5, 480, 576),
              "c3_512_L8_N500k": ((0, 1, 2), 0, 224, 288)}
 CASES = [(w, fp) for w, spec in WORKLOADS.items() for fp in spec[0]]
 
