@@ -405,7 +405,7 @@ def test_bounded_wait_timeout_is_reported_and_context_recovers(P, ctx):
     assert torch.equal(holo, ref)
 
 
-@pytest.mark.parametrize("footprint", [0, 1])
+@pytest.mark.parametrize("footprint", [0, 1, 2])
 def test_render_max_wavelengths_and_planes(P, ctx, footprint):
     # the largest channel and plane counts the API takes (C = 4, L = 16):
     # four-channel records (NR = 4) and sixteen plane lists, forward and adjoint
